@@ -1,0 +1,29 @@
+"""Far field and radar cross section of the equivalent current J_Delta radiating
+in free space (Sec. IV-A: RCS compared with the Mie series).
+
+With j_Delta = j k0 J_Delta (RWG coefficients) and exp(+j w t), the scattered far
+field is E_s = -eta0 exp(-j k0 r)/(4 pi r) (I - rr) . sum_n j_Delta,n N_n(rhat),
+N_n = int f_n(r') exp(+j k0 rhat . r') dS' (6-point rule), so that the bistatic
+RCS is sigma = eta0^2 |(I - rr) . F|^2 / (4 pi |E0|^2).
+"""
+import numpy as np
+
+from . import quadrature as Q
+from .fill import ETA0
+
+
+def rcs(mesh, k0, jd, theta, phi=0.0, E0=1.0):
+    theta = np.atleast_1d(np.asarray(theta, float))
+    phi = np.broadcast_to(np.asarray(phi, float), theta.shape)
+    rhat = np.stack([np.sin(theta) * np.cos(phi), np.sin(theta) * np.sin(phi), np.cos(theta)], axis=1)
+    A = mesh.xyz[mesh.tri]
+    rq = Q.points(A)
+    wq = Q.weights(mesh.area)
+    Fv = np.zeros((len(theta), 3), dtype=complex)
+    ph = np.exp(1j * k0 * np.einsum('tqd,ad->atq', rq, rhat))            # (ang, nt, 6)
+    for i in range(3):
+        fi = (rq - A[:, i][:, None, :]) * (mesh.E.tri_sign[:, i] / (2 * mesh.area))[:, None, None]
+        c = jd[mesh.E.tri_edge[:, i]]
+        Fv += np.einsum('t,tq,atq,tqd->ad', c, wq, ph, fi)
+    Fperp = Fv - rhat * np.einsum('ad,ad->a', rhat, Fv)[:, None]
+    return ETA0 ** 2 * np.sum(np.abs(Fperp) ** 2, axis=1) / (4 * np.pi * abs(E0) ** 2)

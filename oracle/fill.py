@@ -1,0 +1,253 @@
+"""Galerkin fill of the operators of Sec. II-B and II-C, plainly, in FP64.
+
+Readings of the discretisation (Eqs. opLAhgf, opLphihgf, opKhgf, AEFIEintdis):
+
+    L^A[m, n]   = int_T f_m(r) . int_T' f_n(r') G(r, r') dS' dS          (RWG x RWG)
+    L^phi[p, q] = int int h_p(r) h_q(r') G(r, r') dS' dS                (pulse x pulse)
+    Kbar[m, n]  = int f_m(r) . PV int grad_r G(r, r') x b_n(r') dS' dS    (RWG x BC)
+    I_x[m, n]   = int (n x f_m) . b_n dS                                 (Gram, BC tested with n x RWG)
+    e_inc[m]    = int f_m . E_inc / eta0 dS
+
+with G = exp(-j k R) / (4 pi R) (Eq. hgf), time convention exp(+j w t).
+
+Quadrature: the 6-point Dunavant rule on the test and on the source triangle.
+Touching pairs (sharing at least one point) use singularity extraction: for L the
+inner integral of 1/(4 pi R) - k^2 R/(8 pi) is done in closed form and the
+remainder G - 1/(4 pi R) + k^2 R/(8 pi) by the same 6-point rule; for Kbar the
+static gradient grad 1/(4 pi R) is done in closed form.  A barycentric source
+triangle lying inside the test triangle contributes zero to Kbar (coplanar: the
+integrand is normal to the plane while f_m is tangential).  BC functions enter as
+sums of barycentric RWG functions (``mesh.C``), see ``oracle.topology``.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import quadrature as Q
+from .singular import integrals
+
+C0 = 299792458.0
+MU0 = 4e-7 * np.pi
+EPS0 = 1.0 / (MU0 * C0 ** 2)
+ETA0 = MU0 * C0
+
+CHUNK = 4096
+
+
+def green(k, R):
+    return np.exp(-1j * k * R) / (4 * np.pi * R)
+
+
+def green_smooth(k, R):
+    """G - 1/(4 pi R) + k^2 R / (8 pi); a Taylor series where |k R| is small."""
+    x = k * R
+    with np.errstate(invalid='ignore', divide='ignore'):
+        full = (np.exp(-1j * x) - 1.0) / (4 * np.pi * R) + k * k * R / (8 * np.pi)
+    ser = np.zeros_like(full)
+    for n in range(1, 12):
+        if n == 2:
+            continue
+        ser = ser + (-1j * k) ** n * R ** (n - 1) / np.prod(np.arange(1, n + 1), dtype=float)
+    ser = ser / (4 * np.pi)
+    return np.where(np.abs(x) < 0.05, ser, full)
+
+
+def grad_green_factor(k, R):
+    """g1 with grad_r G = (r - r') g1: g1 = -(1 + j k R) exp(-j k R) / (4 pi R^3)."""
+    return -(1 + 1j * k * R) * np.exp(-1j * k * R) / (4 * np.pi * R ** 3)
+
+
+def grad_green_smooth_factor(k, R):
+    """g1 of G - 1/(4 pi R): (1 - (1 + j k R) exp(-j k R)) / (4 pi R^3), series for small |k R|."""
+    x = 1j * k * R
+    full = (1.0 - (1 + x) * np.exp(-x)) / (4 * np.pi * R ** 3)
+    ser = np.zeros_like(full)
+    for n in range(2, 14):
+        ser = ser + (-1) ** n * (n - 1) * x ** n / np.prod(np.arange(1, n + 1), dtype=float)
+    ser = ser / (4 * np.pi * R ** 3)
+    return np.where(np.abs(x) < 0.05, ser, full)
+
+
+# ----------------------------------------------------------------------------- L^A and L^phi
+
+def _touch_primal(tri, a, b):
+    ta, tb = tri[a], tri[b]
+    return (ta[:, :, None] == tb[:, None, :]).any(axis=(1, 2))
+
+
+def _L_pairs(mesh, k, ta, tb):
+    """Local RWG x RWG (P, 3, 3) and pulse x pulse (P,) integrals of triangle pairs."""
+    xyz, tri = mesh.xyz, mesh.tri
+    A, B = xyz[tri[ta]], xyz[tri[tb]]
+    rq, rs = Q.points(A), Q.points(B)
+    wq, ws = Q.weights(mesh.area[ta]), Q.weights(mesh.area[tb])
+    fa = rq[:, :, None, :] - A[:, None, :, :]          # r - v_i   (P, 6, 3, 3)
+    fb = rs[:, :, None, :] - B[:, None, :, :]          # r' - w_j
+    scale = (mesh.E.tri_sign[ta][:, :, None] * mesh.E.tri_sign[tb][:, None, :]
+             / (4 * mesh.area[ta] * mesh.area[tb])[:, None, None])
+    la = np.zeros((len(ta), 3, 3), dtype=complex)
+    lp = np.zeros(len(ta), dtype=complex)
+    touch = _touch_primal(tri, ta, tb)
+    far = ~touch
+    if far.any():
+        R = np.linalg.norm(rq[far][:, :, None, :] - rs[far][:, None, :, :], axis=-1)
+        G = green(k, R) * wq[far][:, :, None] * ws[far][:, None, :]
+        la[far] = np.einsum('pqs,pqid,psjd->pij', G, fa[far], fb[far], optimize='greedy')
+        lp[far] = G.sum(axis=(1, 2))
+    if touch.any():
+        idx = np.nonzero(touch)[0]
+        P = len(idx)
+        R = np.linalg.norm(rq[idx][:, :, None, :] - rs[idx][:, None, :, :], axis=-1)
+        Gs = green_smooth(k, R) * ws[idx][:, None, :]                        # (P, 6q, 6s)
+        inner_a = np.einsum('pqs,psjd->pqjd', Gs, fb[idx])                   # (P, 6, 3, 3)
+        inner_p = Gs.sum(axis=2)                                             # (P, 6)
+        r = rq[idx].reshape(-1, 3)
+        T = np.repeat(B[idx], 6, axis=0)
+        I = integrals(r, T)
+        rho = I['rho'].reshape(P, 6, 1, 3)
+        w = B[idx][:, None, :, :]                                            # (P, 1, 3j, 3)
+        por = I['p_over_r'].reshape(P, 6, 1, 3)
+        pr = I['p_r'].reshape(P, 6, 1, 3)
+        inv_r = I['inv_r'].reshape(P, 6, 1, 1)
+        rr = I['r'].reshape(P, 6, 1, 1)
+        inner_a = inner_a + (por + (rho - w) * inv_r) / (4 * np.pi) \
+            - k * k * (pr + (rho - w) * rr) / (8 * np.pi)
+        inner_p = inner_p + I['inv_r'].reshape(P, 6) / (4 * np.pi) - k * k * I['r'].reshape(P, 6) / (8 * np.pi)
+        la[idx] = np.einsum('pq,pqid,pqjd->pij', wq[idx], fa[idx], inner_a)
+        lp[idx] = np.einsum('pq,pq->p', wq[idx], inner_p)
+    return la * scale, lp / (mesh.area[ta] * mesh.area[tb])
+
+
+def fill_L(mesh, k, tris):
+    """L^A over the edges of triangles ``tris`` and L^phi over ``tris`` (whole objects)."""
+    tris = np.asarray(tris)
+    e_of = mesh.E.tri_edge
+    edges = np.unique(e_of[tris])
+    eidx = -np.ones(mesh.ne, dtype=np.int64)
+    eidx[edges] = np.arange(len(edges))
+    tidx = -np.ones(mesh.nt, dtype=np.int64)
+    tidx[tris] = np.arange(len(tris))
+    LA = np.zeros((len(edges), len(edges)), dtype=complex)
+    LP = np.zeros((len(tris), len(tris)), dtype=complex)
+    ta_all = np.repeat(tris, len(tris))
+    tb_all = np.tile(tris, len(tris))
+    for c in range(0, len(ta_all), CHUNK):
+        ta, tb = ta_all[c:c + CHUNK], tb_all[c:c + CHUNK]
+        la, lp = _L_pairs(mesh, k, ta, tb)
+        rows = eidx[e_of[ta]][:, :, None] * np.ones((1, 1, 3), dtype=np.int64)
+        cols = eidx[e_of[tb]][:, None, :] * np.ones((1, 3, 1), dtype=np.int64)
+        np.add.at(LA, (rows.ravel(), cols.ravel()), la.ravel())
+        np.add.at(LP, (tidx[ta], tidx[tb]), lp)
+    return LA, LP
+
+
+# ----------------------------------------------------------------------------- Kbar
+
+def _touch_bary(mesh, ta, cb):
+    """0 = far, 1 = touching (extraction), 2 = child of the test triangle (zero)."""
+    nv = mesh.nv
+    parent = mesh.bparent[cb]
+    bv = mesh.btri[cb]                                               # (P, 3)
+    tv = mesh.tri[ta]                                                # (P, 3)
+    tm = nv + mesh.E.tri_edge[ta]                                    # midpoint ids of the test edges
+    keys = np.concatenate([tv, tm], axis=1)                          # (P, 6)
+    touch = (bv[:, :, None] == keys[:, None, :]).any(axis=(1, 2))
+    out = np.where(touch, 1, 0)
+    return np.where(parent == ta, 2, out)
+
+
+def _K_pairs(mesh, k, ta, cb):
+    """Local RWG (test, primal) x barycentric RWG (source) integrals of Kbar, (P, 3, 3)."""
+    A = mesh.xyz[mesh.tri[ta]]
+    Bt = mesh.bxyz[mesh.btri[cb]]
+    rq, rs = Q.points(A), Q.points(Bt)
+    wq, ws = Q.weights(mesh.area[ta]), Q.weights(mesh.barea[cb])
+    fa = (rq[:, :, None, :] - A[:, None, :, :]) * \
+        (mesh.E.tri_sign[ta] / (2 * mesh.area[ta][:, None]))[:, None, :, None]          # f_i(r_q)
+    sb = mesh.bE.tri_sign[cb] / (2 * mesh.barea[cb][:, None])                            # (P, 3)
+    gb = (rs[:, :, None, :] - Bt[:, None, :, :]) * sb[:, None, :, None]                  # g_j(r_s)
+    kind = _touch_bary(mesh, ta, cb)
+    out = np.zeros((len(ta), 3, 3), dtype=complex)
+    far = np.nonzero(kind == 0)[0]
+    if len(far):
+        d = rq[far][:, :, None, :] - rs[far][:, None, :, :]                               # r - r'
+        R = np.linalg.norm(d, axis=-1)
+        g1 = grad_green_factor(k, R) * wq[far][:, :, None] * ws[far][:, None, :]
+        # inner[p, q, j] = sum_s g1 (r_q - r'_s) x g_j(r'_s);  out = sum_q f_i(r_q) . inner
+        X = np.cross(d[:, :, :, None, :], gb[far][:, None, :, :, :])                     # (P, q, s, j, 3)
+        inner = np.matmul(g1[:, :, None, :], X.reshape(len(far), 6, 6, 9)).reshape(len(far), 6, 3, 3)
+        out[far] = np.einsum('pqia,pqja->pij', fa[far], inner)
+    near = np.nonzero(kind == 1)[0]
+    if len(near):
+        P = len(near)
+        d = rq[near][:, :, None, :] - rs[near][:, None, :, :]
+        R = np.linalg.norm(d, axis=-1)
+        g1 = grad_green_smooth_factor(k, R) * ws[near][:, None, :]
+        X = np.cross(d[:, :, :, None, :], gb[near][:, None, :, :, :])
+        inner = np.matmul(g1[:, :, None, :], X.reshape(P, 6, 6, 9)).reshape(P, 6, 3, 3)
+        I = integrals(rq[near].reshape(-1, 3), np.repeat(Bt[near], 6, axis=0))
+        gs = I['grad_inv_r'].reshape(P, 6, 1, 3) / (4 * np.pi)
+        # static part: [int grad 1/(4 pi R) dS'] x g_j evaluated through (r - r') x (r' - w) = (r - r') x (r - w)
+        rw = (rq[near][:, :, None, :] - Bt[near][:, None, :, :]) * sb[near][:, None, :, None]
+        inner = inner + np.cross(np.broadcast_to(gs, rw.shape), rw)
+        out[near] = np.einsum('pq,pqid,pqjd->pij', wq[near], fa[near], inner)
+    return out
+
+
+def fill_Kbar(mesh, k, obj):
+    """Kbar (RWG test x BC source) of object ``obj``: (ne_o x ne_o), plus its barycentric form."""
+    t0, t1 = mesh.tri_range[obj]
+    e0, e1 = mesh.edge_range[obj]
+    bidx = np.nonzero(mesh.bE.obj == obj)[0]
+    b0 = bidx[0]
+    tris = np.arange(t0, t1)
+    kids = np.arange(6 * t0, 6 * t1)
+    Kb = np.zeros((e1 - e0, len(bidx)), dtype=complex)
+    ta_all = np.repeat(tris, len(kids))
+    cb_all = np.tile(kids, len(tris))
+    for c in range(0, len(ta_all), CHUNK):
+        ta, cb = ta_all[c:c + CHUNK], cb_all[c:c + CHUNK]
+        loc = _K_pairs(mesh, k, ta, cb)
+        rows = (mesh.E.tri_edge[ta] - e0)[:, :, None] * np.ones((1, 1, 3), dtype=np.int64)
+        cols = (mesh.bE.tri_edge[cb] - b0)[:, None, :] * np.ones((1, 3, 1), dtype=np.int64)
+        np.add.at(Kb, (rows.ravel(), cols.ravel()), loc.ravel())
+    Cobj = mesh.C[b0:b0 + len(bidx), e0:e1].toarray()
+    return Kb @ Cobj, Kb
+
+
+# ----------------------------------------------------------------------------- Gram I_x
+
+def fill_Ix(mesh):
+    """I_x[m, n] = int (n x f_m) . b_n over the whole mesh (block diagonal by object)."""
+    Ixb = np.zeros((mesh.ne, mesh.bE.ne))
+    for t in range(mesh.nt):
+        A = mesh.xyz[mesh.tri[t]]
+        n = mesh.normal[t]
+        for c in range(6 * t, 6 * t + 6):
+            Bt = mesh.bxyz[mesh.btri[c]]
+            rs = Q.points(Bt[None])[0]
+            ws = Q.weights(mesh.barea[c:c + 1])[0]
+            for i in range(3):
+                fi = mesh.E.tri_sign[t, i] * (rs - A[i]) / (2 * mesh.area[t])
+                nf = np.cross(n, fi)
+                for j in range(3):
+                    gj = mesh.bE.tri_sign[c, j] * (rs - Bt[j]) / (2 * mesh.barea[c])
+                    Ixb[mesh.E.tri_edge[t, i], mesh.bE.tri_edge[c, j]] += np.sum(ws * np.einsum('qd,qd->q', nf, gj))
+    return Ixb @ mesh.C.toarray()
+
+
+# ----------------------------------------------------------------------------- excitation
+
+def plane_wave(mesh, k0, khat, pol, E0=1.0):
+    """e_inc[m] = int f_m . E_inc / eta0 with E_inc = pol E0 exp(-j k0 khat . r)."""
+    khat = np.asarray(khat, float)
+    pol = np.asarray(pol, complex)
+    A = mesh.xyz[mesh.tri]
+    rq = Q.points(A)
+    wq = Q.weights(mesh.area)
+    Einc = E0 * pol[None, None, :] * np.exp(-1j * k0 * rq @ khat)[..., None] / ETA0   # (nt, 6, 3)
+    b = np.zeros(mesh.ne, dtype=complex)
+    for i in range(3):
+        fi = (rq - A[:, i][:, None, :]) * (mesh.E.tri_sign[:, i] / (2 * mesh.area))[:, None, None]
+        np.add.at(b, mesh.E.tri_edge[:, i], np.einsum('tq,tqd,tqd->t', wq, fi, Einc))
+    return b
