@@ -1,0 +1,209 @@
+/*
+ * sldm.h - C ABI of the GB300 (sm_103a) implementation of the single-layer
+ * dual-mesh boundary element method (SLDM-BEM) of Sharma & Triverio,
+ * "A Single-Layer Dual-Mesh Boundary Element Method for Multiscale
+ * Electromagnetic Modeling of Penetrable Objects in Layered Media",
+ * arXiv:2106.06184.
+ *
+ * The library computes, on one GPU, the data-parallel hot path of the method:
+ * the triangle-pair Gauss-quadrature fill of the single-layer operators L^(A),
+ * L^(phi) and the double-layer operator Kbar (RWG testing on the primal mesh,
+ * Buffa-Christiansen (BC) sources on its barycentric refinement) with
+ * singularity extraction on touching pairs; the per-object admittance blocks
+ * Y11, Y21 (Eq. Yeqdef); and the dense complex matrix-vector products of the
+ * final system (Eq. finalsystem) that drive GMRES.
+ *
+ * General conventions
+ *  - Every call returns an int status: SLDM_OK (0) or a negative SLDM_E* code;
+ *    sldm_last_error() returns the text of the last error of the calling thread.
+ *  - Handles are opaque, owned by the library, released by the matching
+ *    *_destroy.  Caller arrays are borrowed for the duration of a call only.
+ *  - Arrays passed with `where` = SLDM_HOST are host memory; with SLDM_DEVICE
+ *    they are device memory on the device the handle was created on.
+ *  - `stream` is a cudaStream_t passed as void*; NULL means the legacy default
+ *    stream.  Calls that return results in host memory synchronise the stream.
+ *  - Complex numbers are interleaved {re, im} pairs of double (complex128).
+ *  - SI units; time convention exp(+j w t); G(R) = exp(-j k R)/(4 pi R) (Eq. hgf).
+ *  - A handle may not be used by two threads at once; different handles may.
+ *
+ * Discretisation conventions (the paper defers D, B, F and the BC functions to
+ * its references; these are the readings this library implements):
+ *  - Triangles are given counter-clockwise seen from outside (outward normal);
+ *    each object is a closed, oriented 2-manifold; objects are disjoint and
+ *    occupy contiguous, non-decreasing obj_id ranges of the triangle list.
+ *  - Edge n joins vertices u < v.  T+ is the triangle whose boundary runs
+ *    u -> v, T- runs v -> u.  Edges are numbered by sorting (obj, u, v).
+ *  - Area-normalised RWG f_n = (r - p+)/(2A+) on T+, -(r - p-)/(2A-) on T-
+ *    (p = vertex opposite the edge): unit flux from T+ to T-.
+ *  - Pulses h_p = 1/A_p; D[T+, n] = +1, D[T-, n] = -1.  Charge neutrality per
+ *    object eliminates its last triangle: B = [I; -1^T], F = [I 0].
+ *  - BC function of edge (u, v): unit flux from the dual cell of u to that of
+ *    v, equal integrated divergence on the barycentric triangles of each cell,
+ *    zero flux through the half edges u - m and v - m (b_n close to n x f_n).
+ *  - Unknown vector (length N = 2 ne + nt - nobj), Eq. finalsystem:
+ *        x = [ j k0 H (ne, RWG) ; E/eta0 (ne, BC, of n x E) ; -c0 rho (nt - nobj) ]
+ *    where the charge entries skip each object's last triangle.
+ *  - Final system rows: external EFIE (ne), internal EFIE (ne), external
+ *    continuity (nt - nobj); row 2 carries -K with K = Kbar + I_x/2.
+ */
+#ifndef SLDM_H
+#define SLDM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------- */
+#define SLDM_OK 0
+#define SLDM_EINVAL -1     /* invalid argument or mesh */
+#define SLDM_ENOMEM -2     /* device/host allocation failed or budget exceeded */
+#define SLDM_ENOTCONV -3   /* iterative solver did not reach the tolerance */
+#define SLDM_ENUMERIC -4   /* NaN/Inf or a zero pivot */
+#define SLDM_ECUDA -5      /* a CUDA runtime call failed */
+#define SLDM_EBUSY -6      /* the handle is in use */
+#define SLDM_ENOTSUP -7    /* feature not available in this build */
+
+#define SLDM_HOST 0
+#define SLDM_DEVICE 1
+
+#define SLDM_PREC_F64 0    /* complex128 operator, FP64 fill */
+#define SLDM_PREC_F32 1    /* complex64 operator, FP32 bulk fill, FP64 singular terms */
+
+#define SLDM_BOTTOM_HALFSPACE 0
+#define SLDM_BOTTOM_PEC 1
+
+typedef struct sldm_mesh sldm_mesh;
+typedef struct sldm_stack sldm_stack;
+typedef struct sldm_op sldm_op;
+
+/* Material of one object (Sec. II): relative permittivity, permeability,
+ * conductivity (S/m) and the index of the background layer containing it. */
+typedef struct {
+  double eps_r, mu_r, sigma;
+  int32_t layer;
+  int32_t reserved;
+} sldm_material;
+
+/* One layer of the background, listed top to bottom.  The first layer is the
+ * upper half-space; the last is the lower half-space unless the stack ends in
+ * a PEC ground.  thickness is ignored for half-spaces. */
+typedef struct {
+  double eps_r, mu_r, sigma, thickness;
+} sldm_layer;
+
+typedef struct {
+  int64_t nv, nt, ne, nobj;
+  int64_t n_unknowns;   /* 2 ne + nt - nobj */
+  int64_t n_bary_edges; /* 9 nt */
+} sldm_mesh_info;
+
+typedef struct {
+  int32_t precision;    /* SLDM_PREC_F64 or SLDM_PREC_F32 */
+  int32_t reserved;
+  void* stream;         /* stream the fill runs on (NULL = default) */
+} sldm_assemble_opts;
+
+typedef struct {
+  double tol;           /* relative residual ||b - Z x|| / ||b|| (default 1e-8) */
+  int32_t restart;      /* GMRES restart length m (default 100) */
+  int32_t maxit;        /* maximum total iterations (default 2000) */
+  int32_t x0_given;     /* nonzero: x holds the initial guess on entry */
+  int32_t reserved;
+} sldm_solve_opts;
+
+typedef struct {
+  int32_t iters;        /* total GMRES iterations (over all right-hand sides) */
+  int32_t status;       /* SLDM_OK or SLDM_ENOTCONV */
+  double relres;        /* largest final relative residual over the right-hand sides */
+} sldm_solve_info;
+
+typedef struct {
+  int64_t n_unknowns, ne, nt, nobj;
+  int64_t device_bytes; /* device memory held by the operator */
+  int32_t precision;
+  int32_t reserved;
+  double k0;
+} sldm_op_info;
+
+/* Operator blocks that sldm_op_block can copy out (for verification). */
+#define SLDM_BLOCK_LAM 0    /* L^A_m  = mu_b L^A(k_b), ne x ne, global (Eq. AEFIEextdis) */
+#define SLDM_BLOCK_LPM 1    /* L^phi_m = L^phi(k_b)/eps_b, nt x nt, global */
+#define SLDM_BLOCK_LA 2     /* mu_r L^A(k), object, ne_o x ne_o (Eq. AEFIEintdis) */
+#define SLDM_BLOCK_LP 3     /* L^phi(k)/eps_cr, object, nt_o x nt_o */
+#define SLDM_BLOCK_K 4      /* K = Kbar(k) + I_x/2, object, ne_o x ne_o (Eq. Kmatdef) */
+#define SLDM_BLOCK_Y11 5    /* Y11, object, ne_o x ne_o (Eq. Yeqdef) */
+#define SLDM_BLOCK_Y21 6    /* Y21, object, (nt_o - 1) x ne_o */
+#define SLDM_BLOCK_IX 7     /* I_x, dense copy of the sparse Gram matrix, ne x ne */
+#define SLDM_BLOCK_KBAR_L 8 /* Kbar(k_l), object, ne_o x ne_o (equivalent configuration) */
+
+/* Text of the last error of the calling thread, NUL-terminated, truncated to len. */
+void sldm_last_error(char* buf, size_t len);
+
+/* Build a mesh: topology (edges, T+/T-, barycentric refinement, BC
+ * coefficients, touching-pair lists) on the host, then upload it to the
+ * current device.  xyz: nv x 3 doubles; tri: nt x 3 vertex indices; obj_id: nt
+ * non-decreasing object ids or NULL for one object.  Host pointers.
+ * Errors: SLDM_EINVAL when an object is not a closed oriented manifold, a
+ * triangle is degenerate, or obj_id is not contiguous. */
+int sldm_mesh_create(const double* xyz, int64_t nv, const int32_t* tri, int64_t nt,
+                     const int32_t* obj_id, sldm_mesh** out);
+int sldm_mesh_info_get(const sldm_mesh* mesh, sldm_mesh_info* info);
+/* Edge table in the numbering above: uv (ne x 2), tplus, tminus (ne).  Host pointers; any may be NULL. */
+int sldm_mesh_edges(const sldm_mesh* mesh, int64_t* uv, int64_t* tplus, int64_t* tminus);
+int sldm_mesh_destroy(sldm_mesh* mesh);
+
+/* Background medium (Sec. II, "stratified background").  nlayers == 1 is a
+ * homogeneous background (L^A_m = mu_b L^A(k_b), L^phi_m = L^phi(k_b)/eps_b).
+ * z_top: height of the interface below the upper half-space; layers are
+ * listed top to bottom.  Layered backgrounds return SLDM_ENOTSUP in this build. */
+int sldm_stack_create(const sldm_layer* layers, int32_t nlayers, double z_top, int32_t bottom,
+                      sldm_stack** out);
+int sldm_stack_destroy(sldm_stack* stack);
+
+/* Fill and factor the operator at frequency freq_hz (Sec. II-B to II-E):
+ * internal blocks with each object's k, equivalent-configuration blocks with
+ * the background's k_l, Y11/Y21 by LU of M_l, global external blocks, I_x.
+ * per_obj: nobj materials (host).  The mesh and stack must outlive the op. */
+int sldm_assemble(const sldm_mesh* mesh, const sldm_stack* stack, const sldm_material* per_obj,
+                  double freq_hz, const sldm_assemble_opts* opts, sldm_op** out);
+int sldm_op_info_get(const sldm_op* op, sldm_op_info* info);
+/* Copy block `which` (SLDM_BLOCK_*) of object `obj` (ignored for global blocks)
+ * into dst as row-major complex128; rows/cols receive its shape.  dst may be
+ * NULL to query the shape only. */
+int sldm_op_block(const sldm_op* op, int32_t which, int32_t obj, void* dst, int32_t where,
+                  int64_t* rows, int64_t* cols);
+int sldm_op_destroy(sldm_op* op);
+
+/* y = Z x for nrhs right-hand sides (Eq. finalsystem), column-major N x nrhs
+ * complex128 with leading dimension N.  Z is applied in its structured form:
+ * global L^A_m, L^phi_m products plus per-object blocks, never a dense Z. */
+int sldm_apply(const sldm_op* op, const void* x, void* y, int32_t nrhs, int32_t where, void* stream);
+
+/* Right-hand sides for plane waves (Eq. finalsystem right-hand side):
+ * b = [e_inc; 0; 0], e_inc[m] = int f_m . E_inc / eta0,
+ * E_inc = pol E0 exp(-j k0 khat . r) with E0 = 1 V/m.
+ * khat, pol: nrhs x 3 (real unit direction, real polarisation), host.
+ * b: N x nrhs complex128, column-major. */
+int sldm_rhs_planewave(const sldm_op* op, const double* khat, const double* pol, int32_t nrhs,
+                       void* b, int32_t where, void* stream);
+
+/* Solve Z x = b by restarted GMRES with FP64 Arnoldi (classical Gram-Schmidt
+ * twice) and Givens rotations (Sec. IV, GMRES), matrix-vector products in the
+ * operator's precision.  b, x: N x nrhs complex128 column-major.
+ * Returns SLDM_ENOTCONV (x holds the last iterate) if tol is not reached. */
+int sldm_solve(const sldm_op* op, const void* b, void* x, int32_t nrhs, const sldm_solve_opts* opts,
+               sldm_solve_info* info, int32_t where, void* stream);
+
+/* Bistatic radar cross section (m^2) of the solution x (N complex128, `where`)
+ * in free space: the equivalent current J_Delta = H - H_eq radiating in the
+ * background (Sec. IV-A).  theta, phi, rcs: n doubles, host. */
+int sldm_farfield(const sldm_op* op, const void* x, int32_t where, const double* theta,
+                  const double* phi, int32_t n, double* rcs);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SLDM_H */

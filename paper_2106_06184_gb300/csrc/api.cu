@@ -1,0 +1,728 @@
+// C ABI of libsldm (include/sldm.h): handle management, assembly of the
+// single-layer dual-mesh operator (Sec. II-B to II-E), its structured product
+// and the GMRES solver (Sec. IV).
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <mutex>
+
+#include "dense.h"
+#include "internal.h"
+
+namespace sldm {
+
+static thread_local std::string g_err;
+void set_error(const std::string& m) { g_err = m; }
+
+constexpr double PI_ = 3.14159265358979323846;
+constexpr double C0_ = 299792458.0;
+constexpr double MU0_ = 4e-7 * PI_;
+constexpr double EPS0_ = 1.0 / (MU0_ * C0_ * C0_);
+
+typedef std::complex<double> cplx;
+
+struct ObjInfo {
+  int32_t e0, ne, t0, nt, q0, nq;
+  int64_t oLA, oLP, oK, oY11, oY21;  // element offsets in op->loc
+  cplx k, eps_c;
+  double mu_r;
+};
+
+}  // namespace sldm
+
+struct sldm_op {
+  const sldm_mesh* mesh = nullptr;
+  int prec = SLDM_PREC_F64;
+  size_t esz = 16;
+  double k0 = 0, freq = 0;
+  int device = 0;
+  int64_t N = 0, ne = 0, nt = 0, nq = 0, nobj = 0;
+  sldm::cplx kb, eps_b;
+  double mu_b = 1;
+  sldm::DBuf<char> LAm, LPm, loc;
+  std::vector<sldm::ObjInfo> obj;
+  sldm::DBuf<double> ix_val;
+  // structured product: work vectors for up to WR right-hand sides per pass
+  static constexpr int WR = 8;
+  sldm::DBuf<char> wj, we, wu, wt1, wt2, wa, wc, wbc, wbu, wz1, wz2, ww1, ww2, ww3;
+  sldm::DBuf<sldm::GemvJob> jobs1, jobs2;
+  sldm::DBuf<int64_t> rs1, rs2;
+  sldm::GemvPlan plan1, plan2;
+  // GMRES workspace
+  int ws_m = 0;
+  sldm::DBuf<double2> V, wb, wx, wr, wtmp, dh;
+  sldm::DBuf<double> dnorm;
+  std::mutex busy;
+};
+
+namespace sldm {
+
+static int64_t op_bytes(const sldm_op* op) {
+  return int64_t(op->LAm.bytes() + op->LPm.bytes() + op->loc.bytes() + op->ix_val.bytes() + op->V.bytes());
+}
+
+template <class C>
+static void build_plans(sldm_op* op) {
+  const int64_t ne = op->ne, nt = op->nt, nq = op->nq;
+  const int WR = sldm_op::WR;
+  const size_t es = sizeof(C);
+  op->wj.alloc(ne * WR * es); op->we.alloc(ne * WR * es); op->wu.alloc(std::max<int64_t>(nq, 1) * WR * es);
+  op->wt1.alloc(ne * WR * es); op->wt2.alloc(std::max<int64_t>(nq, 1) * WR * es);
+  op->wa.alloc(ne * WR * es); op->wc.alloc(std::max<int64_t>(nq, 1) * WR * es);
+  op->wbc.alloc(nt * WR * es); op->wbu.alloc(nt * WR * es);
+  op->wz1.alloc(ne * WR * es); op->wz2.alloc(nt * WR * es);
+  op->ww1.alloc(ne * WR * es); op->ww2.alloc(ne * WR * es); op->ww3.alloc(nt * WR * es);
+  auto P = [&](DBuf<char>& b, int64_t off) { return (void*)(b.p + off * es); };
+  const char* loc = op->loc.p;
+  auto L = [&](int64_t off) { return (const void*)(loc + off * es); };
+  std::vector<GemvJob> j1, j2;
+  for (auto& o : op->obj) {
+    j1.push_back({L(o.oY11), o.ne, o.ne, o.ne, P(op->we, o.e0), ne, P(op->wt1, o.e0), ne, 1, 0, 0, 0});
+    if (o.nq > 0) j1.push_back({L(o.oY21), o.ne, o.nq, o.ne, P(op->we, o.e0), ne, P(op->wt2, o.q0), nq, 1, 0, 0, 0});
+  }
+  j2.push_back({op->LAm.p, ne, int32_t(ne), int32_t(ne), P(op->wa, 0), ne, P(op->wz1, 0), ne, 1, 0, 0, 0});
+  j2.push_back({op->LPm.p, nt, int32_t(nt), int32_t(nt), P(op->wbc, 0), nt, P(op->wz2, 0), nt, 1, 0, 0, 0});
+  for (auto& o : op->obj) {
+    j2.push_back({L(o.oLA), o.ne, o.ne, o.ne, P(op->wj, o.e0), ne, P(op->ww1, o.e0), ne, 1, 0, 0, 0});
+    j2.push_back({L(o.oK), o.ne, o.ne, o.ne, P(op->we, o.e0), ne, P(op->ww2, o.e0), ne, 1, 0, 0, 0});
+    j2.push_back({L(o.oLP), o.nt, o.nt, o.nt, P(op->wbu, o.t0), nt, P(op->ww3, o.t0), nt, 1, 0, 0, 0});
+  }
+  auto mk = [&](std::vector<GemvJob>& j, DBuf<GemvJob>& dj, DBuf<int64_t>& drs, GemvPlan& plan) {
+    std::vector<int64_t> rs(j.size());
+    int64_t acc = 0;
+    for (size_t i = 0; i < j.size(); ++i) {
+      rs[i] = acc;
+      acc += j[i].m;
+    }
+    dj.upload(j);
+    drs.upload(rs);
+    plan.jobs = dj.p;
+    plan.rowstart = drs.p;
+    plan.njobs = int(j.size());
+    plan.total_rows = acc;
+  };
+  mk(j1, op->jobs1, op->rs1, op->plan1);
+  mk(j2, op->jobs2, op->rs2, op->plan2);
+}
+
+// y = Z x for nrhs columns, x/y complex128 on the device (column stride N)
+template <class C>
+static void apply_dev(const sldm_op* op_, const double2* x, double2* y, int nrhs, cudaStream_t s) {
+  sldm_op* op = const_cast<sldm_op*>(op_);
+  ApplyDims D{int32_t(op->ne), int32_t(op->nt), int32_t(op->nq), int32_t(op->nobj)};
+  for (int r0 = 0; r0 < nrhs; r0 += sldm_op::WR) {
+    int nr = std::min(sldm_op::WR, nrhs - r0);
+    const double2* xr = x + int64_t(r0) * op->N;
+    double2* yr = y + int64_t(r0) * op->N;
+    apply_glue_split<C>(xr, op->N, D, op->wj.p, op->we.p, op->wu.p, nr, s);
+    gemv_jobs<C>(op->plan1, nr, s);
+    apply_glue_prep<C>(op->mesh, D, op->wj.p, op->wu.p, op->wt1.p, op->wt2.p, op->wa.p, op->wc.p, op->wbc.p, op->wbu.p, nr, s,
+                       op->mesh->d.tri_begin.p, op->mesh->d.edge_begin.p);
+    gemv_jobs<C>(op->plan2, nr, s);
+    apply_glue_combine<C>(op->mesh, D, op->k0, op->ix_val.p, op->wz1.p, op->wz2.p, op->ww1.p, op->ww2.p, op->ww3.p,
+                          op->we.p, op->wa.p, op->wc.p, yr, op->N, nr, s);
+  }
+}
+
+static void apply_any(const sldm_op* op, const double2* x, double2* y, int nrhs, cudaStream_t s) {
+  if (op->prec == SLDM_PREC_F32) apply_dev<float2>(op, x, y, nrhs, s);
+  else apply_dev<double2>(op, x, y, nrhs, s);
+}
+
+static cplx eps_complex(double eps_r, double sigma, double omega) { return cplx(eps_r, -sigma / (omega * EPS0_)); }
+
+template <class R>
+static void assemble_impl(sldm_op* op, const sldm_material* mats, cudaStream_t s) {
+  typedef typename std::conditional<sizeof(R) == 4, float2, double2>::type C;
+  const sldm_mesh* m = op->mesh;
+  const HostMesh& h = m->h;
+  const size_t es = sizeof(C);
+  const double omega = 2 * PI_ * op->freq;
+  // ---- external (global) blocks with the background wavenumber
+  op->LAm.alloc(op->ne * op->ne * es);
+  op->LPm.alloc(op->nt * op->nt * es);
+  op->LAm.zero(s);
+  op->LPm.zero(s);
+  {
+    LTask t{};
+    t.t0 = 0; t.ntest = int32_t(op->nt); t.s0 = 0; t.nsrc = int32_t(op->nt);
+    t.ldA = op->ne; t.ldP = op->nt;
+    t.A = op->LAm.p; t.P = op->LPm.p;
+    t.kr = op->kb.real(); t.ki = op->kb.imag();
+    t.sAr = op->mu_b; t.sAi = 0;
+    cplx ip = 1.0 / op->eps_b;
+    t.sPr = ip.real(); t.sPi = ip.imag();
+    fill_L<R>(m, {t}, s);
+  }
+  // ---- per-object layout of the local blocks
+  int64_t off = 0;
+  op->obj.clear();
+  for (int o = 0; o < op->nobj; ++o) {
+    ObjInfo oi{};
+    oi.e0 = h.edge_begin[o]; oi.ne = h.edge_begin[o + 1] - oi.e0;
+    oi.t0 = h.tri_begin[o]; oi.nt = h.tri_begin[o + 1] - oi.t0;
+    oi.q0 = oi.t0 - o; oi.nq = oi.nt - 1;
+    oi.eps_c = eps_complex(mats[o].eps_r, mats[o].sigma, omega);
+    oi.mu_r = mats[o].mu_r;
+    oi.k = op->k0 * std::sqrt(oi.eps_c * oi.mu_r);
+    auto al = [&](int64_t n) { int64_t r = off; off += (n + 1) & ~int64_t(1); return r; };  // keep 16-byte alignment
+    oi.oLA = al(int64_t(oi.ne) * oi.ne);
+    oi.oLP = al(int64_t(oi.nt) * oi.nt);
+    oi.oK = al(int64_t(oi.ne) * oi.ne);
+    oi.oY11 = al(int64_t(oi.ne) * oi.ne);
+    oi.oY21 = al(int64_t(oi.nq) * oi.ne);
+    op->obj.push_back(oi);
+  }
+  op->loc.alloc(off * es);
+  op->loc.zero(s);
+  char* loc = op->loc.p;
+  // ---- internal L^A, L^phi with each object's wavenumber
+  {
+    std::vector<LTask> tasks;
+    for (auto& oi : op->obj) {
+      LTask t{};
+      t.t0 = oi.t0; t.ntest = oi.nt; t.s0 = oi.t0; t.nsrc = oi.nt;
+      t.e_row0 = oi.e0; t.e_col0 = oi.e0; t.t_row0 = oi.t0; t.t_col0 = oi.t0;
+      t.ldA = oi.ne; t.ldP = oi.nt;
+      t.A = loc + oi.oLA * es; t.P = loc + oi.oLP * es;
+      t.kr = oi.k.real(); t.ki = oi.k.imag();
+      t.sAr = oi.mu_r; t.sAi = 0;
+      cplx ip = 1.0 / oi.eps_c;
+      t.sPr = ip.real(); t.sPi = ip.imag();
+      tasks.push_back(t);
+    }
+    fill_L<R>(m, tasks, s);
+  }
+  // ---- Gram matrix I_x
+  op->ix_val.alloc(std::max<size_t>(h.ix_col.size(), 1));
+  gram_ix(m, op->ix_val.p, s);
+  // ---- Kbar with BC sources: internal (k) and equivalent (k_l) per object
+  int64_t kb_total = 0, kl_total = 0, ml_total = 0, rl_total = 0;
+  std::vector<int64_t> kb_off, kl_off, ml_off, rl_off;
+  for (int o = 0; o < op->nobj; ++o) {
+    const ObjInfo& oi = op->obj[o];
+    int64_t nbe = h.bedge_begin[o + 1] - h.bedge_begin[o];
+    kb_off.push_back(kb_total); kb_total += int64_t(oi.ne) * nbe;
+    kl_off.push_back(kl_total); kl_total += int64_t(oi.ne) * oi.ne;
+    int64_t n = oi.ne + oi.nq;
+    ml_off.push_back(ml_total); ml_total += n * n;
+    rl_off.push_back(rl_total); rl_total += n * oi.ne;
+  }
+  DBuf<char> Kb, Kl;
+  Kb.alloc(kb_total * es);
+  Kl.alloc(kl_total * es);
+  for (int pass = 0; pass < 2; ++pass) {
+    Kb.zero(s);
+    std::vector<KTask> tasks;
+    for (int o = 0; o < op->nobj; ++o) {
+      const ObjInfo& oi = op->obj[o];
+      KTask t{};
+      t.t0 = oi.t0; t.ntest = oi.nt; t.c0 = 6 * oi.t0; t.nsrc = 6 * oi.nt;
+      t.e_row0 = oi.e0; t.b_col0 = h.bedge_begin[o];
+      t.ld = h.bedge_begin[o + 1] - h.bedge_begin[o];
+      t.Kb = Kb.p + kb_off[o] * es;
+      cplx k = pass == 0 ? oi.k : op->kb;
+      t.kr = k.real(); t.ki = k.imag();
+      tasks.push_back(t);
+    }
+    fill_K<R>(m, tasks, s);
+    for (int o = 0; o < op->nobj; ++o) {
+      const ObjInfo& oi = op->obj[o];
+      int64_t ld = h.bedge_begin[o + 1] - h.bedge_begin[o];
+      void* dst = pass == 0 ? (void*)(loc + oi.oK * es) : (void*)(Kl.p + kl_off[o] * es);
+      contract_bc<R>(m, o, Kb.p + kb_off[o] * es, ld, dst, oi.ne, s);
+      if (pass == 0) add_ix<C>(m, o, 0.5, op->ix_val.p, dst, oi.ne, s);
+    }
+  }
+  Kb.release();
+  // ---- Y11, Y21 by LU of M_l (FP64)
+  {
+    DBuf<double2> Ml, Rl;
+    Ml.alloc(ml_total);
+    Rl.alloc(rl_total);
+    std::vector<LUSys> sys;
+    for (int o = 0; o < op->nobj; ++o) {
+      const ObjInfo& oi = op->obj[o];
+      build_Ml<C>(m, o, op->k0, op->LAm.p, op->ne, op->LPm.p, op->nt, Kl.p + kl_off[o] * es, oi.ne, op->ix_val.p,
+                  Ml.p + ml_off[o], Rl.p + rl_off[o], s);
+      sys.push_back({Ml.p + ml_off[o], Rl.p + rl_off[o], oi.ne + oi.nq, oi.ne});
+    }
+    lu_solve_batched(sys, s);
+    for (int o = 0; o < op->nobj; ++o) {
+      const ObjInfo& oi = op->obj[o];
+      from_c128<C>(Rl.p + rl_off[o], int64_t(oi.ne) * oi.ne, loc + oi.oY11 * es, s);
+      from_c128<C>(Rl.p + rl_off[o] + int64_t(oi.ne) * oi.ne, int64_t(oi.nq) * oi.ne, loc + oi.oY21 * es, s);
+    }
+    SLDM_CUDA(cudaStreamSynchronize(s));
+  }
+  build_plans<C>(op);
+  SLDM_CUDA(cudaStreamSynchronize(s));
+}
+
+// ---------------------------------------------------------------- GMRES
+static void ensure_ws(sldm_op* op, int m) {
+  if (op->ws_m == m && op->V.p) return;
+  op->V.alloc(size_t(op->N) * (m + 1));
+  op->wb.alloc(op->N);
+  op->wx.alloc(op->N);
+  op->wr.alloc(op->N);
+  op->wtmp.alloc(op->N);
+  op->dh.alloc(2 * (m + 2));
+  op->dnorm.alloc(1);
+  op->ws_m = m;
+}
+
+static double dnorm(sldm_op* op, const double2* v, cudaStream_t s) {
+  vnorm2(v, op->N, op->dnorm.p, s);
+  double h = 0;
+  SLDM_CUDA(cudaMemcpyAsync(&h, op->dnorm.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+  SLDM_CUDA(cudaStreamSynchronize(s));
+  return std::sqrt(h);
+}
+
+// Solves one right-hand side held in op->wb into op->wx (initial guess in wx).
+static void gmres_one(sldm_op* op, int m, double tol, int maxit, int& iters, double& relres, cudaStream_t s) {
+  const int64_t N = op->N;
+  double2* V = op->V.p;
+  const double bnorm = dnorm(op, op->wb.p, s);
+  if (bnorm == 0) {
+    SLDM_CUDA(cudaMemsetAsync(op->wx.p, 0, N * sizeof(double2), s));
+    relres = 0;
+    return;
+  }
+  // r = b - Z x
+  apply_any(op, op->wx.p, op->wr.p, 1, s);
+  vaxpby(N, 1.0, op->wb.p, -1.0, op->wr.p, s);
+  double beta = dnorm(op, op->wr.p, s);
+  std::vector<cplx> H(size_t(m + 1) * m), g(m + 1), cs(m), sn(m), hh(2 * (m + 2));
+  double hn = 0;
+  while (beta / bnorm > tol && iters < maxit) {
+    SLDM_REQUIRE(std::isfinite(beta), SLDM_ENUMERIC, "GMRES: non-finite residual");
+    vaxpby(N, 1.0 / beta, op->wr.p, 0.0, V, s);
+    std::fill(g.begin(), g.end(), cplx(0));
+    g[0] = beta;
+    int kused = 0;
+    for (int k = 0; k < m; ++k) {
+      double2* w = V + int64_t(k + 1) * N;
+      apply_any(op, V + int64_t(k) * N, w, 1, s);
+      // classical Gram-Schmidt, twice
+      vdots(V, N, k + 1, w, N, op->dh.p, s);
+      vmul(V, N, k + 1, op->dh.p, -1.0, w, N, s);
+      vdots(V, N, k + 1, w, N, op->dh.p + (m + 2), s);
+      vmul(V, N, k + 1, op->dh.p + (m + 2), -1.0, w, N, s);
+      vnorm2(w, N, op->dnorm.p, s);
+      SLDM_CUDA(cudaMemcpyAsync(hh.data(), op->dh.p, 2 * (m + 2) * sizeof(double2), cudaMemcpyDeviceToHost, s));
+      SLDM_CUDA(cudaMemcpyAsync(&hn, op->dnorm.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+      SLDM_CUDA(cudaStreamSynchronize(s));
+      hn = std::sqrt(hn);
+      for (int i = 0; i <= k; ++i) H[size_t(i) * m + k] = hh[i] + hh[(m + 2) + i];
+      H[size_t(k + 1) * m + k] = hn;
+      if (hn > 0) vaxpby(N, 1.0 / hn, w, 0.0, w, s);
+      for (int i = 0; i < k; ++i) {  // previous rotations
+        cplx a = H[size_t(i) * m + k], b = H[size_t(i + 1) * m + k];
+        H[size_t(i) * m + k] = cs[i] * a + sn[i] * b;
+        H[size_t(i + 1) * m + k] = -std::conj(sn[i]) * a + cs[i] * b;
+      }
+      cplx a = H[size_t(k) * m + k], b = H[size_t(k + 1) * m + k];
+      double t = std::sqrt(std::norm(a) + std::norm(b));
+      if (std::abs(a) == 0) {
+        cs[k] = 0;
+        sn[k] = 1;
+        H[size_t(k) * m + k] = b;
+      } else {
+        cs[k] = std::abs(a) / t;
+        sn[k] = (a / std::abs(a)) * std::conj(b) / t;
+        H[size_t(k) * m + k] = (a / std::abs(a)) * t;
+      }
+      H[size_t(k + 1) * m + k] = 0;
+      g[k + 1] = -std::conj(sn[k]) * g[k];
+      g[k] = cs[k] * g[k];
+      ++iters;
+      kused = k + 1;
+      if (std::abs(g[k + 1]) / bnorm <= tol || iters >= maxit || hn == 0) break;
+    }
+    // y = H^-1 g (upper triangular), x += V y
+    std::vector<cplx> y(kused);
+    for (int i = kused - 1; i >= 0; --i) {
+      cplx acc = g[i];
+      for (int j = i + 1; j < kused; ++j) acc -= H[size_t(i) * m + j] * y[j];
+      y[i] = acc / H[size_t(i) * m + i];
+    }
+    SLDM_CUDA(cudaMemcpyAsync(op->dh.p, y.data(), kused * sizeof(double2), cudaMemcpyHostToDevice, s));
+    vmul(V, N, kused, op->dh.p, 1.0, op->wx.p, N, s);
+    apply_any(op, op->wx.p, op->wr.p, 1, s);
+    vaxpby(N, 1.0, op->wb.p, -1.0, op->wr.p, s);
+    beta = dnorm(op, op->wr.p, s);
+  }
+  relres = beta / bnorm;
+}
+
+}  // namespace sldm
+
+using namespace sldm;
+
+#define API_BEGIN try {
+#define API_END                            \
+  }                                        \
+  catch (const sldm::Error& e) {           \
+    sldm::set_error(e.msg);                \
+    return e.code;                         \
+  }                                        \
+  catch (const std::exception& e) {        \
+    sldm::set_error(e.what());             \
+    return SLDM_EINVAL;                    \
+  }                                        \
+  return SLDM_OK;
+
+extern "C" {
+
+void sldm_last_error(char* buf, size_t len) {
+  if (!buf || len == 0) return;
+  std::strncpy(buf, g_err.c_str(), len - 1);
+  buf[len - 1] = 0;
+}
+
+int sldm_mesh_create(const double* xyz, int64_t nv, const int32_t* tri, int64_t nt, const int32_t* obj_id,
+                     sldm_mesh** out) {
+  API_BEGIN
+  SLDM_REQUIRE(out, SLDM_EINVAL, "mesh_create: out is null");
+  *out = nullptr;
+  auto* m = new sldm_mesh();
+  try {
+    build_host_mesh(xyz, nv, tri, nt, obj_id, m->h);
+    SLDM_CUDA(cudaGetDevice(&m->device));
+    const HostMesh& h = m->h;
+    DevMesh& d = m->d;
+    d.xyz.upload(h.xyz);
+    d.tri.upload(h.tri);
+    d.tri_edge.upload(h.tri_edge);
+    d.tri_sign.upload(h.tri_sign);
+    d.tplus.upload(h.tplus);
+    d.tminus.upload(h.tminus);
+    d.obj.upload(h.obj);
+    std::vector<int32_t> q2t;
+    for (int64_t t = 0; t < h.nt; ++t)
+      if (t + 1 != h.tri_begin[h.obj[t] + 1]) q2t.push_back(int32_t(t));
+    d.q2t.upload(q2t);
+    d.tri_begin.upload(h.tri_begin);
+    d.edge_begin.upload(h.edge_begin);
+    d.btri_edge.upload(h.btri_edge);
+    d.btri_sign.upload(h.btri_sign);
+    d.bc_ptr.upload(h.bc_ptr);
+    d.bc_row.upload(h.bc_row);
+    d.bc_val.upload(h.bc_val);
+    d.touchL_a.upload(h.touchL_a);
+    d.touchL_b.upload(h.touchL_b);
+    d.touchK_a.upload(h.touchK_a);
+    d.touchK_c.upload(h.touchK_c);
+    d.ix_ptr.upload(h.ix_ptr);
+    d.ix_col.upload(h.ix_col);
+    d.ixc_ptr.upload(h.ixc_ptr);
+    d.ixc_tri.upload(h.ixc_tri);
+    d.ixc_child.upload(h.ixc_child);
+    d.ixc_i.upload(h.ixc_i);
+    d.ixc_j.upload(h.ixc_j);
+    d.ixc_coef.upload(h.ixc_coef);
+    geometry(h, d, 0);
+    SLDM_CUDA(cudaStreamSynchronize(0));
+  } catch (...) {
+    delete m;
+    throw;
+  }
+  *out = m;
+  API_END
+}
+
+int sldm_mesh_info_get(const sldm_mesh* m, sldm_mesh_info* info) {
+  API_BEGIN
+  SLDM_REQUIRE(m && info, SLDM_EINVAL, "mesh_info: null argument");
+  info->nv = m->h.nv;
+  info->nt = m->h.nt;
+  info->ne = m->h.ne;
+  info->nobj = m->h.nobj;
+  info->n_unknowns = 2 * m->h.ne + m->h.nt - m->h.nobj;
+  info->n_bary_edges = m->h.nbe;
+  API_END
+}
+
+int sldm_mesh_edges(const sldm_mesh* m, int64_t* uv, int64_t* tplus, int64_t* tminus) {
+  API_BEGIN
+  SLDM_REQUIRE(m, SLDM_EINVAL, "mesh_edges: null mesh");
+  for (int64_t n = 0; n < m->h.ne; ++n) {
+    if (uv) {
+      uv[2 * n] = m->h.uv[2 * n];
+      uv[2 * n + 1] = m->h.uv[2 * n + 1];
+    }
+    if (tplus) tplus[n] = m->h.tplus[n];
+    if (tminus) tminus[n] = m->h.tminus[n];
+  }
+  API_END
+}
+
+int sldm_mesh_destroy(sldm_mesh* m) {
+  API_BEGIN
+  delete m;
+  API_END
+}
+
+int sldm_stack_create(const sldm_layer* layers, int32_t nlayers, double z_top, int32_t bottom, sldm_stack** out) {
+  API_BEGIN
+  SLDM_REQUIRE(out && layers && nlayers >= 1, SLDM_EINVAL, "stack_create: invalid arguments");
+  *out = nullptr;
+  SLDM_REQUIRE(nlayers == 1 && bottom == SLDM_BOTTOM_HALFSPACE, SLDM_ENOTSUP,
+               "stack_create: layered backgrounds are not available in this build");
+  SLDM_REQUIRE(layers[0].eps_r > 0 && layers[0].mu_r > 0 && layers[0].sigma >= 0, SLDM_EINVAL,
+               "stack_create: invalid layer material");
+  auto* st = new sldm_stack();
+  st->layers.assign(layers, layers + nlayers);
+  st->z_top = z_top;
+  st->bottom = bottom;
+  *out = st;
+  API_END
+}
+
+int sldm_stack_destroy(sldm_stack* s) {
+  API_BEGIN
+  delete s;
+  API_END
+}
+
+int sldm_assemble(const sldm_mesh* m, const sldm_stack* st, const sldm_material* per_obj, double freq_hz,
+                  const sldm_assemble_opts* opts, sldm_op** out) {
+  API_BEGIN
+  SLDM_REQUIRE(m && st && per_obj && out, SLDM_EINVAL, "assemble: null argument");
+  SLDM_REQUIRE(freq_hz > 0 && std::isfinite(freq_hz), SLDM_EINVAL, "assemble: frequency must be positive");
+  *out = nullptr;
+  int dev = 0;
+  SLDM_CUDA(cudaGetDevice(&dev));
+  SLDM_REQUIRE(dev == m->device, SLDM_EINVAL, "assemble: current device differs from the mesh's device");
+  for (int64_t o = 0; o < m->h.nobj; ++o)
+    SLDM_REQUIRE(per_obj[o].eps_r > 0 && per_obj[o].mu_r > 0 && per_obj[o].sigma >= 0, SLDM_EINVAL,
+                 "assemble: invalid object material");
+  auto* op = new sldm_op();
+  try {
+    op->mesh = m;
+    op->prec = opts ? opts->precision : SLDM_PREC_F64;
+    SLDM_REQUIRE(op->prec == SLDM_PREC_F64 || op->prec == SLDM_PREC_F32, SLDM_EINVAL, "assemble: unknown precision");
+    op->esz = op->prec == SLDM_PREC_F32 ? 8 : 16;
+    op->freq = freq_hz;
+    op->device = dev;
+    op->k0 = 2 * PI_ * freq_hz / C0_;
+    op->ne = m->h.ne;
+    op->nt = m->h.nt;
+    op->nobj = m->h.nobj;
+    op->nq = op->nt - op->nobj;
+    op->N = 2 * op->ne + op->nq;
+    const sldm_layer& L = st->layers[0];
+    op->eps_b = eps_complex(L.eps_r, L.sigma, 2 * PI_ * freq_hz);
+    op->mu_b = L.mu_r;
+    op->kb = op->k0 * std::sqrt(op->eps_b * op->mu_b);
+    cudaStream_t s = opts ? (cudaStream_t)opts->stream : 0;
+    if (op->prec == SLDM_PREC_F32) assemble_impl<float>(op, per_obj, s);
+    else assemble_impl<double>(op, per_obj, s);
+  } catch (...) {
+    delete op;
+    throw;
+  }
+  *out = op;
+  API_END
+}
+
+int sldm_op_info_get(const sldm_op* op, sldm_op_info* info) {
+  API_BEGIN
+  SLDM_REQUIRE(op && info, SLDM_EINVAL, "op_info: null argument");
+  info->n_unknowns = op->N;
+  info->ne = op->ne;
+  info->nt = op->nt;
+  info->nobj = op->nobj;
+  info->device_bytes = op_bytes(op);
+  info->precision = op->prec;
+  info->k0 = op->k0;
+  API_END
+}
+
+int sldm_op_block(const sldm_op* op, int32_t which, int32_t obj, void* dst, int32_t where, int64_t* rows, int64_t* cols) {
+  API_BEGIN
+  SLDM_REQUIRE(op, SLDM_EINVAL, "op_block: null op");
+  const bool global = which == SLDM_BLOCK_LAM || which == SLDM_BLOCK_LPM || which == SLDM_BLOCK_IX;
+  SLDM_REQUIRE(global || (obj >= 0 && obj < op->nobj), SLDM_EINVAL, "op_block: object index out of range");
+  SLDM_REQUIRE(which != SLDM_BLOCK_KBAR_L, SLDM_ENOTSUP, "op_block: Kbar_l is not retained after assembly");
+  int64_t r = 0, c = 0;
+  const char* src = nullptr;
+  const ObjInfo* oi = global ? nullptr : &op->obj[obj];
+  switch (which) {
+    case SLDM_BLOCK_LAM: r = c = op->ne; src = op->LAm.p; break;
+    case SLDM_BLOCK_LPM: r = c = op->nt; src = op->LPm.p; break;
+    case SLDM_BLOCK_IX: r = c = op->ne; break;
+    case SLDM_BLOCK_LA: r = c = oi->ne; src = op->loc.p + oi->oLA * op->esz; break;
+    case SLDM_BLOCK_LP: r = c = oi->nt; src = op->loc.p + oi->oLP * op->esz; break;
+    case SLDM_BLOCK_K: r = c = oi->ne; src = op->loc.p + oi->oK * op->esz; break;
+    case SLDM_BLOCK_Y11: r = c = oi->ne; src = op->loc.p + oi->oY11 * op->esz; break;
+    case SLDM_BLOCK_Y21: r = oi->nq; c = oi->ne; src = op->loc.p + oi->oY21 * op->esz; break;
+    default: SLDM_REQUIRE(false, SLDM_EINVAL, "op_block: unknown block");
+  }
+  if (rows) *rows = r;
+  if (cols) *cols = c;
+  if (!dst) return SLDM_OK;
+  const int64_t n = r * c;
+  std::vector<double2> host;
+  if (which == SLDM_BLOCK_IX) {
+    host.assign(size_t(n), make_double2(0, 0));
+    std::vector<double> v(op->mesh->h.ix_col.size());
+    SLDM_CUDA(cudaMemcpy(v.data(), op->ix_val.p, v.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    for (int64_t mrow = 0; mrow < op->ne; ++mrow)
+      for (int z = op->mesh->h.ix_ptr[mrow]; z < op->mesh->h.ix_ptr[mrow + 1]; ++z)
+        host[size_t(mrow * op->ne + op->mesh->h.ix_col[z])].x = v[z];
+    if (where == SLDM_HOST) std::memcpy(dst, host.data(), n * sizeof(double2));
+    else SLDM_CUDA(cudaMemcpy(dst, host.data(), n * sizeof(double2), cudaMemcpyHostToDevice));
+    return SLDM_OK;
+  }
+  DBuf<double2> tmp;
+  double2* d = (where == SLDM_DEVICE) ? (double2*)dst : nullptr;
+  if (!d) {
+    tmp.alloc(n);
+    d = tmp.p;
+  }
+  if (op->prec == SLDM_PREC_F32) to_c128<float2>(src, n, d, 0);
+  else to_c128<double2>(src, n, d, 0);
+  if (where == SLDM_HOST) SLDM_CUDA(cudaMemcpy(dst, d, n * sizeof(double2), cudaMemcpyDeviceToHost));
+  SLDM_CUDA(cudaDeviceSynchronize());
+  API_END
+}
+
+int sldm_op_destroy(sldm_op* op) {
+  API_BEGIN
+  delete op;
+  API_END
+}
+
+int sldm_apply(const sldm_op* op, const void* x, void* y, int32_t nrhs, int32_t where, void* stream) {
+  API_BEGIN
+  SLDM_REQUIRE(op && x && y && nrhs >= 1, SLDM_EINVAL, "apply: invalid arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = size_t(op->N) * nrhs * sizeof(double2);
+  if (where == SLDM_DEVICE) {
+    apply_any(op, (const double2*)x, (double2*)y, nrhs, s);
+  } else {
+    DBuf<double2> dx, dy;
+    dx.alloc(size_t(op->N) * nrhs);
+    dy.alloc(size_t(op->N) * nrhs);
+    SLDM_CUDA(cudaMemcpyAsync(dx.p, x, bytes, cudaMemcpyHostToDevice, s));
+    apply_any(op, dx.p, dy.p, nrhs, s);
+    SLDM_CUDA(cudaMemcpyAsync(y, dy.p, bytes, cudaMemcpyDeviceToHost, s));
+    SLDM_CUDA(cudaStreamSynchronize(s));
+  }
+  API_END
+}
+
+int sldm_rhs_planewave(const sldm_op* op, const double* khat, const double* pol, int32_t nrhs, void* b, int32_t where,
+                       void* stream) {
+  API_BEGIN
+  SLDM_REQUIRE(op && khat && pol && b && nrhs >= 1, SLDM_EINVAL, "rhs_planewave: invalid arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<double> kp(size_t(6) * nrhs);
+  for (int r = 0; r < nrhs; ++r)
+    for (int d = 0; d < 3; ++d) {
+      kp[6 * r + d] = khat[3 * r + d];
+      kp[6 * r + 3 + d] = pol[3 * r + d];
+    }
+  DBuf<double> dk;
+  dk.upload(kp, s);
+  DBuf<double2> tmp;
+  double2* db = (where == SLDM_DEVICE) ? (double2*)b : nullptr;
+  if (!db) {
+    tmp.alloc(size_t(op->N) * nrhs);
+    db = tmp.p;
+  }
+  SLDM_CUDA(cudaMemsetAsync(db, 0, size_t(op->N) * nrhs * sizeof(double2), s));
+  rhs_planewave(op->mesh, op->k0, dk.p, nrhs, db, op->N, s);
+  if (where == SLDM_HOST)
+    SLDM_CUDA(cudaMemcpyAsync(b, db, size_t(op->N) * nrhs * sizeof(double2), cudaMemcpyDeviceToHost, s));
+  SLDM_CUDA(cudaStreamSynchronize(s));
+  API_END
+}
+
+int sldm_solve(const sldm_op* op_, const void* b, void* x, int32_t nrhs, const sldm_solve_opts* opts,
+               sldm_solve_info* info, int32_t where, void* stream) {
+  API_BEGIN
+  SLDM_REQUIRE(op_ && b && x && nrhs >= 1, SLDM_EINVAL, "solve: invalid arguments");
+  sldm_op* op = const_cast<sldm_op*>(op_);
+  std::unique_lock<std::mutex> lock(op->busy, std::try_to_lock);
+  SLDM_REQUIRE(lock.owns_lock(), SLDM_EBUSY, "solve: operator in use by another thread");
+  double tol = (opts && opts->tol > 0) ? opts->tol : 1e-8;
+  int m = (opts && opts->restart > 0) ? opts->restart : 100;
+  int maxit = (opts && opts->maxit > 0) ? opts->maxit : 2000;
+  bool x0 = opts && opts->x0_given;
+  cudaStream_t s = (cudaStream_t)stream;
+  ensure_ws(op, m);
+  const size_t vb = size_t(op->N) * sizeof(double2);
+  int iters = 0;
+  double worst = 0;
+  for (int r = 0; r < nrhs; ++r) {
+    const char* br = (const char*)b + r * vb;
+    char* xr = (char*)x + r * vb;
+    cudaMemcpyKind k_in = where == SLDM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    SLDM_CUDA(cudaMemcpyAsync(op->wb.p, br, vb, k_in, s));
+    if (x0) SLDM_CUDA(cudaMemcpyAsync(op->wx.p, xr, vb, k_in, s));
+    else SLDM_CUDA(cudaMemsetAsync(op->wx.p, 0, vb, s));
+    double rel = 0;
+    gmres_one(op, m, tol, maxit, iters, rel, s);
+    worst = std::max(worst, rel);
+    cudaMemcpyKind k_out = where == SLDM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    SLDM_CUDA(cudaMemcpyAsync(xr, op->wx.p, vb, k_out, s));
+  }
+  SLDM_CUDA(cudaStreamSynchronize(s));
+  if (info) {
+    info->iters = iters;
+    info->relres = worst;
+    info->status = worst <= tol ? SLDM_OK : SLDM_ENOTCONV;
+  }
+  if (worst > tol) {
+    set_error("solve: GMRES did not reach the tolerance");
+    return SLDM_ENOTCONV;
+  }
+  API_END
+}
+
+int sldm_farfield(const sldm_op* op_, const void* x, int32_t where, const double* theta, const double* phi, int32_t n,
+                  double* rcs) {
+  API_BEGIN
+  SLDM_REQUIRE(op_ && x && theta && phi && rcs && n >= 1, SLDM_EINVAL, "farfield: invalid arguments");
+  sldm_op* op = const_cast<sldm_op*>(op_);
+  cudaStream_t s = 0;
+  DBuf<double2> dx, jd;
+  dx.alloc(op->N);
+  jd.alloc(op->ne);
+  SLDM_CUDA(cudaMemcpyAsync(dx.p, x, op->N * sizeof(double2),
+                            where == SLDM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  // j_Delta = j - Y11 e (per object), from the first two stages of the structured product
+  ApplyDims D{int32_t(op->ne), int32_t(op->nt), int32_t(op->nq), int32_t(op->nobj)};
+  if (op->prec == SLDM_PREC_F32) {
+    apply_glue_split<float2>(dx.p, op->N, D, op->wj.p, op->we.p, op->wu.p, 1, s);
+    gemv_jobs<float2>(op->plan1, 1, s);
+    apply_glue_prep<float2>(op->mesh, D, op->wj.p, op->wu.p, op->wt1.p, op->wt2.p, op->wa.p, op->wc.p, op->wbc.p,
+                            op->wbu.p, 1, s, op->mesh->d.tri_begin.p, op->mesh->d.edge_begin.p);
+    to_c128<float2>(op->wa.p, op->ne, jd.p, s);
+  } else {
+    apply_glue_split<double2>(dx.p, op->N, D, op->wj.p, op->we.p, op->wu.p, 1, s);
+    gemv_jobs<double2>(op->plan1, 1, s);
+    apply_glue_prep<double2>(op->mesh, D, op->wj.p, op->wu.p, op->wt1.p, op->wt2.p, op->wa.p, op->wc.p, op->wbc.p,
+                             op->wbu.p, 1, s, op->mesh->d.tri_begin.p, op->mesh->d.edge_begin.p);
+    to_c128<double2>(op->wa.p, op->ne, jd.p, s);
+  }
+  std::vector<double> ang(2 * size_t(n));
+  for (int i = 0; i < n; ++i) {
+    ang[2 * i] = theta[i];
+    ang[2 * i + 1] = phi[i];
+  }
+  DBuf<double> da, dr;
+  da.upload(ang, s);
+  dr.alloc(n);
+  farfield(op->mesh, op->k0, jd.p, da.p, n, dr.p, s);
+  SLDM_CUDA(cudaMemcpyAsync(rcs, dr.p, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+  SLDM_CUDA(cudaStreamSynchronize(s));
+  API_END
+}
+
+}  // extern "C"

@@ -1,0 +1,656 @@
+// Dense algebra of the SLDM system on the device:
+//  - M_l and its right-hand side [Kbar_l + I_x/2; 0] per object (Eq. AEFIEeqvdis),
+//    batched LU with partial pivoting in FP64 -> Y11, Y21 (Eq. Yeqdef);
+//  - batched skinny GEMV (y = alpha A x + beta y, up to 8 right-hand sides per
+//    pass) streaming row-major complex blocks once per pass: the HBM-bound
+//    matrix-vector product that drives GMRES;
+//  - the sparse/elementwise glue of the structured product Z x (Eq. finalsystem);
+//  - FP64 vector kernels for GMRES (Arnoldi by classical Gram-Schmidt twice).
+#include <algorithm>
+#include <type_traits>
+
+#include "dense.h"
+
+namespace sldm {
+
+template <class C>
+struct CT;
+template <>
+struct CT<float2> {
+  typedef float R;
+};
+template <>
+struct CT<double2> {
+  typedef double R;
+};
+
+// ---------------------------------------------------------------- M_l and R_l
+template <class C>
+__global__ void build_Ml_kernel(int ne_o, int nt_o, int e0, int t0, double k0, const C* __restrict__ LAm, int64_t ldLA,
+                                const C* __restrict__ LPm, int64_t ldLP, const int32_t* __restrict__ tplus,
+                                const int32_t* __restrict__ tminus, double2* Ml) {
+  const int n = ne_o + nt_o - 1;
+  int col = blockIdx.x * blockDim.x + threadIdx.x;
+  int row = blockIdx.y;
+  if (col >= n) return;
+  double2 v = make_double2(0, 0);
+  if (row < ne_o && col < ne_o) {
+    C a = LAm[int64_t(e0 + row) * ldLA + (e0 + col)];
+    v = make_double2(double(a.x), double(a.y));
+  } else if (row < ne_o) {
+    // -(D^T L^phi_m B)[row, q]:  (L B)[t, q] = L[t, q] - L[t, last]
+    int q = col - ne_o;
+    int last = t0 + nt_o - 1;
+    int tp = tplus[e0 + row], tm = tminus[e0 + row];
+    C a = LPm[int64_t(tp) * ldLP + (t0 + q)], b = LPm[int64_t(tp) * ldLP + last];
+    C c = LPm[int64_t(tm) * ldLP + (t0 + q)], d = LPm[int64_t(tm) * ldLP + last];
+    double re = (double(a.x) - double(b.x)) - (double(c.x) - double(d.x));
+    double im = (double(a.y) - double(b.y)) - (double(c.y) - double(d.y));
+    v = make_double2(-re, -im);
+  } else if (col < ne_o) {
+    // (F D)[q, col]: +1 if triangle q is T+ of edge col, -1 if T-
+    int q = row - ne_o;
+    int tp = tplus[e0 + col] - t0, tm = tminus[e0 + col] - t0;
+    v = make_double2((tp == q ? 1.0 : 0.0) - (tm == q ? 1.0 : 0.0), 0.0);
+  } else {
+    v = make_double2(row == col ? -k0 * k0 : 0.0, 0.0);
+  }
+  Ml[int64_t(row) * n + col] = v;
+}
+
+// R = [Kbar_l + I_x/2 ; 0]  (n x ne_o, row-major)
+template <class C>
+__global__ void build_Rl_kernel(int ne_o, int nt_o, int e0, const C* __restrict__ Kl, int64_t ldK,
+                                const int32_t* __restrict__ ix_ptr, const int32_t* __restrict__ ix_col,
+                                const double* __restrict__ ix_val, double2* Rl) {
+  int col = blockIdx.x * blockDim.x + threadIdx.x;
+  int row = blockIdx.y;
+  if (col >= ne_o) return;
+  double2 v = make_double2(0, 0);
+  if (row < ne_o) {
+    C a = Kl[int64_t(row) * ldK + col];
+    v = make_double2(double(a.x), double(a.y));
+    for (int z = ix_ptr[e0 + row]; z < ix_ptr[e0 + row + 1]; ++z)
+      if (ix_col[z] == e0 + col) v.x += 0.5 * ix_val[z];
+  }
+  Rl[int64_t(row) * ne_o + col] = v;
+}
+
+template <class C>
+void build_Ml(const sldm_mesh* m, int obj, double k0, const void* LAm, int64_t ldLA, const void* LPm, int64_t ldLP,
+              const void* Kl, int64_t ldK, const double* ix_val, double2* Ml, double2* Rl, cudaStream_t s) {
+  const HostMesh& h = m->h;
+  int e0 = h.edge_begin[obj], ne_o = h.edge_begin[obj + 1] - e0;
+  int t0 = h.tri_begin[obj], nt_o = h.tri_begin[obj + 1] - t0;
+  int n = ne_o + nt_o - 1;
+  build_Ml_kernel<C><<<dim3((n + 127) / 128, n), 128, 0, s>>>(ne_o, nt_o, e0, t0, k0, (const C*)LAm, ldLA, (const C*)LPm,
+                                                              ldLP, m->d.tplus.p, m->d.tminus.p, Ml);
+  build_Rl_kernel<C><<<dim3((ne_o + 127) / 128, n), 128, 0, s>>>(ne_o, nt_o, e0, (const C*)Kl, ldK, m->d.ix_ptr.p,
+                                                                 m->d.ix_col.p, ix_val, Rl);
+  SLDM_CUDA(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------- batched LU (FP64)
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
+  double d = b.x * b.x + b.y * b.y;
+  return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+
+// Pivot search, row swap and column scaling at step k for each system.
+__global__ void lu_pivot_kernel(const LUSys* __restrict__ sys, int k, int* err) {
+  const LUSys S = sys[blockIdx.x];
+  if (k >= S.n) return;
+  __shared__ double bv[256];
+  __shared__ int bi[256];
+  double best = -1;
+  int besti = k;
+  for (int i = k + threadIdx.x; i < S.n; i += blockDim.x) {
+    double2 a = S.A[int64_t(i) * S.n + k];
+    double v = a.x * a.x + a.y * a.y;
+    if (v > best) {
+      best = v;
+      besti = i;
+    }
+  }
+  bv[threadIdx.x] = best;
+  bi[threadIdx.x] = besti;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      if (bv[threadIdx.x + w] > bv[threadIdx.x] ||
+          (bv[threadIdx.x + w] == bv[threadIdx.x] && bi[threadIdx.x + w] < bi[threadIdx.x])) {
+        bv[threadIdx.x] = bv[threadIdx.x + w];
+        bi[threadIdx.x] = bi[threadIdx.x + w];
+      }
+    }
+    __syncthreads();
+  }
+  const int p = bi[0];
+  if (!(bv[0] > 0.0)) {  // zero or NaN pivot
+    if (threadIdx.x == 0) atomicExch(err, 1);
+    return;
+  }
+  if (p != k) {
+    for (int j = threadIdx.x; j < S.n; j += blockDim.x) {
+      double2 t = S.A[int64_t(k) * S.n + j];
+      S.A[int64_t(k) * S.n + j] = S.A[int64_t(p) * S.n + j];
+      S.A[int64_t(p) * S.n + j] = t;
+    }
+    for (int j = threadIdx.x; j < S.nrhs; j += blockDim.x) {
+      double2 t = S.B[int64_t(k) * S.nrhs + j];
+      S.B[int64_t(k) * S.nrhs + j] = S.B[int64_t(p) * S.nrhs + j];
+      S.B[int64_t(p) * S.nrhs + j] = t;
+    }
+  }
+  __syncthreads();
+  const double2 piv = S.A[int64_t(k) * S.n + k];
+  for (int i = k + 1 + threadIdx.x; i < S.n; i += blockDim.x)
+    S.A[int64_t(i) * S.n + k] = cdiv(S.A[int64_t(i) * S.n + k], piv);
+}
+
+// Trailing update at step k: A[i][j] -= A[i][k] A[k][j] (j > k), B[i][c] -= A[i][k] B[k][c].
+__global__ void lu_update_kernel(const LUSys* __restrict__ sys, int k) {
+  const LUSys S = sys[blockIdx.z];
+  if (k >= S.n) return;
+  const int i = k + 1 + blockIdx.y;
+  if (i >= S.n) return;
+  const double2 l = S.A[int64_t(i) * S.n + k];
+  const int ncols = (S.n - k - 1) + S.nrhs;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncols; c += gridDim.x * blockDim.x) {
+    if (c < S.n - k - 1) {
+      int j = k + 1 + c;
+      double2 u = S.A[int64_t(k) * S.n + j];
+      double2 a = S.A[int64_t(i) * S.n + j];
+      double2 p = cmul(l, u);
+      S.A[int64_t(i) * S.n + j] = make_double2(a.x - p.x, a.y - p.y);
+    } else {
+      int j = c - (S.n - k - 1);
+      double2 u = S.B[int64_t(k) * S.nrhs + j];
+      double2 a = S.B[int64_t(i) * S.nrhs + j];
+      double2 p = cmul(l, u);
+      S.B[int64_t(i) * S.nrhs + j] = make_double2(a.x - p.x, a.y - p.y);
+    }
+  }
+}
+
+// Back substitution U X = B, one CTA per (system, right-hand-side column).
+__global__ void lu_backsub_kernel(const LUSys* __restrict__ sys) {
+  const LUSys S = sys[blockIdx.y];
+  const int c = blockIdx.x;
+  if (c >= S.nrhs) return;
+  __shared__ double2 yk;
+  for (int k = S.n - 1; k >= 0; --k) {
+    if (threadIdx.x == 0) {
+      double2 y = cdiv(S.B[int64_t(k) * S.nrhs + c], S.A[int64_t(k) * S.n + k]);
+      S.B[int64_t(k) * S.nrhs + c] = y;
+      yk = y;
+    }
+    __syncthreads();
+    const double2 y = yk;
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+      double2 u = S.A[int64_t(i) * S.n + k];
+      double2 p = cmul(u, y);
+      double2 b = S.B[int64_t(i) * S.nrhs + c];
+      S.B[int64_t(i) * S.nrhs + c] = make_double2(b.x - p.x, b.y - p.y);
+    }
+    __syncthreads();
+  }
+}
+
+void lu_solve_batched(const std::vector<LUSys>& systems, cudaStream_t s) {
+  if (systems.empty()) return;
+  int nmax = 0, rmax = 0;
+  for (auto& S : systems) {
+    nmax = std::max(nmax, S.n);
+    rmax = std::max(rmax, S.nrhs);
+  }
+  DBuf<LUSys> d;
+  d.upload(systems, s);
+  DBuf<int> err;
+  err.alloc(1);
+  err.zero(s);
+  const int nsys = int(systems.size());
+  for (int k = 0; k < nmax; ++k) {
+    lu_pivot_kernel<<<nsys, 256, 0, s>>>(d.p, k, err.p);
+    int rows = nmax - k - 1;
+    if (rows > 0) {
+      int cols = rows + rmax;
+      dim3 grid(std::min((cols + 127) / 128, 8), rows, nsys);
+      lu_update_kernel<<<grid, 128, 0, s>>>(d.p, k);
+    }
+  }
+  lu_backsub_kernel<<<dim3(rmax, nsys), 256, 0, s>>>(d.p);
+  SLDM_CUDA(cudaGetLastError());
+  int herr = 0;
+  SLDM_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  SLDM_CUDA(cudaStreamSynchronize(s));
+  SLDM_REQUIRE(herr == 0, SLDM_ENUMERIC, "LU of M_l: zero or non-finite pivot");
+}
+
+// ---------------------------------------------------------------- batched skinny GEMV
+// Each warp owns one row of one job and produces that row for all right-hand
+// sides of the pass.  Rows are split over jobs by an exclusive prefix sum.
+template <class C, int NR>
+__global__ void __launch_bounds__(256) gemv_jobs_kernel(const GemvJob* __restrict__ jobs, const int64_t* __restrict__ rowstart,
+                                                        int njobs, int64_t total_rows, int nrhs) {
+  typedef typename CT<C>::R R;
+  const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= total_rows) return;
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (rowstart[mid] <= warp) lo = mid;
+    else hi = mid - 1;
+  }
+  const GemvJob J = jobs[lo];
+  const int64_t row = warp - rowstart[lo];
+  const C* __restrict__ A = reinterpret_cast<const C*>(J.A) + row * J.lda;
+  const C* __restrict__ x = reinterpret_cast<const C*>(J.x);
+  R accr[NR], acci[NR];
+#pragma unroll
+  for (int r = 0; r < NR; ++r) accr[r] = acci[r] = R(0);
+  if (sizeof(C) == 8) {
+    // complex64: 16-byte loads of two consecutive entries
+    const int n2 = J.n / 2;
+    const float4* A4 = reinterpret_cast<const float4*>(A);
+    const bool aligned = ((reinterpret_cast<uintptr_t>(A) & 15) == 0);
+    if (aligned) {
+      for (int c = lane; c < n2; c += 32) {
+        float4 a = __ldcs(A4 + c);
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+          if (r < nrhs) {
+            const C x0 = x[int64_t(r) * J.ldx + 2 * c], x1 = x[int64_t(r) * J.ldx + 2 * c + 1];
+            accr[r] += a.x * R(x0.x) - a.y * R(x0.y) + a.z * R(x1.x) - a.w * R(x1.y);
+            acci[r] += a.x * R(x0.y) + a.y * R(x0.x) + a.z * R(x1.y) + a.w * R(x1.x);
+          }
+        }
+      }
+      for (int c = 2 * n2 + lane; c < J.n; c += 32) {
+        C a = A[c];
+#pragma unroll
+        for (int r = 0; r < NR; ++r)
+          if (r < nrhs) {
+            C xv = x[int64_t(r) * J.ldx + c];
+            accr[r] += R(a.x) * R(xv.x) - R(a.y) * R(xv.y);
+            acci[r] += R(a.x) * R(xv.y) + R(a.y) * R(xv.x);
+          }
+      }
+    } else {
+      for (int c = lane; c < J.n; c += 32) {
+        C a = A[c];
+#pragma unroll
+        for (int r = 0; r < NR; ++r)
+          if (r < nrhs) {
+            C xv = x[int64_t(r) * J.ldx + c];
+            accr[r] += R(a.x) * R(xv.x) - R(a.y) * R(xv.y);
+            acci[r] += R(a.x) * R(xv.y) + R(a.y) * R(xv.x);
+          }
+      }
+    }
+  } else {
+    for (int c = lane; c < J.n; c += 32) {
+      C a = __ldcs(A + c);
+#pragma unroll
+      for (int r = 0; r < NR; ++r)
+        if (r < nrhs) {
+          C xv = x[int64_t(r) * J.ldx + c];
+          accr[r] += R(a.x) * R(xv.x) - R(a.y) * R(xv.y);
+          acci[r] += R(a.x) * R(xv.y) + R(a.y) * R(xv.x);
+        }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      accr[r] += __shfl_xor_sync(0xffffffffu, accr[r], o);
+      acci[r] += __shfl_xor_sync(0xffffffffu, acci[r], o);
+    }
+  }
+  if (lane == 0) {
+    C* y = reinterpret_cast<C*>(J.y);
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+      if (r < nrhs) {
+        R vr = R(J.ar) * accr[r] - R(J.ai) * acci[r];
+        R vi = R(J.ar) * acci[r] + R(J.ai) * accr[r];
+        C* yy = y + int64_t(r) * J.ldy + row;
+        if (J.beta) {
+          vr += yy->x;
+          vi += yy->y;
+        }
+        yy->x = vr;
+        yy->y = vi;
+      }
+  }
+}
+
+template <class C>
+void gemv_jobs(const GemvPlan& plan, int nrhs, cudaStream_t s) {
+  if (plan.njobs == 0) return;
+  const int64_t threads = plan.total_rows * 32;
+  const unsigned blocks = unsigned((threads + 255) / 256);
+  if (nrhs <= 1)
+    gemv_jobs_kernel<C, 1><<<blocks, 256, 0, s>>>(plan.jobs, plan.rowstart, plan.njobs, plan.total_rows, nrhs);
+  else if (nrhs <= 4)
+    gemv_jobs_kernel<C, 4><<<blocks, 256, 0, s>>>(plan.jobs, plan.rowstart, plan.njobs, plan.total_rows, nrhs);
+  else
+    gemv_jobs_kernel<C, 8><<<blocks, 256, 0, s>>>(plan.jobs, plan.rowstart, plan.njobs, plan.total_rows, nrhs);
+  SLDM_CUDA(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------- structured product glue
+// x (complex128, N x nrhs) -> op precision split vectors j (ne), e (ne), u (nq) per rhs.
+template <class C>
+__global__ void split_in_kernel(const double2* __restrict__ x, int64_t ldx, int ne, int nq, C* j, C* e, C* u, int nrhs) {
+  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  int r = blockIdx.y;
+  if (i >= 2 * ne + nq) return;
+  double2 v = x[int64_t(r) * ldx + i];
+  C c;
+  c.x = decltype(c.x)(v.x);
+  c.y = decltype(c.y)(v.y);
+  if (i < ne) j[int64_t(r) * ne + i] = c;
+  else if (i < 2 * ne) e[int64_t(r) * ne + (i - ne)] = c;
+  else u[int64_t(r) * nq + (i - 2 * ne)] = c;
+}
+
+// a = j - t1 (ne);  c = u + t2 (nq);  bc = B c, bu = B u (nt), one CTA per (object, rhs)
+template <class C>
+__global__ void prep_kernel(const ApplyDims D, const int32_t* __restrict__ tri_begin, const int32_t* __restrict__ edge_begin,
+                            const C* __restrict__ j, const C* __restrict__ u, const C* __restrict__ t1, const C* __restrict__ t2,
+                            C* a, C* c, C* bc, C* bu) {
+  typedef typename CT<C>::R R;
+  const int o = blockIdx.x, r = blockIdx.y;
+  const int t0 = tri_begin[o], t1e = tri_begin[o + 1];
+  const int q0 = t0 - o, nq_o = t1e - t0 - 1;
+  const int e0 = edge_begin[o], e1 = edge_begin[o + 1];
+  const C* jr = j + int64_t(r) * D.ne;
+  const C* t1r = t1 + int64_t(r) * D.ne;
+  C* ar = a + int64_t(r) * D.ne;
+  for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+    C v;
+    v.x = jr[e].x - t1r[e].x;
+    v.y = jr[e].y - t1r[e].y;
+    ar[e] = v;
+  }
+  const C* ur = u + int64_t(r) * D.nq;
+  const C* t2r = t2 + int64_t(r) * D.nq;
+  C* cr = c + int64_t(r) * D.nq;
+  C* bcr = bc + int64_t(r) * D.nt;
+  C* bur = bu + int64_t(r) * D.nt;
+  double sc_r = 0, sc_i = 0, su_r = 0, su_i = 0;
+  for (int q = threadIdx.x; q < nq_o; q += blockDim.x) {
+    C uv = ur[q0 + q];
+    C v;
+    v.x = uv.x + t2r[q0 + q].x;
+    v.y = uv.y + t2r[q0 + q].y;
+    cr[q0 + q] = v;
+    bcr[t0 + q] = v;
+    bur[t0 + q] = uv;
+    sc_r += v.x;
+    sc_i += v.y;
+    su_r += uv.x;
+    su_i += uv.y;
+  }
+  __shared__ double red[4][256];
+  red[0][threadIdx.x] = sc_r;
+  red[1][threadIdx.x] = sc_i;
+  red[2][threadIdx.x] = su_r;
+  red[3][threadIdx.x] = su_i;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+      for (int k = 0; k < 4; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    C v;
+    v.x = R(-red[0][0]);
+    v.y = R(-red[1][0]);
+    bcr[t1e - 1] = v;
+    v.x = R(-red[2][0]);
+    v.y = R(-red[3][0]);
+    bur[t1e - 1] = v;
+  }
+}
+
+// y1 = z1 + D^T z2 + I_x e;  y2 = w1 - w2 + D^T w3;  y3 = F D a + k0^2 c   (complex128 output)
+template <class C>
+__global__ void combine_kernel(const ApplyDims D, double k0, const int32_t* __restrict__ tplus, const int32_t* __restrict__ tminus,
+                               const int32_t* __restrict__ tri_edge, const int8_t* __restrict__ tri_sign,
+                               const int32_t* __restrict__ q2t, const int32_t* __restrict__ ix_ptr,
+                               const int32_t* __restrict__ ix_col, const double* __restrict__ ix_val, const C* __restrict__ z1,
+                               const C* __restrict__ z2, const C* __restrict__ w1, const C* __restrict__ w2,
+                               const C* __restrict__ w3, const C* __restrict__ e, const C* __restrict__ a,
+                               const C* __restrict__ c, double2* y, int64_t ldy) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int r = blockIdx.y;
+  const int ne = D.ne, nt = D.nt, nq = D.nq;
+  if (i >= 2 * ne + nq) return;
+  double vr, vi;
+  if (i < ne) {
+    const int m = int(i);
+    C a1 = z1[int64_t(r) * ne + m];
+    C p = z2[int64_t(r) * nt + tplus[m]], q = z2[int64_t(r) * nt + tminus[m]];
+    vr = double(a1.x) + double(p.x) - double(q.x);
+    vi = double(a1.y) + double(p.y) - double(q.y);
+    for (int z = ix_ptr[m]; z < ix_ptr[m + 1]; ++z) {
+      C ev = e[int64_t(r) * ne + ix_col[z]];
+      vr += ix_val[z] * double(ev.x);
+      vi += ix_val[z] * double(ev.y);
+    }
+  } else if (i < 2 * ne) {
+    const int m = int(i - ne);
+    C a1 = w1[int64_t(r) * ne + m], b1 = w2[int64_t(r) * ne + m];
+    C p = w3[int64_t(r) * nt + tplus[m]], q = w3[int64_t(r) * nt + tminus[m]];
+    vr = double(a1.x) - double(b1.x) + double(p.x) - double(q.x);
+    vi = double(a1.y) - double(b1.y) + double(p.y) - double(q.y);
+  } else {
+    const int qq = int(i - 2 * ne);
+    const int t = q2t[qq];  // triangle of charge unknown qq (each object's last triangle has none)
+    double sr = 0, si = 0;
+    for (int k = 0; k < 3; ++k) {
+      C av = a[int64_t(r) * ne + tri_edge[3 * t + k]];
+      double sg = double(tri_sign[3 * t + k]);
+      sr += sg * double(av.x);
+      si += sg * double(av.y);
+    }
+    C cv = c[int64_t(r) * nq + qq];
+    vr = sr + k0 * k0 * double(cv.x);
+    vi = si + k0 * k0 * double(cv.y);
+  }
+  y[int64_t(r) * ldy + i] = make_double2(vr, vi);
+}
+
+template <class C>
+void apply_glue_split(const double2* x, int64_t ldx, const ApplyDims& D, void* j, void* e, void* u, int nrhs, cudaStream_t s) {
+  int64_t N = 2 * D.ne + D.nq;
+  split_in_kernel<C><<<dim3(unsigned((N + 255) / 256), nrhs), 256, 0, s>>>(x, ldx, D.ne, D.nq, (C*)j, (C*)e, (C*)u, nrhs);
+  SLDM_CUDA(cudaGetLastError());
+}
+
+template <class C>
+void apply_glue_prep(const sldm_mesh* m, const ApplyDims& D, const void* j, const void* u, const void* t1, const void* t2,
+                     void* a, void* c, void* bc, void* bu, int nrhs, cudaStream_t s, const int32_t* tri_begin_dev,
+                     const int32_t* edge_begin_dev) {
+  prep_kernel<C><<<dim3(unsigned(D.nobj), nrhs), 256, 0, s>>>(D, tri_begin_dev, edge_begin_dev, (const C*)j, (const C*)u,
+                                                             (const C*)t1, (const C*)t2, (C*)a, (C*)c, (C*)bc, (C*)bu);
+  SLDM_CUDA(cudaGetLastError());
+}
+
+template <class C>
+void apply_glue_combine(const sldm_mesh* m, const ApplyDims& D, double k0, const double* ix_val, const void* z1,
+                        const void* z2, const void* w1, const void* w2, const void* w3, const void* e, const void* a,
+                        const void* c, double2* y, int64_t ldy, int nrhs, cudaStream_t s) {
+  int64_t N = 2 * D.ne + D.nq;
+  const DevMesh& d = m->d;
+  combine_kernel<C><<<dim3(unsigned((N + 255) / 256), nrhs), 256, 0, s>>>(
+      D, k0, d.tplus.p, d.tminus.p, d.tri_edge.p, d.tri_sign.p, d.q2t.p, d.ix_ptr.p, d.ix_col.p, ix_val, (const C*)z1,
+      (const C*)z2, (const C*)w1, (const C*)w2, (const C*)w3, (const C*)e, (const C*)a, (const C*)c, y, ldy);
+  SLDM_CUDA(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------- FP64 vector kernels for GMRES
+// h[i] = V[:, i]^H w  for i < k  (one CTA per column)
+__global__ void dots_kernel(const double2* __restrict__ V, int64_t ldv, const double2* __restrict__ w, int64_t n,
+                            double2* h) {
+  const int i = blockIdx.x;
+  const double2* v = V + int64_t(i) * ldv;
+  double sr = 0, si = 0;
+  for (int64_t t = threadIdx.x; t < n; t += blockDim.x) {
+    double2 a = v[t], b = w[t];
+    sr += a.x * b.x + a.y * b.y;  // conj(a) b
+    si += a.x * b.y - a.y * b.x;
+  }
+  __shared__ double rr[256], ri[256];
+  rr[threadIdx.x] = sr;
+  ri[threadIdx.x] = si;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      rr[threadIdx.x] += rr[threadIdx.x + s];
+      ri[threadIdx.x] += ri[threadIdx.x + s];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) h[i] = make_double2(rr[0], ri[0]);
+}
+
+// w -= V[:, :k] h   (or w += when sign = +1);  optionally accumulate hsum += h
+__global__ void vmul_kernel(const double2* __restrict__ V, int64_t ldv, int k, const double2* __restrict__ h, double sign,
+                            double2* w, int64_t n) {
+  int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  double sr = 0, si = 0;
+  for (int i = 0; i < k; ++i) {
+    double2 v = V[int64_t(i) * ldv + t];
+    double2 c = h[i];
+    sr += v.x * c.x - v.y * c.y;
+    si += v.x * c.y + v.y * c.x;
+  }
+  double2 o = w[t];
+  w[t] = make_double2(o.x + sign * sr, o.y + sign * si);
+}
+
+__global__ void norm2_kernel(const double2* __restrict__ w, int64_t n, double* out) {
+  double s = 0;
+  for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < n; t += int64_t(gridDim.x) * blockDim.x) {
+    double2 a = w[t];
+    s += a.x * a.x + a.y * a.y;
+  }
+  __shared__ double r[256];
+  r[threadIdx.x] = s;
+  __syncthreads();
+  for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+    if (threadIdx.x < k) r[threadIdx.x] += r[threadIdx.x + k];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) atomicAdd(out, r[0]);
+}
+
+// y = alpha * x + beta * y (complex128, real alpha/beta)
+__global__ void axpby_kernel(int64_t n, double alpha, const double2* __restrict__ x, double beta, double2* y) {
+  int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  double2 a = x[t], b = y[t];
+  y[t] = make_double2(alpha * a.x + beta * b.x, alpha * a.y + beta * b.y);
+}
+
+void vdots(const double2* V, int64_t ldv, int k, const double2* w, int64_t n, double2* h, cudaStream_t s) {
+  dots_kernel<<<k, 256, 0, s>>>(V, ldv, w, n, h);
+  SLDM_CUDA(cudaGetLastError());
+}
+void vmul(const double2* V, int64_t ldv, int k, const double2* h, double sign, double2* w, int64_t n, cudaStream_t s) {
+  vmul_kernel<<<unsigned((n + 255) / 256), 256, 0, s>>>(V, ldv, k, h, sign, w, n);
+  SLDM_CUDA(cudaGetLastError());
+}
+void vnorm2(const double2* w, int64_t n, double* out, cudaStream_t s) {
+  SLDM_CUDA(cudaMemsetAsync(out, 0, sizeof(double), s));
+  unsigned b = unsigned(std::min<int64_t>((n + 255) / 256, 1024));
+  norm2_kernel<<<b, 256, 0, s>>>(w, n, out);
+  SLDM_CUDA(cudaGetLastError());
+}
+void vaxpby(int64_t n, double alpha, const double2* x, double beta, double2* y, cudaStream_t s) {
+  axpby_kernel<<<unsigned((n + 255) / 256), 256, 0, s>>>(n, alpha, x, beta, y);
+  SLDM_CUDA(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------- conversions
+template <class C>
+__global__ void to_c128_kernel(const C* __restrict__ src, int64_t n, double2* dst) {
+  int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t < n) dst[t] = make_double2(double(src[t].x), double(src[t].y));
+}
+template <class C>
+__global__ void from_c128_kernel(const double2* __restrict__ src, int64_t n, C* dst) {
+  int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t < n) {
+    dst[t].x = decltype(dst[t].x)(src[t].x);
+    dst[t].y = decltype(dst[t].y)(src[t].y);
+  }
+}
+template <class C>
+void to_c128(const void* src, int64_t n, double2* dst, cudaStream_t s) {
+  to_c128_kernel<C><<<unsigned((n + 255) / 256), 256, 0, s>>>((const C*)src, n, dst);
+  SLDM_CUDA(cudaGetLastError());
+}
+template <class C>
+void from_c128(const double2* src, int64_t n, void* dst, cudaStream_t s) {
+  from_c128_kernel<C><<<unsigned((n + 255) / 256), 256, 0, s>>>(src, n, (C*)dst);
+  SLDM_CUDA(cudaGetLastError());
+}
+
+// add alpha * I_x (CSR, rows of an object) into a dense block
+template <class C>
+__global__ void add_ix_kernel(int e0, int ne_o, double alpha, const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
+                              const double* __restrict__ val, C* K, int64_t ld) {
+  int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= ne_o) return;
+  for (int z = ptr[e0 + m]; z < ptr[e0 + m + 1]; ++z) {
+    int n = col[z] - e0;
+    if (n >= 0 && n < ne_o) {
+      K[int64_t(m) * ld + n].x += decltype(K[0].x)(alpha * val[z]);
+    }
+  }
+}
+template <class C>
+void add_ix(const sldm_mesh* m, int obj, double alpha, const double* ix_val, void* K, int64_t ld, cudaStream_t s) {
+  int e0 = m->h.edge_begin[obj], ne_o = m->h.edge_begin[obj + 1] - e0;
+  add_ix_kernel<C><<<(ne_o + 127) / 128, 128, 0, s>>>(e0, ne_o, alpha, m->d.ix_ptr.p, m->d.ix_col.p, ix_val, (C*)K, ld);
+  SLDM_CUDA(cudaGetLastError());
+}
+
+// scale a dense block by a complex factor
+template <class C>
+__global__ void scale_kernel(C* A, int64_t n, double sr, double si) {
+  int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  double ar = A[t].x, ai = A[t].y;
+  A[t].x = decltype(A[t].x)(ar * sr - ai * si);
+  A[t].y = decltype(A[t].y)(ar * si + ai * sr);
+}
+
+#define INST(C)                                                                                                         \
+  template void build_Ml<C>(const sldm_mesh*, int, double, const void*, int64_t, const void*, int64_t, const void*,     \
+                            int64_t, const double*, double2*, double2*, cudaStream_t);                                  \
+  template void gemv_jobs<C>(const GemvPlan&, int, cudaStream_t);                                                       \
+  template void apply_glue_split<C>(const double2*, int64_t, const ApplyDims&, void*, void*, void*, int, cudaStream_t); \
+  template void apply_glue_prep<C>(const sldm_mesh*, const ApplyDims&, const void*, const void*, const void*,           \
+                                   const void*, void*, void*, void*, void*, int, cudaStream_t, const int32_t*,         \
+                                   const int32_t*);                                                                     \
+  template void apply_glue_combine<C>(const sldm_mesh*, const ApplyDims&, double, const double*, const void*,           \
+                                      const void*, const void*, const void*, const void*, const void*, const void*,     \
+                                      const void*, double2*, int64_t, int, cudaStream_t);                               \
+  template void to_c128<C>(const void*, int64_t, double2*, cudaStream_t);                                               \
+  template void from_c128<C>(const double2*, int64_t, void*, cudaStream_t);                                             \
+  template void add_ix<C>(const sldm_mesh*, int, double, const double*, void*, int64_t, cudaStream_t);
+INST(float2)
+INST(double2)
+
+}  // namespace sldm

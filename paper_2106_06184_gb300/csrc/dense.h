@@ -1,0 +1,67 @@
+// Declarations of the dense-algebra kernels (dense.cu).
+#pragma once
+#include "internal.h"
+
+namespace sldm {
+
+// One dense system A X = B solved in place (A: n x n, B: n x nrhs, row-major complex128).
+struct LUSys {
+  double2* A;
+  double2* B;
+  int32_t n, nrhs;
+};
+void lu_solve_batched(const std::vector<LUSys>& systems, cudaStream_t s);
+
+template <class C>
+void build_Ml(const sldm_mesh* m, int obj, double k0, const void* LAm, int64_t ldLA, const void* LPm, int64_t ldLP,
+              const void* Kl, int64_t ldK, const double* ix_val, double2* Ml, double2* Rl, cudaStream_t s);
+
+// y = (ar + j ai) A x + beta y over rows [0, m) of a row-major block; x, y hold
+// nrhs columns with strides ldx, ldy (entries of the op precision).
+struct GemvJob {
+  const void* A;
+  int64_t lda;
+  int32_t m, n;
+  const void* x;
+  int64_t ldx;
+  void* y;
+  int64_t ldy;
+  double ar, ai;
+  int32_t beta, pad;
+};
+struct GemvPlan {
+  GemvJob* jobs = nullptr;     // device
+  int64_t* rowstart = nullptr; // device, exclusive prefix sum of m
+  int njobs = 0;
+  int64_t total_rows = 0;
+};
+template <class C>
+void gemv_jobs(const GemvPlan& plan, int nrhs, cudaStream_t s);
+
+struct ApplyDims {
+  int32_t ne, nt, nq, nobj;
+};
+template <class C>
+void apply_glue_split(const double2* x, int64_t ldx, const ApplyDims& D, void* j, void* e, void* u, int nrhs, cudaStream_t s);
+template <class C>
+void apply_glue_prep(const sldm_mesh* m, const ApplyDims& D, const void* j, const void* u, const void* t1, const void* t2,
+                     void* a, void* c, void* bc, void* bu, int nrhs, cudaStream_t s, const int32_t* tri_begin_dev,
+                     const int32_t* edge_begin_dev);
+template <class C>
+void apply_glue_combine(const sldm_mesh* m, const ApplyDims& D, double k0, const double* ix_val, const void* z1,
+                        const void* z2, const void* w1, const void* w2, const void* w3, const void* e, const void* a,
+                        const void* c, double2* y, int64_t ldy, int nrhs, cudaStream_t s);
+
+void vdots(const double2* V, int64_t ldv, int k, const double2* w, int64_t n, double2* h, cudaStream_t s);
+void vmul(const double2* V, int64_t ldv, int k, const double2* h, double sign, double2* w, int64_t n, cudaStream_t s);
+void vnorm2(const double2* w, int64_t n, double* out, cudaStream_t s);
+void vaxpby(int64_t n, double alpha, const double2* x, double beta, double2* y, cudaStream_t s);
+
+template <class C>
+void to_c128(const void* src, int64_t n, double2* dst, cudaStream_t s);
+template <class C>
+void from_c128(const double2* src, int64_t n, void* dst, cudaStream_t s);
+template <class C>
+void add_ix(const sldm_mesh* m, int obj, double alpha, const double* ix_val, void* K, int64_t ld, cudaStream_t s);
+
+}  // namespace sldm

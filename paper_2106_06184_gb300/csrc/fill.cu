@@ -1,0 +1,965 @@
+// Triangle-pair Gauss-quadrature fill of the SLDM operators (Sec. II-B, II-C):
+//   L^A[m,n]   = int f_m . int f_n G        (RWG x RWG)           Eq. opLAhgf
+//   L^phi[p,q] = int int h_p h_q G          (pulse x pulse)       Eq. opLphihgf
+//   Kbar[m,k]  = int f_m . PV int grad G x g_k   (RWG x barycentric RWG; the BC
+//                functions are sums of g_k, contracted afterwards)  Eq. opKhgf
+// with G = exp(-j k R)/(4 pi R) (Eq. hgf), 6-point Dunavant rules on both
+// triangles, and singularity extraction on touching pairs computed in FP64.
+//
+// GPU design: every pair is reduced to a handful of complex "moments" in
+// triangle-local coordinates (r = c + rho), so that the 3x3 RWG combinations
+// and the absolute coordinates never enter the inner loop.  One thread owns a
+// source triangle (coalesced SoA record), a CTA walks a tile of test triangles
+// held in shared memory, and the 3x3 results are scattered with atomics
+// (each edge-pair entry gets four triangle-pair contributions).
+#include <cmath>
+
+#include "internal.h"
+
+namespace sldm {
+
+// ---------------------------------------------------------------- Dunavant rule
+// Six-point degree-4 rule (Dunavant 1985): barycentric points and weights
+// (weights sum to 1).
+__constant__ double c_bary[6][3] = {
+    {0.108103018168070, 0.445948490915965, 0.445948490915965},
+    {0.445948490915965, 0.108103018168070, 0.445948490915965},
+    {0.445948490915965, 0.445948490915965, 0.108103018168070},
+    {0.816847572980459, 0.091576213509771, 0.091576213509771},
+    {0.091576213509771, 0.816847572980459, 0.091576213509771},
+    {0.091576213509771, 0.091576213509771, 0.816847572980459}};
+__constant__ double c_w[6] = {0.223381589678011, 0.223381589678011, 0.223381589678011,
+                              0.109951743655322, 0.109951743655322, 0.109951743655322};
+
+constexpr double PI = 3.14159265358979323846;
+constexpr double INV4PI = 0.25 / PI;
+
+// ---------------------------------------------------------------- geometry
+// Writes a GEO_STRIDE record for a triangle with vertices p0, p1, p2 and edge
+// signs s (s_i for the edge opposite vertex i).
+__device__ void write_geo(double* g, const double* p0, const double* p1, const double* p2, const double s[3]) {
+  double c[3], u[3], w[3], cr[3];
+  for (int d = 0; d < 3; ++d) {
+    c[d] = (p0[d] + p1[d] + p2[d]) / 3.0;
+    u[d] = p1[d] - p0[d];
+    w[d] = p2[d] - p0[d];
+  }
+  cr[0] = u[1] * w[2] - u[2] * w[1];
+  cr[1] = u[2] * w[0] - u[0] * w[2];
+  cr[2] = u[0] * w[1] - u[1] * w[0];
+  double n2 = sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+  double A = 0.5 * n2;
+  for (int d = 0; d < 3; ++d) {
+    g[GEO_C + d] = c[d];
+    g[GEO_N + d] = cr[d] / n2;
+  }
+  g[GEO_A] = A;
+  const double* P[3] = {p0, p1, p2};
+  for (int q = 0; q < 6; ++q) {
+    for (int d = 0; d < 3; ++d) {
+      double r = c_bary[q][0] * p0[d] + c_bary[q][1] * p1[d] + c_bary[q][2] * p2[d];
+      g[GEO_RHO + 3 * q + d] = r - c[d];
+    }
+    g[GEO_W + q] = c_w[q] * A;
+  }
+  for (int i = 0; i < 3; ++i) {
+    for (int d = 0; d < 3; ++d) g[GEO_AV + 3 * i + d] = c[d] - P[i][d];
+    g[GEO_SIG + i] = s[i] / (2.0 * A);
+  }
+}
+
+__global__ void geometry_kernel(int nt, const double* __restrict__ xyz, const int32_t* __restrict__ tri,
+                                const int32_t* __restrict__ tri_edge, const int8_t* __restrict__ tri_sign,
+                                const int8_t* __restrict__ btri_sign, int64_t nv, double* geo, double* bgeo) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nt) return;
+  const double* a = xyz + 3 * tri[3 * t];
+  const double* b = xyz + 3 * tri[3 * t + 1];
+  const double* c = xyz + 3 * tri[3 * t + 2];
+  double s[3] = {double(tri_sign[3 * t]), double(tri_sign[3 * t + 1]), double(tri_sign[3 * t + 2])};
+  write_geo(geo + size_t(t) * GEO_STRIDE, a, b, c, s);
+  double mab[3], mbc[3], mca[3], g[3];
+  for (int d = 0; d < 3; ++d) {
+    mab[d] = 0.5 * (a[d] + b[d]);
+    mbc[d] = 0.5 * (b[d] + c[d]);
+    mca[d] = 0.5 * (c[d] + a[d]);
+    g[d] = (a[d] + b[d] + c[d]) / 3.0;
+  }
+  // children: (a, m_ab, g) (m_ab, b, g) (b, m_bc, g) (m_bc, c, g) (c, m_ca, g) (m_ca, a, g)
+  const double* ch[6][3] = {{a, mab, g}, {mab, b, g}, {b, mbc, g}, {mbc, c, g}, {c, mca, g}, {mca, a, g}};
+  for (int k = 0; k < 6; ++k) {
+    int cc = 6 * t + k;
+    double sb[3] = {double(btri_sign[3 * cc]), double(btri_sign[3 * cc + 1]), double(btri_sign[3 * cc + 2])};
+    write_geo(bgeo + size_t(cc) * GEO_STRIDE, ch[k][0], ch[k][1], ch[k][2], sb);
+  }
+}
+
+void geometry(const HostMesh& hm, DevMesh& dm, cudaStream_t s) {
+  dm.geo.alloc(size_t(hm.nt) * GEO_STRIDE);
+  dm.bgeo.alloc(size_t(hm.nt) * 6 * GEO_STRIDE);
+  int nt = int(hm.nt);
+  geometry_kernel<<<(nt + 127) / 128, 128, 0, s>>>(nt, dm.xyz.p, dm.tri.p, dm.tri_edge.p, dm.tri_sign.p,
+                                                   dm.btri_sign.p, hm.nv, dm.geo.p, dm.bgeo.p);
+  SLDM_CUDA(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------- precision traits
+template <class R>
+struct M;
+template <>
+struct M<float> {
+  static __device__ __forceinline__ void sincos_(float x, float* s, float* c) { sincosf(x, s, c); }
+  static __device__ __forceinline__ float exp_(float x) { return expf(x); }
+  static __device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
+  static __device__ __forceinline__ void add(void* base, int64_t idx, float re, float im) {
+    atomicAdd(reinterpret_cast<float2*>(base) + idx, make_float2(re, im));
+  }
+  static __device__ __forceinline__ void store(void* base, int64_t idx, double re, double im) {
+    reinterpret_cast<float2*>(base)[idx] = make_float2(float(re), float(im));
+  }
+};
+template <>
+struct M<double> {
+  static __device__ __forceinline__ void sincos_(double x, double* s, double* c) { sincos(x, s, c); }
+  static __device__ __forceinline__ double exp_(double x) { return exp(x); }
+  static __device__ __forceinline__ double rsqrt_(double x) { return rsqrt(x); }
+  static __device__ __forceinline__ void add(void* base, int64_t idx, double re, double im) {
+    double* p = reinterpret_cast<double*>(base) + 2 * idx;
+    atomicAdd(p, re);
+    atomicAdd(p + 1, im);
+  }
+  static __device__ __forceinline__ void store(void* base, int64_t idx, double re, double im) {
+    reinterpret_cast<double2*>(base)[idx] = make_double2(re, im);
+  }
+};
+// atomic add of a double result into a destination of precision R
+template <class R>
+__device__ __forceinline__ void add_d(void* base, int64_t idx, double re, double im) {
+  M<R>::add(base, idx, R(re), R(im));
+}
+
+// ---------------------------------------------------------------- bulk L kernel
+constexpr int TILE_SRC = 128;  // source triangles per CTA (one per thread)
+constexpr int TILE_TEST = 8;   // test triangles per CTA
+
+struct TileRef {
+  int32_t task, test0, src0, pad;
+};
+
+template <class R>
+struct TestRec {
+  R rho[18], W[6], av[9], sig[3];
+  double c[3];
+  double invA;
+  int32_t v[3], e[3];
+};
+
+template <class R>
+__global__ void __launch_bounds__(TILE_SRC) fill_L_bulk(const LTask* __restrict__ tasks, const TileRef* __restrict__ tiles,
+                                                        const double* __restrict__ geo, const int32_t* __restrict__ tri,
+                                                        const int32_t* __restrict__ tri_edge) {
+  __shared__ TestRec<R> T[TILE_TEST];
+  const TileRef tile = tiles[blockIdx.x];
+  const LTask tk = tasks[tile.task];
+  // load the test tile
+  for (int idx = threadIdx.x; idx < TILE_TEST; idx += blockDim.x) {
+    int t = tile.test0 + idx;
+    if (t < tk.ntest) {
+      int tg = tk.t0 + t;
+      const double* g = geo + size_t(tg) * GEO_STRIDE;
+      for (int d = 0; d < 18; ++d) T[idx].rho[d] = R(g[GEO_RHO + d]);
+      for (int d = 0; d < 6; ++d) T[idx].W[d] = R(g[GEO_W + d]);
+      for (int d = 0; d < 9; ++d) T[idx].av[d] = R(g[GEO_AV + d]);
+      for (int d = 0; d < 3; ++d) {
+        T[idx].sig[d] = R(g[GEO_SIG + d]);
+        T[idx].c[d] = g[GEO_C + d];
+        T[idx].v[d] = tri[3 * tg + d];
+        T[idx].e[d] = tri_edge[3 * tg + d];
+      }
+      T[idx].invA = 1.0 / g[GEO_A];
+    }
+  }
+  __syncthreads();
+  const int s = tile.src0 + threadIdx.x;
+  if (s >= tk.nsrc) return;
+  const int sg = tk.s0 + s;
+  const double* gs = geo + size_t(sg) * GEO_STRIDE;
+  R rs[18], Ws[6], bv[9], sg_[3];
+  double cs[3];
+#pragma unroll
+  for (int d = 0; d < 18; ++d) rs[d] = R(gs[GEO_RHO + d]);
+#pragma unroll
+  for (int d = 0; d < 6; ++d) Ws[d] = R(gs[GEO_W + d]);
+#pragma unroll
+  for (int d = 0; d < 9; ++d) bv[d] = R(gs[GEO_AV + d]);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    sg_[d] = R(gs[GEO_SIG + d]);
+    cs[d] = gs[GEO_C + d];
+  }
+  const double invAs = 1.0 / gs[GEO_A];
+  const int32_t sv0 = tri[3 * sg], sv1 = tri[3 * sg + 1], sv2 = tri[3 * sg + 2];
+  const int32_t se[3] = {tri_edge[3 * sg], tri_edge[3 * sg + 1], tri_edge[3 * sg + 2]};
+  const R kr = R(tk.kr), ki = R(tk.ki);
+  const R c4pi = R(INV4PI);
+
+  for (int tt = 0; tt < TILE_TEST; ++tt) {
+    if (tile.test0 + tt >= tk.ntest) break;
+    const TestRec<R>& X = T[tt];
+    // touching pairs (sharing a vertex) are computed by the FP64 extraction kernel
+    bool touch = false;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) touch |= (X.v[i] == sv0) | (X.v[i] == sv1) | (X.v[i] == sv2);
+    if (touch) continue;
+    const R dc0 = R(X.c[0] - cs[0]), dc1 = R(X.c[1] - cs[1]), dc2 = R(X.c[2] - cs[2]);
+    R m0r = 0, m0i = 0, mqr[3] = {0, 0, 0}, mqi[3] = {0, 0, 0}, msr[3] = {0, 0, 0}, msi[3] = {0, 0, 0};
+    R mqsr = 0, mqsi = 0;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      const R px = dc0 + X.rho[3 * q], py = dc1 + X.rho[3 * q + 1], pz = dc2 + X.rho[3 * q + 2];
+      R ar = 0, ai = 0, br[3] = {0, 0, 0}, bi[3] = {0, 0, 0};
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        const R dx = px - rs[3 * k], dy = py - rs[3 * k + 1], dz = pz - rs[3 * k + 2];
+        const R r2 = dx * dx + dy * dy + dz * dz;
+        const R ir = M<R>::rsqrt_(r2);
+        const R Rr = r2 * ir;
+        R sn, cn;
+        M<R>::sincos_(kr * Rr, &sn, &cn);
+        const R amp = (ki != R(0) ? M<R>::exp_(ki * Rr) : R(1)) * c4pi * ir * Ws[k];
+        const R gr = amp * cn, gi = -amp * sn;
+        ar += gr;
+        ai += gi;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          br[d] += gr * rs[3 * k + d];
+          bi[d] += gi * rs[3 * k + d];
+        }
+      }
+      const R w = X.W[q];
+      m0r += w * ar;
+      m0i += w * ai;
+      R dotr = 0, doti = 0;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const R rq = X.rho[3 * q + d];
+        mqr[d] += w * ar * rq;
+        mqi[d] += w * ai * rq;
+        msr[d] += w * br[d];
+        msi[d] += w * bi[d];
+        dotr += rq * br[d];
+        doti += rq * bi[d];
+      }
+      mqsr += w * dotr;
+      mqsi += w * doti;
+    }
+    // local RWG x RWG: sig_i sig_j [Mqs + a_i.Ms + b_j.Mq + (a_i.b_j) M0]
+    if (tk.A) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const R ax = X.av[3 * i], ay = X.av[3 * i + 1], az = X.av[3 * i + 2];
+        const R ams_r = ax * msr[0] + ay * msr[1] + az * msr[2];
+        const R ams_i = ax * msi[0] + ay * msi[1] + az * msi[2];
+        const int64_t row = int64_t(X.e[i] - tk.e_row0) * tk.ldA;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          const R bx = bv[3 * j], by = bv[3 * j + 1], bz = bv[3 * j + 2];
+          const R ab = ax * bx + ay * by + az * bz;
+          R vr = mqsr + ams_r + bx * mqr[0] + by * mqr[1] + bz * mqr[2] + ab * m0r;
+          R vi = mqsi + ams_i + bx * mqi[0] + by * mqi[1] + bz * mqi[2] + ab * m0i;
+          const R sc = X.sig[i] * sg_[j];
+          vr *= sc;
+          vi *= sc;
+          M<R>::add(tk.A, row + (se[j] - tk.e_col0), vr * R(tk.sAr) - vi * R(tk.sAi), vr * R(tk.sAi) + vi * R(tk.sAr));
+        }
+      }
+    }
+    if (tk.P) {
+      const R sc = R(X.invA * invAs);
+      const R vr = m0r * sc, vi = m0i * sc;
+      const int t = tile.test0 + tt;
+      M<R>::store(tk.P, int64_t(t + tk.t0 - tk.t_row0) * tk.ldP + (sg - tk.t_col0), double(vr * R(tk.sPr) - vi * R(tk.sPi)),
+                  double(vr * R(tk.sPi) + vi * R(tk.sPr)));
+    }
+  }
+}
+
+// ---------------------------------------------------------------- FP64 closed forms
+// Integrals over the flat triangle (p1, p2, p3) seen from r (see the oracle's
+// derivation: contour reduction with the surface divergence theorem).
+struct Pot {
+  double inv_r, r;            // int 1/R, int R
+  double por[3], pr[3];       // int (rho' - rho)/R, int (rho' - rho) R
+  double grad[3];             // int grad_r (1/R)
+  double rho[3];              // projection of r on the plane
+};
+
+__device__ void potentials(const double* r, const double* p1, const double* p2, const double* p3, Pot& o) {
+  double u[3], w[3], n[3];
+  for (int d = 0; d < 3; ++d) {
+    u[d] = p2[d] - p1[d];
+    w[d] = p3[d] - p1[d];
+  }
+  n[0] = u[1] * w[2] - u[2] * w[1];
+  n[1] = u[2] * w[0] - u[0] * w[2];
+  n[2] = u[0] * w[1] - u[1] * w[0];
+  double nn = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+  for (int d = 0; d < 3; ++d) n[d] /= nn;
+  double h = n[0] * (r[0] - p1[0]) + n[1] * (r[1] - p1[1]) + n[2] * (r[2] - p1[2]);
+  for (int d = 0; d < 3; ++d) o.rho[d] = r[d] - h * n[d];
+  double ah = fabs(h);
+  double sum_tf = 0, omega = 0, sum_r = 0;
+  double por[3] = {0, 0, 0}, pr[3] = {0, 0, 0}, gm[3] = {0, 0, 0};
+  const double* P[4] = {p1, p2, p3, p1};
+  for (int e = 0; e < 3; ++e) {
+    const double* a = P[e];
+    const double* b = P[e + 1];
+    double s[3], m[3];
+    double L = sqrt((b[0] - a[0]) * (b[0] - a[0]) + (b[1] - a[1]) * (b[1] - a[1]) + (b[2] - a[2]) * (b[2] - a[2]));
+    for (int d = 0; d < 3; ++d) s[d] = (b[d] - a[d]) / L;
+    m[0] = s[1] * n[2] - s[2] * n[1];
+    m[1] = s[2] * n[0] - s[0] * n[2];
+    m[2] = s[0] * n[1] - s[1] * n[0];
+    double sm = 0, sp = 0, t0 = 0;
+    for (int d = 0; d < 3; ++d) {
+      sm += (a[d] - o.rho[d]) * s[d];
+      sp += (b[d] - o.rho[d]) * s[d];
+      t0 += (a[d] - o.rho[d]) * m[d];
+    }
+    double R02 = t0 * t0 + h * h;
+    double Rm = sqrt(sm * sm + R02), Rp = sqrt(sp * sp + R02);
+    double f;
+    if (sp <= 0 && sm <= 0) {
+      f = log((Rm - sm) / (Rp - sp));
+    } else {
+      double num = sp > 0 ? Rp + sp : R02 / (Rp - sp);
+      double den = sm > 0 ? Rm + sm : R02 / (Rm - sm);
+      f = log(num / den);
+    }
+    double q1 = R02 + ah * Rp, q2 = R02 + ah * Rm;
+    double beta = (q1 > 0 ? atan(t0 * sp / q1) : 0.0) - (q2 > 0 ? atan(t0 * sm / q2) : 0.0);
+    omega += beta;
+    sum_tf += t0 * f;
+    double line1 = sp * Rp - sm * Rm + R02 * f;  // 2 int_edge R dl
+    sum_r += t0 * line1;
+    double line3 = (sp * Rp * Rp * Rp - sm * Rm * Rm * Rm) / 4.0 + 3.0 * R02 * (sp * Rp - sm * Rm) / 8.0 +
+                   3.0 * R02 * R02 * f / 8.0;   // int_edge R^3 dl
+    for (int d = 0; d < 3; ++d) {
+      por[d] += m[d] * 0.5 * line1;
+      pr[d] += m[d] * line3 / 3.0;
+      gm[d] -= m[d] * f;
+    }
+  }
+  o.inv_r = sum_tf - ah * omega;
+  o.r = sum_r / 6.0 + h * h / 3.0 * o.inv_r;
+  double sg = h > 0 ? 1.0 : (h < 0 ? -1.0 : 0.0);
+  for (int d = 0; d < 3; ++d) {
+    o.por[d] = por[d];
+    o.pr[d] = pr[d];
+    o.grad[d] = gm[d] - sg * omega * n[d];
+  }
+}
+
+// complex helpers (double)
+struct cd {
+  double r, i;
+};
+__device__ __forceinline__ cd cmul(cd a, cd b) { return {a.r * b.r - a.i * b.i, a.r * b.i + a.i * b.r}; }
+
+// G - 1/(4 pi R) + k^2 R/(8 pi) (Taylor series for |kR| < 0.05)
+__device__ cd green_smooth(cd k, double R) {
+  cd x = {k.r * R, k.i * R};
+  double ax = sqrt(x.r * x.r + x.i * x.i);
+  if (ax < 0.05) {
+    // sum_{n>=1, n!=2} (-j k)^n R^(n-1) / n!
+    cd mjk = {k.i, -k.r};  // -j k
+    cd p = mjk;            // (-jk)^1
+    cd acc = p;            // n = 1 term (R^0)
+    double Rp = 1.0, fact = 1.0;
+    for (int n = 2; n <= 11; ++n) {
+      p = cmul(p, mjk);
+      Rp *= R;
+      fact *= n;
+      if (n == 2) continue;
+      acc.r += p.r * Rp / fact;
+      acc.i += p.i * Rp / fact;
+    }
+    return {acc.r * INV4PI, acc.i * INV4PI};
+  }
+  double sn, cn;
+  sincos(x.r, &sn, &cn);
+  double ex = exp(x.i);  // exp(-j k R) = exp(ki R) (cos - j sin)
+  cd e = {ex * cn - 1.0, -ex * sn};
+  cd k2 = cmul(k, k);
+  return {e.r * INV4PI / R + k2.r * R * 0.5 * INV4PI, e.i * INV4PI / R + k2.i * R * 0.5 * INV4PI};
+}
+
+// g1 of grad(G - 1/(4 pi R)) = (r - r') g1: (1 - (1 + jkR) exp(-jkR)) / (4 pi R^3)
+__device__ cd grad_smooth(cd k, double R) {
+  cd x = {-k.i * R, k.r * R};  // j k R
+  double ax = sqrt(x.r * x.r + x.i * x.i);
+  double iR3 = INV4PI / (R * R * R);
+  if (ax < 0.05) {
+    // sum_{n>=2} (-1)^n (n-1) x^n / n!
+    cd p = x, acc = {0, 0};
+    double fact = 1.0;
+    for (int n = 2; n <= 13; ++n) {
+      p = cmul(p, x);
+      fact *= n;
+      double c = ((n & 1) ? -1.0 : 1.0) * (n - 1) / fact;
+      acc.r += c * p.r;
+      acc.i += c * p.i;
+    }
+    return {acc.r * iR3, acc.i * iR3};
+  }
+  double sn, cn;
+  sincos(k.r * R, &sn, &cn);
+  double ex = exp(k.i * R);
+  cd e = {ex * cn, -ex * sn};              // exp(-jkR)
+  cd one_x = {1.0 + x.r, x.i};             // 1 + jkR
+  cd pr = cmul(one_x, e);
+  return {(1.0 - pr.r) * iR3, -pr.i * iR3};
+}
+
+// ---------------------------------------------------------------- FP64 touching L pairs
+template <class R>
+__global__ void fill_L_touch(LTask tk, const int32_t* __restrict__ pa, const int32_t* __restrict__ pb, int npairs,
+                             const double* __restrict__ geo, const double* __restrict__ xyz,
+                             const int32_t* __restrict__ tri, const int32_t* __restrict__ tri_edge) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= npairs) return;
+  const int t = pa[p], s = pb[p];
+  if (t < tk.t0 || t >= tk.t0 + tk.ntest || s < tk.s0 || s >= tk.s0 + tk.nsrc) return;
+  const double* gt = geo + size_t(t) * GEO_STRIDE;
+  const double* gs = geo + size_t(s) * GEO_STRIDE;
+  const double* v1 = xyz + 3 * tri[3 * s];
+  const double* v2 = xyz + 3 * tri[3 * s + 1];
+  const double* v3 = xyz + 3 * tri[3 * s + 2];
+  const cd k = {tk.kr, tk.ki};
+  const cd k2 = cmul(k, k);
+  cd m0 = {0, 0}, mq[3] = {{0, 0}, {0, 0}, {0, 0}}, ms[3] = {{0, 0}, {0, 0}, {0, 0}}, mqs = {0, 0};
+  for (int q = 0; q < 6; ++q) {
+    double r[3];
+    for (int d = 0; d < 3; ++d) r[d] = gt[GEO_C + d] + gt[GEO_RHO + 3 * q + d];
+    // remainder by the 6-point rule: A = sum W' Gs, B = sum W' Gs rho'
+    cd A = {0, 0}, B[3] = {{0, 0}, {0, 0}, {0, 0}};
+    for (int j = 0; j < 6; ++j) {
+      double dx = r[0] - gs[GEO_C] - gs[GEO_RHO + 3 * j];
+      double dy = r[1] - gs[GEO_C + 1] - gs[GEO_RHO + 3 * j + 1];
+      double dz = r[2] - gs[GEO_C + 2] - gs[GEO_RHO + 3 * j + 2];
+      double Rr = sqrt(dx * dx + dy * dy + dz * dz);
+      cd g = green_smooth(k, Rr);
+      double w = gs[GEO_W + j];
+      A.r += w * g.r;
+      A.i += w * g.i;
+      for (int d = 0; d < 3; ++d) {
+        B[d].r += w * g.r * gs[GEO_RHO + 3 * j + d];
+        B[d].i += w * g.i * gs[GEO_RHO + 3 * j + d];
+      }
+    }
+    // closed forms: 1/(4 pi R) - k^2 R/(8 pi)
+    Pot P;
+    potentials(r, v1, v2, v3, P);
+    A.r += INV4PI * P.inv_r - k2.r * 0.5 * INV4PI * P.r;
+    A.i += -k2.i * 0.5 * INV4PI * P.r;
+    for (int d = 0; d < 3; ++d) {
+      double off = P.rho[d] - gs[GEO_C + d];  // (r' - c') = P + (rho - c')
+      double s1 = P.por[d] + off * P.inv_r;
+      double sR = P.pr[d] + off * P.r;
+      B[d].r += INV4PI * s1 - k2.r * 0.5 * INV4PI * sR;
+      B[d].i += -k2.i * 0.5 * INV4PI * sR;
+    }
+    double w = gt[GEO_W + q];
+    m0.r += w * A.r;
+    m0.i += w * A.i;
+    for (int d = 0; d < 3; ++d) {
+      double rq = gt[GEO_RHO + 3 * q + d];
+      mq[d].r += w * A.r * rq;
+      mq[d].i += w * A.i * rq;
+      ms[d].r += w * B[d].r;
+      ms[d].i += w * B[d].i;
+      mqs.r += w * rq * B[d].r;
+      mqs.i += w * rq * B[d].i;
+    }
+  }
+  if (tk.A) {
+    for (int i = 0; i < 3; ++i) {
+      const double* a = gt + GEO_AV + 3 * i;
+      for (int j = 0; j < 3; ++j) {
+        const double* b = gs + GEO_AV + 3 * j;
+        double ab = a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+        cd v = mqs;
+        for (int d = 0; d < 3; ++d) {
+          v.r += a[d] * ms[d].r + b[d] * mq[d].r;
+          v.i += a[d] * ms[d].i + b[d] * mq[d].i;
+        }
+        v.r += ab * m0.r;
+        v.i += ab * m0.i;
+        double sc = gt[GEO_SIG + i] * gs[GEO_SIG + j];
+        cd out = cmul({v.r * sc, v.i * sc}, {tk.sAr, tk.sAi});
+        add_d<R>(tk.A, int64_t(tri_edge[3 * t + i] - tk.e_row0) * tk.ldA + (tri_edge[3 * s + j] - tk.e_col0), out.r, out.i);
+      }
+    }
+  }
+  if (tk.P) {
+    double sc = 1.0 / (gt[GEO_A] * gs[GEO_A]);
+    cd out = cmul({m0.r * sc, m0.i * sc}, {tk.sPr, tk.sPi});
+    M<R>::store(tk.P, int64_t(t - tk.t_row0) * tk.ldP + (s - tk.t_col0), out.r, out.i);
+  }
+}
+
+// ---------------------------------------------------------------- bulk Kbar kernel (primal test x child source)
+template <class R>
+__global__ void __launch_bounds__(TILE_SRC) fill_K_bulk(const KTask* __restrict__ tasks, const TileRef* __restrict__ tiles,
+                                                        const double* __restrict__ geo, const double* __restrict__ bgeo,
+                                                        const int32_t* __restrict__ tri, const int32_t* __restrict__ tri_edge,
+                                                        const int32_t* __restrict__ btri_edge) {
+  __shared__ TestRec<R> T[TILE_TEST];
+  const TileRef tile = tiles[blockIdx.x];
+  const KTask tk = tasks[tile.task];
+  for (int idx = threadIdx.x; idx < TILE_TEST; idx += blockDim.x) {
+    int t = tile.test0 + idx;
+    if (t < tk.ntest) {
+      int tg = tk.t0 + t;
+      const double* g = geo + size_t(tg) * GEO_STRIDE;
+      for (int d = 0; d < 18; ++d) T[idx].rho[d] = R(g[GEO_RHO + d]);
+      for (int d = 0; d < 6; ++d) T[idx].W[d] = R(g[GEO_W + d]);
+      for (int d = 0; d < 9; ++d) T[idx].av[d] = R(g[GEO_AV + d]);
+      for (int d = 0; d < 3; ++d) {
+        T[idx].sig[d] = R(g[GEO_SIG + d]);
+        T[idx].c[d] = g[GEO_C + d];
+        T[idx].v[d] = tri[3 * tg + d];
+        T[idx].e[d] = tri_edge[3 * tg + d];
+      }
+    }
+  }
+  __syncthreads();
+  const int s = tile.src0 + threadIdx.x;
+  if (s >= tk.nsrc) return;
+  const int cg = tk.c0 + s;       // child id
+  const int par = cg / 6, kk = cg % 6, pp = kk / 2;
+  const int32_t cv = tri[3 * par + ((kk & 1) ? (pp + 1) % 3 : pp)];  // child's primal vertex
+  const int32_t ce = tri_edge[3 * par + (pp + 2) % 3];                // edge of the child's midpoint
+  const double* gs = bgeo + size_t(cg) * GEO_STRIDE;
+  R rs[18], Ws[6], bv[9], sg_[3];
+  double cs[3];
+#pragma unroll
+  for (int d = 0; d < 18; ++d) rs[d] = R(gs[GEO_RHO + d]);
+#pragma unroll
+  for (int d = 0; d < 6; ++d) Ws[d] = R(gs[GEO_W + d]);
+#pragma unroll
+  for (int d = 0; d < 9; ++d) bv[d] = R(gs[GEO_AV + d]);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    sg_[d] = R(gs[GEO_SIG + d]);
+    cs[d] = gs[GEO_C + d];
+  }
+  const int32_t be[3] = {btri_edge[3 * cg], btri_edge[3 * cg + 1], btri_edge[3 * cg + 2]};
+  const R kr = R(tk.kr), ki = R(tk.ki);
+  const R c4pi = R(INV4PI);
+
+  for (int tt = 0; tt < TILE_TEST; ++tt) {
+    const int t = tile.test0 + tt;
+    if (t >= tk.ntest) break;
+    const TestRec<R>& X = T[tt];
+    if (tk.t0 + t == par) continue;  // child of the test triangle: coplanar, Kbar = 0
+    bool touch = false;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) touch |= (X.v[i] == cv) | (X.e[i] == ce);
+    if (touch) continue;  // FP64 extraction kernel
+    const R dc0 = R(X.c[0] - cs[0]), dc1 = R(X.c[1] - cs[1]), dc2 = R(X.c[2] - cs[2]);
+    R p1r = 0, p1i = 0, p2r[3] = {0, 0, 0}, p2i[3] = {0, 0, 0}, xr[3] = {0, 0, 0}, xi[3] = {0, 0, 0};
+    R sr[3] = {0, 0, 0}, si[3] = {0, 0, 0};
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      const R rqx = X.rho[3 * q], rqy = X.rho[3 * q + 1], rqz = X.rho[3 * q + 2];
+      const R px = dc0 + rqx, py = dc1 + rqy, pz = dc2 + rqz;
+      R ur[3] = {0, 0, 0}, ui[3] = {0, 0, 0}, vr[3] = {0, 0, 0}, vi[3] = {0, 0, 0};
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        const R dx = px - rs[3 * k], dy = py - rs[3 * k + 1], dz = pz - rs[3 * k + 2];
+        const R r2 = dx * dx + dy * dy + dz * dz;
+        const R ir = M<R>::rsqrt_(r2);
+        const R Rr = r2 * ir;
+        R sn, cn;
+        M<R>::sincos_(kr * Rr, &sn, &cn);
+        const R amp = (ki != R(0) ? M<R>::exp_(ki * Rr) : R(1)) * c4pi * ir * ir * ir * Ws[k];
+        // g1 = -(1 + j k R) exp(-j k R) / (4 pi R^3)
+        const R er = amp * cn, ei = -amp * sn;
+        const R ar = R(1) - ki * Rr, ai = kr * Rr;
+        const R g1r = -(ar * er - ai * ei), g1i = -(ar * ei + ai * er);
+        // D x rho'
+        const R cx = dy * rs[3 * k + 2] - dz * rs[3 * k + 1];
+        const R cy = dz * rs[3 * k] - dx * rs[3 * k + 2];
+        const R cz = dx * rs[3 * k + 1] - dy * rs[3 * k];
+        ur[0] += g1r * cx; ui[0] += g1i * cx;
+        ur[1] += g1r * cy; ui[1] += g1i * cy;
+        ur[2] += g1r * cz; ui[2] += g1i * cz;
+        vr[0] += g1r * dx; vi[0] += g1i * dx;
+        vr[1] += g1r * dy; vi[1] += g1i * dy;
+        vr[2] += g1r * dz; vi[2] += g1i * dz;
+      }
+      const R w = X.W[q];
+      p1r += w * (rqx * ur[0] + rqy * ur[1] + rqz * ur[2]);
+      p1i += w * (rqx * ui[0] + rqy * ui[1] + rqz * ui[2]);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        p2r[d] += w * ur[d];
+        p2i[d] += w * ui[d];
+        sr[d] += w * vr[d];
+        si[d] += w * vi[d];
+      }
+      // rho_q x V
+      xr[0] += w * (rqy * vr[2] - rqz * vr[1]); xi[0] += w * (rqy * vi[2] - rqz * vi[1]);
+      xr[1] += w * (rqz * vr[0] - rqx * vr[2]); xi[1] += w * (rqz * vi[0] - rqx * vi[2]);
+      xr[2] += w * (rqx * vr[1] - rqy * vr[0]); xi[2] += w * (rqx * vi[1] - rqy * vi[0]);
+    }
+    // local: sig_i sig'_j [P1 + a_i.P2 + b_j.X + b_j.(a_i x S)]
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const R ax = X.av[3 * i], ay = X.av[3 * i + 1], az = X.av[3 * i + 2];
+      const R baser = p1r + ax * p2r[0] + ay * p2r[1] + az * p2r[2];
+      const R basei = p1i + ax * p2i[0] + ay * p2i[1] + az * p2i[2];
+      // a_i x S
+      const R csr0 = ay * sr[2] - az * sr[1], csr1 = az * sr[0] - ax * sr[2], csr2 = ax * sr[1] - ay * sr[0];
+      const R csi0 = ay * si[2] - az * si[1], csi1 = az * si[0] - ax * si[2], csi2 = ax * si[1] - ay * si[0];
+      const int64_t row = int64_t(X.e[i] - tk.e_row0) * tk.ld;
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const R bx = bv[3 * j], by = bv[3 * j + 1], bz = bv[3 * j + 2];
+        R vr_ = baser + bx * (xr[0] + csr0) + by * (xr[1] + csr1) + bz * (xr[2] + csr2);
+        R vi_ = basei + bx * (xi[0] + csi0) + by * (xi[1] + csi1) + bz * (xi[2] + csi2);
+        const R sc = X.sig[i] * sg_[j];
+        M<R>::add(tk.Kb, row + (be[j] - tk.b_col0), vr_ * sc, vi_ * sc);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- FP64 touching Kbar pairs
+template <class R>
+__global__ void fill_K_touch(KTask tk, const int32_t* __restrict__ pa, const int32_t* __restrict__ pc, int npairs,
+                             const double* __restrict__ geo, const double* __restrict__ bgeo,
+                             const double* __restrict__ xyz, const int32_t* __restrict__ tri,
+                             const int32_t* __restrict__ tri_edge, const int32_t* __restrict__ btri_edge) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= npairs) return;
+  const int t = pa[p], cg = pc[p];
+  if (t < tk.t0 || t >= tk.t0 + tk.ntest || cg < tk.c0 || cg >= tk.c0 + tk.nsrc) return;
+  const double* gt = geo + size_t(t) * GEO_STRIDE;
+  const double* gs = bgeo + size_t(cg) * GEO_STRIDE;
+  // child vertices: rebuild from the parent (a, m_ab, g) ... pattern
+  const int par = cg / 6, kk = cg % 6;
+  const double* a = xyz + 3 * tri[3 * par];
+  const double* b = xyz + 3 * tri[3 * par + 1];
+  const double* c = xyz + 3 * tri[3 * par + 2];
+  double V[7][3];  // a, b, c, m_ab, m_bc, m_ca, g
+  for (int d = 0; d < 3; ++d) {
+    V[0][d] = a[d]; V[1][d] = b[d]; V[2][d] = c[d];
+    V[3][d] = 0.5 * (a[d] + b[d]); V[4][d] = 0.5 * (b[d] + c[d]); V[5][d] = 0.5 * (c[d] + a[d]);
+    V[6][d] = (a[d] + b[d] + c[d]) / 3.0;
+  }
+  const int cv[6][3] = {{0, 3, 6}, {3, 1, 6}, {1, 4, 6}, {4, 2, 6}, {2, 5, 6}, {5, 0, 6}};
+  const double* p1 = V[cv[kk][0]];
+  const double* p2 = V[cv[kk][1]];
+  const double* p3 = V[cv[kk][2]];
+  const cd k = {tk.kr, tk.ki};
+  cd P1 = {0, 0}, P2[3] = {{0, 0}, {0, 0}, {0, 0}}, X[3] = {{0, 0}, {0, 0}, {0, 0}}, S[3] = {{0, 0}, {0, 0}, {0, 0}};
+  for (int q = 0; q < 6; ++q) {
+    double r[3], rq[3];
+    for (int d = 0; d < 3; ++d) {
+      rq[d] = gt[GEO_RHO + 3 * q + d];
+      r[d] = gt[GEO_C + d] + rq[d];
+    }
+    cd U[3] = {{0, 0}, {0, 0}, {0, 0}}, Vv[3] = {{0, 0}, {0, 0}, {0, 0}};
+    for (int j = 0; j < 6; ++j) {
+      const double* rs = gs + GEO_RHO + 3 * j;
+      double D[3] = {r[0] - gs[GEO_C] - rs[0], r[1] - gs[GEO_C + 1] - rs[1], r[2] - gs[GEO_C + 2] - rs[2]};
+      double Rr = sqrt(D[0] * D[0] + D[1] * D[1] + D[2] * D[2]);
+      cd g1 = grad_smooth(k, Rr);
+      double w = gs[GEO_W + j];
+      g1.r *= w;
+      g1.i *= w;
+      double cr[3] = {D[1] * rs[2] - D[2] * rs[1], D[2] * rs[0] - D[0] * rs[2], D[0] * rs[1] - D[1] * rs[0]};
+      for (int d = 0; d < 3; ++d) {
+        U[d].r += g1.r * cr[d];
+        U[d].i += g1.i * cr[d];
+        Vv[d].r += g1.r * D[d];
+        Vv[d].i += g1.i * D[d];
+      }
+    }
+    // static part: V_s = int grad 1/(4 pi R) dS', U_s = V_s x (r - c')
+    Pot P;
+    potentials(r, p1, p2, p3, P);
+    double vs[3], rc[3];
+    for (int d = 0; d < 3; ++d) {
+      vs[d] = INV4PI * P.grad[d];
+      rc[d] = r[d] - gs[GEO_C + d];
+    }
+    double us[3] = {vs[1] * rc[2] - vs[2] * rc[1], vs[2] * rc[0] - vs[0] * rc[2], vs[0] * rc[1] - vs[1] * rc[0]};
+    for (int d = 0; d < 3; ++d) {
+      U[d].r += us[d];
+      Vv[d].r += vs[d];
+    }
+    double w = gt[GEO_W + q];
+    for (int d = 0; d < 3; ++d) {
+      P1.r += w * rq[d] * U[d].r;
+      P1.i += w * rq[d] * U[d].i;
+      P2[d].r += w * U[d].r;
+      P2[d].i += w * U[d].i;
+      S[d].r += w * Vv[d].r;
+      S[d].i += w * Vv[d].i;
+    }
+    X[0].r += w * (rq[1] * Vv[2].r - rq[2] * Vv[1].r); X[0].i += w * (rq[1] * Vv[2].i - rq[2] * Vv[1].i);
+    X[1].r += w * (rq[2] * Vv[0].r - rq[0] * Vv[2].r); X[1].i += w * (rq[2] * Vv[0].i - rq[0] * Vv[2].i);
+    X[2].r += w * (rq[0] * Vv[1].r - rq[1] * Vv[0].r); X[2].i += w * (rq[0] * Vv[1].i - rq[1] * Vv[0].i);
+  }
+  for (int i = 0; i < 3; ++i) {
+    const double* av = gt + GEO_AV + 3 * i;
+    cd base = P1;
+    for (int d = 0; d < 3; ++d) {
+      base.r += av[d] * P2[d].r;
+      base.i += av[d] * P2[d].i;
+    }
+    cd axs[3] = {{av[1] * S[2].r - av[2] * S[1].r, av[1] * S[2].i - av[2] * S[1].i},
+                 {av[2] * S[0].r - av[0] * S[2].r, av[2] * S[0].i - av[0] * S[2].i},
+                 {av[0] * S[1].r - av[1] * S[0].r, av[0] * S[1].i - av[1] * S[0].i}};
+    for (int j = 0; j < 3; ++j) {
+      const double* bv = gs + GEO_AV + 3 * j;
+      cd v = base;
+      for (int d = 0; d < 3; ++d) {
+        v.r += bv[d] * (X[d].r + axs[d].r);
+        v.i += bv[d] * (X[d].i + axs[d].i);
+      }
+      double sc = gt[GEO_SIG + i] * gs[GEO_SIG + j];
+      add_d<R>(tk.Kb, int64_t(tri_edge[3 * t + i] - tk.e_row0) * tk.ld + (btri_edge[3 * cg + j] - tk.b_col0), v.r * sc,
+               v.i * sc);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- host launchers
+template <class R>
+void fill_L(const sldm_mesh* m, const std::vector<LTask>& tasks, cudaStream_t s) {
+  if (tasks.empty()) return;
+  std::vector<TileRef> tiles;
+  for (size_t i = 0; i < tasks.size(); ++i)
+    for (int t0 = 0; t0 < tasks[i].ntest; t0 += TILE_TEST)
+      for (int s0 = 0; s0 < tasks[i].nsrc; s0 += TILE_SRC) tiles.push_back({int32_t(i), t0, s0, 0});
+  DBuf<LTask> dt;
+  DBuf<TileRef> dtl;
+  dt.upload(tasks, s);
+  dtl.upload(tiles, s);
+  const DevMesh& d = m->d;
+  for (size_t off = 0; off < tiles.size(); off += 1u << 30) {
+    unsigned nb = unsigned(std::min<size_t>(tiles.size() - off, 1u << 30));
+    fill_L_bulk<R><<<nb, TILE_SRC, 0, s>>>(dt.p, dtl.p + off, d.geo.p, d.tri.p, d.tri_edge.p);
+  }
+  SLDM_CUDA(cudaGetLastError());
+  const int np = int(m->h.touchL_a.size());
+  for (const LTask& tk : tasks)
+    fill_L_touch<R><<<(np + 127) / 128, 128, 0, s>>>(tk, d.touchL_a.p, d.touchL_b.p, np, d.geo.p, d.xyz.p, d.tri.p,
+                                                     d.tri_edge.p);
+  SLDM_CUDA(cudaGetLastError());
+  SLDM_CUDA(cudaStreamSynchronize(s));  // task/tile buffers are released on return
+}
+
+template <class R>
+void fill_K(const sldm_mesh* m, const std::vector<KTask>& tasks, cudaStream_t s) {
+  if (tasks.empty()) return;
+  std::vector<TileRef> tiles;
+  for (size_t i = 0; i < tasks.size(); ++i)
+    for (int t0 = 0; t0 < tasks[i].ntest; t0 += TILE_TEST)
+      for (int s0 = 0; s0 < tasks[i].nsrc; s0 += TILE_SRC) tiles.push_back({int32_t(i), t0, s0, 0});
+  DBuf<KTask> dt;
+  DBuf<TileRef> dtl;
+  dt.upload(tasks, s);
+  dtl.upload(tiles, s);
+  const DevMesh& d = m->d;
+  fill_K_bulk<R><<<unsigned(tiles.size()), TILE_SRC, 0, s>>>(dt.p, dtl.p, d.geo.p, d.bgeo.p, d.tri.p, d.tri_edge.p,
+                                                             d.btri_edge.p);
+  SLDM_CUDA(cudaGetLastError());
+  const int np = int(m->h.touchK_a.size());
+  for (const KTask& tk : tasks)
+    fill_K_touch<R><<<(np + 127) / 128, 128, 0, s>>>(tk, d.touchK_a.p, d.touchK_c.p, np, d.geo.p, d.bgeo.p, d.xyz.p,
+                                                     d.tri.p, d.tri_edge.p, d.btri_edge.p);
+  SLDM_CUDA(cudaGetLastError());
+  SLDM_CUDA(cudaStreamSynchronize(s));
+}
+
+// ---------------------------------------------------------------- BC contraction
+// K[m][n] = sum_q Kb[m][row_q - b0] * val_q over the CSC column n of C.
+template <class R>
+__global__ void contract_bc_kernel(int ne_o, int e0, int b0, const int32_t* __restrict__ ptr, const int32_t* __restrict__ row,
+                                   const double* __restrict__ val, const void* __restrict__ Kb_, int64_t ldKb, void* K_,
+                                   int64_t ldK) {
+  int n = blockIdx.x * blockDim.x + threadIdx.x;
+  int m = blockIdx.y;
+  if (n >= ne_o) return;
+  typedef typename std::conditional<sizeof(R) == 4, float2, double2>::type C2;
+  const C2* Kb = reinterpret_cast<const C2*>(Kb_) + int64_t(m) * ldKb;
+  double sr = 0, si = 0;
+  for (int q = ptr[e0 + n]; q < ptr[e0 + n + 1]; ++q) {
+    C2 v = Kb[row[q] - b0];
+    sr += double(v.x) * val[q];
+    si += double(v.y) * val[q];
+  }
+  C2* K = reinterpret_cast<C2*>(K_) + int64_t(m) * ldK;
+  K[n].x = decltype(K[n].x)(sr);
+  K[n].y = decltype(K[n].y)(si);
+}
+
+template <class R>
+void contract_bc(const sldm_mesh* m, int obj, const void* Kb, int64_t ldKb, void* K, int64_t ldK, cudaStream_t s) {
+  const HostMesh& h = m->h;
+  int e0 = h.edge_begin[obj], ne_o = h.edge_begin[obj + 1] - e0;
+  int b0 = h.bedge_begin[obj];
+  dim3 grid((ne_o + 127) / 128, ne_o);
+  contract_bc_kernel<R><<<grid, 128, 0, s>>>(ne_o, e0, b0, m->d.bc_ptr.p, m->d.bc_row.p, m->d.bc_val.p, Kb, ldKb, K, ldK);
+  SLDM_CUDA(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------- Gram I_x
+// value of nonzero z: sum over its contributions of coef * int_child (n_T x f_i) . g_j (6-point, exact)
+__global__ void gram_kernel(int nnz, const int32_t* __restrict__ cptr, const int32_t* __restrict__ ctri,
+                            const int32_t* __restrict__ cchild, const int32_t* __restrict__ ci,
+                            const int32_t* __restrict__ cj, const double* __restrict__ ccoef,
+                            const double* __restrict__ geo, const double* __restrict__ bgeo, double* vals) {
+  int z = blockIdx.x * blockDim.x + threadIdx.x;
+  if (z >= nnz) return;
+  double acc = 0;
+  for (int q = cptr[z]; q < cptr[z + 1]; ++q) {
+    const double* gt = geo + size_t(ctri[q]) * GEO_STRIDE;
+    const double* gc = bgeo + size_t(cchild[q]) * GEO_STRIDE;
+    int i = ci[q], j = cj[q];
+    const double* n = gt + GEO_N;
+    double sum = 0;
+    for (int p = 0; p < 6; ++p) {
+      double r[3], f[3], g[3];
+      for (int d = 0; d < 3; ++d) {
+        r[d] = gc[GEO_C + d] + gc[GEO_RHO + 3 * p + d];
+        f[d] = gt[GEO_SIG + i] * (r[d] - gt[GEO_C + d] + gt[GEO_AV + 3 * i + d]);
+        g[d] = gc[GEO_SIG + j] * (gc[GEO_RHO + 3 * p + d] + gc[GEO_AV + 3 * j + d]);
+      }
+      double nf[3] = {n[1] * f[2] - n[2] * f[1], n[2] * f[0] - n[0] * f[2], n[0] * f[1] - n[1] * f[0]};
+      sum += gc[GEO_W + p] * (nf[0] * g[0] + nf[1] * g[1] + nf[2] * g[2]);
+    }
+    acc += ccoef[q] * sum;
+  }
+  vals[z] = acc;
+}
+
+void gram_ix(const sldm_mesh* m, double* vals, cudaStream_t s) {
+  int nnz = int(m->h.ix_col.size());
+  const DevMesh& d = m->d;
+  gram_kernel<<<(nnz + 127) / 128, 128, 0, s>>>(nnz, d.ixc_ptr.p, d.ixc_tri.p, d.ixc_child.p, d.ixc_i.p, d.ixc_j.p,
+                                                d.ixc_coef.p, d.geo.p, d.bgeo.p, vals);
+  SLDM_CUDA(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------- plane-wave right-hand side
+constexpr double ETA0 = 4e-7 * PI * 299792458.0;
+
+__global__ void rhs_kernel(int ne, int nrhs, double k0, const double* __restrict__ kp, const int32_t* __restrict__ tplus,
+                           const int32_t* __restrict__ tminus, const int32_t* __restrict__ tri_edge,
+                           const double* __restrict__ geo, double2* b, int64_t ld) {
+  int m = blockIdx.x * blockDim.x + threadIdx.x;
+  int r = blockIdx.y;
+  if (m >= ne) return;
+  const double* kh = kp + 6 * r;
+  const double* pol = kh + 3;
+  double acc_r = 0, acc_i = 0;
+  for (int side = 0; side < 2; ++side) {
+    int t = side == 0 ? tplus[m] : tminus[m];
+    const double* g = geo + size_t(t) * GEO_STRIDE;
+    int i = tri_edge[3 * t] == m ? 0 : (tri_edge[3 * t + 1] == m ? 1 : 2);
+    for (int q = 0; q < 6; ++q) {
+      double fp = 0, ph = 0;
+      for (int d = 0; d < 3; ++d) {
+        double rl = g[GEO_RHO + 3 * q + d];
+        fp += g[GEO_SIG + i] * (rl + g[GEO_AV + 3 * i + d]) * pol[d];
+        ph += kh[d] * (g[GEO_C + d] + rl);
+      }
+      double sn, cn;
+      sincos(k0 * ph, &sn, &cn);
+      double w = g[GEO_W + q] * fp / ETA0;
+      acc_r += w * cn;
+      acc_i -= w * sn;
+    }
+  }
+  b[int64_t(r) * ld + m] = make_double2(acc_r, acc_i);
+}
+
+void rhs_planewave(const sldm_mesh* m, double k0, const double* kp, int nrhs, double2* b, int64_t ld, cudaStream_t s) {
+  int ne = int(m->h.ne);
+  dim3 grid((ne + 127) / 128, nrhs);
+  rhs_kernel<<<grid, 128, 0, s>>>(ne, nrhs, k0, kp, m->d.tplus.p, m->d.tminus.p, m->d.tri_edge.p, m->d.geo.p, b, ld);
+  SLDM_CUDA(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------- far field / RCS
+// F = sum_m jd_m int f_m exp(+j k0 rhat . r); sigma = eta0^2 |(I - rr) F|^2 / (4 pi)
+__global__ void farfield_kernel(int nt, double k0, const double2* __restrict__ jd, const int32_t* __restrict__ tri_edge,
+                                const double* __restrict__ geo, const double* __restrict__ ang, double* rcs) {
+  const int a = blockIdx.x;
+  const double th = ang[2 * a], ph = ang[2 * a + 1];
+  const double rh[3] = {sin(th) * cos(ph), sin(th) * sin(ph), cos(th)};
+  double F[6] = {0, 0, 0, 0, 0, 0};
+  for (int t = threadIdx.x; t < nt; t += blockDim.x) {
+    const double* g = geo + size_t(t) * GEO_STRIDE;
+    for (int q = 0; q < 6; ++q) {
+      double pr = 0;
+      for (int d = 0; d < 3; ++d) pr += rh[d] * (g[GEO_C + d] + g[GEO_RHO + 3 * q + d]);
+      double sn, cn;
+      sincos(k0 * pr, &sn, &cn);
+      for (int i = 0; i < 3; ++i) {
+        double2 c = jd[tri_edge[3 * t + i]];
+        double wr = g[GEO_W + q] * g[GEO_SIG + i];
+        // c * exp(+j k0 rhat.r)
+        double er = (c.x * cn - c.y * sn) * wr, ei = (c.x * sn + c.y * cn) * wr;
+        for (int d = 0; d < 3; ++d) {
+          double f = g[GEO_RHO + 3 * q + d] + g[GEO_AV + 3 * i + d];
+          F[2 * d] += er * f;
+          F[2 * d + 1] += ei * f;
+        }
+      }
+    }
+  }
+  __shared__ double sh[6][256];
+  for (int c = 0; c < 6; ++c) sh[c][threadIdx.x] = F[c];
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+      for (int c = 0; c < 6; ++c) sh[c][threadIdx.x] += sh[c][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double fr[3], fi[3];
+    for (int d = 0; d < 3; ++d) {
+      fr[d] = sh[2 * d][0];
+      fi[d] = sh[2 * d + 1][0];
+    }
+    double dr = rh[0] * fr[0] + rh[1] * fr[1] + rh[2] * fr[2];
+    double di = rh[0] * fi[0] + rh[1] * fi[1] + rh[2] * fi[2];
+    double s = 0;
+    for (int d = 0; d < 3; ++d) {
+      double pr_ = fr[d] - rh[d] * dr, pi_ = fi[d] - rh[d] * di;
+      s += pr_ * pr_ + pi_ * pi_;
+    }
+    rcs[a] = ETA0 * ETA0 * s / (4 * PI);
+  }
+}
+
+void farfield(const sldm_mesh* m, double k0, const double2* jd, const double* ang, int n, double* rcs, cudaStream_t s) {
+  farfield_kernel<<<n, 256, 0, s>>>(int(m->h.nt), k0, jd, m->d.tri_edge.p, m->d.geo.p, ang, rcs);
+  SLDM_CUDA(cudaGetLastError());
+}
+
+template void fill_L<float>(const sldm_mesh*, const std::vector<LTask>&, cudaStream_t);
+template void fill_L<double>(const sldm_mesh*, const std::vector<LTask>&, cudaStream_t);
+template void fill_K<float>(const sldm_mesh*, const std::vector<KTask>&, cudaStream_t);
+template void fill_K<double>(const sldm_mesh*, const std::vector<KTask>&, cudaStream_t);
+template void contract_bc<float>(const sldm_mesh*, int, const void*, int64_t, void*, int64_t, cudaStream_t);
+template void contract_bc<double>(const sldm_mesh*, int, const void*, int64_t, void*, int64_t, cudaStream_t);
+
+}  // namespace sldm

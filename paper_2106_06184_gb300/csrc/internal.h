@@ -1,0 +1,176 @@
+// Internal declarations shared by the translation units of libsldm.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuComplex.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/sldm.h"
+
+namespace sldm {
+
+// ---------------------------------------------------------------- errors
+void set_error(const std::string& msg);
+struct Error {
+  int code;
+  std::string msg;
+};
+#define SLDM_CUDA(call)                                                                   \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      throw ::sldm::Error{SLDM_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)}; \
+  } while (0)
+#define SLDM_REQUIRE(cond, code, msg)                 \
+  do {                                                \
+    if (!(cond)) throw ::sldm::Error{(code), (msg)};  \
+  } while (0)
+
+// ---------------------------------------------------------------- device buffers
+template <class T>
+struct DBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  DBuf() = default;
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  ~DBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  void alloc(size_t count) {
+    release();
+    if (count == 0) return;
+    cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+    if (e != cudaSuccess) {
+      p = nullptr;
+      throw Error{SLDM_ENOMEM, "cudaMalloc of " + std::to_string(count * sizeof(T)) + " bytes failed"};
+    }
+    n = count;
+  }
+  void upload(const std::vector<T>& h, cudaStream_t s = 0) {
+    alloc(h.size());
+    if (!h.empty()) SLDM_CUDA(cudaMemcpyAsync(p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+  }
+  void zero(cudaStream_t s = 0) {
+    if (n) SLDM_CUDA(cudaMemsetAsync(p, 0, n * sizeof(T), s));
+  }
+  size_t bytes() const { return n * sizeof(T); }
+};
+
+// ---------------------------------------------------------------- mesh
+// Host topology and its device copy.  Triangle-local index i names the vertex
+// tri[t][i] and the edge opposite to it.
+struct HostMesh {
+  int64_t nv = 0, nt = 0, ne = 0, nobj = 0, nbe = 0;
+  std::vector<double> xyz;                 // nv*3
+  std::vector<int32_t> tri;                // nt*3
+  std::vector<int32_t> obj;                // nt
+  std::vector<int32_t> tri_edge;           // nt*3 edge opposite local vertex i
+  std::vector<int8_t> tri_sign;            // nt*3 (+1: this triangle is T+)
+  std::vector<int64_t> uv;                 // ne*2
+  std::vector<int32_t> tplus, tminus;      // ne
+  std::vector<int32_t> tri_begin, edge_begin, bedge_begin;  // nobj+1 each
+  // barycentric refinement: child c = 6 t + k; its edges
+  std::vector<int32_t> btri_edge;          // 6nt*3 barycentric edge opposite child-local vertex j
+  std::vector<int8_t> btri_sign;           // 6nt*3
+  // BC coefficients, CSC by BC column n: rows are barycentric edges
+  std::vector<int32_t> bc_ptr, bc_row;     // ne+1, nnz
+  std::vector<double> bc_val;              // nnz
+  // touching pairs (within an object): primal-primal and primal-child
+  std::vector<int32_t> touchL_a, touchL_b; // pairs sharing a vertex (including self)
+  std::vector<int32_t> touchK_a, touchK_c; // (test triangle, touching child), own children excluded
+  // I_x sparsity: CSR rows = edges; each nonzero lists its contributions
+  std::vector<int32_t> ix_ptr, ix_col;     // ne+1, nnz
+  std::vector<int32_t> ixc_ptr;            // nnz+1
+  std::vector<int32_t> ixc_tri, ixc_child, ixc_i, ixc_j;  // per contribution
+  std::vector<double> ixc_coef;            // C coefficient of the barycentric edge in BC n
+};
+
+struct DevMesh {
+  DBuf<double> xyz;
+  DBuf<int32_t> tri, tri_edge, tplus, tminus, obj, q2t, tri_begin, edge_begin;
+  DBuf<int8_t> tri_sign, btri_sign;
+  DBuf<int32_t> btri_edge;
+  DBuf<int32_t> bc_ptr, bc_row;
+  DBuf<double> bc_val;
+  DBuf<int32_t> touchL_a, touchL_b, touchK_a, touchK_c;
+  DBuf<int32_t> ix_ptr, ix_col, ixc_ptr, ixc_tri, ixc_child, ixc_i, ixc_j;
+  DBuf<double> ixc_coef;
+  // geometry computed on the device (see fill.cu: geometry_kernel)
+  DBuf<double> geo;   // per triangle: GEO_STRIDE doubles
+  DBuf<double> bgeo;  // per child: BGEO_STRIDE doubles
+};
+
+// Per-triangle geometry record (doubles): centroid(3) area(1) normal(3)
+// quad local points rho_q = r_q - c (18) weights W_q = w_q A (6) a_i = c - v_i (9)
+// edge factors s_i/(2A) (3)
+constexpr int GEO_C = 0, GEO_A = 3, GEO_N = 4, GEO_RHO = 7, GEO_W = 25, GEO_AV = 31, GEO_SIG = 40;
+constexpr int GEO_STRIDE = 43;
+
+void build_host_mesh(const double* xyz, int64_t nv, const int32_t* tri, int64_t nt, const int32_t* obj,
+                     HostMesh& hm);
+
+}  // namespace sldm
+
+struct sldm_mesh {
+  sldm::HostMesh h;
+  sldm::DevMesh d;
+  int device = 0;
+};
+
+struct sldm_stack {
+  std::vector<sldm_layer> layers;
+  double z_top = 0;
+  int32_t bottom = 0;
+};
+
+namespace sldm {
+
+// ---------------------------------------------------------------- fill (fill.cu)
+void geometry(const HostMesh& hm, DevMesh& dm, cudaStream_t s);
+
+// One fill task: triangles [t0, t0+nt_test) x [s0, s0+nt_src) of the same
+// mesh, results scattered (atomically added) into row-major complex blocks.
+struct LTask {
+  int32_t t0, ntest, s0, nsrc;
+  int32_t e_row0, e_col0;     // edge offsets subtracted from global edge ids
+  int32_t t_row0, t_col0;     // triangle offsets
+  int64_t ldA, ldP;           // leading dimensions
+  void* A;                    // L^A destination (complex of the op precision) or null
+  void* P;                    // L^phi destination or null
+  double kr, ki;              // wavenumber
+  double sAr, sAi, sPr, sPi;  // complex scale of L^A and L^phi
+};
+struct KTask {
+  int32_t t0, ntest;          // primal test triangles
+  int32_t c0, nsrc;           // children [c0, c0 + nsrc) = 6 * source triangles
+  int32_t e_row0, b_col0;     // edge and barycentric-edge offsets
+  int64_t ld;
+  void* Kb;                   // barycentric Kbar destination, complex of op precision
+  double kr, ki;
+};
+
+template <class R>
+void fill_L(const sldm_mesh* m, const std::vector<LTask>& tasks, cudaStream_t s);
+template <class R>
+void fill_K(const sldm_mesh* m, const std::vector<KTask>& tasks, cudaStream_t s);
+// Kbar (ne_o x ne_o, op precision) = Kb (ne_o x nbe_o) * C_o, plus beta * I_x/2 (dense add of Gram)
+template <class R>
+void contract_bc(const sldm_mesh* m, int obj, const void* Kb, int64_t ldKb, void* K, int64_t ldK,
+                 cudaStream_t s);
+// Gram matrix values for the CSR pattern ix_ptr/ix_col (double)
+void gram_ix(const sldm_mesh* m, double* vals, cudaStream_t s);
+// e_inc for nrhs plane waves into b (complex128, column-major N x nrhs, ld)
+void rhs_planewave(const sldm_mesh* m, double k0, const double* khat_pol_dev, int nrhs, double2* b,
+                   int64_t ld, cudaStream_t s);
+// far field vector F(theta, phi) of RWG coefficients jd (complex128) -> rcs (double), device
+void farfield(const sldm_mesh* m, double k0, const double2* jd, const double* ang_dev, int n, double* rcs,
+              cudaStream_t s);
+
+}  // namespace sldm

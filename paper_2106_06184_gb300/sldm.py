@@ -1,0 +1,262 @@
+"""ctypes binding of libsldm (the C ABI in ``include/sldm.h``), same names.
+
+Argument marshalling only: numpy arrays are passed as host pointers and torch
+CUDA tensors as device pointers (``where`` = SLDM_DEVICE).  The library must
+have been built (``paper_2106_06184_gb300.build.build()``); there is no
+fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libsldm.so")
+
+OK, EINVAL, ENOMEM, ENOTCONV, ENUMERIC, ECUDA, EBUSY, ENOTSUP = 0, -1, -2, -3, -4, -5, -6, -7
+HOST, DEVICE = 0, 1
+PREC_F64, PREC_F32 = 0, 1
+BOTTOM_HALFSPACE, BOTTOM_PEC = 0, 1
+(BLOCK_LAM, BLOCK_LPM, BLOCK_LA, BLOCK_LP, BLOCK_K, BLOCK_Y11, BLOCK_Y21, BLOCK_IX, BLOCK_KBAR_L) = range(9)
+
+
+class SldmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"sldm error {code}: {msg}")
+        self.code = code
+
+
+class Material(C.Structure):
+    _fields_ = [("eps_r", C.c_double), ("mu_r", C.c_double), ("sigma", C.c_double),
+                ("layer", C.c_int32), ("reserved", C.c_int32)]
+
+
+class Layer(C.Structure):
+    _fields_ = [("eps_r", C.c_double), ("mu_r", C.c_double), ("sigma", C.c_double), ("thickness", C.c_double)]
+
+
+class MeshInfo(C.Structure):
+    _fields_ = [("nv", C.c_int64), ("nt", C.c_int64), ("ne", C.c_int64), ("nobj", C.c_int64),
+                ("n_unknowns", C.c_int64), ("n_bary_edges", C.c_int64)]
+
+
+class AssembleOpts(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("reserved", C.c_int32), ("stream", C.c_void_p)]
+
+
+class SolveOpts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("restart", C.c_int32), ("maxit", C.c_int32),
+                ("x0_given", C.c_int32), ("reserved", C.c_int32)]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("status", C.c_int32), ("relres", C.c_double)]
+
+
+class OpInfo(C.Structure):
+    _fields_ = [("n_unknowns", C.c_int64), ("ne", C.c_int64), ("nt", C.c_int64), ("nobj", C.c_int64),
+                ("device_bytes", C.c_int64), ("precision", C.c_int32), ("reserved", C.c_int32), ("k0", C.c_double)]
+
+
+EXPORTS = {
+    "sldm_last_error": (None, [C.c_char_p, C.c_size_t]),
+    "sldm_mesh_create": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p, C.POINTER(C.c_void_p)]),
+    "sldm_mesh_info_get": (C.c_int, [C.c_void_p, C.POINTER(MeshInfo)]),
+    "sldm_mesh_edges": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "sldm_mesh_destroy": (C.c_int, [C.c_void_p]),
+    "sldm_stack_create": (C.c_int, [C.c_void_p, C.c_int32, C.c_double, C.c_int32, C.POINTER(C.c_void_p)]),
+    "sldm_stack_destroy": (C.c_int, [C.c_void_p]),
+    "sldm_assemble": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.POINTER(AssembleOpts),
+                                C.POINTER(C.c_void_p)]),
+    "sldm_op_info_get": (C.c_int, [C.c_void_p, C.POINTER(OpInfo)]),
+    "sldm_op_block": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_int32,
+                                C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "sldm_op_destroy": (C.c_int, [C.c_void_p]),
+    "sldm_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p]),
+    "sldm_rhs_planewave": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_int32,
+                                     C.c_void_p]),
+    "sldm_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.POINTER(SolveOpts),
+                             C.POINTER(SolveInfo), C.c_int32, C.c_void_p]),
+    "sldm_farfield": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
+}
+
+
+class Library:
+    """The loaded shared library with typed entry points."""
+
+    def __init__(self, path=LIB_PATH):
+        if not os.path.exists(path):
+            raise SldmError(ENOTSUP, f"libsldm not built: {path} is missing (run paper_2106_06184_gb300.build)")
+        self.path = path
+        self.lib = C.CDLL(path)
+        for name, (res, args) in EXPORTS.items():
+            fn = getattr(self.lib, name)
+            fn.restype = res
+            fn.argtypes = args
+
+    def check(self, code):
+        if code != OK:
+            buf = C.create_string_buffer(1024)
+            self.lib.sldm_last_error(buf, 1024)
+            raise SldmError(code, buf.value.decode(errors="replace"))
+        return code
+
+
+_LIB = None
+
+
+def load(path=LIB_PATH) -> Library:
+    global _LIB
+    if _LIB is None or _LIB.path != path:
+        _LIB = Library(path)
+    return _LIB
+
+
+def _ptr(a):
+    """(pointer, where) of a numpy array (host) or a torch CUDA tensor (device)."""
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data_as(C.c_void_p), HOST
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return C.c_void_p(a.data_ptr()), (DEVICE if a.is_cuda else HOST)
+    raise TypeError("expected a numpy array or a torch tensor")
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    return C.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+
+
+class Mesh:
+    """sldm_mesh: closed outward-oriented triangle meshes, one or more objects."""
+
+    h = None
+
+    def __init__(self, xyz, tri, obj=None, lib=None):
+        self.L = lib or load()
+        xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+        tri = np.ascontiguousarray(tri, dtype=np.int32)
+        objp = None
+        if obj is not None:
+            self._obj = np.ascontiguousarray(obj, dtype=np.int32)
+            objp = self._obj.ctypes.data_as(C.c_void_p)
+        h = C.c_void_p()
+        self.L.check(self.L.lib.sldm_mesh_create(xyz.ctypes.data_as(C.c_void_p), len(xyz),
+                                                 tri.ctypes.data_as(C.c_void_p), len(tri), objp, C.byref(h)))
+        self.h = h
+        info = MeshInfo()
+        self.L.check(self.L.lib.sldm_mesh_info_get(h, C.byref(info)))
+        self.nv, self.nt, self.ne, self.nobj = info.nv, info.nt, info.ne, info.nobj
+        self.n_unknowns, self.n_bary_edges = info.n_unknowns, info.n_bary_edges
+
+    def edges(self):
+        uv = np.zeros((self.ne, 2), np.int64)
+        tp = np.zeros(self.ne, np.int64)
+        tm = np.zeros(self.ne, np.int64)
+        self.L.check(self.L.lib.sldm_mesh_edges(self.h, uv.ctypes.data_as(C.c_void_p), tp.ctypes.data_as(C.c_void_p),
+                                                tm.ctypes.data_as(C.c_void_p)))
+        return uv, tp, tm
+
+    def close(self):
+        if self.h:
+            self.L.lib.sldm_mesh_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+
+class Stack:
+    """sldm_stack: background layers listed top to bottom (one layer = homogeneous)."""
+
+    h = None
+
+    def __init__(self, layers, z_top=0.0, bottom=BOTTOM_HALFSPACE, lib=None):
+        self.L = lib or load()
+        arr = (Layer * len(layers))(*[Layer(*l) for l in layers])
+        h = C.c_void_p()
+        self.L.check(self.L.lib.sldm_stack_create(arr, len(layers), z_top, bottom, C.byref(h)))
+        self.h = h
+
+    def close(self):
+        if self.h:
+            self.L.lib.sldm_stack_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+
+class Operator:
+    """sldm_op: the assembled single-layer dual-mesh operator at one frequency."""
+
+    h = None
+
+    def __init__(self, mesh: Mesh, stack: Stack, materials, freq_hz, precision=PREC_F64, stream=None):
+        self.L = mesh.L
+        self.mesh, self.stack = mesh, stack
+        mats = (Material * len(materials))(*[Material(m[0], m[1], m[2], m[3] if len(m) > 3 else 0, 0)
+                                             for m in materials])
+        opts = AssembleOpts(precision, 0, _stream(stream))
+        h = C.c_void_p()
+        self.L.check(self.L.lib.sldm_assemble(mesh.h, stack.h, mats, freq_hz, C.byref(opts), C.byref(h)))
+        self.h = h
+        info = OpInfo()
+        self.L.check(self.L.lib.sldm_op_info_get(h, C.byref(info)))
+        self.N, self.ne, self.nt, self.nobj = info.n_unknowns, info.ne, info.nt, info.nobj
+        self.k0, self.device_bytes, self.precision = info.k0, info.device_bytes, info.precision
+
+    def block(self, which, obj=0):
+        r, c = C.c_int64(), C.c_int64()
+        self.L.check(self.L.lib.sldm_op_block(self.h, which, obj, None, HOST, C.byref(r), C.byref(c)))
+        out = np.zeros((r.value, c.value), np.complex128)
+        self.L.check(self.L.lib.sldm_op_block(self.h, which, obj, out.ctypes.data_as(C.c_void_p), HOST,
+                                              C.byref(r), C.byref(c)))
+        return out
+
+    def apply(self, x, y, nrhs=1, stream=None):
+        px, wx = _ptr(x)
+        py, wy = _ptr(y)
+        assert wx == wy
+        self.L.check(self.L.lib.sldm_apply(self.h, px, py, nrhs, wx, _stream(stream)))
+        return y
+
+    def rhs_planewave(self, khat, pol, b, stream=None):
+        khat = np.ascontiguousarray(np.atleast_2d(khat), np.float64)
+        pol = np.ascontiguousarray(np.atleast_2d(pol), np.float64)
+        pb, wb = _ptr(b)
+        self.L.check(self.L.lib.sldm_rhs_planewave(self.h, khat.ctypes.data_as(C.c_void_p),
+                                                   pol.ctypes.data_as(C.c_void_p), len(khat), pb, wb, _stream(stream)))
+        return b
+
+    def solve(self, b, x, nrhs=1, tol=1e-8, restart=100, maxit=2000, x0=False, stream=None, check=True):
+        pb, wb = _ptr(b)
+        px, wx = _ptr(x)
+        assert wb == wx
+        opts = SolveOpts(tol, restart, maxit, int(bool(x0)), 0)
+        info = SolveInfo()
+        code = self.L.lib.sldm_solve(self.h, pb, px, nrhs, C.byref(opts), C.byref(info), wb, _stream(stream))
+        if check:
+            self.L.check(code)
+        return dict(iters=info.iters, relres=info.relres, status=info.status, code=code)
+
+    def farfield(self, x, theta, phi):
+        theta = np.ascontiguousarray(theta, np.float64)
+        phi = np.ascontiguousarray(np.broadcast_to(phi, theta.shape), np.float64)
+        out = np.zeros(len(theta))
+        px, wx = _ptr(x)
+        self.L.check(self.L.lib.sldm_farfield(self.h, px, wx, theta.ctypes.data_as(C.c_void_p),
+                                              phi.ctypes.data_as(C.c_void_p), len(theta),
+                                              out.ctypes.data_as(C.c_void_p)))
+        return out
+
+    def close(self):
+        if self.h:
+            self.L.lib.sldm_op_destroy(self.h)
+            self.h = None
+
+    __del__ = close

@@ -1,0 +1,178 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle on the
+same seeded inputs.
+
+Tolerances: FP64 fill and solve agree with the oracle to rounding (the two
+differ only in summation order and in the atomic accumulation of the four
+triangle-pair contributions of each entry): 1e-10 relative (Frobenius and max).
+The FP32 bulk fill (FP64 singular terms) agrees to 1e-5 relative in the
+Frobenius norm of each block and 1e-5 of the block's largest entry elementwise.
+"""
+import numpy as np
+import pytest
+
+from oracle import farfield as OF
+from oracle import system as S
+from oracle.topology import Mesh as OMesh
+from workloads.meshes import ellipsoid, icosphere, merge
+
+pytestmark = pytest.mark.gpu
+
+FREQ = 300e6
+
+
+def _sl():
+    import torch  # noqa: F401  (initialises the CUDA context the library uses)
+    from paper_2106_06184_gb300 import sldm
+    return sldm
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def relmax(a, b):
+    return np.max(np.abs(a - b)) / np.max(np.abs(b))
+
+
+class Case:
+    def __init__(self, xyz, tri, obj, mats, bg, freq):
+        self.xyz, self.tri, self.obj, self.mats, self.bg, self.freq = xyz, tri, obj, mats, bg, freq
+        self.om = OMesh(xyz, tri, obj)
+        self.A = S.assemble(self.om, [S.Material(*m[:3]) for m in mats], S.Material(*bg), freq)
+        self.b = S.rhs(self.A)
+        self.x = S.solve(self.A, self.b)
+
+
+@pytest.fixture(scope="module")
+def sphere():
+    """Dielectric sphere r = 0.1 m, eps_r 4, icosphere sub 2 (320 triangles), 300 MHz."""
+    v, f = icosphere(2, 0.1)
+    return Case(v, f, None, [(4.0, 1.0, 0.0)], (1.0, 1.0, 0.0), FREQ)
+
+
+@pytest.fixture(scope="module")
+def two_lossy():
+    """Two objects: a lossy ellipsoid and a sphere (ragged tiles, complex k)."""
+    xyz, tri, obj = merge(ellipsoid(1, (0.06, 0.04, 0.05), (0, 0, 0)), icosphere(1, 0.05, (0.15, 0.02, 0.0)))
+    return Case(xyz, tri, obj, [(6.0, 1.0, 0.05), (2.5, 1.0, 0.0)], (1.0, 1.0, 0.0), 500e6)
+
+
+def build_op(case, prec):
+    sl = _sl()
+    m = sl.Mesh(case.xyz, case.tri, case.obj)
+    st = sl.Stack([(case.bg[0], case.bg[1], case.bg[2], 0.0)])
+    op = sl.Operator(m, st, case.mats, case.freq, precision=prec)
+    return sl, m, st, op
+
+
+def test_edges_match_oracle(sphere, two_lossy):
+    for c in (sphere, two_lossy):
+        sl = _sl()
+        m = sl.Mesh(c.xyz, c.tri, c.obj)
+        uv, tp, tm = m.edges()
+        assert np.array_equal(uv, c.om.E.uv) and np.array_equal(tp, c.om.E.tp) and np.array_equal(tm, c.om.E.tm)
+        assert m.n_unknowns == 2 * c.om.ne + c.om.nt - c.om.nobj
+
+
+def _blocks(case, op, sl):
+    A = case.A
+    out = [("LAm", op.block(sl.BLOCK_LAM), A.LAm), ("LPm", op.block(sl.BLOCK_LPM), A.LPm),
+           ("Ix", op.block(sl.BLOCK_IX), A.Ix)]
+    for o, b in enumerate(A.blocks):
+        out += [(f"LA{o}", op.block(sl.BLOCK_LA, o), b["LA"]), (f"LP{o}", op.block(sl.BLOCK_LP, o), b["LP"]),
+                (f"K{o}", op.block(sl.BLOCK_K, o), b["K"]), (f"Y11_{o}", op.block(sl.BLOCK_Y11, o), b["Y11"]),
+                (f"Y21_{o}", op.block(sl.BLOCK_Y21, o), b["Y21"])]
+    return out
+
+
+@pytest.mark.parametrize("which", ["sphere", "two_lossy"])
+def test_fp64_blocks_match_oracle(which, request):
+    case = request.getfixturevalue(which)
+    sl, m, st, op = build_op(case, 0)
+    for name, got, ref in _blocks(case, op, sl):
+        assert got.shape == ref.shape, name
+        assert rel(got, ref) < 1e-10 and relmax(got, ref) < 1e-10, (name, rel(got, ref), relmax(got, ref))
+
+
+@pytest.mark.parametrize("which", ["sphere", "two_lossy"])
+def test_fp32_blocks_match_oracle(which, request):
+    case = request.getfixturevalue(which)
+    sl, m, st, op = build_op(case, 1)
+    for name, got, ref in _blocks(case, op, sl):
+        if name.startswith("Y"):
+            continue  # Y inherits the FP32 operator error amplified by M_l^-1; checked through the solution
+        assert rel(got, ref) < 1e-5 and relmax(got, ref) < 1e-5, (name, rel(got, ref), relmax(got, ref))
+
+
+@pytest.mark.parametrize("which", ["sphere", "two_lossy"])
+def test_apply_matches_oracle(which, request):
+    case = request.getfixturevalue(which)
+    sl, m, st, op = build_op(case, 0)
+    rng = np.random.default_rng(7)
+    X = rng.standard_normal((3, op.N)) + 1j * rng.standard_normal((3, op.N))
+    X = np.ascontiguousarray(X)
+    Y = np.zeros_like(X)
+    op.apply(X, Y, nrhs=3)
+    ref = (case.A.Z @ X.T).T
+    assert rel(Y, ref) < 1e-10
+
+
+@pytest.mark.parametrize("which", ["sphere", "two_lossy"])
+def test_rhs_and_solve_match_oracle(which, request):
+    case = request.getfixturevalue(which)
+    sl, m, st, op = build_op(case, 0)
+    b = np.zeros(op.N, complex)
+    op.rhs_planewave([0, 0, -1.0], [1.0, 0, 0], b)
+    assert rel(b, case.b) < 1e-12
+    x = np.zeros(op.N, complex)
+    info = op.solve(b, x, tol=1e-10)
+    assert info["relres"] < 1e-10
+    assert rel(x, case.x) < 1e-8
+    th = np.radians(np.arange(0, 181, 10.0))
+    got = op.farfield(x, th, np.zeros_like(th))
+    ref = OF.rcs(case.om, case.A.k0, S.j_delta(case.A, case.x), th)
+    assert np.max(np.abs(10 * np.log10(got / ref))) < 0.05
+
+
+def test_fp32_solution_matches_oracle(sphere):
+    sl, m, st, op = build_op(sphere, 1)
+    b = np.zeros(op.N, complex)
+    op.rhs_planewave([0, 0, -1.0], [1.0, 0, 0], b)
+    x = np.zeros(op.N, complex)
+    info = op.solve(b, x, tol=1e-8)
+    assert rel(x, sphere.x) < 1e-4
+    th = np.radians(np.arange(0, 181, 15.0))
+    got = op.farfield(x, th, np.zeros_like(th))
+    ref = OF.rcs(sphere.om, sphere.A.k0, S.j_delta(sphere.A, sphere.x), th)
+    assert np.max(np.abs(10 * np.log10(got / ref))) < 0.05
+
+
+def test_device_pointers_and_multi_rhs(sphere):
+    import torch
+    sl, m, st, op = build_op(sphere, 0)
+    khat = np.array([[0, 0, -1.0], [1.0, 0, 0], [0, 1.0, 0]])
+    pol = np.array([[1.0, 0, 0], [0, 0, 1.0], [1.0, 0, 0]])
+    b = torch.zeros((3, op.N), dtype=torch.complex128, device="cuda")
+    op.rhs_planewave(khat, pol, b)
+    x = torch.zeros_like(b)
+    op.solve(b, x, nrhs=3, tol=1e-10)
+    xh = x.cpu().numpy()
+    assert rel(xh[0], sphere.x) < 1e-8
+    # each column solves its own system
+    r = np.zeros_like(xh)
+    op.apply(np.ascontiguousarray(xh), r, nrhs=3)
+    assert rel(r, b.cpu().numpy()) < 1e-9
+
+
+def test_invalid_meshes_rejected():
+    sl = _sl()
+    v, f = icosphere(1, 1.0)
+    with pytest.raises(sl.SldmError) as e:
+        sl.Mesh(v, f[:-1])              # open surface
+    assert e.value.code == -1
+    with pytest.raises(sl.SldmError):
+        sl.Mesh(v, f[:, ::-1].copy() if False else np.concatenate([f, f[:1]]))  # edge used twice
+    g = f.copy()
+    g[0] = [0, 0, 1]                    # degenerate triangle
+    with pytest.raises(sl.SldmError):
+        sl.Mesh(v, g)
