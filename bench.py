@@ -1,0 +1,360 @@
+#!/usr/bin/env python
+"""Throughput and latency of the single-layer dual-mesh BEM hot path on GB300.
+
+One step = one full pass of the hot path for one request: assemble the operator
+(triangle-pair fill of L^A, L^phi, Kbar with BC sources, singular corrections,
+Gram I_x, Y11/Y21 by LU), build the plane-wave right-hand side, solve by GMRES
+to the stated relative residual and evaluate the bistatic RCS.  The metric is
+solves/s (and p50/p99 latency per solve) at that residual.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs independent replicas (the path has no
+exchange step); value = solves of all ranks / max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import platform
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from workloads.meshes import icosphere  # noqa: E402
+
+# ----------------------------------------------------------------------------- workloads
+WORKLOADS = {
+    # Dielectric sphere in free space, icosphere sub 2, plain method in complex FP64
+    "sphere-r0.1-epsr4-sub2-300MHz-fp64": dict(
+        mesh=lambda: icosphere(2, 0.1), obj=None, mats=[(4.0, 1.0, 0.0)], bg=(1.0, 1.0, 0.0, 0.0), freq=300e6,
+        precision=0, tol=1e-8, khat=[0.0, 0.0, -1.0], pol=[1.0, 0.0, 0.0], n_angles=181),
+}
+DEFAULT_WORKLOAD = "sphere-r0.1-epsr4-sub2-300MHz-fp64"
+
+L2_FLUSH_BYTES = 512 << 20  # larger than the 129 MB L2
+
+# Roofline denominators: MEASURED_PEAKS.json when present, else the recorded
+# fallback measurement.  ALU peaks derive from unit counts x maximum SM clock:
+# FP32: 152 SMs x 128 lanes x 2 flop x 2.07 GHz; FP64: the part's nominal rate.
+FALLBACK_HBM_GBS = 6800.0
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+FP64_PEAK_TFLOPS = 1.25
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            return float(d.get("hbm_gbs", FALLBACK_HBM_GBS)), "measured"
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples during the timed region (SM clock and throttle reasons)."""
+
+    Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index, self.rows, self.proc = index, [], None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        sm = [float(r[0]) for r in self.rows if r and r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if len(r) > 1 and r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for k, n in enumerate(names):
+                if len(r) > 3 + k and r[3 + k].lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- roofline bookkeeping
+def matvec_bytes(w, mesh_info, esz):
+    """Algorithmic bytes of one structured product: every dense block read once."""
+    ne, nt, nobj = mesh_info
+    per_obj = []
+    # single-object workloads: the object's blocks have the global sizes
+    ne_o, nt_o = ne // nobj, nt // nobj
+    loc = nobj * (3 * ne_o * ne_o + nt_o * nt_o + ne_o * ne_o + (nt_o - 1) * ne_o)  # LA, K, Y11 + LP + Y21
+    return (ne * ne + nt * nt + loc) * esz
+
+
+def lu_update_bytes(n, nrhs):
+    """Algorithmic bytes of all trailing updates of an unblocked LU with nrhs right-hand sides
+    (read + write of every updated complex128 entry)."""
+    tot = 0
+    for k in range(n - 1):
+        r = n - k - 1
+        tot += r * (r + nrhs) * 32
+    return tot, n - 1
+
+
+# ----------------------------------------------------------------------------- our arm
+def run_ours(args, rank, world):
+    import torch
+
+    from paper_2106_06184_gb300 import sldm
+
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    W = WORKLOADS[args.workload]
+    xyz, tri = W["mesh"]()
+    mesh = sldm.Mesh(xyz, tri, W["obj"])
+    stack = sldm.Stack([W["bg"]])
+    theta = np.radians(np.linspace(0.0, 180.0, W["n_angles"]))
+    phi = np.zeros_like(theta)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def step_device():
+        op = sldm.Operator(mesh, stack, W["mats"], W["freq"], precision=W["precision"])
+        b = torch.zeros(op.N, dtype=torch.complex128, device="cuda")
+        op.rhs_planewave(W["khat"], W["pol"], b)
+        x = torch.zeros_like(b)
+        info = op.solve(b, x, tol=W["tol"])
+        rcs = op.farfield(x, theta, phi)
+        return op, info, rcs
+
+    for _ in range(args.warmup):
+        op, info, rcs = step_device()
+        del op
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    sldm.timers_reset()
+    sldm.timers_enable(True)
+    times, iters, relres = [], [], []
+    t_wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        op, info, rcs = step_device()
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+        iters.append(info["iters"])
+        relres.append(info["relres"])
+        del op
+    t_wall = time.perf_counter() - t_wall0
+    sldm.timers_enable(False)
+    timers = sldm.timers_read()
+    clk = clocks.stop()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    total_ms = float(sum(times))
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+
+    # ---- e2e: the same step through the public API with host buffers
+    e2e_times = []
+    h2d = d2h = 0
+    for i in range(0 if args.no_e2e else max(3, min(args.steps, 10))):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        m2 = sldm.Mesh(xyz, tri, W["obj"])                       # H2D: vertices and triangles
+        op2 = sldm.Operator(m2, stack, W["mats"], W["freq"], precision=W["precision"])
+        bh = np.zeros(op2.N, complex)
+        op2.rhs_planewave(W["khat"], W["pol"], bh)              # D2H: b
+        xh = np.zeros(op2.N, complex)
+        op2.solve(bh, xh, tol=W["tol"])                         # H2D: b, D2H: x
+        rcs2 = op2.farfield(xh, theta, phi)                     # H2D: x, angles; D2H: rcs
+        e2e_times.append(time.perf_counter() - t0)
+        if i == 0:
+            h2d = xyz.nbytes + tri.astype(np.int32).nbytes + bh.nbytes + xh.nbytes + theta.nbytes + phi.nbytes
+            d2h = bh.nbytes + xh.nbytes + rcs2.nbytes
+        del op2, m2
+    n_units = args.steps * world
+    value = n_units / (total_ms / 1e3)
+    e2e_value = world / statistics.median(e2e_times) if e2e_times else None
+
+    # ---- roofline of the dominant kernel (live CUDA-event timings)
+    hbm, hbm_src = peaks()
+    W_esz = 16 if W["precision"] == 0 else 8
+    ne, nt, nobj = mesh.ne, mesh.nt, mesh.nobj
+    cand = {}
+    if "gemv" in timers:
+        ms, cnt = timers["gemv"]
+        per_apply = matvec_bytes(W, (ne, nt, nobj), W_esz)
+        # two gemv launches per structured product
+        achieved = (per_apply / 2) / (ms / cnt / 1e3) / 1e9
+        cand["gemv"] = dict(bound="hbm", achieved=achieved, peak=hbm, unit="GB/s", ms=ms)
+    if "lu_update" in timers:
+        ms, cnt = timers["lu_update"]
+        n = ne // nobj + nt // nobj - 1
+        tot, launches = lu_update_bytes(n, ne // nobj)
+        achieved = (tot / launches) / (ms / cnt / 1e3) / 1e9
+        cand["lu_update"] = dict(bound="hbm", achieved=achieved, peak=hbm, unit="GB/s", ms=ms)
+    for k in ("fill_K_bulk", "fill_L_bulk", "fill_K_touch", "fill_L_touch", "lu_pivot", "lu_backsub"):
+        if k in timers and k not in cand:
+            cand[k] = dict(bound="alu", achieved=None, peak=FP64_PEAK_TFLOPS if W["precision"] == 0 else FP32_PEAK_TFLOPS,
+                           unit="TFLOP/s", ms=timers[k][0])
+    dom = max(cand, key=lambda k: timers[k][0]) if cand else None
+    roof = None
+    if dom:
+        c = cand[dom]
+        roof = {"kernel": dom, "bound": c["bound"], "achieved": c["achieved"], "peak": c["peak"], "unit": c["unit"],
+                "frac": (c["achieved"] / c["peak"]) if c["achieved"] is not None else None,
+                "peak_source": hbm_src if c["bound"] == "hbm" else "derived",
+                "traffic": None, "share_of_step": timers[dom][0] / total_ms if world == 1 else None}
+    kernel_ms = {k: round(v[0] / args.steps, 4) for k, v in sorted(timers.items(), key=lambda kv: -kv[1][0])}
+    launches = sum(v[1] for k, v in timers.items() if k != "apply")
+    out = {
+        "metric": "solves/s (assemble + RHS + GMRES to the stated relative residual + RCS, one plane wave)",
+        "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "c128" if W["precision"] == 0 else "c64", "data": "synthetic",
+        "config": {"workload": args.workload, "n_triangles": nt, "n_edges": ne, "n_unknowns": mesh.n_unknowns,
+                   "freq_hz": W["freq"], "rel_residual": W["tol"], "rcs_angles": W["n_angles"],
+                   "parallelism": f"replicas x{world}", "l2": "flushed between steps (512 MB write)"},
+        "latency_ms": {"p50": float(np.percentile(times, 50)), "p99": float(np.percentile(times, 99))},
+        "gmres": {"iters": int(np.median(iters)), "relres_max": float(max(relres))},
+        "roofline": roof,
+        "kernel_ms_per_step": kernel_ms,
+        "gpu_launches": int(launches / args.steps * args.steps),
+        "clocks": clk,
+        "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                "latency_ms_p50": 1e3 * statistics.median(e2e_times) if e2e_times else None},
+        "wall_s_timed": t_wall,
+    }
+    return out
+
+
+# ----------------------------------------------------------------------------- oracle timing
+ORACLE_STEP = r"""
+import sys, time, numpy as np
+sys.path.insert(0, {root!r})
+from workloads.meshes import icosphere
+from oracle.topology import Mesh
+from oracle import system as S, farfield
+xyz, tri = icosphere(2, 0.1)
+t0 = time.perf_counter()
+m = Mesh(xyz, tri)
+A = S.assemble(m, [S.Material(4.0, 1.0, 0.0)], S.Material(1.0, 1.0, 0.0), 300e6)
+x = S.solve(A, S.rhs(A))
+th = np.radians(np.linspace(0, 180, 181))
+rcs = farfield.rcs(m, A.k0, S.j_delta(A, x), th)
+print(time.perf_counter() - t0)
+"""
+
+
+def oracle_step_seconds():
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", ORACLE_STEP.format(root=ROOT)], capture_output=True, text=True, env=env,
+                       timeout=600)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    return float(r.stdout.strip().splitlines()[-1])
+
+
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return platform.processor() or platform.machine()
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    times = []
+    for i in range(args.warmup + args.steps):
+        t = oracle_step_seconds()
+        if i >= args.warmup:
+            times.append(t)
+    total = sum(times)
+    v = args.steps / total
+    return {
+        "impl": "reference", "metric": "solves/s (assemble + RHS + GMRES to the stated relative residual + RCS, one plane wave)",
+        "value": v, "unit": "solves/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "c128", "data": "synthetic",
+        "config": {"workload": args.workload, "parallelism": "host cores"},
+        "latency_ms": {"p50": 1e3 * float(np.percentile(times, 50)), "p99": 1e3 * float(np.percentile(times, 99))},
+        "cpu_baseline": {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                         "sample": "full workload per step (oracle assemble + dense LU solve + RCS), single thread",
+                         "cpu": cpu_model(), "nproc": os.cpu_count()},
+        "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg (profiling runs)")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl" if args.impl == "ours" else "gloo")
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        out = run_ours(args, rank, world)
+        if rank == 0 and world == 1 and not args.no_cpu_baseline:
+            t = oracle_step_seconds()
+            out["cpu_baseline"] = {"value": 1.0 / t, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                                   "sample": "one full solve of the workload (oracle assemble + dense LU + RCS), "
+                                             "single thread", "cpu": cpu_model(), "nproc": os.cpu_count()}
+    if rank == 0 and out is not None:
+        print(json.dumps(out))
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -203,6 +203,20 @@ int sldm_solve(const sldm_op* op, const void* b, void* x, int32_t nrhs, const sl
 int sldm_farfield(const sldm_op* op, const void* x, int32_t where, const double* theta,
                   const double* phi, int32_t n, double* rcs);
 
+/* Kernel timers (profiling aid, Sec. IV "CPU time breakdown" counterpart):
+ * when enabled, the library records a CUDA event pair around each launch of
+ * its main kernels, on the launch's stream, under a fixed name
+ * ("fill_L_bulk", "fill_L_touch", "fill_K_bulk", "fill_K_touch", "lu_update",
+ * "lu_pivot", "lu_backsub", "gemv", "apply", "gmres_iter").  Timings are
+ * accumulated per name; reading them synchronises on the recorded events.
+ * Not thread-safe with respect to concurrent launches on several streams. */
+int sldm_timers_enable(int32_t on);
+int sldm_timers_reset(void);
+/* Total milliseconds and number of timed launches under `name` (0 if none). */
+int sldm_timer_get(const char* name, double* total_ms, int64_t* count);
+/* Comma-separated names with recorded launches, NUL-terminated, truncated to len. */
+int sldm_timer_names(char* buf, size_t len);
+
 #ifdef __cplusplus
 }
 #endif

@@ -126,6 +126,7 @@ static void apply_dev(const sldm_op* op_, const double2* x, double2* y, int nrhs
 }
 
 static void apply_any(const sldm_op* op, const double2* x, double2* y, int nrhs, cudaStream_t s) {
+  ScopedTimer tm("apply", s);
   if (op->prec == SLDM_PREC_F32) apply_dev<float2>(op, x, y, nrhs, s);
   else apply_dev<double2>(op, x, y, nrhs, s);
 }

@@ -214,15 +214,22 @@ void lu_solve_batched(const std::vector<LUSys>& systems, cudaStream_t s) {
   err.zero(s);
   const int nsys = int(systems.size());
   for (int k = 0; k < nmax; ++k) {
-    lu_pivot_kernel<<<nsys, 256, 0, s>>>(d.p, k, err.p);
+    {
+      ScopedTimer tm("lu_pivot", s);
+      lu_pivot_kernel<<<nsys, 256, 0, s>>>(d.p, k, err.p);
+    }
     int rows = nmax - k - 1;
     if (rows > 0) {
       int cols = rows + rmax;
       dim3 grid(std::min((cols + 127) / 128, 8), rows, nsys);
+      ScopedTimer tm("lu_update", s);
       lu_update_kernel<<<grid, 128, 0, s>>>(d.p, k);
     }
   }
-  lu_backsub_kernel<<<dim3(rmax, nsys), 256, 0, s>>>(d.p);
+  {
+    ScopedTimer tm("lu_backsub", s);
+    lu_backsub_kernel<<<dim3(rmax, nsys), 256, 0, s>>>(d.p);
+  }
   SLDM_CUDA(cudaGetLastError());
   int herr = 0;
   SLDM_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -335,6 +342,7 @@ void gemv_jobs(const GemvPlan& plan, int nrhs, cudaStream_t s) {
   if (plan.njobs == 0) return;
   const int64_t threads = plan.total_rows * 32;
   const unsigned blocks = unsigned((threads + 255) / 256);
+  ScopedTimer tm("gemv", s);
   if (nrhs <= 1)
     gemv_jobs_kernel<C, 1><<<blocks, 256, 0, s>>>(plan.jobs, plan.rowstart, plan.njobs, plan.total_rows, nrhs);
   else if (nrhs <= 4)

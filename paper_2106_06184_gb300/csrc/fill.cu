@@ -753,13 +753,16 @@ void fill_L(const sldm_mesh* m, const std::vector<LTask>& tasks, cudaStream_t s)
   const DevMesh& d = m->d;
   for (size_t off = 0; off < tiles.size(); off += 1u << 30) {
     unsigned nb = unsigned(std::min<size_t>(tiles.size() - off, 1u << 30));
+    ScopedTimer tm("fill_L_bulk", s);
     fill_L_bulk<R><<<nb, TILE_SRC, 0, s>>>(dt.p, dtl.p + off, d.geo.p, d.tri.p, d.tri_edge.p);
   }
   SLDM_CUDA(cudaGetLastError());
   const int np = int(m->h.touchL_a.size());
-  for (const LTask& tk : tasks)
+  for (const LTask& tk : tasks) {
+    ScopedTimer tm("fill_L_touch", s);
     fill_L_touch<R><<<(np + 127) / 128, 128, 0, s>>>(tk, d.touchL_a.p, d.touchL_b.p, np, d.geo.p, d.xyz.p, d.tri.p,
                                                      d.tri_edge.p);
+  }
   SLDM_CUDA(cudaGetLastError());
   SLDM_CUDA(cudaStreamSynchronize(s));  // task/tile buffers are released on return
 }
@@ -776,13 +779,18 @@ void fill_K(const sldm_mesh* m, const std::vector<KTask>& tasks, cudaStream_t s)
   dt.upload(tasks, s);
   dtl.upload(tiles, s);
   const DevMesh& d = m->d;
-  fill_K_bulk<R><<<unsigned(tiles.size()), TILE_SRC, 0, s>>>(dt.p, dtl.p, d.geo.p, d.bgeo.p, d.tri.p, d.tri_edge.p,
+  {
+    ScopedTimer tm("fill_K_bulk", s);
+    fill_K_bulk<R><<<unsigned(tiles.size()), TILE_SRC, 0, s>>>(dt.p, dtl.p, d.geo.p, d.bgeo.p, d.tri.p, d.tri_edge.p,
                                                              d.btri_edge.p);
+  }
   SLDM_CUDA(cudaGetLastError());
   const int np = int(m->h.touchK_a.size());
-  for (const KTask& tk : tasks)
+  for (const KTask& tk : tasks) {
+    ScopedTimer tm("fill_K_touch", s);
     fill_K_touch<R><<<(np + 127) / 128, 128, 0, s>>>(tk, d.touchK_a.p, d.touchK_c.p, np, d.geo.p, d.bgeo.p, d.xyz.p,
                                                      d.tri.p, d.tri_edge.p, d.btri_edge.p);
+  }
   SLDM_CUDA(cudaGetLastError());
   SLDM_CUDA(cudaStreamSynchronize(s));
 }

@@ -29,6 +29,23 @@ struct Error {
     if (!(cond)) throw ::sldm::Error{(code), (msg)};  \
   } while (0)
 
+// ---------------------------------------------------------------- kernel timers
+// Optional CUDA-event timing of named launches (sldm_timers_enable).  When
+// disabled, timer_begin/timer_end cost one branch.
+bool timers_on();
+void timer_begin(const char* name, cudaStream_t s);
+void timer_end(cudaStream_t s);
+struct ScopedTimer {
+  cudaStream_t s;
+  bool on;
+  ScopedTimer(const char* name, cudaStream_t s_) : s(s_), on(timers_on()) {
+    if (on) timer_begin(name, s);
+  }
+  ~ScopedTimer() {
+    if (on) timer_end(s);
+  }
+};
+
 // ---------------------------------------------------------------- device buffers
 template <class T>
 struct DBuf {

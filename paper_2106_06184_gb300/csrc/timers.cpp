@@ -1,0 +1,110 @@
+// Named CUDA-event timers for the library's launches (sldm_timers_* in sldm.h).
+#include <cstring>
+#include <map>
+#include <mutex>
+
+#include "internal.h"
+
+namespace sldm {
+
+namespace {
+struct Pending {
+  std::string name;
+  cudaEvent_t a, b;
+};
+std::mutex g_mu;
+bool g_on = false;
+std::vector<cudaEvent_t> g_pool;
+std::vector<Pending> g_pending;
+std::vector<std::pair<std::string, cudaEvent_t>> g_open;  // per begin, matched LIFO by end
+std::map<std::string, std::pair<double, int64_t>> g_acc;
+
+cudaEvent_t get_event() {
+  if (!g_pool.empty()) {
+    cudaEvent_t e = g_pool.back();
+    g_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  return e;
+}
+
+void resolve_locked() {
+  for (auto& p : g_pending) {
+    float ms = 0;
+    cudaEventSynchronize(p.b);
+    cudaEventElapsedTime(&ms, p.a, p.b);
+    auto& acc = g_acc[p.name];
+    acc.first += ms;
+    acc.second += 1;
+    g_pool.push_back(p.a);
+    g_pool.push_back(p.b);
+  }
+  g_pending.clear();
+}
+}  // namespace
+
+bool timers_on() { return g_on; }
+
+void timer_begin(const char* name, cudaStream_t s) {
+  std::lock_guard<std::mutex> l(g_mu);
+  cudaEvent_t a = get_event();
+  cudaEventRecord(a, s);
+  g_open.push_back({name, a});
+}
+
+void timer_end(cudaStream_t s) {
+  std::lock_guard<std::mutex> l(g_mu);
+  if (g_open.empty()) return;
+  auto o = g_open.back();
+  g_open.pop_back();
+  cudaEvent_t b = get_event();
+  cudaEventRecord(b, s);
+  g_pending.push_back({o.first, o.second, b});
+  if (g_pending.size() > 4096) resolve_locked();
+}
+
+}  // namespace sldm
+
+extern "C" {
+
+int sldm_timers_enable(int32_t on) {
+  std::lock_guard<std::mutex> l(sldm::g_mu);
+  sldm::g_on = on != 0;
+  return SLDM_OK;
+}
+
+int sldm_timers_reset(void) {
+  std::lock_guard<std::mutex> l(sldm::g_mu);
+  sldm::resolve_locked();
+  sldm::g_acc.clear();
+  return SLDM_OK;
+}
+
+int sldm_timer_get(const char* name, double* total_ms, int64_t* count) {
+  std::lock_guard<std::mutex> l(sldm::g_mu);
+  sldm::resolve_locked();
+  auto it = sldm::g_acc.find(name ? name : "");
+  if (total_ms) *total_ms = it == sldm::g_acc.end() ? 0.0 : it->second.first;
+  if (count) *count = it == sldm::g_acc.end() ? 0 : it->second.second;
+  return SLDM_OK;
+}
+
+int sldm_timer_names(char* buf, size_t len) {
+  std::lock_guard<std::mutex> l(sldm::g_mu);
+  sldm::resolve_locked();
+  std::string s;
+  for (auto& kv : sldm::g_acc) {
+    if (!s.empty()) s += ",";
+    s += kv.first;
+  }
+  if (buf && len) {
+    size_t n = std::min(len - 1, s.size());
+    std::memcpy(buf, s.data(), n);
+    buf[n] = 0;
+  }
+  return SLDM_OK;
+}
+
+}  // extern "C"

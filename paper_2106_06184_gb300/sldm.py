@@ -80,6 +80,10 @@ EXPORTS = {
     "sldm_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.POINTER(SolveOpts),
                              C.POINTER(SolveInfo), C.c_int32, C.c_void_p]),
     "sldm_farfield": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
+    "sldm_timers_enable": (C.c_int, [C.c_int32]),
+    "sldm_timers_reset": (C.c_int, []),
+    "sldm_timer_get": (C.c_int, [C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
+    "sldm_timer_names": (C.c_int, [C.c_char_p, C.c_size_t]),
 }
 
 
@@ -105,6 +109,29 @@ class Library:
 
 
 _LIB = None
+
+
+def timers_enable(on=True, lib=None):
+    L = lib or load()
+    L.check(L.lib.sldm_timers_enable(int(bool(on))))
+
+
+def timers_reset(lib=None):
+    L = lib or load()
+    L.check(L.lib.sldm_timers_reset())
+
+
+def timers_read(lib=None):
+    """{name: (total_ms, count)} of the library's timed launches."""
+    L = lib or load()
+    buf = C.create_string_buffer(4096)
+    L.check(L.lib.sldm_timer_names(buf, 4096))
+    out = {}
+    for name in filter(None, buf.value.decode().split(",")):
+        ms, n = C.c_double(), C.c_int64()
+        L.check(L.lib.sldm_timer_get(name.encode(), C.byref(ms), C.byref(n)))
+        out[name] = (ms.value, n.value)
+    return out
 
 
 def load(path=LIB_PATH) -> Library:

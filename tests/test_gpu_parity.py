@@ -139,7 +139,10 @@ def test_fp32_solution_matches_oracle(sphere):
     b = np.zeros(op.N, complex)
     op.rhs_planewave([0, 0, -1.0], [1.0, 0, 0], b)
     x = np.zeros(op.N, complex)
-    info = op.solve(b, x, tol=1e-8)
+    # the FP32 product's rounding, amplified by the conditioning of Z, floors
+    # the certifiable residual near 1e-6 at this size
+    info = op.solve(b, x, tol=1e-5)
+    assert info["relres"] < 1e-5
     assert rel(x, sphere.x) < 1e-4
     th = np.radians(np.arange(0, 181, 15.0))
     got = op.farfield(x, th, np.zeros_like(th))
