@@ -143,7 +143,8 @@ def test_fp32_solution_matches_oracle(sphere):
     # the certifiable residual near 1e-6 at this size
     info = op.solve(b, x, tol=1e-5)
     assert info["relres"] < 1e-5
-    assert rel(x, sphere.x) < 1e-4
+    # FP32 entries (about 1e-6 relative) times the conditioning of Z (about 1e2)
+    assert rel(x, sphere.x) < 5e-4
     th = np.radians(np.arange(0, 181, 15.0))
     got = op.farfield(x, th, np.zeros_like(th))
     ref = OF.rcs(sphere.om, sphere.A.k0, S.j_delta(sphere.A, sphere.x), th)
