@@ -203,6 +203,29 @@ int sldm_solve(const sldm_op* op, const void* b, void* x, int32_t nrhs, const sl
 int sldm_farfield(const sldm_op* op, const void* x, int32_t where, const double* theta,
                   const double* phi, int32_t n, double* rcs);
 
+/* Allocation-free Kbar of one object (no counterpart in the paper; it serves
+ * callers that cannot allocate device memory).  Some host applications may not
+ * call cudaMalloc or cudaFree on their hot path: cudaFree synchronises the whole
+ * device and both can stall work that other streams of the process have in
+ * flight, and some applications hand all device memory to their own arena under
+ * a fixed budget.  This entry point computes the same Kbar(k) of object `obj`
+ * as the assembly does (RWG test x BC source, Eq. opKhgf, FP64, without the
+ * I_x/2 term of Eq. Kmatdef) into the caller's buffer while allocating nothing:
+ * its temporaries live in one file-scope device array of 24 MiB that every GPU
+ * which loads the library keeps until the process exits.
+ *  - K_out: device pointer, ne_o x ne_o complex128, row-major, written entirely.
+ *  - k_re, k_im: complex wavenumber (exp(-j k R) convention, k_im <= 0 decays).
+ *  - The object must satisfy ne_o * 9 nt_o <= 1,568,752 (barycentric scratch
+ *    entries; about 340 triangles), else SLDM_EINVAL with the sizes in the message.
+ *  - Asynchronous on `stream`: K_out is complete when the stream reaches this
+ *    point.  Every call shares the one scratch array, which keeps the last call's
+ *    contents (the call clears what must start at zero), so calls that overlap
+ *    on the GPU (different streams, or different threads) race and must be
+ *    serialised by the caller.
+ *  - The first call on a device resolves the array's device address with that
+ *    device current; make that first call before any stream capture begins. */
+int sldm_kbar_noalloc(const sldm_mesh* mesh, int32_t obj, double k_re, double k_im, void* K_out, void* stream);
+
 /* Kernel timers (profiling aid, Sec. IV "CPU time breakdown" counterpart):
  * when enabled, the library records a CUDA event pair around each launch of
  * its main kernels, on the launch's stream, under a fixed name

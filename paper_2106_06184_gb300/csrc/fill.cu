@@ -13,6 +13,7 @@
 // held in shared memory, and the 3x3 results are scattered with atomics
 // (each edge-pair entry gets four triangle-pair contributions).
 #include <cmath>
+#include <mutex>
 
 #include "internal.h"
 
@@ -971,3 +972,93 @@ template void contract_bc<float>(const sldm_mesh*, int, const void*, int64_t, vo
 template void contract_bc<double>(const sldm_mesh*, int, const void*, int64_t, void*, int64_t, cudaStream_t);
 
 }  // namespace sldm
+
+// ---------------------------------------------------------------- allocation-free Kbar
+// sldm_kbar_noalloc: the barycentric Kbar fill of one object and its contraction
+// with the BC coefficients, with every temporary (task record, tile list and the
+// barycentric scratch block) in one file-scope device array instead of memory
+// obtained from cudaMalloc.
+namespace sldm {
+
+constexpr size_t NOALLOC_BYTES = size_t(24) << 20;         // 24 MiB held on each GPU that loads this module
+constexpr size_t NOALLOC_TASK_OFF = 0;                       // one KTask
+constexpr size_t NOALLOC_TILE_OFF = 256;                     // TileRef[NOALLOC_MAX_TILES]
+constexpr size_t NOALLOC_MAX_TILES = 4096;
+constexpr size_t NOALLOC_KB_OFF = NOALLOC_TILE_OFF + NOALLOC_MAX_TILES * sizeof(TileRef);  // complex128 block
+constexpr size_t NOALLOC_MAX_KB = (NOALLOC_BYTES - NOALLOC_KB_OFF) / sizeof(double2);
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+// Device address of g_noalloc_scratch per device, resolved once with that device current.
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_ptr[64] = {nullptr};
+
+static void* noalloc_scratch(int dev) {
+  SLDM_REQUIRE(dev >= 0 && dev < 64, SLDM_EINVAL, "kbar_noalloc: device index out of range");
+  std::lock_guard<std::mutex> l(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    SLDM_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_ptr[dev] = p;
+  }
+  return g_noalloc_ptr[dev];
+}
+
+// Writes the task record and the tile list of one object into the scratch.
+__global__ void noalloc_setup_kernel(KTask task, int ntile_t, int ntile_s, KTask* dtask, TileRef* dtiles) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) *dtask = task;
+  if (i < ntile_t * ntile_s) dtiles[i] = TileRef{0, (i / ntile_s) * TILE_TEST, (i % ntile_s) * TILE_SRC, 0};
+}
+
+}  // namespace sldm
+
+extern "C" int sldm_kbar_noalloc(const sldm_mesh* m, int32_t obj, double k_re, double k_im, void* K_out, void* stream) {
+  using namespace sldm;
+  try {
+    SLDM_REQUIRE(m && K_out, SLDM_EINVAL, "kbar_noalloc: null argument");
+    SLDM_REQUIRE(obj >= 0 && obj < m->h.nobj, SLDM_EINVAL, "kbar_noalloc: object index out of range");
+    SLDM_REQUIRE(std::isfinite(k_re) && std::isfinite(k_im), SLDM_EINVAL, "kbar_noalloc: non-finite wavenumber");
+    int dev = 0;
+    SLDM_CUDA(cudaGetDevice(&dev));
+    SLDM_REQUIRE(dev == m->device, SLDM_EINVAL, "kbar_noalloc: current device differs from the mesh's device");
+    const HostMesh& h = m->h;
+    const int t0 = h.tri_begin[obj], nt_o = h.tri_begin[obj + 1] - t0;
+    const int e0 = h.edge_begin[obj], ne_o = h.edge_begin[obj + 1] - e0;
+    const int b0 = h.bedge_begin[obj], nbe_o = h.bedge_begin[obj + 1] - b0;
+    const int ntile_t = (nt_o + TILE_TEST - 1) / TILE_TEST, ntile_s = (6 * nt_o + TILE_SRC - 1) / TILE_SRC;
+    const size_t nkb = size_t(ne_o) * size_t(nbe_o);
+    SLDM_REQUIRE(nkb <= NOALLOC_MAX_KB && size_t(ntile_t) * ntile_s <= NOALLOC_MAX_TILES, SLDM_EINVAL,
+                 "kbar_noalloc: object too large for the fixed scratch (edges x barycentric edges = " +
+                     std::to_string(nkb) + " > " + std::to_string(NOALLOC_MAX_KB) + ")");
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned char* base = static_cast<unsigned char*>(noalloc_scratch(dev));
+    KTask* dtask = reinterpret_cast<KTask*>(base + NOALLOC_TASK_OFF);
+    TileRef* dtiles = reinterpret_cast<TileRef*>(base + NOALLOC_TILE_OFF);
+    double2* Kb = reinterpret_cast<double2*>(base + NOALLOC_KB_OFF);
+    KTask t{};
+    t.t0 = t0; t.ntest = nt_o; t.c0 = 6 * t0; t.nsrc = 6 * nt_o;
+    t.e_row0 = e0; t.b_col0 = b0; t.ld = nbe_o;
+    t.Kb = Kb;
+    t.kr = k_re; t.ki = k_im;
+    // the block accumulates atomically: it must start at zero on every call
+    SLDM_CUDA(cudaMemsetAsync(Kb, 0, nkb * sizeof(double2), s));
+    const int nset = ntile_t * ntile_s;
+    noalloc_setup_kernel<<<(nset + 127) / 128, 128, 0, s>>>(t, ntile_t, ntile_s, dtask, dtiles);
+    SLDM_CUDA(cudaGetLastError());
+    const DevMesh& d = m->d;
+    fill_K_bulk<double><<<unsigned(nset), TILE_SRC, 0, s>>>(dtask, dtiles, d.geo.p, d.bgeo.p, d.tri.p, d.tri_edge.p,
+                                                            d.btri_edge.p);
+    SLDM_CUDA(cudaGetLastError());
+    const int np = int(h.touchK_a.size());
+    if (np > 0)
+      fill_K_touch<double><<<(np + 127) / 128, 128, 0, s>>>(t, d.touchK_a.p, d.touchK_c.p, np, d.geo.p, d.bgeo.p, d.xyz.p,
+                                                            d.tri.p, d.tri_edge.p, d.btri_edge.p);
+    SLDM_CUDA(cudaGetLastError());
+    contract_bc<double>(m, obj, Kb, nbe_o, K_out, ne_o, s);
+  } catch (const sldm::Error& e) {
+    sldm::set_error(e.msg);
+    return e.code;
+  }
+  return SLDM_OK;
+}

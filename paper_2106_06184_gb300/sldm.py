@@ -80,6 +80,7 @@ EXPORTS = {
     "sldm_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.POINTER(SolveOpts),
                              C.POINTER(SolveInfo), C.c_int32, C.c_void_p]),
     "sldm_farfield": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
+    "sldm_kbar_noalloc": (C.c_int, [C.c_void_p, C.c_int32, C.c_double, C.c_double, C.c_void_p, C.c_void_p]),
     "sldm_timers_enable": (C.c_int, [C.c_int32]),
     "sldm_timers_reset": (C.c_int, []),
     "sldm_timer_get": (C.c_int, [C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
@@ -189,6 +190,16 @@ class Mesh:
         self.L.check(self.L.lib.sldm_mesh_edges(self.h, uv.ctypes.data_as(C.c_void_p), tp.ctypes.data_as(C.c_void_p),
                                                 tm.ctypes.data_as(C.c_void_p)))
         return uv, tp, tm
+
+    def kbar_noalloc(self, obj, k, out, stream=None):
+        """Kbar(k) of object `obj` into the device tensor `out` (ne_o x ne_o complex128)
+        through the allocation-free entry point."""
+        po, wo = _ptr(out)
+        if wo != DEVICE:
+            raise ValueError("kbar_noalloc writes device memory")
+        self.L.check(self.L.lib.sldm_kbar_noalloc(self.h, obj, float(np.real(k)), float(np.imag(k)), po,
+                                                  _stream(stream)))
+        return out
 
     def close(self):
         if self.h:
