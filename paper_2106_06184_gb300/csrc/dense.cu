@@ -99,141 +99,371 @@ __device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
   return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
 }
 
-// Pivot search, row swap and column scaling at step k for each system.
-__global__ void lu_pivot_kernel(const LUSys* __restrict__ sys, int k, int* err) {
-  const LUSys S = sys[blockIdx.x];
-  if (k >= S.n) return;
-  __shared__ double bv[256];
-  __shared__ int bi[256];
-  double best = -1;
-  int besti = k;
-  for (int i = k + threadIdx.x; i < S.n; i += blockDim.x) {
-    double2 a = S.A[int64_t(i) * S.n + k];
-    double v = a.x * a.x + a.y * a.y;
-    if (v > best) {
-      best = v;
-      besti = i;
-    }
-  }
-  bv[threadIdx.x] = best;
-  bi[threadIdx.x] = besti;
+// Batched LU with partial pivoting and look-ahead, one cooperative launch.
+// The CTAs are split into groups, one group per system (or one CTA per system
+// when there are more systems than CTAs).  Within a group the columns of
+// [A | B] are owned block-cyclically (blocks of two columns) by the group's
+// CTAs.  Column k is "published" by its owner: pivot row p_k in piv_row[k],
+// pivot in diag[k], the multipliers of rows > k (of the row-swapped column) in
+// place, then flag[k] = 1.  At step k every CTA waits for flag[k], swaps rows
+// k and p_k of its own columns and eliminates their rows > k; the owner of
+// column k+1 does that column first and publishes it before touching the rest,
+// so no step needs a barrier across the group.  The right-hand sides are
+// eliminated in the same sweep; after one group barrier each CTA
+// back-substitutes the right-hand-side columns it owns.
+//
+// Every wait is bounded: a wait that runs out records an error, after which
+// every CTA leaves at its next wait.
+constexpr int LU_THREADS = 512;
+constexpr unsigned LU_SPIN_LIMIT = 1u << 22;
+
+struct LUGroup {
+  int32_t sys0, nsys_stride;  // systems handled: sys0, sys0 + stride, ... (< nsys)
+  int32_t cta0, gs;           // first CTA and size of the group
+};
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" : : "l"(p), "r"(v) : "memory");
+}
+
+// Thread 0 waits until *p >= target (bounded), then the CTA continues.
+// Returns false when the kernel must stop.
+__device__ bool wait_at_least(const unsigned* p, unsigned target, int* err) {
+  __shared__ int s_ok;
   __syncthreads();
-  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w) {
-      if (bv[threadIdx.x + w] > bv[threadIdx.x] ||
-          (bv[threadIdx.x + w] == bv[threadIdx.x] && bi[threadIdx.x + w] < bi[threadIdx.x])) {
-        bv[threadIdx.x] = bv[threadIdx.x + w];
-        bi[threadIdx.x] = bi[threadIdx.x + w];
-      }
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    unsigned it = 0;
+    while (ld_acquire(p) < target) {
+      if (*(volatile int*)err) { ok = 0; break; }
+      if (++it > LU_SPIN_LIMIT) { atomicExch(err, 2); ok = 0; break; }
+      __nanosleep(32);
     }
-    __syncthreads();
+    s_ok = ok && !*(volatile int*)err;
   }
-  const int p = bi[0];
-  if (!(bv[0] > 0.0)) {  // zero or NaN pivot
-    if (threadIdx.x == 0) atomicExch(err, 1);
+  __syncthreads();
+  return s_ok != 0;
+}
+
+__device__ __forceinline__ double2* lu_colptr(const LUSys& S, int J) { return J < S.n ? S.A + J : S.B + (J - S.n); }
+__device__ __forceinline__ int lu_owner(int J, int gs) { return (J >> 1) % gs; }
+
+// Pivot search over v[0..m) (rows base..base+m-1): largest |v|^2, smallest row on ties.
+__device__ void lu_argmax(const double2* v, int m, int base, int* out_p) {
+  __shared__ double s_bv[LU_THREADS / 32];
+  __shared__ int s_bi[LU_THREADS / 32];
+  double best = -1.0;
+  int bi = base;
+  for (int t = threadIdx.x; t < m; t += blockDim.x) {
+    const double a = v[t].x * v[t].x + v[t].y * v[t].y;
+    if (a > best || (a == best && base + t < bi)) { best = a; bi = base + t; }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    double ob = __shfl_xor_sync(0xffffffffu, best, o);
+    int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+  }
+  if ((threadIdx.x & 31) == 0) { s_bv[threadIdx.x >> 5] = best; s_bi[threadIdx.x >> 5] = bi; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = s_bv[0];
+    int p = s_bi[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+      if (s_bv[w] > b || (s_bv[w] == b && s_bi[w] < p)) { b = s_bv[w]; p = s_bi[w]; }
+    *out_p = (b > 0.0) ? p : -1;
+  }
+  __syncthreads();
+}
+
+// Publishes column J (its rows J.. already hold the values of all earlier
+// steps, copied to v[0..n-J)): pivot, row swap, multipliers, flag.
+__device__ void lu_publish(const LUSys& S, int J, double2* v, double2* diag, int* piv_row, unsigned* flag, int* err) {
+  __shared__ int s_p;
+  const int n = S.n, m = n - J;
+  lu_argmax(v, m, J, &s_p);
+  const int p = s_p;
+  if (p < 0) {
+    if (threadIdx.x == 0) atomicExch(err, 1);  // zero or non-finite pivot
+    __syncthreads();
     return;
   }
-  if (p != k) {
-    for (int j = threadIdx.x; j < S.n; j += blockDim.x) {
-      double2 t = S.A[int64_t(k) * S.n + j];
-      S.A[int64_t(k) * S.n + j] = S.A[int64_t(p) * S.n + j];
-      S.A[int64_t(p) * S.n + j] = t;
-    }
-    for (int j = threadIdx.x; j < S.nrhs; j += blockDim.x) {
-      double2 t = S.B[int64_t(k) * S.nrhs + j];
-      S.B[int64_t(k) * S.nrhs + j] = S.B[int64_t(p) * S.nrhs + j];
-      S.B[int64_t(p) * S.nrhs + j] = t;
-    }
+  const double2 piv = v[p - J];
+  const double den = piv.x * piv.x + piv.y * piv.y;
+  double2* col = S.A + J;
+  for (int t = 1 + threadIdx.x; t < m; t += blockDim.x) {
+    const int i = J + t;
+    const double2 a = (i == p) ? v[0] : v[t];
+    col[int64_t(i) * n] = make_double2((a.x * piv.x + a.y * piv.y) / den, (a.y * piv.x - a.x * piv.y) / den);
+  }
+  if (threadIdx.x == 0) {
+    col[int64_t(J) * n] = piv;
+    diag[J] = piv;
+    piv_row[J] = p;
   }
   __syncthreads();
-  const double2 piv = S.A[int64_t(k) * S.n + k];
-  for (int i = k + 1 + threadIdx.x; i < S.n; i += blockDim.x)
-    S.A[int64_t(i) * S.n + k] = cdiv(S.A[int64_t(i) * S.n + k], piv);
-}
-
-// Trailing update at step k: A[i][j] -= A[i][k] A[k][j] (j > k), B[i][c] -= A[i][k] B[k][c].
-__global__ void lu_update_kernel(const LUSys* __restrict__ sys, int k) {
-  const LUSys S = sys[blockIdx.z];
-  if (k >= S.n) return;
-  const int i = k + 1 + blockIdx.y;
-  if (i >= S.n) return;
-  const double2 l = S.A[int64_t(i) * S.n + k];
-  const int ncols = (S.n - k - 1) + S.nrhs;
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncols; c += gridDim.x * blockDim.x) {
-    if (c < S.n - k - 1) {
-      int j = k + 1 + c;
-      double2 u = S.A[int64_t(k) * S.n + j];
-      double2 a = S.A[int64_t(i) * S.n + j];
-      double2 p = cmul(l, u);
-      S.A[int64_t(i) * S.n + j] = make_double2(a.x - p.x, a.y - p.y);
-    } else {
-      int j = c - (S.n - k - 1);
-      double2 u = S.B[int64_t(k) * S.nrhs + j];
-      double2 a = S.B[int64_t(i) * S.nrhs + j];
-      double2 p = cmul(l, u);
-      S.B[int64_t(i) * S.nrhs + j] = make_double2(a.x - p.x, a.y - p.y);
-    }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    st_release(flag + J, 1u);
   }
 }
 
-// Back substitution U X = B, one CTA per (system, right-hand-side column).
-__global__ void lu_backsub_kernel(const LUSys* __restrict__ sys) {
-  const LUSys S = sys[blockIdx.y];
-  const int c = blockIdx.x;
-  if (c >= S.nrhs) return;
-  __shared__ double2 yk;
-  for (int k = S.n - 1; k >= 0; --k) {
-    if (threadIdx.x == 0) {
-      double2 y = cdiv(S.B[int64_t(k) * S.nrhs + c], S.A[int64_t(k) * S.n + k]);
-      S.B[int64_t(k) * S.nrhs + c] = y;
-      yk = y;
-    }
+__global__ void __launch_bounds__(LU_THREADS) lu_coop_kernel(const LUSys* __restrict__ sys, int nsys,
+                                                             const LUGroup* __restrict__ groups, const int* __restrict__ cta_group,
+                                                             double2* diag_all, int* pivrow_all, unsigned* flag_all,
+                                                             const int64_t* __restrict__ off, unsigned* ctr, int* err,
+                                                             int max_own) {
+  extern __shared__ double2 smem[];
+  const int gid = cta_group[blockIdx.x];
+  const LUGroup G = groups[gid];
+  const int rank = blockIdx.x - G.cta0;
+  unsigned epoch = 0;
+  for (int si = G.sys0; si < nsys; si += G.nsys_stride) {
     __syncthreads();
-    const double2 y = yk;
-    for (int i = threadIdx.x; i < k; i += blockDim.x) {
-      double2 u = S.A[int64_t(i) * S.n + k];
-      double2 p = cmul(u, y);
-      double2 b = S.B[int64_t(i) * S.nrhs + c];
-      S.B[int64_t(i) * S.nrhs + c] = make_double2(b.x - p.x, b.y - p.y);
-    }
+    const LUSys S = sys[si];
+    const int n = S.n, r = S.nrhs, ncol = n + r;
+    double2* diag = diag_all + off[si];
+    int* piv_row = pivrow_all + off[si];
+    unsigned* flag = flag_all + off[si];
+    double2* colv = smem;            // n: working copy of the column being published
+    double2* mult = colv + n;        // n: multipliers of the current step
+    double2* rowk = mult + n;        // max_own
+    double2* rowp = rowk + max_own;  // max_own
+    int* own = reinterpret_cast<int*>(rowp + max_own);
+    int nown = 0;
+    for (int b = rank; 2 * b < ncol; b += G.gs)
+      for (int jj = 0; jj < 2; ++jj)
+        if (2 * b + jj < ncol) {
+          if (threadIdx.x == 0) own[nown] = 2 * b + jj;
+          ++nown;
+        }
     __syncthreads();
+    // column 0 is published by its owner before the first step
+    if (lu_owner(0, G.gs) == rank) {
+      for (int t = threadIdx.x; t < n; t += blockDim.x) colv[t] = S.A[int64_t(t) * n];
+      __syncthreads();
+      lu_publish(S, 0, colv, diag, piv_row, flag, err);
+    }
+    int first = 0;
+    for (int k = 0; k < n; ++k) {
+      if (!wait_at_least(flag + k, 1u, err)) return;
+      while (first < nown && own[first] <= k) ++first;
+      const int p = __ldcg(piv_row + k);
+      const int rows = n - k - 1;
+      const int na = nown - first;
+      for (int t = threadIdx.x; t < rows; t += blockDim.x) mult[t] = __ldcg(S.A + int64_t(k + 1 + t) * n + k);
+      for (int c = threadIdx.x; c < na; c += blockDim.x) {
+        const int J = own[first + c];
+        const double2* col = lu_colptr(S, J);
+        const int64_t ld = J < n ? n : r;
+        rowk[c] = __ldcg(col + int64_t(k) * ld);
+        rowp[c] = __ldcg(col + int64_t(p) * ld);
+      }
+      __syncthreads();
+      // look-ahead: the owner of column k+1 eliminates and publishes it first
+      int skip = -1;
+      if (k + 1 < n && lu_owner(k + 1, G.gs) == rank) {
+        const int c = 0;  // own[first] == k + 1 for the owner of column k + 1
+        skip = c;
+        double2* col = S.A + (k + 1);
+        const double2 u = rowp[c];
+        for (int t = threadIdx.x; t <= rows; t += blockDim.x) {
+          // t = 0 is row k (takes row p), t >= 1 are rows k + t
+          if (t == 0) continue;
+          const int i = k + t;
+          const double2 l = mult[t - 1];
+          double2 a = (i == p) ? rowk[c] : __ldcg(col + int64_t(i) * n);
+          a.x -= l.x * u.x - l.y * u.y;
+          a.y -= l.x * u.y + l.y * u.x;
+          colv[t - 1] = a;  // rows k+1 .. n-1
+        }
+        if (threadIdx.x == 0) col[int64_t(k) * n] = u;
+        __syncthreads();
+        lu_publish(S, k + 1, colv, diag, piv_row, flag, err);
+      }
+      // the other owned columns
+      const int c0 = (skip == 0) ? 1 : 0;
+      const int nb = na - c0;
+      if (p != k)
+        for (int c = c0 + threadIdx.x; c < na; c += blockDim.x) {
+          const int J = own[first + c];
+          double2* col = lu_colptr(S, J);
+          col[int64_t(k) * (J < n ? n : r)] = rowp[c];
+        }
+      const int64_t work = int64_t(rows) * nb;
+      for (int64_t w0 = threadIdx.x; w0 < work; w0 += 4 * int64_t(blockDim.x)) {
+        double2 a[4];
+        int64_t addr[4];
+        double2* base[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int64_t w = w0 + int64_t(q) * blockDim.x;
+          base[q] = nullptr;
+          if (w < work) {
+            const int t = int(w / nb), c = c0 + int(w % nb);
+            const int i = k + 1 + t;
+            const int J = own[first + c];
+            base[q] = lu_colptr(S, J);
+            addr[q] = int64_t(i) * (J < n ? n : r);
+            a[q] = (i == p) ? rowk[c] : __ldcg(base[q] + addr[q]);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int64_t w = w0 + int64_t(q) * blockDim.x;
+          if (w < work) {
+            const int t = int(w / nb), c = c0 + int(w % nb);
+            const double2 l = mult[t];
+            const double2 u = rowp[c];
+            double2 v = a[q];
+            v.x -= l.x * u.x - l.y * u.y;
+            v.y -= l.x * u.y + l.y * u.x;
+            base[q][addr[q]] = v;
+          }
+        }
+      }
+      __syncthreads();
+      // errors are acted on at the next (CTA-uniform) wait
+    }
+    // every column is final once every CTA of the group has finished its last step
+    ++epoch;
+    if (G.gs > 1) {
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(ctr + gid, 1u);
+      }
+      if (!wait_at_least(ctr + gid, epoch * G.gs, err)) return;
+    }
+    // ---- back substitution U X = B on the owned right-hand-side columns
+    int rfirst = 0;
+    while (rfirst < nown && own[rfirst] < n) ++rfirst;
+    const int nr = nown - rfirst;
+    double2* ys = rowk;
+    for (int k = n - 1; k >= 0 && nr > 0; --k) {
+      const double2 dk = __ldcg(diag + k);
+      const double dd = dk.x * dk.x + dk.y * dk.y;
+      for (int c = threadIdx.x; c < nr; c += blockDim.x) {
+        double2* col = S.B + (own[rfirst + c] - n);
+        const double2 bk = __ldcg(col + int64_t(k) * r);
+        const double2 y = make_double2((bk.x * dk.x + bk.y * dk.y) / dd, (bk.y * dk.x - bk.x * dk.y) / dd);
+        ys[c] = y;
+        col[int64_t(k) * r] = y;
+      }
+      __syncthreads();
+      const int64_t work = int64_t(k) * nr;
+      for (int64_t w = threadIdx.x; w < work; w += blockDim.x) {
+        const int i = int(w / nr), c = int(w % nr);
+        double2* col = S.B + (own[rfirst + c] - n);
+        const double2 u = __ldcg(S.A + int64_t(i) * n + k);
+        const double2 y = ys[c];
+        double2 v = __ldcg(col + int64_t(i) * r);
+        v.x -= u.x * y.x - u.y * y.y;
+        v.y -= u.x * y.y + u.y * y.x;
+        col[int64_t(i) * r] = v;
+      }
+      __syncthreads();
+    }
+    // the next system of this group starts only after every CTA finished this one
+    ++epoch;
+    if (G.gs > 1) {
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(ctr + gid, 1u);
+      }
+      if (!wait_at_least(ctr + gid, epoch * G.gs, err)) return;
+    }
   }
 }
 
 void lu_solve_batched(const std::vector<LUSys>& systems, cudaStream_t s) {
   if (systems.empty()) return;
-  int nmax = 0, rmax = 0;
+  int dev = 0, nsm = 0;
+  SLDM_CUDA(cudaGetDevice(&dev));
+  SLDM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  int coop = 0;
+  SLDM_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  SLDM_REQUIRE(coop, SLDM_ENOTSUP, "LU: device does not support cooperative launches");
+  int nmax = 0, cmax = 0;
   for (auto& S : systems) {
     nmax = std::max(nmax, S.n);
-    rmax = std::max(rmax, S.nrhs);
+    cmax = std::max(cmax, S.n + S.nrhs);
+  }
+  const int nsys_ = int(systems.size());
+  const int gs_min = nsys_ <= nsm ? nsm / nsys_ : 1;
+  const int max_own = 2 * ((cmax + 1) / 2 / gs_min + 1);
+  const size_t smem = size_t(2) * nmax * sizeof(double2) + size_t(2) * max_own * sizeof(double2) + size_t(max_own) * sizeof(int);
+  SLDM_REQUIRE(smem <= 220 * 1024, SLDM_ENOTSUP,
+               "LU: object too large for the in-kernel direct factorisation (n = " + std::to_string(nmax) + ")");
+  SLDM_CUDA(cudaFuncSetAttribute(lu_coop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+  int per_sm = 0;
+  SLDM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lu_coop_kernel, LU_THREADS, smem));
+  SLDM_REQUIRE(per_sm >= 1, SLDM_ENOTSUP, "LU: kernel does not fit on an SM");
+  const int nsys = int(systems.size());
+  const int G = nsm;  // one CTA per SM
+  std::vector<LUGroup> groups;
+  std::vector<int> cta_group(G);
+  if (nsys <= G) {
+    const int gs = G / nsys;
+    for (int g = 0; g < nsys; ++g) groups.push_back({g, nsys, g * gs, gs});
+    for (int b = 0; b < G; ++b) cta_group[b] = std::min(b / gs, nsys - 1);
+    // CTAs beyond nsys * gs join the last group's range but own no columns: extend the last group
+    groups.back().gs = G - groups.back().cta0;
+  } else {
+    for (int g = 0; g < G; ++g) groups.push_back({g, G, g, 1});
+    for (int b = 0; b < G; ++b) cta_group[b] = b;
+  }
+  std::vector<int64_t> doff(nsys);
+  int64_t dtot = 0;
+  for (int i = 0; i < nsys; ++i) {
+    doff[i] = dtot;
+    dtot += systems[i].n;
   }
   DBuf<LUSys> d;
+  DBuf<LUGroup> dg;
+  DBuf<int> dcg, err;
+  DBuf<int64_t> ddo;
+  DBuf<double2> diag;
+  DBuf<int> pivrow;
+  DBuf<unsigned> ctr, flags;
   d.upload(systems, s);
-  DBuf<int> err;
+  dg.upload(groups, s);
+  dcg.upload(cta_group, s);
+  ddo.upload(doff, s);
+  diag.alloc(dtot);
+  pivrow.alloc(dtot);
+  flags.alloc(dtot);
+  flags.zero(s);
+  ctr.alloc(groups.size());
+  ctr.zero(s);
   err.alloc(1);
   err.zero(s);
-  const int nsys = int(systems.size());
-  for (int k = 0; k < nmax; ++k) {
-    {
-      ScopedTimer tm("lu_pivot", s);
-      lu_pivot_kernel<<<nsys, 256, 0, s>>>(d.p, k, err.p);
-    }
-    int rows = nmax - k - 1;
-    if (rows > 0) {
-      int cols = rows + rmax;
-      dim3 grid(std::min((cols + 127) / 128, 8), rows, nsys);
-      ScopedTimer tm("lu_update", s);
-      lu_update_kernel<<<grid, 128, 0, s>>>(d.p, k);
-    }
-  }
+  const LUSys* a0 = d.p;
+  int a1 = nsys;
+  const LUGroup* a2 = dg.p;
+  const int* a3 = dcg.p;
+  double2* a4 = diag.p;
+  int* a5 = pivrow.p;
+  unsigned* a6 = flags.p;
+  const int64_t* a7 = ddo.p;
+  unsigned* a8 = ctr.p;
+  int* a9 = err.p;
+  int a10 = max_own;
+  void* args[] = {(void*)&a0, (void*)&a1, (void*)&a2, (void*)&a3, (void*)&a4, (void*)&a5,
+                  (void*)&a6, (void*)&a7, (void*)&a8, (void*)&a9, (void*)&a10};
   {
-    ScopedTimer tm("lu_backsub", s);
-    lu_backsub_kernel<<<dim3(rmax, nsys), 256, 0, s>>>(d.p);
+    ScopedTimer tm("lu_coop", s);
+    SLDM_CUDA(cudaLaunchCooperativeKernel((void*)lu_coop_kernel, dim3(G), dim3(LU_THREADS), args, smem, s));
   }
-  SLDM_CUDA(cudaGetLastError());
   int herr = 0;
   SLDM_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
   SLDM_CUDA(cudaStreamSynchronize(s));
+  SLDM_REQUIRE(herr != 2, SLDM_ECUDA, "LU: a wait for a published column ran out of its limit");
   SLDM_REQUIRE(herr == 0, SLDM_ENUMERIC, "LU of M_l: zero or non-finite pivot");
 }
 
@@ -530,20 +760,33 @@ __global__ void dots_kernel(const double2* __restrict__ V, int64_t ldv, const do
   if (threadIdx.x == 0) h[i] = make_double2(rr[0], ri[0]);
 }
 
-// w -= V[:, :k] h   (or w += when sign = +1);  optionally accumulate hsum += h
-__global__ void vmul_kernel(const double2* __restrict__ V, int64_t ldv, int k, const double2* __restrict__ h, double sign,
-                            double2* w, int64_t n) {
-  int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (t >= n) return;
+// w += sign * V[:, :k] h.  A CTA owns 32 rows; its 8 warps take every 8th
+// Krylov column, and the partial sums meet in shared memory.
+__global__ void __launch_bounds__(256) vmul_kernel(const double2* __restrict__ V, int64_t ldv, int k,
+                                                   const double2* __restrict__ h, double sign, double2* w, int64_t n) {
+  __shared__ double2 part[8][32];
+  const int lane = threadIdx.x & 31, slice = threadIdx.x >> 5;
+  const int64_t t = int64_t(blockIdx.x) * 32 + lane;
   double sr = 0, si = 0;
-  for (int i = 0; i < k; ++i) {
-    double2 v = V[int64_t(i) * ldv + t];
-    double2 c = h[i];
-    sr += v.x * c.x - v.y * c.y;
-    si += v.x * c.y + v.y * c.x;
+  if (t < n) {
+    for (int i = slice; i < k; i += 8) {
+      const double2 v = V[int64_t(i) * ldv + t];
+      const double2 c = h[i];
+      sr += v.x * c.x - v.y * c.y;
+      si += v.x * c.y + v.y * c.x;
+    }
   }
-  double2 o = w[t];
-  w[t] = make_double2(o.x + sign * sr, o.y + sign * si);
+  part[slice][lane] = make_double2(sr, si);
+  __syncthreads();
+  if (slice == 0 && t < n) {
+    double ar = 0, ai = 0;
+    for (int s = 0; s < 8; ++s) {
+      ar += part[s][lane].x;
+      ai += part[s][lane].y;
+    }
+    const double2 o = w[t];
+    w[t] = make_double2(o.x + sign * ar, o.y + sign * ai);
+  }
 }
 
 __global__ void norm2_kernel(const double2* __restrict__ w, int64_t n, double* out) {
@@ -575,7 +818,7 @@ void vdots(const double2* V, int64_t ldv, int k, const double2* w, int64_t n, do
   SLDM_CUDA(cudaGetLastError());
 }
 void vmul(const double2* V, int64_t ldv, int k, const double2* h, double sign, double2* w, int64_t n, cudaStream_t s) {
-  vmul_kernel<<<unsigned((n + 255) / 256), 256, 0, s>>>(V, ldv, k, h, sign, w, n);
+  vmul_kernel<<<unsigned((n + 31) / 32), 256, 0, s>>>(V, ldv, k, h, sign, w, n);
   SLDM_CUDA(cudaGetLastError());
 }
 void vnorm2(const double2* w, int64_t n, double* out, cudaStream_t s) {
