@@ -13,7 +13,7 @@ import pytest
 from oracle import farfield as OF
 from oracle import system as S
 from oracle.topology import Mesh as OMesh
-from workloads.meshes import ellipsoid, icosphere, merge
+from workloads.meshes import cylinder_array, ellipsoid, icosphere, merge
 
 pytestmark = pytest.mark.gpu
 
@@ -57,6 +57,13 @@ def two_lossy():
     return Case(xyz, tri, obj, [(6.0, 1.0, 0.05), (2.5, 1.0, 0.0)], (1.0, 1.0, 0.0), 500e6)
 
 
+@pytest.fixture(scope="module")
+def cyl4():
+    """2 x 2 dielectric cylinders (eps_r 6, r 120 nm, h 300 nm, period 500 nm) at 1 um."""
+    xyz, tri, obj = cylinder_array(2, 2, 120e-9, 300e-9, 500e-9)
+    return Case(xyz, tri, obj, [(6.0, 1.0, 0.0)] * 4, (1.0, 1.0, 0.0), 299792458.0 / 1e-6)
+
+
 def build_op(case, prec):
     sl = _sl()
     m = sl.Mesh(case.xyz, case.tri, case.obj)
@@ -85,7 +92,7 @@ def _blocks(case, op, sl):
     return out
 
 
-@pytest.mark.parametrize("which", ["sphere", "two_lossy"])
+@pytest.mark.parametrize("which", ["sphere", "two_lossy", "cyl4"])
 def test_fp64_blocks_match_oracle(which, request):
     case = request.getfixturevalue(which)
     sl, m, st, op = build_op(case, 0)
@@ -94,7 +101,7 @@ def test_fp64_blocks_match_oracle(which, request):
         assert rel(got, ref) < 1e-10 and relmax(got, ref) < 1e-10, (name, rel(got, ref), relmax(got, ref))
 
 
-@pytest.mark.parametrize("which", ["sphere", "two_lossy"])
+@pytest.mark.parametrize("which", ["sphere", "two_lossy", "cyl4"])
 def test_fp32_blocks_match_oracle(which, request):
     case = request.getfixturevalue(which)
     sl, m, st, op = build_op(case, 1)
@@ -117,7 +124,7 @@ def test_apply_matches_oracle(which, request):
     assert rel(Y, ref) < 1e-10
 
 
-@pytest.mark.parametrize("which", ["sphere", "two_lossy"])
+@pytest.mark.parametrize("which", ["sphere", "two_lossy", "cyl4"])
 def test_rhs_and_solve_match_oracle(which, request):
     case = request.getfixturevalue(which)
     sl, m, st, op = build_op(case, 0)

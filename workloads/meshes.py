@@ -211,3 +211,14 @@ def merge(*meshes):
         obj.append(np.full(len(f), o, dtype=np.int32))
         off += len(v)
     return np.concatenate(xyz), np.concatenate(tri).astype(np.int32), np.concatenate(obj)
+
+
+def cylinder_array(nx: int, ny: int, radius: float, height: float, period: float, z0: float = 0.0):
+    """nx x ny capped cylinders (240 triangles each) on a square lattice, bases at z0.
+
+    Returns (xyz, tri, obj) with one object per cylinder, row by row.
+    """
+    ox = -(nx - 1) * period / 2
+    oy = -(ny - 1) * period / 2
+    return merge(*[cylinder(radius, height, center=(ox + i * period, oy + j * period, z0))
+                   for j in range(ny) for i in range(nx)])
