@@ -106,12 +106,15 @@ typedef struct {
   void* stream;         /* stream the fill runs on (NULL = default) */
 } sldm_assemble_opts;
 
+#define SLDM_PRECOND_P 0     /* right preconditioner P of Eq. pcext (default) */
+#define SLDM_PRECOND_NONE 1  /* no preconditioner */
+
 typedef struct {
-  double tol;           /* relative residual ||b - Z x|| / ||b|| (default 1e-8) */
+  double tol;           /* relative residual of the length-scaled system (default 1e-8), see sldm_solve */
   int32_t restart;      /* GMRES restart length m (default 100) */
   int32_t maxit;        /* maximum total iterations (default 2000) */
   int32_t x0_given;     /* nonzero: x holds the initial guess on entry */
-  int32_t reserved;
+  int32_t precond;      /* SLDM_PRECOND_P (0, default) or SLDM_PRECOND_NONE */
 } sldm_solve_opts;
 
 typedef struct {
@@ -192,7 +195,14 @@ int sldm_rhs_planewave(const sldm_op* op, const double* khat, const double* pol,
 
 /* Solve Z x = b by restarted GMRES with FP64 Arnoldi (classical Gram-Schmidt
  * twice) and Givens rotations (Sec. IV, GMRES), matrix-vector products in the
- * operator's precision.  b, x: N x nrhs complex128 column-major.
+ * operator's precision, right-preconditioned by P of Eq. pcext (Sec. III:
+ * diagonals of the blocks, with the analytic block inverse through the Schur
+ * complement of the charge block, formed per object at assembly).
+ * b, x: N x nrhs complex128 column-major.
+ * The iteration runs on the length-scaled system Dr Z Dc (Dr = diag(1, 1, l),
+ * Dc = diag(1/l, 1, l) on the blocks [j; e; u], l = the mesh's mean edge
+ * length), whose blocks are O(1) for any geometry size in metres; tol and the
+ * reported relres refer to ||Dr (b - Z x)|| / ||Dr b||.
  * Returns SLDM_ENOTCONV (x holds the last iterate) if tol is not reached. */
 int sldm_solve(const sldm_op* op, const void* b, void* x, int32_t nrhs, const sldm_solve_opts* opts,
                sldm_solve_info* info, int32_t where, void* stream);

@@ -9,6 +9,7 @@
 
 #include "dense.h"
 #include "internal.h"
+#include "precond.h"
 
 namespace sldm {
 
@@ -49,9 +50,11 @@ struct sldm_op {
   sldm::DBuf<sldm::GemvJob> jobs1, jobs2;
   sldm::DBuf<int64_t> rs1, rs2;
   sldm::GemvPlan plan1, plan2;
+  // preconditioner of Eq. pcext
+  sldm::Precond pc;
   // GMRES workspace
   int ws_m = 0;
-  sldm::DBuf<double2> V, wb, wx, wr, wtmp, dh;
+  sldm::DBuf<double2> V, wb, wx, wr, wtmp, wtmp2, wacc, dh;
   sldm::DBuf<double> dnorm;
   std::mutex busy;
 };
@@ -59,7 +62,8 @@ struct sldm_op {
 namespace sldm {
 
 static int64_t op_bytes(const sldm_op* op) {
-  return int64_t(op->LAm.bytes() + op->LPm.bytes() + op->loc.bytes() + op->ix_val.bytes() + op->V.bytes());
+  return int64_t(op->LAm.bytes() + op->LPm.bytes() + op->loc.bytes() + op->ix_val.bytes() + op->V.bytes() +
+                 op->pc.sinv.bytes() + op->pc.lam.bytes() + op->pc.pdiag.bytes());
 }
 
 template <class C>
@@ -258,6 +262,13 @@ static void assemble_impl(sldm_op* op, const sldm_material* mats, cudaStream_t s
     SLDM_CUDA(cudaStreamSynchronize(s));
   }
   build_plans<C>(op);
+  // ---- preconditioner P (Eq. pcext): diagonals and the per-object Schur complement inverses
+  {
+    std::vector<PrecObj> po;
+    for (auto& oi : op->obj) po.push_back({oi.e0, oi.ne, oi.t0, oi.nt, oi.q0, 0, oi.oLA, oi.oK, oi.oLP});
+    prec_setup<C>(op->pc, m, po, op->k0, op->LAm.p, op->LPm.p, op->loc.p, op->ix_val.p, s);
+    op->pc.ready = true;
+  }
   SLDM_CUDA(cudaStreamSynchronize(s));
 }
 
@@ -269,6 +280,8 @@ static void ensure_ws(sldm_op* op, int m) {
   op->wx.alloc(op->N);
   op->wr.alloc(op->N);
   op->wtmp.alloc(op->N);
+  op->wtmp2.alloc(op->N);
+  op->wacc.alloc(op->N);
   op->dh.alloc(2 * (m + 2));
   op->dnorm.alloc(1);
   op->ws_m = m;
@@ -282,20 +295,46 @@ static double dnorm(sldm_op* op, const double2* v, cudaStream_t s) {
   return std::sqrt(h);
 }
 
-// Solves one right-hand side held in op->wb into op->wx (initial guess in wx).
-static void gmres_one(sldm_op* op, int m, double tol, int maxit, int& iters, double& relres, cudaStream_t s) {
+// The Krylov iteration runs on the length-scaled system Dr Z Dc, Dr = diag(1,
+// 1, l), Dc = diag(1/l, 1, l) (blocks j, e, u; l = mean edge length).  The
+// blocks of Z scale as l (L^A), 1 (K, I_x, D), 1/l (L^phi) and 1/l^2 (k0^2), so
+// the scaled system has O(1) blocks whatever the size of the geometry in
+// metres, which is what the frequency scalings of the final system presume.
+// With the preconditioner P of Eq. pcext applied on the right, the scaled
+// preconditioner Dr P Dc cancels Dc:  operator = Dr Z P^-1 Dr^-1.
+static void op_hat(sldm_op* op, bool use_p, const double2* v, double2* w, cudaStream_t s) {
+  const double l = op->mesh->h.ell;
+  if (use_p) {
+    vscale3(op->N, op->ne, 1.0, 1.0, 1.0 / l, v, op->wtmp2.p, s);
+    prec_apply(op->pc, op->mesh, op->wtmp2.p, op->wtmp.p, s);
+  } else {
+    vscale3(op->N, op->ne, 1.0 / l, 1.0, l, v, op->wtmp.p, s);
+  }
+  apply_any(op, op->wtmp.p, w, 1, s);
+  vscale3(op->N, op->ne, 1.0, 1.0, l, w, w, s);
+}
+
+// Solves one right-hand side held in op->wb into op->wx (initial guess in wx)
+// by restarted, right-preconditioned GMRES on the length-scaled system;
+// relres = ||Dr (b - Z x)|| / ||Dr b||.
+static void gmres_one(sldm_op* op, bool use_p, int m, double tol, int maxit, int& iters, double& relres, cudaStream_t s) {
   const int64_t N = op->N;
+  const double l = op->mesh->h.ell;
   double2* V = op->V.p;
+  vscale3(N, op->ne, 1.0, 1.0, l, op->wb.p, op->wb.p, s);  // bh = Dr b
   const double bnorm = dnorm(op, op->wb.p, s);
   if (bnorm == 0) {
     SLDM_CUDA(cudaMemsetAsync(op->wx.p, 0, N * sizeof(double2), s));
     relres = 0;
     return;
   }
-  // r = b - Z x
-  apply_any(op, op->wx.p, op->wr.p, 1, s);
-  vaxpby(N, 1.0, op->wb.p, -1.0, op->wr.p, s);
-  double beta = dnorm(op, op->wr.p, s);
+  auto residual = [&]() {  // wr = Dr (b - Z x)
+    apply_any(op, op->wx.p, op->wr.p, 1, s);
+    vscale3(N, op->ne, 1.0, 1.0, l, op->wr.p, op->wr.p, s);
+    vaxpby(N, 1.0, op->wb.p, -1.0, op->wr.p, s);
+    return dnorm(op, op->wr.p, s);
+  };
+  double beta = residual();
   std::vector<cplx> H(size_t(m + 1) * m), g(m + 1), cs(m), sn(m), hh(2 * (m + 2));
   double hn = 0;
   while (beta / bnorm > tol && iters < maxit) {
@@ -306,7 +345,7 @@ static void gmres_one(sldm_op* op, int m, double tol, int maxit, int& iters, dou
     int kused = 0;
     for (int k = 0; k < m; ++k) {
       double2* w = V + int64_t(k + 1) * N;
-      apply_any(op, V + int64_t(k) * N, w, 1, s);
+      op_hat(op, use_p, V + int64_t(k) * N, w, s);
       // classical Gram-Schmidt, twice
       vdots(V, N, k + 1, w, N, op->dh.p, s);
       vmul(V, N, k + 1, op->dh.p, -1.0, w, N, s);
@@ -343,7 +382,7 @@ static void gmres_one(sldm_op* op, int m, double tol, int maxit, int& iters, dou
       kused = k + 1;
       if (std::abs(g[k + 1]) / bnorm <= tol || iters >= maxit || hn == 0) break;
     }
-    // y = H^-1 g (upper triangular), x += V y
+    // y = H^-1 g (upper triangular);  x += (P^-1 Dr^-1 or Dc) V y
     std::vector<cplx> y(kused);
     for (int i = kused - 1; i >= 0; --i) {
       cplx acc = g[i];
@@ -351,10 +390,16 @@ static void gmres_one(sldm_op* op, int m, double tol, int maxit, int& iters, dou
       y[i] = acc / H[size_t(i) * m + i];
     }
     SLDM_CUDA(cudaMemcpyAsync(op->dh.p, y.data(), kused * sizeof(double2), cudaMemcpyHostToDevice, s));
-    vmul(V, N, kused, op->dh.p, 1.0, op->wx.p, N, s);
-    apply_any(op, op->wx.p, op->wr.p, 1, s);
-    vaxpby(N, 1.0, op->wb.p, -1.0, op->wr.p, s);
-    beta = dnorm(op, op->wr.p, s);
+    SLDM_CUDA(cudaMemsetAsync(op->wacc.p, 0, N * sizeof(double2), s));
+    vmul(V, N, kused, op->dh.p, 1.0, op->wacc.p, N, s);
+    if (use_p) {
+      vscale3(N, op->ne, 1.0, 1.0, 1.0 / l, op->wacc.p, op->wtmp2.p, s);
+      prec_apply(op->pc, op->mesh, op->wtmp2.p, op->wtmp.p, s);
+    } else {
+      vscale3(N, op->ne, 1.0 / l, 1.0, l, op->wacc.p, op->wtmp.p, s);
+    }
+    vaxpby(N, 1.0, op->wtmp.p, 1.0, op->wx.p, s);
+    beta = residual();
   }
   relres = beta / bnorm;
 }
@@ -655,6 +700,7 @@ int sldm_solve(const sldm_op* op_, const void* b, void* x, int32_t nrhs, const s
   int m = (opts && opts->restart > 0) ? opts->restart : 100;
   int maxit = (opts && opts->maxit > 0) ? opts->maxit : 2000;
   bool x0 = opts && opts->x0_given;
+  bool use_p = !(opts && opts->precond == SLDM_PRECOND_NONE) && op->pc.ready;
   cudaStream_t s = (cudaStream_t)stream;
   ensure_ws(op, m);
   const size_t vb = size_t(op->N) * sizeof(double2);
@@ -668,7 +714,7 @@ int sldm_solve(const sldm_op* op_, const void* b, void* x, int32_t nrhs, const s
     if (x0) SLDM_CUDA(cudaMemcpyAsync(op->wx.p, xr, vb, k_in, s));
     else SLDM_CUDA(cudaMemsetAsync(op->wx.p, 0, vb, s));
     double rel = 0;
-    gmres_one(op, m, tol, maxit, iters, rel, s);
+    gmres_one(op, use_p, m, tol, maxit, iters, rel, s);
     worst = std::max(worst, rel);
     cudaMemcpyKind k_out = where == SLDM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     SLDM_CUDA(cudaMemcpyAsync(xr, op->wx.p, vb, k_out, s));

@@ -813,6 +813,20 @@ __global__ void axpby_kernel(int64_t n, double alpha, const double2* __restrict_
   y[t] = make_double2(alpha * a.x + beta * b.x, alpha * a.y + beta * b.y);
 }
 
+// y[i] = s_b x[i] with s_b = s1 on [0, ne), s2 on [ne, 2 ne), s3 on [2 ne, n) (in place allowed)
+__global__ void vscale3_kernel(int64_t n, int64_t ne, double s1, double s2, double s3, const double2* __restrict__ x, double2* y) {
+  int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const double s = t < ne ? s1 : (t < 2 * ne ? s2 : s3);
+  const double2 a = x[t];
+  y[t] = make_double2(s * a.x, s * a.y);
+}
+
+void vscale3(int64_t n, int64_t ne, double s1, double s2, double s3, const double2* x, double2* y, cudaStream_t s) {
+  vscale3_kernel<<<unsigned((n + 255) / 256), 256, 0, s>>>(n, ne, s1, s2, s3, x, y);
+  SLDM_CUDA(cudaGetLastError());
+}
+
 void vdots(const double2* V, int64_t ldv, int k, const double2* w, int64_t n, double2* h, cudaStream_t s) {
   dots_kernel<<<k, 256, 0, s>>>(V, ldv, w, n, h);
   SLDM_CUDA(cudaGetLastError());

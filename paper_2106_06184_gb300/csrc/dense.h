@@ -56,6 +56,7 @@ void vdots(const double2* V, int64_t ldv, int k, const double2* w, int64_t n, do
 void vmul(const double2* V, int64_t ldv, int k, const double2* h, double sign, double2* w, int64_t n, cudaStream_t s);
 void vnorm2(const double2* w, int64_t n, double* out, cudaStream_t s);
 void vaxpby(int64_t n, double alpha, const double2* x, double beta, double2* y, cudaStream_t s);
+void vscale3(int64_t n, int64_t ne, double s1, double s2, double s3, const double2* x, double2* y, cudaStream_t s);
 
 template <class C>
 void to_c128(const void* src, int64_t n, double2* dst, cudaStream_t s);

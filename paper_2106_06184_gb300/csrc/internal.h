@@ -85,6 +85,7 @@ struct DBuf {
 // tri[t][i] and the edge opposite to it.
 struct HostMesh {
   int64_t nv = 0, nt = 0, ne = 0, nobj = 0, nbe = 0;
+  double ell = 1.0;                        // mean edge length: the length unit of the scaled solve
   std::vector<double> xyz;                 // nv*3
   std::vector<int32_t> tri;                // nt*3
   std::vector<int32_t> obj;                // nt

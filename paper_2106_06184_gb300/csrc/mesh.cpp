@@ -143,6 +143,15 @@ void build_host_mesh(const double* xyz, int64_t nv, const int32_t* tri, int64_t 
   SLDM_REQUIRE(build_edges(tv, nt, hm.obj, hm.uv, hm.tplus, hm.tminus, hm.tri_edge, hm.tri_sign, dir, msg),
                SLDM_EINVAL, msg);
   hm.ne = int64_t(hm.tplus.size());
+  {
+    double acc = 0;
+    for (int64_t n = 0; n < hm.ne; ++n) {
+      const double* a = &xyz[3 * hm.uv[2 * n]];
+      const double* b = &xyz[3 * hm.uv[2 * n + 1]];
+      acc += std::sqrt((a[0] - b[0]) * (a[0] - b[0]) + (a[1] - b[1]) * (a[1] - b[1]) + (a[2] - b[2]) * (a[2] - b[2]));
+    }
+    hm.ell = acc / double(hm.ne);
+  }
   hm.edge_begin.assign(size_t(hm.nobj) + 1, 0);
   for (int64_t n = 0, o = 0; o <= hm.nobj; ++o) {
     while (n < hm.ne && hm.obj[hm.tplus[n]] < o) ++n;
