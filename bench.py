@@ -237,28 +237,28 @@ def run_ours(args, rank, world):
     tri_obj = np.zeros(nt, np.int64) if obj_ids is None else np.asarray(obj_ids)
     obj_sizes = [(int(np.sum(tri_obj[tp] == o)), int(np.sum(tri_obj == o))) for o in range(nobj)]
     cand = {}
-    if "gemv" in timers:
-        ms, cnt = timers["gemv"]
+    if "gemv_main" in timers:
+        # the HBM-streaming stage: L^A_m, L^phi_m and every object's L^A, K, L^phi, once per launch
+        ms, cnt = timers["gemv_main"]
         s1, s2 = gemv_split(ne, nt, obj_sizes, W_esz)
-        # launches alternate between the two stages of the structured product
-        achieved = ((s1 + s2) / 2) / (ms / cnt / 1e3) / 1e9
-        cand["gemv"] = dict(bound="hbm", achieved=achieved, peak=hbm, unit="GB/s", ms=ms,
-                            bytes_per_launch=(s1 + s2) / 2)
+        achieved = s2 / (ms / cnt / 1e3) / 1e9
+        cand["gemv_main"] = dict(bound="hbm", achieved=achieved, peak=hbm, unit="GB/s", ms=ms, bytes_per_launch=s2)
     for k in ("fill_K_bulk", "fill_L_bulk", "lu_coop", "fill_K_touch", "fill_L_touch"):
         if k in timers and k not in cand:
             cand[k] = dict(bound="alu", achieved=None, peak=FP64_PEAK_TFLOPS if W["precision"] == 0 else FP32_PEAK_TFLOPS,
                            unit="TFLOP/s", ms=timers[k][0])
     dom = max(cand, key=lambda k: timers[k][0]) if cand else None
     # report the HBM-bound product when it is a large share, else the dominant kernel
-    if "gemv" in cand and timers["gemv"][0] >= 0.25 * timers[dom][0]:
-        dom = "gemv"
+    if "gemv_main" in cand and timers["gemv_main"][0] >= 0.25 * timers[dom][0]:
+        dom = "gemv_main"
     roof = None
     if dom:
         c = cand[dom]
         roof = {"kernel": dom, "bound": c["bound"], "achieved": c["achieved"], "peak": c["peak"], "unit": c["unit"],
                 "frac": (c["achieved"] / c["peak"]) if c["achieved"] is not None else None,
                 "peak_source": hbm_src if c["bound"] == "hbm" else "derived",
-                "traffic": None, "share_of_step": timers[dom][0] / total_ms if world == 1 else None}
+                "traffic": None, "share_of_step": timers[dom][0] / total_ms if world == 1 else None,
+                "algorithmic_unit": c.get("bytes_per_launch")}
     kernel_ms = {k: round(v[0] / args.steps, 4) for k, v in sorted(timers.items(), key=lambda kv: -kv[1][0])}
     launches = sum(v[1] for k, v in timers.items() if k != "apply")
     out = {

@@ -108,6 +108,8 @@ static void build_plans(sldm_op* op) {
   };
   mk(j1, op->jobs1, op->rs1, op->plan1);
   mk(j2, op->jobs2, op->rs2, op->plan2);
+  op->plan1.name = "gemv_y";     // Y11, Y21 (per object)
+  op->plan2.name = "gemv_main";  // L^A_m, L^phi_m and the internal blocks
 }
 
 // y = Z x for nrhs columns, x/y complex128 on the device (column stride N)
@@ -241,23 +243,24 @@ static void assemble_impl(sldm_op* op, const sldm_material* mats, cudaStream_t s
     }
   }
   Kb.release();
-  // ---- Y11, Y21 by LU of M_l (FP64)
+  // ---- Y11, Y21 by LU of M_l, in the operator's precision
   {
-    DBuf<double2> Ml, Rl;
+    DBuf<C> Ml, Rl;
     Ml.alloc(ml_total);
     Rl.alloc(rl_total);
-    std::vector<LUSys> sys;
+    std::vector<LUSysT<C>> sys;
     for (int o = 0; o < op->nobj; ++o) {
       const ObjInfo& oi = op->obj[o];
       build_Ml<C>(m, o, op->k0, op->LAm.p, op->ne, op->LPm.p, op->nt, Kl.p + kl_off[o] * es, oi.ne, op->ix_val.p,
                   Ml.p + ml_off[o], Rl.p + rl_off[o], s);
       sys.push_back({Ml.p + ml_off[o], Rl.p + rl_off[o], oi.ne + oi.nq, oi.ne});
     }
-    lu_solve_batched(sys, s);
+    lu_solve_batched<C>(sys, s);
     for (int o = 0; o < op->nobj; ++o) {
       const ObjInfo& oi = op->obj[o];
-      from_c128<C>(Rl.p + rl_off[o], int64_t(oi.ne) * oi.ne, loc + oi.oY11 * es, s);
-      from_c128<C>(Rl.p + rl_off[o] + int64_t(oi.ne) * oi.ne, int64_t(oi.nq) * oi.ne, loc + oi.oY21 * es, s);
+      // undo the length scaling of M_l: Y11 = Yh11 / l, Y21 = l Yh21
+      copy_scaled<C>(Rl.p + rl_off[o], int64_t(oi.ne) * oi.ne, 1.0 / h.ell, loc + oi.oY11 * es, s);
+      copy_scaled<C>(Rl.p + rl_off[o] + int64_t(oi.ne) * oi.ne, int64_t(oi.nq) * oi.ne, h.ell, loc + oi.oY21 * es, s);
     }
     SLDM_CUDA(cudaStreamSynchronize(s));
   }

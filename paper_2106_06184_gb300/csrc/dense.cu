@@ -25,10 +25,13 @@ struct CT<double2> {
 };
 
 // ---------------------------------------------------------------- M_l and R_l
+// M_l is built length-scaled (l = mean edge length): Mh = diag(1, l) M_l diag(1/l, l)
+// = [[mu_l L^A_l / l, -l D^T L^phi_l B], [F D, -k0^2 l^2 I]], whose entries are O(1);
+// its solution Yh gives Y11 = Yh11 / l and Y21 = l Yh21 (the right-hand side is unchanged).
 template <class C>
-__global__ void build_Ml_kernel(int ne_o, int nt_o, int e0, int t0, double k0, const C* __restrict__ LAm, int64_t ldLA,
+__global__ void build_Ml_kernel(int ne_o, int nt_o, int e0, int t0, double k0, double ell, const C* __restrict__ LAm, int64_t ldLA,
                                 const C* __restrict__ LPm, int64_t ldLP, const int32_t* __restrict__ tplus,
-                                const int32_t* __restrict__ tminus, double2* Ml) {
+                                const int32_t* __restrict__ tminus, C* Ml) {
   const int n = ne_o + nt_o - 1;
   int col = blockIdx.x * blockDim.x + threadIdx.x;
   int row = blockIdx.y;
@@ -36,7 +39,7 @@ __global__ void build_Ml_kernel(int ne_o, int nt_o, int e0, int t0, double k0, c
   double2 v = make_double2(0, 0);
   if (row < ne_o && col < ne_o) {
     C a = LAm[int64_t(e0 + row) * ldLA + (e0 + col)];
-    v = make_double2(double(a.x), double(a.y));
+    v = make_double2(double(a.x) / ell, double(a.y) / ell);
   } else if (row < ne_o) {
     // -(D^T L^phi_m B)[row, q]:  (L B)[t, q] = L[t, q] - L[t, last]
     int q = col - ne_o;
@@ -46,23 +49,26 @@ __global__ void build_Ml_kernel(int ne_o, int nt_o, int e0, int t0, double k0, c
     C c = LPm[int64_t(tm) * ldLP + (t0 + q)], d = LPm[int64_t(tm) * ldLP + last];
     double re = (double(a.x) - double(b.x)) - (double(c.x) - double(d.x));
     double im = (double(a.y) - double(b.y)) - (double(c.y) - double(d.y));
-    v = make_double2(-re, -im);
+    v = make_double2(-re * ell, -im * ell);
   } else if (col < ne_o) {
     // (F D)[q, col]: +1 if triangle q is T+ of edge col, -1 if T-
     int q = row - ne_o;
     int tp = tplus[e0 + col] - t0, tm = tminus[e0 + col] - t0;
     v = make_double2((tp == q ? 1.0 : 0.0) - (tm == q ? 1.0 : 0.0), 0.0);
   } else {
-    v = make_double2(row == col ? -k0 * k0 : 0.0, 0.0);
+    v = make_double2(row == col ? -k0 * k0 * ell * ell : 0.0, 0.0);
   }
-  Ml[int64_t(row) * n + col] = v;
+  C o;
+  o.x = decltype(o.x)(v.x);
+  o.y = decltype(o.y)(v.y);
+  Ml[int64_t(row) * n + col] = o;
 }
 
 // R = [Kbar_l + I_x/2 ; 0]  (n x ne_o, row-major)
 template <class C>
 __global__ void build_Rl_kernel(int ne_o, int nt_o, int e0, const C* __restrict__ Kl, int64_t ldK,
                                 const int32_t* __restrict__ ix_ptr, const int32_t* __restrict__ ix_col,
-                                const double* __restrict__ ix_val, double2* Rl) {
+                                const double* __restrict__ ix_val, C* Rl) {
   int col = blockIdx.x * blockDim.x + threadIdx.x;
   int row = blockIdx.y;
   if (col >= ne_o) return;
@@ -73,17 +79,20 @@ __global__ void build_Rl_kernel(int ne_o, int nt_o, int e0, const C* __restrict_
     for (int z = ix_ptr[e0 + row]; z < ix_ptr[e0 + row + 1]; ++z)
       if (ix_col[z] == e0 + col) v.x += 0.5 * ix_val[z];
   }
-  Rl[int64_t(row) * ne_o + col] = v;
+  C o;
+  o.x = decltype(o.x)(v.x);
+  o.y = decltype(o.y)(v.y);
+  Rl[int64_t(row) * ne_o + col] = o;
 }
 
 template <class C>
 void build_Ml(const sldm_mesh* m, int obj, double k0, const void* LAm, int64_t ldLA, const void* LPm, int64_t ldLP,
-              const void* Kl, int64_t ldK, const double* ix_val, double2* Ml, double2* Rl, cudaStream_t s) {
+              const void* Kl, int64_t ldK, const double* ix_val, C* Ml, C* Rl, cudaStream_t s) {
   const HostMesh& h = m->h;
   int e0 = h.edge_begin[obj], ne_o = h.edge_begin[obj + 1] - e0;
   int t0 = h.tri_begin[obj], nt_o = h.tri_begin[obj + 1] - t0;
   int n = ne_o + nt_o - 1;
-  build_Ml_kernel<C><<<dim3((n + 127) / 128, n), 128, 0, s>>>(ne_o, nt_o, e0, t0, k0, (const C*)LAm, ldLA, (const C*)LPm,
+  build_Ml_kernel<C><<<dim3((n + 127) / 128, n), 128, 0, s>>>(ne_o, nt_o, e0, t0, k0, h.ell, (const C*)LAm, ldLA, (const C*)LPm,
                                                               ldLP, m->d.tplus.p, m->d.tminus.p, Ml);
   build_Rl_kernel<C><<<dim3((ne_o + 127) / 128, n), 128, 0, s>>>(ne_o, nt_o, e0, (const C*)Kl, ldK, m->d.ix_ptr.p,
                                                                  m->d.ix_col.p, ix_val, Rl);
@@ -150,17 +159,19 @@ __device__ bool wait_at_least(const unsigned* p, unsigned target, int* err) {
   return s_ok != 0;
 }
 
-__device__ __forceinline__ double2* lu_colptr(const LUSys& S, int J) { return J < S.n ? S.A + J : S.B + (J - S.n); }
+template <class C>
+__device__ __forceinline__ C* lu_colptr(const LUSysT<C>& S, int J) { return J < S.n ? S.A + J : S.B + (J - S.n); }
 __device__ __forceinline__ int lu_owner(int J, int gs) { return (J >> 1) % gs; }
 
 // Pivot search over v[0..m) (rows base..base+m-1): largest |v|^2, smallest row on ties.
-__device__ void lu_argmax(const double2* v, int m, int base, int* out_p) {
+template <class C>
+__device__ void lu_argmax(const C* v, int m, int base, int* out_p) {
   __shared__ double s_bv[LU_THREADS / 32];
   __shared__ int s_bi[LU_THREADS / 32];
   double best = -1.0;
   int bi = base;
   for (int t = threadIdx.x; t < m; t += blockDim.x) {
-    const double a = v[t].x * v[t].x + v[t].y * v[t].y;
+    const double a = double(v[t].x) * double(v[t].x) + double(v[t].y) * double(v[t].y);
     if (a > best || (a == best && base + t < bi)) { best = a; bi = base + t; }
   }
   for (int o = 16; o > 0; o >>= 1) {
@@ -182,7 +193,9 @@ __device__ void lu_argmax(const double2* v, int m, int base, int* out_p) {
 
 // Publishes column J (its rows J.. already hold the values of all earlier
 // steps, copied to v[0..n-J)): pivot, row swap, multipliers, flag.
-__device__ void lu_publish(const LUSys& S, int J, double2* v, double2* diag, int* piv_row, unsigned* flag, int* err) {
+template <class C>
+__device__ void lu_publish(const LUSysT<C>& S, int J, C* v, C* diag, int* piv_row, unsigned* flag, int* err) {
+  typedef decltype(v->x) R;
   __shared__ int s_p;
   const int n = S.n, m = n - J;
   lu_argmax(v, m, J, &s_p);
@@ -192,13 +205,16 @@ __device__ void lu_publish(const LUSys& S, int J, double2* v, double2* diag, int
     __syncthreads();
     return;
   }
-  const double2 piv = v[p - J];
-  const double den = piv.x * piv.x + piv.y * piv.y;
-  double2* col = S.A + J;
+  const C piv = v[p - J];
+  const R den = piv.x * piv.x + piv.y * piv.y;
+  C* col = S.A + J;
   for (int t = 1 + threadIdx.x; t < m; t += blockDim.x) {
     const int i = J + t;
-    const double2 a = (i == p) ? v[0] : v[t];
-    col[int64_t(i) * n] = make_double2((a.x * piv.x + a.y * piv.y) / den, (a.y * piv.x - a.x * piv.y) / den);
+    const C a = (i == p) ? v[0] : v[t];
+    C q;
+    q.x = (a.x * piv.x + a.y * piv.y) / den;
+    q.y = (a.y * piv.x - a.x * piv.y) / den;
+    col[int64_t(i) * n] = q;
   }
   if (threadIdx.x == 0) {
     col[int64_t(J) * n] = piv;
@@ -212,27 +228,30 @@ __device__ void lu_publish(const LUSys& S, int J, double2* v, double2* diag, int
   }
 }
 
-__global__ void __launch_bounds__(LU_THREADS) lu_coop_kernel(const LUSys* __restrict__ sys, int nsys,
+template <class C>
+__global__ void __launch_bounds__(LU_THREADS) lu_coop_kernel(const LUSysT<C>* __restrict__ sys, int nsys,
                                                              const LUGroup* __restrict__ groups, const int* __restrict__ cta_group,
-                                                             double2* diag_all, int* pivrow_all, unsigned* flag_all,
+                                                             C* diag_all, int* pivrow_all, unsigned* flag_all,
                                                              const int64_t* __restrict__ off, unsigned* ctr, int* err,
                                                              int max_own) {
-  extern __shared__ double2 smem[];
+  typedef decltype(diag_all->x) R;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* smem = reinterpret_cast<C*>(smem_raw);
   const int gid = cta_group[blockIdx.x];
   const LUGroup G = groups[gid];
   const int rank = blockIdx.x - G.cta0;
   unsigned epoch = 0;
   for (int si = G.sys0; si < nsys; si += G.nsys_stride) {
     __syncthreads();
-    const LUSys S = sys[si];
+    const LUSysT<C> S = sys[si];
     const int n = S.n, r = S.nrhs, ncol = n + r;
-    double2* diag = diag_all + off[si];
+    C* diag = diag_all + off[si];
     int* piv_row = pivrow_all + off[si];
     unsigned* flag = flag_all + off[si];
-    double2* colv = smem;            // n: working copy of the column being published
-    double2* mult = colv + n;        // n: multipliers of the current step
-    double2* rowk = mult + n;        // max_own
-    double2* rowp = rowk + max_own;  // max_own
+    C* colv = smem;            // n: working copy of the column being published
+    C* mult = colv + n;        // n: multipliers of the current step
+    C* rowk = mult + n;        // max_own
+    C* rowp = rowk + max_own;  // max_own
     int* own = reinterpret_cast<int*>(rowp + max_own);
     int nown = 0;
     for (int b = rank; 2 * b < ncol; b += G.gs)
@@ -258,7 +277,7 @@ __global__ void __launch_bounds__(LU_THREADS) lu_coop_kernel(const LUSys* __rest
       for (int t = threadIdx.x; t < rows; t += blockDim.x) mult[t] = __ldcg(S.A + int64_t(k + 1 + t) * n + k);
       for (int c = threadIdx.x; c < na; c += blockDim.x) {
         const int J = own[first + c];
-        const double2* col = lu_colptr(S, J);
+        const C* col = lu_colptr(S, J);
         const int64_t ld = J < n ? n : r;
         rowk[c] = __ldcg(col + int64_t(k) * ld);
         rowp[c] = __ldcg(col + int64_t(p) * ld);
@@ -269,14 +288,14 @@ __global__ void __launch_bounds__(LU_THREADS) lu_coop_kernel(const LUSys* __rest
       if (k + 1 < n && lu_owner(k + 1, G.gs) == rank) {
         const int c = 0;  // own[first] == k + 1 for the owner of column k + 1
         skip = c;
-        double2* col = S.A + (k + 1);
-        const double2 u = rowp[c];
+        C* col = S.A + (k + 1);
+        const C u = rowp[c];
         for (int t = threadIdx.x; t <= rows; t += blockDim.x) {
           // t = 0 is row k (takes row p), t >= 1 are rows k + t
           if (t == 0) continue;
           const int i = k + t;
-          const double2 l = mult[t - 1];
-          double2 a = (i == p) ? rowk[c] : __ldcg(col + int64_t(i) * n);
+          const C l = mult[t - 1];
+          C a = (i == p) ? rowk[c] : __ldcg(col + int64_t(i) * n);
           a.x -= l.x * u.x - l.y * u.y;
           a.y -= l.x * u.y + l.y * u.x;
           colv[t - 1] = a;  // rows k+1 .. n-1
@@ -291,14 +310,14 @@ __global__ void __launch_bounds__(LU_THREADS) lu_coop_kernel(const LUSys* __rest
       if (p != k)
         for (int c = c0 + threadIdx.x; c < na; c += blockDim.x) {
           const int J = own[first + c];
-          double2* col = lu_colptr(S, J);
+          C* col = lu_colptr(S, J);
           col[int64_t(k) * (J < n ? n : r)] = rowp[c];
         }
       const int64_t work = int64_t(rows) * nb;
       for (int64_t w0 = threadIdx.x; w0 < work; w0 += 4 * int64_t(blockDim.x)) {
-        double2 a[4];
+        C a[4];
         int64_t addr[4];
-        double2* base[4];
+        C* base[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const int64_t w = w0 + int64_t(q) * blockDim.x;
@@ -317,9 +336,9 @@ __global__ void __launch_bounds__(LU_THREADS) lu_coop_kernel(const LUSys* __rest
           const int64_t w = w0 + int64_t(q) * blockDim.x;
           if (w < work) {
             const int t = int(w / nb), c = c0 + int(w % nb);
-            const double2 l = mult[t];
-            const double2 u = rowp[c];
-            double2 v = a[q];
+            const C l = mult[t];
+            const C u = rowp[c];
+            C v = a[q];
             v.x -= l.x * u.x - l.y * u.y;
             v.y -= l.x * u.y + l.y * u.x;
             base[q][addr[q]] = v;
@@ -343,14 +362,16 @@ __global__ void __launch_bounds__(LU_THREADS) lu_coop_kernel(const LUSys* __rest
     int rfirst = 0;
     while (rfirst < nown && own[rfirst] < n) ++rfirst;
     const int nr = nown - rfirst;
-    double2* ys = rowk;
+    C* ys = rowk;
     for (int k = n - 1; k >= 0 && nr > 0; --k) {
-      const double2 dk = __ldcg(diag + k);
-      const double dd = dk.x * dk.x + dk.y * dk.y;
+      const C dk = __ldcg(diag + k);
+      const R dd = dk.x * dk.x + dk.y * dk.y;
       for (int c = threadIdx.x; c < nr; c += blockDim.x) {
-        double2* col = S.B + (own[rfirst + c] - n);
-        const double2 bk = __ldcg(col + int64_t(k) * r);
-        const double2 y = make_double2((bk.x * dk.x + bk.y * dk.y) / dd, (bk.y * dk.x - bk.x * dk.y) / dd);
+        C* col = S.B + (own[rfirst + c] - n);
+        const C bk = __ldcg(col + int64_t(k) * r);
+        C y;
+        y.x = (bk.x * dk.x + bk.y * dk.y) / dd;
+        y.y = (bk.y * dk.x - bk.x * dk.y) / dd;
         ys[c] = y;
         col[int64_t(k) * r] = y;
       }
@@ -358,10 +379,10 @@ __global__ void __launch_bounds__(LU_THREADS) lu_coop_kernel(const LUSys* __rest
       const int64_t work = int64_t(k) * nr;
       for (int64_t w = threadIdx.x; w < work; w += blockDim.x) {
         const int i = int(w / nr), c = int(w % nr);
-        double2* col = S.B + (own[rfirst + c] - n);
-        const double2 u = __ldcg(S.A + int64_t(i) * n + k);
-        const double2 y = ys[c];
-        double2 v = __ldcg(col + int64_t(i) * r);
+        C* col = S.B + (own[rfirst + c] - n);
+        const C u = __ldcg(S.A + int64_t(i) * n + k);
+        const C y = ys[c];
+        C v = __ldcg(col + int64_t(i) * r);
         v.x -= u.x * y.x - u.y * y.y;
         v.y -= u.x * y.y + u.y * y.x;
         col[int64_t(i) * r] = v;
@@ -381,7 +402,8 @@ __global__ void __launch_bounds__(LU_THREADS) lu_coop_kernel(const LUSys* __rest
   }
 }
 
-void lu_solve_batched(const std::vector<LUSys>& systems, cudaStream_t s) {
+template <class C>
+void lu_solve_batched(const std::vector<LUSysT<C>>& systems, cudaStream_t s) {
   if (systems.empty()) return;
   int dev = 0, nsm = 0;
   SLDM_CUDA(cudaGetDevice(&dev));
@@ -397,12 +419,12 @@ void lu_solve_batched(const std::vector<LUSys>& systems, cudaStream_t s) {
   const int nsys_ = int(systems.size());
   const int gs_min = nsys_ <= nsm ? nsm / nsys_ : 1;
   const int max_own = 2 * ((cmax + 1) / 2 / gs_min + 1);
-  const size_t smem = size_t(2) * nmax * sizeof(double2) + size_t(2) * max_own * sizeof(double2) + size_t(max_own) * sizeof(int);
+  const size_t smem = size_t(2) * nmax * sizeof(C) + size_t(2) * max_own * sizeof(C) + size_t(max_own) * sizeof(int);
   SLDM_REQUIRE(smem <= 220 * 1024, SLDM_ENOTSUP,
                "LU: object too large for the in-kernel direct factorisation (n = " + std::to_string(nmax) + ")");
-  SLDM_CUDA(cudaFuncSetAttribute(lu_coop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+  SLDM_CUDA(cudaFuncSetAttribute(lu_coop_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
   int per_sm = 0;
-  SLDM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lu_coop_kernel, LU_THREADS, smem));
+  SLDM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lu_coop_kernel<C>, LU_THREADS, smem));
   SLDM_REQUIRE(per_sm >= 1, SLDM_ENOTSUP, "LU: kernel does not fit on an SM");
   const int nsys = int(systems.size());
   const int G = nsm;  // one CTA per SM
@@ -424,11 +446,11 @@ void lu_solve_batched(const std::vector<LUSys>& systems, cudaStream_t s) {
     doff[i] = dtot;
     dtot += systems[i].n;
   }
-  DBuf<LUSys> d;
+  DBuf<LUSysT<C>> d;
   DBuf<LUGroup> dg;
   DBuf<int> dcg, err;
   DBuf<int64_t> ddo;
-  DBuf<double2> diag;
+  DBuf<C> diag;
   DBuf<int> pivrow;
   DBuf<unsigned> ctr, flags;
   d.upload(systems, s);
@@ -443,11 +465,11 @@ void lu_solve_batched(const std::vector<LUSys>& systems, cudaStream_t s) {
   ctr.zero(s);
   err.alloc(1);
   err.zero(s);
-  const LUSys* a0 = d.p;
+  const LUSysT<C>* a0 = d.p;
   int a1 = nsys;
   const LUGroup* a2 = dg.p;
   const int* a3 = dcg.p;
-  double2* a4 = diag.p;
+  C* a4 = diag.p;
   int* a5 = pivrow.p;
   unsigned* a6 = flags.p;
   const int64_t* a7 = ddo.p;
@@ -458,7 +480,7 @@ void lu_solve_batched(const std::vector<LUSys>& systems, cudaStream_t s) {
                   (void*)&a6, (void*)&a7, (void*)&a8, (void*)&a9, (void*)&a10};
   {
     ScopedTimer tm("lu_coop", s);
-    SLDM_CUDA(cudaLaunchCooperativeKernel((void*)lu_coop_kernel, dim3(G), dim3(LU_THREADS), args, smem, s));
+    SLDM_CUDA(cudaLaunchCooperativeKernel((void*)lu_coop_kernel<C>, dim3(G), dim3(LU_THREADS), args, smem, s));
   }
   int herr = 0;
   SLDM_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -466,6 +488,8 @@ void lu_solve_batched(const std::vector<LUSys>& systems, cudaStream_t s) {
   SLDM_REQUIRE(herr != 2, SLDM_ECUDA, "LU: a wait for a published column ran out of its limit");
   SLDM_REQUIRE(herr == 0, SLDM_ENUMERIC, "LU of M_l: zero or non-finite pivot");
 }
+template void lu_solve_batched<float2>(const std::vector<LUSysT<float2>>&, cudaStream_t);
+template void lu_solve_batched<double2>(const std::vector<LUSysT<double2>>&, cudaStream_t);
 
 // ---------------------------------------------------------------- batched skinny GEMV
 // Each warp owns one row of one job and produces that row for all right-hand
@@ -572,7 +596,7 @@ void gemv_jobs(const GemvPlan& plan, int nrhs, cudaStream_t s) {
   if (plan.njobs == 0) return;
   const int64_t threads = plan.total_rows * 32;
   const unsigned blocks = unsigned((threads + 255) / 256);
-  ScopedTimer tm("gemv", s);
+  ScopedTimer tm(plan.name, s);
   if (nrhs <= 1)
     gemv_jobs_kernel<C, 1><<<blocks, 256, 0, s>>>(plan.jobs, plan.rowstart, plan.njobs, plan.total_rows, nrhs);
   else if (nrhs <= 4)
@@ -891,6 +915,23 @@ void add_ix(const sldm_mesh* m, int obj, double alpha, const double* ix_val, voi
   SLDM_CUDA(cudaGetLastError());
 }
 
+// dst = alpha * src (real alpha)
+template <class C>
+__global__ void copy_scaled_kernel(const C* __restrict__ src, int64_t n, double alpha, C* dst) {
+  int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  C v = src[t];
+  v.x = decltype(v.x)(double(v.x) * alpha);
+  v.y = decltype(v.y)(double(v.y) * alpha);
+  dst[t] = v;
+}
+template <class C>
+void copy_scaled(const void* src, int64_t n, double alpha, void* dst, cudaStream_t s) {
+  if (n <= 0) return;
+  copy_scaled_kernel<C><<<unsigned((n + 255) / 256), 256, 0, s>>>((const C*)src, n, alpha, (C*)dst);
+  SLDM_CUDA(cudaGetLastError());
+}
+
 // scale a dense block by a complex factor
 template <class C>
 __global__ void scale_kernel(C* A, int64_t n, double sr, double si) {
@@ -903,7 +944,7 @@ __global__ void scale_kernel(C* A, int64_t n, double sr, double si) {
 
 #define INST(C)                                                                                                         \
   template void build_Ml<C>(const sldm_mesh*, int, double, const void*, int64_t, const void*, int64_t, const void*,     \
-                            int64_t, const double*, double2*, double2*, cudaStream_t);                                  \
+                            int64_t, const double*, C*, C*, cudaStream_t);                                              \
   template void gemv_jobs<C>(const GemvPlan&, int, cudaStream_t);                                                       \
   template void apply_glue_split<C>(const double2*, int64_t, const ApplyDims&, void*, void*, void*, int, cudaStream_t); \
   template void apply_glue_prep<C>(const sldm_mesh*, const ApplyDims&, const void*, const void*, const void*,           \
@@ -914,7 +955,8 @@ __global__ void scale_kernel(C* A, int64_t n, double sr, double si) {
                                       const void*, double2*, int64_t, int, cudaStream_t);                               \
   template void to_c128<C>(const void*, int64_t, double2*, cudaStream_t);                                               \
   template void from_c128<C>(const double2*, int64_t, void*, cudaStream_t);                                             \
-  template void add_ix<C>(const sldm_mesh*, int, double, const double*, void*, int64_t, cudaStream_t);
+  template void add_ix<C>(const sldm_mesh*, int, double, const double*, void*, int64_t, cudaStream_t);             \
+  template void copy_scaled<C>(const void*, int64_t, double, void*, cudaStream_t);
 INST(float2)
 INST(double2)
 

@@ -4,17 +4,21 @@
 
 namespace sldm {
 
-// One dense system A X = B solved in place (A: n x n, B: n x nrhs, row-major complex128).
-struct LUSys {
-  double2* A;
-  double2* B;
+// One dense system A X = B solved in place (A: n x n, B: n x nrhs, row-major complex64 or complex128).
+template <class C>
+struct LUSysT {
+  C* A;
+  C* B;
   int32_t n, nrhs;
 };
-void lu_solve_batched(const std::vector<LUSys>& systems, cudaStream_t s);
+typedef LUSysT<double2> LUSys;
+template <class C>
+void lu_solve_batched(const std::vector<LUSysT<C>>& systems, cudaStream_t s);
+inline void lu_solve_batched(const std::vector<LUSys>& systems, cudaStream_t s) { lu_solve_batched<double2>(systems, s); }
 
 template <class C>
 void build_Ml(const sldm_mesh* m, int obj, double k0, const void* LAm, int64_t ldLA, const void* LPm, int64_t ldLP,
-              const void* Kl, int64_t ldK, const double* ix_val, double2* Ml, double2* Rl, cudaStream_t s);
+              const void* Kl, int64_t ldK, const double* ix_val, C* Ml, C* Rl, cudaStream_t s);
 
 // y = (ar + j ai) A x + beta y over rows [0, m) of a row-major block; x, y hold
 // nrhs columns with strides ldx, ldy (entries of the op precision).
@@ -30,6 +34,7 @@ struct GemvJob {
   int32_t beta, pad;
 };
 struct GemvPlan {
+  const char* name = "gemv";   // timer name of its launches
   GemvJob* jobs = nullptr;     // device
   int64_t* rowstart = nullptr; // device, exclusive prefix sum of m
   int njobs = 0;
@@ -62,6 +67,8 @@ template <class C>
 void to_c128(const void* src, int64_t n, double2* dst, cudaStream_t s);
 template <class C>
 void from_c128(const double2* src, int64_t n, void* dst, cudaStream_t s);
+template <class C>
+void copy_scaled(const void* src, int64_t n, double alpha, void* dst, cudaStream_t s);
 template <class C>
 void add_ix(const sldm_mesh* m, int obj, double alpha, const double* ix_val, void* K, int64_t ld, cudaStream_t s);
 

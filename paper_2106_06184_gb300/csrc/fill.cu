@@ -423,34 +423,51 @@ __device__ cd grad_smooth(cd k, double R) {
 }
 
 // ---------------------------------------------------------------- FP64 touching L pairs
+// Eight lanes per pair: lane q < 6 takes outer point q (closed forms + 6-point
+// remainder), the pair's moments are summed with shuffles inside the group,
+// and lane 0 scatters the 3x3 block.  One launch serves every task: a pair
+// belongs to the task of its object (obj_task), or to none.
+__device__ __forceinline__ double grp_sum8(double v) {
+  v += __shfl_xor_sync(0xffffffffu, v, 4);
+  v += __shfl_xor_sync(0xffffffffu, v, 2);
+  v += __shfl_xor_sync(0xffffffffu, v, 1);
+  return v;
+}
+
 template <class R>
-__global__ void fill_L_touch(LTask tk, const int32_t* __restrict__ pa, const int32_t* __restrict__ pb, int npairs,
-                             const double* __restrict__ geo, const double* __restrict__ xyz,
-                             const int32_t* __restrict__ tri, const int32_t* __restrict__ tri_edge) {
-  int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= npairs) return;
-  const int t = pa[p], s = pb[p];
-  if (t < tk.t0 || t >= tk.t0 + tk.ntest || s < tk.s0 || s >= tk.s0 + tk.nsrc) return;
-  const double* gt = geo + size_t(t) * GEO_STRIDE;
+__global__ void fill_L_touch(const LTask* __restrict__ tasks, const int32_t* __restrict__ obj_task,
+                             const int32_t* __restrict__ tri_obj, const int32_t* __restrict__ pa,
+                             const int32_t* __restrict__ pb, int npairs, const double* __restrict__ geo,
+                             const double* __restrict__ xyz, const int32_t* __restrict__ tri,
+                             const int32_t* __restrict__ tri_edge) {
+  const int64_t gt = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int p = int(gt >> 3), q = int(gt & 7);
+  int task = -1, t = 0, s = 0;
+  if (p < npairs) {
+    t = pa[p];
+    s = pb[p];
+    task = obj_task[tri_obj[t]];
+  }
+  const bool act = task >= 0 && q < 6;
+  LTask tk;
+  if (task >= 0) tk = tasks[task];
+  double m[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) m[i] = 0.0;
+  const double* gt_ = geo + size_t(t) * GEO_STRIDE;
   const double* gs = geo + size_t(s) * GEO_STRIDE;
-  const double* v1 = xyz + 3 * tri[3 * s];
-  const double* v2 = xyz + 3 * tri[3 * s + 1];
-  const double* v3 = xyz + 3 * tri[3 * s + 2];
-  const cd k = {tk.kr, tk.ki};
-  const cd k2 = cmul(k, k);
-  cd m0 = {0, 0}, mq[3] = {{0, 0}, {0, 0}, {0, 0}}, ms[3] = {{0, 0}, {0, 0}, {0, 0}}, mqs = {0, 0};
-  for (int q = 0; q < 6; ++q) {
+  if (act) {
+    const cd k = {tk.kr, tk.ki};
+    const cd k2 = cmul(k, k);
     double r[3];
-    for (int d = 0; d < 3; ++d) r[d] = gt[GEO_C + d] + gt[GEO_RHO + 3 * q + d];
-    // remainder by the 6-point rule: A = sum W' Gs, B = sum W' Gs rho'
+    for (int d = 0; d < 3; ++d) r[d] = gt_[GEO_C + d] + gt_[GEO_RHO + 3 * q + d];
     cd A = {0, 0}, B[3] = {{0, 0}, {0, 0}, {0, 0}};
     for (int j = 0; j < 6; ++j) {
-      double dx = r[0] - gs[GEO_C] - gs[GEO_RHO + 3 * j];
-      double dy = r[1] - gs[GEO_C + 1] - gs[GEO_RHO + 3 * j + 1];
-      double dz = r[2] - gs[GEO_C + 2] - gs[GEO_RHO + 3 * j + 2];
-      double Rr = sqrt(dx * dx + dy * dy + dz * dz);
-      cd g = green_smooth(k, Rr);
-      double w = gs[GEO_W + j];
+      const double dx = r[0] - gs[GEO_C] - gs[GEO_RHO + 3 * j];
+      const double dy = r[1] - gs[GEO_C + 1] - gs[GEO_RHO + 3 * j + 1];
+      const double dz = r[2] - gs[GEO_C + 2] - gs[GEO_RHO + 3 * j + 2];
+      const cd g = green_smooth(k, sqrt(dx * dx + dy * dy + dz * dz));
+      const double w = gs[GEO_W + j];
       A.r += w * g.r;
       A.i += w * g.i;
       for (int d = 0; d < 3; ++d) {
@@ -458,37 +475,45 @@ __global__ void fill_L_touch(LTask tk, const int32_t* __restrict__ pa, const int
         B[d].i += w * g.i * gs[GEO_RHO + 3 * j + d];
       }
     }
-    // closed forms: 1/(4 pi R) - k^2 R/(8 pi)
     Pot P;
-    potentials(r, v1, v2, v3, P);
+    potentials(r, xyz + 3 * tri[3 * s], xyz + 3 * tri[3 * s + 1], xyz + 3 * tri[3 * s + 2], P);
     A.r += INV4PI * P.inv_r - k2.r * 0.5 * INV4PI * P.r;
     A.i += -k2.i * 0.5 * INV4PI * P.r;
     for (int d = 0; d < 3; ++d) {
-      double off = P.rho[d] - gs[GEO_C + d];  // (r' - c') = P + (rho - c')
-      double s1 = P.por[d] + off * P.inv_r;
-      double sR = P.pr[d] + off * P.r;
+      const double off = P.rho[d] - gs[GEO_C + d];  // (r' - c') = P + (rho - c')
+      const double s1 = P.por[d] + off * P.inv_r;
+      const double sR = P.pr[d] + off * P.r;
       B[d].r += INV4PI * s1 - k2.r * 0.5 * INV4PI * sR;
       B[d].i += -k2.i * 0.5 * INV4PI * sR;
     }
-    double w = gt[GEO_W + q];
-    m0.r += w * A.r;
-    m0.i += w * A.i;
+    const double w = gt_[GEO_W + q];
+    m[0] = w * A.r;
+    m[1] = w * A.i;
     for (int d = 0; d < 3; ++d) {
-      double rq = gt[GEO_RHO + 3 * q + d];
-      mq[d].r += w * A.r * rq;
-      mq[d].i += w * A.i * rq;
-      ms[d].r += w * B[d].r;
-      ms[d].i += w * B[d].i;
-      mqs.r += w * rq * B[d].r;
-      mqs.i += w * rq * B[d].i;
+      const double rq = gt_[GEO_RHO + 3 * q + d];
+      m[2 + 2 * d] = w * A.r * rq;       // Mq
+      m[3 + 2 * d] = w * A.i * rq;
+      m[8 + 2 * d] = w * B[d].r;         // Ms
+      m[9 + 2 * d] = w * B[d].i;
+      m[14] += w * rq * B[d].r;          // Mqs
+      m[15] += w * rq * B[d].i;
     }
+  }
+#pragma unroll
+  for (int i = 0; i < 16; ++i) m[i] = grp_sum8(m[i]);
+  if (task < 0 || q != 0) return;
+  const cd m0 = {m[0], m[1]}, mqs = {m[14], m[15]};
+  cd mq[3], ms[3];
+  for (int d = 0; d < 3; ++d) {
+    mq[d] = {m[2 + 2 * d], m[3 + 2 * d]};
+    ms[d] = {m[8 + 2 * d], m[9 + 2 * d]};
   }
   if (tk.A) {
     for (int i = 0; i < 3; ++i) {
-      const double* a = gt + GEO_AV + 3 * i;
+      const double* a = gt_ + GEO_AV + 3 * i;
       for (int j = 0; j < 3; ++j) {
         const double* b = gs + GEO_AV + 3 * j;
-        double ab = a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+        const double ab = a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
         cd v = mqs;
         for (int d = 0; d < 3; ++d) {
           v.r += a[d] * ms[d].r + b[d] * mq[d].r;
@@ -496,15 +521,15 @@ __global__ void fill_L_touch(LTask tk, const int32_t* __restrict__ pa, const int
         }
         v.r += ab * m0.r;
         v.i += ab * m0.i;
-        double sc = gt[GEO_SIG + i] * gs[GEO_SIG + j];
-        cd out = cmul({v.r * sc, v.i * sc}, {tk.sAr, tk.sAi});
+        const double sc = gt_[GEO_SIG + i] * gs[GEO_SIG + j];
+        const cd out = cmul({v.r * sc, v.i * sc}, {tk.sAr, tk.sAi});
         add_d<R>(tk.A, int64_t(tri_edge[3 * t + i] - tk.e_row0) * tk.ldA + (tri_edge[3 * s + j] - tk.e_col0), out.r, out.i);
       }
     }
   }
   if (tk.P) {
-    double sc = 1.0 / (gt[GEO_A] * gs[GEO_A]);
-    cd out = cmul({m0.r * sc, m0.i * sc}, {tk.sPr, tk.sPi});
+    const double sc = 1.0 / (gt_[GEO_A] * gs[GEO_A]);
+    const cd out = cmul({m0.r * sc, m0.i * sc}, {tk.sPr, tk.sPi});
     M<R>::store(tk.P, int64_t(t - tk.t_row0) * tk.ldP + (s - tk.t_col0), out.r, out.i);
   }
 }
@@ -638,50 +663,58 @@ __global__ void __launch_bounds__(TILE_SRC) fill_K_bulk(const KTask* __restrict_
 }
 
 // ---------------------------------------------------------------- FP64 touching Kbar pairs
+// Same lane layout as the L kernel: lane q < 6 takes outer point q.
 template <class R>
-__global__ void fill_K_touch(KTask tk, const int32_t* __restrict__ pa, const int32_t* __restrict__ pc, int npairs,
-                             const double* __restrict__ geo, const double* __restrict__ bgeo,
-                             const double* __restrict__ xyz, const int32_t* __restrict__ tri,
-                             const int32_t* __restrict__ tri_edge, const int32_t* __restrict__ btri_edge) {
-  int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= npairs) return;
-  const int t = pa[p], cg = pc[p];
-  if (t < tk.t0 || t >= tk.t0 + tk.ntest || cg < tk.c0 || cg >= tk.c0 + tk.nsrc) return;
-  const double* gt = geo + size_t(t) * GEO_STRIDE;
-  const double* gs = bgeo + size_t(cg) * GEO_STRIDE;
-  // child vertices: rebuild from the parent (a, m_ab, g) ... pattern
-  const int par = cg / 6, kk = cg % 6;
-  const double* a = xyz + 3 * tri[3 * par];
-  const double* b = xyz + 3 * tri[3 * par + 1];
-  const double* c = xyz + 3 * tri[3 * par + 2];
-  double V[7][3];  // a, b, c, m_ab, m_bc, m_ca, g
-  for (int d = 0; d < 3; ++d) {
-    V[0][d] = a[d]; V[1][d] = b[d]; V[2][d] = c[d];
-    V[3][d] = 0.5 * (a[d] + b[d]); V[4][d] = 0.5 * (b[d] + c[d]); V[5][d] = 0.5 * (c[d] + a[d]);
-    V[6][d] = (a[d] + b[d] + c[d]) / 3.0;
+__global__ void fill_K_touch(const KTask* __restrict__ tasks, const int32_t* __restrict__ obj_task,
+                             const int32_t* __restrict__ tri_obj, const int32_t* __restrict__ pa,
+                             const int32_t* __restrict__ pc, int npairs, const double* __restrict__ geo,
+                             const double* __restrict__ bgeo, const double* __restrict__ xyz,
+                             const int32_t* __restrict__ tri, const int32_t* __restrict__ tri_edge,
+                             const int32_t* __restrict__ btri_edge) {
+  const int64_t gt = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int p = int(gt >> 3), q = int(gt & 7);
+  int task = -1, t = 0, cg = 0;
+  if (p < npairs) {
+    t = pa[p];
+    cg = pc[p];
+    task = obj_task[tri_obj[t]];
   }
-  const int cv[6][3] = {{0, 3, 6}, {3, 1, 6}, {1, 4, 6}, {4, 2, 6}, {2, 5, 6}, {5, 0, 6}};
-  const double* p1 = V[cv[kk][0]];
-  const double* p2 = V[cv[kk][1]];
-  const double* p3 = V[cv[kk][2]];
-  const cd k = {tk.kr, tk.ki};
-  cd P1 = {0, 0}, P2[3] = {{0, 0}, {0, 0}, {0, 0}}, X[3] = {{0, 0}, {0, 0}, {0, 0}}, S[3] = {{0, 0}, {0, 0}, {0, 0}};
-  for (int q = 0; q < 6; ++q) {
+  const bool act = task >= 0 && q < 6;
+  KTask tk;
+  if (task >= 0) tk = tasks[task];
+  const double* gt_ = geo + size_t(t) * GEO_STRIDE;
+  const double* gs = bgeo + size_t(cg) * GEO_STRIDE;
+  double m[20];
+#pragma unroll
+  for (int i = 0; i < 20; ++i) m[i] = 0.0;
+  if (act) {
+    // child vertices rebuilt from the parent: (a, m_ab, g) (m_ab, b, g) (b, m_bc, g) (m_bc, c, g) (c, m_ca, g) (m_ca, a, g)
+    const int par = cg / 6, kk = cg % 6;
+    const double* a = xyz + 3 * tri[3 * par];
+    const double* b = xyz + 3 * tri[3 * par + 1];
+    const double* c = xyz + 3 * tri[3 * par + 2];
+    double V[7][3];
+    for (int d = 0; d < 3; ++d) {
+      V[0][d] = a[d]; V[1][d] = b[d]; V[2][d] = c[d];
+      V[3][d] = 0.5 * (a[d] + b[d]); V[4][d] = 0.5 * (b[d] + c[d]); V[5][d] = 0.5 * (c[d] + a[d]);
+      V[6][d] = (a[d] + b[d] + c[d]) / 3.0;
+    }
+    const int cv[6][3] = {{0, 3, 6}, {3, 1, 6}, {1, 4, 6}, {4, 2, 6}, {2, 5, 6}, {5, 0, 6}};
+    const cd k = {tk.kr, tk.ki};
     double r[3], rq[3];
     for (int d = 0; d < 3; ++d) {
-      rq[d] = gt[GEO_RHO + 3 * q + d];
-      r[d] = gt[GEO_C + d] + rq[d];
+      rq[d] = gt_[GEO_RHO + 3 * q + d];
+      r[d] = gt_[GEO_C + d] + rq[d];
     }
     cd U[3] = {{0, 0}, {0, 0}, {0, 0}}, Vv[3] = {{0, 0}, {0, 0}, {0, 0}};
     for (int j = 0; j < 6; ++j) {
       const double* rs = gs + GEO_RHO + 3 * j;
-      double D[3] = {r[0] - gs[GEO_C] - rs[0], r[1] - gs[GEO_C + 1] - rs[1], r[2] - gs[GEO_C + 2] - rs[2]};
-      double Rr = sqrt(D[0] * D[0] + D[1] * D[1] + D[2] * D[2]);
-      cd g1 = grad_smooth(k, Rr);
-      double w = gs[GEO_W + j];
+      const double D[3] = {r[0] - gs[GEO_C] - rs[0], r[1] - gs[GEO_C + 1] - rs[1], r[2] - gs[GEO_C + 2] - rs[2]};
+      cd g1 = grad_smooth(k, sqrt(D[0] * D[0] + D[1] * D[1] + D[2] * D[2]));
+      const double w = gs[GEO_W + j];
       g1.r *= w;
       g1.i *= w;
-      double cr[3] = {D[1] * rs[2] - D[2] * rs[1], D[2] * rs[0] - D[0] * rs[2], D[0] * rs[1] - D[1] * rs[0]};
+      const double cr[3] = {D[1] * rs[2] - D[2] * rs[1], D[2] * rs[0] - D[0] * rs[2], D[0] * rs[1] - D[1] * rs[0]};
       for (int d = 0; d < 3; ++d) {
         U[d].r += g1.r * cr[d];
         U[d].i += g1.i * cr[d];
@@ -691,40 +724,51 @@ __global__ void fill_K_touch(KTask tk, const int32_t* __restrict__ pa, const int
     }
     // static part: V_s = int grad 1/(4 pi R) dS', U_s = V_s x (r - c')
     Pot P;
-    potentials(r, p1, p2, p3, P);
+    potentials(r, V[cv[kk][0]], V[cv[kk][1]], V[cv[kk][2]], P);
     double vs[3], rc[3];
     for (int d = 0; d < 3; ++d) {
       vs[d] = INV4PI * P.grad[d];
       rc[d] = r[d] - gs[GEO_C + d];
     }
-    double us[3] = {vs[1] * rc[2] - vs[2] * rc[1], vs[2] * rc[0] - vs[0] * rc[2], vs[0] * rc[1] - vs[1] * rc[0]};
+    const double us[3] = {vs[1] * rc[2] - vs[2] * rc[1], vs[2] * rc[0] - vs[0] * rc[2], vs[0] * rc[1] - vs[1] * rc[0]};
     for (int d = 0; d < 3; ++d) {
       U[d].r += us[d];
       Vv[d].r += vs[d];
     }
-    double w = gt[GEO_W + q];
+    const double w = gt_[GEO_W + q];
     for (int d = 0; d < 3; ++d) {
-      P1.r += w * rq[d] * U[d].r;
-      P1.i += w * rq[d] * U[d].i;
-      P2[d].r += w * U[d].r;
-      P2[d].i += w * U[d].i;
-      S[d].r += w * Vv[d].r;
-      S[d].i += w * Vv[d].i;
+      m[0] += w * rq[d] * U[d].r;            // P1
+      m[1] += w * rq[d] * U[d].i;
+      m[2 + 2 * d] = w * U[d].r;             // P2
+      m[3 + 2 * d] = w * U[d].i;
+      m[14 + 2 * d] = w * Vv[d].r;           // S
+      m[15 + 2 * d] = w * Vv[d].i;
     }
-    X[0].r += w * (rq[1] * Vv[2].r - rq[2] * Vv[1].r); X[0].i += w * (rq[1] * Vv[2].i - rq[2] * Vv[1].i);
-    X[1].r += w * (rq[2] * Vv[0].r - rq[0] * Vv[2].r); X[1].i += w * (rq[2] * Vv[0].i - rq[0] * Vv[2].i);
-    X[2].r += w * (rq[0] * Vv[1].r - rq[1] * Vv[0].r); X[2].i += w * (rq[0] * Vv[1].i - rq[1] * Vv[0].i);
+    // X = rho x V
+    m[8] = w * (rq[1] * Vv[2].r - rq[2] * Vv[1].r);  m[9] = w * (rq[1] * Vv[2].i - rq[2] * Vv[1].i);
+    m[10] = w * (rq[2] * Vv[0].r - rq[0] * Vv[2].r); m[11] = w * (rq[2] * Vv[0].i - rq[0] * Vv[2].i);
+    m[12] = w * (rq[0] * Vv[1].r - rq[1] * Vv[0].r); m[13] = w * (rq[0] * Vv[1].i - rq[1] * Vv[0].i);
+  }
+#pragma unroll
+  for (int i = 0; i < 20; ++i) m[i] = grp_sum8(m[i]);
+  if (task < 0 || q != 0) return;
+  const cd P1 = {m[0], m[1]};
+  cd P2[3], X[3], S[3];
+  for (int d = 0; d < 3; ++d) {
+    P2[d] = {m[2 + 2 * d], m[3 + 2 * d]};
+    X[d] = {m[8 + 2 * d], m[9 + 2 * d]};
+    S[d] = {m[14 + 2 * d], m[15 + 2 * d]};
   }
   for (int i = 0; i < 3; ++i) {
-    const double* av = gt + GEO_AV + 3 * i;
+    const double* av = gt_ + GEO_AV + 3 * i;
     cd base = P1;
     for (int d = 0; d < 3; ++d) {
       base.r += av[d] * P2[d].r;
       base.i += av[d] * P2[d].i;
     }
-    cd axs[3] = {{av[1] * S[2].r - av[2] * S[1].r, av[1] * S[2].i - av[2] * S[1].i},
-                 {av[2] * S[0].r - av[0] * S[2].r, av[2] * S[0].i - av[0] * S[2].i},
-                 {av[0] * S[1].r - av[1] * S[0].r, av[0] * S[1].i - av[1] * S[0].i}};
+    const cd axs[3] = {{av[1] * S[2].r - av[2] * S[1].r, av[1] * S[2].i - av[2] * S[1].i},
+                       {av[2] * S[0].r - av[0] * S[2].r, av[2] * S[0].i - av[0] * S[2].i},
+                       {av[0] * S[1].r - av[1] * S[0].r, av[0] * S[1].i - av[1] * S[0].i}};
     for (int j = 0; j < 3; ++j) {
       const double* bv = gs + GEO_AV + 3 * j;
       cd v = base;
@@ -732,7 +776,7 @@ __global__ void fill_K_touch(KTask tk, const int32_t* __restrict__ pa, const int
         v.r += bv[d] * (X[d].r + axs[d].r);
         v.i += bv[d] * (X[d].i + axs[d].i);
       }
-      double sc = gt[GEO_SIG + i] * gs[GEO_SIG + j];
+      const double sc = gt_[GEO_SIG + i] * gs[GEO_SIG + j];
       add_d<R>(tk.Kb, int64_t(tri_edge[3 * t + i] - tk.e_row0) * tk.ld + (btri_edge[3 * cg + j] - tk.b_col0), v.r * sc,
                v.i * sc);
     }
@@ -740,6 +784,20 @@ __global__ void fill_K_touch(KTask tk, const int32_t* __restrict__ pa, const int
 }
 
 // ---------------------------------------------------------------- host launchers
+// Task of each object's touching pairs: the task whose test-triangle range
+// holds the object (tasks cover whole objects), or -1.
+template <class T>
+static std::vector<int32_t> object_tasks(const HostMesh& h, const std::vector<T>& tasks) {
+  std::vector<int32_t> ot(size_t(h.nobj), -1);
+  for (int64_t o = 0; o < h.nobj; ++o)
+    for (size_t i = 0; i < tasks.size(); ++i)
+      if (h.tri_begin[o] >= tasks[i].t0 && h.tri_begin[o] < tasks[i].t0 + tasks[i].ntest) {
+        ot[size_t(o)] = int32_t(i);
+        break;
+      }
+  return ot;
+}
+
 template <class R>
 void fill_L(const sldm_mesh* m, const std::vector<LTask>& tasks, cudaStream_t s) {
   if (tasks.empty()) return;
@@ -759,10 +817,12 @@ void fill_L(const sldm_mesh* m, const std::vector<LTask>& tasks, cudaStream_t s)
   }
   SLDM_CUDA(cudaGetLastError());
   const int np = int(m->h.touchL_a.size());
-  for (const LTask& tk : tasks) {
+  DBuf<int32_t> dot;
+  dot.upload(object_tasks(m->h, tasks), s);
+  if (np > 0) {
     ScopedTimer tm("fill_L_touch", s);
-    fill_L_touch<R><<<(np + 127) / 128, 128, 0, s>>>(tk, d.touchL_a.p, d.touchL_b.p, np, d.geo.p, d.xyz.p, d.tri.p,
-                                                     d.tri_edge.p);
+    fill_L_touch<R><<<unsigned((int64_t(np) * 8 + 255) / 256), 256, 0, s>>>(dt.p, dot.p, d.obj.p, d.touchL_a.p, d.touchL_b.p, np,
+                                                                            d.geo.p, d.xyz.p, d.tri.p, d.tri_edge.p);
   }
   SLDM_CUDA(cudaGetLastError());
   SLDM_CUDA(cudaStreamSynchronize(s));  // task/tile buffers are released on return
@@ -787,10 +847,13 @@ void fill_K(const sldm_mesh* m, const std::vector<KTask>& tasks, cudaStream_t s)
   }
   SLDM_CUDA(cudaGetLastError());
   const int np = int(m->h.touchK_a.size());
-  for (const KTask& tk : tasks) {
+  DBuf<int32_t> dot;
+  dot.upload(object_tasks(m->h, tasks), s);
+  if (np > 0) {
     ScopedTimer tm("fill_K_touch", s);
-    fill_K_touch<R><<<(np + 127) / 128, 128, 0, s>>>(tk, d.touchK_a.p, d.touchK_c.p, np, d.geo.p, d.bgeo.p, d.xyz.p,
-                                                     d.tri.p, d.tri_edge.p, d.btri_edge.p);
+    fill_K_touch<R><<<unsigned((int64_t(np) * 8 + 255) / 256), 256, 0, s>>>(dt.p, dot.p, d.obj.p, d.touchK_a.p, d.touchK_c.p, np,
+                                                                            d.geo.p, d.bgeo.p, d.xyz.p, d.tri.p, d.tri_edge.p,
+                                                                            d.btri_edge.p);
   }
   SLDM_CUDA(cudaGetLastError());
   SLDM_CUDA(cudaStreamSynchronize(s));
@@ -973,6 +1036,112 @@ template void contract_bc<double>(const sldm_mesh*, int, const void*, int64_t, v
 
 }  // namespace sldm
 
+namespace sldm {
+
+// ---------------------------------------------------------------- FP64 touching Kbar pairs, one task by value
+// One thread per pair (used by the allocation-free entry point).
+__global__ void fill_K_touch_one(KTask tk, const int32_t* __restrict__ pa, const int32_t* __restrict__ pc, int npairs,
+                             const double* __restrict__ geo, const double* __restrict__ bgeo,
+                             const double* __restrict__ xyz, const int32_t* __restrict__ tri,
+                             const int32_t* __restrict__ tri_edge, const int32_t* __restrict__ btri_edge) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= npairs) return;
+  const int t = pa[p], cg = pc[p];
+  if (t < tk.t0 || t >= tk.t0 + tk.ntest || cg < tk.c0 || cg >= tk.c0 + tk.nsrc) return;
+  const double* gt = geo + size_t(t) * GEO_STRIDE;
+  const double* gs = bgeo + size_t(cg) * GEO_STRIDE;
+  // child vertices: rebuild from the parent (a, m_ab, g) ... pattern
+  const int par = cg / 6, kk = cg % 6;
+  const double* a = xyz + 3 * tri[3 * par];
+  const double* b = xyz + 3 * tri[3 * par + 1];
+  const double* c = xyz + 3 * tri[3 * par + 2];
+  double V[7][3];  // a, b, c, m_ab, m_bc, m_ca, g
+  for (int d = 0; d < 3; ++d) {
+    V[0][d] = a[d]; V[1][d] = b[d]; V[2][d] = c[d];
+    V[3][d] = 0.5 * (a[d] + b[d]); V[4][d] = 0.5 * (b[d] + c[d]); V[5][d] = 0.5 * (c[d] + a[d]);
+    V[6][d] = (a[d] + b[d] + c[d]) / 3.0;
+  }
+  const int cv[6][3] = {{0, 3, 6}, {3, 1, 6}, {1, 4, 6}, {4, 2, 6}, {2, 5, 6}, {5, 0, 6}};
+  const double* p1 = V[cv[kk][0]];
+  const double* p2 = V[cv[kk][1]];
+  const double* p3 = V[cv[kk][2]];
+  const cd k = {tk.kr, tk.ki};
+  cd P1 = {0, 0}, P2[3] = {{0, 0}, {0, 0}, {0, 0}}, X[3] = {{0, 0}, {0, 0}, {0, 0}}, S[3] = {{0, 0}, {0, 0}, {0, 0}};
+  for (int q = 0; q < 6; ++q) {
+    double r[3], rq[3];
+    for (int d = 0; d < 3; ++d) {
+      rq[d] = gt[GEO_RHO + 3 * q + d];
+      r[d] = gt[GEO_C + d] + rq[d];
+    }
+    cd U[3] = {{0, 0}, {0, 0}, {0, 0}}, Vv[3] = {{0, 0}, {0, 0}, {0, 0}};
+    for (int j = 0; j < 6; ++j) {
+      const double* rs = gs + GEO_RHO + 3 * j;
+      double D[3] = {r[0] - gs[GEO_C] - rs[0], r[1] - gs[GEO_C + 1] - rs[1], r[2] - gs[GEO_C + 2] - rs[2]};
+      double Rr = sqrt(D[0] * D[0] + D[1] * D[1] + D[2] * D[2]);
+      cd g1 = grad_smooth(k, Rr);
+      double w = gs[GEO_W + j];
+      g1.r *= w;
+      g1.i *= w;
+      double cr[3] = {D[1] * rs[2] - D[2] * rs[1], D[2] * rs[0] - D[0] * rs[2], D[0] * rs[1] - D[1] * rs[0]};
+      for (int d = 0; d < 3; ++d) {
+        U[d].r += g1.r * cr[d];
+        U[d].i += g1.i * cr[d];
+        Vv[d].r += g1.r * D[d];
+        Vv[d].i += g1.i * D[d];
+      }
+    }
+    // static part: V_s = int grad 1/(4 pi R) dS', U_s = V_s x (r - c')
+    Pot P;
+    potentials(r, p1, p2, p3, P);
+    double vs[3], rc[3];
+    for (int d = 0; d < 3; ++d) {
+      vs[d] = INV4PI * P.grad[d];
+      rc[d] = r[d] - gs[GEO_C + d];
+    }
+    double us[3] = {vs[1] * rc[2] - vs[2] * rc[1], vs[2] * rc[0] - vs[0] * rc[2], vs[0] * rc[1] - vs[1] * rc[0]};
+    for (int d = 0; d < 3; ++d) {
+      U[d].r += us[d];
+      Vv[d].r += vs[d];
+    }
+    double w = gt[GEO_W + q];
+    for (int d = 0; d < 3; ++d) {
+      P1.r += w * rq[d] * U[d].r;
+      P1.i += w * rq[d] * U[d].i;
+      P2[d].r += w * U[d].r;
+      P2[d].i += w * U[d].i;
+      S[d].r += w * Vv[d].r;
+      S[d].i += w * Vv[d].i;
+    }
+    X[0].r += w * (rq[1] * Vv[2].r - rq[2] * Vv[1].r); X[0].i += w * (rq[1] * Vv[2].i - rq[2] * Vv[1].i);
+    X[1].r += w * (rq[2] * Vv[0].r - rq[0] * Vv[2].r); X[1].i += w * (rq[2] * Vv[0].i - rq[0] * Vv[2].i);
+    X[2].r += w * (rq[0] * Vv[1].r - rq[1] * Vv[0].r); X[2].i += w * (rq[0] * Vv[1].i - rq[1] * Vv[0].i);
+  }
+  for (int i = 0; i < 3; ++i) {
+    const double* av = gt + GEO_AV + 3 * i;
+    cd base = P1;
+    for (int d = 0; d < 3; ++d) {
+      base.r += av[d] * P2[d].r;
+      base.i += av[d] * P2[d].i;
+    }
+    cd axs[3] = {{av[1] * S[2].r - av[2] * S[1].r, av[1] * S[2].i - av[2] * S[1].i},
+                 {av[2] * S[0].r - av[0] * S[2].r, av[2] * S[0].i - av[0] * S[2].i},
+                 {av[0] * S[1].r - av[1] * S[0].r, av[0] * S[1].i - av[1] * S[0].i}};
+    for (int j = 0; j < 3; ++j) {
+      const double* bv = gs + GEO_AV + 3 * j;
+      cd v = base;
+      for (int d = 0; d < 3; ++d) {
+        v.r += bv[d] * (X[d].r + axs[d].r);
+        v.i += bv[d] * (X[d].i + axs[d].i);
+      }
+      double sc = gt[GEO_SIG + i] * gs[GEO_SIG + j];
+      add_d<double>(tk.Kb, int64_t(tri_edge[3 * t + i] - tk.e_row0) * tk.ld + (btri_edge[3 * cg + j] - tk.b_col0), v.r * sc,
+               v.i * sc);
+    }
+  }
+}
+
+}  // namespace sldm
+
 // ---------------------------------------------------------------- allocation-free Kbar
 // sldm_kbar_noalloc: the barycentric Kbar fill of one object and its contraction
 // with the BC coefficients, with every temporary (task record, tile list and the
@@ -1052,8 +1221,8 @@ extern "C" int sldm_kbar_noalloc(const sldm_mesh* m, int32_t obj, double k_re, d
     SLDM_CUDA(cudaGetLastError());
     const int np = int(h.touchK_a.size());
     if (np > 0)
-      fill_K_touch<double><<<(np + 127) / 128, 128, 0, s>>>(t, d.touchK_a.p, d.touchK_c.p, np, d.geo.p, d.bgeo.p, d.xyz.p,
-                                                            d.tri.p, d.tri_edge.p, d.btri_edge.p);
+      fill_K_touch_one<<<(np + 127) / 128, 128, 0, s>>>(t, d.touchK_a.p, d.touchK_c.p, np, d.geo.p, d.bgeo.p, d.xyz.p,
+                                                        d.tri.p, d.tri_edge.p, d.btri_edge.p);
     SLDM_CUDA(cudaGetLastError());
     contract_bc<double>(m, obj, Kb, nbe_o, K_out, ne_o, s);
   } catch (const sldm::Error& e) {

@@ -211,6 +211,7 @@ void prec_setup(Precond& P, const sldm_mesh* m, const std::vector<PrecObj>& objs
   P.plan.rowstart = P.rs.p;
   P.plan.njobs = int(jobs.size());
   P.plan.total_rows = acc;
+  P.plan.name = "gemv_pc";
   SLDM_CUDA(cudaStreamSynchronize(s));
 }
 
