@@ -62,15 +62,31 @@ class Assembled:
     Z: np.ndarray = None
 
 
-def assemble(mesh, materials, background: Material, freq: float, build_Z: bool = True) -> Assembled:
+def assemble(mesh, materials, background, freq: float, build_Z: bool = True, layer: int = None,
+             tables=None) -> Assembled:
+    """background: a Material (homogeneous) or an oracle.layered.Stack with every object in
+    ``layer``.  In a stack, the equivalent configuration (M_l, Eq. AEFIEeqvdis) uses the
+    homogeneous kernels of layer l and L^A_m, L^phi_m add the reflected part of the
+    multilayer kernel (images + tabulated remainder, see oracle.layered)."""
     omega = 2 * np.pi * freq
     k0 = omega / C0
+    layered = not isinstance(background, Material)
+    if layered:
+        from . import layered as LY
+        stack = background
+        background = Material(stack.layers[layer][0], stack.layers[layer][1], stack.layers[layer][2])
     kb = wavenumber(background, k0)
     eb = eps_c(background, omega)
     all_tris = np.arange(mesh.nt)
     LA_b, LP_b = fill_L(mesh, kb, all_tris)
-    LAm = background.mu_r * LA_b
-    LPm = LP_b / eb
+    LA_hom = background.mu_r * LA_b
+    LP_hom = LP_b / eb
+    LAm, LPm = LA_hom, LP_hom
+    if layered:
+        if tables is None:
+            tables = default_tables(mesh, stack, layer, omega)
+        LA_r, LP_r = LY.fill_reflected(mesh, stack, layer, omega, tables, all_tris)
+        LAm, LPm = LA_hom + LA_r, LP_hom + LP_r
     Ix = fill_Ix(mesh)
     D, B, F = mesh.D(), mesh.B(), mesh.F()
     out = Assembled(mesh=mesh, k0=k0, LAm=LAm, LPm=LPm, Ix=Ix)
@@ -86,9 +102,10 @@ def assemble(mesh, materials, background: Material, freq: float, build_Z: bool =
         Do = D[t0:t1, e0:e1]
         Bo = B[t0:t1, t0 - o:t1 - o - 1]
         Fo = F[t0 - o:t1 - o - 1, t0:t1]
-        # equivalent configuration: the object replaced by the background (Eq. AEFIEeqvdis)
-        LA_l = LAm[e0:e1, e0:e1] / background.mu_r
-        LP_l = LPm[t0:t1, t0:t1] * eb
+        # equivalent configuration: the object replaced by the background (Eq. AEFIEeqvdis),
+        # homogeneous kernels of the background layer
+        LA_l = LA_hom[e0:e1, e0:e1] / background.mu_r
+        LP_l = LP_hom[t0:t1, t0:t1] * eb
         Kb_l, _ = fill_Kbar(mesh, kb, o)
         ne_o, nt_o = e1 - e0, t1 - t0
         Ml = np.block([[background.mu_r * LA_l, -(Do.T @ LP_l @ Bo) / eb],
@@ -99,9 +116,19 @@ def assemble(mesh, materials, background: Material, freq: float, build_Z: bool =
             LA=mat.mu_r * LA_o, LP=LP_o / eo, K=Kb_o + 0.5 * Ix_o, Kbar=Kb_o,
             Kbar_l=Kb_l, Y11=Y[:ne_o], Y21=Y[ne_o:], Ml=Ml, k=ko, eps_c=eo,
             D=Do, B=Bo, F=Fo))
+    out.layered = (stack, layer, tables) if layered else None
     if build_Z:
         out.Z = final_matrix(out)
     return out
+
+
+def default_tables(mesh, stack, layer, omega):
+    """Remainder tables over the objects' extent: 256 log-spaced rho x 128 (z + z') and 128 |z - z'|."""
+    from . import layered as LY
+    lo, hi = mesh.xyz.min(axis=0), mesh.xyz.max(axis=0)
+    span = np.linalg.norm(hi - lo) * 1.01
+    edge = np.min(np.linalg.norm(mesh.xyz[mesh.E.uv[:, 0]] - mesh.xyz[mesh.E.uv[:, 1]], axis=1))
+    return LY.build_tables(stack, layer, omega, 1e-3 * edge, span, lo[2], hi[2])
 
 
 def final_matrix(a: Assembled) -> np.ndarray:
@@ -129,6 +156,23 @@ def final_matrix(a: Assembled) -> np.ndarray:
 def rhs(a: Assembled, khat=(0, 0, -1), pol=(1, 0, 0), E0=1.0):
     m = a.mesh
     b = np.zeros(2 * m.ne + m.nt - m.nobj, dtype=complex)
+    if getattr(a, "layered", None):
+        from . import layered as LY
+        from .fill import ETA0
+        from . import quadrature as Q
+        stack, layer, _ = a.layered
+        if tuple(khat) != (0, 0, -1):
+            raise ValueError("layered backgrounds: normal incidence from the top only")
+        ca, cc, k, zref = LY.plane_wave_normal(stack, layer, a.k0 * C0, E0)
+        A = m.xyz[m.tri]
+        rq = Q.points(A)
+        wq = Q.weights(m.area)
+        ez = ca * np.exp(1j * k * (rq[..., 2] - zref)) + cc * np.exp(-1j * k * (rq[..., 2] - zref))
+        Einc = np.asarray(pol, complex)[None, None, :] * ez[..., None] / ETA0
+        for i in range(3):
+            fi = (rq - A[:, i][:, None, :]) * (m.E.tri_sign[:, i] / (2 * m.area))[:, None, None]
+            np.add.at(b, m.E.tri_edge[:, i], np.einsum('tq,tqd,tqd->t', wq, fi, Einc))
+        return b
     b[:m.ne] = plane_wave(m, a.k0, khat, pol, E0)
     return b
 
