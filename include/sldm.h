@@ -158,10 +158,19 @@ int sldm_mesh_info_get(const sldm_mesh* mesh, sldm_mesh_info* info);
 int sldm_mesh_edges(const sldm_mesh* mesh, int64_t* uv, int64_t* tplus, int64_t* tminus);
 int sldm_mesh_destroy(sldm_mesh* mesh);
 
-/* Background medium (Sec. II, "stratified background").  nlayers == 1 is a
- * homogeneous background (L^A_m = mu_b L^A(k_b), L^phi_m = L^phi(k_b)/eps_b).
- * z_top: height of the interface below the upper half-space; layers are
- * listed top to bottom.  Layered backgrounds return SLDM_ENOTSUP in this build. */
+/* Background medium (Sec. II, "stratified background").  nlayers == 1 with a
+ * half-space bottom is a homogeneous background (L^A_m = mu_b L^A(k_b),
+ * L^phi_m = L^phi(k_b)/eps_b).  Otherwise layers are listed top to bottom:
+ * layer 0 is the upper half-space above z_top; each following layer is finite
+ * (thickness > 0) except the last one when bottom = SLDM_BOTTOM_HALFSPACE; with
+ * SLDM_BOTTOM_PEC a perfect conductor lies under the last layer.  At most 8 layers.
+ * In a stratified background every object must lie strictly inside one layer l
+ * (sldm_material.layer) and away from its interfaces; the external operators use
+ * the multilayer kernel of that layer (homogeneous kernel of layer l, quasistatic
+ * images of the adjacent interfaces, and a remainder tabulated from Sommerfeld
+ * integrals on 256 log-spaced rho x 128 points in z + z' and in |z - z'|,
+ * bilinearly interpolated); the equivalent configuration (Eq. AEFIEeqvdis) uses
+ * the homogeneous kernel of layer l.  Plane waves: normal incidence from the top. */
 int sldm_stack_create(const sldm_layer* layers, int32_t nlayers, double z_top, int32_t bottom,
                       sldm_stack** out);
 int sldm_stack_destroy(sldm_stack* stack);
@@ -179,6 +188,12 @@ int sldm_op_info_get(const sldm_op* op, sldm_op_info* info);
 int sldm_op_block(const sldm_op* op, int32_t which, int32_t obj, void* dst, int32_t where,
                   int64_t* rows, int64_t* cols);
 int sldm_op_destroy(sldm_op* op);
+/* Remainder table of a layered operator (verification): which = 0 for the part
+ * in (rho, z + z'), 1 for the part in (rho, |z - z'|).  dst receives
+ * 5 x nr x n2 complex128 (components xx, phi, zz, z-rho, rho-z; rho log-spaced);
+ * dims = {5, nr, n2}; grid = {log rho_min, log rho_max, (z+z')_min, (z+z')_max,
+ * |z - z'|_max}.  Host pointers; dst may be NULL.  SLDM_EINVAL if homogeneous. */
+int sldm_op_table(const sldm_op* op, int32_t which, void* dst, int64_t* dims, double* grid);
 
 /* y = Z x for nrhs right-hand sides (Eq. finalsystem), column-major N x nrhs
  * complex128 with leading dimension N.  Z is applied in its structured form:
@@ -209,7 +224,8 @@ int sldm_solve(const sldm_op* op, const void* b, void* x, int32_t nrhs, const sl
 
 /* Bistatic radar cross section (m^2) of the solution x (N complex128, `where`)
  * in free space: the equivalent current J_Delta = H - H_eq radiating in the
- * background (Sec. IV-A).  theta, phi, rcs: n doubles, host. */
+ * background (Sec. IV-A).  theta, phi, rcs: n doubles, host.  SLDM_ENOTSUP for
+ * stratified backgrounds. */
 int sldm_farfield(const sldm_op* op, const void* x, int32_t where, const double* theta,
                   const double* phi, int32_t n, double* rcs);
 

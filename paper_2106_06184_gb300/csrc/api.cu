@@ -9,6 +9,7 @@
 
 #include "dense.h"
 #include "internal.h"
+#include "mgf.h"
 #include "precond.h"
 
 namespace sldm {
@@ -50,6 +51,12 @@ struct sldm_op {
   sldm::DBuf<sldm::GemvJob> jobs1, jobs2;
   sldm::DBuf<int64_t> rs1, rs2;
   sldm::GemvPlan plan1, plan2;
+  // layered background (external problem with the multilayer kernel)
+  bool layered = false;
+  sldm::MgfStackHost H;
+  sldm::MgfTables T;
+  std::vector<double> thick;
+  double z_top = 0;
   // preconditioner of Eq. pcext
   sldm::Precond pc;
   // GMRES workspace
@@ -243,7 +250,8 @@ static void assemble_impl(sldm_op* op, const sldm_material* mats, cudaStream_t s
     }
   }
   Kb.release();
-  // ---- Y11, Y21 by LU of M_l, in the operator's precision
+  // ---- Y11, Y21 by LU of M_l, in the operator's precision (M_l uses the homogeneous
+  //      kernel of the background layer: LAm/LPm hold only that part at this point)
   {
     DBuf<C> Ml, Rl;
     Ml.alloc(ml_total);
@@ -262,6 +270,27 @@ static void assemble_impl(sldm_op* op, const sldm_material* mats, cudaStream_t s
       copy_scaled<C>(Rl.p + rl_off[o], int64_t(oi.ne) * oi.ne, 1.0 / h.ell, loc + oi.oY11 * es, s);
       copy_scaled<C>(Rl.p + rl_off[o] + int64_t(oi.ne) * oi.ne, int64_t(oi.nq) * oi.ne, h.ell, loc + oi.oY21 * es, s);
     }
+    SLDM_CUDA(cudaStreamSynchronize(s));
+  }
+  // ---- layered background: add the reflected part (images + tabulated remainder) to L^A_m, L^phi_m
+  if (op->layered) {
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (int64_t v = 0; v < h.nv; ++v)
+      for (int d = 0; d < 3; ++d) {
+        lo[d] = std::min(lo[d], h.xyz[3 * v + d]);
+        hi[d] = std::max(hi[d], h.xyz[3 * v + d]);
+      }
+    double span = 0, emin = 1e300;
+    for (int d = 0; d < 3; ++d) span += (hi[d] - lo[d]) * (hi[d] - lo[d]);
+    span = std::sqrt(span) * 1.01;
+    for (int64_t n = 0; n < h.ne; ++n) {
+      const double* p = &h.xyz[3 * h.uv[2 * n]];
+      const double* q = &h.xyz[3 * h.uv[2 * n + 1]];
+      emin = std::min(emin, std::sqrt((p[0] - q[0]) * (p[0] - q[0]) + (p[1] - q[1]) * (p[1] - q[1]) + (p[2] - q[2]) * (p[2] - q[2])));
+    }
+    op->T.Q = mgf_static(op->H);
+    mgf_build_tables(op->H, omega, 1e-3 * emin, span, lo[2], hi[2], op->T, s);
+    mgf_fill_reflected<C>(m, op->H, omega, op->T, op->LAm.p, op->ne, op->LPm.p, op->nt, s);
     SLDM_CUDA(cudaStreamSynchronize(s));
   }
   build_plans<C>(op);
@@ -519,10 +548,15 @@ int sldm_stack_create(const sldm_layer* layers, int32_t nlayers, double z_top, i
   API_BEGIN
   SLDM_REQUIRE(out && layers && nlayers >= 1, SLDM_EINVAL, "stack_create: invalid arguments");
   *out = nullptr;
-  SLDM_REQUIRE(nlayers == 1 && bottom == SLDM_BOTTOM_HALFSPACE, SLDM_ENOTSUP,
-               "stack_create: layered backgrounds are not available in this build");
-  SLDM_REQUIRE(layers[0].eps_r > 0 && layers[0].mu_r > 0 && layers[0].sigma >= 0, SLDM_EINVAL,
-               "stack_create: invalid layer material");
+  SLDM_REQUIRE(nlayers <= MGF_MAX_LAYERS, SLDM_ENOTSUP, "stack_create: too many layers");
+  SLDM_REQUIRE(bottom == SLDM_BOTTOM_HALFSPACE || bottom == SLDM_BOTTOM_PEC, SLDM_EINVAL, "stack_create: unknown bottom");
+  for (int i = 0; i < nlayers; ++i) {
+    SLDM_REQUIRE(layers[i].eps_r > 0 && layers[i].mu_r > 0 && layers[i].sigma >= 0, SLDM_EINVAL,
+                 "stack_create: invalid layer material");
+    const bool finite = i > 0 && (bottom == SLDM_BOTTOM_PEC || i < nlayers - 1);
+    SLDM_REQUIRE(!finite || (layers[i].thickness > 0 && std::isfinite(layers[i].thickness)), SLDM_EINVAL,
+                 "stack_create: finite layers need a positive thickness");
+  }
   auto* st = new sldm_stack();
   st->layers.assign(layers, layers + nlayers);
   st->z_top = z_top;
@@ -563,7 +597,44 @@ int sldm_assemble(const sldm_mesh* m, const sldm_stack* st, const sldm_material*
     op->nobj = m->h.nobj;
     op->nq = op->nt - op->nobj;
     op->N = 2 * op->ne + op->nq;
-    const sldm_layer& L = st->layers[0];
+    const int nl = int(st->layers.size());
+    op->layered = nl > 1 || st->bottom == SLDM_BOTTOM_PEC;
+    int lay = 0;
+    if (op->layered) {
+      lay = per_obj[0].layer;
+      for (int64_t o = 0; o < m->h.nobj; ++o)
+        SLDM_REQUIRE(per_obj[o].layer == lay, SLDM_ENOTSUP, "assemble: every object must lie in the same layer");
+      SLDM_REQUIRE(lay >= 0 && lay < nl, SLDM_EINVAL, "assemble: layer index out of range");
+      // layer bounds: layer 0 above z_top; finite layers below, top to bottom
+      MgfStackHost& H = op->H;
+      H.l = lay;
+      H.pec = st->bottom == SLDM_BOTTOM_PEC;
+      op->thick.assign(nl, 0.0);
+      double z = st->z_top, zb = -1e300, zu = 1e300;
+      for (int i = 0; i < nl; ++i) {
+        H.eps.push_back(eps_complex(st->layers[i].eps_r, st->layers[i].sigma, 2 * PI_ * freq_hz));
+        H.mu.push_back(st->layers[i].mu_r);
+        const bool finite = i > 0 && (H.pec || i < nl - 1);
+        op->thick[i] = finite ? st->layers[i].thickness : 0.0;
+        H.d.push_back(op->thick[i]);
+        const double top = i == 0 ? 1e300 : z;
+        const double bot = i == 0 ? st->z_top : (finite ? z - op->thick[i] : -1e300);
+        if (i == lay) {
+          zb = bot;
+          zu = top;
+        }
+        if (i > 0 && finite) z -= op->thick[i];
+      }
+      H.zb = zb;
+      H.zu = zu;
+      H.top = lay > 0;
+      H.bot = zb > -1e299;
+      op->z_top = st->z_top;
+      for (int64_t v = 0; v < m->h.nv; ++v)
+        SLDM_REQUIRE(m->h.xyz[3 * v + 2] > zb && m->h.xyz[3 * v + 2] < zu, SLDM_EINVAL,
+                     "assemble: the objects must lie strictly inside their layer");
+    }
+    const sldm_layer& L = st->layers[lay];
     op->eps_b = eps_complex(L.eps_r, L.sigma, 2 * PI_ * freq_hz);
     op->mu_b = L.mu_r;
     op->kb = op->k0 * std::sqrt(op->eps_b * op->mu_b);
@@ -640,6 +711,30 @@ int sldm_op_block(const sldm_op* op, int32_t which, int32_t obj, void* dst, int3
   API_END
 }
 
+int sldm_op_table(const sldm_op* op, int32_t which, void* dst, int64_t* dims, double* grid) {
+  API_BEGIN
+  SLDM_REQUIRE(op, SLDM_EINVAL, "op_table: null op");
+  SLDM_REQUIRE(op->layered, SLDM_EINVAL, "op_table: the operator has a homogeneous background");
+  SLDM_REQUIRE(which == 0 || which == 1, SLDM_EINVAL, "op_table: which must be 0 (z + z') or 1 (z - z')");
+  const int n2 = which == 0 ? op->T.ns : op->T.nd;
+  if (dims) {
+    dims[0] = 5;
+    dims[1] = op->T.nr;
+    dims[2] = n2;
+  }
+  if (grid) {
+    grid[0] = op->T.lr0;
+    grid[1] = op->T.lr1;
+    grid[2] = op->T.s0;
+    grid[3] = op->T.s1;
+    grid[4] = op->T.d1;
+  }
+  if (dst)
+    SLDM_CUDA(cudaMemcpy(dst, which == 0 ? op->T.A.p : op->T.B.p, size_t(5) * op->T.nr * n2 * sizeof(double2),
+                         cudaMemcpyDeviceToHost));
+  API_END
+}
+
 int sldm_op_destroy(sldm_op* op) {
   API_BEGIN
   delete op;
@@ -685,7 +780,18 @@ int sldm_rhs_planewave(const sldm_op* op, const double* khat, const double* pol,
     db = tmp.p;
   }
   SLDM_CUDA(cudaMemsetAsync(db, 0, size_t(op->N) * nrhs * sizeof(double2), s));
-  rhs_planewave(op->mesh, op->k0, dk.p, nrhs, db, op->N, s);
+  if (op->layered) {
+    for (int r = 0; r < nrhs; ++r)
+      SLDM_REQUIRE(std::fabs(khat[3 * r]) < 1e-12 && std::fabs(khat[3 * r + 1]) < 1e-12 && khat[3 * r + 2] < 0, SLDM_ENOTSUP,
+                   "rhs_planewave: layered backgrounds take normal incidence from the top (khat = -z)");
+    std::complex<double> ca, cc, ck;
+    double zref;
+    mgf_plane_wave_normal(op->H, op->thick, op->z_top, 2 * PI_ * op->freq, &ca, &cc, &ck, &zref);
+    const double coef[7] = {ca.real(), ca.imag(), cc.real(), cc.imag(), ck.real(), ck.imag(), zref};
+    rhs_planewave_layered(op->mesh, coef, dk.p, nrhs, db, op->N, s);
+  } else {
+    rhs_planewave(op->mesh, op->k0, dk.p, nrhs, db, op->N, s);
+  }
   if (where == SLDM_HOST)
     SLDM_CUDA(cudaMemcpyAsync(b, db, size_t(op->N) * nrhs * sizeof(double2), cudaMemcpyDeviceToHost, s));
   SLDM_CUDA(cudaStreamSynchronize(s));
@@ -739,6 +845,7 @@ int sldm_farfield(const sldm_op* op_, const void* x, int32_t where, const double
                   double* rcs) {
   API_BEGIN
   SLDM_REQUIRE(op_ && x && theta && phi && rcs && n >= 1, SLDM_EINVAL, "farfield: invalid arguments");
+  SLDM_REQUIRE(!op_->layered, SLDM_ENOTSUP, "farfield: free-space far field only (homogeneous background)");
   sldm_op* op = const_cast<sldm_op*>(op_);
   cudaStream_t s = 0;
   DBuf<double2> dx, jd;

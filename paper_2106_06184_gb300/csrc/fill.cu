@@ -962,6 +962,48 @@ __global__ void rhs_kernel(int ne, int nrhs, double k0, const double* __restrict
   b[int64_t(r) * ld + m] = make_double2(acc_r, acc_i);
 }
 
+// Normal incidence through a stack: in the objects' layer E_inc = pol (a e^{+j k (z - zref)} + c e^{-j k (z - zref)}).
+__global__ void rhs_layered_kernel(int ne, int nrhs, double ar, double ai, double cr, double ci, double kr, double ki, double zref,
+                                   const double* __restrict__ kp, const int32_t* __restrict__ tplus,
+                                   const int32_t* __restrict__ tminus, const int32_t* __restrict__ tri_edge,
+                                   const double* __restrict__ geo, double2* b, int64_t ld) {
+  int m = blockIdx.x * blockDim.x + threadIdx.x;
+  int r = blockIdx.y;
+  if (m >= ne) return;
+  const double* pol = kp + 6 * r + 3;
+  double acc_r = 0, acc_i = 0;
+  for (int side = 0; side < 2; ++side) {
+    int t = side == 0 ? tplus[m] : tminus[m];
+    const double* g = geo + size_t(t) * GEO_STRIDE;
+    int i = tri_edge[3 * t] == m ? 0 : (tri_edge[3 * t + 1] == m ? 1 : 2);
+    for (int q = 0; q < 6; ++q) {
+      double fp = 0;
+      for (int d = 0; d < 3; ++d) fp += g[GEO_SIG + i] * (g[GEO_RHO + 3 * q + d] + g[GEO_AV + 3 * i + d]) * pol[d];
+      const double dz = g[GEO_C + 2] + g[GEO_RHO + 3 * q + 2] - zref;
+      // e^{+j k dz} = e^{-ki dz} (cos(kr dz) + j sin(kr dz)),  e^{-j k dz} = e^{ki dz} (cos - j sin)
+      double sn, cn;
+      sincos(kr * dz, &sn, &cn);
+      const double ep = exp(-ki * dz), em = exp(ki * dz);
+      const double ur = ep * cn, ui = ep * sn, vr = em * cn, vi = -em * sn;
+      const double er = ar * ur - ai * ui + cr * vr - ci * vi;
+      const double ei = ar * ui + ai * ur + cr * vi + ci * vr;
+      const double w = g[GEO_W + q] * fp / ETA0;
+      acc_r += w * er;
+      acc_i += w * ei;
+    }
+  }
+  b[int64_t(r) * ld + m] = make_double2(acc_r, acc_i);
+}
+
+void rhs_planewave_layered(const sldm_mesh* m, const double coef[7], const double* kp, int nrhs, double2* b, int64_t ld,
+                           cudaStream_t s) {
+  int ne = int(m->h.ne);
+  dim3 grid((ne + 127) / 128, nrhs);
+  rhs_layered_kernel<<<grid, 128, 0, s>>>(ne, nrhs, coef[0], coef[1], coef[2], coef[3], coef[4], coef[5], coef[6], kp,
+                                          m->d.tplus.p, m->d.tminus.p, m->d.tri_edge.p, m->d.geo.p, b, ld);
+  SLDM_CUDA(cudaGetLastError());
+}
+
 void rhs_planewave(const sldm_mesh* m, double k0, const double* kp, int nrhs, double2* b, int64_t ld, cudaStream_t s) {
   int ne = int(m->h.ne);
   dim3 grid((ne + 127) / 128, nrhs);

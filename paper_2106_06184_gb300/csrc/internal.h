@@ -187,6 +187,9 @@ void gram_ix(const sldm_mesh* m, double* vals, cudaStream_t s);
 // e_inc for nrhs plane waves into b (complex128, column-major N x nrhs, ld)
 void rhs_planewave(const sldm_mesh* m, double k0, const double* khat_pol_dev, int nrhs, double2* b,
                    int64_t ld, cudaStream_t s);
+// e_inc for normal incidence through a stack: coef = (Re a, Im a, Re c, Im c, Re k, Im k, zref)
+void rhs_planewave_layered(const sldm_mesh* m, const double coef[7], const double* khat_pol_dev, int nrhs, double2* b,
+                           int64_t ld, cudaStream_t s);
 // far field vector F(theta, phi) of RWG coefficients jd (complex128) -> rcs (double), device
 void farfield(const sldm_mesh* m, double k0, const double2* jd, const double* ang_dev, int n, double* rcs,
               cudaStream_t s);

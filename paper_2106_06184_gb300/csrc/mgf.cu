@@ -1,0 +1,586 @@
+// Layered-medium Green's function of the external problem (Sec. II-C; Sec. IV:
+// quasistatic part extracted and added back analytically, Sommerfeld integrals
+// of the rest tabulated and interpolated), for source and observation points in
+// one layer l of a stratified background.
+//
+// Mixed-potential kernels (normalised like the paper's operators: L^A_m uses
+// G^A/mu0, L^phi_m uses eps0 K^phi), spectral form from transmission-line
+// Green's functions of the TM (e) and TE (h) lines of layer l:
+//   g_xx = V_i^h/(j w mu0),  k_phi = eps0 (j w/k_rho^2)(V_i^e - V_i^h),
+//   g_zz = [mu_r (k_rho^2 - k_z^2)/(eps k_rho^2) I_v^e + (w^2 mu mu_r/k_rho^2) I_v^h]/(j w),
+//   g_zu = j (mu_r/k_rho)(I_i^e - I_i^h),  g_uz = j (mu_r/k_rho)(V_v^e - V_v^h),
+// spatial: S0 for xx, phi, zz and -j S1 for z-rho, rho-z (S_n[f] = 1/(2 pi) int f J_n k dk).
+// The direct term (homogeneous kernel of layer l) is filled by the homogeneous
+// path; the quasistatic images of the two adjacent interfaces are evaluated in
+// closed form here; the remainder is A(rho, z + z') + B(rho, z - z') from two
+// sets of 2-D tables (256 log-spaced rho x 128), bilinear in (log rho, .).
+#include <algorithm>
+#include <cmath>
+#include <complex>
+
+#include "dense.h"
+#include "mgf.h"
+
+namespace sldm {
+
+// ---------------------------------------------------------------- complex FP64 helpers
+struct cx {
+  double r, i;
+};
+__host__ __device__ __forceinline__ cx mk(double r, double i = 0.0) { return {r, i}; }
+__host__ __device__ __forceinline__ cx operator+(cx a, cx b) { return {a.r + b.r, a.i + b.i}; }
+__host__ __device__ __forceinline__ cx operator-(cx a, cx b) { return {a.r - b.r, a.i - b.i}; }
+__host__ __device__ __forceinline__ cx operator-(cx a) { return {-a.r, -a.i}; }
+__host__ __device__ __forceinline__ cx operator*(cx a, cx b) { return {a.r * b.r - a.i * b.i, a.r * b.i + a.i * b.r}; }
+__host__ __device__ __forceinline__ cx operator*(double s, cx a) { return {s * a.r, s * a.i}; }
+__host__ __device__ __forceinline__ cx operator*(cx a, double s) { return {s * a.r, s * a.i}; }
+__host__ __device__ __forceinline__ cx operator/(cx a, cx b) {
+  const double d = b.r * b.r + b.i * b.i;
+  return {(a.r * b.r + a.i * b.i) / d, (a.i * b.r - a.r * b.i) / d};
+}
+__device__ __forceinline__ cx cexp_(cx a) {
+  double s, c;
+  sincos(a.i, &s, &c);
+  const double e = exp(a.r);
+  return {e * c, e * s};
+}
+__device__ __forceinline__ cx csqrt_(cx a) {
+  const double m = sqrt(a.r * a.r + a.i * a.i);
+  double re = sqrt(fmax(0.5 * (m + a.r), 0.0));
+  double im = sqrt(fmax(0.5 * (m - a.r), 0.0));
+  if (a.i < 0) im = -im;
+  return {re, im};
+}
+// k_z = sqrt(k^2 - k_rho^2) with Im k_z <= 0
+__device__ __forceinline__ cx kz_of(cx k, cx kr) {
+  cx q = csqrt_(k * k - kr * kr);
+  if (q.i > 0) q = -q;
+  return q;
+}
+
+// J_n(z), n = 0, 1, complex z: periodic trapezoid rule of (1/2pi) int_0^2pi cos(n t - z sin t) dt
+__device__ void bessel01_complex(cx z, cx* j0, cx* j1) {
+  const double az = sqrt(z.r * z.r + z.i * z.i);
+  const int M = 2 * (int(az) + 40);
+  cx s0 = mk(0), s1 = mk(0);
+  for (int m = 0; m < M; ++m) {
+    double st, ct;
+    sincospi(2.0 * m / M, &st, &ct);
+    // cos(n t - z sin t) = (e^{i(nt - z st)} + e^{-i(nt - z st)})/2, z complex
+    const cx ph = mk(z.r * st, z.i * st);  // z sin t
+    // cos(w) for complex w = a + j b: cos a cosh b - j sin a sinh b
+    auto ccos = [](cx w) {
+      double sa, ca;
+      sincos(w.r, &sa, &ca);
+      return cx{ca * cosh(w.i), -sa * sinh(w.i)};
+    };
+    s0 = s0 + ccos(-ph);
+    // n = 1: cos(t - z sin t)
+    const double t = 2.0 * M_PI * m / M;
+    s1 = s1 + ccos(mk(t - ph.r, -ph.i));
+  }
+  *j0 = (1.0 / M) * s0;
+  *j1 = (1.0 / M) * s1;
+}
+
+// ---------------------------------------------------------------- stack on the device
+struct DevStack {
+  int nl, l, pec, pad;
+  double omega;
+  cx eps[MGF_MAX_LAYERS];
+  double mu[MGF_MAX_LAYERS];
+  double d[MGF_MAX_LAYERS];  // thickness (finite layers)
+  double zb, zu;             // bounds of layer l (+-1e300 for none)
+  int top, bot;              // adjacent interfaces exist
+};
+
+constexpr double EPS0_ = 1.0 / (4e-7 * 3.14159265358979323846 * 299792458.0 * 299792458.0);
+constexpr double MU0_ = 4e-7 * 3.14159265358979323846;
+constexpr double C0_ = 299792458.0;
+
+// generalised reflections (Gu, Gd) of line `te` (0 = e, 1 = h) seen from layer l
+__device__ void reflections(const DevStack& S, cx kr, int te, cx* Gu, cx* Gd) {
+  const double k0 = S.omega / C0_;
+  cx Z[MGF_MAX_LAYERS], kz[MGF_MAX_LAYERS];
+  for (int i = 0; i < S.nl; ++i) {
+    // k_i = k0 sqrt(eps mu)
+    cx k = csqrt_(S.mu[i] * S.eps[i]);
+    k = k0 * k;
+    kz[i] = kz_of(k, kr);
+    Z[i] = te == 0 ? kz[i] / (S.omega * EPS0_ * S.eps[i]) : (S.omega * MU0_ * S.mu[i]) * (mk(1) / kz[i]);
+  }
+  auto fres = [&](int i, int j) { return (Z[j] - Z[i]) / (Z[j] + Z[i]); };
+  cx up = mk(0);
+  for (int i = 1; i <= S.l; ++i) {
+    const cx f = fres(i, i - 1);
+    if (i - 1 == 0) {
+      up = f;
+    } else {
+      const cx ph = up * cexp_(mk(0, -2.0) * kz[i - 1] * mk(S.d[i - 1]));
+      up = (f + ph) / (mk(1) + f * ph);
+    }
+  }
+  const int last = S.nl - 1;
+  cx down = S.pec ? mk(-1) : mk(0);
+  for (int i = last - 1; i >= S.l; --i) {
+    const cx f = fres(i, i + 1);
+    if (i + 1 == last && !S.pec) {
+      down = f;
+    } else {
+      const cx ph = down * cexp_(mk(0, -2.0) * kz[i + 1] * mk(S.d[i + 1]));
+      down = (f + ph) / (mk(1) + f * ph);
+    }
+  }
+  if (S.l == last) down = S.pec ? mk(-1) : mk(0);
+  if (S.l == 0) up = mk(0);
+  *Gu = up;
+  *Gd = down;
+}
+
+// Remainder spectral kernels at one node: part 0 = single reflections minus the
+// quasistatic images (argument s = z + z'), part 1 = double reflections (argument d = z - z').
+__device__ void spectral_rem(const DevStack& S, const MgfStatic& Q, cx kr, int part, double arg, cx out[5]) {
+  const double k0 = S.omega / C0_;
+  const cx epsl = S.eps[S.l];
+  const double mur = S.mu[S.l];
+  cx k = k0 * csqrt_(mur * epsl);
+  const cx kz = kz_of(k, kr);
+  const cx Ze = kz / (S.omega * EPS0_ * epsl);
+  const cx Zh = (S.omega * MU0_ * mur) * (mk(1) / kz);
+  cx Gue, Gde, Guh, Gdh;
+  reflections(S, kr, 0, &Gue, &Gde);
+  reflections(S, kr, 1, &Guh, &Gdh);
+  const double dl = S.zu - S.zb;
+  const cx zero = mk(0);
+  cx E1 = zero, E2 = zero, E3 = zero, E4 = zero;
+  const cx mj = mk(0, -1);
+  if (part == 0) {
+    if (S.top) E1 = cexp_(mj * kz * mk(2 * S.zu - arg));
+    if (S.bot) E2 = cexp_(mj * kz * mk(arg - 2 * S.zb));
+  } else if (S.top && S.bot) {
+    E3 = cexp_(mj * kz * mk(2 * dl + arg));
+    E4 = cexp_(mj * kz * mk(2 * dl - arg));
+  }
+  const cx e2d = (S.top && S.bot) ? cexp_(mk(0, -2.0) * kz * mk(dl)) : zero;
+  const cx De = mk(1) - Gue * Gde * e2d, Dh = mk(1) - Guh * Gdh * e2d;
+  // reflected parts of the line functions
+  auto Vi = [&](cx Z, cx Gu, cx Gd, cx D) { return (0.5 * Z) * ((Gu * E1 + Gd * E2 + Gu * Gd * (E3 + E4)) / D); };
+  auto Iv = [&](cx Z, cx Gu, cx Gd, cx D) {
+    return (mk(0.5) / Z) * ((-(Gu * E1) - Gd * E2 + Gu * Gd * (E3 + E4)) / D);
+  };
+  auto Ii = [&](cx Gu, cx Gd, cx D) { return 0.5 * ((-(Gu * E1) + Gd * E2 + Gu * Gd * (E3 - E4)) / D); };
+  auto Vv = [&](cx Gu, cx Gd, cx D) { return 0.5 * ((Gu * E1 - Gd * E2 + Gu * Gd * (E3 - E4)) / D); };
+  const cx Vie = Vi(Ze, Gue, Gde, De), Vih = Vi(Zh, Guh, Gdh, Dh);
+  const cx Ive = Iv(Ze, Gue, Gde, De), Ivh = Iv(Zh, Guh, Gdh, Dh);
+  const cx Iie = Ii(Gue, Gde, De), Iih = Ii(Guh, Gdh, Dh);
+  const cx Vve = Vv(Gue, Gde, De), Vvh = Vv(Guh, Gdh, Dh);
+  const cx jw = mk(0, S.omega);
+  const cx kr2 = kr * kr;
+  const cx gue = {Q.gue.r, Q.gue.i}, guh = {Q.guh.r, Q.guh.i}, gde = {Q.gde.r, Q.gde.i}, gdh = {Q.gdh.r, Q.gdh.i};
+  out[0] = Vih / (jw * mk(MU0_));                                                    // xx
+  out[1] = (EPS0_ * (jw / kr2)) * (Vie - Vih);                                        // phi
+  out[2] = ((mur * ((kr2 - kz * kz) / (EPS0_ * epsl * kr2))) * Ive +
+            ((S.omega * S.omega * MU0_ * mur * mur) * (mk(1) / kr2)) * Ivh) / jw;     // zz
+  out[3] = (mk(0, mur) / kr) * (Iie - Iih);                                           // z-rho
+  out[4] = (mk(0, mur) / kr) * (Vve - Vvh);                                           // rho-z
+  if (part == 0) {
+    const cx g = mk(1) / (mk(0, 2) * kz);
+    out[0] = out[0] - (mur * (guh * E1 + gdh * E2)) * g;
+    out[1] = out[1] - ((gue * E1 + gde * E2) * g) / epsl;
+    out[2] = out[2] - (mur * ((guh - 2.0 * gue) * E1 + (gdh - 2.0 * gde) * E2)) * g;
+  }
+}
+
+// F[node][j][c] = w_node k_node g_c(k_node; arg_j) / (2 pi)
+__global__ void mgf_spectral_kernel(DevStack S, MgfStatic Q, const double2* __restrict__ nodes,
+                                    const double2* __restrict__ weights, int nnodes, const double* __restrict__ args,
+                                    int nargs, int part, double2* F) {
+  const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (idx >= int64_t(nnodes) * nargs) return;
+  const int n = int(idx / nargs), j = int(idx % nargs);
+  const cx kr = {nodes[n].x, nodes[n].y};
+  const cx w = {weights[n].x, weights[n].y};
+  cx g[5];
+  spectral_rem(S, Q, kr, part, args[j], g);
+  const cx f = (0.5 / 3.14159265358979323846) * (w * kr);
+  for (int c = 0; c < 5; ++c) {
+    const cx v = f * g[c];
+    F[(int64_t(n) * nargs + j) * 5 + c] = make_double2(v.r, v.i);
+  }
+}
+
+// Jm[order][i][n] = J_order(k_n rho_i)
+__global__ void mgf_bessel_kernel(const double2* __restrict__ nodes, int nnodes, const double* __restrict__ rho, int nr,
+                                  double2* Jm) {
+  const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (idx >= int64_t(nnodes) * nr) return;
+  const int i = int(idx / nnodes), n = int(idx % nnodes);
+  const double2 k = nodes[n];
+  cx j0, j1;
+  if (k.y == 0.0) {
+    const double x = k.x * rho[i];
+    j0 = mk(::j0(x));
+    j1 = mk(::j1(x));
+  } else {
+    bessel01_complex(mk(k.x * rho[i], k.y * rho[i]), &j0, &j1);
+  }
+  Jm[int64_t(i) * nnodes + n] = make_double2(j0.r, j0.i);
+  Jm[int64_t(nr) * nnodes + int64_t(i) * nnodes + n] = make_double2(j1.r, j1.i);
+}
+
+// table[c][i][j] = sum_n J_{order(c)}[i][n] F[n][j][c]  (times -j for the order-1 components)
+__global__ void mgf_contract_kernel(const double2* __restrict__ Jm, const double2* __restrict__ F, int nnodes, int nr,
+                                    int nargs, double2* table) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.y;
+  const int c = blockIdx.z;
+  if (j >= nargs) return;
+  const int order = c >= 3 ? 1 : 0;
+  const double2* J = Jm + int64_t(order) * nr * nnodes + int64_t(i) * nnodes;
+  cx acc = mk(0);
+  for (int n = 0; n < nnodes; ++n) {
+    const double2 a = J[n];
+    const double2 b = F[(int64_t(n) * nargs + j) * 5 + c];
+    acc = acc + cx{a.x, a.y} * cx{b.x, b.y};
+  }
+  if (order == 1) acc = mk(0, -1) * acc;
+  table[(int64_t(c) * nr + i) * nargs + j] = make_double2(acc.r, acc.i);
+}
+
+// ---------------------------------------------------------------- host: nodes and tables
+static void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.resize(n);
+  w.resize(n);
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+    for (int it = 0; it < 100; ++it) {
+      double p1 = 1.0, p2 = 0.0;
+      for (int j = 1; j <= n; ++j) {
+        const double p3 = p2;
+        p2 = p1;
+        p1 = ((2.0 * j - 1.0) * z * p2 - (j - 1.0) * p3) / j;
+      }
+      const double pp = n * (z * p1 - p2) / (z * z - 1.0);
+      const double z1 = z;
+      z = z1 - p1 / pp;
+      if (std::fabs(z - z1) < 1e-16) {
+        x[i] = -z;
+        w[i] = 2.0 / ((1.0 - z * z) * pp * pp);
+        break;
+      }
+      x[i] = -z;
+      w[i] = 2.0 / ((1.0 - z * z) * pp * pp);
+    }
+  }
+}
+
+// Elliptic arc k(t) = a/2 (1 - cos t) + j b sin t over t in [0, pi] (n_e Gauss points),
+// a = max(1.5 max Re k_i, 2 k0), b = min(a/2, 2/rho_max); then Gauss-Legendre panels
+// (16 points) of width min(pi/rho_max, (k_end - a)/4) up to k_end = a + 32/zeta_min.
+static void sommerfeld_nodes(const MgfStackHost& H, double omega, double rho_max, double zeta_min,
+                             std::vector<double2>& nodes, std::vector<double2>& weights) {
+  const double k0 = omega / C0_;
+  double kmax = 0;
+  for (size_t i = 0; i < H.eps.size(); ++i) kmax = std::max(kmax, std::abs((k0 * std::sqrt(H.eps[i] * H.mu[i])).real()));
+  const double a = std::max(1.5 * kmax, 2.0 * k0);
+  const double b = std::min(0.5 * a, 2.0 / rho_max);
+  std::vector<double> x, w;
+  gauss_legendre(MGF_N_ELLIPSE, x, w);
+  nodes.clear();
+  weights.clear();
+  for (int i = 0; i < MGF_N_ELLIPSE; ++i) {
+    const double t = 0.5 * M_PI * (x[i] + 1), wt = 0.5 * M_PI * w[i];
+    nodes.push_back(make_double2(0.5 * a * (1 - std::cos(t)), b * std::sin(t)));
+    weights.push_back(make_double2(0.5 * a * std::sin(t) * wt, b * std::cos(t) * wt));
+  }
+  const double kend = a + 32.0 / zeta_min;
+  const double width = std::min(M_PI / rho_max, (kend - a) / 4);
+  const int npan = int(std::ceil((kend - a) / width));
+  gauss_legendre(MGF_PER_PANEL, x, w);
+  for (int p = 0; p < npan; ++p) {
+    const double mid = a + width * (p + 0.5);
+    for (int q = 0; q < MGF_PER_PANEL; ++q) {
+      nodes.push_back(make_double2(mid + 0.5 * width * x[q], 0.0));
+      weights.push_back(make_double2(0.5 * width * w[q], 0.0));
+    }
+  }
+}
+
+static DevStack dev_stack(const MgfStackHost& H, double omega) {
+  DevStack S{};
+  S.nl = int(H.eps.size());
+  S.l = H.l;
+  S.pec = H.pec;
+  S.omega = omega;
+  for (int i = 0; i < S.nl; ++i) {
+    S.eps[i] = {H.eps[i].real(), H.eps[i].imag()};
+    S.mu[i] = H.mu[i];
+    S.d[i] = H.d[i];
+  }
+  S.zb = H.zb;
+  S.zu = H.zu;
+  S.top = H.top;
+  S.bot = H.bot;
+  return S;
+}
+
+static void build_one(const MgfStackHost& H, const MgfStatic& Q, double omega, const std::vector<double>& rho,
+                      const std::vector<double>& args, int part, double zeta_min, double2* out, cudaStream_t s) {
+  std::vector<double2> nodes, weights;
+  sommerfeld_nodes(H, omega, rho.back() / 1.0, zeta_min, nodes, weights);
+  const int nn = int(nodes.size()), nr = int(rho.size()), na = int(args.size());
+  DBuf<double2> dn, dw, F, Jm;
+  DBuf<double> dr, da;
+  dn.upload(nodes, s);
+  dw.upload(weights, s);
+  dr.upload(rho, s);
+  da.upload(args, s);
+  F.alloc(size_t(nn) * na * 5);
+  Jm.alloc(size_t(2) * nr * nn);
+  const DevStack S = dev_stack(H, omega);
+  {
+    ScopedTimer tm("mgf_tables", s);
+    const int64_t tot = int64_t(nn) * na;
+    mgf_spectral_kernel<<<unsigned((tot + 127) / 128), 128, 0, s>>>(S, Q, dn.p, dw.p, nn, da.p, na, part, F.p);
+    const int64_t totb = int64_t(nn) * nr;
+    mgf_bessel_kernel<<<unsigned((totb + 127) / 128), 128, 0, s>>>(dn.p, nn, dr.p, nr, Jm.p);
+    mgf_contract_kernel<<<dim3((na + 127) / 128, nr, 5), 128, 0, s>>>(Jm.p, F.p, nn, nr, na, out);
+  }
+  SLDM_CUDA(cudaGetLastError());
+  SLDM_CUDA(cudaStreamSynchronize(s));
+}
+
+void mgf_build_tables(const MgfStackHost& H, double omega, double rho_min, double rho_max, double zmin, double zmax,
+                      MgfTables& T, cudaStream_t s) {
+  T.nr = MGF_NR;
+  T.ns = MGF_NS;
+  T.nd = MGF_ND;
+  std::vector<double> rho(T.nr), sv(T.ns), dv(T.nd);
+  for (int i = 0; i < T.nr; ++i)
+    rho[i] = std::exp(std::log(rho_min) + (std::log(rho_max) - std::log(rho_min)) * i / (T.nr - 1));
+  for (int j = 0; j < T.ns; ++j) sv[j] = 2 * zmin + (2 * zmax - 2 * zmin) * j / (T.ns - 1);
+  for (int j = 0; j < T.nd; ++j) dv[j] = (zmax - zmin) * j / (T.nd - 1);
+  T.lr0 = std::log(rho_min);
+  T.lr1 = std::log(rho_max);
+  T.s0 = 2 * zmin;
+  T.s1 = 2 * zmax;
+  T.d1 = zmax - zmin;
+  T.A.alloc(size_t(5) * T.nr * T.ns);
+  T.B.alloc(size_t(5) * T.nr * T.nd);
+  double zeta_a = 1.0;
+  {
+    bool any = false;
+    double zm = 1e300;
+    if (H.top) {
+      zm = std::min(zm, 2 * H.zu - 2 * zmax);
+      any = true;
+    }
+    if (H.bot) {
+      zm = std::min(zm, 2 * zmin - 2 * H.zb);
+      any = true;
+    }
+    if (any) zeta_a = zm;
+  }
+  SLDM_REQUIRE(zeta_a > 0, SLDM_EINVAL, "layered background: an object touches or crosses an interface");
+  build_one(H, T.Q, omega, rho, sv, 0, zeta_a, T.A.p, s);
+  if (H.top && H.bot) {
+    const double zeta_b = 2 * (H.zu - H.zb) - (zmax - zmin);
+    build_one(H, T.Q, omega, rho, dv, 1, zeta_b, T.B.p, s);
+  } else {
+    T.B.zero(s);
+  }
+}
+
+// ---------------------------------------------------------------- reflected fill of L^A_m, L^phi_m
+struct TabView {
+  const double2* A;
+  const double2* B;
+  int nr, ns, nd;
+  double lr0, lr1, s0, s1, d1;
+};
+
+__device__ __forceinline__ cx bilin(const double2* t, int nr, int ny, double fx, double fy, int c) {
+  fx = fmin(fmax(fx, 0.0), nr - 1 - 1e-9);
+  fy = ny > 1 ? fmin(fmax(fy, 0.0), ny - 1 - 1e-9) : 0.0;
+  const int ix = int(fx), iy = int(fy);
+  const double tx = fx - ix, ty = fy - iy;
+  const int iy1 = min(iy + 1, ny - 1);
+  const double2* b = t + int64_t(c) * nr * ny;
+  const double2 a00 = b[int64_t(ix) * ny + iy], a10 = b[int64_t(ix + 1) * ny + iy];
+  const double2 a01 = b[int64_t(ix) * ny + iy1], a11 = b[int64_t(ix + 1) * ny + iy1];
+  const double w00 = (1 - tx) * (1 - ty), w10 = tx * (1 - ty), w01 = (1 - tx) * ty, w11 = tx * ty;
+  return {w00 * a00.x + w10 * a10.x + w01 * a01.x + w11 * a11.x, w00 * a00.y + w10 * a10.y + w01 * a01.y + w11 * a11.y};
+}
+
+// One thread per (test, source) triangle pair, 6 x 6 points; kernels are smooth
+// (objects keep away from the interfaces), so every pair uses the product rule.
+template <class C>
+__global__ void __launch_bounds__(128) fill_reflected_kernel(int nt, const double* __restrict__ geo, const int32_t* __restrict__ tri_edge,
+                                                             DevStack S, MgfStatic Q, TabView T, C* LA, int64_t ldA, C* LP,
+                                                             int64_t ldP) {
+  const int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (p >= int64_t(nt) * nt) return;
+  const int t = int(p / nt), sidx = int(p % nt);
+  const double* gt = geo + size_t(t) * GEO_STRIDE;
+  const double* gs = geo + size_t(sidx) * GEO_STRIDE;
+  const double k0 = S.omega / C0_;
+  const cx epsl = S.eps[S.l];
+  const double mur = S.mu[S.l];
+  const cx k = k0 * csqrt_(mur * epsl);
+  cx loc[9];
+  for (int i = 0; i < 9; ++i) loc[i] = mk(0);
+  cx lp = mk(0);
+  const double inv4pi = 0.25 / 3.14159265358979323846;
+  for (int q = 0; q < 6; ++q) {
+    double r[3], f[3][3];
+    for (int d = 0; d < 3; ++d) r[d] = gt[GEO_C + d] + gt[GEO_RHO + 3 * q + d];
+    for (int i = 0; i < 3; ++i)
+      for (int d = 0; d < 3; ++d) f[i][d] = gt[GEO_SIG + i] * (gt[GEO_RHO + 3 * q + d] + gt[GEO_AV + 3 * i + d]);
+    cx V[3][3];  // sum_s W' T . f_j(r'_s)
+    for (int j = 0; j < 3; ++j)
+      for (int d = 0; d < 3; ++d) V[j][d] = mk(0);
+    cx sphi = mk(0);
+    for (int sq = 0; sq < 6; ++sq) {
+      double rs[3];
+      for (int d = 0; d < 3; ++d) rs[d] = gs[GEO_C + d] + gs[GEO_RHO + 3 * sq + d];
+      const double dx = r[0] - rs[0], dy = r[1] - rs[1];
+      const double rho = sqrt(dx * dx + dy * dy);
+      const double zz = r[2], zp = rs[2];
+      // quasistatic images
+      cx G1 = mk(0), G2 = mk(0);
+      if (S.top) {
+        const double R = sqrt(rho * rho + (2 * S.zu - zz - zp) * (2 * S.zu - zz - zp));
+        G1 = (inv4pi / R) * cexp_(mk(0, -R) * k);
+      }
+      if (S.bot) {
+        const double R = sqrt(rho * rho + (zz + zp - 2 * S.zb) * (zz + zp - 2 * S.zb));
+        G2 = (inv4pi / R) * cexp_(mk(0, -R) * k);
+      }
+      const cx gue = {Q.gue.r, Q.gue.i}, guh = {Q.guh.r, Q.guh.i}, gde = {Q.gde.r, Q.gde.i}, gdh = {Q.gdh.r, Q.gdh.i};
+      cx gxx = mur * (guh * G1 + gdh * G2);
+      cx gphi = (gue * G1 + gde * G2) / epsl;
+      cx gzz = mur * ((guh - 2.0 * gue) * G1 + (gdh - 2.0 * gde) * G2);
+      // tabulated remainder
+      const double lr = log(fmax(rho, exp(T.lr0)));
+      const double fx = (lr - T.lr0) / (T.lr1 - T.lr0) * (T.nr - 1);
+      const double fs = (zz + zp - T.s0) / (T.s1 - T.s0) * (T.ns - 1);
+      const double dd = zz - zp;
+      const double fd = T.d1 > 0 ? fabs(dd) / T.d1 * (T.nd - 1) : 0.0;
+      const double sg = dd > 0 ? 1.0 : (dd < 0 ? -1.0 : 0.0);
+      gxx = gxx + bilin(T.A, T.nr, T.ns, fx, fs, 0) + bilin(T.B, T.nr, T.nd, fx, fd, 0);
+      gphi = gphi + bilin(T.A, T.nr, T.ns, fx, fs, 1) + bilin(T.B, T.nr, T.nd, fx, fd, 1);
+      gzz = gzz + bilin(T.A, T.nr, T.ns, fx, fs, 2) + bilin(T.B, T.nr, T.nd, fx, fd, 2);
+      const cx gzr = bilin(T.A, T.nr, T.ns, fx, fs, 3) + sg * bilin(T.B, T.nr, T.nd, fx, fd, 3);
+      const cx grz = bilin(T.A, T.nr, T.ns, fx, fs, 4) + sg * bilin(T.B, T.nr, T.nd, fx, fd, 4);
+      const double hx = rho > 0 ? dx / rho : 0.0, hy = rho > 0 ? dy / rho : 0.0;
+      const double w = gs[GEO_W + sq];
+      for (int j = 0; j < 3; ++j) {
+        double fj[3];
+        for (int d = 0; d < 3; ++d) fj[d] = gs[GEO_SIG + j] * (gs[GEO_RHO + 3 * sq + d] + gs[GEO_AV + 3 * j + d]);
+        const double rf = hx * fj[0] + hy * fj[1];
+        // T . f_j: x,y: gxx f_t + grz rhohat f_z ; z: gzz f_z + gzr (rhohat . f_t)
+        V[j][0] = V[j][0] + w * (fj[0] * gxx + (hx * fj[2]) * grz);
+        V[j][1] = V[j][1] + w * (fj[1] * gxx + (hy * fj[2]) * grz);
+        V[j][2] = V[j][2] + w * (fj[2] * gzz + rf * gzr);
+      }
+      sphi = sphi + w * gphi;
+    }
+    const double wq = gt[GEO_W + q];
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) loc[3 * i + j] = loc[3 * i + j] + wq * (f[i][0] * V[j][0] + f[i][1] * V[j][1] + f[i][2] * V[j][2]);
+    lp = lp + wq * sphi;
+  }
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      C* dst = LA + int64_t(tri_edge[3 * t + i]) * ldA + tri_edge[3 * sidx + j];
+      if (sizeof(dst->x) == 4) {
+        atomicAdd(reinterpret_cast<float2*>(dst), make_float2(float(loc[3 * i + j].r), float(loc[3 * i + j].i)));
+      } else {
+        atomicAdd(reinterpret_cast<double*>(dst), loc[3 * i + j].r);
+        atomicAdd(reinterpret_cast<double*>(dst) + 1, loc[3 * i + j].i);
+      }
+    }
+  const double sc = 1.0 / (gt[GEO_A] * gs[GEO_A]);
+  C* dp = LP + int64_t(t) * ldP + sidx;
+  dp->x = decltype(dp->x)(double(dp->x) + sc * lp.r);
+  dp->y = decltype(dp->y)(double(dp->y) + sc * lp.i);
+}
+
+template <class C>
+void mgf_fill_reflected(const sldm_mesh* m, const MgfStackHost& H, double omega, const MgfTables& T, void* LA, int64_t ldA,
+                        void* LP, int64_t ldP, cudaStream_t s) {
+  const DevStack S = dev_stack(H, omega);
+  TabView tv{T.A.p, T.B.p, T.nr, T.ns, T.nd, T.lr0, T.lr1, T.s0, T.s1, T.d1};
+  const int nt = int(m->h.nt);
+  const int64_t np = int64_t(nt) * nt;
+  ScopedTimer tm("fill_reflected", s);
+  fill_reflected_kernel<C><<<unsigned((np + 127) / 128), 128, 0, s>>>(nt, m->d.geo.p, m->d.tri_edge.p, S, T.Q, tv, (C*)LA, ldA,
+                                                                      (C*)LP, ldP);
+  SLDM_CUDA(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------- stack helpers (host)
+MgfStatic mgf_static(const MgfStackHost& H) {
+  MgfStatic Q{};
+  const int L = int(H.eps.size()), l = H.l;
+  const std::complex<double> el = H.eps[l];
+  const double ml = H.mu[l];
+  auto pair = [&](int j, std::complex<double>* ge, double* gh) {
+    *ge = (el - H.eps[j]) / (el + H.eps[j]);
+    *gh = (H.mu[j] - ml) / (H.mu[j] + ml);
+  };
+  std::complex<double> gue = 0, gde = 0;
+  double guh = 0, gdh = 0;
+  if (l > 0) pair(l - 1, &gue, &guh);
+  if (l < L - 1) pair(l + 1, &gde, &gdh);
+  else if (H.pec) {
+    gde = -1.0;
+    gdh = -1.0;
+  }
+  Q.gue = {gue.real(), gue.imag()};
+  Q.gde = {gde.real(), gde.imag()};
+  Q.guh = {guh, 0.0};
+  Q.gdh = {gdh, 0.0};
+  return Q;
+}
+
+// Normal-incidence plane wave through the stack: E_x = a e^{+j k (z - zref)} + c e^{-j k (z - zref)} in layer l.
+void mgf_plane_wave_normal(const MgfStackHost& H, const std::vector<double>& thick, double z_top, double omega,
+                           std::complex<double>* a_out, std::complex<double>* c_out, std::complex<double>* k_out,
+                           double* zref_out) {
+  typedef std::complex<double> C;
+  const int L = int(H.eps.size());
+  const double k0 = omega / C0_;
+  std::vector<C> ks(L), eta(L), down(L);
+  std::vector<bool> finite(L);
+  for (int i = 0; i < L; ++i) {
+    ks[i] = k0 * std::sqrt(H.eps[i] * H.mu[i]);
+    eta[i] = std::sqrt(H.mu[i] / H.eps[i]);
+    finite[i] = i > 0 && (H.pec || i < L - 1);
+  }
+  down[L - 1] = H.pec ? C(-1) : C(0);
+  for (int i = L - 2; i >= 0; --i) {
+    const C f = (eta[i + 1] - eta[i]) / (eta[i + 1] + eta[i]);
+    const C ph = finite[i + 1] ? down[i + 1] * std::exp(C(0, -2) * ks[i + 1] * thick[i + 1]) : C(0);
+    down[i] = (f + ph) / (C(1) + f * ph);
+  }
+  C a = std::exp(C(0, 1) * k0 * z_top), c = a * down[0];
+  C v = a + c;
+  for (int i = 1; i <= H.l; ++i) {
+    const C gtop = finite[i] ? down[i] * std::exp(C(0, -2) * ks[i] * thick[i]) : C(0);
+    a = v / (C(1) + gtop);
+    c = a * gtop;
+    if (finite[i]) v = a * std::exp(C(0, -1) * ks[i] * thick[i]) + c * std::exp(C(0, 1) * ks[i] * thick[i]);
+  }
+  *a_out = a;
+  *c_out = c;
+  *k_out = ks[H.l];
+  *zref_out = H.l == 0 ? z_top : H.zu;
+}
+
+template void mgf_fill_reflected<float2>(const sldm_mesh*, const MgfStackHost&, double, const MgfTables&, void*, int64_t, void*,
+                                         int64_t, cudaStream_t);
+template void mgf_fill_reflected<double2>(const sldm_mesh*, const MgfStackHost&, double, const MgfTables&, void*, int64_t, void*,
+                                          int64_t, cudaStream_t);
+
+}  // namespace sldm

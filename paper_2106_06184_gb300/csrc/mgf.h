@@ -1,0 +1,46 @@
+// Layered-medium Green's function tables and reflected fill (mgf.cu).
+#pragma once
+#include <complex>
+
+#include "internal.h"
+
+namespace sldm {
+
+constexpr int MGF_MAX_LAYERS = 8;
+constexpr int MGF_N_ELLIPSE = 400;  // Gauss points on the elliptic arc of the Sommerfeld path
+constexpr int MGF_PER_PANEL = 16;   // Gauss points per real-axis panel
+constexpr int MGF_NR = 256, MGF_NS = 128, MGF_ND = 128;
+
+// Quasistatic (k_rho -> infinity) reflection coefficients of layer l: e (TM) and h (TE), up and down.
+struct MgfStatic {
+  struct {
+    double r, i;
+  } gue, guh, gde, gdh;
+};
+
+// Stack as seen from layer l at one frequency.
+struct MgfStackHost {
+  std::vector<std::complex<double>> eps;  // complex relative permittivity per layer
+  std::vector<double> mu, d;              // relative permeability, thickness (finite layers)
+  int l = 0, pec = 0;
+  double zb = -1e300, zu = 1e300;         // bounds of layer l
+  int top = 0, bot = 0;                   // interfaces above / below layer l exist
+};
+
+struct MgfTables {
+  DBuf<double2> A, B;  // [5][nr][ns], [5][nr][nd]
+  int nr = 0, ns = 0, nd = 0;
+  double lr0 = 0, lr1 = 0, s0 = 0, s1 = 0, d1 = 0;
+  MgfStatic Q{};
+};
+
+MgfStatic mgf_static(const MgfStackHost& H);
+void mgf_build_tables(const MgfStackHost& H, double omega, double rho_min, double rho_max, double zmin, double zmax,
+                      MgfTables& T, cudaStream_t s);
+template <class C>
+void mgf_fill_reflected(const sldm_mesh* m, const MgfStackHost& H, double omega, const MgfTables& T, void* LA, int64_t ldA,
+                        void* LP, int64_t ldP, cudaStream_t s);
+void mgf_plane_wave_normal(const MgfStackHost& H, const std::vector<double>& thick, double z_top, double omega,
+                           std::complex<double>* a, std::complex<double>* c, std::complex<double>* k, double* zref);
+
+}  // namespace sldm

@@ -74,6 +74,7 @@ EXPORTS = {
     "sldm_op_block": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_int32,
                                 C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "sldm_op_destroy": (C.c_int, [C.c_void_p]),
+    "sldm_op_table": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
     "sldm_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p]),
     "sldm_rhs_planewave": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_int32,
                                      C.c_void_p]),
@@ -255,6 +256,15 @@ class Operator:
         self.L.check(self.L.lib.sldm_op_block(self.h, which, obj, out.ctypes.data_as(C.c_void_p), HOST,
                                               C.byref(r), C.byref(c)))
         return out
+
+    def table(self, which):
+        """Remainder table of a layered operator: (array (5, nr, n2), grid (5,))."""
+        dims = (C.c_int64 * 3)()
+        grid = (C.c_double * 5)()
+        self.L.check(self.L.lib.sldm_op_table(self.h, which, None, dims, grid))
+        out = np.zeros(tuple(dims), np.complex128)
+        self.L.check(self.L.lib.sldm_op_table(self.h, which, out.ctypes.data_as(C.c_void_p), dims, grid))
+        return out, np.array(list(grid))
 
     def apply(self, x, y, nrhs=1, stream=None):
         px, wx = _ptr(x)
