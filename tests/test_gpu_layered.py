@@ -4,8 +4,11 @@ stack-transferred plane wave and the solution.
 
 Both sides integrate the same Sommerfeld path (elliptic arc + Gauss-Legendre
 panels, same node rule) with their own Bessel functions and summation order, so
-the tables and the blocks built from them agree to 1e-9 of their largest entry;
-everything else matches the homogeneous path's 1e-10.
+the tables agree to 1e-9 of their largest entry.  The TM - TE difference of the
+scalar-potential kernel cancels as k_rho -> 0, which leaves rounding noise of
+about 1e-10 of the kernel in a table that should vanish (PEC ground), so the
+blocks built from the tables are compared at 3e-9; everything else matches the
+homogeneous path's 1e-10.
 """
 import numpy as np
 import pytest
@@ -64,7 +67,7 @@ def test_layered_blocks_and_solution(which, request):
     c = request.getfixturevalue(which)
     sl, m, st, op = c.gpu(0)
     A = c.A
-    for name, got, ref, tol in (("LAm", op.block(sl.BLOCK_LAM), A.LAm, 1e-9), ("LPm", op.block(sl.BLOCK_LPM), A.LPm, 1e-9),
+    for name, got, ref, tol in (("LAm", op.block(sl.BLOCK_LAM), A.LAm, 3e-9), ("LPm", op.block(sl.BLOCK_LPM), A.LPm, 3e-9),
                                 ("Y11", op.block(sl.BLOCK_Y11), A.blocks[0]["Y11"], 1e-10),
                                 ("K", op.block(sl.BLOCK_K), A.blocks[0]["K"], 1e-10)):
         assert relmax(got, ref) < tol and rel(got, ref) < tol, (name, relmax(got, ref))
