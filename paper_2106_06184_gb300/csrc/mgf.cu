@@ -72,6 +72,7 @@ __device__ void bessel01_complex(cx z, cx* j0, cx* j1) {
     auto ccos = [](cx w) {
       double sa, ca;
       sincos(w.r, &sa, &ca);
+      if (w.i == 0.0) return cx{ca, 0.0};
       return cx{ca * cosh(w.i), -sa * sinh(w.i)};
     };
     s0 = s0 + ccos(-ph);
@@ -217,13 +218,9 @@ __global__ void mgf_bessel_kernel(const double2* __restrict__ nodes, int nnodes,
   const int i = int(idx / nnodes), n = int(idx % nnodes);
   const double2 k = nodes[n];
   cx j0, j1;
-  if (k.y == 0.0) {
-    const double x = k.x * rho[i];
-    j0 = mk(::j0(x));
-    j1 = mk(::j1(x));
-  } else {
-    bessel01_complex(mk(k.x * rho[i], k.y * rho[i]), &j0, &j1);
-  }
+  // real and complex arguments alike: the periodic trapezoid rule is accurate to
+  // rounding for any argument once it has 2(|z| + 40) points
+  bessel01_complex(mk(k.x * rho[i], k.y * rho[i]), &j0, &j1);
   Jm[int64_t(i) * nnodes + n] = make_double2(j0.r, j0.i);
   Jm[int64_t(nr) * nnodes + int64_t(i) * nnodes + n] = make_double2(j1.r, j1.i);
 }
