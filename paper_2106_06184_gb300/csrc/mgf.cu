@@ -44,12 +44,13 @@ __device__ __forceinline__ cx cexp_(cx a) {
   const double e = exp(a.r);
   return {e * c, e * s};
 }
+// principal square root without cancellation: the larger of |Re|, |Im| comes
+// from sqrt((|a| + |Re a|)/2), the other from Im a / (2 that)
 __device__ __forceinline__ cx csqrt_(cx a) {
-  const double m = sqrt(a.r * a.r + a.i * a.i);
-  double re = sqrt(fmax(0.5 * (m + a.r), 0.0));
-  double im = sqrt(fmax(0.5 * (m - a.r), 0.0));
-  if (a.i < 0) im = -im;
-  return {re, im};
+  if (a.r == 0.0 && a.i == 0.0) return {0.0, 0.0};
+  const double t = sqrt(0.5 * (hypot(a.r, a.i) + fabs(a.r)));
+  if (a.r >= 0.0) return {t, a.i / (2.0 * t)};
+  return {fabs(a.i) / (2.0 * t), a.i < 0 ? -t : t};
 }
 // k_z = sqrt(k^2 - k_rho^2) with Im k_z <= 0
 __device__ __forceinline__ cx kz_of(cx k, cx kr) {
