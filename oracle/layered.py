@@ -333,16 +333,23 @@ def _bilinear(tab, xg, yg, x, y):
 
 
 def remainder(T: Tables, rho, z, zp):
-    """Interpolated remainder kernels {component: array} at (rho, z, z')."""
+    """Interpolated remainder kernels {component: array} at (rho, z, z').
+
+    Below the first table point the S0 kernels keep their value at rho_min, and the
+    S1 kernels (z-rho, rho-z), which vanish linearly at rho = 0 (J1(0) = 0), are
+    scaled by rho / rho_min."""
     lr = np.log(np.maximum(rho, T.rho[0]))
     lg = np.log(T.rho)
     s = z + zp
     dd = z - zp
+    lin = np.minimum(rho / T.rho[0], 1.0)
     out = {}
     for c in COMPONENTS:
         a = _bilinear(T.A[c], lg, T.s, lr, s)
         b = _bilinear(T.B[c], lg, T.d, lr, np.abs(dd))
         out[c] = a + (np.sign(dd) * b if ODD_IN_D.get(c) else b)
+        if ORDER[c] == 1:
+            out[c] = out[c] * lin
     return out
 
 

@@ -468,8 +468,10 @@ __global__ void __launch_bounds__(128) fill_reflected_kernel(int nt, const doubl
       gxx = gxx + bilin(T.A, T.nr, T.ns, fx, fs, 0) + bilin(T.B, T.nr, T.nd, fx, fd, 0);
       gphi = gphi + bilin(T.A, T.nr, T.ns, fx, fs, 1) + bilin(T.B, T.nr, T.nd, fx, fd, 1);
       gzz = gzz + bilin(T.A, T.nr, T.ns, fx, fs, 2) + bilin(T.B, T.nr, T.nd, fx, fd, 2);
-      const cx gzr = bilin(T.A, T.nr, T.ns, fx, fs, 3) + sg * bilin(T.B, T.nr, T.nd, fx, fd, 3);
-      const cx grz = bilin(T.A, T.nr, T.ns, fx, fs, 4) + sg * bilin(T.B, T.nr, T.nd, fx, fd, 4);
+      // the S1 (z-rho, rho-z) kernels vanish linearly at rho = 0: below rho_min scale by rho / rho_min
+      const double lin = fmin(rho * exp(-T.lr0), 1.0);
+      const cx gzr = lin * (bilin(T.A, T.nr, T.ns, fx, fs, 3) + sg * bilin(T.B, T.nr, T.nd, fx, fd, 3));
+      const cx grz = lin * (bilin(T.A, T.nr, T.ns, fx, fs, 4) + sg * bilin(T.B, T.nr, T.nd, fx, fd, 4));
       const double hx = rho > 0 ? dx / rho : 0.0, hy = rho > 0 ? dy / rho : 0.0;
       const double w = gs[GEO_W + sq];
       for (int j = 0; j < 3; ++j) {
