@@ -38,29 +38,62 @@ WORKLOADS = {
         mesh=lambda: icosphere(2, 0.1), obj=None, mats=[(4.0, 1.0, 0.0)], bg=(1.0, 1.0, 0.0, 0.0), freq=300e6,
         precision=0, tol=1e-8, khat=[0.0, 0.0, -1.0], pol=[1.0, 0.0, 0.0], n_angles=181),
 }
-# 8 x 8 dielectric cylinders (eps_r 6, r 120 nm, h 300 nm, period 500 nm, 240 triangles
-# each: 15,360 triangles, N = 61,376) in free space at 1 um, complex FP32 operator
-# (FP64 singular terms), one plane wave at normal incidence
-WORKLOADS["metasurface-8x8-cyl-epsr6-1um-freespace-c64"] = dict(
-    mesh=lambda: cylinder_array(8, 8, 120e-9, 300e-9, 500e-9)[:2], obj="array8", mats=[(6.0, 1.0, 0.0)] * 64,
-    bg=(1.0, 1.0, 0.0, 0.0), freq=299792458.0 / 1e-6, precision=1, tol=1e-5, khat=[0.0, 0.0, -1.0],
-    pol=[1.0, 0.0, 0.0], n_angles=181)
+# n x n dielectric cylinders (eps_r 6, r 120 nm, h 300 nm, period 500 nm, 240 triangles
+# each) in free space at 1 um, complex FP32 operator (FP64 singular terms), one plane
+# wave at normal incidence.  8 x 8: 15,360 triangles, N = 61,376; 4 x 4 is the small
+# case kept for profiling captures (global blocks 383 MB, above the L2 size).
+for _n in (8, 4):
+    WORKLOADS[f"metasurface-{_n}x{_n}-cyl-epsr6-1um-freespace-c64"] = dict(
+        mesh=(lambda n=_n: cylinder_array(n, n, 120e-9, 300e-9, 500e-9)[:2]), obj=("array", _n),
+        mats=[(6.0, 1.0, 0.0)] * (_n * _n), bg=(1.0, 1.0, 0.0, 0.0), freq=299792458.0 / 1e-6, precision=1,
+        tol=1e-5, khat=[0.0, 0.0, -1.0], pol=[1.0, 0.0, 0.0], n_angles=181)
 DEFAULT_WORKLOAD = "sphere-r0.1-epsr4-sub2-300MHz-fp64"
 
 
 def _obj_ids(W):
-    if W["obj"] == "array8":
-        return cylinder_array(8, 8, 120e-9, 300e-9, 500e-9)[2]
+    if isinstance(W["obj"], tuple) and W["obj"][0] == "array":
+        n = W["obj"][1]
+        return cylinder_array(n, n, 120e-9, 300e-9, 500e-9)[2]
     return W["obj"]
 
 L2_FLUSH_BYTES = 512 << 20  # larger than the 129 MB L2
 
 # Roofline denominators: MEASURED_PEAKS.json when present, else the recorded
 # fallback measurement.  ALU peaks derive from unit counts x maximum SM clock:
-# FP32: 152 SMs x 128 lanes x 2 flop x 2.07 GHz; FP64: the part's nominal rate.
+# FP32: 152 SMs x 128 lanes x 2 flop x 2.07 GHz; FP64: 152 SMs x 2 FMA x 2 flop x 2.07 GHz
+# (1.26 TFLOP/s, the part's nominal 1.25).
 FALLBACK_HBM_GBS = 6800.0
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-FP64_PEAK_TFLOPS = 1.25
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+# DRAM traffic per algorithmic byte of the HBM-streaming GEMV stage, from one
+# ncu capture (dram__bytes_read.sum + dram__bytes_write.sum of the gemv_main
+# launch, 4 x 4 metasurface, 423,936,000 algorithmic bytes per launch; summary in
+# profiles/gemv_main_metasurface-4x4-c64.md), valid while the kernel source is
+# unchanged (sha256 prefix of the kernel's text in dense.cu).
+GEMV_TRAFFIC = dict(sha="77ea3d80e5b34126", per_alg_byte=(424.172288e6 + 2.975232e6) / 423.936e6)
+
+
+def gemv_kernel_sha():
+    import hashlib
+    s = open(os.path.join(ROOT, "paper_2106_06184_gb300", "csrc", "dense.cu")).read()
+    a = s.index("// ---------------------------------------------------------------- batched skinny GEMV")
+    b = s.index("template <class C>\nvoid gemv_jobs(")
+    return hashlib.sha256(s[a:b].encode()).hexdigest()[:16]
+
+
+def lu_flops(obj_sizes):
+    """Real flops of the batched direct solves of one assembly: per object the LU of
+    M_l (n = N_e^o + N_t^o - 1) with its N_e^o right-hand sides, and the inverse of
+    the preconditioner's Schur complement (n = N_t^o - 1, n right-hand sides).
+    Complex LU: n^3/3 multiply-adds; forward plus back substitution: n^2 per
+    right-hand side; 8 real flops per complex multiply-add."""
+    f = 0.0
+    for ne_o, nt_o in obj_sizes:
+        for n, r in ((ne_o + nt_o - 1, ne_o), (nt_o - 1, nt_o - 1)):
+            f += 8.0 * (n ** 3 / 3.0 + n * n * r)
+    return f
 
 
 def peaks():
@@ -179,6 +212,7 @@ def run_ours(args, rank, world):
     sldm.timers_reset()
     sldm.timers_enable(True)
     times, iters, relres = [], [], []
+    launches0 = sldm.launch_count()
     t_wall0 = time.perf_counter()
     for _ in range(args.steps):
         flush.zero_()
@@ -193,6 +227,7 @@ def run_ours(args, rank, world):
         relres.append(info["relres"])
         del op
     t_wall = time.perf_counter() - t_wall0
+    launches = sldm.launch_count() - launches0
     sldm.timers_enable(False)
     timers = sldm.timers_read()
     clk = clocks.stop()
@@ -243,6 +278,10 @@ def run_ours(args, rank, world):
         s1, s2 = gemv_split(ne, nt, obj_sizes, W_esz)
         achieved = s2 / (ms / cnt / 1e3) / 1e9
         cand["gemv_main"] = dict(bound="hbm", achieved=achieved, peak=hbm, unit="GB/s", ms=ms, bytes_per_launch=s2)
+    if "lu_coop" in timers and W["precision"] == 0:
+        ms = timers["lu_coop"][0] / args.steps
+        cand["lu_coop"] = dict(bound="alu", achieved=lu_flops(obj_sizes) / (ms / 1e3) / 1e12, peak=FP64_PEAK_TFLOPS,
+                               unit="TFLOP/s", ms=timers["lu_coop"][0], flops_per_step=lu_flops(obj_sizes))
     for k in ("fill_K_bulk", "fill_L_bulk", "lu_coop", "fill_K_touch", "fill_L_touch"):
         if k in timers and k not in cand:
             cand[k] = dict(bound="alu", achieved=None, peak=FP64_PEAK_TFLOPS if W["precision"] == 0 else FP32_PEAK_TFLOPS,
@@ -258,9 +297,11 @@ def run_ours(args, rank, world):
                 "frac": (c["achieved"] / c["peak"]) if c["achieved"] is not None else None,
                 "peak_source": hbm_src if c["bound"] == "hbm" else "derived",
                 "traffic": None, "share_of_step": timers[dom][0] / total_ms if world == 1 else None,
-                "algorithmic_unit": c.get("bytes_per_launch")}
+                "algorithmic_unit": c.get("bytes_per_launch") or c.get("flops_per_step")}
+        if dom == "gemv_main" and gemv_kernel_sha() == GEMV_TRAFFIC["sha"]:
+            roof["traffic"] = GEMV_TRAFFIC["per_alg_byte"] * c["bytes_per_launch"]
+            roof["traffic_source"] = "ncu capture of the 4x4 case, scaled by algorithmic bytes"
     kernel_ms = {k: round(v[0] / args.steps, 4) for k, v in sorted(timers.items(), key=lambda kv: -kv[1][0])}
-    launches = sum(v[1] for k, v in timers.items() if k != "apply")
     out = {
         "metric": "solves/s (assemble + RHS + GMRES to the stated relative residual + RCS, one plane wave)",
         "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -274,7 +315,7 @@ def run_ours(args, rank, world):
         "gmres": {"iters": int(np.median(iters)), "relres_max": float(max(relres))},
         "roofline": roof,
         "kernel_ms_per_step": kernel_ms,
-        "gpu_launches": int(launches / args.steps * args.steps),
+        "gpu_launches": int(launches),
         "clocks": clk,
         "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "latency_ms_p50": 1e3 * statistics.median(e2e_times) if e2e_times else None},

@@ -265,6 +265,10 @@ int sldm_timers_reset(void);
 int sldm_timer_get(const char* name, double* total_ms, int64_t* count);
 /* Comma-separated names with recorded launches, NUL-terminated, truncated to len. */
 int sldm_timer_names(char* buf, size_t len);
+/* Number of kernel launches the library has made in this process (every
+ * kernel, timed or not), for counting the launches of a timed region.
+ * The paper has no counterpart.  SLDM_EINVAL if out is NULL. */
+int sldm_launch_count(int64_t* out);
 
 #ifdef __cplusplus
 }

@@ -93,9 +93,9 @@ void build_Ml(const sldm_mesh* m, int obj, double k0, const void* LAm, int64_t l
   int t0 = h.tri_begin[obj], nt_o = h.tri_begin[obj + 1] - t0;
   int n = ne_o + nt_o - 1;
   build_Ml_kernel<C><<<dim3((n + 127) / 128, n), 128, 0, s>>>(ne_o, nt_o, e0, t0, k0, h.ell, (const C*)LAm, ldLA, (const C*)LPm,
-                                                              ldLP, m->d.tplus.p, m->d.tminus.p, Ml);
+                                                              ldLP, m->d.tplus.p, m->d.tminus.p, Ml), ::sldm::count_launch();
   build_Rl_kernel<C><<<dim3((ne_o + 127) / 128, n), 128, 0, s>>>(ne_o, nt_o, e0, (const C*)Kl, ldK, m->d.ix_ptr.p,
-                                                                 m->d.ix_col.p, ix_val, Rl);
+                                                                 m->d.ix_col.p, ix_val, Rl), ::sldm::count_launch();
   SLDM_CUDA(cudaGetLastError());
 }
 
@@ -481,6 +481,7 @@ void lu_solve_batched(const std::vector<LUSysT<C>>& systems, cudaStream_t s) {
   {
     ScopedTimer tm("lu_coop", s);
     SLDM_CUDA(cudaLaunchCooperativeKernel((void*)lu_coop_kernel<C>, dim3(G), dim3(LU_THREADS), args, smem, s));
+    count_launch();
   }
   int herr = 0;
   SLDM_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -598,11 +599,11 @@ void gemv_jobs(const GemvPlan& plan, int nrhs, cudaStream_t s) {
   const unsigned blocks = unsigned((threads + 255) / 256);
   ScopedTimer tm(plan.name, s);
   if (nrhs <= 1)
-    gemv_jobs_kernel<C, 1><<<blocks, 256, 0, s>>>(plan.jobs, plan.rowstart, plan.njobs, plan.total_rows, nrhs);
+    gemv_jobs_kernel<C, 1><<<blocks, 256, 0, s>>>(plan.jobs, plan.rowstart, plan.njobs, plan.total_rows, nrhs), ::sldm::count_launch();
   else if (nrhs <= 4)
-    gemv_jobs_kernel<C, 4><<<blocks, 256, 0, s>>>(plan.jobs, plan.rowstart, plan.njobs, plan.total_rows, nrhs);
+    gemv_jobs_kernel<C, 4><<<blocks, 256, 0, s>>>(plan.jobs, plan.rowstart, plan.njobs, plan.total_rows, nrhs), ::sldm::count_launch();
   else
-    gemv_jobs_kernel<C, 8><<<blocks, 256, 0, s>>>(plan.jobs, plan.rowstart, plan.njobs, plan.total_rows, nrhs);
+    gemv_jobs_kernel<C, 8><<<blocks, 256, 0, s>>>(plan.jobs, plan.rowstart, plan.njobs, plan.total_rows, nrhs), ::sldm::count_launch();
   SLDM_CUDA(cudaGetLastError());
 }
 
@@ -733,7 +734,7 @@ __global__ void combine_kernel(const ApplyDims D, double k0, const int32_t* __re
 template <class C>
 void apply_glue_split(const double2* x, int64_t ldx, const ApplyDims& D, void* j, void* e, void* u, int nrhs, cudaStream_t s) {
   int64_t N = 2 * D.ne + D.nq;
-  split_in_kernel<C><<<dim3(unsigned((N + 255) / 256), nrhs), 256, 0, s>>>(x, ldx, D.ne, D.nq, (C*)j, (C*)e, (C*)u, nrhs);
+  split_in_kernel<C><<<dim3(unsigned((N + 255) / 256), nrhs), 256, 0, s>>>(x, ldx, D.ne, D.nq, (C*)j, (C*)e, (C*)u, nrhs), ::sldm::count_launch();
   SLDM_CUDA(cudaGetLastError());
 }
 
@@ -742,7 +743,7 @@ void apply_glue_prep(const sldm_mesh* m, const ApplyDims& D, const void* j, cons
                      void* a, void* c, void* bc, void* bu, int nrhs, cudaStream_t s, const int32_t* tri_begin_dev,
                      const int32_t* edge_begin_dev) {
   prep_kernel<C><<<dim3(unsigned(D.nobj), nrhs), 256, 0, s>>>(D, tri_begin_dev, edge_begin_dev, (const C*)j, (const C*)u,
-                                                             (const C*)t1, (const C*)t2, (C*)a, (C*)c, (C*)bc, (C*)bu);
+                                                             (const C*)t1, (const C*)t2, (C*)a, (C*)c, (C*)bc, (C*)bu), ::sldm::count_launch();
   SLDM_CUDA(cudaGetLastError());
 }
 
@@ -754,7 +755,7 @@ void apply_glue_combine(const sldm_mesh* m, const ApplyDims& D, double k0, const
   const DevMesh& d = m->d;
   combine_kernel<C><<<dim3(unsigned((N + 255) / 256), nrhs), 256, 0, s>>>(
       D, k0, d.tplus.p, d.tminus.p, d.tri_edge.p, d.tri_sign.p, d.q2t.p, d.ix_ptr.p, d.ix_col.p, ix_val, (const C*)z1,
-      (const C*)z2, (const C*)w1, (const C*)w2, (const C*)w3, (const C*)e, (const C*)a, (const C*)c, y, ldy);
+      (const C*)z2, (const C*)w1, (const C*)w2, (const C*)w3, (const C*)e, (const C*)a, (const C*)c, y, ldy), ::sldm::count_launch();
   SLDM_CUDA(cudaGetLastError());
 }
 
@@ -847,26 +848,26 @@ __global__ void vscale3_kernel(int64_t n, int64_t ne, double s1, double s2, doub
 }
 
 void vscale3(int64_t n, int64_t ne, double s1, double s2, double s3, const double2* x, double2* y, cudaStream_t s) {
-  vscale3_kernel<<<unsigned((n + 255) / 256), 256, 0, s>>>(n, ne, s1, s2, s3, x, y);
+  vscale3_kernel<<<unsigned((n + 255) / 256), 256, 0, s>>>(n, ne, s1, s2, s3, x, y), ::sldm::count_launch();
   SLDM_CUDA(cudaGetLastError());
 }
 
 void vdots(const double2* V, int64_t ldv, int k, const double2* w, int64_t n, double2* h, cudaStream_t s) {
-  dots_kernel<<<k, 256, 0, s>>>(V, ldv, w, n, h);
+  dots_kernel<<<k, 256, 0, s>>>(V, ldv, w, n, h), ::sldm::count_launch();
   SLDM_CUDA(cudaGetLastError());
 }
 void vmul(const double2* V, int64_t ldv, int k, const double2* h, double sign, double2* w, int64_t n, cudaStream_t s) {
-  vmul_kernel<<<unsigned((n + 31) / 32), 256, 0, s>>>(V, ldv, k, h, sign, w, n);
+  vmul_kernel<<<unsigned((n + 31) / 32), 256, 0, s>>>(V, ldv, k, h, sign, w, n), ::sldm::count_launch();
   SLDM_CUDA(cudaGetLastError());
 }
 void vnorm2(const double2* w, int64_t n, double* out, cudaStream_t s) {
   SLDM_CUDA(cudaMemsetAsync(out, 0, sizeof(double), s));
   unsigned b = unsigned(std::min<int64_t>((n + 255) / 256, 1024));
-  norm2_kernel<<<b, 256, 0, s>>>(w, n, out);
+  norm2_kernel<<<b, 256, 0, s>>>(w, n, out), ::sldm::count_launch();
   SLDM_CUDA(cudaGetLastError());
 }
 void vaxpby(int64_t n, double alpha, const double2* x, double beta, double2* y, cudaStream_t s) {
-  axpby_kernel<<<unsigned((n + 255) / 256), 256, 0, s>>>(n, alpha, x, beta, y);
+  axpby_kernel<<<unsigned((n + 255) / 256), 256, 0, s>>>(n, alpha, x, beta, y), ::sldm::count_launch();
   SLDM_CUDA(cudaGetLastError());
 }
 
@@ -886,12 +887,12 @@ __global__ void from_c128_kernel(const double2* __restrict__ src, int64_t n, C* 
 }
 template <class C>
 void to_c128(const void* src, int64_t n, double2* dst, cudaStream_t s) {
-  to_c128_kernel<C><<<unsigned((n + 255) / 256), 256, 0, s>>>((const C*)src, n, dst);
+  to_c128_kernel<C><<<unsigned((n + 255) / 256), 256, 0, s>>>((const C*)src, n, dst), ::sldm::count_launch();
   SLDM_CUDA(cudaGetLastError());
 }
 template <class C>
 void from_c128(const double2* src, int64_t n, void* dst, cudaStream_t s) {
-  from_c128_kernel<C><<<unsigned((n + 255) / 256), 256, 0, s>>>(src, n, (C*)dst);
+  from_c128_kernel<C><<<unsigned((n + 255) / 256), 256, 0, s>>>(src, n, (C*)dst), ::sldm::count_launch();
   SLDM_CUDA(cudaGetLastError());
 }
 
@@ -911,7 +912,7 @@ __global__ void add_ix_kernel(int e0, int ne_o, double alpha, const int32_t* __r
 template <class C>
 void add_ix(const sldm_mesh* m, int obj, double alpha, const double* ix_val, void* K, int64_t ld, cudaStream_t s) {
   int e0 = m->h.edge_begin[obj], ne_o = m->h.edge_begin[obj + 1] - e0;
-  add_ix_kernel<C><<<(ne_o + 127) / 128, 128, 0, s>>>(e0, ne_o, alpha, m->d.ix_ptr.p, m->d.ix_col.p, ix_val, (C*)K, ld);
+  add_ix_kernel<C><<<(ne_o + 127) / 128, 128, 0, s>>>(e0, ne_o, alpha, m->d.ix_ptr.p, m->d.ix_col.p, ix_val, (C*)K, ld), ::sldm::count_launch();
   SLDM_CUDA(cudaGetLastError());
 }
 
@@ -928,7 +929,7 @@ __global__ void copy_scaled_kernel(const C* __restrict__ src, int64_t n, double 
 template <class C>
 void copy_scaled(const void* src, int64_t n, double alpha, void* dst, cudaStream_t s) {
   if (n <= 0) return;
-  copy_scaled_kernel<C><<<unsigned((n + 255) / 256), 256, 0, s>>>((const C*)src, n, alpha, (C*)dst);
+  copy_scaled_kernel<C><<<unsigned((n + 255) / 256), 256, 0, s>>>((const C*)src, n, alpha, (C*)dst), ::sldm::count_launch();
   SLDM_CUDA(cudaGetLastError());
 }
 

@@ -100,7 +100,7 @@ void geometry(const HostMesh& hm, DevMesh& dm, cudaStream_t s) {
   dm.bgeo.alloc(size_t(hm.nt) * 6 * GEO_STRIDE);
   int nt = int(hm.nt);
   geometry_kernel<<<(nt + 127) / 128, 128, 0, s>>>(nt, dm.xyz.p, dm.tri.p, dm.tri_edge.p, dm.tri_sign.p,
-                                                   dm.btri_sign.p, hm.nv, dm.geo.p, dm.bgeo.p);
+                                                   dm.btri_sign.p, hm.nv, dm.geo.p, dm.bgeo.p), ::sldm::count_launch();
   SLDM_CUDA(cudaGetLastError());
 }
 
@@ -813,7 +813,7 @@ void fill_L(const sldm_mesh* m, const std::vector<LTask>& tasks, cudaStream_t s)
   for (size_t off = 0; off < tiles.size(); off += 1u << 30) {
     unsigned nb = unsigned(std::min<size_t>(tiles.size() - off, 1u << 30));
     ScopedTimer tm("fill_L_bulk", s);
-    fill_L_bulk<R><<<nb, TILE_SRC, 0, s>>>(dt.p, dtl.p + off, d.geo.p, d.tri.p, d.tri_edge.p);
+    fill_L_bulk<R><<<nb, TILE_SRC, 0, s>>>(dt.p, dtl.p + off, d.geo.p, d.tri.p, d.tri_edge.p), ::sldm::count_launch();
   }
   SLDM_CUDA(cudaGetLastError());
   const int np = int(m->h.touchL_a.size());
@@ -822,7 +822,7 @@ void fill_L(const sldm_mesh* m, const std::vector<LTask>& tasks, cudaStream_t s)
   if (np > 0) {
     ScopedTimer tm("fill_L_touch", s);
     fill_L_touch<R><<<unsigned((int64_t(np) * 8 + 255) / 256), 256, 0, s>>>(dt.p, dot.p, d.obj.p, d.touchL_a.p, d.touchL_b.p, np,
-                                                                            d.geo.p, d.xyz.p, d.tri.p, d.tri_edge.p);
+                                                                            d.geo.p, d.xyz.p, d.tri.p, d.tri_edge.p), ::sldm::count_launch();
   }
   SLDM_CUDA(cudaGetLastError());
   SLDM_CUDA(cudaStreamSynchronize(s));  // task/tile buffers are released on return
@@ -843,7 +843,7 @@ void fill_K(const sldm_mesh* m, const std::vector<KTask>& tasks, cudaStream_t s)
   {
     ScopedTimer tm("fill_K_bulk", s);
     fill_K_bulk<R><<<unsigned(tiles.size()), TILE_SRC, 0, s>>>(dt.p, dtl.p, d.geo.p, d.bgeo.p, d.tri.p, d.tri_edge.p,
-                                                             d.btri_edge.p);
+                                                             d.btri_edge.p), ::sldm::count_launch();
   }
   SLDM_CUDA(cudaGetLastError());
   const int np = int(m->h.touchK_a.size());
@@ -853,7 +853,7 @@ void fill_K(const sldm_mesh* m, const std::vector<KTask>& tasks, cudaStream_t s)
     ScopedTimer tm("fill_K_touch", s);
     fill_K_touch<R><<<unsigned((int64_t(np) * 8 + 255) / 256), 256, 0, s>>>(dt.p, dot.p, d.obj.p, d.touchK_a.p, d.touchK_c.p, np,
                                                                             d.geo.p, d.bgeo.p, d.xyz.p, d.tri.p, d.tri_edge.p,
-                                                                            d.btri_edge.p);
+                                                                            d.btri_edge.p), ::sldm::count_launch();
   }
   SLDM_CUDA(cudaGetLastError());
   SLDM_CUDA(cudaStreamSynchronize(s));
@@ -887,7 +887,7 @@ void contract_bc(const sldm_mesh* m, int obj, const void* Kb, int64_t ldKb, void
   int e0 = h.edge_begin[obj], ne_o = h.edge_begin[obj + 1] - e0;
   int b0 = h.bedge_begin[obj];
   dim3 grid((ne_o + 127) / 128, ne_o);
-  contract_bc_kernel<R><<<grid, 128, 0, s>>>(ne_o, e0, b0, m->d.bc_ptr.p, m->d.bc_row.p, m->d.bc_val.p, Kb, ldKb, K, ldK);
+  contract_bc_kernel<R><<<grid, 128, 0, s>>>(ne_o, e0, b0, m->d.bc_ptr.p, m->d.bc_row.p, m->d.bc_val.p, Kb, ldKb, K, ldK), ::sldm::count_launch();
   SLDM_CUDA(cudaGetLastError());
 }
 
@@ -925,7 +925,7 @@ void gram_ix(const sldm_mesh* m, double* vals, cudaStream_t s) {
   int nnz = int(m->h.ix_col.size());
   const DevMesh& d = m->d;
   gram_kernel<<<(nnz + 127) / 128, 128, 0, s>>>(nnz, d.ixc_ptr.p, d.ixc_tri.p, d.ixc_child.p, d.ixc_i.p, d.ixc_j.p,
-                                                d.ixc_coef.p, d.geo.p, d.bgeo.p, vals);
+                                                d.ixc_coef.p, d.geo.p, d.bgeo.p, vals), ::sldm::count_launch();
   SLDM_CUDA(cudaGetLastError());
 }
 
@@ -1000,14 +1000,14 @@ void rhs_planewave_layered(const sldm_mesh* m, const double coef[7], const doubl
   int ne = int(m->h.ne);
   dim3 grid((ne + 127) / 128, nrhs);
   rhs_layered_kernel<<<grid, 128, 0, s>>>(ne, nrhs, coef[0], coef[1], coef[2], coef[3], coef[4], coef[5], coef[6], kp,
-                                          m->d.tplus.p, m->d.tminus.p, m->d.tri_edge.p, m->d.geo.p, b, ld);
+                                          m->d.tplus.p, m->d.tminus.p, m->d.tri_edge.p, m->d.geo.p, b, ld), ::sldm::count_launch();
   SLDM_CUDA(cudaGetLastError());
 }
 
 void rhs_planewave(const sldm_mesh* m, double k0, const double* kp, int nrhs, double2* b, int64_t ld, cudaStream_t s) {
   int ne = int(m->h.ne);
   dim3 grid((ne + 127) / 128, nrhs);
-  rhs_kernel<<<grid, 128, 0, s>>>(ne, nrhs, k0, kp, m->d.tplus.p, m->d.tminus.p, m->d.tri_edge.p, m->d.geo.p, b, ld);
+  rhs_kernel<<<grid, 128, 0, s>>>(ne, nrhs, k0, kp, m->d.tplus.p, m->d.tminus.p, m->d.tri_edge.p, m->d.geo.p, b, ld), ::sldm::count_launch();
   SLDM_CUDA(cudaGetLastError());
 }
 
@@ -1065,7 +1065,7 @@ __global__ void farfield_kernel(int nt, double k0, const double2* __restrict__ j
 }
 
 void farfield(const sldm_mesh* m, double k0, const double2* jd, const double* ang, int n, double* rcs, cudaStream_t s) {
-  farfield_kernel<<<n, 256, 0, s>>>(int(m->h.nt), k0, jd, m->d.tri_edge.p, m->d.geo.p, ang, rcs);
+  farfield_kernel<<<n, 256, 0, s>>>(int(m->h.nt), k0, jd, m->d.tri_edge.p, m->d.geo.p, ang, rcs), ::sldm::count_launch();
   SLDM_CUDA(cudaGetLastError());
 }
 
@@ -1255,16 +1255,16 @@ extern "C" int sldm_kbar_noalloc(const sldm_mesh* m, int32_t obj, double k_re, d
     // the block accumulates atomically: it must start at zero on every call
     SLDM_CUDA(cudaMemsetAsync(Kb, 0, nkb * sizeof(double2), s));
     const int nset = ntile_t * ntile_s;
-    noalloc_setup_kernel<<<(nset + 127) / 128, 128, 0, s>>>(t, ntile_t, ntile_s, dtask, dtiles);
+    noalloc_setup_kernel<<<(nset + 127) / 128, 128, 0, s>>>(t, ntile_t, ntile_s, dtask, dtiles), ::sldm::count_launch();
     SLDM_CUDA(cudaGetLastError());
     const DevMesh& d = m->d;
     fill_K_bulk<double><<<unsigned(nset), TILE_SRC, 0, s>>>(dtask, dtiles, d.geo.p, d.bgeo.p, d.tri.p, d.tri_edge.p,
-                                                            d.btri_edge.p);
+                                                            d.btri_edge.p), ::sldm::count_launch();
     SLDM_CUDA(cudaGetLastError());
     const int np = int(h.touchK_a.size());
     if (np > 0)
       fill_K_touch_one<<<(np + 127) / 128, 128, 0, s>>>(t, d.touchK_a.p, d.touchK_c.p, np, d.geo.p, d.bgeo.p, d.xyz.p,
-                                                        d.tri.p, d.tri_edge.p, d.btri_edge.p);
+                                                        d.tri.p, d.tri_edge.p, d.btri_edge.p), ::sldm::count_launch();
     SLDM_CUDA(cudaGetLastError());
     contract_bc<double>(m, obj, Kb, nbe_o, K_out, ne_o, s);
   } catch (const sldm::Error& e) {

@@ -33,6 +33,9 @@ struct Error {
 // Optional CUDA-event timing of named launches (sldm_timers_enable).  When
 // disabled, timer_begin/timer_end cost one branch.
 bool timers_on();
+// Counts kernel launches made by the library (sldm_launch_count); called right
+// after each launch statement.
+void count_launch();
 void timer_begin(const char* name, cudaStream_t s);
 void timer_end(cudaStream_t s);
 struct ScopedTimer {

@@ -339,10 +339,10 @@ static void build_one(const MgfStackHost& H, const MgfStatic& Q, double omega, c
   {
     ScopedTimer tm("mgf_tables", s);
     const int64_t tot = int64_t(nn) * na;
-    mgf_spectral_kernel<<<unsigned((tot + 127) / 128), 128, 0, s>>>(S, Q, dn.p, dw.p, nn, da.p, na, part, F.p);
+    mgf_spectral_kernel<<<unsigned((tot + 127) / 128), 128, 0, s>>>(S, Q, dn.p, dw.p, nn, da.p, na, part, F.p), ::sldm::count_launch();
     const int64_t totb = int64_t(nn) * nr;
-    mgf_bessel_kernel<<<unsigned((totb + 127) / 128), 128, 0, s>>>(dn.p, nn, dr.p, nr, Jm.p);
-    mgf_contract_kernel<<<dim3((na + 127) / 128, nr, 5), 128, 0, s>>>(Jm.p, F.p, nn, nr, na, out);
+    mgf_bessel_kernel<<<unsigned((totb + 127) / 128), 128, 0, s>>>(dn.p, nn, dr.p, nr, Jm.p), ::sldm::count_launch();
+    mgf_contract_kernel<<<dim3((na + 127) / 128, nr, 5), 128, 0, s>>>(Jm.p, F.p, nn, nr, na, out), ::sldm::count_launch();
   }
   SLDM_CUDA(cudaGetLastError());
   SLDM_CUDA(cudaStreamSynchronize(s));
@@ -515,7 +515,7 @@ void mgf_fill_reflected(const sldm_mesh* m, const MgfStackHost& H, double omega,
   const int64_t np = int64_t(nt) * nt;
   ScopedTimer tm("fill_reflected", s);
   fill_reflected_kernel<C><<<unsigned((np + 127) / 128), 128, 0, s>>>(nt, m->d.geo.p, m->d.tri_edge.p, S, T.Q, tv, (C*)LA, ldA,
-                                                                      (C*)LP, ldP);
+                                                                      (C*)LP, ldP), ::sldm::count_launch();
   SLDM_CUDA(cudaGetLastError());
 }
 

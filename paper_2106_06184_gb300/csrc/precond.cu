@@ -169,8 +169,8 @@ void prec_setup(Precond& P, const sldm_mesh* m, const std::vector<PrecObj>& objs
   P.lam.alloc(size_t(4) * ne);
   P.pdiag.alloc(size_t(2) * nt);
   prec_edges_kernel<C><<<(ne + 127) / 128, 128, 0, s>>>(ne, d.tplus.p, d.obj.p, P.objs.p, (const C*)LAm, loc, d.ix_ptr.p,
-                                                        d.ix_col.p, ix_val, P.lam.p);
-  prec_tris_kernel<C><<<(nt + 127) / 128, 128, 0, s>>>(nt, d.obj.p, P.objs.p, (const C*)LPm, loc, P.pdiag.p);
+                                                        d.ix_col.p, ix_val, P.lam.p), ::sldm::count_launch();
+  prec_tris_kernel<C><<<(nt + 127) / 128, 128, 0, s>>>(nt, d.obj.p, P.objs.p, (const C*)LPm, loc, P.pdiag.p), ::sldm::count_launch();
   SLDM_CUDA(cudaGetLastError());
   int64_t tot = 0;
   std::vector<int64_t> off;
@@ -186,7 +186,7 @@ void prec_setup(Precond& P, const sldm_mesh* m, const std::vector<PrecObj>& objs
     const PrecObj& o = objs[i];
     const int nq = o.nt - 1;
     prec_schur_kernel<<<dim3((nq + 127) / 128, nq), 128, 0, s>>>(o, k0, d.tri_edge.p, d.tri_sign.p, d.tplus.p, d.tminus.p,
-                                                                P.lam.p, P.pdiag.p, Sm.p + off[i], P.sinv.p + off[i]);
+                                                                P.lam.p, P.pdiag.p, Sm.p + off[i], P.sinv.p + off[i]), ::sldm::count_launch();
     sys.push_back({Sm.p + off[i], P.sinv.p + off[i], nq, nq});
   }
   SLDM_CUDA(cudaGetLastError());
@@ -220,11 +220,11 @@ void prec_apply(const Precond& P, const sldm_mesh* m, const double2* r, double2*
   const HostMesh& h = m->h;
   const DevMesh& d = m->d;
   const int ne = int(h.ne), nq = int(h.nt - h.nobj);
-  prec_apply1_kernel<<<(nq + 255) / 256, 256, 0, s>>>(ne, nq, d.q2t.p, d.tri_edge.p, d.tri_sign.p, P.lam.p, r, P.t3.p);
+  prec_apply1_kernel<<<(nq + 255) / 256, 256, 0, s>>>(ne, nq, d.q2t.p, d.tri_edge.p, d.tri_sign.p, P.lam.p, r, P.t3.p), ::sldm::count_launch();
   gemv_jobs<double2>(P.plan, 1, s);
-  prec_apply3_kernel<<<unsigned(h.nobj), 256, 0, s>>>(P.objs.p, P.x3.p, P.bx.p);
+  prec_apply3_kernel<<<unsigned(h.nobj), 256, 0, s>>>(P.objs.p, P.x3.p, P.bx.p), ::sldm::count_launch();
   const int n = std::max(ne, nq);
-  prec_apply45_kernel<<<(n + 255) / 256, 256, 0, s>>>(ne, nq, d.tplus.p, d.tminus.p, P.lam.p, P.pdiag.p, r, P.bx.p, P.x3.p, x);
+  prec_apply45_kernel<<<(n + 255) / 256, 256, 0, s>>>(ne, nq, d.tplus.p, d.tminus.p, P.lam.p, P.pdiag.p, r, P.bx.p, P.x3.p, x), ::sldm::count_launch();
   SLDM_CUDA(cudaGetLastError());
 }
 

@@ -1,4 +1,5 @@
 // Named CUDA-event timers for the library's launches (sldm_timers_* in sldm.h).
+#include <atomic>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -65,9 +66,18 @@ void timer_end(cudaStream_t s) {
   if (g_pending.size() > 4096) resolve_locked();
 }
 
+static std::atomic<int64_t> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
 }  // namespace sldm
 
 extern "C" {
+
+int sldm_launch_count(int64_t* out) {
+  if (!out) return SLDM_EINVAL;
+  *out = sldm::g_launches.load(std::memory_order_relaxed);
+  return SLDM_OK;
+}
 
 int sldm_timers_enable(int32_t on) {
   std::lock_guard<std::mutex> l(sldm::g_mu);

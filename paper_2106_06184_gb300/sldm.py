@@ -86,6 +86,7 @@ EXPORTS = {
     "sldm_timers_reset": (C.c_int, []),
     "sldm_timer_get": (C.c_int, [C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "sldm_timer_names": (C.c_int, [C.c_char_p, C.c_size_t]),
+    "sldm_launch_count": (C.c_int, [C.POINTER(C.c_int64)]),
 }
 
 
@@ -134,6 +135,14 @@ def timers_read(lib=None):
         L.check(L.lib.sldm_timer_get(name.encode(), C.byref(ms), C.byref(n)))
         out[name] = (ms.value, n.value)
     return out
+
+
+def launch_count(lib=None) -> int:
+    """Kernel launches the library has made in this process."""
+    L = lib or load()
+    n = C.c_int64()
+    L.check(L.lib.sldm_launch_count(C.byref(n)))
+    return n.value
 
 
 def load(path=LIB_PATH) -> Library:
