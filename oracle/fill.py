@@ -18,6 +18,17 @@ static gradient grad 1/(4 pi R) is done in closed form.  A barycentric source
 triangle lying inside the test triangle contributes zero to Kbar (coplanar: the
 integrand is normal to the plane while f_m is tangential).  BC functions enter as
 sums of barycentric RWG functions (``mesh.C``), see ``oracle.topology``.
+
+Good conductors (Sec. II-B: the entries of highly conductive objects need
+integration that follows the fast decay of G over a skin depth).  Reading: a
+source triangle T' (primal for L, barycentric for Kbar) of diameter d (its
+longest edge) is split L times by edge midpoints, L the smallest level with
+|Im k| d / 2^L <= 1, and the 6-point rule is applied on each of the 4^L children
+(``sub_rule``).  For L > 0 the touching-pair extraction of L keeps only the static
+1/(4 pi R) term: the k^2 R/(8 pi) term is no longer small against G once
+|k| d > 1.  When any source of a fill needs L > 0, that fill also drops the
+non-touching pairs whose bounding spheres are farther apart than 40 / |Im k|
+(G has decayed below exp(-40) there).
 """
 from __future__ import annotations
 
@@ -32,6 +43,8 @@ EPS0 = 1.0 / (MU0 * C0 ** 2)
 ETA0 = MU0 * C0
 
 CHUNK = 4096
+SUB_MAX = 7        # deepest subdivision of a source triangle (4^7 children)
+R8_CUTOFF = 40.0   # |Im k| x (distance of the bounding spheres) beyond which a pair is dropped
 
 
 def green(k, R):
@@ -50,6 +63,65 @@ def green_smooth(k, R):
         ser = ser + (-1j * k) ** n * R ** (n - 1) / np.prod(np.arange(1, n + 1), dtype=float)
     ser = ser / (4 * np.pi)
     return np.where(np.abs(x) < 0.05, ser, full)
+
+
+def green_smooth1(k, R):
+    """G - 1/(4 pi R) = (exp(-j k R) - 1)/(4 pi R); a Taylor series where |k R| is small."""
+    x = k * R
+    with np.errstate(invalid='ignore', divide='ignore'):
+        full = (np.exp(-1j * x) - 1.0) / (4 * np.pi * R)
+    ser = np.zeros_like(full)
+    for n in range(1, 12):
+        ser = ser + (-1j * k) ** n * R ** (n - 1) / np.prod(np.arange(1, n + 1), dtype=float)
+    ser = ser / (4 * np.pi)
+    return np.where(np.abs(x) < 0.05, ser, full)
+
+
+def sub_level(k, diam):
+    """Subdivision level of source triangles of diameter ``diam``: the smallest
+    L >= 0 with |Im k| diam / 2^L <= 1."""
+    x = abs(np.imag(k)) * np.asarray(diam, dtype=float)
+    L = np.zeros(x.shape, dtype=np.int64)
+    big = x > 1.0
+    L[big] = np.ceil(np.log2(x[big])).astype(np.int64)
+    if L.size and L.max() > SUB_MAX:
+        raise ValueError("source triangles too large for the skin depth: subdivision level "
+                         f"{L.max()} > {SUB_MAX}")
+    return L
+
+
+def sub_rule(L):
+    """Composite rule on a triangle split L times through its edge midpoints:
+    barycentric points (6 * 4^L, 3) and weights (6 * 4^L,) summing to 1."""
+    tris = [np.eye(3)]
+    for _ in range(L):
+        nxt = []
+        for a, b, c in tris:
+            ab, bc, ca = (a + b) / 2, (b + c) / 2, (c + a) / 2
+            nxt += [np.array([a, ab, ca]), np.array([ab, b, bc]), np.array([ca, bc, c]), np.array([ab, bc, ca])]
+        tris = nxt
+    T = np.array(tris)
+    pts = np.einsum('qk,nkd->nqd', Q.BARY, T).reshape(-1, 3)
+    return pts, np.tile(Q.W, len(tris)) / len(tris)
+
+
+def _diam(P):
+    """Longest edge of triangles P (n, 3, 3)."""
+    return np.max(np.linalg.norm(P - np.roll(P, 1, axis=1), axis=2), axis=1)
+
+
+def _sphere(P):
+    """Bounding sphere of triangles P: centroid and largest vertex distance."""
+    c = P.mean(axis=1)
+    return c, np.max(np.linalg.norm(P - c[:, None, :], axis=2), axis=1)
+
+
+def _kept(k, Pa, Pb, touch):
+    """Pairs kept by the far-pair rule: touching, or |Im k| (|c - c'| - r - r') <= 40."""
+    ca, ra = _sphere(Pa)
+    cb, rb = _sphere(Pb)
+    gap = np.linalg.norm(ca - cb, axis=1) - ra - rb
+    return touch | (abs(np.imag(k)) * gap <= R8_CUTOFF)
 
 
 def grad_green_factor(k, R):
@@ -75,12 +147,14 @@ def _touch_primal(tri, a, b):
     return (ta[:, :, None] == tb[:, None, :]).any(axis=(1, 2))
 
 
-def _L_pairs(mesh, k, ta, tb):
-    """Local RWG x RWG (P, 3, 3) and pulse x pulse (P,) integrals of triangle pairs."""
+def _L_pairs(mesh, k, ta, tb, level=0):
+    """Local RWG x RWG (P, 3, 3) and pulse x pulse (P,) integrals of triangle pairs,
+    the source triangles split ``level`` times."""
     xyz, tri = mesh.xyz, mesh.tri
     A, B = xyz[tri[ta]], xyz[tri[tb]]
-    rq, rs = Q.points(A), Q.points(B)
-    wq, ws = Q.weights(mesh.area[ta]), Q.weights(mesh.area[tb])
+    bs, wsub = sub_rule(level)
+    rq, rs = Q.points(A), np.einsum('qk,nkd->nqd', bs, B)
+    wq, ws = Q.weights(mesh.area[ta]), np.outer(mesh.area[tb], wsub)
     fa = rq[:, :, None, :] - A[:, None, :, :]          # r - v_i   (P, 6, 3, 3)
     fb = rs[:, :, None, :] - B[:, None, :, :]          # r' - w_j
     scale = (mesh.E.tri_sign[ta][:, :, None] * mesh.E.tri_sign[tb][:, None, :]
@@ -98,9 +172,11 @@ def _L_pairs(mesh, k, ta, tb):
         idx = np.nonzero(touch)[0]
         P = len(idx)
         R = np.linalg.norm(rq[idx][:, :, None, :] - rs[idx][:, None, :, :], axis=-1)
-        Gs = green_smooth(k, R) * ws[idx][:, None, :]                        # (P, 6q, 6s)
+        two = level == 0                                                     # extract 1/R and R, else 1/R only
+        Gs = (green_smooth(k, R) if two else green_smooth1(k, R)) * ws[idx][:, None, :]   # (P, 6q, ns)
         inner_a = np.einsum('pqs,psjd->pqjd', Gs, fb[idx])                   # (P, 6, 3, 3)
         inner_p = Gs.sum(axis=2)                                             # (P, 6)
+        kk = k * k if two else 0.0
         r = rq[idx].reshape(-1, 3)
         T = np.repeat(B[idx], 6, axis=0)
         I = integrals(r, T)
@@ -111,8 +187,8 @@ def _L_pairs(mesh, k, ta, tb):
         inv_r = I['inv_r'].reshape(P, 6, 1, 1)
         rr = I['r'].reshape(P, 6, 1, 1)
         inner_a = inner_a + (por + (rho - w) * inv_r) / (4 * np.pi) \
-            - k * k * (pr + (rho - w) * rr) / (8 * np.pi)
-        inner_p = inner_p + I['inv_r'].reshape(P, 6) / (4 * np.pi) - k * k * I['r'].reshape(P, 6) / (8 * np.pi)
+            - kk * (pr + (rho - w) * rr) / (8 * np.pi)
+        inner_p = inner_p + I['inv_r'].reshape(P, 6) / (4 * np.pi) - kk * I['r'].reshape(P, 6) / (8 * np.pi)
         la[idx] = np.einsum('pq,pqid,pqjd->pij', wq[idx], fa[idx], inner_a)
         lp[idx] = np.einsum('pq,pq->p', wq[idx], inner_p)
     return la * scale, lp / (mesh.area[ta] * mesh.area[tb])
@@ -129,15 +205,24 @@ def fill_L(mesh, k, tris):
     tidx[tris] = np.arange(len(tris))
     LA = np.zeros((len(edges), len(edges)), dtype=complex)
     LP = np.zeros((len(tris), len(tris)), dtype=complex)
-    ta_all = np.repeat(tris, len(tris))
-    tb_all = np.tile(tris, len(tris))
-    for c in range(0, len(ta_all), CHUNK):
-        ta, tb = ta_all[c:c + CHUNK], tb_all[c:c + CHUNK]
-        la, lp = _L_pairs(mesh, k, ta, tb)
-        rows = eidx[e_of[ta]][:, :, None] * np.ones((1, 1, 3), dtype=np.int64)
-        cols = eidx[e_of[tb]][:, None, :] * np.ones((1, 3, 1), dtype=np.int64)
-        np.add.at(LA, (rows.ravel(), cols.ravel()), la.ravel())
-        np.add.at(LP, (tidx[ta], tidx[tb]), lp)
+    P = mesh.xyz[mesh.tri]
+    lev = sub_level(k, _diam(P[tris]))
+    sub = lev.max(initial=0) > 0
+    for L in np.unique(lev):
+        srcs = tris[lev == L]
+        ta_all = np.repeat(tris, len(srcs))
+        tb_all = np.tile(srcs, len(tris))
+        if sub:
+            keep = _kept(k, P[ta_all], P[tb_all], _touch_primal(mesh.tri, ta_all, tb_all))
+            ta_all, tb_all = ta_all[keep], tb_all[keep]
+        step = max(1, CHUNK // 4 ** int(L))
+        for c in range(0, len(ta_all), step):
+            ta, tb = ta_all[c:c + step], tb_all[c:c + step]
+            la, lp = _L_pairs(mesh, k, ta, tb, int(L))
+            rows = eidx[e_of[ta]][:, :, None] * np.ones((1, 1, 3), dtype=np.int64)
+            cols = eidx[e_of[tb]][:, None, :] * np.ones((1, 3, 1), dtype=np.int64)
+            np.add.at(LA, (rows.ravel(), cols.ravel()), la.ravel())
+            np.add.at(LP, (tidx[ta], tidx[tb]), lp)
     return LA, LP
 
 
@@ -156,12 +241,15 @@ def _touch_bary(mesh, ta, cb):
     return np.where(parent == ta, 2, out)
 
 
-def _K_pairs(mesh, k, ta, cb):
-    """Local RWG (test, primal) x barycentric RWG (source) integrals of Kbar, (P, 3, 3)."""
+def _K_pairs(mesh, k, ta, cb, level=0):
+    """Local RWG (test, primal) x barycentric RWG (source) integrals of Kbar, (P, 3, 3),
+    the source triangles split ``level`` times."""
     A = mesh.xyz[mesh.tri[ta]]
     Bt = mesh.bxyz[mesh.btri[cb]]
-    rq, rs = Q.points(A), Q.points(Bt)
-    wq, ws = Q.weights(mesh.area[ta]), Q.weights(mesh.barea[cb])
+    bs, wsub = sub_rule(level)
+    rq, rs = Q.points(A), np.einsum('qk,nkd->nqd', bs, Bt)
+    wq, ws = Q.weights(mesh.area[ta]), np.outer(mesh.barea[cb], wsub)
+    ns = rs.shape[1]
     fa = (rq[:, :, None, :] - A[:, None, :, :]) * \
         (mesh.E.tri_sign[ta] / (2 * mesh.area[ta][:, None]))[:, None, :, None]          # f_i(r_q)
     sb = mesh.bE.tri_sign[cb] / (2 * mesh.barea[cb][:, None])                            # (P, 3)
@@ -175,7 +263,7 @@ def _K_pairs(mesh, k, ta, cb):
         g1 = grad_green_factor(k, R) * wq[far][:, :, None] * ws[far][:, None, :]
         # inner[p, q, j] = sum_s g1 (r_q - r'_s) x g_j(r'_s);  out = sum_q f_i(r_q) . inner
         X = np.cross(d[:, :, :, None, :], gb[far][:, None, :, :, :])                     # (P, q, s, j, 3)
-        inner = np.matmul(g1[:, :, None, :], X.reshape(len(far), 6, 6, 9)).reshape(len(far), 6, 3, 3)
+        inner = np.matmul(g1[:, :, None, :], X.reshape(len(far), 6, ns, 9)).reshape(len(far), 6, 3, 3)
         out[far] = np.einsum('pqia,pqja->pij', fa[far], inner)
     near = np.nonzero(kind == 1)[0]
     if len(near):
@@ -184,7 +272,7 @@ def _K_pairs(mesh, k, ta, cb):
         R = np.linalg.norm(d, axis=-1)
         g1 = grad_green_smooth_factor(k, R) * ws[near][:, None, :]
         X = np.cross(d[:, :, :, None, :], gb[near][:, None, :, :, :])
-        inner = np.matmul(g1[:, :, None, :], X.reshape(P, 6, 6, 9)).reshape(P, 6, 3, 3)
+        inner = np.matmul(g1[:, :, None, :], X.reshape(P, 6, ns, 9)).reshape(P, 6, 3, 3)
         I = integrals(rq[near].reshape(-1, 3), np.repeat(Bt[near], 6, axis=0))
         gs = I['grad_inv_r'].reshape(P, 6, 1, 3) / (4 * np.pi)
         # static part: [int grad 1/(4 pi R) dS'] x g_j evaluated through (r - r') x (r' - w) = (r - r') x (r - w)
@@ -203,14 +291,24 @@ def fill_Kbar(mesh, k, obj):
     tris = np.arange(t0, t1)
     kids = np.arange(6 * t0, 6 * t1)
     Kb = np.zeros((e1 - e0, len(bidx)), dtype=complex)
-    ta_all = np.repeat(tris, len(kids))
-    cb_all = np.tile(kids, len(tris))
-    for c in range(0, len(ta_all), CHUNK):
-        ta, cb = ta_all[c:c + CHUNK], cb_all[c:c + CHUNK]
-        loc = _K_pairs(mesh, k, ta, cb)
-        rows = (mesh.E.tri_edge[ta] - e0)[:, :, None] * np.ones((1, 1, 3), dtype=np.int64)
-        cols = (mesh.bE.tri_edge[cb] - b0)[:, None, :] * np.ones((1, 3, 1), dtype=np.int64)
-        np.add.at(Kb, (rows.ravel(), cols.ravel()), loc.ravel())
+    P = mesh.xyz[mesh.tri]
+    Pb = mesh.bxyz[mesh.btri]
+    lev = sub_level(k, _diam(Pb[kids]))
+    sub = lev.max(initial=0) > 0
+    for L in np.unique(lev):
+        srcs = kids[lev == L]
+        ta_all = np.repeat(tris, len(srcs))
+        cb_all = np.tile(srcs, len(tris))
+        if sub:
+            keep = _kept(k, P[ta_all], Pb[cb_all], _touch_bary(mesh, ta_all, cb_all) > 0)
+            ta_all, cb_all = ta_all[keep], cb_all[keep]
+        step = max(1, CHUNK // 4 ** int(L))
+        for c in range(0, len(ta_all), step):
+            ta, cb = ta_all[c:c + step], cb_all[c:c + step]
+            loc = _K_pairs(mesh, k, ta, cb, int(L))
+            rows = (mesh.E.tri_edge[ta] - e0)[:, :, None] * np.ones((1, 1, 3), dtype=np.int64)
+            cols = (mesh.bE.tri_edge[cb] - b0)[:, None, :] * np.ones((1, 3, 1), dtype=np.int64)
+            np.add.at(Kb, (rows.ravel(), cols.ravel()), loc.ravel())
     Cobj = mesh.C[b0:b0 + len(bidx), e0:e1].toarray()
     return Kb @ Cobj, Kb
 
