@@ -12,28 +12,13 @@
 // source triangle (coalesced SoA record), a CTA walks a tile of test triangles
 // held in shared memory, and the 3x3 results are scattered with atomics
 // (each edge-pair entry gets four triangle-pair contributions).
+#include <algorithm>
 #include <cmath>
 #include <mutex>
 
-#include "internal.h"
+#include "fill_dev.cuh"
 
 namespace sldm {
-
-// ---------------------------------------------------------------- Dunavant rule
-// Six-point degree-4 rule (Dunavant 1985): barycentric points and weights
-// (weights sum to 1).
-__constant__ double c_bary[6][3] = {
-    {0.108103018168070, 0.445948490915965, 0.445948490915965},
-    {0.445948490915965, 0.108103018168070, 0.445948490915965},
-    {0.445948490915965, 0.445948490915965, 0.108103018168070},
-    {0.816847572980459, 0.091576213509771, 0.091576213509771},
-    {0.091576213509771, 0.816847572980459, 0.091576213509771},
-    {0.091576213509771, 0.091576213509771, 0.816847572980459}};
-__constant__ double c_w[6] = {0.223381589678011, 0.223381589678011, 0.223381589678011,
-                              0.109951743655322, 0.109951743655322, 0.109951743655322};
-
-constexpr double PI = 3.14159265358979323846;
-constexpr double INV4PI = 0.25 / PI;
 
 // ---------------------------------------------------------------- geometry
 // Writes a GEO_STRIDE record for a triangle with vertices p0, p1, p2 and edge
@@ -102,41 +87,6 @@ void geometry(const HostMesh& hm, DevMesh& dm, cudaStream_t s) {
   geometry_kernel<<<(nt + 127) / 128, 128, 0, s>>>(nt, dm.xyz.p, dm.tri.p, dm.tri_edge.p, dm.tri_sign.p,
                                                    dm.btri_sign.p, hm.nv, dm.geo.p, dm.bgeo.p), ::sldm::count_launch();
   SLDM_CUDA(cudaGetLastError());
-}
-
-// ---------------------------------------------------------------- precision traits
-template <class R>
-struct M;
-template <>
-struct M<float> {
-  static __device__ __forceinline__ void sincos_(float x, float* s, float* c) { sincosf(x, s, c); }
-  static __device__ __forceinline__ float exp_(float x) { return expf(x); }
-  static __device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
-  static __device__ __forceinline__ void add(void* base, int64_t idx, float re, float im) {
-    atomicAdd(reinterpret_cast<float2*>(base) + idx, make_float2(re, im));
-  }
-  static __device__ __forceinline__ void store(void* base, int64_t idx, double re, double im) {
-    reinterpret_cast<float2*>(base)[idx] = make_float2(float(re), float(im));
-  }
-};
-template <>
-struct M<double> {
-  static __device__ __forceinline__ void sincos_(double x, double* s, double* c) { sincos(x, s, c); }
-  static __device__ __forceinline__ double exp_(double x) { return exp(x); }
-  static __device__ __forceinline__ double rsqrt_(double x) { return rsqrt(x); }
-  static __device__ __forceinline__ void add(void* base, int64_t idx, double re, double im) {
-    double* p = reinterpret_cast<double*>(base) + 2 * idx;
-    atomicAdd(p, re);
-    atomicAdd(p + 1, im);
-  }
-  static __device__ __forceinline__ void store(void* base, int64_t idx, double re, double im) {
-    reinterpret_cast<double2*>(base)[idx] = make_double2(re, im);
-  }
-};
-// atomic add of a double result into a destination of precision R
-template <class R>
-__device__ __forceinline__ void add_d(void* base, int64_t idx, double re, double im) {
-  M<R>::add(base, idx, R(re), R(im));
 }
 
 // ---------------------------------------------------------------- bulk L kernel
@@ -285,154 +235,11 @@ __global__ void __launch_bounds__(TILE_SRC) fill_L_bulk(const LTask* __restrict_
   }
 }
 
-// ---------------------------------------------------------------- FP64 closed forms
-// Integrals over the flat triangle (p1, p2, p3) seen from r (see the oracle's
-// derivation: contour reduction with the surface divergence theorem).
-struct Pot {
-  double inv_r, r;            // int 1/R, int R
-  double por[3], pr[3];       // int (rho' - rho)/R, int (rho' - rho) R
-  double grad[3];             // int grad_r (1/R)
-  double rho[3];              // projection of r on the plane
-};
-
-__device__ void potentials(const double* r, const double* p1, const double* p2, const double* p3, Pot& o) {
-  double u[3], w[3], n[3];
-  for (int d = 0; d < 3; ++d) {
-    u[d] = p2[d] - p1[d];
-    w[d] = p3[d] - p1[d];
-  }
-  n[0] = u[1] * w[2] - u[2] * w[1];
-  n[1] = u[2] * w[0] - u[0] * w[2];
-  n[2] = u[0] * w[1] - u[1] * w[0];
-  double nn = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
-  for (int d = 0; d < 3; ++d) n[d] /= nn;
-  double h = n[0] * (r[0] - p1[0]) + n[1] * (r[1] - p1[1]) + n[2] * (r[2] - p1[2]);
-  for (int d = 0; d < 3; ++d) o.rho[d] = r[d] - h * n[d];
-  double ah = fabs(h);
-  double sum_tf = 0, omega = 0, sum_r = 0;
-  double por[3] = {0, 0, 0}, pr[3] = {0, 0, 0}, gm[3] = {0, 0, 0};
-  const double* P[4] = {p1, p2, p3, p1};
-  for (int e = 0; e < 3; ++e) {
-    const double* a = P[e];
-    const double* b = P[e + 1];
-    double s[3], m[3];
-    double L = sqrt((b[0] - a[0]) * (b[0] - a[0]) + (b[1] - a[1]) * (b[1] - a[1]) + (b[2] - a[2]) * (b[2] - a[2]));
-    for (int d = 0; d < 3; ++d) s[d] = (b[d] - a[d]) / L;
-    m[0] = s[1] * n[2] - s[2] * n[1];
-    m[1] = s[2] * n[0] - s[0] * n[2];
-    m[2] = s[0] * n[1] - s[1] * n[0];
-    double sm = 0, sp = 0, t0 = 0;
-    for (int d = 0; d < 3; ++d) {
-      sm += (a[d] - o.rho[d]) * s[d];
-      sp += (b[d] - o.rho[d]) * s[d];
-      t0 += (a[d] - o.rho[d]) * m[d];
-    }
-    double R02 = t0 * t0 + h * h;
-    double Rm = sqrt(sm * sm + R02), Rp = sqrt(sp * sp + R02);
-    double f;
-    if (sp <= 0 && sm <= 0) {
-      f = log((Rm - sm) / (Rp - sp));
-    } else {
-      double num = sp > 0 ? Rp + sp : R02 / (Rp - sp);
-      double den = sm > 0 ? Rm + sm : R02 / (Rm - sm);
-      f = log(num / den);
-    }
-    double q1 = R02 + ah * Rp, q2 = R02 + ah * Rm;
-    double beta = (q1 > 0 ? atan(t0 * sp / q1) : 0.0) - (q2 > 0 ? atan(t0 * sm / q2) : 0.0);
-    omega += beta;
-    sum_tf += t0 * f;
-    double line1 = sp * Rp - sm * Rm + R02 * f;  // 2 int_edge R dl
-    sum_r += t0 * line1;
-    double line3 = (sp * Rp * Rp * Rp - sm * Rm * Rm * Rm) / 4.0 + 3.0 * R02 * (sp * Rp - sm * Rm) / 8.0 +
-                   3.0 * R02 * R02 * f / 8.0;   // int_edge R^3 dl
-    for (int d = 0; d < 3; ++d) {
-      por[d] += m[d] * 0.5 * line1;
-      pr[d] += m[d] * line3 / 3.0;
-      gm[d] -= m[d] * f;
-    }
-  }
-  o.inv_r = sum_tf - ah * omega;
-  o.r = sum_r / 6.0 + h * h / 3.0 * o.inv_r;
-  double sg = h > 0 ? 1.0 : (h < 0 ? -1.0 : 0.0);
-  for (int d = 0; d < 3; ++d) {
-    o.por[d] = por[d];
-    o.pr[d] = pr[d];
-    o.grad[d] = gm[d] - sg * omega * n[d];
-  }
-}
-
-// complex helpers (double)
-struct cd {
-  double r, i;
-};
-__device__ __forceinline__ cd cmul(cd a, cd b) { return {a.r * b.r - a.i * b.i, a.r * b.i + a.i * b.r}; }
-
-// G - 1/(4 pi R) + k^2 R/(8 pi) (Taylor series for |kR| < 0.05)
-__device__ cd green_smooth(cd k, double R) {
-  cd x = {k.r * R, k.i * R};
-  double ax = sqrt(x.r * x.r + x.i * x.i);
-  if (ax < 0.05) {
-    // sum_{n>=1, n!=2} (-j k)^n R^(n-1) / n!
-    cd mjk = {k.i, -k.r};  // -j k
-    cd p = mjk;            // (-jk)^1
-    cd acc = p;            // n = 1 term (R^0)
-    double Rp = 1.0, fact = 1.0;
-    for (int n = 2; n <= 11; ++n) {
-      p = cmul(p, mjk);
-      Rp *= R;
-      fact *= n;
-      if (n == 2) continue;
-      acc.r += p.r * Rp / fact;
-      acc.i += p.i * Rp / fact;
-    }
-    return {acc.r * INV4PI, acc.i * INV4PI};
-  }
-  double sn, cn;
-  sincos(x.r, &sn, &cn);
-  double ex = exp(x.i);  // exp(-j k R) = exp(ki R) (cos - j sin)
-  cd e = {ex * cn - 1.0, -ex * sn};
-  cd k2 = cmul(k, k);
-  return {e.r * INV4PI / R + k2.r * R * 0.5 * INV4PI, e.i * INV4PI / R + k2.i * R * 0.5 * INV4PI};
-}
-
-// g1 of grad(G - 1/(4 pi R)) = (r - r') g1: (1 - (1 + jkR) exp(-jkR)) / (4 pi R^3)
-__device__ cd grad_smooth(cd k, double R) {
-  cd x = {-k.i * R, k.r * R};  // j k R
-  double ax = sqrt(x.r * x.r + x.i * x.i);
-  double iR3 = INV4PI / (R * R * R);
-  if (ax < 0.05) {
-    // sum_{n>=2} (-1)^n (n-1) x^n / n!
-    cd p = x, acc = {0, 0};
-    double fact = 1.0;
-    for (int n = 2; n <= 13; ++n) {
-      p = cmul(p, x);
-      fact *= n;
-      double c = ((n & 1) ? -1.0 : 1.0) * (n - 1) / fact;
-      acc.r += c * p.r;
-      acc.i += c * p.i;
-    }
-    return {acc.r * iR3, acc.i * iR3};
-  }
-  double sn, cn;
-  sincos(k.r * R, &sn, &cn);
-  double ex = exp(k.i * R);
-  cd e = {ex * cn, -ex * sn};              // exp(-jkR)
-  cd one_x = {1.0 + x.r, x.i};             // 1 + jkR
-  cd pr = cmul(one_x, e);
-  return {(1.0 - pr.r) * iR3, -pr.i * iR3};
-}
-
 // ---------------------------------------------------------------- FP64 touching L pairs
 // Eight lanes per pair: lane q < 6 takes outer point q (closed forms + 6-point
 // remainder), the pair's moments are summed with shuffles inside the group,
 // and lane 0 scatters the 3x3 block.  One launch serves every task: a pair
 // belongs to the task of its object (obj_task), or to none.
-__device__ __forceinline__ double grp_sum8(double v) {
-  v += __shfl_xor_sync(0xffffffffu, v, 4);
-  v += __shfl_xor_sync(0xffffffffu, v, 2);
-  v += __shfl_xor_sync(0xffffffffu, v, 1);
-  return v;
-}
 
 template <class R>
 __global__ void fill_L_touch(const LTask* __restrict__ tasks, const int32_t* __restrict__ obj_task,
@@ -798,13 +605,31 @@ static std::vector<int32_t> object_tasks(const HostMesh& h, const std::vector<T>
   return ot;
 }
 
+// Tasks with a source split for a good conductor go to the split kernels whole
+// (their touching pairs included); the others to the bulk and touching kernels.
+template <class T>
+static std::vector<int32_t> unsplit_object_tasks(const HostMesh& h, const std::vector<T>& tasks, const std::vector<char>& split) {
+  std::vector<int32_t> ot = object_tasks(h, tasks);
+  for (auto& o : ot)
+    if (o >= 0 && split[size_t(o)]) o = -1;
+  return ot;
+}
+
 template <class R>
 void fill_L(const sldm_mesh* m, const std::vector<LTask>& tasks, cudaStream_t s) {
   if (tasks.empty()) return;
+  std::vector<std::vector<int8_t>> lev(tasks.size());
+  std::vector<char> split(tasks.size(), 0);
+  for (size_t i = 0; i < tasks.size(); ++i) {
+    lev[i] = split_levels_L(m->h, tasks[i]);
+    split[i] = *std::max_element(lev[i].begin(), lev[i].end()) > 0;
+  }
   std::vector<TileRef> tiles;
-  for (size_t i = 0; i < tasks.size(); ++i)
+  for (size_t i = 0; i < tasks.size(); ++i) {
+    if (split[i]) continue;
     for (int t0 = 0; t0 < tasks[i].ntest; t0 += TILE_TEST)
       for (int s0 = 0; s0 < tasks[i].nsrc; s0 += TILE_SRC) tiles.push_back({int32_t(i), t0, s0, 0});
+  }
   DBuf<LTask> dt;
   DBuf<TileRef> dtl;
   dt.upload(tasks, s);
@@ -818,29 +643,39 @@ void fill_L(const sldm_mesh* m, const std::vector<LTask>& tasks, cudaStream_t s)
   SLDM_CUDA(cudaGetLastError());
   const int np = int(m->h.touchL_a.size());
   DBuf<int32_t> dot;
-  dot.upload(object_tasks(m->h, tasks), s);
+  dot.upload(unsplit_object_tasks(m->h, tasks, split), s);
   if (np > 0) {
     ScopedTimer tm("fill_L_touch", s);
     fill_L_touch<R><<<unsigned((int64_t(np) * 8 + 255) / 256), 256, 0, s>>>(dt.p, dot.p, d.obj.p, d.touchL_a.p, d.touchL_b.p, np,
                                                                             d.geo.p, d.xyz.p, d.tri.p, d.tri_edge.p), ::sldm::count_launch();
   }
   SLDM_CUDA(cudaGetLastError());
+  for (size_t i = 0; i < tasks.size(); ++i)
+    if (split[i]) fill_L_split_task<R>(m, tasks[i], lev[i], s);
   SLDM_CUDA(cudaStreamSynchronize(s));  // task/tile buffers are released on return
 }
 
 template <class R>
 void fill_K(const sldm_mesh* m, const std::vector<KTask>& tasks, cudaStream_t s) {
   if (tasks.empty()) return;
+  std::vector<std::vector<int8_t>> lev(tasks.size());
+  std::vector<char> split(tasks.size(), 0);
+  for (size_t i = 0; i < tasks.size(); ++i) {
+    lev[i] = split_levels_K(m->h, tasks[i]);
+    split[i] = *std::max_element(lev[i].begin(), lev[i].end()) > 0;
+  }
   std::vector<TileRef> tiles;
-  for (size_t i = 0; i < tasks.size(); ++i)
+  for (size_t i = 0; i < tasks.size(); ++i) {
+    if (split[i]) continue;
     for (int t0 = 0; t0 < tasks[i].ntest; t0 += TILE_TEST)
       for (int s0 = 0; s0 < tasks[i].nsrc; s0 += TILE_SRC) tiles.push_back({int32_t(i), t0, s0, 0});
+  }
   DBuf<KTask> dt;
   DBuf<TileRef> dtl;
   dt.upload(tasks, s);
   dtl.upload(tiles, s);
   const DevMesh& d = m->d;
-  {
+  if (!tiles.empty()) {
     ScopedTimer tm("fill_K_bulk", s);
     fill_K_bulk<R><<<unsigned(tiles.size()), TILE_SRC, 0, s>>>(dt.p, dtl.p, d.geo.p, d.bgeo.p, d.tri.p, d.tri_edge.p,
                                                              d.btri_edge.p), ::sldm::count_launch();
@@ -848,7 +683,7 @@ void fill_K(const sldm_mesh* m, const std::vector<KTask>& tasks, cudaStream_t s)
   SLDM_CUDA(cudaGetLastError());
   const int np = int(m->h.touchK_a.size());
   DBuf<int32_t> dot;
-  dot.upload(object_tasks(m->h, tasks), s);
+  dot.upload(unsplit_object_tasks(m->h, tasks, split), s);
   if (np > 0) {
     ScopedTimer tm("fill_K_touch", s);
     fill_K_touch<R><<<unsigned((int64_t(np) * 8 + 255) / 256), 256, 0, s>>>(dt.p, dot.p, d.obj.p, d.touchK_a.p, d.touchK_c.p, np,
@@ -856,6 +691,8 @@ void fill_K(const sldm_mesh* m, const std::vector<KTask>& tasks, cudaStream_t s)
                                                                             d.btri_edge.p), ::sldm::count_launch();
   }
   SLDM_CUDA(cudaGetLastError());
+  for (size_t i = 0; i < tasks.size(); ++i)
+    if (split[i]) fill_K_split_task<R>(m, tasks[i], lev[i], s);
   SLDM_CUDA(cudaStreamSynchronize(s));
 }
 
@@ -1252,6 +1089,10 @@ extern "C" int sldm_kbar_noalloc(const sldm_mesh* m, int32_t obj, double k_re, d
     t.e_row0 = e0; t.b_col0 = b0; t.ld = nbe_o;
     t.Kb = Kb;
     t.kr = k_re; t.ki = k_im;
+    const std::vector<int8_t> lev = split_levels_K(h, t);
+    SLDM_REQUIRE(*std::max_element(lev.begin(), lev.end()) == 0, SLDM_ENOTSUP,
+                 "kbar_noalloc: the object's sources must be split for this wavenumber (good conductor); "
+                 "sldm_assemble handles it");
     // the block accumulates atomically: it must start at zero on every call
     SLDM_CUDA(cudaMemsetAsync(Kb, 0, nkb * sizeof(double2), s));
     const int nset = ntile_t * ntile_s;
