@@ -806,7 +806,8 @@ int sldm_solve(const sldm_op* op_, const void* b, void* x, int32_t nrhs, const s
   std::unique_lock<std::mutex> lock(op->busy, std::try_to_lock);
   SLDM_REQUIRE(lock.owns_lock(), SLDM_EBUSY, "solve: operator in use by another thread");
   double tol = (opts && opts->tol > 0) ? opts->tol : 1e-8;
-  int m = (opts && opts->restart > 0) ? opts->restart : 100;
+  int m = (opts && opts->restart > 0) ? opts->restart : 300;
+  m = int(std::min<int64_t>(m, op->N));
   int maxit = (opts && opts->maxit > 0) ? opts->maxit : 2000;
   bool x0 = opts && opts->x0_given;
   bool use_p = !(opts && opts->precond == SLDM_PRECOND_NONE) && op->pc.ready;

@@ -24,6 +24,24 @@ struct CT<double2> {
   typedef double R;
 };
 
+// acc += a b and acc -= a b for complex numbers as chains of fused multiply-adds:
+// four per complex product (a sum of two products written as one expression
+// compiles to a multiply, an FMA and an add, and the FP64 pipe is the bound).
+template <class R>
+__device__ __forceinline__ void cfma(R& cr, R& ci, R ar, R ai, R br, R bi) {
+  cr = fma(ar, br, cr);
+  cr = fma(-ai, bi, cr);
+  ci = fma(ar, bi, ci);
+  ci = fma(ai, br, ci);
+}
+template <class R>
+__device__ __forceinline__ void cfms(R& cr, R& ci, R ar, R ai, R br, R bi) {
+  cr = fma(-ar, br, cr);
+  cr = fma(ai, bi, cr);
+  ci = fma(-ar, bi, ci);
+  ci = fma(-ai, br, ci);
+}
+
 // ---------------------------------------------------------------- M_l and R_l
 // M_l is built length-scaled (l = mean edge length): Mh = diag(1, l) M_l diag(1/l, l)
 // = [[mu_l L^A_l / l, -l D^T L^phi_l B], [F D, -k0^2 l^2 I]], whose entries are O(1);
@@ -296,8 +314,7 @@ __global__ void __launch_bounds__(LU_THREADS) lu_coop_kernel(const LUSysT<C>* __
           const int i = k + t;
           const C l = mult[t - 1];
           C a = (i == p) ? rowk[c] : __ldcg(col + int64_t(i) * n);
-          a.x -= l.x * u.x - l.y * u.y;
-          a.y -= l.x * u.y + l.y * u.x;
+          cfms(a.x, a.y, l.x, l.y, u.x, u.y);
           colv[t - 1] = a;  // rows k+1 .. n-1
         }
         if (threadIdx.x == 0) col[int64_t(k) * n] = u;
@@ -339,8 +356,7 @@ __global__ void __launch_bounds__(LU_THREADS) lu_coop_kernel(const LUSysT<C>* __
             const C l = mult[t];
             const C u = rowp[c];
             C v = a[q];
-            v.x -= l.x * u.x - l.y * u.y;
-            v.y -= l.x * u.y + l.y * u.x;
+            cfms(v.x, v.y, l.x, l.y, u.x, u.y);
             base[q][addr[q]] = v;
           }
         }
@@ -383,8 +399,7 @@ __global__ void __launch_bounds__(LU_THREADS) lu_coop_kernel(const LUSysT<C>* __
         const C u = __ldcg(S.A + int64_t(i) * n + k);
         const C y = ys[c];
         C v = __ldcg(col + int64_t(i) * r);
-        v.x -= u.x * y.x - u.y * y.y;
-        v.y -= u.x * y.y + u.y * y.x;
+        cfms(v.x, v.y, u.x, u.y, y.x, y.y);
         col[int64_t(i) * r] = v;
       }
       __syncthreads();
@@ -403,7 +418,12 @@ __global__ void __launch_bounds__(LU_THREADS) lu_coop_kernel(const LUSysT<C>* __
 }
 
 template <class C>
-void lu_solve_batched(const std::vector<LUSysT<C>>& systems, cudaStream_t s) {
+void lu_solve_batched(const std::vector<LUSysT<C>>& all, cudaStream_t s) {
+  std::vector<LUSysT<C>> systems;
+  for (auto& S : all) {
+    if (S.n >= LU_BLOCKED_MIN) lu_solve_blocked<C>(S, s);
+    else systems.push_back(S);
+  }
   if (systems.empty()) return;
   int dev = 0, nsm = 0;
   SLDM_CUDA(cudaGetDevice(&dev));
@@ -527,8 +547,8 @@ __global__ void __launch_bounds__(256) gemv_jobs_kernel(const GemvJob* __restric
         for (int r = 0; r < NR; ++r) {
           if (r < nrhs) {
             const C x0 = x[int64_t(r) * J.ldx + 2 * c], x1 = x[int64_t(r) * J.ldx + 2 * c + 1];
-            accr[r] += a.x * R(x0.x) - a.y * R(x0.y) + a.z * R(x1.x) - a.w * R(x1.y);
-            acci[r] += a.x * R(x0.y) + a.y * R(x0.x) + a.z * R(x1.y) + a.w * R(x1.x);
+            cfma(accr[r], acci[r], R(a.x), R(a.y), R(x0.x), R(x0.y));
+            cfma(accr[r], acci[r], R(a.z), R(a.w), R(x1.x), R(x1.y));
           }
         }
       }
@@ -538,8 +558,7 @@ __global__ void __launch_bounds__(256) gemv_jobs_kernel(const GemvJob* __restric
         for (int r = 0; r < NR; ++r)
           if (r < nrhs) {
             C xv = x[int64_t(r) * J.ldx + c];
-            accr[r] += R(a.x) * R(xv.x) - R(a.y) * R(xv.y);
-            acci[r] += R(a.x) * R(xv.y) + R(a.y) * R(xv.x);
+            cfma(accr[r], acci[r], R(a.x), R(a.y), R(xv.x), R(xv.y));
           }
       }
     } else {
@@ -549,8 +568,7 @@ __global__ void __launch_bounds__(256) gemv_jobs_kernel(const GemvJob* __restric
         for (int r = 0; r < NR; ++r)
           if (r < nrhs) {
             C xv = x[int64_t(r) * J.ldx + c];
-            accr[r] += R(a.x) * R(xv.x) - R(a.y) * R(xv.y);
-            acci[r] += R(a.x) * R(xv.y) + R(a.y) * R(xv.x);
+            cfma(accr[r], acci[r], R(a.x), R(a.y), R(xv.x), R(xv.y));
           }
       }
     }
@@ -561,8 +579,7 @@ __global__ void __launch_bounds__(256) gemv_jobs_kernel(const GemvJob* __restric
       for (int r = 0; r < NR; ++r)
         if (r < nrhs) {
           C xv = x[int64_t(r) * J.ldx + c];
-          accr[r] += R(a.x) * R(xv.x) - R(a.y) * R(xv.y);
-          acci[r] += R(a.x) * R(xv.y) + R(a.y) * R(xv.x);
+          cfma(accr[r], acci[r], R(a.x), R(a.y), R(xv.x), R(xv.y));
         }
     }
   }
@@ -760,29 +777,40 @@ void apply_glue_combine(const sldm_mesh* m, const ApplyDims& D, double k0, const
 }
 
 // ---------------------------------------------------------------- FP64 vector kernels for GMRES
-// h[i] = V[:, i]^H w  for i < k  (one CTA per column)
-__global__ void dots_kernel(const double2* __restrict__ V, int64_t ldv, const double2* __restrict__ w, int64_t n,
-                            double2* h) {
-  const int i = blockIdx.x;
+// h[i] = V[:, i]^H w  for i < k.  Grid (ceil(k / 8), row chunks): warp j of a CTA
+// takes column 8 blockIdx.x + j over the CTA's chunk of DOTS_CHUNK rows, two
+// 16-byte loads of V and w per lane in flight, and adds its sum to h[i] with
+// atomics (h is cleared first).  V streams once, at full width of the grid.
+constexpr int DOTS_CHUNK = 2048;
+__global__ void __launch_bounds__(256) dots_kernel(const double2* __restrict__ V, int64_t ldv, int k,
+                                                   const double2* __restrict__ w, int64_t n, double2* h) {
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (i >= k) return;
+  const int64_t r0 = int64_t(blockIdx.y) * DOTS_CHUNK;
+  const int64_t r1 = r0 + DOTS_CHUNK < n ? r0 + DOTS_CHUNK : n;
   const double2* v = V + int64_t(i) * ldv;
-  double sr = 0, si = 0;
-  for (int64_t t = threadIdx.x; t < n; t += blockDim.x) {
-    double2 a = v[t], b = w[t];
-    sr += a.x * b.x + a.y * b.y;  // conj(a) b
-    si += a.x * b.y - a.y * b.x;
+  double sr = 0, si = 0, tr = 0, ti = 0;
+  int64_t t = r0 + lane;
+  for (; t + 32 < r1; t += 64) {
+    const double2 a0 = v[t], b0 = w[t], a1 = v[t + 32], b1 = w[t + 32];
+    cfma(sr, si, a0.x, -a0.y, b0.x, b0.y);  // conj(a) b
+    cfma(tr, ti, a1.x, -a1.y, b1.x, b1.y);
   }
-  __shared__ double rr[256], ri[256];
-  rr[threadIdx.x] = sr;
-  ri[threadIdx.x] = si;
-  __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) {
-      rr[threadIdx.x] += rr[threadIdx.x + s];
-      ri[threadIdx.x] += ri[threadIdx.x + s];
-    }
-    __syncthreads();
+  if (t < r1) {
+    const double2 a0 = v[t], b0 = w[t];
+    cfma(sr, si, a0.x, -a0.y, b0.x, b0.y);
   }
-  if (threadIdx.x == 0) h[i] = make_double2(rr[0], ri[0]);
+  sr += tr;
+  si += ti;
+  for (int o = 16; o > 0; o >>= 1) {
+    sr += __shfl_xor_sync(0xffffffffu, sr, o);
+    si += __shfl_xor_sync(0xffffffffu, si, o);
+  }
+  if (lane == 0) {
+    atomicAdd(&h[i].x, sr);
+    atomicAdd(&h[i].y, si);
+  }
 }
 
 // w += sign * V[:, :k] h.  A CTA owns 32 rows; its 8 warps take every 8th
@@ -797,8 +825,7 @@ __global__ void __launch_bounds__(256) vmul_kernel(const double2* __restrict__ V
     for (int i = slice; i < k; i += 8) {
       const double2 v = V[int64_t(i) * ldv + t];
       const double2 c = h[i];
-      sr += v.x * c.x - v.y * c.y;
-      si += v.x * c.y + v.y * c.x;
+      cfma(sr, si, v.x, v.y, c.x, c.y);
     }
   }
   part[slice][lane] = make_double2(sr, si);
@@ -853,7 +880,9 @@ void vscale3(int64_t n, int64_t ne, double s1, double s2, double s3, const doubl
 }
 
 void vdots(const double2* V, int64_t ldv, int k, const double2* w, int64_t n, double2* h, cudaStream_t s) {
-  dots_kernel<<<k, 256, 0, s>>>(V, ldv, w, n, h), ::sldm::count_launch();
+  SLDM_CUDA(cudaMemsetAsync(h, 0, size_t(k) * sizeof(double2), s));
+  dots_kernel<<<dim3(unsigned((k + 7) / 8), unsigned((n + DOTS_CHUNK - 1) / DOTS_CHUNK)), 256, 0, s>>>(V, ldv, k, w, n, h),
+      ::sldm::count_launch();
   SLDM_CUDA(cudaGetLastError());
 }
 void vmul(const double2* V, int64_t ldv, int k, const double2* h, double sign, double2* w, int64_t n, cudaStream_t s) {

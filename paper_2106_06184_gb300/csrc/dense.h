@@ -14,6 +14,12 @@ struct LUSysT {
 typedef LUSysT<double2> LUSys;
 template <class C>
 void lu_solve_batched(const std::vector<LUSysT<C>>& systems, cudaStream_t s);
+// Blocked LU of one large system (lu_blocked.cu); lu_solve_batched sends there
+// every system of order LU_BLOCKED_MIN or more (below that the look-ahead
+// kernel, whose steps need no grid barrier, is faster).
+constexpr int LU_BLOCKED_MIN = 1024;
+template <class C>
+void lu_solve_blocked(const LUSysT<C>& S, cudaStream_t s);
 inline void lu_solve_batched(const std::vector<LUSys>& systems, cudaStream_t s) { lu_solve_batched<double2>(systems, s); }
 
 template <class C>

@@ -7,12 +7,14 @@
 // static grad 1/(4 pi R) is extracted as always.  Pairs whose bounding spheres
 // are farther apart than 40/|Im k| are dropped (G has decayed below e^-40).
 //
-// One warp per (test, source) pair: the lanes stride over the 6 x 4^L source
-// points (each against the six test points), the lanes 0..5 add the closed forms
+// One warp per (test, source) pair: the lanes stride over the 6 x (6 x 4^L)
+// (test point, source point) pairs, the lanes 0..5 add the closed forms
 // of test point q = lane on touching pairs, the moments are summed with
 // shuffles, and lane 0 scatters the 3x3 local block as the unsplit kernels do.
 // Everything is FP64; the destination precision is R.
 #include <algorithm>
+#include <array>
+#include <mutex>
 
 #include "fill_dev.cuh"
 
@@ -68,30 +70,19 @@ __device__ __forceinline__ cd grad_full(cd k, double R) {
   return {-p.r, -p.i};
 }
 
-// Point j of child `sub` of a triangle split L times, relative to the triangle's
-// centroid: ev[i] = v_i - c.  Children of (a, b, c): (a, ab, ca) (ab, b, bc)
-// (ca, bc, c) (ab, bc, ca), the level-l digit of `sub` in bits 2l, 2l+1 (the
-// first split in the highest digit).
-__device__ __forceinline__ void split_point(int sub, int L, int j, const double ev[3][3], double rp[3]) {
-  double B[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
-  for (int l = L - 1; l >= 0; --l) {
-    const int c = (sub >> (2 * l)) & 3;
-    double ab[3], bc[3], ca[3];
-    for (int v = 0; v < 3; ++v) {
-      ab[v] = 0.5 * (B[0][v] + B[1][v]);
-      bc[v] = 0.5 * (B[1][v] + B[2][v]);
-      ca[v] = 0.5 * (B[2][v] + B[0][v]);
-    }
-    for (int v = 0; v < 3; ++v) {
-      if (c == 0) { B[1][v] = ab[v]; B[2][v] = ca[v]; }
-      else if (c == 1) { B[0][v] = ab[v]; B[2][v] = bc[v]; }
-      else if (c == 2) { B[0][v] = ca[v]; B[1][v] = bc[v]; }
-      else { B[0][v] = ab[v]; B[1][v] = bc[v]; B[2][v] = ca[v]; }
-    }
-  }
-  double b[3];
-  for (int v = 0; v < 3; ++v) b[v] = c_bary[j][0] * B[0][v] + c_bary[j][1] * B[1][v] + c_bary[j][2] * B[2][v];
-  for (int d = 0; d < 3; ++d) rp[d] = b[0] * ev[0][d] + b[1] * ev[1][d] + b[2] * ev[2][d];
+// Barycentric coordinates of the points of the composite rule on a triangle
+// split L times (children of (a, b, c): (a, ab, ca) (ab, b, bc) (ca, bc, c)
+// (ab, bc, ca), the 6-point rule on each): point 6 c + j of level L is entry
+// split_off(L) + 6 c + j of the table, x y z = weights of the three vertices.
+__host__ __device__ __forceinline__ int split_off(int L) { return 2 * ((1 << (2 * L)) - 1); }
+struct __align__(32) Bary {
+  double x, y, z, pad;
+};
+
+__device__ __forceinline__ void split_point(const Bary* __restrict__ tab, int L, int pnt, const double ev[3][3],
+                                            double rp[3]) {
+  const Bary b = tab[split_off(L) + pnt];
+  for (int d = 0; d < 3; ++d) rp[d] = b.x * ev[0][d] + b.y * ev[1][d] + b.z * ev[2][d];
 }
 
 __device__ __forceinline__ double bound_radius(const double* c, const double* p0, const double* p1, const double* p2) {
@@ -106,9 +97,9 @@ __device__ __forceinline__ double bound_radius(const double* c, const double* p0
 
 // ---------------------------------------------------------------- L^A, L^phi
 template <class R>
-__global__ void __launch_bounds__(256) fill_L_split(LTask tk, const int8_t* __restrict__ lev, const double* __restrict__ geo,
-                                                    const double* __restrict__ xyz, const int32_t* __restrict__ tri,
-                                                    const int32_t* __restrict__ tri_edge) {
+__global__ void __launch_bounds__(256) fill_L_split(LTask tk, const int8_t* __restrict__ lev, const Bary* __restrict__ tab,
+                                                    const double* __restrict__ geo, const double* __restrict__ xyz,
+                                                    const int32_t* __restrict__ tri, const int32_t* __restrict__ tri_edge) {
   const int64_t pair = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (pair >= int64_t(tk.ntest) * tk.nsrc) return;  // whole warps
@@ -140,31 +131,30 @@ __global__ void __launch_bounds__(256) fill_L_split(LTask tk, const int8_t* __re
   double m[16];
 #pragma unroll
   for (int i = 0; i < 16; ++i) m[i] = 0.0;
-  for (int u = lane; u < nu; u += 32) {
-    const int sub = u / 6, j = u - 6 * (u / 6);
+  // unit u = (source point u / 6, test point u % 6): 36 units even when unsplit
+  for (int u = lane; u < 6 * nu; u += 32) {
+    const int pnt = u / 6, q = u - 6 * pnt;
     double rp[3];
-    split_point(sub, L, j, ev, rp);
-    const double ws = gs[GEO_W + j] * wsc;
-    for (int q = 0; q < 6; ++q) {
-      const double* rq = gt + GEO_RHO + 3 * q;
-      const double D0 = dc[0] + rq[0] - rp[0], D1 = dc[1] + rq[1] - rp[1], D2 = dc[2] + rq[2] - rp[2];
-      const double Rr = sqrt(D0 * D0 + D1 * D1 + D2 * D2);
-      cd g = touch ? (L == 0 ? green_smooth(k, Rr) : green_smooth1(k, Rr)) : green_full(k, Rr);
-      const double w = gt[GEO_W + q] * ws;
-      g.r *= w;
-      g.i *= w;
-      const double qs = rq[0] * rp[0] + rq[1] * rp[1] + rq[2] * rp[2];
-      m[0] += g.r;
-      m[1] += g.i;
-      for (int d = 0; d < 3; ++d) {
-        m[2 + 2 * d] += g.r * rq[d];
-        m[3 + 2 * d] += g.i * rq[d];
-        m[8 + 2 * d] += g.r * rp[d];
-        m[9 + 2 * d] += g.i * rp[d];
-      }
-      m[14] += g.r * qs;
-      m[15] += g.i * qs;
+    split_point(tab, L, pnt, ev, rp);
+    const double ws = gs[GEO_W + pnt % 6] * wsc;
+    const double* rq = gt + GEO_RHO + 3 * q;
+    const double D0 = dc[0] + rq[0] - rp[0], D1 = dc[1] + rq[1] - rp[1], D2 = dc[2] + rq[2] - rp[2];
+    const double Rr = sqrt(D0 * D0 + D1 * D1 + D2 * D2);
+    cd g = touch ? (L == 0 ? green_smooth(k, Rr) : green_smooth1(k, Rr)) : green_full(k, Rr);
+    const double w = gt[GEO_W + q] * ws;
+    g.r *= w;
+    g.i *= w;
+    const double qs = rq[0] * rp[0] + rq[1] * rp[1] + rq[2] * rp[2];
+    m[0] += g.r;
+    m[1] += g.i;
+    for (int d = 0; d < 3; ++d) {
+      m[2 + 2 * d] += g.r * rq[d];
+      m[3 + 2 * d] += g.i * rq[d];
+      m[8 + 2 * d] += g.r * rp[d];
+      m[9 + 2 * d] += g.i * rp[d];
     }
+    m[14] += g.r * qs;
+    m[15] += g.i * qs;
   }
   if (touch && lane < 6) {
     const int q = lane;
@@ -232,7 +222,8 @@ __global__ void __launch_bounds__(256) fill_L_split(LTask tk, const int8_t* __re
 
 // ---------------------------------------------------------------- Kbar (primal test x barycentric child)
 template <class R>
-__global__ void __launch_bounds__(256) fill_K_split(KTask tk, const int8_t* __restrict__ lev, const double* __restrict__ geo,
+__global__ void __launch_bounds__(256) fill_K_split(KTask tk, const int8_t* __restrict__ lev, const Bary* __restrict__ tab,
+                                                    const double* __restrict__ geo,
                                                     const double* __restrict__ bgeo, const double* __restrict__ xyz,
                                                     const int32_t* __restrict__ tri, const int32_t* __restrict__ tri_edge,
                                                     const int32_t* __restrict__ btri_edge) {
@@ -278,32 +269,31 @@ __global__ void __launch_bounds__(256) fill_K_split(KTask tk, const int8_t* __re
   double m[20];
 #pragma unroll
   for (int i = 0; i < 20; ++i) m[i] = 0.0;
-  for (int u = lane; u < nu; u += 32) {
-    const int sub = u / 6, j = u - 6 * (u / 6);
+  // unit u = (source point u / 6, test point u % 6)
+  for (int u = lane; u < 6 * nu; u += 32) {
+    const int pnt = u / 6, q = u - 6 * pnt;
     double rp[3];
-    split_point(sub, L, j, ev, rp);
-    const double ws = gs[GEO_W + j] * wsc;
-    for (int q = 0; q < 6; ++q) {
-      const double* rq = gt + GEO_RHO + 3 * q;
-      const double D[3] = {dc[0] + rq[0] - rp[0], dc[1] + rq[1] - rp[1], dc[2] + rq[2] - rp[2]};
-      const double Rr = sqrt(D[0] * D[0] + D[1] * D[1] + D[2] * D[2]);
-      cd g1 = touch ? grad_smooth(k, Rr) : grad_full(k, Rr);
-      const double w = gt[GEO_W + q] * ws;
-      g1.r *= w;
-      g1.i *= w;
-      const double cr[3] = {D[1] * rp[2] - D[2] * rp[1], D[2] * rp[0] - D[0] * rp[2], D[0] * rp[1] - D[1] * rp[0]};
-      const double xq[3] = {rq[1] * D[2] - rq[2] * D[1], rq[2] * D[0] - rq[0] * D[2], rq[0] * D[1] - rq[1] * D[0]};
-      const double p1 = rq[0] * cr[0] + rq[1] * cr[1] + rq[2] * cr[2];
-      m[0] += g1.r * p1;
-      m[1] += g1.i * p1;
-      for (int d = 0; d < 3; ++d) {
-        m[2 + 2 * d] += g1.r * cr[d];
-        m[3 + 2 * d] += g1.i * cr[d];
-        m[8 + 2 * d] += g1.r * xq[d];
-        m[9 + 2 * d] += g1.i * xq[d];
-        m[14 + 2 * d] += g1.r * D[d];
-        m[15 + 2 * d] += g1.i * D[d];
-      }
+    split_point(tab, L, pnt, ev, rp);
+    const double ws = gs[GEO_W + pnt % 6] * wsc;
+    const double* rq = gt + GEO_RHO + 3 * q;
+    const double D[3] = {dc[0] + rq[0] - rp[0], dc[1] + rq[1] - rp[1], dc[2] + rq[2] - rp[2]};
+    const double Rr = sqrt(D[0] * D[0] + D[1] * D[1] + D[2] * D[2]);
+    cd g1 = touch ? grad_smooth(k, Rr) : grad_full(k, Rr);
+    const double w = gt[GEO_W + q] * ws;
+    g1.r *= w;
+    g1.i *= w;
+    const double cr[3] = {D[1] * rp[2] - D[2] * rp[1], D[2] * rp[0] - D[0] * rp[2], D[0] * rp[1] - D[1] * rp[0]};
+    const double xq[3] = {rq[1] * D[2] - rq[2] * D[1], rq[2] * D[0] - rq[0] * D[2], rq[0] * D[1] - rq[1] * D[0]};
+    const double p1 = rq[0] * cr[0] + rq[1] * cr[1] + rq[2] * cr[2];
+    m[0] += g1.r * p1;
+    m[1] += g1.i * p1;
+    for (int d = 0; d < 3; ++d) {
+      m[2 + 2 * d] += g1.r * cr[d];
+      m[3 + 2 * d] += g1.i * cr[d];
+      m[8 + 2 * d] += g1.r * xq[d];
+      m[9 + 2 * d] += g1.i * xq[d];
+      m[14 + 2 * d] += g1.r * D[d];
+      m[15 + 2 * d] += g1.i * D[d];
     }
   }
   if (touch && lane < 6) {
@@ -409,15 +399,67 @@ std::vector<int8_t> split_levels_K(const HostMesh& h, const KTask& tk) {
   return lev;
 }
 
+// The composite-rule table of every level up to SUB_MAX, built and uploaded once
+// per device and kept for the life of the process (4 MiB).
+static std::mutex g_tab_mu;
+static const Bary* g_tab[64] = {nullptr};
+
+static const Bary* split_table() {
+  int dev = 0;
+  SLDM_CUDA(cudaGetDevice(&dev));
+  SLDM_REQUIRE(dev >= 0 && dev < 64, SLDM_EINVAL, "split table: device index out of range");
+  std::lock_guard<std::mutex> l(g_tab_mu);
+  if (g_tab[dev]) return g_tab[dev];
+  static const double bary[6][3] = {
+      {0.108103018168070, 0.445948490915965, 0.445948490915965}, {0.445948490915965, 0.108103018168070, 0.445948490915965},
+      {0.445948490915965, 0.445948490915965, 0.108103018168070}, {0.816847572980459, 0.091576213509771, 0.091576213509771},
+      {0.091576213509771, 0.816847572980459, 0.091576213509771}, {0.091576213509771, 0.091576213509771, 0.816847572980459}};
+  std::vector<Bary> h(size_t(split_off(SUB_MAX + 1)));
+  typedef std::array<std::array<double, 3>, 3> Tri;  // vertex v: barycentric coordinates
+  std::vector<Tri> cur(1);
+  cur[0] = {{{1, 0, 0}, {0, 1, 0}, {0, 0, 1}}};
+  for (int L = 0; L <= SUB_MAX; ++L) {
+    for (size_t c = 0; c < cur.size(); ++c)
+      for (int j = 0; j < 6; ++j) {
+        double b[3] = {0, 0, 0};
+        for (int v = 0; v < 3; ++v)
+          for (int d = 0; d < 3; ++d) b[d] += bary[j][v] * cur[c][v][d];
+        h[size_t(split_off(L)) + 6 * c + j] = Bary{b[0], b[1], b[2], 0.0};
+      }
+    if (L == SUB_MAX) break;
+    std::vector<Tri> nxt;
+    nxt.reserve(cur.size() * 4);
+    for (const Tri& t : cur) {
+      std::array<double, 3> mab, mbc, mca;
+      for (int d = 0; d < 3; ++d) {
+        mab[d] = 0.5 * (t[0][d] + t[1][d]);
+        mbc[d] = 0.5 * (t[1][d] + t[2][d]);
+        mca[d] = 0.5 * (t[2][d] + t[0][d]);
+      }
+      nxt.push_back({{t[0], mab, mca}});
+      nxt.push_back({{mab, t[1], mbc}});
+      nxt.push_back({{mca, mbc, t[2]}});
+      nxt.push_back({{mab, mbc, mca}});
+    }
+    cur.swap(nxt);
+  }
+  Bary* d = nullptr;
+  SLDM_CUDA(cudaMalloc(&d, h.size() * sizeof(Bary)));
+  SLDM_CUDA(cudaMemcpy(d, h.data(), h.size() * sizeof(Bary), cudaMemcpyHostToDevice));
+  g_tab[dev] = d;
+  return d;
+}
+
 template <class R>
 void fill_L_split_task(const sldm_mesh* m, const LTask& tk, const std::vector<int8_t>& lev, cudaStream_t s) {
+  const Bary* tab = split_table();
   DBuf<int8_t> dl;
   dl.upload(lev, s);
   const int64_t threads = int64_t(tk.ntest) * tk.nsrc * 32;
   const DevMesh& d = m->d;
   {
     ScopedTimer tm("fill_L_split", s);
-    fill_L_split<R><<<unsigned((threads + 255) / 256), 256, 0, s>>>(tk, dl.p, d.geo.p, d.xyz.p, d.tri.p, d.tri_edge.p),
+    fill_L_split<R><<<unsigned((threads + 255) / 256), 256, 0, s>>>(tk, dl.p, tab, d.geo.p, d.xyz.p, d.tri.p, d.tri_edge.p),
         ::sldm::count_launch();
   }
   SLDM_CUDA(cudaGetLastError());
@@ -426,13 +468,14 @@ void fill_L_split_task(const sldm_mesh* m, const LTask& tk, const std::vector<in
 
 template <class R>
 void fill_K_split_task(const sldm_mesh* m, const KTask& tk, const std::vector<int8_t>& lev, cudaStream_t s) {
+  const Bary* tab = split_table();
   DBuf<int8_t> dl;
   dl.upload(lev, s);
   const int64_t threads = int64_t(tk.ntest) * tk.nsrc * 32;
   const DevMesh& d = m->d;
   {
     ScopedTimer tm("fill_K_split", s);
-    fill_K_split<R><<<unsigned((threads + 255) / 256), 256, 0, s>>>(tk, dl.p, d.geo.p, d.bgeo.p, d.xyz.p, d.tri.p,
+    fill_K_split<R><<<unsigned((threads + 255) / 256), 256, 0, s>>>(tk, dl.p, tab, d.geo.p, d.bgeo.p, d.xyz.p, d.tri.p,
                                                                    d.tri_edge.p, d.btri_edge.p), ::sldm::count_launch();
   }
   SLDM_CUDA(cudaGetLastError());

@@ -290,7 +290,7 @@ class Operator:
                                                    pol.ctypes.data_as(C.c_void_p), len(khat), pb, wb, _stream(stream)))
         return b
 
-    def solve(self, b, x, nrhs=1, tol=1e-8, restart=100, maxit=2000, x0=False, precond=True, stream=None, check=True):
+    def solve(self, b, x, nrhs=1, tol=1e-8, restart=300, maxit=2000, x0=False, precond=True, stream=None, check=True):
         pb, wb = _ptr(b)
         px, wx = _ptr(x)
         assert wb == wx
