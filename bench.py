@@ -43,13 +43,13 @@ WORKLOADS = {
 }
 # n x n dielectric cylinders (eps_r 6, r 120 nm, h 300 nm, period 500 nm, 240 triangles
 # each) in free space at 1 um, complex FP32 operator (FP64 singular terms), one plane
-# wave at normal incidence.  8 x 8: 15,360 triangles, N = 61,376; 4 x 4 is the small
+# wave at normal incidence, GMRES with FP64-residual iterative refinement to 1e-8.  8 x 8: 15,360 triangles, N = 61,376; 4 x 4 is the small
 # case kept for profiling captures (global blocks 383 MB, above the L2 size).
 for _n in (8, 4):
     WORKLOADS[f"metasurface-{_n}x{_n}-cyl-epsr6-1um-freespace-c64"] = dict(
         mesh=(lambda n=_n: cylinder_array(n, n, 120e-9, 300e-9, 500e-9)[:2]), obj=("array", _n),
         mats=[(6.0, 1.0, 0.0)] * (_n * _n), bg=(1.0, 1.0, 0.0, 0.0), freq=299792458.0 / 1e-6, precision=1,
-        tol=1e-5, khat=[0.0, 0.0, -1.0], pol=[1.0, 0.0, 0.0], n_angles=181)
+        tol=1e-8, khat=[0.0, 0.0, -1.0], pol=[1.0, 0.0, 0.0], n_angles=181)
 # Multiscale conductor in a layered substrate: a copper bar (sigma 5.8e7 S/m,
 # 100 x 2 x 1 um, 2,048 graded triangles, N = 8,191) in the middle of a 10 um SiO2
 # layer (eps_r 3.9) over 200 um of Si (eps_r 11.9, sigma 10 S/m) over a PEC ground,

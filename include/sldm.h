@@ -108,6 +108,8 @@ typedef struct {
 
 #define SLDM_PRECOND_P 0     /* right preconditioner P of Eq. pcext (default) */
 #define SLDM_PRECOND_NONE 1  /* no preconditioner */
+#define SLDM_REFINE_AUTO 0   /* complex64 operators: FP64 residuals, iterative refinement (default) */
+#define SLDM_REFINE_OFF 1    /* residuals in the operator's precision */
 
 typedef struct {
   double tol;           /* relative residual of the length-scaled system (default 1e-8), see sldm_solve */
@@ -115,6 +117,8 @@ typedef struct {
   int32_t maxit;        /* maximum total iterations (default 2000) */
   int32_t x0_given;     /* nonzero: x holds the initial guess on entry */
   int32_t precond;      /* SLDM_PRECOND_P (0, default) or SLDM_PRECOND_NONE */
+  int32_t refine;       /* SLDM_REFINE_AUTO (0, default) or SLDM_REFINE_OFF; see sldm_solve */
+  int32_t reserved;
 } sldm_solve_opts;
 
 typedef struct {
@@ -222,6 +226,11 @@ int sldm_rhs_planewave(const sldm_op* op, const double* khat, const double* pol,
  * Dc = diag(1/l, 1, l) on the blocks [j; e; u], l = the mesh's mean edge
  * length), whose blocks are O(1) for any geometry size in metres; tol and the
  * reported relres refer to ||Dr (b - Z x)|| / ||Dr b||.
+ * Complex64 operators (unless refine = SLDM_REFINE_OFF): iterative refinement
+ * with an FP64 residual.  The residual at every restart is the product of the
+ * stored complex64 blocks with complex128 vectors, accumulated in FP64, and each
+ * GMRES cycle (products in complex64) stops once it has reduced that residual
+ * by 1e-5; tol then refers to the FP64 residual of the stored operator.
  * Returns SLDM_ENOTCONV (x holds the last iterate) if tol is not reached. */
 int sldm_solve(const sldm_op* op, const void* b, void* x, int32_t nrhs, const sldm_solve_opts* opts,
                sldm_solve_info* info, int32_t where, void* stream);

@@ -51,6 +51,10 @@ struct sldm_op {
   sldm::DBuf<sldm::GemvJob> jobs1, jobs2;
   sldm::DBuf<int64_t> rs1, rs2;
   sldm::GemvPlan plan1, plan2;
+  // complex64 operator applied with complex128 vectors (FP64 residuals of iterative refinement)
+  sldm::DBuf<sldm::GemvJob> jobs1d, jobs2d;
+  sldm::DBuf<int64_t> rs1d, rs2d;
+  sldm::GemvPlan plan1d, plan2d;
   // layered background (external problem with the multilayer kernel)
   bool layered = false;
   sldm::MgfStackHost H;
@@ -73,20 +77,15 @@ static int64_t op_bytes(const sldm_op* op) {
                  op->pc.sinv.bytes() + op->pc.lam.bytes() + op->pc.pdiag.bytes());
 }
 
-template <class C>
-static void build_plans(sldm_op* op) {
+// GEMV plans of the structured product with matrix entries of es_m bytes and
+// vector entries of es_v bytes (the work vectors hold complex128, so both the
+// operator's precision and FP64 fit).
+static void make_plans(sldm_op* op, size_t es_m, size_t es_v, DBuf<GemvJob>& dj1, DBuf<int64_t>& drs1, GemvPlan& p1,
+                       DBuf<GemvJob>& dj2, DBuf<int64_t>& drs2, GemvPlan& p2) {
   const int64_t ne = op->ne, nt = op->nt, nq = op->nq;
-  const int WR = sldm_op::WR;
-  const size_t es = sizeof(C);
-  op->wj.alloc(ne * WR * es); op->we.alloc(ne * WR * es); op->wu.alloc(std::max<int64_t>(nq, 1) * WR * es);
-  op->wt1.alloc(ne * WR * es); op->wt2.alloc(std::max<int64_t>(nq, 1) * WR * es);
-  op->wa.alloc(ne * WR * es); op->wc.alloc(std::max<int64_t>(nq, 1) * WR * es);
-  op->wbc.alloc(nt * WR * es); op->wbu.alloc(nt * WR * es);
-  op->wz1.alloc(ne * WR * es); op->wz2.alloc(nt * WR * es);
-  op->ww1.alloc(ne * WR * es); op->ww2.alloc(ne * WR * es); op->ww3.alloc(nt * WR * es);
-  auto P = [&](DBuf<char>& b, int64_t off) { return (void*)(b.p + off * es); };
+  auto P = [&](DBuf<char>& b, int64_t off) { return (void*)(b.p + off * es_v); };
   const char* loc = op->loc.p;
-  auto L = [&](int64_t off) { return (const void*)(loc + off * es); };
+  auto L = [&](int64_t off) { return (const void*)(loc + off * es_m); };
   std::vector<GemvJob> j1, j2;
   for (auto& o : op->obj) {
     j1.push_back({L(o.oY11), o.ne, o.ne, o.ne, P(op->we, o.e0), ne, P(op->wt1, o.e0), ne, 1, 0, 0, 0});
@@ -113,35 +112,61 @@ static void build_plans(sldm_op* op) {
     plan.njobs = int(j.size());
     plan.total_rows = acc;
   };
-  mk(j1, op->jobs1, op->rs1, op->plan1);
-  mk(j2, op->jobs2, op->rs2, op->plan2);
-  op->plan1.name = "gemv_y";     // Y11, Y21 (per object)
-  op->plan2.name = "gemv_main";  // L^A_m, L^phi_m and the internal blocks
+  mk(j1, dj1, drs1, p1);
+  mk(j2, dj2, drs2, p2);
+  p1.name = "gemv_y";     // Y11, Y21 (per object)
+  p2.name = "gemv_main";  // L^A_m, L^phi_m and the internal blocks
+}
+
+template <class C>
+static void build_plans(sldm_op* op) {
+  const int64_t ne = op->ne, nt = op->nt, nq = op->nq;
+  const int WR = sldm_op::WR;
+  const size_t ev = sizeof(double2);
+  op->wj.alloc(ne * WR * ev); op->we.alloc(ne * WR * ev); op->wu.alloc(std::max<int64_t>(nq, 1) * WR * ev);
+  op->wt1.alloc(ne * WR * ev); op->wt2.alloc(std::max<int64_t>(nq, 1) * WR * ev);
+  op->wa.alloc(ne * WR * ev); op->wc.alloc(std::max<int64_t>(nq, 1) * WR * ev);
+  op->wbc.alloc(nt * WR * ev); op->wbu.alloc(nt * WR * ev);
+  op->wz1.alloc(ne * WR * ev); op->wz2.alloc(nt * WR * ev);
+  op->ww1.alloc(ne * WR * ev); op->ww2.alloc(ne * WR * ev); op->ww3.alloc(nt * WR * ev);
+  make_plans(op, sizeof(C), sizeof(C), op->jobs1, op->rs1, op->plan1, op->jobs2, op->rs2, op->plan2);
+  if (sizeof(C) == sizeof(float2)) {
+    make_plans(op, sizeof(C), sizeof(double2), op->jobs1d, op->rs1d, op->plan1d, op->jobs2d, op->rs2d, op->plan2d);
+    op->plan1d.name = "gemv_y_f64acc";
+    op->plan2d.name = "gemv_main_f64acc";
+  }
 }
 
 // y = Z x for nrhs columns, x/y complex128 on the device (column stride N)
-template <class C>
-static void apply_dev(const sldm_op* op_, const double2* x, double2* y, int nrhs, cudaStream_t s) {
+// y = Z x: matrix entries CM, vectors and accumulation CV
+template <class CM, class CV>
+static void apply_dev(const sldm_op* op_, const double2* x, double2* y, int nrhs, cudaStream_t s, const GemvPlan& p1,
+                      const GemvPlan& p2) {
   sldm_op* op = const_cast<sldm_op*>(op_);
   ApplyDims D{int32_t(op->ne), int32_t(op->nt), int32_t(op->nq), int32_t(op->nobj)};
   for (int r0 = 0; r0 < nrhs; r0 += sldm_op::WR) {
     int nr = std::min(sldm_op::WR, nrhs - r0);
     const double2* xr = x + int64_t(r0) * op->N;
     double2* yr = y + int64_t(r0) * op->N;
-    apply_glue_split<C>(xr, op->N, D, op->wj.p, op->we.p, op->wu.p, nr, s);
-    gemv_jobs<C>(op->plan1, nr, s);
-    apply_glue_prep<C>(op->mesh, D, op->wj.p, op->wu.p, op->wt1.p, op->wt2.p, op->wa.p, op->wc.p, op->wbc.p, op->wbu.p, nr, s,
-                       op->mesh->d.tri_begin.p, op->mesh->d.edge_begin.p);
-    gemv_jobs<C>(op->plan2, nr, s);
-    apply_glue_combine<C>(op->mesh, D, op->k0, op->ix_val.p, op->wz1.p, op->wz2.p, op->ww1.p, op->ww2.p, op->ww3.p,
-                          op->we.p, op->wa.p, op->wc.p, yr, op->N, nr, s);
+    apply_glue_split<CV>(xr, op->N, D, op->wj.p, op->we.p, op->wu.p, nr, s);
+    gemv_jobs_mixed<CM, CV>(p1, nr, s);
+    apply_glue_prep<CV>(op->mesh, D, op->wj.p, op->wu.p, op->wt1.p, op->wt2.p, op->wa.p, op->wc.p, op->wbc.p, op->wbu.p, nr,
+                        s, op->mesh->d.tri_begin.p, op->mesh->d.edge_begin.p);
+    gemv_jobs_mixed<CM, CV>(p2, nr, s);
+    apply_glue_combine<CV>(op->mesh, D, op->k0, op->ix_val.p, op->wz1.p, op->wz2.p, op->ww1.p, op->ww2.p, op->ww3.p,
+                           op->we.p, op->wa.p, op->wc.p, yr, op->N, nr, s);
   }
 }
 
-static void apply_any(const sldm_op* op, const double2* x, double2* y, int nrhs, cudaStream_t s) {
+// acc64: a complex64 operator's product accumulated in FP64 (iterative refinement)
+static void apply_any(const sldm_op* op, const double2* x, double2* y, int nrhs, cudaStream_t s, bool acc64 = false) {
   ScopedTimer tm("apply", s);
-  if (op->prec == SLDM_PREC_F32) apply_dev<float2>(op, x, y, nrhs, s);
-  else apply_dev<double2>(op, x, y, nrhs, s);
+  if (op->prec == SLDM_PREC_F32) {
+    if (acc64) apply_dev<float2, double2>(op, x, y, nrhs, s, op->plan1d, op->plan2d);
+    else apply_dev<float2, float2>(op, x, y, nrhs, s, op->plan1, op->plan2);
+  } else {
+    apply_dev<double2, double2>(op, x, y, nrhs, s, op->plan1, op->plan2);
+  }
 }
 
 static cplx eps_complex(double eps_r, double sigma, double omega) { return cplx(eps_r, -sigma / (omega * EPS0_)); }
@@ -348,8 +373,13 @@ static void op_hat(sldm_op* op, bool use_p, const double2* v, double2* w, cudaSt
 
 // Solves one right-hand side held in op->wb into op->wx (initial guess in wx)
 // by restarted, right-preconditioned GMRES on the length-scaled system;
-// relres = ||Dr (b - Z x)|| / ||Dr b||.
-static void gmres_one(sldm_op* op, bool use_p, int m, double tol, int maxit, int& iters, double& relres, cudaStream_t s) {
+// relres = ||Dr (b - Z x)|| / ||Dr b||.  With `refine` (complex64 operators) the
+// true residual at every restart is accumulated in FP64 and each cycle stops
+// once it has reduced that residual by REFINE_CYCLE: the cycles are the
+// correction solves of iterative refinement, in the operator's precision.
+constexpr double REFINE_CYCLE = 1e-5;
+static void gmres_one(sldm_op* op, bool use_p, bool refine, int m, double tol, int maxit, int& iters, double& relres,
+                      cudaStream_t s) {
   const int64_t N = op->N;
   const double l = op->mesh->h.ell;
   double2* V = op->V.p;
@@ -361,7 +391,7 @@ static void gmres_one(sldm_op* op, bool use_p, int m, double tol, int maxit, int
     return;
   }
   auto residual = [&]() {  // wr = Dr (b - Z x)
-    apply_any(op, op->wx.p, op->wr.p, 1, s);
+    apply_any(op, op->wx.p, op->wr.p, 1, s, refine);
     vscale3(N, op->ne, 1.0, 1.0, l, op->wr.p, op->wr.p, s);
     vaxpby(N, 1.0, op->wb.p, -1.0, op->wr.p, s);
     return dnorm(op, op->wr.p, s);
@@ -413,6 +443,7 @@ static void gmres_one(sldm_op* op, bool use_p, int m, double tol, int maxit, int
       ++iters;
       kused = k + 1;
       if (std::abs(g[k + 1]) / bnorm <= tol || iters >= maxit || hn == 0) break;
+      if (refine && std::abs(g[k + 1]) <= REFINE_CYCLE * beta) break;
     }
     // y = H^-1 g (upper triangular);  x += (P^-1 Dr^-1 or Dc) V y
     std::vector<cplx> y(kused);
@@ -811,6 +842,7 @@ int sldm_solve(const sldm_op* op_, const void* b, void* x, int32_t nrhs, const s
   int maxit = (opts && opts->maxit > 0) ? opts->maxit : 2000;
   bool x0 = opts && opts->x0_given;
   bool use_p = !(opts && opts->precond == SLDM_PRECOND_NONE) && op->pc.ready;
+  bool refine = op->prec == SLDM_PREC_F32 && !(opts && opts->refine == SLDM_REFINE_OFF);
   cudaStream_t s = (cudaStream_t)stream;
   ensure_ws(op, m);
   const size_t vb = size_t(op->N) * sizeof(double2);
@@ -824,7 +856,7 @@ int sldm_solve(const sldm_op* op_, const void* b, void* x, int32_t nrhs, const s
     if (x0) SLDM_CUDA(cudaMemcpyAsync(op->wx.p, xr, vb, k_in, s));
     else SLDM_CUDA(cudaMemsetAsync(op->wx.p, 0, vb, s));
     double rel = 0;
-    gmres_one(op, use_p, m, tol, maxit, iters, rel, s);
+    gmres_one(op, use_p, refine, m, tol, maxit, iters, rel, s);
     worst = std::max(worst, rel);
     cudaMemcpyKind k_out = where == SLDM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     SLDM_CUDA(cudaMemcpyAsync(xr, op->wx.p, vb, k_out, s));

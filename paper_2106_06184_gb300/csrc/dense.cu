@@ -514,11 +514,15 @@ template void lu_solve_batched<double2>(const std::vector<LUSysT<double2>>&, cud
 
 // ---------------------------------------------------------------- batched skinny GEMV
 // Each warp owns one row of one job and produces that row for all right-hand
-// sides of the pass.  Rows are split over jobs by an exclusive prefix sum.
-template <class C, int NR>
+// sides of the pass.  Rows are split over jobs by an exclusive prefix sum.  The
+// matrix entries are CM (complex64 or complex128) and stream through once with
+// two 16-byte loads per lane in flight; the vectors and the accumulation are CV
+// (a complex64 matrix may be applied in FP64: the residual of iterative
+// refinement).
+template <class CM, class CV, int NR>
 __global__ void __launch_bounds__(256) gemv_jobs_kernel(const GemvJob* __restrict__ jobs, const int64_t* __restrict__ rowstart,
                                                         int njobs, int64_t total_rows, int nrhs) {
-  typedef typename CT<C>::R R;
+  typedef typename CT<CV>::R R;
   const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= total_rows) return;
@@ -530,59 +534,52 @@ __global__ void __launch_bounds__(256) gemv_jobs_kernel(const GemvJob* __restric
   }
   const GemvJob J = jobs[lo];
   const int64_t row = warp - rowstart[lo];
-  const C* __restrict__ A = reinterpret_cast<const C*>(J.A) + row * J.lda;
-  const C* __restrict__ x = reinterpret_cast<const C*>(J.x);
+  const CM* __restrict__ A = reinterpret_cast<const CM*>(J.A) + row * J.lda;
+  const CV* __restrict__ x = reinterpret_cast<const CV*>(J.x);
   R accr[NR], acci[NR];
 #pragma unroll
   for (int r = 0; r < NR; ++r) accr[r] = acci[r] = R(0);
-  if (sizeof(C) == 8) {
+  auto mac1 = [&](const CM a, int c) {
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+      if (r < nrhs) {
+        const CV xv = x[int64_t(r) * J.ldx + c];
+        cfma(accr[r], acci[r], R(a.x), R(a.y), R(xv.x), R(xv.y));
+      }
+  };
+  int c0 = 0;  // first column left to the scalar loop
+  if (sizeof(CM) == 8 && ((reinterpret_cast<uintptr_t>(A) & 15) == 0)) {
     // complex64: 16-byte loads of two consecutive entries
     const int n2 = J.n / 2;
     const float4* A4 = reinterpret_cast<const float4*>(A);
-    const bool aligned = ((reinterpret_cast<uintptr_t>(A) & 15) == 0);
-    if (aligned) {
-      for (int c = lane; c < n2; c += 32) {
-        float4 a = __ldcs(A4 + c);
-#pragma unroll
-        for (int r = 0; r < NR; ++r) {
-          if (r < nrhs) {
-            const C x0 = x[int64_t(r) * J.ldx + 2 * c], x1 = x[int64_t(r) * J.ldx + 2 * c + 1];
-            cfma(accr[r], acci[r], R(a.x), R(a.y), R(x0.x), R(x0.y));
-            cfma(accr[r], acci[r], R(a.z), R(a.w), R(x1.x), R(x1.y));
-          }
-        }
-      }
-      for (int c = 2 * n2 + lane; c < J.n; c += 32) {
-        C a = A[c];
-#pragma unroll
-        for (int r = 0; r < NR; ++r)
-          if (r < nrhs) {
-            C xv = x[int64_t(r) * J.ldx + c];
-            cfma(accr[r], acci[r], R(a.x), R(a.y), R(xv.x), R(xv.y));
-          }
-      }
-    } else {
-      for (int c = lane; c < J.n; c += 32) {
-        C a = A[c];
-#pragma unroll
-        for (int r = 0; r < NR; ++r)
-          if (r < nrhs) {
-            C xv = x[int64_t(r) * J.ldx + c];
-            cfma(accr[r], acci[r], R(a.x), R(a.y), R(xv.x), R(xv.y));
-          }
-      }
-    }
-  } else {
-    for (int c = lane; c < J.n; c += 32) {
-      C a = __ldcs(A + c);
+    auto mac2 = [&](const float4 a, int c) {
 #pragma unroll
       for (int r = 0; r < NR; ++r)
         if (r < nrhs) {
-          C xv = x[int64_t(r) * J.ldx + c];
-          cfma(accr[r], acci[r], R(a.x), R(a.y), R(xv.x), R(xv.y));
+          const CV x0 = x[int64_t(r) * J.ldx + 2 * c], x1 = x[int64_t(r) * J.ldx + 2 * c + 1];
+          cfma(accr[r], acci[r], R(a.x), R(a.y), R(x0.x), R(x0.y));
+          cfma(accr[r], acci[r], R(a.z), R(a.w), R(x1.x), R(x1.y));
         }
+    };
+    int c = lane;
+    for (; c + 32 < n2; c += 64) {
+      const float4 a0 = __ldcs(A4 + c), a1 = __ldcs(A4 + c + 32);
+      mac2(a0, c);
+      mac2(a1, c + 32);
     }
+    if (c < n2) mac2(__ldcs(A4 + c), c);
+    c0 = 2 * n2;
+  } else if (sizeof(CM) == 16) {
+    int c = lane;
+    for (; c + 32 < J.n; c += 64) {
+      const CM a0 = __ldcs(A + c), a1 = __ldcs(A + c + 32);
+      mac1(a0, c);
+      mac1(a1, c + 32);
+    }
+    if (c < J.n) mac1(__ldcs(A + c), c);
+    c0 = J.n;
   }
+  for (int c = c0 + lane; c < J.n; c += 32) mac1(A[c], c);
 #pragma unroll
   for (int r = 0; r < NR; ++r) {
 #pragma unroll
@@ -592,13 +589,13 @@ __global__ void __launch_bounds__(256) gemv_jobs_kernel(const GemvJob* __restric
     }
   }
   if (lane == 0) {
-    C* y = reinterpret_cast<C*>(J.y);
+    CV* y = reinterpret_cast<CV*>(J.y);
 #pragma unroll
     for (int r = 0; r < NR; ++r)
       if (r < nrhs) {
         R vr = R(J.ar) * accr[r] - R(J.ai) * acci[r];
         R vi = R(J.ar) * acci[r] + R(J.ai) * accr[r];
-        C* yy = y + int64_t(r) * J.ldy + row;
+        CV* yy = y + int64_t(r) * J.ldy + row;
         if (J.beta) {
           vr += yy->x;
           vi += yy->y;
@@ -609,19 +606,27 @@ __global__ void __launch_bounds__(256) gemv_jobs_kernel(const GemvJob* __restric
   }
 }
 
-template <class C>
-void gemv_jobs(const GemvPlan& plan, int nrhs, cudaStream_t s) {
+template <class CM, class CV>
+void gemv_jobs_mixed(const GemvPlan& plan, int nrhs, cudaStream_t s) {
   if (plan.njobs == 0) return;
   const int64_t threads = plan.total_rows * 32;
   const unsigned blocks = unsigned((threads + 255) / 256);
   ScopedTimer tm(plan.name, s);
   if (nrhs <= 1)
-    gemv_jobs_kernel<C, 1><<<blocks, 256, 0, s>>>(plan.jobs, plan.rowstart, plan.njobs, plan.total_rows, nrhs), ::sldm::count_launch();
+    gemv_jobs_kernel<CM, CV, 1><<<blocks, 256, 0, s>>>(plan.jobs, plan.rowstart, plan.njobs, plan.total_rows, nrhs), ::sldm::count_launch();
   else if (nrhs <= 4)
-    gemv_jobs_kernel<C, 4><<<blocks, 256, 0, s>>>(plan.jobs, plan.rowstart, plan.njobs, plan.total_rows, nrhs), ::sldm::count_launch();
+    gemv_jobs_kernel<CM, CV, 4><<<blocks, 256, 0, s>>>(plan.jobs, plan.rowstart, plan.njobs, plan.total_rows, nrhs), ::sldm::count_launch();
   else
-    gemv_jobs_kernel<C, 8><<<blocks, 256, 0, s>>>(plan.jobs, plan.rowstart, plan.njobs, plan.total_rows, nrhs), ::sldm::count_launch();
+    gemv_jobs_kernel<CM, CV, 8><<<blocks, 256, 0, s>>>(plan.jobs, plan.rowstart, plan.njobs, plan.total_rows, nrhs), ::sldm::count_launch();
   SLDM_CUDA(cudaGetLastError());
+}
+template void gemv_jobs_mixed<float2, double2>(const GemvPlan&, int, cudaStream_t);
+template void gemv_jobs_mixed<float2, float2>(const GemvPlan&, int, cudaStream_t);
+template void gemv_jobs_mixed<double2, double2>(const GemvPlan&, int, cudaStream_t);
+
+template <class C>
+void gemv_jobs(const GemvPlan& plan, int nrhs, cudaStream_t s) {
+  gemv_jobs_mixed<C, C>(plan, nrhs, s);
 }
 
 // ---------------------------------------------------------------- structured product glue

@@ -48,6 +48,9 @@ struct GemvPlan {
 };
 template <class C>
 void gemv_jobs(const GemvPlan& plan, int nrhs, cudaStream_t s);
+// complex64 matrix, complex128 vectors, FP64 accumulation
+template <class CM, class CV>
+void gemv_jobs_mixed(const GemvPlan& plan, int nrhs, cudaStream_t s);
 
 struct ApplyDims {
   int32_t ne, nt, nq, nobj;

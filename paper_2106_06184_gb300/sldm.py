@@ -48,7 +48,7 @@ class AssembleOpts(C.Structure):
 
 class SolveOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("restart", C.c_int32), ("maxit", C.c_int32),
-                ("x0_given", C.c_int32), ("precond", C.c_int32)]
+                ("x0_given", C.c_int32), ("precond", C.c_int32), ("refine", C.c_int32), ("reserved", C.c_int32)]
 
 
 class SolveInfo(C.Structure):
@@ -290,11 +290,12 @@ class Operator:
                                                    pol.ctypes.data_as(C.c_void_p), len(khat), pb, wb, _stream(stream)))
         return b
 
-    def solve(self, b, x, nrhs=1, tol=1e-8, restart=300, maxit=2000, x0=False, precond=True, stream=None, check=True):
+    def solve(self, b, x, nrhs=1, tol=1e-8, restart=300, maxit=2000, x0=False, precond=True, refine=True, stream=None,
+              check=True):
         pb, wb = _ptr(b)
         px, wx = _ptr(x)
         assert wb == wx
-        opts = SolveOpts(tol, restart, maxit, int(bool(x0)), 0 if precond else 1)
+        opts = SolveOpts(tol, restart, maxit, int(bool(x0)), 0 if precond else 1, 0 if refine else 1, 0)
         info = SolveInfo()
         code = self.L.lib.sldm_solve(self.h, pb, px, nrhs, C.byref(opts), C.byref(info), wb, _stream(stream))
         if check:

@@ -202,3 +202,33 @@ def test_preconditioner_cuts_iterations_same_solution(which, request):
     inn = op.solve(b, xn, tol=1e-10, maxit=3000, precond=False)
     assert ip["iters"] < inn["iters"] / 2, (ip, inn)
     assert rel(xp, case.x) < 1e-8 and rel(xn, case.x) < 1e-8
+
+
+def test_fp32_refinement_reaches_fp64_residual(sphere):
+    """Iterative refinement of a complex64 operator: the FP64 residual of the stored
+    complex64 system (rebuilt here from the copied-out blocks by the oracle's
+    final_matrix) reaches 1e-10, while the solution stays within the FP32 fill's
+    distance of the FP64 oracle."""
+    import copy
+    sl, m, st, op = build_op(sphere, 1)
+    b = np.zeros(op.N, complex)
+    op.rhs_planewave([0, 0, -1.0], [1.0, 0, 0], b)
+    x = np.zeros(op.N, complex)
+    info = op.solve(b, x, tol=1e-10)
+    assert info["relres"] < 1e-10
+    A32 = copy.copy(sphere.A)
+    A32.LAm, A32.LPm, A32.Ix = op.block(sl.BLOCK_LAM), op.block(sl.BLOCK_LPM), op.block(sl.BLOCK_IX)
+    A32.blocks = [dict(bl, LA=op.block(sl.BLOCK_LA, o), LP=op.block(sl.BLOCK_LP, o), K=op.block(sl.BLOCK_K, o),
+                       Y11=op.block(sl.BLOCK_Y11, o), Y21=op.block(sl.BLOCK_Y21, o))
+                  for o, bl in enumerate(sphere.A.blocks)]
+    Z32 = S.final_matrix(A32)
+    om = sphere.om
+    ell = np.mean(np.linalg.norm(om.xyz[om.E.uv[:, 0]] - om.xyz[om.E.uv[:, 1]], axis=1))
+    dr = np.ones(op.N)
+    dr[2 * om.ne:] = ell
+    assert np.linalg.norm(dr * (Z32 @ x - b)) < 2e-10 * np.linalg.norm(dr * b)
+    assert rel(x, sphere.x) < 5e-4
+    # without refinement the complex64 products floor the residual far above that
+    x2 = np.zeros(op.N, complex)
+    info2 = op.solve(b, x2, tol=1e-10, refine=False, maxit=400, check=False)
+    assert info2["relres"] > 1e-9
