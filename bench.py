@@ -450,10 +450,10 @@ for o in range(m.nobj):
         est += timed_pairs(F._K_pairs, k, ta, cb, Pb, touch_K, 6.0 * n_o ** 2)
     # Y = M_l^-1 R_l on half-size random matrices, scaled by 8
     e0_, e1_ = m.edge_range[o]
-    n, r = (e1_ - e0_ + n_o - 1) // 2, (e1_ - e0_) // 2
+    n, r = (e1_ - e0_ + n_o - 1) // {ddiv}, (e1_ - e0_) // {ddiv}
     A_ = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
     B_ = rng.standard_normal((n, r)) + 1j * rng.standard_normal((n, r))
-    t0 = time.perf_counter(); np.linalg.solve(A_, B_); est += 8 * (time.perf_counter() - t0)
+    t0 = time.perf_counter(); np.linalg.solve(A_, B_); est += {ddiv} ** 3 * (time.perf_counter() - t0)
 if st is not None:
     t0 = time.perf_counter()
     T = S.default_tables(m, st, lay, omega)
@@ -463,25 +463,27 @@ if st is not None:
     LY.fill_reflected(m, st, lay, omega, T, sub)
     est += (time.perf_counter() - t0) * (m.nt / len(sub)) ** 2
 N = 2 * m.ne + m.nt - m.nobj
-A_ = rng.standard_normal((N // 2, N // 2)) + 1j * rng.standard_normal((N // 2, N // 2))
-t0 = time.perf_counter(); sla.lu_solve(sla.lu_factor(A_), np.ones(N // 2)); est += 8 * (time.perf_counter() - t0)
+A_ = rng.standard_normal((N // {ddiv}, N // {ddiv})) + 1j * rng.standard_normal((N // {ddiv}, N // {ddiv}))
+t0 = time.perf_counter(); sla.lu_solve(sla.lu_factor(A_), np.ones(N // {ddiv})); est += {ddiv} ** 3 * (time.perf_counter() - t0)
 print(est, time.perf_counter() - t_all)
 """
 
 
-def oracle_step_seconds(name=None, step=0):
-    """Seconds of one oracle solve of the workload (single thread) and the sample's description."""
+def oracle_step_seconds(name=None, step=0, quick=False):
+    """Seconds of one oracle solve of the workload (single thread) and the sample's description.
+    quick: a smaller sample (the reference arm times one per step)."""
     name = name or DEFAULT_WORKLOAD
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     if name.startswith("sphere"):
         script = ORACLE_FULL.format(root=ROOT)
         sample = "one full solve of the workload (oracle assemble + dense LU + RCS), single thread"
     else:
-        npairs, nsub = 3000, 96
-        script = ORACLE_SAMPLED.format(root=ROOT, name=name, step=step, npairs=npairs, nsub=nsub)
+        npairs, nsub, ddiv = (1000, 48, 4) if quick else (3000, 96, 2)
+        script = ORACLE_SAMPLED.format(root=ROOT, name=name, step=step, npairs=npairs, nsub=nsub, ddiv=ddiv)
         sample = (f"extrapolated from a sample at frequency index {step}: {npairs} uniformly drawn triangle pairs per "
                   f"fill (global L, each object's L, Kbar with k and k_l), the reflected fill on {nsub} random "
-                  "triangles, the layered tables whole, the dense solves on half-size matrices; single thread")
+                  f"triangles, the layered tables whole, the dense solves on matrices 1/{ddiv} of the size; "
+                  "single thread")
     r = subprocess.run([sys.executable, "-c", script], capture_output=True, text=True, env=env, timeout=900, cwd=ROOT)
     if r.returncode != 0:
         raise RuntimeError(r.stderr[-2000:])
@@ -504,7 +506,7 @@ def run_reference(args, rank, world):
     times = []
     sample = None
     for i in range(args.warmup + args.steps):
-        t, sample = oracle_step_seconds(args.workload, i)
+        t, sample = oracle_step_seconds(args.workload, i, quick=True)
         if i >= args.warmup:
             times.append(t)
     total = sum(times)
