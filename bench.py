@@ -416,27 +416,39 @@ Pb = m.bxyz[m.btri]
 est = 0.0
 NS = {npairs}
 
-def timed_pairs(fn, k, ta, tb, Psrc, touch_fn, total):
-    # uniformly drawn pairs, grouped by the source's level with the far-pair rule
-    lev = F.sub_level(k, F._diam(Psrc[tb]))
-    split = F.sub_level(k, F._diam(Psrc)).max() > 0
+def timed_pairs(fn, k, ta, tb, Psrc, touch_fn, total, nsrc):
+    # uniformly drawn pairs; with split sources: the far-pair rule, then grouped by the size
+    # of the source's quadrature.  The quadrature rules of the drawn sources are timed apart
+    # and scaled to the fill's nsrc sources (the fill builds each source's rule once).
+    t_rules = 0.0
     t0 = time.perf_counter()
-    for L in np.unique(lev):
-        sel = lev == L
-        a, b = ta[sel], tb[sel]
-        if split:
-            keep = F._kept(k, P[a], Psrc[b], touch_fn(a, b))
-            a, b = a[keep], b[keep]
-        step = max(1, F.CHUNK // 4 ** int(L))
-        for c in range(0, len(a), step):
-            fn(m, k, a[c:c + step], b[c:c + step], int(L))
+    if not F.needs_split(k, Psrc).any():
+        for c in range(0, len(ta), F.CHUNK):
+            fn(m, k, ta[c:c + F.CHUNK], tb[c:c + F.CHUNK])
+    else:
+        keep = F._kept(k, P[ta], Psrc[tb], touch_fn(ta, tb))
+        a, b = ta[keep], tb[keep]
+        t1 = time.perf_counter()
+        rules = {{int(s): F.source_rule(Psrc[s], k) for s in np.unique(b)}}
+        t_rules = (time.perf_counter() - t1)
+        t_rules_est = t_rules * nsrc / max(len(rules), 1)
+        ns = np.array([len(rules[int(s)][1]) for s in b], dtype=np.int64)
+        for n in np.unique(ns):
+            sel = np.nonzero(ns == n)[0]
+            step = max(1, F.CHUNK * 6 // int(n))
+            for c in range(0, len(sel), step):
+                idx = sel[c:c + step]
+                pts = np.stack([rules[int(b[i])][0] for i in idx])
+                w = np.stack([rules[int(b[i])][1] for i in idx])
+                fn(m, k, a[idx], b[idx], (pts, w))
+        return (time.perf_counter() - t0 - t_rules) * total / len(ta) + t_rules_est
     return (time.perf_counter() - t0) * total / len(ta)
 
 touch_L = lambda a, b: F._touch_primal(m.tri, a, b)
 touch_K = lambda a, b: F._touch_bary(m, a, b) > 0
 # global L with the background's k (the equivalent blocks are its diagonal blocks)
 ta = rng.integers(0, m.nt, NS); tb = rng.integers(0, m.nt, NS)
-est += timed_pairs(F._L_pairs, kb, ta, tb, P, touch_L, float(m.nt) ** 2)
+est += timed_pairs(F._L_pairs, kb, ta, tb, P, touch_L, float(m.nt) ** 2, m.nt)
 for o in range(m.nobj):
     t0_, t1_ = m.tri_range[o]
     mat = S.Material(*W["mats"][o][:3])
@@ -444,10 +456,10 @@ for o in range(m.nobj):
     n_o = t1_ - t0_
     ns = max(NS // m.nobj, 64)
     ta = rng.integers(t0_, t1_, ns); tb = rng.integers(t0_, t1_, ns)
-    est += timed_pairs(F._L_pairs, ko, ta, tb, P, touch_L, float(n_o) ** 2)
+    est += timed_pairs(F._L_pairs, ko, ta, tb, P, touch_L, float(n_o) ** 2, n_o)
     for k in (ko, kb):
         ta = rng.integers(t0_, t1_, ns); cb = rng.integers(6 * t0_, 6 * t1_, ns)
-        est += timed_pairs(F._K_pairs, k, ta, cb, Pb, touch_K, 6.0 * n_o ** 2)
+        est += timed_pairs(F._K_pairs, k, ta, cb, Pb, touch_K, 6.0 * n_o ** 2, 6 * n_o)
     # Y = M_l^-1 R_l on half-size random matrices, scaled by 8
     e0_, e1_ = m.edge_range[o]
     n, r = (e1_ - e0_ + n_o - 1) // {ddiv}, (e1_ - e0_) // {ddiv}

@@ -182,10 +182,11 @@ int sldm_stack_destroy(sldm_stack* stack);
 /* Fill and factor the operator at frequency freq_hz (Sec. II-B to II-E):
  * internal blocks with each object's k, equivalent-configuration blocks with
  * the background's k_l, Y11/Y21 by LU of M_l, global external blocks, I_x.
- * Good conductors (Sec. II-B): a source triangle whose longest edge d has
- * |Im k| d > 1 is split L times through its edge midpoints (|Im k| d / 2^L <= 1)
- * for the quadrature, and a fill with split sources drops the pairs whose
- * bounding spheres are more than 40/|Im k| apart; SLDM_ENOTSUP beyond L = 7.
+ * Good conductors (Sec. II-B): a source triangle with an edge longer than
+ * 1/|Im k| is bisected through its longest edge, recursively, until no child has
+ * an edge longer than 1/|Im k|, and the 6-point rule runs on each child; a fill
+ * with split sources drops the pairs whose bounding spheres are more than
+ * 40/|Im k| apart.  SLDM_ENOTSUP beyond 4096 children of one source.
  * per_obj: nobj materials (host).  The mesh and stack must outlive the op. */
 int sldm_assemble(const sldm_mesh* mesh, const sldm_stack* stack, const sldm_material* per_obj,
                   double freq_hz, const sldm_assemble_opts* opts, sldm_op** out);
@@ -256,9 +257,8 @@ int sldm_farfield(const sldm_op* op, const void* x, int32_t where, const double*
  *  - k_re, k_im: complex wavenumber (exp(-j k R) convention, k_im <= 0 decays).
  *  - The object must satisfy ne_o * 9 nt_o <= 1,568,752 (barycentric scratch
  *    entries; about 340 triangles), else SLDM_EINVAL with the sizes in the message.
- *  - Unsplit sources only: when |Im k| times the longest edge of a barycentric
- *    triangle exceeds 1 (a good conductor, whose assembly splits the sources),
- *    SLDM_ENOTSUP.
+ *  - Unsplit sources only: when a barycentric triangle has an edge longer than
+ *    1/|Im k| (a good conductor, whose assembly splits the sources), SLDM_ENOTSUP.
  *  - Asynchronous on `stream`: K_out is complete when the stream reaches this
  *    point.  Every call shares the one scratch array, which keeps the last call's
  *    contents (the call clears what must start at zero), so calls that overlap

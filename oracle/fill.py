@@ -21,12 +21,14 @@ sums of barycentric RWG functions (``mesh.C``), see ``oracle.topology``.
 
 Good conductors (Sec. II-B: the entries of highly conductive objects need
 integration that follows the fast decay of G over a skin depth).  Reading: a
-source triangle T' (primal for L, barycentric for Kbar) of diameter d (its
-longest edge) is split L times by edge midpoints, L the smallest level with
-|Im k| d / 2^L <= 1, and the 6-point rule is applied on each of the 4^L children
-(``sub_rule``).  For L > 0 the touching-pair extraction of L keeps only the static
+source triangle T' (primal for L, barycentric for Kbar) with an edge longer than
+1/|Im k| is bisected through the midpoint of its longest edge, recursively,
+until no child has an edge longer than 1/|Im k| (``source_rule``), and the
+6-point rule is applied on each child.  Bisection refines only across the long
+direction, so the thin triangles of a graded conductor mesh are not split
+across their short side.  A split touching pair extracts only the static
 1/(4 pi R) term: the k^2 R/(8 pi) term is no longer small against G once
-|k| d > 1.  When any source of a fill needs L > 0, that fill also drops the
+|k| d > 1.  When any source of a fill is split, that fill also drops the
 non-touching pairs whose bounding spheres are farther apart than 40 / |Im k|
 (G has decayed below exp(-40) there).
 """
@@ -43,7 +45,8 @@ EPS0 = 1.0 / (MU0 * C0 ** 2)
 ETA0 = MU0 * C0
 
 CHUNK = 4096
-SUB_MAX = 7        # deepest subdivision of a source triangle (4^7 children)
+SUB_MAX_CHILDREN = 4096  # most children of one split source triangle
+SPLIT_TIE = 1e-9         # edges within this relative distance of the longest count as longest
 R8_CUTOFF = 40.0   # |Im k| x (distance of the bounding spheres) beyond which a pair is dropped
 
 
@@ -77,32 +80,47 @@ def green_smooth1(k, R):
     return np.where(np.abs(x) < 0.05, ser, full)
 
 
-def sub_level(k, diam):
-    """Subdivision level of source triangles of diameter ``diam``: the smallest
-    L >= 0 with |Im k| diam / 2^L <= 1."""
-    x = abs(np.imag(k)) * np.asarray(diam, dtype=float)
-    L = np.zeros(x.shape, dtype=np.int64)
-    big = x > 1.0
-    L[big] = np.ceil(np.log2(x[big])).astype(np.int64)
-    if L.size and L.max() > SUB_MAX:
-        raise ValueError("source triangles too large for the skin depth: subdivision level "
-                         f"{L.max()} > {SUB_MAX}")
-    return L
+def split_children(P, h):
+    """Children of the triangle with vertices P (3, 3) under longest-edge bisection
+    until no child has an edge longer than h: barycentric vertex triples with
+    respect to P (nc, 3, 3) and area fractions (nc,).  Edge i joins vertices i and
+    i + 1; the edge split is the first within SPLIT_TIE of the longest; the child
+    holding the edge's first vertex comes first."""
+    todo = [(np.eye(3), 1.0)]
+    out_b, out_f = [], []
+    while todo:
+        B, f = todo.pop()
+        X = B @ P
+        L = np.linalg.norm(X - np.roll(X, -1, axis=0), axis=1)
+        Lmax = L.max()
+        if not (Lmax > h):
+            out_b.append(B)
+            out_f.append(f)
+            continue
+        i = int(np.nonzero(L >= (1.0 - SPLIT_TIE) * Lmax)[0][0])
+        a, b, c = B[i], B[(i + 1) % 3], B[(i + 2) % 3]
+        m = 0.5 * (a + b)
+        todo.append((np.array([m, b, c]), 0.5 * f))
+        todo.append((np.array([a, m, c]), 0.5 * f))
+        if len(out_b) + len(todo) > SUB_MAX_CHILDREN:
+            raise ValueError(f"source triangle too large for the skin depth: more than {SUB_MAX_CHILDREN} children")
+    return np.array(out_b), np.array(out_f)
 
 
-def sub_rule(L):
-    """Composite rule on a triangle split L times through its edge midpoints:
-    barycentric points (6 * 4^L, 3) and weights (6 * 4^L,) summing to 1."""
-    tris = [np.eye(3)]
-    for _ in range(L):
-        nxt = []
-        for a, b, c in tris:
-            ab, bc, ca = (a + b) / 2, (b + c) / 2, (c + a) / 2
-            nxt += [np.array([a, ab, ca]), np.array([ab, b, bc]), np.array([ca, bc, c]), np.array([ab, bc, ca])]
-        tris = nxt
-    T = np.array(tris)
-    pts = np.einsum('qk,nkd->nqd', Q.BARY, T).reshape(-1, 3)
-    return pts, np.tile(Q.W, len(tris)) / len(tris)
+def source_rule(P, k):
+    """Quadrature of one source triangle (vertices P) for wavenumber k: barycentric
+    points (ns, 3) and weights (ns,) summing to 1; the 6-point rule when no edge
+    exceeds 1/|Im k|, else the 6-point rule on each child of ``split_children``."""
+    aki = abs(np.imag(k))
+    h = 1.0 / aki if aki > 0 else np.inf
+    Bc, fr = split_children(np.asarray(P, dtype=float), h)
+    pts = np.einsum('qk,ckd->cqd', Q.BARY, Bc).reshape(-1, 3)
+    return pts, (fr[:, None] * Q.W[None, :]).reshape(-1)
+
+
+def needs_split(k, P):
+    """Per triangle (P: (n, 3, 3)): has an edge longer than 1/|Im k|."""
+    return abs(np.imag(k)) * _diam(P) > 1.0
 
 
 def _diam(P):
@@ -147,14 +165,17 @@ def _touch_primal(tri, a, b):
     return (ta[:, :, None] == tb[:, None, :]).any(axis=(1, 2))
 
 
-def _L_pairs(mesh, k, ta, tb, level=0):
-    """Local RWG x RWG (P, 3, 3) and pulse x pulse (P,) integrals of triangle pairs,
-    the source triangles split ``level`` times."""
+def _L_pairs(mesh, k, ta, tb, rule=None):
+    """Local RWG x RWG (P, 3, 3) and pulse x pulse (P,) integrals of triangle pairs.
+    rule: per-pair source quadrature (barycentric points (P, ns, 3), weights (P, ns)),
+    the same ns for every pair; None = the 6-point rule.  ns > 6 means split."""
     xyz, tri = mesh.xyz, mesh.tri
     A, B = xyz[tri[ta]], xyz[tri[tb]]
-    bs, wsub = sub_rule(level)
-    rq, rs = Q.points(A), np.einsum('qk,nkd->nqd', bs, B)
-    wq, ws = Q.weights(mesh.area[ta]), np.outer(mesh.area[tb], wsub)
+    if rule is None:
+        rule = (np.broadcast_to(Q.BARY, (len(tb), 6, 3)), np.broadcast_to(Q.W, (len(tb), 6)))
+    bs, wsub = rule
+    rq, rs = Q.points(A), np.einsum('pqk,pkd->pqd', bs, B)
+    wq, ws = Q.weights(mesh.area[ta]), mesh.area[tb][:, None] * wsub
     fa = rq[:, :, None, :] - A[:, None, :, :]          # r - v_i   (P, 6, 3, 3)
     fb = rs[:, :, None, :] - B[:, None, :, :]          # r' - w_j
     scale = (mesh.E.tri_sign[ta][:, :, None] * mesh.E.tri_sign[tb][:, None, :]
@@ -172,7 +193,7 @@ def _L_pairs(mesh, k, ta, tb, level=0):
         idx = np.nonzero(touch)[0]
         P = len(idx)
         R = np.linalg.norm(rq[idx][:, :, None, :] - rs[idx][:, None, :, :], axis=-1)
-        two = level == 0                                                     # extract 1/R and R, else 1/R only
+        two = bs.shape[1] == 6                                               # unsplit: extract 1/R and R, else 1/R only
         Gs = (green_smooth(k, R) if two else green_smooth1(k, R)) * ws[idx][:, None, :]   # (P, 6q, ns)
         inner_a = np.einsum('pqs,psjd->pqjd', Gs, fb[idx])                   # (P, 6, 3, 3)
         inner_p = Gs.sum(axis=2)                                             # (P, 6)
@@ -194,6 +215,22 @@ def _L_pairs(mesh, k, ta, tb, level=0):
     return la * scale, lp / (mesh.area[ta] * mesh.area[tb])
 
 
+def _rule_groups(k, P, srcs):
+    """Sources grouped by the size of their quadrature, with the rules stacked:
+    [(sources, (points (S, ns, 3), weights (S, ns)) or None for the plain 6-point
+    rule when no source of the fill is split)]."""
+    srcs = np.asarray(srcs)
+    if not needs_split(k, P[srcs]).any():
+        return [(srcs, None)]
+    rules = [source_rule(P[s], k) for s in srcs]
+    ns = np.array([len(r[1]) for r in rules])
+    out = []
+    for n in np.unique(ns):
+        sel = np.nonzero(ns == n)[0]
+        out.append((srcs[sel], (np.stack([rules[i][0] for i in sel]), np.stack([rules[i][1] for i in sel]))))
+    return out
+
+
 def fill_L(mesh, k, tris):
     """L^A over the edges of triangles ``tris`` and L^phi over ``tris`` (whole objects)."""
     tris = np.asarray(tris)
@@ -206,19 +243,17 @@ def fill_L(mesh, k, tris):
     LA = np.zeros((len(edges), len(edges)), dtype=complex)
     LP = np.zeros((len(tris), len(tris)), dtype=complex)
     P = mesh.xyz[mesh.tri]
-    lev = sub_level(k, _diam(P[tris]))
-    sub = lev.max(initial=0) > 0
-    for L in np.unique(lev):
-        srcs = tris[lev == L]
+    for srcs, rules in _rule_groups(k, P, tris):
         ta_all = np.repeat(tris, len(srcs))
         tb_all = np.tile(srcs, len(tris))
-        if sub:
+        ri_all = np.tile(np.arange(len(srcs)), len(tris))
+        if rules is not None:
             keep = _kept(k, P[ta_all], P[tb_all], _touch_primal(mesh.tri, ta_all, tb_all))
-            ta_all, tb_all = ta_all[keep], tb_all[keep]
-        step = max(1, CHUNK // 4 ** int(L))
+            ta_all, tb_all, ri_all = ta_all[keep], tb_all[keep], ri_all[keep]
+        step = max(1, CHUNK * 6 // (rules[0].shape[1] if rules is not None else 6))
         for c in range(0, len(ta_all), step):
-            ta, tb = ta_all[c:c + step], tb_all[c:c + step]
-            la, lp = _L_pairs(mesh, k, ta, tb, int(L))
+            ta, tb, ri = ta_all[c:c + step], tb_all[c:c + step], ri_all[c:c + step]
+            la, lp = _L_pairs(mesh, k, ta, tb, None if rules is None else (rules[0][ri], rules[1][ri]))
             rows = eidx[e_of[ta]][:, :, None] * np.ones((1, 1, 3), dtype=np.int64)
             cols = eidx[e_of[tb]][:, None, :] * np.ones((1, 3, 1), dtype=np.int64)
             np.add.at(LA, (rows.ravel(), cols.ravel()), la.ravel())
@@ -241,14 +276,16 @@ def _touch_bary(mesh, ta, cb):
     return np.where(parent == ta, 2, out)
 
 
-def _K_pairs(mesh, k, ta, cb, level=0):
-    """Local RWG (test, primal) x barycentric RWG (source) integrals of Kbar, (P, 3, 3),
-    the source triangles split ``level`` times."""
+def _K_pairs(mesh, k, ta, cb, rule=None):
+    """Local RWG (test, primal) x barycentric RWG (source) integrals of Kbar, (P, 3, 3).
+    rule: per-pair source quadrature as for _L_pairs (None = the 6-point rule)."""
     A = mesh.xyz[mesh.tri[ta]]
     Bt = mesh.bxyz[mesh.btri[cb]]
-    bs, wsub = sub_rule(level)
-    rq, rs = Q.points(A), np.einsum('qk,nkd->nqd', bs, Bt)
-    wq, ws = Q.weights(mesh.area[ta]), np.outer(mesh.barea[cb], wsub)
+    if rule is None:
+        rule = (np.broadcast_to(Q.BARY, (len(cb), 6, 3)), np.broadcast_to(Q.W, (len(cb), 6)))
+    bs, wsub = rule
+    rq, rs = Q.points(A), np.einsum('pqk,pkd->pqd', bs, Bt)
+    wq, ws = Q.weights(mesh.area[ta]), mesh.barea[cb][:, None] * wsub
     ns = rs.shape[1]
     fa = (rq[:, :, None, :] - A[:, None, :, :]) * \
         (mesh.E.tri_sign[ta] / (2 * mesh.area[ta][:, None]))[:, None, :, None]          # f_i(r_q)
@@ -293,19 +330,17 @@ def fill_Kbar(mesh, k, obj):
     Kb = np.zeros((e1 - e0, len(bidx)), dtype=complex)
     P = mesh.xyz[mesh.tri]
     Pb = mesh.bxyz[mesh.btri]
-    lev = sub_level(k, _diam(Pb[kids]))
-    sub = lev.max(initial=0) > 0
-    for L in np.unique(lev):
-        srcs = kids[lev == L]
+    for srcs, rules in _rule_groups(k, Pb, kids):
         ta_all = np.repeat(tris, len(srcs))
         cb_all = np.tile(srcs, len(tris))
-        if sub:
+        ri_all = np.tile(np.arange(len(srcs)), len(tris))
+        if rules is not None:
             keep = _kept(k, P[ta_all], Pb[cb_all], _touch_bary(mesh, ta_all, cb_all) > 0)
-            ta_all, cb_all = ta_all[keep], cb_all[keep]
-        step = max(1, CHUNK // 4 ** int(L))
+            ta_all, cb_all, ri_all = ta_all[keep], cb_all[keep], ri_all[keep]
+        step = max(1, CHUNK * 6 // (rules[0].shape[1] if rules is not None else 6))
         for c in range(0, len(ta_all), step):
-            ta, cb = ta_all[c:c + step], cb_all[c:c + step]
-            loc = _K_pairs(mesh, k, ta, cb, int(L))
+            ta, cb, ri = ta_all[c:c + step], cb_all[c:c + step], ri_all[c:c + step]
+            loc = _K_pairs(mesh, k, ta, cb, None if rules is None else (rules[0][ri], rules[1][ri]))
             rows = (mesh.E.tri_edge[ta] - e0)[:, :, None] * np.ones((1, 1, 3), dtype=np.int64)
             cols = (mesh.bE.tri_edge[cb] - b0)[:, None, :] * np.ones((1, 3, 1), dtype=np.int64)
             np.add.at(Kb, (rows.ravel(), cols.ravel()), loc.ravel())

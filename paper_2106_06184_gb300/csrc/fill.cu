@@ -618,11 +618,11 @@ static std::vector<int32_t> unsplit_object_tasks(const HostMesh& h, const std::v
 template <class R>
 void fill_L(const sldm_mesh* m, const std::vector<LTask>& tasks, cudaStream_t s) {
   if (tasks.empty()) return;
-  std::vector<std::vector<int8_t>> lev(tasks.size());
+  std::vector<SplitRules> rules(tasks.size());
   std::vector<char> split(tasks.size(), 0);
   for (size_t i = 0; i < tasks.size(); ++i) {
-    lev[i] = split_levels_L(m->h, tasks[i]);
-    split[i] = *std::max_element(lev[i].begin(), lev[i].end()) > 0;
+    rules[i] = split_rules_L(m->h, tasks[i]);
+    split[i] = rules[i].split;
   }
   std::vector<TileRef> tiles;
   for (size_t i = 0; i < tasks.size(); ++i) {
@@ -651,18 +651,18 @@ void fill_L(const sldm_mesh* m, const std::vector<LTask>& tasks, cudaStream_t s)
   }
   SLDM_CUDA(cudaGetLastError());
   for (size_t i = 0; i < tasks.size(); ++i)
-    if (split[i]) fill_L_split_task<R>(m, tasks[i], lev[i], s);
+    if (split[i]) fill_L_split_task<R>(m, tasks[i], rules[i], s);
   SLDM_CUDA(cudaStreamSynchronize(s));  // task/tile buffers are released on return
 }
 
 template <class R>
 void fill_K(const sldm_mesh* m, const std::vector<KTask>& tasks, cudaStream_t s) {
   if (tasks.empty()) return;
-  std::vector<std::vector<int8_t>> lev(tasks.size());
+  std::vector<SplitRules> rules(tasks.size());
   std::vector<char> split(tasks.size(), 0);
   for (size_t i = 0; i < tasks.size(); ++i) {
-    lev[i] = split_levels_K(m->h, tasks[i]);
-    split[i] = *std::max_element(lev[i].begin(), lev[i].end()) > 0;
+    rules[i] = split_rules_K(m->h, tasks[i]);
+    split[i] = rules[i].split;
   }
   std::vector<TileRef> tiles;
   for (size_t i = 0; i < tasks.size(); ++i) {
@@ -692,7 +692,7 @@ void fill_K(const sldm_mesh* m, const std::vector<KTask>& tasks, cudaStream_t s)
   }
   SLDM_CUDA(cudaGetLastError());
   for (size_t i = 0; i < tasks.size(); ++i)
-    if (split[i]) fill_K_split_task<R>(m, tasks[i], lev[i], s);
+    if (split[i]) fill_K_split_task<R>(m, tasks[i], rules[i], s);
   SLDM_CUDA(cudaStreamSynchronize(s));
 }
 
@@ -1089,8 +1089,7 @@ extern "C" int sldm_kbar_noalloc(const sldm_mesh* m, int32_t obj, double k_re, d
     t.e_row0 = e0; t.b_col0 = b0; t.ld = nbe_o;
     t.Kb = Kb;
     t.kr = k_re; t.ki = k_im;
-    const std::vector<int8_t> lev = split_levels_K(h, t);
-    SLDM_REQUIRE(*std::max_element(lev.begin(), lev.end()) == 0, SLDM_ENOTSUP,
+    SLDM_REQUIRE(!split_rules_K(h, t).split, SLDM_ENOTSUP,
                  "kbar_noalloc: the object's sources must be split for this wavenumber (good conductor); "
                  "sldm_assemble handles it");
     // the block accumulates atomically: it must start at zero on every call

@@ -1,27 +1,29 @@
 // Good-conductor fill (Sec. II-B: inside highly conductive objects the entries
 // need integration that follows the decay of G over a skin depth).  A source
-// triangle of longest edge d is split L times through its edge midpoints, L the
-// smallest level with |Im k| d / 2^L <= 1, and the 6-point rule runs on each of
-// the 4^L children.  Touching pairs extract 1/(4 pi R) in closed form (and
-// -k^2 R/(8 pi) as well when L = 0, as the unsplit kernels do); for Kbar the
-// static grad 1/(4 pi R) is extracted as always.  Pairs whose bounding spheres
-// are farther apart than 40/|Im k| are dropped (G has decayed below e^-40).
+// triangle with an edge longer than 1/|Im k| is bisected through the midpoint
+// of its longest edge, recursively, until no child has an edge longer than
+// 1/|Im k|, and the 6-point rule runs on each child; the rules are built on the
+// host per source.  Touching pairs extract 1/(4 pi R) in closed form (and
+// -k^2 R/(8 pi) as well for an unsplit source, as the unsplit kernels do); for
+// Kbar the static grad 1/(4 pi R) is extracted as always.  Pairs whose bounding
+// spheres are farther apart than 40/|Im k| are dropped (G has decayed below e^-40).
 //
-// One warp per (test, source) pair: the lanes stride over the 6 x (6 x 4^L)
-// (test point, source point) pairs, the lanes 0..5 add the closed forms
+// One warp per (test, source) pair: the lanes stride over the 6 x (points of
+// the source's rule) (test point, source point) pairs, the lanes 0..5 add the closed forms
 // of test point q = lane on touching pairs, the moments are summed with
 // shuffles, and lane 0 scatters the 3x3 local block as the unsplit kernels do.
 // Everything is FP64; the destination precision is R.
 #include <algorithm>
-#include <array>
-#include <mutex>
+#include <string>
+#include <vector>
 
 #include "fill_dev.cuh"
 
 namespace sldm {
 
 constexpr double R8_CUTOFF = 40.0;
-constexpr int SUB_MAX = 7;
+constexpr int SUB_MAX_CHILDREN = 4096;  // most children of one split source
+constexpr double SPLIT_TIE = 1e-9;      // edges within this relative distance of the longest count as longest
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -70,18 +72,7 @@ __device__ __forceinline__ cd grad_full(cd k, double R) {
   return {-p.r, -p.i};
 }
 
-// Barycentric coordinates of the points of the composite rule on a triangle
-// split L times (children of (a, b, c): (a, ab, ca) (ab, b, bc) (ca, bc, c)
-// (ab, bc, ca), the 6-point rule on each): point 6 c + j of level L is entry
-// split_off(L) + 6 c + j of the table, x y z = weights of the three vertices.
-__host__ __device__ __forceinline__ int split_off(int L) { return 2 * ((1 << (2 * L)) - 1); }
-struct __align__(32) Bary {
-  double x, y, z, pad;
-};
-
-__device__ __forceinline__ void split_point(const Bary* __restrict__ tab, int L, int pnt, const double ev[3][3],
-                                            double rp[3]) {
-  const Bary b = tab[split_off(L) + pnt];
+__device__ __forceinline__ void src_point(const SrcPoint& b, const double ev[3][3], double rp[3]) {
   for (int d = 0; d < 3; ++d) rp[d] = b.x * ev[0][d] + b.y * ev[1][d] + b.z * ev[2][d];
 }
 
@@ -97,7 +88,8 @@ __device__ __forceinline__ double bound_radius(const double* c, const double* p0
 
 // ---------------------------------------------------------------- L^A, L^phi
 template <class R>
-__global__ void __launch_bounds__(256) fill_L_split(LTask tk, const int8_t* __restrict__ lev, const Bary* __restrict__ tab,
+__global__ void __launch_bounds__(256) fill_L_split(LTask tk, const int32_t* __restrict__ soff,
+                                                    const SrcPoint* __restrict__ spts,
                                                     const double* __restrict__ geo, const double* __restrict__ xyz,
                                                     const int32_t* __restrict__ tri, const int32_t* __restrict__ tri_edge) {
   const int64_t pair = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
@@ -119,9 +111,10 @@ __global__ void __launch_bounds__(256) fill_L_split(LTask tk, const int8_t* __re
     const double dx = gt[GEO_C] - gs[GEO_C], dy = gt[GEO_C + 1] - gs[GEO_C + 1], dz = gt[GEO_C + 2] - gs[GEO_C + 2];
     if (fabs(tk.ki) * (sqrt(dx * dx + dy * dy + dz * dz) - rt - rs) > R8_CUTOFF) return;
   }
-  const int L = lev[s - tk.s0];
-  const int nu = 6 << (2 * L);
-  const double wsc = 1.0 / double(1 << (2 * L));
+  const SrcPoint* rule = spts + soff[s - tk.s0];
+  const int nu = soff[s - tk.s0 + 1] - soff[s - tk.s0];
+  const bool split = nu > 6;
+  const double As = gs[GEO_A];
   double ev[3][3], dc[3];
   for (int i = 0; i < 3; ++i)
     for (int d = 0; d < 3; ++d) ev[i][d] = ps[i][d] - gs[GEO_C + d];
@@ -134,13 +127,14 @@ __global__ void __launch_bounds__(256) fill_L_split(LTask tk, const int8_t* __re
   // unit u = (source point u / 6, test point u % 6): 36 units even when unsplit
   for (int u = lane; u < 6 * nu; u += 32) {
     const int pnt = u / 6, q = u - 6 * pnt;
+    const SrcPoint sp = rule[pnt];
     double rp[3];
-    split_point(tab, L, pnt, ev, rp);
-    const double ws = gs[GEO_W + pnt % 6] * wsc;
+    src_point(sp, ev, rp);
+    const double ws = As * sp.w;
     const double* rq = gt + GEO_RHO + 3 * q;
     const double D0 = dc[0] + rq[0] - rp[0], D1 = dc[1] + rq[1] - rp[1], D2 = dc[2] + rq[2] - rp[2];
     const double Rr = sqrt(D0 * D0 + D1 * D1 + D2 * D2);
-    cd g = touch ? (L == 0 ? green_smooth(k, Rr) : green_smooth1(k, Rr)) : green_full(k, Rr);
+    cd g = touch ? (split ? green_smooth1(k, Rr) : green_smooth(k, Rr)) : green_full(k, Rr);
     const double w = gt[GEO_W + q] * ws;
     g.r *= w;
     g.i *= w;
@@ -164,7 +158,7 @@ __global__ void __launch_bounds__(256) fill_L_split(LTask tk, const int8_t* __re
     Pot P;
     potentials(r, ps[0], ps[1], ps[2], P);
     const cd k2 = cmul(k, k);
-    const double two = (L == 0) ? 1.0 : 0.0;  // the k^2 R term is extracted only when unsplit
+    const double two = split ? 0.0 : 1.0;  // the k^2 R term is extracted only when unsplit
     cd A = {INV4PI * P.inv_r - two * k2.r * 0.5 * INV4PI * P.r, -two * k2.i * 0.5 * INV4PI * P.r};
     cd Bv[3];
     for (int d = 0; d < 3; ++d) {
@@ -222,7 +216,8 @@ __global__ void __launch_bounds__(256) fill_L_split(LTask tk, const int8_t* __re
 
 // ---------------------------------------------------------------- Kbar (primal test x barycentric child)
 template <class R>
-__global__ void __launch_bounds__(256) fill_K_split(KTask tk, const int8_t* __restrict__ lev, const Bary* __restrict__ tab,
+__global__ void __launch_bounds__(256) fill_K_split(KTask tk, const int32_t* __restrict__ soff,
+                                                    const SrcPoint* __restrict__ spts,
                                                     const double* __restrict__ geo,
                                                     const double* __restrict__ bgeo, const double* __restrict__ xyz,
                                                     const int32_t* __restrict__ tri, const int32_t* __restrict__ tri_edge,
@@ -257,9 +252,9 @@ __global__ void __launch_bounds__(256) fill_K_split(KTask tk, const int8_t* __re
     const double dx = gt[GEO_C] - gs[GEO_C], dy = gt[GEO_C + 1] - gs[GEO_C + 1], dz = gt[GEO_C + 2] - gs[GEO_C + 2];
     if (fabs(tk.ki) * (sqrt(dx * dx + dy * dy + dz * dz) - rt - rs) > R8_CUTOFF) return;
   }
-  const int L = lev[cg - tk.c0];
-  const int nu = 6 << (2 * L);
-  const double wsc = 1.0 / double(1 << (2 * L));
+  const SrcPoint* rule = spts + soff[cg - tk.c0];
+  const int nu = soff[cg - tk.c0 + 1] - soff[cg - tk.c0];
+  const double As = gs[GEO_A];
   double ev[3][3], dc[3];
   for (int i = 0; i < 3; ++i)
     for (int d = 0; d < 3; ++d) ev[i][d] = ps[i][d] - gs[GEO_C + d];
@@ -272,9 +267,10 @@ __global__ void __launch_bounds__(256) fill_K_split(KTask tk, const int8_t* __re
   // unit u = (source point u / 6, test point u % 6)
   for (int u = lane; u < 6 * nu; u += 32) {
     const int pnt = u / 6, q = u - 6 * pnt;
+    const SrcPoint sp = rule[pnt];
     double rp[3];
-    split_point(tab, L, pnt, ev, rp);
-    const double ws = gs[GEO_W + pnt % 6] * wsc;
+    src_point(sp, ev, rp);
+    const double ws = As * sp.w;
     const double* rq = gt + GEO_RHO + 3 * q;
     const double D[3] = {dc[0] + rq[0] - rp[0], dc[1] + rq[1] - rp[1], dc[2] + rq[2] - rp[2]};
     const double Rr = sqrt(D[0] * D[0] + D[1] * D[1] + D[2] * D[2]);
@@ -354,36 +350,107 @@ __global__ void __launch_bounds__(256) fill_K_split(KTask tk, const int8_t* __re
 }
 
 // ---------------------------------------------------------------- host side
-// Level of a source triangle with vertices p0, p1, p2 for |Im k| = aki.
-static int split_level(double aki, const double* p0, const double* p1, const double* p2) {
-  auto len = [](const double* a, const double* b) {
-    return std::sqrt((a[0] - b[0]) * (a[0] - b[0]) + (a[1] - b[1]) * (a[1] - b[1]) + (a[2] - b[2]) * (a[2] - b[2]));
-  };
-  const double x = aki * std::max(len(p0, p1), std::max(len(p1, p2), len(p2, p0)));
-  if (!(x > 1.0)) return 0;
-  const int L = int(std::ceil(std::log2(x)));
-  SLDM_REQUIRE(L <= SUB_MAX, SLDM_ENOTSUP,
-               "source triangles too large for the skin depth: subdivision level " + std::to_string(L) + " > " +
-                   std::to_string(SUB_MAX));
-  return L;
+static const double kBary[6][3] = {
+    {0.108103018168070, 0.445948490915965, 0.445948490915965}, {0.445948490915965, 0.108103018168070, 0.445948490915965},
+    {0.445948490915965, 0.445948490915965, 0.108103018168070}, {0.816847572980459, 0.091576213509771, 0.091576213509771},
+    {0.091576213509771, 0.816847572980459, 0.091576213509771}, {0.091576213509771, 0.091576213509771, 0.816847572980459}};
+static const double kW[6] = {0.223381589678011, 0.223381589678011, 0.223381589678011,
+                              0.109951743655322, 0.109951743655322, 0.109951743655322};
+
+static double edge_len(const double* a, const double* b) {
+  return std::sqrt((a[0] - b[0]) * (a[0] - b[0]) + (a[1] - b[1]) * (a[1] - b[1]) + (a[2] - b[2]) * (a[2] - b[2]));
 }
 
-std::vector<int8_t> split_levels_L(const HostMesh& h, const LTask& tk) {
-  std::vector<int8_t> lev(size_t(tk.nsrc));
-  const double aki = std::fabs(tk.ki);
-  for (int i = 0; i < tk.nsrc; ++i) {
-    const int s = tk.s0 + i;
-    lev[size_t(i)] = int8_t(split_level(aki, &h.xyz[3 * size_t(h.tri[3 * s])], &h.xyz[3 * size_t(h.tri[3 * s + 1])],
-                                        &h.xyz[3 * size_t(h.tri[3 * s + 2])]));
+// The source's quadrature appended to `pts`: longest-edge bisection of the
+// triangle (p0, p1, p2) until no child has an edge longer than h (edge i joins
+// vertices i and i + 1; the first edge within SPLIT_TIE of the longest is cut;
+// the child holding the cut edge's first vertex is refined first), then the
+// 6-point rule on each child.
+struct Child {
+  double B[3][3];  // barycentric coordinates of the child's vertices
+  double f;        // area fraction
+};
+static void append_rule(const double* p0, const double* p1, const double* p2, double h, std::vector<SrcPoint>& pts) {
+  const double* P[3] = {p0, p1, p2};
+  std::vector<Child> todo(1), done;
+  todo[0] = Child{{{1, 0, 0}, {0, 1, 0}, {0, 0, 1}}, 1.0};
+  while (!todo.empty()) {
+    const Child c = todo.back();
+    todo.pop_back();
+    double X[3][3];
+    for (int v = 0; v < 3; ++v)
+      for (int d = 0; d < 3; ++d) X[v][d] = c.B[v][0] * P[0][d] + c.B[v][1] * P[1][d] + c.B[v][2] * P[2][d];
+    const double L[3] = {edge_len(X[0], X[1]), edge_len(X[1], X[2]), edge_len(X[2], X[0])};
+    const double Lmax = std::max(L[0], std::max(L[1], L[2]));
+    if (!(Lmax > h)) {
+      done.push_back(c);
+      continue;
+    }
+    int i = 0;
+    while (!(L[i] >= (1.0 - SPLIT_TIE) * Lmax)) ++i;
+    const double* a = c.B[i];
+    const double* b = c.B[(i + 1) % 3];
+    const double* cc = c.B[(i + 2) % 3];
+    Child c1, c2;
+    for (int d = 0; d < 3; ++d) {
+      const double m = 0.5 * (a[d] + b[d]);
+      c1.B[0][d] = m; c1.B[1][d] = b[d]; c1.B[2][d] = cc[d];
+      c2.B[0][d] = a[d]; c2.B[1][d] = m; c2.B[2][d] = cc[d];
+    }
+    c1.f = c2.f = 0.5 * c.f;
+    todo.push_back(c1);
+    todo.push_back(c2);
+    SLDM_REQUIRE(done.size() + todo.size() <= size_t(SUB_MAX_CHILDREN), SLDM_ENOTSUP,
+                 "source triangle too large for the skin depth: more than " + std::to_string(SUB_MAX_CHILDREN) +
+                     " children");
   }
-  return lev;
+  for (const Child& c : done)
+    for (int j = 0; j < 6; ++j) {
+      double b[3] = {0, 0, 0};
+      for (int v = 0; v < 3; ++v)
+        for (int d = 0; d < 3; ++d) b[d] += kBary[j][v] * c.B[v][d];
+      pts.push_back(SrcPoint{b[0], b[1], b[2], c.f * kW[j]});
+    }
 }
 
-std::vector<int8_t> split_levels_K(const HostMesh& h, const KTask& tk) {
-  std::vector<int8_t> lev(size_t(tk.nsrc));
-  const double aki = std::fabs(tk.ki);
-  const int cvt[6][3] = {{0, 3, 6}, {3, 1, 6}, {1, 4, 6}, {4, 2, 6}, {2, 5, 6}, {5, 0, 6}};
-  for (int i = 0; i < tk.nsrc; ++i) {
+static double longest_edge(const double* p0, const double* p1, const double* p2) {
+  return std::max(edge_len(p0, p2), std::max(edge_len(p1, p0), edge_len(p2, p1)));
+}
+
+template <class VertexFn>
+static SplitRules make_rules(int nsrc, double ki, VertexFn vertices) {
+  SplitRules R;
+  const double aki = std::fabs(ki);
+  for (int i = 0; i < nsrc && !R.split; ++i) {
+    const double* p[3];
+    double store[3][3];
+    vertices(i, p, store);
+    R.split = aki * longest_edge(p[0], p[1], p[2]) > 1.0;
+  }
+  if (!R.split) return R;
+  const double h = 1.0 / aki;
+  R.off.reserve(size_t(nsrc) + 1);
+  for (int i = 0; i < nsrc; ++i) {
+    R.off.push_back(int32_t(R.pts.size()));
+    const double* p[3];
+    double store[3][3];
+    vertices(i, p, store);
+    append_rule(p[0], p[1], p[2], h, R.pts);
+  }
+  R.off.push_back(int32_t(R.pts.size()));
+  return R;
+}
+
+SplitRules split_rules_L(const HostMesh& h, const LTask& tk) {
+  return make_rules(tk.nsrc, tk.ki, [&](int i, const double* p[3], double (*)[3]) {
+    const int s = tk.s0 + i;
+    for (int v = 0; v < 3; ++v) p[v] = &h.xyz[3 * size_t(h.tri[3 * s + v])];
+  });
+}
+
+SplitRules split_rules_K(const HostMesh& h, const KTask& tk) {
+  static const int cvt[6][3] = {{0, 3, 6}, {3, 1, 6}, {1, 4, 6}, {4, 2, 6}, {2, 5, 6}, {5, 0, 6}};
+  return make_rules(tk.nsrc, tk.ki, [&](int i, const double* p[3], double (*store)[3]) {
     const int cg = tk.c0 + i, par = cg / 6, kk = cg % 6;
     const double* a = &h.xyz[3 * size_t(h.tri[3 * par])];
     const double* b = &h.xyz[3 * size_t(h.tri[3 * par + 1])];
@@ -394,97 +461,50 @@ std::vector<int8_t> split_levels_K(const HostMesh& h, const KTask& tk) {
       V[3][d] = 0.5 * (a[d] + b[d]); V[4][d] = 0.5 * (b[d] + c[d]); V[5][d] = 0.5 * (c[d] + a[d]);
       V[6][d] = (a[d] + b[d] + c[d]) / 3.0;
     }
-    lev[size_t(i)] = int8_t(split_level(aki, V[cvt[kk][0]], V[cvt[kk][1]], V[cvt[kk][2]]));
-  }
-  return lev;
-}
-
-// The composite-rule table of every level up to SUB_MAX, built and uploaded once
-// per device and kept for the life of the process (4 MiB).
-static std::mutex g_tab_mu;
-static const Bary* g_tab[64] = {nullptr};
-
-static const Bary* split_table() {
-  int dev = 0;
-  SLDM_CUDA(cudaGetDevice(&dev));
-  SLDM_REQUIRE(dev >= 0 && dev < 64, SLDM_EINVAL, "split table: device index out of range");
-  std::lock_guard<std::mutex> l(g_tab_mu);
-  if (g_tab[dev]) return g_tab[dev];
-  static const double bary[6][3] = {
-      {0.108103018168070, 0.445948490915965, 0.445948490915965}, {0.445948490915965, 0.108103018168070, 0.445948490915965},
-      {0.445948490915965, 0.445948490915965, 0.108103018168070}, {0.816847572980459, 0.091576213509771, 0.091576213509771},
-      {0.091576213509771, 0.816847572980459, 0.091576213509771}, {0.091576213509771, 0.091576213509771, 0.816847572980459}};
-  std::vector<Bary> h(size_t(split_off(SUB_MAX + 1)));
-  typedef std::array<std::array<double, 3>, 3> Tri;  // vertex v: barycentric coordinates
-  std::vector<Tri> cur(1);
-  cur[0] = {{{1, 0, 0}, {0, 1, 0}, {0, 0, 1}}};
-  for (int L = 0; L <= SUB_MAX; ++L) {
-    for (size_t c = 0; c < cur.size(); ++c)
-      for (int j = 0; j < 6; ++j) {
-        double b[3] = {0, 0, 0};
-        for (int v = 0; v < 3; ++v)
-          for (int d = 0; d < 3; ++d) b[d] += bary[j][v] * cur[c][v][d];
-        h[size_t(split_off(L)) + 6 * c + j] = Bary{b[0], b[1], b[2], 0.0};
-      }
-    if (L == SUB_MAX) break;
-    std::vector<Tri> nxt;
-    nxt.reserve(cur.size() * 4);
-    for (const Tri& t : cur) {
-      std::array<double, 3> mab, mbc, mca;
-      for (int d = 0; d < 3; ++d) {
-        mab[d] = 0.5 * (t[0][d] + t[1][d]);
-        mbc[d] = 0.5 * (t[1][d] + t[2][d]);
-        mca[d] = 0.5 * (t[2][d] + t[0][d]);
-      }
-      nxt.push_back({{t[0], mab, mca}});
-      nxt.push_back({{mab, t[1], mbc}});
-      nxt.push_back({{mca, mbc, t[2]}});
-      nxt.push_back({{mab, mbc, mca}});
+    for (int v = 0; v < 3; ++v) {
+      for (int d = 0; d < 3; ++d) store[v][d] = V[cvt[kk][v]][d];
+      p[v] = store[v];
     }
-    cur.swap(nxt);
-  }
-  Bary* d = nullptr;
-  SLDM_CUDA(cudaMalloc(&d, h.size() * sizeof(Bary)));
-  SLDM_CUDA(cudaMemcpy(d, h.data(), h.size() * sizeof(Bary), cudaMemcpyHostToDevice));
-  g_tab[dev] = d;
-  return d;
+  });
 }
 
 template <class R>
-void fill_L_split_task(const sldm_mesh* m, const LTask& tk, const std::vector<int8_t>& lev, cudaStream_t s) {
-  const Bary* tab = split_table();
-  DBuf<int8_t> dl;
-  dl.upload(lev, s);
+void fill_L_split_task(const sldm_mesh* m, const LTask& tk, const SplitRules& rules, cudaStream_t s) {
+  DBuf<int32_t> doff;
+  DBuf<SrcPoint> dpts;
+  doff.upload(rules.off, s);
+  dpts.upload(rules.pts, s);
   const int64_t threads = int64_t(tk.ntest) * tk.nsrc * 32;
   const DevMesh& d = m->d;
   {
     ScopedTimer tm("fill_L_split", s);
-    fill_L_split<R><<<unsigned((threads + 255) / 256), 256, 0, s>>>(tk, dl.p, tab, d.geo.p, d.xyz.p, d.tri.p, d.tri_edge.p),
-        ::sldm::count_launch();
+    fill_L_split<R><<<unsigned((threads + 255) / 256), 256, 0, s>>>(tk, doff.p, dpts.p, d.geo.p, d.xyz.p, d.tri.p,
+                                                                   d.tri_edge.p), ::sldm::count_launch();
   }
   SLDM_CUDA(cudaGetLastError());
   SLDM_CUDA(cudaStreamSynchronize(s));
 }
 
 template <class R>
-void fill_K_split_task(const sldm_mesh* m, const KTask& tk, const std::vector<int8_t>& lev, cudaStream_t s) {
-  const Bary* tab = split_table();
-  DBuf<int8_t> dl;
-  dl.upload(lev, s);
+void fill_K_split_task(const sldm_mesh* m, const KTask& tk, const SplitRules& rules, cudaStream_t s) {
+  DBuf<int32_t> doff;
+  DBuf<SrcPoint> dpts;
+  doff.upload(rules.off, s);
+  dpts.upload(rules.pts, s);
   const int64_t threads = int64_t(tk.ntest) * tk.nsrc * 32;
   const DevMesh& d = m->d;
   {
     ScopedTimer tm("fill_K_split", s);
-    fill_K_split<R><<<unsigned((threads + 255) / 256), 256, 0, s>>>(tk, dl.p, tab, d.geo.p, d.bgeo.p, d.xyz.p, d.tri.p,
+    fill_K_split<R><<<unsigned((threads + 255) / 256), 256, 0, s>>>(tk, doff.p, dpts.p, d.geo.p, d.bgeo.p, d.xyz.p, d.tri.p,
                                                                    d.tri_edge.p, d.btri_edge.p), ::sldm::count_launch();
   }
   SLDM_CUDA(cudaGetLastError());
   SLDM_CUDA(cudaStreamSynchronize(s));
 }
 
-template void fill_L_split_task<float>(const sldm_mesh*, const LTask&, const std::vector<int8_t>&, cudaStream_t);
-template void fill_L_split_task<double>(const sldm_mesh*, const LTask&, const std::vector<int8_t>&, cudaStream_t);
-template void fill_K_split_task<float>(const sldm_mesh*, const KTask&, const std::vector<int8_t>&, cudaStream_t);
-template void fill_K_split_task<double>(const sldm_mesh*, const KTask&, const std::vector<int8_t>&, cudaStream_t);
+template void fill_L_split_task<float>(const sldm_mesh*, const LTask&, const SplitRules&, cudaStream_t);
+template void fill_L_split_task<double>(const sldm_mesh*, const LTask&, const SplitRules&, cudaStream_t);
+template void fill_K_split_task<float>(const sldm_mesh*, const KTask&, const SplitRules&, cudaStream_t);
+template void fill_K_split_task<double>(const sldm_mesh*, const KTask&, const SplitRules&, cudaStream_t);
 
 }  // namespace sldm

@@ -182,14 +182,26 @@ void fill_L(const sldm_mesh* m, const std::vector<LTask>& tasks, cudaStream_t s)
 template <class R>
 void fill_K(const sldm_mesh* m, const std::vector<KTask>& tasks, cudaStream_t s);
 
-// Good-conductor fills (fill_sub.cu): the subdivision level of every source of a
-// task (0 = unsplit), and the split fill of a task that has a level above 0.
-std::vector<int8_t> split_levels_L(const HostMesh& h, const LTask& tk);
-std::vector<int8_t> split_levels_K(const HostMesh& h, const KTask& tk);
+// Good-conductor fills (fill_sub.cu).  One point of a source's quadrature:
+// barycentric coordinates with respect to the source triangle and its weight as
+// a fraction of the source's area.
+struct __align__(32) SrcPoint {
+  double x, y, z, w;
+};
+// The quadrature of every source of a task that has at least one source to
+// split (else split = false and nothing else is filled): source i's points are
+// pts[off[i] .. off[i + 1]).
+struct SplitRules {
+  bool split = false;
+  std::vector<int32_t> off;
+  std::vector<SrcPoint> pts;
+};
+SplitRules split_rules_L(const HostMesh& h, const LTask& tk);
+SplitRules split_rules_K(const HostMesh& h, const KTask& tk);
 template <class R>
-void fill_L_split_task(const sldm_mesh* m, const LTask& tk, const std::vector<int8_t>& lev, cudaStream_t s);
+void fill_L_split_task(const sldm_mesh* m, const LTask& tk, const SplitRules& rules, cudaStream_t s);
 template <class R>
-void fill_K_split_task(const sldm_mesh* m, const KTask& tk, const std::vector<int8_t>& lev, cudaStream_t s);
+void fill_K_split_task(const sldm_mesh* m, const KTask& tk, const SplitRules& rules, cudaStream_t s);
 // Kbar (ne_o x ne_o, op precision) = Kb (ne_o x nbe_o) * C_o, plus beta * I_x/2 (dense add of Gram)
 template <class R>
 void contract_bc(const sldm_mesh* m, int obj, const void* Kb, int64_t ldKb, void* K, int64_t ldK,

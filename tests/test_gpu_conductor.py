@@ -2,9 +2,9 @@
 with the FP64 oracle, through the C ABI.
 
 A copper bar 20 x 2 x 1 um (80 triangles, 1% seeded jitter) in free space:
-at 50 GHz (skin depth 0.30 um) the primal sources are split 3-4 times, the
-barycentric ones 1-3 times, and 536 of the 6,400 primal pairs lie beyond the
-|Im k| R = 40 cut; at 5 GHz levels 1-2 and 0-2 with no cut.
+at 50 GHz (skin depth 0.30 um) the primal and barycentric sources are bisected
+into up to tens of children, and 536 of the 6,400 primal pairs lie beyond the
+|Im k| R = 40 cut; at 5 GHz fewer children and no cut.
 
 Tolerances as for the unsplit FP64 path: blocks 1e-10 relative (Frobenius and
 max; summation order and atomics differ).  The system has a condition number
@@ -56,8 +56,10 @@ def bar(request):
 def test_case_exercises_splitting(bar):
     m = bar.om
     k = S.wavenumber(S.Material(*COPPER), bar.A.k0)
-    assert OFL.sub_level(k, OFL._diam(m.xyz[m.tri])).max() >= 2
-    assert OFL.sub_level(k, OFL._diam(m.bxyz[m.btri])).max() >= 2
+    P, Pb = m.xyz[m.tri], m.bxyz[m.btri]
+    assert OFL.needs_split(k, P).any() and OFL.needs_split(k, Pb).any()
+    assert max(len(OFL.source_rule(p, k)[1]) for p in P) >= 6 * 4
+    assert max(len(OFL.source_rule(p, k)[1]) for p in Pb) >= 6 * 4
 
 
 @pytest.mark.parametrize("prec", [0, 1])

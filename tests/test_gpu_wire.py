@@ -100,17 +100,20 @@ def wire():
 
 def _L_entry_pairs(om, k, tris_a, tris_b):
     """Oracle local blocks of the given triangle pairs, as oracle.fill.fill_L forms them:
-    the source's split level, and the far-pair cut when any source of the fill is split."""
+    the source's split rule, and the far-pair cut when any source of the fill is split."""
     P = om.xyz[om.tri]
-    split = OFL.sub_level(k, OFL._diam(P)).max() > 0
-    lev = OFL.sub_level(k, OFL._diam(P[tris_b]))
+    split = OFL.needs_split(k, P).any()
     la = np.zeros((len(tris_a), 3, 3), complex)
     lp = np.zeros(len(tris_a), complex)
     keep = np.ones(len(tris_a), bool)
     if split:
         keep = OFL._kept(k, P[tris_a], P[tris_b], OFL._touch_primal(om.tri, tris_a, tris_b))
     for i in np.nonzero(keep)[0]:
-        a, b = OFL._L_pairs(om, k, tris_a[i:i + 1], tris_b[i:i + 1], int(lev[i]))
+        rule = None
+        if split:
+            pts, w = OFL.source_rule(P[tris_b[i]], k)
+            rule = (pts[None], w[None])
+        a, b = OFL._L_pairs(om, k, tris_a[i:i + 1], tris_b[i:i + 1], rule)
         la[i], lp[i] = a[0], b[0]
     return la, lp
 

@@ -1,6 +1,7 @@
-"""Pins of the oracle's good-conductor integration (source triangles split through
-their edge midpoints until |Im k| d <= 1, one-term extraction on split touching
-pairs, far pairs dropped beyond |Im k| R = 40), against facts fixed outside it:
+"""Pins of the oracle's good-conductor integration (source triangles bisected
+through their longest edge until no edge exceeds 1/|Im k|, one-term extraction
+on split touching pairs, far pairs dropped beyond |Im k| R = 40), against facts
+fixed outside it:
 polynomial exactness of the composite rule, closed-form integrals of a smooth
 function, brute-force integration of strongly decaying kernels, and the size of
 the dropped entries."""
@@ -25,39 +26,58 @@ def copper_k(freq, sigma=5.8e7):
     return k0 * np.sqrt(complex(1.0, -sigma / (w * EPS0)))
 
 
-@pytest.mark.parametrize("L", [0, 1, 2, 3])
-def test_sub_rule_exact_to_degree_4(L):
-    pts, w = fill.sub_rule(L)
-    assert pts.shape == (6 * 4 ** L, 3) and abs(w.sum() - 1.0) < 1e-14
-    assert np.allclose(pts.sum(axis=1), 1.0) and pts.min() > 0.0
-    # reference triangle (0,0), (1,0), (0,1): int x^a y^b = a! b! / (a + b + 2)!
+REF = np.array([[0.0, 0, 0], [1.0, 0, 0], [0.0, 1, 0]])   # reference triangle (0,0), (1,0), (0,1)
+
+
+@pytest.mark.parametrize("h", [2.0, 0.9, 0.4, 0.2])
+def test_split_rule_exact_to_degree_4(h):
+    pts, w = fill.source_rule(REF, 1j / h)
+    assert abs(w.sum() - 1.0) < 1e-14 and np.allclose(pts.sum(axis=1), 1.0) and pts.min() > 0.0
+    # int x^a y^b = a! b! / (a + b + 2)!
     x, y = pts[:, 1], pts[:, 2]
     for a in range(5):
         for b in range(5 - a):
             exact = math.factorial(a) * math.factorial(b) / math.factorial(a + b + 2)
-            assert abs(0.5 * np.sum(w * x ** a * y ** b) - exact) < 1e-14, (L, a, b)
+            assert abs(0.5 * np.sum(w * x ** a * y ** b) - exact) < 1e-14, (h, a, b)
 
 
-def test_sub_rule_converges_on_a_smooth_function():
+def test_split_children_geometry():
+    """Every child's longest edge is at most h, the area fractions are powers of 1/2
+    summing to 1, an unsplit triangle is its own child, and a thin triangle is cut
+    across its long direction only."""
+    for P, h in ((REF, 0.3), (np.array([[0.0, 0, 0], [10.0, 0, 0], [3.0, 0.5, 0]]), 1.0)):
+        B, f = fill.split_children(P, h)
+        X = np.einsum('cvk,kd->cvd', B, P)
+        assert np.max(np.linalg.norm(X - np.roll(X, -1, axis=1), axis=2)) <= h
+        assert abs(f.sum() - 1.0) < 1e-15 and np.allclose(np.log2(f), np.round(np.log2(f)))
+        area = 0.5 * np.linalg.norm(np.cross(X[:, 1] - X[:, 0], X[:, 2] - X[:, 0]), axis=1)
+        assert np.allclose(area / (0.5 * np.linalg.norm(np.cross(P[1] - P[0], P[2] - P[0]))), f)
+    B, f = fill.split_children(REF, 2.0)
+    assert len(f) == 1 and np.array_equal(B[0], np.eye(3))
+    thin = np.array([[0.0, 0, 0], [10.0, 0, 0], [3.0, 0.5, 0]])
+    _, f = fill.split_children(thin, 1.0)
+    assert len(f) <= 48            # edge-midpoint quartering to the same edge bound needs 4^4 = 256
+
+
+def test_split_rule_converges_on_a_smooth_function():
     """int exp(a x + b y) over the reference triangle = [(e^a - e^b)/(a - b) - (e^a - 1)/a] / b."""
     a, b = 2.0, -3.0
     exact = ((np.exp(a) - np.exp(b)) / (a - b) - (np.exp(a) - 1) / a) / b
     err = []
-    for L in range(4):
-        pts, w = fill.sub_rule(L)
+    for h in (2.0, 1.0, 0.5, 0.25):
+        pts, w = fill.source_rule(REF, 1j / h)
         err.append(abs(0.5 * np.sum(w * np.exp(a * pts[:, 1] + b * pts[:, 2])) - exact))
-    # a degree-4 rule on children of half the size: error ratio 2^5 or better per level
     for e0, e1 in zip(err, err[1:]):
-        assert e1 < e0 / 25.0, err
+        assert e1 < e0 / 10.0, err
 
 
-def test_sub_level_rule():
+def test_needs_split_rule():
     k = 1.0 - 1.0j
-    d = np.array([0.5, 1.0, 1.5, 2.0, 2.1, 40.0, 128.0])
-    assert list(fill.sub_level(k, d)) == [0, 0, 1, 1, 2, 6, 7]
-    assert list(fill.sub_level(3.0 + 0j, d)) == [0] * len(d)       # lossless: never split
+    P = np.array([d * REF / np.sqrt(2) for d in (0.5, 1.0, 1.5)])   # longest edge d
+    assert list(fill.needs_split(k, P)) == [False, False, True]
+    assert not fill.needs_split(3.0 + 0j, P).any()                   # lossless: never split
     with pytest.raises(ValueError):
-        fill.sub_level(k, np.array([129.0]))
+        fill.source_rule(REF * 1e3, k)                               # too many children
 
 
 def _lp_brute(k, A, B, n=160):
@@ -74,7 +94,7 @@ def _lp_brute(k, A, B, n=160):
 @pytest.mark.parametrize("case", ["self", "edge"])
 def test_split_touching_pair_vs_brute_force(case):
     """Copper at 50 GHz (skin depth 0.30 um) on a 3.6 um triangle: the split rule
-    (level 4) matches brute force; the unsplit 6-point rule is off by tens of per cent."""
+    matches brute force; the unsplit 6-point rule is off by tens of per cent."""
     k = copper_k(50e9)
     A = np.array([[0, 0, 0], [3.6e-6, 0, 0], [0.9e-6, 3.0e-6, 0]])
     if case == "self":
@@ -88,11 +108,11 @@ def test_split_touching_pair_vs_brute_force(case):
         tri = np.array([[0, 1, 2], [1, 0, 3]])
         ta, tb = np.array([0]), np.array([1])
     m = _Pair(xyz, tri)
-    L = int(fill.sub_level(k, [np.max(np.linalg.norm(B - np.roll(B, 1, axis=0), axis=1))])[0])
-    assert L == 4
+    pts, w = fill.source_rule(B, k)
+    assert len(w) >= 6 * 16
     ref = _lp_brute(k, A, B, n=200)
-    _, lp = fill._L_pairs(m, k, ta, tb, L)
-    _, lp0 = fill._L_pairs(m, k, ta, tb, 0)
+    _, lp = fill._L_pairs(m, k, ta, tb, (pts[None], w[None]))
+    _, lp0 = fill._L_pairs(m, k, ta, tb)
     assert abs(lp[0] - ref) < 3e-4 * abs(ref), (lp[0], ref)
     assert abs(lp0[0] - ref) > 0.5 * abs(ref)
 
@@ -116,15 +136,17 @@ def test_dropped_pairs_are_negligible():
     v, f = icosphere(1, 15e-6)
     m = Mesh(v, f)
     P = m.xyz[m.tri]
-    lev = fill.sub_level(k, fill._diam(P))
     ta = np.repeat(np.arange(m.nt), m.nt)
     tb = np.tile(np.arange(m.nt), m.nt)
     keep = fill._kept(k, P[ta], P[tb], fill._touch_primal(m.tri, ta, tb))
     assert 0 < np.sum(~keep) < len(ta)
     drop = np.nonzero(~keep)[0][:40]
-    la, lp = fill._L_pairs(m, k, ta[drop], tb[drop], int(lev.max()))
-    _, lself = fill._L_pairs(m, k, np.array([0]), np.array([0]), int(lev[0]))
-    assert np.max(np.abs(lp)) < 1e-15 * abs(lself[0])
+
+    def lp_of(a, b):
+        pts, w = fill.source_rule(P[b], k)
+        return fill._L_pairs(m, k, np.array([a]), np.array([b]), (pts[None], w[None]))[1][0]
+    lp = np.array([lp_of(ta[i], tb[i]) for i in drop])
+    assert np.max(np.abs(lp)) < 1e-15 * abs(lp_of(0, 0))
 
 
 def _copper_sphere(split=True):
@@ -171,6 +193,6 @@ def test_copper_sphere_vs_mie(monkeypatch):
     s = farfield.rcs(m, A.k0, S.j_delta(A, x), th)
     assert np.max(np.abs(10 * np.log10(s / mie.rcs_eplane(A.k0, a_eq, eps, np.pi - th)))) < 0.15
     # planted mistake: no splitting
-    monkeypatch.setattr(fill, "sub_level", lambda k, d: np.zeros(np.shape(d), dtype=np.int64))
+    monkeypatch.setattr(fill, "needs_split", lambda k, P: np.zeros(len(P), dtype=bool))
     m, A, x, a_eq, eps = _copper_sphere()
     assert _absorbed(A, x) / _mie_absorbed(A.k0, a_eq, eps) < 0.5
