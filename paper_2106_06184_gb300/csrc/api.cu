@@ -171,6 +171,54 @@ static void apply_any(const sldm_op* op, const double2* x, double2* y, int nrhs,
 
 static cplx eps_complex(double eps_r, double sigma, double omega) { return cplx(eps_r, -sigma / (omega * EPS0_)); }
 
+// ref[o] = the first object that object o repeats, else o.  Object o repeats r
+// when they have the same material, the same triangles and edges in the same
+// local order (vertex and edge ids shifted by constants, the same edge signs)
+// and vertices that differ by one translation to 1e-12 of the object's size.
+// Interior blocks and Y depend only on that shape and material (the
+// equivalent configuration uses the homogeneous kernel of the background
+// layer, which a translation leaves unchanged), so they are filled once.
+static std::vector<int> repeated_objects(const HostMesh& h, const sldm_material* mats) {
+  const int nobj = int(h.nobj);
+  std::vector<int> ref(nobj);
+  for (int o = 0; o < nobj; ++o) {
+    ref[o] = o;
+    const int t0 = h.tri_begin[o], nt = h.tri_begin[o + 1] - t0, e0 = h.edge_begin[o], ne = h.edge_begin[o + 1] - e0;
+    for (int r = 0; r < o && ref[o] == o; ++r) {
+      if (ref[r] != r) continue;
+      const int u0 = h.tri_begin[r], ue0 = h.edge_begin[r];
+      if (h.tri_begin[r + 1] - u0 != nt || h.edge_begin[r + 1] - ue0 != ne) continue;
+      if (h.bedge_begin[o + 1] - h.bedge_begin[o] != h.bedge_begin[r + 1] - h.bedge_begin[r]) continue;
+      const sldm_material &a = mats[o], &b = mats[r];
+      if (a.eps_r != b.eps_r || a.mu_r != b.mu_r || a.sigma != b.sigma || a.layer != b.layer) continue;
+      const int64_t dv = int64_t(h.tri[3 * size_t(t0)]) - h.tri[3 * size_t(u0)];
+      bool same = true;
+      double shift[3], lo = 1e300, hi = -1e300;
+      for (int d = 0; d < 3; ++d) shift[d] = h.xyz[3 * size_t(h.tri[3 * size_t(t0)]) + d] - h.xyz[3 * size_t(h.tri[3 * size_t(u0)]) + d];
+      for (int i = 0; i < 3 * nt && same; ++i) {
+        const size_t io = 3 * size_t(t0) + i, ir = 3 * size_t(u0) + i;
+        same = int64_t(h.tri[io]) - h.tri[ir] == dv && h.tri_edge[io] - e0 == h.tri_edge[ir] - ue0 &&
+               h.tri_sign[io] == h.tri_sign[ir];
+      }
+      for (int j = 0; j < ne && same; ++j)
+        same = h.uv[2 * size_t(e0 + j)] - h.uv[2 * size_t(ue0 + j)] == dv &&
+               h.uv[2 * size_t(e0 + j) + 1] - h.uv[2 * size_t(ue0 + j) + 1] == dv;
+      if (!same) continue;
+      double dmax = 0;
+      for (int i = 0; i < 3 * nt; ++i) {
+        const size_t vo = size_t(h.tri[3 * size_t(t0) + i]), vr = size_t(h.tri[3 * size_t(u0) + i]);
+        for (int d = 0; d < 3; ++d) {
+          dmax = std::max(dmax, std::fabs(h.xyz[3 * vo + d] - h.xyz[3 * vr + d] - shift[d]));
+          lo = std::min(lo, h.xyz[3 * vr + d]);
+          hi = std::max(hi, h.xyz[3 * vr + d]);
+        }
+      }
+      if (dmax <= 1e-12 * (hi - lo)) ref[o] = r;
+    }
+  }
+  return ref;
+}
+
 template <class R>
 static void assemble_impl(sldm_op* op, const sldm_material* mats, cudaStream_t s) {
   typedef typename std::conditional<sizeof(R) == 4, float2, double2>::type C;
@@ -216,10 +264,14 @@ static void assemble_impl(sldm_op* op, const sldm_material* mats, cudaStream_t s
   op->loc.alloc(off * es);
   op->loc.zero(s);
   char* loc = op->loc.p;
+  // ---- objects that repeat an earlier one take its interior blocks and Y
+  const std::vector<int> ref = repeated_objects(h, mats);
   // ---- internal L^A, L^phi with each object's wavenumber
   {
     std::vector<LTask> tasks;
-    for (auto& oi : op->obj) {
+    for (int o = 0; o < op->nobj; ++o) {
+      if (ref[o] != o) continue;
+      const ObjInfo& oi = op->obj[o];
       LTask t{};
       t.t0 = oi.t0; t.ntest = oi.nt; t.s0 = oi.t0; t.nsrc = oi.nt;
       t.e_row0 = oi.e0; t.e_col0 = oi.e0; t.t_row0 = oi.t0; t.t_col0 = oi.t0;
@@ -255,6 +307,7 @@ static void assemble_impl(sldm_op* op, const sldm_material* mats, cudaStream_t s
     Kb.zero(s);
     std::vector<KTask> tasks;
     for (int o = 0; o < op->nobj; ++o) {
+      if (ref[o] != o) continue;
       const ObjInfo& oi = op->obj[o];
       KTask t{};
       t.t0 = oi.t0; t.ntest = oi.nt; t.c0 = 6 * oi.t0; t.nsrc = 6 * oi.nt;
@@ -267,6 +320,7 @@ static void assemble_impl(sldm_op* op, const sldm_material* mats, cudaStream_t s
     }
     fill_K<R>(m, tasks, s);
     for (int o = 0; o < op->nobj; ++o) {
+      if (ref[o] != o) continue;
       const ObjInfo& oi = op->obj[o];
       int64_t ld = h.bedge_begin[o + 1] - h.bedge_begin[o];
       void* dst = pass == 0 ? (void*)(loc + oi.oK * es) : (void*)(Kl.p + kl_off[o] * es);
@@ -283,6 +337,7 @@ static void assemble_impl(sldm_op* op, const sldm_material* mats, cudaStream_t s
     Rl.alloc(rl_total);
     std::vector<LUSysT<C>> sys;
     for (int o = 0; o < op->nobj; ++o) {
+      if (ref[o] != o) continue;
       const ObjInfo& oi = op->obj[o];
       build_Ml<C>(m, o, op->k0, op->LAm.p, op->ne, op->LPm.p, op->nt, Kl.p + kl_off[o] * es, oi.ne, op->ix_val.p,
                   Ml.p + ml_off[o], Rl.p + rl_off[o], s);
@@ -290,10 +345,25 @@ static void assemble_impl(sldm_op* op, const sldm_material* mats, cudaStream_t s
     }
     lu_solve_batched<C>(sys, s);
     for (int o = 0; o < op->nobj; ++o) {
+      if (ref[o] != o) continue;
       const ObjInfo& oi = op->obj[o];
       // undo the length scaling of M_l: Y11 = Yh11 / l, Y21 = l Yh21
       copy_scaled<C>(Rl.p + rl_off[o], int64_t(oi.ne) * oi.ne, 1.0 / h.ell, loc + oi.oY11 * es, s);
       copy_scaled<C>(Rl.p + rl_off[o] + int64_t(oi.ne) * oi.ne, int64_t(oi.nq) * oi.ne, h.ell, loc + oi.oY21 * es, s);
+    }
+    // repeated objects: the first one's L^A, L^phi, K, Y11, Y21 (same layout, same sizes)
+    for (int o = 0; o < op->nobj; ++o) {
+      if (ref[o] == o) continue;
+      const ObjInfo& oi = op->obj[o];
+      const ObjInfo& ri = op->obj[ref[o]];
+      const int64_t n_ee = int64_t(oi.ne) * oi.ne;
+      SLDM_CUDA(cudaMemcpyAsync(loc + oi.oLA * es, loc + ri.oLA * es, n_ee * es, cudaMemcpyDeviceToDevice, s));
+      SLDM_CUDA(cudaMemcpyAsync(loc + oi.oLP * es, loc + ri.oLP * es, int64_t(oi.nt) * oi.nt * es,
+                                cudaMemcpyDeviceToDevice, s));
+      SLDM_CUDA(cudaMemcpyAsync(loc + oi.oK * es, loc + ri.oK * es, n_ee * es, cudaMemcpyDeviceToDevice, s));
+      SLDM_CUDA(cudaMemcpyAsync(loc + oi.oY11 * es, loc + ri.oY11 * es, n_ee * es, cudaMemcpyDeviceToDevice, s));
+      SLDM_CUDA(cudaMemcpyAsync(loc + oi.oY21 * es, loc + ri.oY21 * es, int64_t(oi.nq) * oi.ne * es,
+                                cudaMemcpyDeviceToDevice, s));
     }
     SLDM_CUDA(cudaStreamSynchronize(s));
   }

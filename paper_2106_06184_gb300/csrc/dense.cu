@@ -520,7 +520,7 @@ template void lu_solve_batched<double2>(const std::vector<LUSysT<double2>>&, cud
 // (a complex64 matrix may be applied in FP64: the residual of iterative
 // refinement).
 template <class CM, class CV, int NR>
-__global__ void __launch_bounds__(256) gemv_jobs_kernel(const GemvJob* __restrict__ jobs, const int64_t* __restrict__ rowstart,
+__global__ void __launch_bounds__(256, NR == 1 ? 6 : 1) gemv_jobs_kernel(const GemvJob* __restrict__ jobs, const int64_t* __restrict__ rowstart,
                                                         int njobs, int64_t total_rows, int nrhs) {
   typedef typename CT<CV>::R R;
   const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
