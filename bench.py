@@ -97,7 +97,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # launch, 4 x 4 metasurface, 423,936,000 algorithmic bytes per launch; summary in
 # profiles/gemv_main_metasurface-4x4-c64.md), valid while the kernel source is
 # unchanged (sha256 prefix of the kernel's text in dense.cu).
-GEMV_TRAFFIC = dict(sha="500e573e8fd00170", per_alg_byte=(424.168704e6 + 2.987520e6) / 423.936e6)
+GEMV_TRAFFIC = dict(sha="e09483bce0c5daf0", per_alg_byte=(424.169472e6 + 3.703040e6) / 423.936e6)
 
 
 def gemv_kernel_sha():

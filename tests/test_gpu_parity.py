@@ -64,6 +64,15 @@ def cyl4():
     return Case(xyz, tri, obj, [(6.0, 1.0, 0.0)] * 4, (1.0, 1.0, 0.0), 299792458.0 / 1e-6)
 
 
+@pytest.fixture(scope="module")
+def cyl3_mixed():
+    """Three translated cylinders: the first and third of one material (the third's
+    blocks are copied from the first), the middle one of another (filled itself)."""
+    xyz, tri, obj = cylinder_array(3, 1, 120e-9, 300e-9, 500e-9)
+    return Case(xyz, tri, obj, [(6.0, 1.0, 0.0), (3.0, 1.0, 0.0), (6.0, 1.0, 0.0)], (1.0, 1.0, 0.0),
+                299792458.0 / 1e-6)
+
+
 def build_op(case, prec):
     sl = _sl()
     m = sl.Mesh(case.xyz, case.tri, case.obj)
@@ -92,7 +101,7 @@ def _blocks(case, op, sl):
     return out
 
 
-@pytest.mark.parametrize("which", ["sphere", "two_lossy", "cyl4"])
+@pytest.mark.parametrize("which", ["sphere", "two_lossy", "cyl4", "cyl3_mixed"])
 def test_fp64_blocks_match_oracle(which, request):
     case = request.getfixturevalue(which)
     sl, m, st, op = build_op(case, 0)
