@@ -60,7 +60,7 @@ WORKLOADS["copper-wire-sio2-si-pec-1MHz-50GHz-fp64"] = dict(
     mesh=copper_wire, obj=None, mats=[(1.0, 1.0, 5.8e7, 1)],
     layers=[(1.0, 1.0, 0.0, 0.0), (3.9, 1.0, 0.0, 10e-6), (11.9, 1.0, 10.0, 200e-6)], z_top=0.0, bottom="pec",
     freqs=WIRE_FREQS, precision=0, tol=1e-8, maxit=6000, khat=[0.0, 0.0, -1.0], pol=[1.0, 0.0, 0.0], n_angles=0,
-    e2e_steps=3)
+    e2e_steps=20)
 DEFAULT_WORKLOAD = "copper-wire-sio2-si-pec-1MHz-50GHz-fp64"
 
 

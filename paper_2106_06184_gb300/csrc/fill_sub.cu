@@ -53,19 +53,19 @@ __device__ cd green_smooth1(cd k, double R) {
   return {(ex * cn - 1.0) * INV4PI / R, -ex * sn * INV4PI / R};
 }
 
-// G = exp(-j k R)/(4 pi R)
-__device__ __forceinline__ cd green_full(cd k, double R) {
+// G = exp(-j k R)/(4 pi R), from R and 1/R (no division on the FP64 pipe)
+__device__ __forceinline__ cd green_full(cd k, double R, double iR) {
   double sn, cn;
   sincos(k.r * R, &sn, &cn);
-  const double a = exp(k.i * R) * INV4PI / R;
+  const double a = exp(k.i * R) * INV4PI * iR;
   return {a * cn, -a * sn};
 }
 
 // g1 of grad G = (r - r') g1 = -(1 + j k R) exp(-j k R)/(4 pi R^3)
-__device__ __forceinline__ cd grad_full(cd k, double R) {
+__device__ __forceinline__ cd grad_full(cd k, double R, double iR) {
   double sn, cn;
   sincos(k.r * R, &sn, &cn);
-  const double a = exp(k.i * R) * INV4PI / (R * R * R);
+  const double a = exp(k.i * R) * INV4PI * (iR * iR * iR);
   const cd e = {a * cn, -a * sn};
   const cd f = {1.0 - k.i * R, k.r * R};  // 1 + j k R
   const cd p = cmul(f, e);
@@ -133,8 +133,9 @@ __global__ void __launch_bounds__(256) fill_L_split(LTask tk, const int32_t* __r
     const double ws = As * sp.w;
     const double* rq = gt + GEO_RHO + 3 * q;
     const double D0 = dc[0] + rq[0] - rp[0], D1 = dc[1] + rq[1] - rp[1], D2 = dc[2] + rq[2] - rp[2];
-    const double Rr = sqrt(D0 * D0 + D1 * D1 + D2 * D2);
-    cd g = touch ? (split ? green_smooth1(k, Rr) : green_smooth(k, Rr)) : green_full(k, Rr);
+    const double r2 = D0 * D0 + D1 * D1 + D2 * D2;
+    const double iR = rsqrt(r2), Rr = r2 * iR;
+    cd g = touch ? (split ? green_smooth1(k, sqrt(r2)) : green_smooth(k, sqrt(r2))) : green_full(k, Rr, iR);
     const double w = gt[GEO_W + q] * ws;
     g.r *= w;
     g.i *= w;
@@ -273,8 +274,9 @@ __global__ void __launch_bounds__(256) fill_K_split(KTask tk, const int32_t* __r
     const double ws = As * sp.w;
     const double* rq = gt + GEO_RHO + 3 * q;
     const double D[3] = {dc[0] + rq[0] - rp[0], dc[1] + rq[1] - rp[1], dc[2] + rq[2] - rp[2]};
-    const double Rr = sqrt(D[0] * D[0] + D[1] * D[1] + D[2] * D[2]);
-    cd g1 = touch ? grad_smooth(k, Rr) : grad_full(k, Rr);
+    const double r2 = D[0] * D[0] + D[1] * D[1] + D[2] * D[2];
+    const double iR = rsqrt(r2), Rr = r2 * iR;
+    cd g1 = touch ? grad_smooth(k, sqrt(r2)) : grad_full(k, Rr, iR);
     const double w = gt[GEO_W + q] * ws;
     g1.r *= w;
     g1.i *= w;
