@@ -200,6 +200,17 @@ def lu_update_bytes(n, nrhs):
     return tot, n - 1
 
 
+# ----------------------------------------------------------------------------- ranks
+def max_over_ranks(value, world, device):
+    """The largest of every rank's value (the job's time is its slowest rank's)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ----------------------------------------------------------------------------- our arm
 def run_ours(args, rank, world):
     import torch
@@ -260,11 +271,7 @@ def run_ours(args, rank, world):
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
-    total_ms = float(sum(times))
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(float(sum(times)), world, "cuda")
 
     # ---- e2e: the same step through the public API with host buffers
     e2e_times = []
