@@ -114,7 +114,7 @@ typedef struct {
 typedef struct {
   double tol;           /* relative residual of the length-scaled system (default 1e-8), see sldm_solve */
   int32_t restart;      /* GMRES restart length m (default 300; at most N) */
-  int32_t maxit;        /* maximum total iterations (default 2000) */
+  int32_t maxit;        /* maximum iterations per right-hand side (default 2000) */
   int32_t x0_given;     /* nonzero: x holds the initial guess on entry */
   int32_t precond;      /* SLDM_PRECOND_P (0, default) or SLDM_PRECOND_NONE */
   int32_t refine;       /* SLDM_REFINE_AUTO (0, default) or SLDM_REFINE_OFF; see sldm_solve */
@@ -221,7 +221,9 @@ int sldm_rhs_planewave(const sldm_op* op, const double* khat, const double* pol,
  * twice) and Givens rotations (Sec. IV, GMRES), matrix-vector products in the
  * operator's precision, right-preconditioned by P of Eq. pcext (Sec. III:
  * diagonals of the blocks, with the analytic block inverse through the Schur
- * complement of the charge block, formed per object at assembly).
+ * complement of the charge block, formed per object at assembly).  Up to 8
+ * right-hand sides run in lockstep, each with its own Krylov basis, sharing one
+ * multi-RHS pass over the blocks per step; more are taken 8 at a time.
  * b, x: N x nrhs complex128 column-major.
  * The iteration runs on the length-scaled system Dr Z Dc (Dr = diag(1, 1, l),
  * Dc = diag(1/l, 1, l) on the blocks [j; e; u], l = the mesh's mean edge

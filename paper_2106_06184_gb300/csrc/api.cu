@@ -65,7 +65,8 @@ struct sldm_op {
   sldm::Precond pc;
   // GMRES workspace
   int ws_m = 0;
-  sldm::DBuf<double2> V, wb, wx, wr, wtmp, wtmp2, wacc, dh;
+  sldm::DBuf<double2> V, wb, wx, wr, wtmp, wtmp2, wacc, wz, dh;
+  int ws_nr = 0;
   sldm::DBuf<double> dnorm;
   std::mutex busy;
 };
@@ -400,18 +401,22 @@ static void assemble_impl(sldm_op* op, const sldm_material* mats, cudaStream_t s
 }
 
 // ---------------------------------------------------------------- GMRES
-static void ensure_ws(sldm_op* op, int m) {
-  if (op->ws_m == m && op->V.p) return;
-  op->V.alloc(size_t(op->N) * (m + 1));
-  op->wb.alloc(op->N);
-  op->wx.alloc(op->N);
-  op->wr.alloc(op->N);
-  op->wtmp.alloc(op->N);
-  op->wtmp2.alloc(op->N);
-  op->wacc.alloc(op->N);
-  op->dh.alloc(2 * (m + 2));
-  op->dnorm.alloc(1);
+// GMRES workspace for nr right-hand sides in lockstep (Krylov bases N x (m+1) each)
+static void ensure_ws(sldm_op* op, int m, int nr) {
+  if (op->ws_m == m && op->ws_nr >= nr && op->V.p) return;
+  const size_t N = size_t(op->N), W = size_t(sldm_op::WR);
+  op->V.alloc(N * (m + 1) * nr);
+  op->wb.alloc(N * W);
+  op->wx.alloc(N * W);
+  op->wr.alloc(N * W);
+  op->wtmp.alloc(N * W);
+  op->wtmp2.alloc(N * W);
+  op->wacc.alloc(N * W);
+  op->wz.alloc(N * W);
+  op->dh.alloc(W * 2 * (m + 2));
+  op->dnorm.alloc(W);
   op->ws_m = m;
+  op->ws_nr = nr;
 }
 
 static double dnorm(sldm_op* op, const double2* v, cudaStream_t s) {
@@ -429,112 +434,148 @@ static double dnorm(sldm_op* op, const double2* v, cudaStream_t s) {
 // metres, which is what the frequency scalings of the final system presume.
 // With the preconditioner P of Eq. pcext applied on the right, the scaled
 // preconditioner Dr P Dc cancels Dc:  operator = Dr Z P^-1 Dr^-1.
-static void op_hat(sldm_op* op, bool use_p, const double2* v, double2* w, cudaStream_t s) {
-  const double l = op->mesh->h.ell;
-  if (use_p) {
-    vscale3(op->N, op->ne, 1.0, 1.0, 1.0 / l, v, op->wtmp2.p, s);
-    prec_apply(op->pc, op->mesh, op->wtmp2.p, op->wtmp.p, s);
-  } else {
-    vscale3(op->N, op->ne, 1.0 / l, 1.0, l, v, op->wtmp.p, s);
-  }
-  apply_any(op, op->wtmp.p, w, 1, s);
-  vscale3(op->N, op->ne, 1.0, 1.0, l, w, w, s);
-}
-
-// Solves one right-hand side held in op->wb into op->wx (initial guess in wx)
-// by restarted, right-preconditioned GMRES on the length-scaled system;
-// relres = ||Dr (b - Z x)|| / ||Dr b||.  With `refine` (complex64 operators) the
-// true residual at every restart is accumulated in FP64 and each cycle stops
-// once it has reduced that residual by REFINE_CYCLE: the cycles are the
-// correction solves of iterative refinement, in the operator's precision.
+//
+// Restarted, right-preconditioned GMRES for nr <= WR right-hand sides in
+// lockstep: each has its own Krylov basis, Hessenberg matrix and rotations, and
+// the products of one step are made together (one multi-RHS pass over the
+// blocks).  Right-hand sides in op->wb, initial guesses in op->wx (N x nr);
+// relres[r] = ||Dr (b_r - Z x_r)|| / ||Dr b_r||.  With `refine` (complex64
+// operators) the true residual at every restart is accumulated in FP64 and each
+// cycle stops once it has reduced that residual by REFINE_CYCLE: the cycles are
+// the correction solves of iterative refinement, in the operator's precision.
 constexpr double REFINE_CYCLE = 1e-5;
-static void gmres_one(sldm_op* op, bool use_p, bool refine, int m, double tol, int maxit, int& iters, double& relres,
-                      cudaStream_t s) {
-  const int64_t N = op->N;
+static void gmres_block(sldm_op* op, bool use_p, bool refine, int m, double tol, int maxit, int nr, int& iters,
+                        double* relres, cudaStream_t s) {
+  const int64_t N = op->N, ne = op->ne;
   const double l = op->mesh->h.ell;
-  double2* V = op->V.p;
-  vscale3(N, op->ne, 1.0, 1.0, l, op->wb.p, op->wb.p, s);  // bh = Dr b
-  const double bnorm = dnorm(op, op->wb.p, s);
-  if (bnorm == 0) {
-    SLDM_CUDA(cudaMemsetAsync(op->wx.p, 0, N * sizeof(double2), s));
-    relres = 0;
-    return;
+  auto col = [&](DBuf<double2>& b, int r) { return b.p + int64_t(r) * N; };
+  auto Vr = [&](int r) { return op->V.p + int64_t(r) * N * (m + 1); };
+  auto dhr = [&](int r) { return op->dh.p + int64_t(r) * 2 * (m + 2); };
+  std::vector<double> bnorm(nr), beta(nr);
+  for (int r = 0; r < nr; ++r) {
+    vscale3(N, ne, 1.0, 1.0, l, col(op->wb, r), col(op->wb, r), s);  // bh = Dr b
+    bnorm[r] = dnorm(op, col(op->wb, r), s);
+    if (bnorm[r] == 0) SLDM_CUDA(cudaMemsetAsync(col(op->wx, r), 0, N * sizeof(double2), s));  // b = 0: x = 0
   }
-  auto residual = [&]() {  // wr = Dr (b - Z x)
-    apply_any(op, op->wx.p, op->wr.p, 1, s, refine);
-    vscale3(N, op->ne, 1.0, 1.0, l, op->wr.p, op->wr.p, s);
-    vaxpby(N, 1.0, op->wb.p, -1.0, op->wr.p, s);
-    return dnorm(op, op->wr.p, s);
+  auto residuals = [&]() {  // wr = Dr (b - Z x), every column
+    apply_any(op, op->wx.p, op->wr.p, nr, s, refine);
+    for (int r = 0; r < nr; ++r) {
+      vscale3(N, ne, 1.0, 1.0, l, col(op->wr, r), col(op->wr, r), s);
+      vaxpby(N, 1.0, col(op->wb, r), -1.0, col(op->wr, r), s);
+      beta[r] = dnorm(op, col(op->wr, r), s);
+    }
   };
-  double beta = residual();
-  std::vector<cplx> H(size_t(m + 1) * m), g(m + 1), cs(m), sn(m), hh(2 * (m + 2));
-  double hn = 0;
-  while (beta / bnorm > tol && iters < maxit) {
-    SLDM_REQUIRE(std::isfinite(beta), SLDM_ENUMERIC, "GMRES: non-finite residual");
-    vaxpby(N, 1.0 / beta, op->wr.p, 0.0, V, s);
-    std::fill(g.begin(), g.end(), cplx(0));
-    g[0] = beta;
-    int kused = 0;
+  residuals();
+  std::vector<std::vector<cplx>> H(nr, std::vector<cplx>(size_t(m + 1) * m)), g(nr, std::vector<cplx>(m + 1)),
+      cs(nr, std::vector<cplx>(m)), sn(nr, std::vector<cplx>(m));
+  std::vector<int> it(nr, 0), kused(nr, 0);
+  std::vector<char> live(nr, 0);
+  std::vector<double2> hh(size_t(sldm_op::WR) * 2 * (m + 2));
+  std::vector<double> hn(sldm_op::WR);
+  for (;;) {
+    std::vector<int> act;
+    for (int r = 0; r < nr; ++r) {
+      SLDM_REQUIRE(std::isfinite(beta[r]), SLDM_ENUMERIC, "GMRES: non-finite residual");
+      if (bnorm[r] > 0 && beta[r] / bnorm[r] > tol && it[r] < maxit) act.push_back(r);
+    }
+    if (act.empty()) break;
+    for (int r : act) {
+      vaxpby(N, 1.0 / beta[r], col(op->wr, r), 0.0, Vr(r), s);
+      std::fill(g[r].begin(), g[r].end(), cplx(0));
+      g[r][0] = beta[r];
+      kused[r] = 0;
+      live[r] = 1;
+    }
     for (int k = 0; k < m; ++k) {
-      double2* w = V + int64_t(k + 1) * N;
-      op_hat(op, use_p, V + int64_t(k) * N, w, s);
-      // classical Gram-Schmidt, twice
-      vdots(V, N, k + 1, w, N, op->dh.p, s);
-      vmul(V, N, k + 1, op->dh.p, -1.0, w, N, s);
-      vdots(V, N, k + 1, w, N, op->dh.p + (m + 2), s);
-      vmul(V, N, k + 1, op->dh.p + (m + 2), -1.0, w, N, s);
-      vnorm2(w, N, op->dnorm.p, s);
-      SLDM_CUDA(cudaMemcpyAsync(hh.data(), op->dh.p, 2 * (m + 2) * sizeof(double2), cudaMemcpyDeviceToHost, s));
-      SLDM_CUDA(cudaMemcpyAsync(&hn, op->dnorm.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+      std::vector<int> on;
+      for (int r : act)
+        if (live[r]) on.push_back(r);
+      if (on.empty()) break;
+      const int na = int(on.size());
+      // the products of this step, together: w_r = Dr Z P^-1 Dr^-1 v_r (or Dr Z Dc v_r)
+      for (int j = 0; j < na; ++j) {
+        const double2* v = Vr(on[j]) + int64_t(k) * N;
+        if (use_p) {
+          vscale3(N, ne, 1.0, 1.0, 1.0 / l, v, col(op->wtmp2, j), s);
+          prec_apply(op->pc, op->mesh, col(op->wtmp2, j), col(op->wtmp, j), s);
+        } else {
+          vscale3(N, ne, 1.0 / l, 1.0, l, v, col(op->wtmp, j), s);
+        }
+      }
+      apply_any(op, op->wtmp.p, op->wz.p, na, s);
+      for (int j = 0; j < na; ++j) {
+        const int r = on[j];
+        double2* w = Vr(r) + int64_t(k + 1) * N;
+        vscale3(N, ne, 1.0, 1.0, l, col(op->wz, j), w, s);
+        // classical Gram-Schmidt, twice
+        vdots(Vr(r), N, k + 1, w, N, dhr(r), s);
+        vmul(Vr(r), N, k + 1, dhr(r), -1.0, w, N, s);
+        vdots(Vr(r), N, k + 1, w, N, dhr(r) + (m + 2), s);
+        vmul(Vr(r), N, k + 1, dhr(r) + (m + 2), -1.0, w, N, s);
+        vnorm2(w, N, op->dnorm.p + j, s);
+      }
+      SLDM_CUDA(cudaMemcpyAsync(hh.data(), op->dh.p, size_t(nr) * 2 * (m + 2) * sizeof(double2), cudaMemcpyDeviceToHost, s));
+      SLDM_CUDA(cudaMemcpyAsync(hn.data(), op->dnorm.p, size_t(na) * sizeof(double), cudaMemcpyDeviceToHost, s));
       SLDM_CUDA(cudaStreamSynchronize(s));
-      hn = std::sqrt(hn);
-      for (int i = 0; i <= k; ++i) H[size_t(i) * m + k] = hh[i] + hh[(m + 2) + i];
-      H[size_t(k + 1) * m + k] = hn;
-      if (hn > 0) vaxpby(N, 1.0 / hn, w, 0.0, w, s);
-      for (int i = 0; i < k; ++i) {  // previous rotations
-        cplx a = H[size_t(i) * m + k], b = H[size_t(i + 1) * m + k];
-        H[size_t(i) * m + k] = cs[i] * a + sn[i] * b;
-        H[size_t(i + 1) * m + k] = -std::conj(sn[i]) * a + cs[i] * b;
+      for (int j = 0; j < na; ++j) {
+        const int r = on[j];
+        const double2* hr = hh.data() + size_t(r) * 2 * (m + 2);
+        const double h1 = std::sqrt(hn[j]);
+        std::vector<cplx>& Hr = H[r];
+        for (int i = 0; i <= k; ++i) Hr[size_t(i) * m + k] = cplx(hr[i].x, hr[i].y) + cplx(hr[(m + 2) + i].x, hr[(m + 2) + i].y);
+        Hr[size_t(k + 1) * m + k] = h1;
+        if (h1 > 0) vaxpby(N, 1.0 / h1, Vr(r) + int64_t(k + 1) * N, 0.0, Vr(r) + int64_t(k + 1) * N, s);
+        for (int i = 0; i < k; ++i) {  // previous rotations
+          cplx a = Hr[size_t(i) * m + k], b = Hr[size_t(i + 1) * m + k];
+          Hr[size_t(i) * m + k] = cs[r][i] * a + sn[r][i] * b;
+          Hr[size_t(i + 1) * m + k] = -std::conj(sn[r][i]) * a + cs[r][i] * b;
+        }
+        cplx a = Hr[size_t(k) * m + k], b = Hr[size_t(k + 1) * m + k];
+        double t = std::sqrt(std::norm(a) + std::norm(b));
+        if (std::abs(a) == 0) {
+          cs[r][k] = 0;
+          sn[r][k] = 1;
+          Hr[size_t(k) * m + k] = b;
+        } else {
+          cs[r][k] = std::abs(a) / t;
+          sn[r][k] = (a / std::abs(a)) * std::conj(b) / t;
+          Hr[size_t(k) * m + k] = (a / std::abs(a)) * t;
+        }
+        Hr[size_t(k + 1) * m + k] = 0;
+        g[r][k + 1] = -std::conj(sn[r][k]) * g[r][k];
+        g[r][k] = cs[r][k] * g[r][k];
+        ++it[r];
+        kused[r] = k + 1;
+        if (std::abs(g[r][k + 1]) / bnorm[r] <= tol || it[r] >= maxit || h1 == 0) live[r] = 0;
+        if (refine && std::abs(g[r][k + 1]) <= REFINE_CYCLE * beta[r]) live[r] = 0;
       }
-      cplx a = H[size_t(k) * m + k], b = H[size_t(k + 1) * m + k];
-      double t = std::sqrt(std::norm(a) + std::norm(b));
-      if (std::abs(a) == 0) {
-        cs[k] = 0;
-        sn[k] = 1;
-        H[size_t(k) * m + k] = b;
-      } else {
-        cs[k] = std::abs(a) / t;
-        sn[k] = (a / std::abs(a)) * std::conj(b) / t;
-        H[size_t(k) * m + k] = (a / std::abs(a)) * t;
-      }
-      H[size_t(k + 1) * m + k] = 0;
-      g[k + 1] = -std::conj(sn[k]) * g[k];
-      g[k] = cs[k] * g[k];
-      ++iters;
-      kused = k + 1;
-      if (std::abs(g[k + 1]) / bnorm <= tol || iters >= maxit || hn == 0) break;
-      if (refine && std::abs(g[k + 1]) <= REFINE_CYCLE * beta) break;
     }
     // y = H^-1 g (upper triangular);  x += (P^-1 Dr^-1 or Dc) V y
-    std::vector<cplx> y(kused);
-    for (int i = kused - 1; i >= 0; --i) {
-      cplx acc = g[i];
-      for (int j = i + 1; j < kused; ++j) acc -= H[size_t(i) * m + j] * y[j];
-      y[i] = acc / H[size_t(i) * m + i];
+    for (int r : act) {
+      const int ku = kused[r];
+      std::vector<cplx> y(ku);
+      for (int i = ku - 1; i >= 0; --i) {
+        cplx acc = g[r][i];
+        for (int j = i + 1; j < ku; ++j) acc -= H[r][size_t(i) * m + j] * y[j];
+        y[i] = acc / H[r][size_t(i) * m + i];
+      }
+      SLDM_CUDA(cudaMemcpyAsync(dhr(r), y.data(), ku * sizeof(double2), cudaMemcpyHostToDevice, s));
+      SLDM_CUDA(cudaMemsetAsync(col(op->wacc, r), 0, N * sizeof(double2), s));
+      vmul(Vr(r), N, ku, dhr(r), 1.0, col(op->wacc, r), N, s);
+      if (use_p) {
+        vscale3(N, ne, 1.0, 1.0, 1.0 / l, col(op->wacc, r), col(op->wtmp2, 0), s);
+        prec_apply(op->pc, op->mesh, col(op->wtmp2, 0), col(op->wtmp, 0), s);
+      } else {
+        vscale3(N, ne, 1.0 / l, 1.0, l, col(op->wacc, r), col(op->wtmp, 0), s);
+      }
+      vaxpby(N, 1.0, col(op->wtmp, 0), 1.0, col(op->wx, r), s);
     }
-    SLDM_CUDA(cudaMemcpyAsync(op->dh.p, y.data(), kused * sizeof(double2), cudaMemcpyHostToDevice, s));
-    SLDM_CUDA(cudaMemsetAsync(op->wacc.p, 0, N * sizeof(double2), s));
-    vmul(V, N, kused, op->dh.p, 1.0, op->wacc.p, N, s);
-    if (use_p) {
-      vscale3(N, op->ne, 1.0, 1.0, 1.0 / l, op->wacc.p, op->wtmp2.p, s);
-      prec_apply(op->pc, op->mesh, op->wtmp2.p, op->wtmp.p, s);
-    } else {
-      vscale3(N, op->ne, 1.0 / l, 1.0, l, op->wacc.p, op->wtmp.p, s);
-    }
-    vaxpby(N, 1.0, op->wtmp.p, 1.0, op->wx.p, s);
-    beta = residual();
+    residuals();
   }
-  relres = beta / bnorm;
+  for (int r = 0; r < nr; ++r) {
+    relres[r] = bnorm[r] > 0 ? beta[r] / bnorm[r] : 0.0;
+    iters += it[r];
+  }
 }
 
 }  // namespace sldm
@@ -914,22 +955,24 @@ int sldm_solve(const sldm_op* op_, const void* b, void* x, int32_t nrhs, const s
   bool use_p = !(opts && opts->precond == SLDM_PRECOND_NONE) && op->pc.ready;
   bool refine = op->prec == SLDM_PREC_F32 && !(opts && opts->refine == SLDM_REFINE_OFF);
   cudaStream_t s = (cudaStream_t)stream;
-  ensure_ws(op, m);
+  const int W = sldm_op::WR;
+  ensure_ws(op, m, std::min<int>(nrhs, W));
   const size_t vb = size_t(op->N) * sizeof(double2);
   int iters = 0;
   double worst = 0;
-  for (int r = 0; r < nrhs; ++r) {
-    const char* br = (const char*)b + r * vb;
-    char* xr = (char*)x + r * vb;
+  for (int r0 = 0; r0 < nrhs; r0 += W) {
+    const int nr = std::min(W, nrhs - r0);
+    const char* br = (const char*)b + r0 * vb;
+    char* xr = (char*)x + r0 * vb;
     cudaMemcpyKind k_in = where == SLDM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    SLDM_CUDA(cudaMemcpyAsync(op->wb.p, br, vb, k_in, s));
-    if (x0) SLDM_CUDA(cudaMemcpyAsync(op->wx.p, xr, vb, k_in, s));
-    else SLDM_CUDA(cudaMemsetAsync(op->wx.p, 0, vb, s));
-    double rel = 0;
-    gmres_one(op, use_p, refine, m, tol, maxit, iters, rel, s);
-    worst = std::max(worst, rel);
+    SLDM_CUDA(cudaMemcpyAsync(op->wb.p, br, nr * vb, k_in, s));
+    if (x0) SLDM_CUDA(cudaMemcpyAsync(op->wx.p, xr, nr * vb, k_in, s));
+    else SLDM_CUDA(cudaMemsetAsync(op->wx.p, 0, nr * vb, s));
+    double rel[sldm_op::WR];
+    gmres_block(op, use_p, refine, m, tol, maxit, nr, iters, rel, s);
+    for (int r = 0; r < nr; ++r) worst = std::max(worst, rel[r]);
     cudaMemcpyKind k_out = where == SLDM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-    SLDM_CUDA(cudaMemcpyAsync(xr, op->wx.p, vb, k_out, s));
+    SLDM_CUDA(cudaMemcpyAsync(xr, op->wx.p, nr * vb, k_out, s));
   }
   SLDM_CUDA(cudaStreamSynchronize(s));
   if (info) {
