@@ -46,14 +46,16 @@ struct sldm_op {
   std::vector<sldm::ObjInfo> obj;
   sldm::DBuf<double> ix_val;
   // structured product: work vectors for up to WR right-hand sides per pass
-  static constexpr int WR = 8;
+  static constexpr int WR = sldm::MAX_NRHS;
   sldm::DBuf<char> wj, we, wu, wt1, wt2, wa, wc, wbc, wbu, wz1, wz2, ww1, ww2, ww3;
   sldm::DBuf<sldm::GemvJob> jobs1, jobs2;
   sldm::DBuf<int64_t> rs1, rs2;
+  sldm::DBuf<int2> tl1, tl2;
   sldm::GemvPlan plan1, plan2;
   // complex64 operator applied with complex128 vectors (FP64 residuals of iterative refinement)
   sldm::DBuf<sldm::GemvJob> jobs1d, jobs2d;
   sldm::DBuf<int64_t> rs1d, rs2d;
+  sldm::DBuf<int2> tl1d, tl2d;
   sldm::GemvPlan plan1d, plan2d;
   // layered background (external problem with the multilayer kernel)
   bool layered = false;
@@ -75,14 +77,14 @@ namespace sldm {
 
 static int64_t op_bytes(const sldm_op* op) {
   return int64_t(op->LAm.bytes() + op->LPm.bytes() + op->loc.bytes() + op->ix_val.bytes() + op->V.bytes() +
-                 op->pc.sinv.bytes() + op->pc.lam.bytes() + op->pc.pdiag.bytes());
+                 op->pc.sinv.bytes() + op->pc.sinv32.bytes() + op->pc.lam.bytes() + op->pc.pdiag.bytes());
 }
 
 // GEMV plans of the structured product with matrix entries of es_m bytes and
 // vector entries of es_v bytes (the work vectors hold complex128, so both the
 // operator's precision and FP64 fit).
-static void make_plans(sldm_op* op, size_t es_m, size_t es_v, DBuf<GemvJob>& dj1, DBuf<int64_t>& drs1, GemvPlan& p1,
-                       DBuf<GemvJob>& dj2, DBuf<int64_t>& drs2, GemvPlan& p2) {
+static void make_plans(sldm_op* op, size_t es_m, size_t es_v, DBuf<GemvJob>& dj1, DBuf<int64_t>& drs1, DBuf<int2>& dt1,
+                       GemvPlan& p1, DBuf<GemvJob>& dj2, DBuf<int64_t>& drs2, DBuf<int2>& dt2, GemvPlan& p2) {
   const int64_t ne = op->ne, nt = op->nt, nq = op->nq;
   auto P = [&](DBuf<char>& b, int64_t off) { return (void*)(b.p + off * es_v); };
   const char* loc = op->loc.p;
@@ -99,22 +101,28 @@ static void make_plans(sldm_op* op, size_t es_m, size_t es_v, DBuf<GemvJob>& dj1
     j2.push_back({L(o.oK), o.ne, o.ne, o.ne, P(op->we, o.e0), ne, P(op->ww2, o.e0), ne, 1, 0, 0, 0});
     j2.push_back({L(o.oLP), o.nt, o.nt, o.nt, P(op->wbu, o.t0), nt, P(op->ww3, o.t0), nt, 1, 0, 0, 0});
   }
-  auto mk = [&](std::vector<GemvJob>& j, DBuf<GemvJob>& dj, DBuf<int64_t>& drs, GemvPlan& plan) {
+  auto mk = [&](std::vector<GemvJob>& j, DBuf<GemvJob>& dj, DBuf<int64_t>& drs, DBuf<int2>& dt, GemvPlan& plan) {
     std::vector<int64_t> rs(j.size());
+    std::vector<int2> tiles;
     int64_t acc = 0;
     for (size_t i = 0; i < j.size(); ++i) {
       rs[i] = acc;
       acc += j[i].m;
+      for (int r0 = 0; r0 < j[i].m; r0 += gemv_tile_rows(es_v)) tiles.push_back(make_int2(int(i), r0));
     }
     dj.upload(j);
     drs.upload(rs);
+    dt.upload(tiles);
     plan.jobs = dj.p;
     plan.rowstart = drs.p;
     plan.njobs = int(j.size());
     plan.total_rows = acc;
+    plan.tiles = dt.p;
+    plan.ntiles = int(tiles.size());
+    plan.tile_rows = gemv_tile_rows(es_v);
   };
-  mk(j1, dj1, drs1, p1);
-  mk(j2, dj2, drs2, p2);
+  mk(j1, dj1, drs1, dt1, p1);
+  mk(j2, dj2, drs2, dt2, p2);
   p1.name = "gemv_y";     // Y11, Y21 (per object)
   p2.name = "gemv_main";  // L^A_m, L^phi_m and the internal blocks
 }
@@ -130,9 +138,10 @@ static void build_plans(sldm_op* op) {
   op->wbc.alloc(nt * WR * ev); op->wbu.alloc(nt * WR * ev);
   op->wz1.alloc(ne * WR * ev); op->wz2.alloc(nt * WR * ev);
   op->ww1.alloc(ne * WR * ev); op->ww2.alloc(ne * WR * ev); op->ww3.alloc(nt * WR * ev);
-  make_plans(op, sizeof(C), sizeof(C), op->jobs1, op->rs1, op->plan1, op->jobs2, op->rs2, op->plan2);
+  make_plans(op, sizeof(C), sizeof(C), op->jobs1, op->rs1, op->tl1, op->plan1, op->jobs2, op->rs2, op->tl2, op->plan2);
   if (sizeof(C) == sizeof(float2)) {
-    make_plans(op, sizeof(C), sizeof(double2), op->jobs1d, op->rs1d, op->plan1d, op->jobs2d, op->rs2d, op->plan2d);
+    make_plans(op, sizeof(C), sizeof(double2), op->jobs1d, op->rs1d, op->tl1d, op->plan1d, op->jobs2d, op->rs2d, op->tl2d,
+               op->plan2d);
     op->plan1d.name = "gemv_y_f64acc";
     op->plan2d.name = "gemv_main_f64acc";
   }
@@ -444,12 +453,13 @@ static double dnorm(sldm_op* op, const double2* v, cudaStream_t s) {
 // cycle stops once it has reduced that residual by REFINE_CYCLE: the cycles are
 // the correction solves of iterative refinement, in the operator's precision.
 constexpr double REFINE_CYCLE = 1e-5;
+template <class CB>
 static void gmres_block(sldm_op* op, bool use_p, bool refine, int m, double tol, int maxit, int nr, int& iters,
                         double* relres, cudaStream_t s) {
   const int64_t N = op->N, ne = op->ne;
   const double l = op->mesh->h.ell;
   auto col = [&](DBuf<double2>& b, int r) { return b.p + int64_t(r) * N; };
-  auto Vr = [&](int r) { return op->V.p + int64_t(r) * N * (m + 1); };
+  auto Vr = [&](int r) { return reinterpret_cast<CB*>(op->V.p) + int64_t(r) * N * (m + 1); };
   auto dhr = [&](int r) { return op->dh.p + int64_t(r) * 2 * (m + 2); };
   std::vector<double> bnorm(nr), beta(nr);
   for (int r = 0; r < nr; ++r) {
@@ -480,7 +490,7 @@ static void gmres_block(sldm_op* op, bool use_p, bool refine, int m, double tol,
     }
     if (act.empty()) break;
     for (int r : act) {
-      vaxpby(N, 1.0 / beta[r], col(op->wr, r), 0.0, Vr(r), s);
+      vaxpby<double2, CB>(N, 1.0 / beta[r], col(op->wr, r), 0.0, Vr(r), s);
       std::fill(g[r].begin(), g[r].end(), cplx(0));
       g[r][0] = beta[r];
       kused[r] = 0;
@@ -494,25 +504,25 @@ static void gmres_block(sldm_op* op, bool use_p, bool refine, int m, double tol,
       const int na = int(on.size());
       // the products of this step, together: w_r = Dr Z P^-1 Dr^-1 v_r (or Dr Z Dc v_r)
       for (int j = 0; j < na; ++j) {
-        const double2* v = Vr(on[j]) + int64_t(k) * N;
-        if (use_p) {
-          vscale3(N, ne, 1.0, 1.0, 1.0 / l, v, col(op->wtmp2, j), s);
-          prec_apply(op->pc, op->mesh, col(op->wtmp2, j), col(op->wtmp, j), s);
-        } else {
-          vscale3(N, ne, 1.0 / l, 1.0, l, v, col(op->wtmp, j), s);
-        }
+        const CB* v = Vr(on[j]) + int64_t(k) * N;
+        if (use_p) vscale3<CB, double2>(N, ne, 1.0, 1.0, 1.0 / l, v, col(op->wtmp2, j), s);
+        else vscale3<CB, double2>(N, ne, 1.0 / l, 1.0, l, v, col(op->wtmp, j), s);
       }
+      if (use_p) prec_apply(op->pc, op->mesh, op->wtmp2.p, op->wtmp.p, N, na, s);
       apply_any(op, op->wtmp.p, op->wz.p, na, s);
-      for (int j = 0; j < na; ++j) {
-        const int r = on[j];
-        double2* w = Vr(r) + int64_t(k + 1) * N;
-        vscale3(N, ne, 1.0, 1.0, l, col(op->wz, j), w, s);
-        // classical Gram-Schmidt, twice
-        vdots(Vr(r), N, k + 1, w, N, dhr(r), s);
-        vmul(Vr(r), N, k + 1, dhr(r), -1.0, w, N, s);
-        vdots(Vr(r), N, k + 1, w, N, dhr(r) + (m + 2), s);
-        vmul(Vr(r), N, k + 1, dhr(r) + (m + 2), -1.0, w, N, s);
-        vnorm2(w, N, op->dnorm.p + j, s);
+      {
+        ScopedTimer tgs("gram_schmidt", s);
+        for (int j = 0; j < na; ++j) {
+          const int r = on[j];
+          CB* w = Vr(r) + int64_t(k + 1) * N;
+          vscale3<double2, CB>(N, ne, 1.0, 1.0, l, col(op->wz, j), w, s);
+          // classical Gram-Schmidt, twice
+          vdots<CB>(Vr(r), N, k + 1, w, N, dhr(r), s);
+          vmul<CB, CB>(Vr(r), N, k + 1, dhr(r), -1.0, w, N, s);
+          vdots<CB>(Vr(r), N, k + 1, w, N, dhr(r) + (m + 2), s);
+          vmul<CB, CB>(Vr(r), N, k + 1, dhr(r) + (m + 2), -1.0, w, N, s);
+          vnorm2<CB>(w, N, op->dnorm.p + j, s);
+        }
       }
       SLDM_CUDA(cudaMemcpyAsync(hh.data(), op->dh.p, size_t(nr) * 2 * (m + 2) * sizeof(double2), cudaMemcpyDeviceToHost, s));
       SLDM_CUDA(cudaMemcpyAsync(hn.data(), op->dnorm.p, size_t(na) * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -524,7 +534,7 @@ static void gmres_block(sldm_op* op, bool use_p, bool refine, int m, double tol,
         std::vector<cplx>& Hr = H[r];
         for (int i = 0; i <= k; ++i) Hr[size_t(i) * m + k] = cplx(hr[i].x, hr[i].y) + cplx(hr[(m + 2) + i].x, hr[(m + 2) + i].y);
         Hr[size_t(k + 1) * m + k] = h1;
-        if (h1 > 0) vaxpby(N, 1.0 / h1, Vr(r) + int64_t(k + 1) * N, 0.0, Vr(r) + int64_t(k + 1) * N, s);
+        if (h1 > 0) vaxpby<CB, CB>(N, 1.0 / h1, Vr(r) + int64_t(k + 1) * N, 0.0, Vr(r) + int64_t(k + 1) * N, s);
         for (int i = 0; i < k; ++i) {  // previous rotations
           cplx a = Hr[size_t(i) * m + k], b = Hr[size_t(i + 1) * m + k];
           Hr[size_t(i) * m + k] = cs[r][i] * a + sn[r][i] * b;
@@ -561,10 +571,10 @@ static void gmres_block(sldm_op* op, bool use_p, bool refine, int m, double tol,
       }
       SLDM_CUDA(cudaMemcpyAsync(dhr(r), y.data(), ku * sizeof(double2), cudaMemcpyHostToDevice, s));
       SLDM_CUDA(cudaMemsetAsync(col(op->wacc, r), 0, N * sizeof(double2), s));
-      vmul(Vr(r), N, ku, dhr(r), 1.0, col(op->wacc, r), N, s);
+      vmul<CB, double2>(Vr(r), N, ku, dhr(r), 1.0, col(op->wacc, r), N, s);
       if (use_p) {
         vscale3(N, ne, 1.0, 1.0, 1.0 / l, col(op->wacc, r), col(op->wtmp2, 0), s);
-        prec_apply(op->pc, op->mesh, col(op->wtmp2, 0), col(op->wtmp, 0), s);
+        prec_apply(op->pc, op->mesh, col(op->wtmp2, 0), col(op->wtmp, 0), N, 1, s);
       } else {
         vscale3(N, ne, 1.0 / l, 1.0, l, col(op->wacc, r), col(op->wtmp, 0), s);
       }
@@ -781,6 +791,7 @@ int sldm_assemble(const sldm_mesh* m, const sldm_stack* st, const sldm_material*
     op->mu_b = L.mu_r;
     op->kb = op->k0 * std::sqrt(op->eps_b * op->mu_b);
     cudaStream_t s = opts ? (cudaStream_t)opts->stream : 0;
+    ScopedTimer tm("assemble", s);
     if (op->prec == SLDM_PREC_F32) assemble_impl<float>(op, per_obj, s);
     else assemble_impl<double>(op, per_obj, s);
   } catch (...) {
@@ -969,7 +980,14 @@ int sldm_solve(const sldm_op* op_, const void* b, void* x, int32_t nrhs, const s
     if (x0) SLDM_CUDA(cudaMemcpyAsync(op->wx.p, xr, nr * vb, k_in, s));
     else SLDM_CUDA(cudaMemsetAsync(op->wx.p, 0, nr * vb, s));
     double rel[sldm_op::WR];
-    gmres_block(op, use_p, refine, m, tol, maxit, nr, iters, rel, s);
+    {
+      ScopedTimer tm("gmres", s);
+      // complex64 operators keep the Krylov basis in complex64 and orthogonalise
+      // in FP32 (the cycles are correction solves; the residual that decides
+      // convergence is formed in FP64 at each restart when refining)
+      if (op->prec == SLDM_PREC_F32) gmres_block<float2>(op, use_p, refine, m, tol, maxit, nr, iters, rel, s);
+      else gmres_block<double2>(op, use_p, refine, m, tol, maxit, nr, iters, rel, s);
+    }
     for (int r = 0; r < nr; ++r) worst = std::max(worst, rel[r]);
     cudaMemcpyKind k_out = where == SLDM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     SLDM_CUDA(cudaMemcpyAsync(xr, op->wx.p, nr * vb, k_out, s));
@@ -994,6 +1012,7 @@ int sldm_farfield(const sldm_op* op_, const void* x, int32_t where, const double
   SLDM_REQUIRE(!op_->layered, SLDM_ENOTSUP, "farfield: free-space far field only (homogeneous background)");
   sldm_op* op = const_cast<sldm_op*>(op_);
   cudaStream_t s = 0;
+  ScopedTimer tm("farfield", s);
   DBuf<double2> dx, jd;
   dx.alloc(op->N);
   jd.alloc(op->ne);

@@ -7,6 +7,7 @@
 //  - the sparse/elementwise glue of the structured product Z x (Eq. finalsystem);
 //  - FP64 vector kernels for GMRES (Arnoldi by classical Gram-Schmidt twice).
 #include <algorithm>
+#include <atomic>
 #include <type_traits>
 
 #include "dense.h"
@@ -606,13 +607,196 @@ __global__ void __launch_bounds__(256, NR == 1 ? 6 : 1) gemv_jobs_kernel(const G
   }
 }
 
+// ---------------------------------------------------------------- several right-hand sides
+// With NR right-hand sides every matrix entry feeds 4 NR FMAs, so at NR = 8 a
+// complex64 pass needs 32 FP32 FMAs per 8 bytes streamed: the one-row-per-warp
+// kernel above, which re-reads x from L1 for every row, is load-issue bound
+// there.  This kernel gives each warp RW rows and each CTA 8 RW consecutive
+// rows of one job, stages x once per CTA in shared memory and streams A
+// through a 4-stage cp.async pipeline (each lane copies, then reads back, its
+// own entries; the x chunk is shared, so a CTA barrier guards each stage).
+// Columns go in chunks of 64, two per lane; entries outside the block or
+// beyond nrhs are zero-filled by the copy, so the inner loop has no branches.
+// The partial sums are reduced by a transposing butterfly that halves the
+// values held per lane at every step (about 2K shuffles for K values rather
+// than 5K) and leaves each lane with the sums it writes.
+template <class CM, class CV>
+struct GemvTile {
+  static constexpr int RW = sizeof(CV) == 8 ? 4 : 2;  // rows per warp
+  static constexpr int CW = 64;                        // columns per chunk
+  static constexpr int ST = 4;                         // pipeline stages
+  static constexpr int ROWS = 8 * RW;                  // rows per CTA
+  static constexpr size_t a_stage = size_t(8) * RW * CW * sizeof(CM);
+  template <int NR>
+  static constexpr size_t smem() {
+    return size_t(ST) * (a_stage + size_t(NR) * CW * sizeof(CV));
+  }
+};
+static_assert(GemvTile<float2, float2>::ROWS == 32 && GemvTile<double2, double2>::ROWS == 16, "tile rows");
+
+template <int N>
+__device__ __forceinline__ void cp_async(void* dst, const void* src, bool valid) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+  const int n = valid ? N : 0;  // 0: fill the destination with zeros, read nothing
+  if constexpr (N == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Sum v over the warp, C values per lane left, next exchange distance O.  When
+// done lane l holds max(1, K/32) sums: value j is the total of index
+// j + max(1, K/32) (l >> S), S = log2(32/K) for K < 32 and 0 otherwise.
+template <int C, int O, class R, int K>
+__device__ __forceinline__ void warp_tsum(R (&v)[K], int lane) {
+  if constexpr (O > 0) {
+    if constexpr (C >= 2) {
+      const bool up = lane & O;
+#pragma unroll
+      for (int i = 0; i < C / 2; ++i) {
+        const R send = up ? v[i] : v[i + C / 2];
+        const R keep = up ? v[i + C / 2] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, O);
+      }
+      warp_tsum<C / 2, O / 2>(v, lane);
+    } else {
+      v[0] += __shfl_xor_sync(0xffffffffu, v[0], O);
+      warp_tsum<C, O / 2>(v, lane);
+    }
+  }
+}
+
+template <class CM, class CV, int NR>
+__global__ void __launch_bounds__(256, 2) gemv_tile_kernel(const GemvJob* __restrict__ jobs, const int2* __restrict__ tiles,
+                                                          int nrhs) {
+  typedef GemvTile<CM, CV> T;
+  typedef typename CT<CV>::R R;
+  constexpr int RW = T::RW, CW = T::CW, ST = T::ST;
+  extern __shared__ __align__(16) unsigned char gsm[];
+  CM* As = reinterpret_cast<CM*>(gsm);                     // [ST][8 warps][RW][2][32]
+  CV* Xs = reinterpret_cast<CV*>(gsm + ST * T::a_stage);   // [ST][NR][CW]
+  const int2 t = tiles[blockIdx.x];
+  const GemvJob J = jobs[t.x];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row0 = t.y + warp * RW;
+  const CM* __restrict__ A = reinterpret_cast<const CM*>(J.A);
+  const CV* __restrict__ x = reinterpret_cast<const CV*>(J.x);
+  const int nch = (J.n + CW - 1) / CW;
+  auto issue = [&](int ch) {
+    if (ch < nch) {
+      const int st = ch % ST;
+      CM* a = As + (st * 8 + warp) * RW * CW;
+#pragma unroll
+      for (int i = 0; i < RW; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          const int col = ch * CW + j * 32 + lane, row = row0 + i;
+          const bool ok = row < J.m && col < J.n;
+          cp_async<sizeof(CM)>(a + (i * 2 + j) * 32 + lane, ok ? A + int64_t(row) * J.lda + col : A, ok);
+        }
+      CV* xs = Xs + st * NR * CW;
+#pragma unroll
+      for (int e0 = 0; e0 < NR * CW; e0 += 256) {
+        const int e = e0 + threadIdx.x;
+        if (NR * CW % 256 == 0 || e < NR * CW) {
+          const int r = e / CW, col = ch * CW + e % CW;
+          const bool ok = r < nrhs && col < J.n;
+          cp_async<sizeof(CV)>(xs + e, ok ? x + int64_t(r) * J.ldx + col : x, ok);
+        }
+      }
+    }
+    cp_commit();  // possibly empty: keeps one group per chunk
+  };
+#pragma unroll
+  for (int c = 0; c < ST - 1; ++c) issue(c);
+  R acc[RW * NR * 2];
+#pragma unroll
+  for (int i = 0; i < RW * NR * 2; ++i) acc[i] = R(0);
+  for (int ch = 0; ch < nch; ++ch) {
+    cp_wait<ST - 2>();  // this thread's copies of chunk ch have landed
+    __syncthreads();    // everyone's have, and chunk ch - 1 is consumed
+    issue(ch + ST - 1); // into the slot of chunk ch - 1
+    const int st = ch % ST;
+    const CM* a = As + (st * 8 + warp) * RW * CW;
+    const CV* xs = Xs + st * NR * CW;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      CM av[RW];
+#pragma unroll
+      for (int i = 0; i < RW; ++i) av[i] = a[(i * 2 + j) * 32 + lane];
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        const CV xv = xs[r * CW + j * 32 + lane];
+#pragma unroll
+        for (int i = 0; i < RW; ++i)
+          cfma(acc[(i * NR + r) * 2], acc[(i * NR + r) * 2 + 1], R(av[i].x), R(av[i].y), R(xv.x), R(xv.y));
+      }
+    }
+  }
+  cp_wait<0>();
+  constexpr int K = RW * NR * 2;
+  constexpr int V = K >= 32 ? K / 32 : 1;
+  constexpr int S = K >= 32 ? 0 : (K == 16 ? 1 : K == 8 ? 2 : K == 4 ? 3 : 4);
+  warp_tsum<K, 16>(acc, lane);
+  CV* y = reinterpret_cast<CV*>(J.y);
+  auto put = [&](int p, R re, R im) {  // p = row-in-warp * NR + rhs
+    const int i = p / NR, r = p % NR, row = row0 + i;
+    if (row < J.m && r < nrhs) {
+      R vr = R(J.ar) * re - R(J.ai) * im;
+      R vi = R(J.ar) * im + R(J.ai) * re;
+      CV* yy = y + int64_t(r) * J.ldy + row;
+      if (J.beta) {
+        vr += yy->x;
+        vi += yy->y;
+      }
+      yy->x = vr;
+      yy->y = vi;
+    }
+  };
+  if constexpr (V >= 2) {
+#pragma unroll
+    for (int q = 0; q < V / 2; ++q) put((V / 2) * lane + q, acc[2 * q], acc[2 * q + 1]);
+  } else {
+    const R other = __shfl_xor_sync(0xffffffffu, acc[0], 1 << S);
+    const int idx = lane >> S;
+    if ((lane & ((1 << S) - 1)) == 0 && (idx & 1) == 0) put(idx >> 1, acc[0], other);
+  }
+}
+
+template <class CM, class CV, int NR>
+static void launch_tile(const GemvPlan& plan, int nrhs, cudaStream_t s) {
+  typedef GemvTile<CM, CV> T;
+  constexpr size_t smem = T::template smem<NR>();
+  static std::atomic<uint64_t> done{0};  // devices whose attribute is set
+  int dev = 0;
+  SLDM_CUDA(cudaGetDevice(&dev));
+  const uint64_t bit = uint64_t(1) << (dev & 63);
+  if (!(done.load() & bit)) {
+    SLDM_CUDA(cudaFuncSetAttribute(gemv_tile_kernel<CM, CV, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    done.fetch_or(bit);
+  }
+  gemv_tile_kernel<CM, CV, NR><<<unsigned(plan.ntiles), 256, smem, s>>>(plan.jobs, plan.tiles, nrhs);
+  count_launch();
+}
+
 template <class CM, class CV>
 void gemv_jobs_mixed(const GemvPlan& plan, int nrhs, cudaStream_t s) {
   if (plan.njobs == 0) return;
   const int64_t threads = plan.total_rows * 32;
   const unsigned blocks = unsigned((threads + 255) / 256);
   ScopedTimer tm(plan.name, s);
-  if (nrhs <= 1)
+  if (nrhs >= 2 && plan.tiles != nullptr) {
+    if (plan.ntiles == 0) return;
+    SLDM_REQUIRE((plan.tile_rows == GemvTile<CM, CV>::ROWS), SLDM_EINVAL, "GEMV plan tiled for another vector type");
+    if (nrhs <= 2) launch_tile<CM, CV, 2>(plan, nrhs, s);
+    else if (nrhs <= 4) launch_tile<CM, CV, 4>(plan, nrhs, s);
+    else launch_tile<CM, CV, 8>(plan, nrhs, s);
+  } else if (nrhs <= 1)
     gemv_jobs_kernel<CM, CV, 1><<<blocks, 256, 0, s>>>(plan.jobs, plan.rowstart, plan.njobs, plan.total_rows, nrhs), ::sldm::count_launch();
   else if (nrhs <= 4)
     gemv_jobs_kernel<CM, CV, 4><<<blocks, 256, 0, s>>>(plan.jobs, plan.rowstart, plan.njobs, plan.total_rows, nrhs), ::sldm::count_launch();
@@ -781,76 +965,108 @@ void apply_glue_combine(const sldm_mesh* m, const ApplyDims& D, double k0, const
   SLDM_CUDA(cudaGetLastError());
 }
 
-// ---------------------------------------------------------------- FP64 vector kernels for GMRES
+// ---------------------------------------------------------------- vector kernels for GMRES
+// Templated on the storage of the Krylov basis and of the vector being
+// orthogonalised: complex128 (FP64 arithmetic) for complex128 operators,
+// complex64 (FP32 arithmetic, FP64 sums across threads) for complex64 ones.
+// On this part FP64 issues at 1/64 of the FP32 rate, so an FP64 dot product
+// or update (4 FMAs per complex entry) tops out near 2.5 TB/s of complex128
+// entries, below HBM; in complex64 the same kernels are HBM-bound.
+template <class C>
+__device__ __forceinline__ C cmake(double x, double y);
+template <>
+__device__ __forceinline__ float2 cmake<float2>(double x, double y) { return make_float2(float(x), float(y)); }
+template <>
+__device__ __forceinline__ double2 cmake<double2>(double x, double y) { return make_double2(x, y); }
+
 // h[i] = V[:, i]^H w  for i < k.  Grid (ceil(k / 8), row chunks): warp j of a CTA
 // takes column 8 blockIdx.x + j over the CTA's chunk of DOTS_CHUNK rows, two
-// 16-byte loads of V and w per lane in flight, and adds its sum to h[i] with
+// loads of V and w per lane in flight, and adds its sum to h[i] with FP64
 // atomics (h is cleared first).  V streams once, at full width of the grid.
 constexpr int DOTS_CHUNK = 2048;
-__global__ void __launch_bounds__(256) dots_kernel(const double2* __restrict__ V, int64_t ldv, int k,
-                                                   const double2* __restrict__ w, int64_t n, double2* h) {
+template <class CB>
+__global__ void __launch_bounds__(256) dots_kernel(const CB* __restrict__ V, int64_t ldv, int k, const CB* __restrict__ w,
+                                                   int64_t n, double2* h) {
+  typedef typename CT<CB>::R R;
   const int lane = threadIdx.x & 31;
   const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
   if (i >= k) return;
   const int64_t r0 = int64_t(blockIdx.y) * DOTS_CHUNK;
   const int64_t r1 = r0 + DOTS_CHUNK < n ? r0 + DOTS_CHUNK : n;
-  const double2* v = V + int64_t(i) * ldv;
-  double sr = 0, si = 0, tr = 0, ti = 0;
+  const CB* v = V + int64_t(i) * ldv;
+  R sr = 0, si = 0, tr = 0, ti = 0;
   int64_t t = r0 + lane;
   for (; t + 32 < r1; t += 64) {
-    const double2 a0 = v[t], b0 = w[t], a1 = v[t + 32], b1 = w[t + 32];
+    const CB a0 = v[t], b0 = w[t], a1 = v[t + 32], b1 = w[t + 32];
     cfma(sr, si, a0.x, -a0.y, b0.x, b0.y);  // conj(a) b
     cfma(tr, ti, a1.x, -a1.y, b1.x, b1.y);
   }
   if (t < r1) {
-    const double2 a0 = v[t], b0 = w[t];
+    const CB a0 = v[t], b0 = w[t];
     cfma(sr, si, a0.x, -a0.y, b0.x, b0.y);
   }
-  sr += tr;
-  si += ti;
+  double dr = double(sr) + double(tr), di = double(si) + double(ti);
   for (int o = 16; o > 0; o >>= 1) {
-    sr += __shfl_xor_sync(0xffffffffu, sr, o);
-    si += __shfl_xor_sync(0xffffffffu, si, o);
+    dr += __shfl_xor_sync(0xffffffffu, dr, o);
+    di += __shfl_xor_sync(0xffffffffu, di, o);
   }
   if (lane == 0) {
-    atomicAdd(&h[i].x, sr);
-    atomicAdd(&h[i].y, si);
+    atomicAdd(&h[i].x, dr);
+    atomicAdd(&h[i].y, di);
   }
 }
 
-// w += sign * V[:, :k] h.  A CTA owns 32 rows; its 8 warps take every 8th
-// Krylov column, and the partial sums meet in shared memory.
-__global__ void __launch_bounds__(256) vmul_kernel(const double2* __restrict__ V, int64_t ldv, int k,
-                                                   const double2* __restrict__ h, double sign, double2* w, int64_t n) {
-  __shared__ double2 part[8][32];
+// w += sign * V[:, :k] h (arithmetic in w's precision).  A CTA owns 32 rows;
+// its 8 warps take every 8th Krylov column, four columns in flight, and the
+// partial sums meet in shared memory.
+template <class CB, class CW>
+__global__ void __launch_bounds__(256) vmul_kernel(const CB* __restrict__ V, int64_t ldv, int k,
+                                                   const double2* __restrict__ h, double sign, CW* w, int64_t n) {
+  typedef typename CT<CW>::R R;
+  __shared__ R part[8][32][2];
   const int lane = threadIdx.x & 31, slice = threadIdx.x >> 5;
   const int64_t t = int64_t(blockIdx.x) * 32 + lane;
-  double sr = 0, si = 0;
+  R sr = 0, si = 0;
   if (t < n) {
-    for (int i = slice; i < k; i += 8) {
-      const double2 v = V[int64_t(i) * ldv + t];
+    int i = slice;
+    for (; i + 24 < k; i += 32) {
+      CB v[4];
+      double2 c[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        v[u] = V[int64_t(i + 8 * u) * ldv + t];
+        c[u] = h[i + 8 * u];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) cfma(sr, si, R(v[u].x), R(v[u].y), R(c[u].x), R(c[u].y));
+    }
+    for (; i < k; i += 8) {
+      const CB v = V[int64_t(i) * ldv + t];
       const double2 c = h[i];
-      cfma(sr, si, v.x, v.y, c.x, c.y);
+      cfma(sr, si, R(v.x), R(v.y), R(c.x), R(c.y));
     }
   }
-  part[slice][lane] = make_double2(sr, si);
+  part[slice][lane][0] = sr;
+  part[slice][lane][1] = si;
   __syncthreads();
   if (slice == 0 && t < n) {
-    double ar = 0, ai = 0;
-    for (int s = 0; s < 8; ++s) {
-      ar += part[s][lane].x;
-      ai += part[s][lane].y;
+    R ar = 0, ai = 0;
+    for (int q = 0; q < 8; ++q) {
+      ar += part[q][lane][0];
+      ai += part[q][lane][1];
     }
-    const double2 o = w[t];
-    w[t] = make_double2(o.x + sign * ar, o.y + sign * ai);
+    const CW o = w[t];
+    w[t].x = o.x + R(sign) * ar;
+    w[t].y = o.y + R(sign) * ai;
   }
 }
 
-__global__ void norm2_kernel(const double2* __restrict__ w, int64_t n, double* out) {
+template <class C>
+__global__ void norm2_kernel(const C* __restrict__ w, int64_t n, double* out) {
   double s = 0;
   for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < n; t += int64_t(gridDim.x) * blockDim.x) {
-    double2 a = w[t];
-    s += a.x * a.x + a.y * a.y;
+    const C a = w[t];
+    s += double(a.x) * double(a.x) + double(a.y) * double(a.y);
   }
   __shared__ double r[256];
   r[threadIdx.x] = s;
@@ -862,48 +1078,74 @@ __global__ void norm2_kernel(const double2* __restrict__ w, int64_t n, double* o
   if (threadIdx.x == 0) atomicAdd(out, r[0]);
 }
 
-// y = alpha * x + beta * y (complex128, real alpha/beta)
-__global__ void axpby_kernel(int64_t n, double alpha, const double2* __restrict__ x, double beta, double2* y) {
+// y = alpha * x + beta * y (real alpha, beta; FP64 arithmetic, y stored in its type;
+// beta = 0 ignores the old y)
+template <class CX, class CY>
+__global__ void axpby_kernel(int64_t n, double alpha, const CX* __restrict__ x, double beta, CY* y) {
   int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (t >= n) return;
-  double2 a = x[t], b = y[t];
-  y[t] = make_double2(alpha * a.x + beta * b.x, alpha * a.y + beta * b.y);
+  const CX a = x[t];
+  double vr = alpha * double(a.x), vi = alpha * double(a.y);
+  if (beta != 0.0) {
+    const CY b = y[t];
+    vr += beta * double(b.x);
+    vi += beta * double(b.y);
+  }
+  y[t] = cmake<CY>(vr, vi);
 }
 
 // y[i] = s_b x[i] with s_b = s1 on [0, ne), s2 on [ne, 2 ne), s3 on [2 ne, n) (in place allowed)
-__global__ void vscale3_kernel(int64_t n, int64_t ne, double s1, double s2, double s3, const double2* __restrict__ x, double2* y) {
+template <class CX, class CY>
+__global__ void vscale3_kernel(int64_t n, int64_t ne, double s1, double s2, double s3, const CX* __restrict__ x, CY* y) {
   int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (t >= n) return;
   const double s = t < ne ? s1 : (t < 2 * ne ? s2 : s3);
-  const double2 a = x[t];
-  y[t] = make_double2(s * a.x, s * a.y);
+  const CX a = x[t];
+  y[t] = cmake<CY>(s * double(a.x), s * double(a.y));
 }
 
-void vscale3(int64_t n, int64_t ne, double s1, double s2, double s3, const double2* x, double2* y, cudaStream_t s) {
-  vscale3_kernel<<<unsigned((n + 255) / 256), 256, 0, s>>>(n, ne, s1, s2, s3, x, y), ::sldm::count_launch();
+template <class CX, class CY>
+void vscale3(int64_t n, int64_t ne, double s1, double s2, double s3, const CX* x, CY* y, cudaStream_t s) {
+  vscale3_kernel<CX, CY><<<unsigned((n + 255) / 256), 256, 0, s>>>(n, ne, s1, s2, s3, x, y), ::sldm::count_launch();
   SLDM_CUDA(cudaGetLastError());
 }
-
-void vdots(const double2* V, int64_t ldv, int k, const double2* w, int64_t n, double2* h, cudaStream_t s) {
+template <class CB>
+void vdots(const CB* V, int64_t ldv, int k, const CB* w, int64_t n, double2* h, cudaStream_t s) {
   SLDM_CUDA(cudaMemsetAsync(h, 0, size_t(k) * sizeof(double2), s));
-  dots_kernel<<<dim3(unsigned((k + 7) / 8), unsigned((n + DOTS_CHUNK - 1) / DOTS_CHUNK)), 256, 0, s>>>(V, ldv, k, w, n, h),
+  dots_kernel<CB><<<dim3(unsigned((k + 7) / 8), unsigned((n + DOTS_CHUNK - 1) / DOTS_CHUNK)), 256, 0, s>>>(V, ldv, k, w, n, h),
       ::sldm::count_launch();
   SLDM_CUDA(cudaGetLastError());
 }
-void vmul(const double2* V, int64_t ldv, int k, const double2* h, double sign, double2* w, int64_t n, cudaStream_t s) {
-  vmul_kernel<<<unsigned((n + 31) / 32), 256, 0, s>>>(V, ldv, k, h, sign, w, n), ::sldm::count_launch();
+template <class CB, class CW>
+void vmul(const CB* V, int64_t ldv, int k, const double2* h, double sign, CW* w, int64_t n, cudaStream_t s) {
+  vmul_kernel<CB, CW><<<unsigned((n + 31) / 32), 256, 0, s>>>(V, ldv, k, h, sign, w, n), ::sldm::count_launch();
   SLDM_CUDA(cudaGetLastError());
 }
-void vnorm2(const double2* w, int64_t n, double* out, cudaStream_t s) {
+template <class C>
+void vnorm2(const C* w, int64_t n, double* out, cudaStream_t s) {
   SLDM_CUDA(cudaMemsetAsync(out, 0, sizeof(double), s));
   unsigned b = unsigned(std::min<int64_t>((n + 255) / 256, 1024));
-  norm2_kernel<<<b, 256, 0, s>>>(w, n, out), ::sldm::count_launch();
+  norm2_kernel<C><<<b, 256, 0, s>>>(w, n, out), ::sldm::count_launch();
   SLDM_CUDA(cudaGetLastError());
 }
-void vaxpby(int64_t n, double alpha, const double2* x, double beta, double2* y, cudaStream_t s) {
-  axpby_kernel<<<unsigned((n + 255) / 256), 256, 0, s>>>(n, alpha, x, beta, y), ::sldm::count_launch();
+template <class CX, class CY>
+void vaxpby(int64_t n, double alpha, const CX* x, double beta, CY* y, cudaStream_t s) {
+  axpby_kernel<CX, CY><<<unsigned((n + 255) / 256), 256, 0, s>>>(n, alpha, x, beta, y), ::sldm::count_launch();
   SLDM_CUDA(cudaGetLastError());
 }
+#define SLDM_VEC_INST(CX, CY)                                                                                   \
+  template void vscale3<CX, CY>(int64_t, int64_t, double, double, double, const CX*, CY*, cudaStream_t);       \
+  template void vmul<CX, CY>(const CX*, int64_t, int, const double2*, double, CY*, int64_t, cudaStream_t);     \
+  template void vaxpby<CX, CY>(int64_t, double, const CX*, double, CY*, cudaStream_t);
+SLDM_VEC_INST(double2, double2)
+SLDM_VEC_INST(float2, float2)
+SLDM_VEC_INST(float2, double2)
+SLDM_VEC_INST(double2, float2)
+#undef SLDM_VEC_INST
+template void vdots<double2>(const double2*, int64_t, int, const double2*, int64_t, double2*, cudaStream_t);
+template void vdots<float2>(const float2*, int64_t, int, const float2*, int64_t, double2*, cudaStream_t);
+template void vnorm2<double2>(const double2*, int64_t, double*, cudaStream_t);
+template void vnorm2<float2>(const float2*, int64_t, double*, cudaStream_t);
 
 // ---------------------------------------------------------------- conversions
 template <class C>

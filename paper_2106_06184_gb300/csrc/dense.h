@@ -45,7 +45,16 @@ struct GemvPlan {
   int64_t* rowstart = nullptr; // device, exclusive prefix sum of m
   int njobs = 0;
   int64_t total_rows = 0;
+  // tiles of tile_rows rows of one job each (job, first row), device; used
+  // with several right-hand sides (null: the one-row-per-warp kernel throughout)
+  int2* tiles = nullptr;
+  int ntiles = 0;
+  int tile_rows = 0;
 };
+// right-hand sides per pass of the structured product and the preconditioner
+constexpr int MAX_NRHS = 8;
+// rows per tile of the several-right-hand-side kernel for vectors of es_v bytes
+inline int gemv_tile_rows(size_t es_v) { return es_v == 8 ? 32 : 16; }
 template <class C>
 void gemv_jobs(const GemvPlan& plan, int nrhs, cudaStream_t s);
 // complex64 matrix, complex128 vectors, FP64 accumulation
@@ -66,11 +75,18 @@ void apply_glue_combine(const sldm_mesh* m, const ApplyDims& D, double k0, const
                         const void* z2, const void* w1, const void* w2, const void* w3, const void* e, const void* a,
                         const void* c, double2* y, int64_t ldy, int nrhs, cudaStream_t s);
 
-void vdots(const double2* V, int64_t ldv, int k, const double2* w, int64_t n, double2* h, cudaStream_t s);
-void vmul(const double2* V, int64_t ldv, int k, const double2* h, double sign, double2* w, int64_t n, cudaStream_t s);
-void vnorm2(const double2* w, int64_t n, double* out, cudaStream_t s);
-void vaxpby(int64_t n, double alpha, const double2* x, double beta, double2* y, cudaStream_t s);
-void vscale3(int64_t n, int64_t ne, double s1, double s2, double s3, const double2* x, double2* y, cudaStream_t s);
+// complex128 or complex64 storage (instantiated for double2 and float2; mixed
+// pairs for vmul, vaxpby and vscale3)
+template <class CB>
+void vdots(const CB* V, int64_t ldv, int k, const CB* w, int64_t n, double2* h, cudaStream_t s);
+template <class CB, class CW>
+void vmul(const CB* V, int64_t ldv, int k, const double2* h, double sign, CW* w, int64_t n, cudaStream_t s);
+template <class C>
+void vnorm2(const C* w, int64_t n, double* out, cudaStream_t s);
+template <class CX, class CY>
+void vaxpby(int64_t n, double alpha, const CX* x, double beta, CY* y, cudaStream_t s);
+template <class CX, class CY>
+void vscale3(int64_t n, int64_t ne, double s1, double s2, double s3, const CX* x, CY* y, cudaStream_t s);
 
 template <class C>
 void to_c128(const void* src, int64_t n, double2* dst, cudaStream_t s);

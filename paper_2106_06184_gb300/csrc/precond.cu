@@ -100,12 +100,21 @@ __global__ void prec_schur_kernel(const PrecObj O, double k0, const int32_t* __r
   I[int64_t(q) * nq + q2] = make_double2(q == q2 ? 1.0 : 0.0, 0.0);
 }
 
-// t3 = r3 - F D (L11 r1 + L12 r2) (per charge unknown)
+template <class CV>
+__device__ __forceinline__ CV to_cv(double2 v);
+template <>
+__device__ __forceinline__ double2 to_cv<double2>(double2 v) { return v; }
+template <>
+__device__ __forceinline__ float2 to_cv<float2>(double2 v) { return make_float2(float(v.x), float(v.y)); }
+
+// t3 = r3 - F D (L11 r1 + L12 r2) (per charge unknown; column blockIdx.y)
+template <class CV>
 __global__ void prec_apply1_kernel(int ne, int nq, const int32_t* __restrict__ q2t, const int32_t* __restrict__ tri_edge,
                                    const int8_t* __restrict__ tri_sign, const double2* __restrict__ lam,
-                                   const double2* __restrict__ r, double2* t3) {
+                                   const double2* __restrict__ r, int64_t ld, CV* t3) {
   int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= nq) return;
+  r += int64_t(blockIdx.y) * ld;
   const int t = q2t[q];
   double2 acc = r[2 * ne + q];
   for (int i = 0; i < 3; ++i) {
@@ -115,19 +124,24 @@ __global__ void prec_apply1_kernel(int ne, int nq, const int32_t* __restrict__ q
     acc.x -= s * v.x;
     acc.y -= s * v.y;
   }
-  t3[q] = acc;
+  t3[int64_t(blockIdx.y) * nq + q] = to_cv<CV>(acc);
 }
 
-// full charges bx = B x3 per object (the last triangle carries minus the sum), one CTA per object
-__global__ void prec_apply3_kernel(const PrecObj* __restrict__ objs, const double2* __restrict__ x3, double2* bx) {
+// full charges bx = B x3 per object (the last triangle carries minus the sum),
+// one CTA per object and column
+template <class CV>
+__global__ void prec_apply3_kernel(const PrecObj* __restrict__ objs, int nq_all, int nt, const CV* __restrict__ x3,
+                                   double2* bx) {
   const PrecObj O = objs[blockIdx.x];
+  x3 += int64_t(blockIdx.y) * nq_all;
+  bx += int64_t(blockIdx.y) * nt;
   const int nq = O.nt - 1;
   double sr = 0, si = 0;
   for (int q = threadIdx.x; q < nq; q += blockDim.x) {
-    const double2 v = x3[O.q0 + q];
-    bx[O.t0 + q] = v;
-    sr += v.x;
-    si += v.y;
+    const CV v = x3[O.q0 + q];
+    bx[O.t0 + q] = make_double2(double(v.x), double(v.y));
+    sr += double(v.x);
+    si += double(v.y);
   }
   __shared__ double rr[256], ri[256];
   rr[threadIdx.x] = sr;
@@ -143,12 +157,17 @@ __global__ void prec_apply3_kernel(const PrecObj* __restrict__ objs, const doubl
   if (threadIdx.x == 0) bx[O.t0 + O.nt - 1] = make_double2(-rr[0], -ri[0]);
 }
 
-// x1, x2 = Lambda (r1 - P13 x3, r2 - P23 x3); x3 copied into the output
-__global__ void prec_apply45_kernel(int ne, int nq, const int32_t* __restrict__ tplus, const int32_t* __restrict__ tminus,
-                                    const double2* __restrict__ lam, const double2* __restrict__ pdiag,
-                                    const double2* __restrict__ r, const double2* __restrict__ bx,
-                                    const double2* __restrict__ x3, double2* x) {
+// x1, x2 = Lambda (r1 - P13 x3, r2 - P23 x3); x3 copied into the output (column blockIdx.y)
+template <class CV>
+__global__ void prec_apply45_kernel(int ne, int nq, int nt, const int32_t* __restrict__ tplus,
+                                    const int32_t* __restrict__ tminus, const double2* __restrict__ lam,
+                                    const double2* __restrict__ pdiag, const double2* __restrict__ r, int64_t ld,
+                                    const double2* __restrict__ bx, const CV* __restrict__ x3, double2* x) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
+  r += int64_t(blockIdx.y) * ld;
+  x += int64_t(blockIdx.y) * ld;
+  bx += int64_t(blockIdx.y) * nt;
+  x3 += int64_t(blockIdx.y) * nq;
   if (i < ne) {
     const int tp = tplus[i], tm = tminus[i];
     const double2 y1 = c_sub(r[i], c_sub(c_mul(pdiag[2 * tp], bx[tp]), c_mul(pdiag[2 * tm], bx[tm])));
@@ -156,7 +175,12 @@ __global__ void prec_apply45_kernel(int ne, int nq, const int32_t* __restrict__ 
     x[i] = c_add(c_mul(lam[4 * i + 0], y1), c_mul(lam[4 * i + 1], y2));
     x[ne + i] = c_add(c_mul(lam[4 * i + 2], y1), c_mul(lam[4 * i + 3], y2));
   }
-  if (i < nq) x[2 * ne + i] = x3[i];
+  if (i < nq) x[2 * ne + i] = make_double2(double(x3[i].x), double(x3[i].y));
+}
+
+__global__ void to_c64_kernel(int64_t n, const double2* __restrict__ a, float2* b) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    b[i] = make_float2(float(a[i].x), float(a[i].y));
 }
 
 template <class C>
@@ -191,41 +215,76 @@ void prec_setup(Precond& P, const sldm_mesh* m, const std::vector<PrecObj>& objs
   }
   SLDM_CUDA(cudaGetLastError());
   lu_solve_batched(sys, s);  // sinv <- S^-1
-  // GEMV plan: x3_o = S_o^-1 t3_o
-  P.t3.alloc(std::max<int64_t>(h.nt - h.nobj, 1));
-  P.x3.alloc(std::max<int64_t>(h.nt - h.nobj, 1));
-  P.bx.alloc(h.nt);
+  // a complex64 operator takes an FP32 preconditioner: S^-1 (inverted in FP64)
+  // rounded to complex64, applied with FP32 arithmetic
+  P.f32 = sizeof(C) == sizeof(float2);
+  if (P.f32 && tot > 0) {
+    P.sinv32.alloc(tot);
+    to_c64_kernel<<<std::min<int64_t>((tot + 255) / 256, 4096), 256, 0, s>>>(tot, P.sinv.p, P.sinv32.p), ::sldm::count_launch();
+    SLDM_CUDA(cudaGetLastError());
+    SLDM_CUDA(cudaStreamSynchronize(s));
+    P.sinv.release();
+  }
+  // GEMV plan: x3_o = S_o^-1 t3_o, WR columns of nq
+  const size_t ev = P.f32 ? sizeof(float2) : sizeof(double2);
+  P.nq = h.nt - h.nobj;
+  const int64_t nq1 = std::max<int64_t>(P.nq, 1);
+  P.t3.alloc(nq1 * MAX_NRHS);
+  P.x3.alloc(nq1 * MAX_NRHS);
+  P.bx.alloc(h.nt * MAX_NRHS);
   std::vector<GemvJob> jobs;
   std::vector<int64_t> rs;
+  std::vector<int2> tiles;
   int64_t acc = 0;
+  const char* A0 = P.f32 ? (const char*)P.sinv32.p : (const char*)P.sinv.p;
   for (size_t i = 0; i < objs.size(); ++i) {
     const int nq = objs[i].nt - 1;
     if (nq <= 0) continue;
-    jobs.push_back({P.sinv.p + off[i], nq, nq, nq, P.t3.p + objs[i].q0, 0, P.x3.p + objs[i].q0, 0, 1, 0, 0, 0});
+    for (int r0 = 0; r0 < nq; r0 += gemv_tile_rows(ev)) tiles.push_back(make_int2(int(jobs.size()), r0));
+    jobs.push_back({A0 + off[i] * ev, nq, nq, nq, (char*)P.t3.p + objs[i].q0 * ev, P.nq, (char*)P.x3.p + objs[i].q0 * ev,
+                    P.nq, 1, 0, 0, 0});
     rs.push_back(acc);
     acc += nq;
   }
   P.jobs.upload(jobs, s);
   P.rs.upload(rs, s);
+  P.tiles.upload(tiles, s);
   P.plan.jobs = P.jobs.p;
   P.plan.rowstart = P.rs.p;
   P.plan.njobs = int(jobs.size());
   P.plan.total_rows = acc;
+  P.plan.tiles = P.tiles.p;
+  P.plan.ntiles = int(tiles.size());
+  P.plan.tile_rows = gemv_tile_rows(ev);
   P.plan.name = "gemv_pc";
   SLDM_CUDA(cudaStreamSynchronize(s));
 }
 
-void prec_apply(const Precond& P, const sldm_mesh* m, const double2* r, double2* x, cudaStream_t s) {
-  ScopedTimer tm("precond", s);
+template <class CV>
+static void prec_apply_t(const Precond& P, const sldm_mesh* m, const double2* r, double2* x, int64_t ld, int nr,
+                         cudaStream_t s) {
   const HostMesh& h = m->h;
   const DevMesh& d = m->d;
-  const int ne = int(h.ne), nq = int(h.nt - h.nobj);
-  prec_apply1_kernel<<<(nq + 255) / 256, 256, 0, s>>>(ne, nq, d.q2t.p, d.tri_edge.p, d.tri_sign.p, P.lam.p, r, P.t3.p), ::sldm::count_launch();
-  gemv_jobs<double2>(P.plan, 1, s);
-  prec_apply3_kernel<<<unsigned(h.nobj), 256, 0, s>>>(P.objs.p, P.x3.p, P.bx.p), ::sldm::count_launch();
+  const int ne = int(h.ne), nq = int(P.nq), nt = int(h.nt);
+  CV* t3 = reinterpret_cast<CV*>(P.t3.p);
+  CV* x3 = reinterpret_cast<CV*>(P.x3.p);
+  if (nq > 0) {
+    prec_apply1_kernel<CV><<<dim3((nq + 255) / 256, nr), 256, 0, s>>>(ne, nq, d.q2t.p, d.tri_edge.p, d.tri_sign.p, P.lam.p,
+                                                                       r, ld, t3), ::sldm::count_launch();
+    gemv_jobs<CV>(P.plan, nr, s);
+  }
+  prec_apply3_kernel<CV><<<dim3(unsigned(h.nobj), nr), 256, 0, s>>>(P.objs.p, nq, nt, x3, P.bx.p), ::sldm::count_launch();
   const int n = std::max(ne, nq);
-  prec_apply45_kernel<<<(n + 255) / 256, 256, 0, s>>>(ne, nq, d.tplus.p, d.tminus.p, P.lam.p, P.pdiag.p, r, P.bx.p, P.x3.p, x), ::sldm::count_launch();
+  prec_apply45_kernel<CV><<<dim3((n + 255) / 256, nr), 256, 0, s>>>(ne, nq, nt, d.tplus.p, d.tminus.p, P.lam.p, P.pdiag.p,
+                                                                     r, ld, P.bx.p, x3, x), ::sldm::count_launch();
   SLDM_CUDA(cudaGetLastError());
+}
+
+void prec_apply(const Precond& P, const sldm_mesh* m, const double2* r, double2* x, int64_t ld, int nr, cudaStream_t s) {
+  ScopedTimer tm("precond", s);
+  SLDM_REQUIRE((nr >= 1 && nr <= MAX_NRHS), SLDM_EINVAL, "preconditioner: 1 to 8 columns");
+  if (P.f32) prec_apply_t<float2>(P, m, r, x, ld, nr, s);
+  else prec_apply_t<double2>(P, m, r, x, ld, nr, s);
 }
 
 template void prec_setup<float2>(Precond&, const sldm_mesh*, const std::vector<PrecObj>&, double, const void*, const void*,

@@ -14,10 +14,15 @@ struct Precond {
   DBuf<PrecObj> objs;
   DBuf<double2> lam;    // 4 per edge: Lambda11, Lambda12, Lambda21, Lambda22
   DBuf<double2> pdiag;  // 2 per triangle: diag L^phi_m, diag of the object's L^phi/eps
-  DBuf<double2> sinv;   // per object (nt_o - 1)^2: S_o^-1, row-major
+  DBuf<double2> sinv;   // per object (nt_o - 1)^2: S_o^-1, row-major (complex128 operators)
+  DBuf<float2> sinv32;  // the same in complex64 (complex64 operators: an FP32 preconditioner)
+  bool f32 = false;
+  // WR columns each: t3, x3 of nq (entries of the preconditioner's precision), bx of nt
   DBuf<double2> t3, x3, bx;
+  int64_t nq = 0;
   DBuf<GemvJob> jobs;
   DBuf<int64_t> rs;
+  DBuf<int2> tiles;
   GemvPlan plan;
   bool ready = false;
 };
@@ -25,7 +30,7 @@ struct Precond {
 template <class C>
 void prec_setup(Precond& P, const sldm_mesh* m, const std::vector<PrecObj>& objs, double k0, const void* LAm,
                 const void* LPm, const char* loc, const double* ix_val, cudaStream_t s);
-// x = P^-1 r (complex128 vectors of length N)
-void prec_apply(const Precond& P, const sldm_mesh* m, const double2* r, double2* x, cudaStream_t s);
+// x = P^-1 r for nr <= WR columns (complex128 vectors of length N, column stride ld)
+void prec_apply(const Precond& P, const sldm_mesh* m, const double2* r, double2* x, int64_t ld, int nr, cudaStream_t s);
 
 }  // namespace sldm
