@@ -54,12 +54,14 @@ for _n in (8, 4):
 # 2.5 deg steps in the xz plane, TE and TM alternating), solved together: one
 # assembly and one lockstep 8-RHS GMRES per step; every right-hand side counts as
 # a solve.
+# (4 x 4: the small case kept for profiling captures of the several-RHS kernels.)
 _TH8 = np.radians(2.5 * np.arange(8))
-WORKLOADS["metasurface-8x8-cyl-epsr6-1um-freespace-c64-8angles"] = dict(
-    WORKLOADS["metasurface-8x8-cyl-epsr6-1um-freespace-c64"],
-    khat=[[float(np.sin(t)), 0.0, -float(np.cos(t))] for t in _TH8],
-    pol=[[0.0, 1.0, 0.0] if i % 2 == 0 else [float(np.cos(t)), 0.0, float(np.sin(t))] for i, t in enumerate(_TH8)],
-    n_angles=181, e2e_steps=3)
+for _n in (8, 4):
+    WORKLOADS[f"metasurface-{_n}x{_n}-cyl-epsr6-1um-freespace-c64-8angles"] = dict(
+        WORKLOADS[f"metasurface-{_n}x{_n}-cyl-epsr6-1um-freespace-c64"],
+        khat=[[float(np.sin(t)), 0.0, -float(np.cos(t))] for t in _TH8],
+        pol=[[0.0, 1.0, 0.0] if i % 2 == 0 else [float(np.cos(t)), 0.0, float(np.sin(t))] for i, t in enumerate(_TH8)],
+        n_angles=181, e2e_steps=3)
 # Multiscale conductor in a layered substrate: a copper bar (sigma 5.8e7 S/m,
 # 100 x 2 x 1 um, 2,048 graded triangles, N = 8,191) in the middle of a 10 um SiO2
 # layer (eps_r 3.9) over 200 um of Si (eps_r 11.9, sigma 10 S/m) over a PEC ground,

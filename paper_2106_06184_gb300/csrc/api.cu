@@ -67,6 +67,7 @@ struct sldm_op {
   sldm::Precond pc;
   // GMRES workspace
   int ws_m = 0;
+  int64_t ldv = 0;  // column stride of the Krylov bases: N rounded up to 64, zero rows beyond N
   sldm::DBuf<double2> V, wb, wx, wr, wtmp, wtmp2, wacc, wz, dh;
   int ws_nr = 0;
   sldm::DBuf<double> dnorm;
@@ -414,7 +415,9 @@ static void assemble_impl(sldm_op* op, const sldm_material* mats, cudaStream_t s
 static void ensure_ws(sldm_op* op, int m, int nr) {
   if (op->ws_m == m && op->ws_nr >= nr && op->V.p) return;
   const size_t N = size_t(op->N), W = size_t(sldm_op::WR);
-  op->V.alloc(N * (m + 1) * nr);
+  op->ldv = (op->N + 63) / 64 * 64;
+  op->V.alloc(size_t(op->ldv) * (m + 1) * nr);
+  op->V.zero();  // the padding rows stay zero
   op->wb.alloc(N * W);
   op->wx.alloc(N * W);
   op->wr.alloc(N * W);
@@ -452,14 +455,18 @@ static double dnorm(sldm_op* op, const double2* v, cudaStream_t s) {
 // operators) the true residual at every restart is accumulated in FP64 and each
 // cycle stops once it has reduced that residual by REFINE_CYCLE: the cycles are
 // the correction solves of iterative refinement, in the operator's precision.
+// CB is the storage of the Krylov bases (complex64 for complex64 operators,
+// orthogonalised in FP32); x_zero says the initial guesses are zero (the first
+// residual is then b, with no product).
 constexpr double REFINE_CYCLE = 1e-5;
 template <class CB>
-static void gmres_block(sldm_op* op, bool use_p, bool refine, int m, double tol, int maxit, int nr, int& iters,
-                        double* relres, cudaStream_t s) {
+static void gmres_block(sldm_op* op, bool use_p, bool refine, bool x_zero, int m, double tol, int maxit, int nr,
+                        int& iters, double* relres, cudaStream_t s) {
   const int64_t N = op->N, ne = op->ne;
   const double l = op->mesh->h.ell;
   auto col = [&](DBuf<double2>& b, int r) { return b.p + int64_t(r) * N; };
-  auto Vr = [&](int r) { return reinterpret_cast<CB*>(op->V.p) + int64_t(r) * N * (m + 1); };
+  const int64_t ldv = op->ldv;
+  auto Vr = [&](int r) { return reinterpret_cast<CB*>(op->V.p) + int64_t(r) * ldv * (m + 1); };
   auto dhr = [&](int r) { return op->dh.p + int64_t(r) * 2 * (m + 2); };
   std::vector<double> bnorm(nr), beta(nr);
   for (int r = 0; r < nr; ++r) {
@@ -468,7 +475,9 @@ static void gmres_block(sldm_op* op, bool use_p, bool refine, int m, double tol,
     if (bnorm[r] == 0) SLDM_CUDA(cudaMemsetAsync(col(op->wx, r), 0, N * sizeof(double2), s));  // b = 0: x = 0
   }
   auto residuals = [&]() {  // wr = Dr (b - Z x), every column
-    apply_any(op, op->wx.p, op->wr.p, nr, s, refine);
+    if (x_zero) SLDM_CUDA(cudaMemsetAsync(op->wr.p, 0, size_t(nr) * N * sizeof(double2), s));  // Z 0 = 0
+    else apply_any(op, op->wx.p, op->wr.p, nr, s, refine);
+    x_zero = false;
     for (int r = 0; r < nr; ++r) {
       vscale3(N, ne, 1.0, 1.0, l, col(op->wr, r), col(op->wr, r), s);
       vaxpby(N, 1.0, col(op->wb, r), -1.0, col(op->wr, r), s);
@@ -503,38 +512,58 @@ static void gmres_block(sldm_op* op, bool use_p, bool refine, int m, double tol,
       if (on.empty()) break;
       const int na = int(on.size());
       // the products of this step, together: w_r = Dr Z P^-1 Dr^-1 v_r (or Dr Z Dc v_r)
+      VecBatch<CB, double2> bv;
       for (int j = 0; j < na; ++j) {
-        const CB* v = Vr(on[j]) + int64_t(k) * N;
-        if (use_p) vscale3<CB, double2>(N, ne, 1.0, 1.0, 1.0 / l, v, col(op->wtmp2, j), s);
-        else vscale3<CB, double2>(N, ne, 1.0 / l, 1.0, l, v, col(op->wtmp, j), s);
+        bv.x[j] = Vr(on[j]) + int64_t(k) * ldv;
+        bv.y[j] = col(use_p ? op->wtmp2 : op->wtmp, j);
+        bv.a[j] = 1.0;
       }
-      if (use_p) prec_apply(op->pc, op->mesh, op->wtmp2.p, op->wtmp.p, N, na, s);
+      if (use_p) {
+        vscale3_batch(N, ne, 1.0, 1.0, 1.0 / l, bv, na, s);
+        prec_apply(op->pc, op->mesh, op->wtmp2.p, op->wtmp.p, N, na, s);
+      } else {
+        vscale3_batch(N, ne, 1.0 / l, 1.0, l, bv, na, s);
+      }
       apply_any(op, op->wtmp.p, op->wz.p, na, s);
       {
+        // classical Gram-Schmidt, twice, of every w_r = Dr wz_r against its basis
         ScopedTimer tgs("gram_schmidt", s);
+        SLDM_CUDA(cudaMemsetAsync(op->dh.p, 0, op->dh.bytes(), s));
+        SLDM_CUDA(cudaMemsetAsync(op->dnorm.p, 0, op->dnorm.bytes(), s));
+        VecBatch<double2, CB> bw;
+        KrylovStep ks;
+        ks.n = N;
+        ks.ldv = ldv;
+        ks.k = k + 1;
+        ks.na = na;
+        ks.nrm = op->dnorm.p;
         for (int j = 0; j < na; ++j) {
-          const int r = on[j];
-          CB* w = Vr(r) + int64_t(k + 1) * N;
-          vscale3<double2, CB>(N, ne, 1.0, 1.0, l, col(op->wz, j), w, s);
-          // classical Gram-Schmidt, twice
-          vdots<CB>(Vr(r), N, k + 1, w, N, dhr(r), s);
-          vmul<CB, CB>(Vr(r), N, k + 1, dhr(r), -1.0, w, N, s);
-          vdots<CB>(Vr(r), N, k + 1, w, N, dhr(r) + (m + 2), s);
-          vmul<CB, CB>(Vr(r), N, k + 1, dhr(r) + (m + 2), -1.0, w, N, s);
-          vnorm2<CB>(w, N, op->dnorm.p + j, s);
+          bw.x[j] = col(op->wz, j);
+          bw.y[j] = Vr(on[j]) + int64_t(k + 1) * ldv;
+          bw.a[j] = 1.0;
+          ks.V[j] = Vr(on[j]);
+          ks.h[j] = dhr(on[j]);
         }
+        vscale3_batch(N, ne, 1.0, 1.0, l, bw, na, s);
+        krylov_dots<CB>(ks, s);
+        krylov_update<CB>(ks, false, s);
+        for (int j = 0; j < na; ++j) ks.h[j] = dhr(on[j]) + (m + 2);
+        krylov_dots<CB>(ks, s);
+        krylov_update<CB>(ks, true, s);
       }
       SLDM_CUDA(cudaMemcpyAsync(hh.data(), op->dh.p, size_t(nr) * 2 * (m + 2) * sizeof(double2), cudaMemcpyDeviceToHost, s));
       SLDM_CUDA(cudaMemcpyAsync(hn.data(), op->dnorm.p, size_t(na) * sizeof(double), cudaMemcpyDeviceToHost, s));
       SLDM_CUDA(cudaStreamSynchronize(s));
+      VecBatch<CB, CB> bn;  // v_{k+1} = w / h_{k+1,k}
       for (int j = 0; j < na; ++j) {
         const int r = on[j];
         const double2* hr = hh.data() + size_t(r) * 2 * (m + 2);
         const double h1 = std::sqrt(hn[j]);
+        bn.x[j] = bn.y[j] = Vr(r) + int64_t(k + 1) * ldv;
+        bn.a[j] = h1 > 0 ? 1.0 / h1 : 0.0;
         std::vector<cplx>& Hr = H[r];
         for (int i = 0; i <= k; ++i) Hr[size_t(i) * m + k] = cplx(hr[i].x, hr[i].y) + cplx(hr[(m + 2) + i].x, hr[(m + 2) + i].y);
         Hr[size_t(k + 1) * m + k] = h1;
-        if (h1 > 0) vaxpby<CB, CB>(N, 1.0 / h1, Vr(r) + int64_t(k + 1) * N, 0.0, Vr(r) + int64_t(k + 1) * N, s);
         for (int i = 0; i < k; ++i) {  // previous rotations
           cplx a = Hr[size_t(i) * m + k], b = Hr[size_t(i + 1) * m + k];
           Hr[size_t(i) * m + k] = cs[r][i] * a + sn[r][i] * b;
@@ -559,6 +588,7 @@ static void gmres_block(sldm_op* op, bool use_p, bool refine, int m, double tol,
         if (std::abs(g[r][k + 1]) / bnorm[r] <= tol || it[r] >= maxit || h1 == 0) live[r] = 0;
         if (refine && std::abs(g[r][k + 1]) <= REFINE_CYCLE * beta[r]) live[r] = 0;
       }
+      vscale3_batch(N, ne, 1.0, 1.0, 1.0, bn, na, s);
     }
     // y = H^-1 g (upper triangular);  x += (P^-1 Dr^-1 or Dc) V y
     for (int r : act) {
@@ -571,7 +601,7 @@ static void gmres_block(sldm_op* op, bool use_p, bool refine, int m, double tol,
       }
       SLDM_CUDA(cudaMemcpyAsync(dhr(r), y.data(), ku * sizeof(double2), cudaMemcpyHostToDevice, s));
       SLDM_CUDA(cudaMemsetAsync(col(op->wacc, r), 0, N * sizeof(double2), s));
-      vmul<CB, double2>(Vr(r), N, ku, dhr(r), 1.0, col(op->wacc, r), N, s);
+      vmul<CB, double2>(Vr(r), ldv, ku, dhr(r), 1.0, col(op->wacc, r), N, s);
       if (use_p) {
         vscale3(N, ne, 1.0, 1.0, 1.0 / l, col(op->wacc, r), col(op->wtmp2, 0), s);
         prec_apply(op->pc, op->mesh, col(op->wtmp2, 0), col(op->wtmp, 0), N, 1, s);
@@ -985,8 +1015,8 @@ int sldm_solve(const sldm_op* op_, const void* b, void* x, int32_t nrhs, const s
       // complex64 operators keep the Krylov basis in complex64 and orthogonalise
       // in FP32 (the cycles are correction solves; the residual that decides
       // convergence is formed in FP64 at each restart when refining)
-      if (op->prec == SLDM_PREC_F32) gmres_block<float2>(op, use_p, refine, m, tol, maxit, nr, iters, rel, s);
-      else gmres_block<double2>(op, use_p, refine, m, tol, maxit, nr, iters, rel, s);
+      if (op->prec == SLDM_PREC_F32) gmres_block<float2>(op, use_p, refine, !x0, m, tol, maxit, nr, iters, rel, s);
+      else gmres_block<double2>(op, use_p, refine, !x0, m, tol, maxit, nr, iters, rel, s);
     }
     for (int r = 0; r < nr; ++r) worst = std::max(worst, rel[r]);
     cudaMemcpyKind k_out = where == SLDM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;

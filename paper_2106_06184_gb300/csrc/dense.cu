@@ -979,43 +979,6 @@ __device__ __forceinline__ float2 cmake<float2>(double x, double y) { return mak
 template <>
 __device__ __forceinline__ double2 cmake<double2>(double x, double y) { return make_double2(x, y); }
 
-// h[i] = V[:, i]^H w  for i < k.  Grid (ceil(k / 8), row chunks): warp j of a CTA
-// takes column 8 blockIdx.x + j over the CTA's chunk of DOTS_CHUNK rows, two
-// loads of V and w per lane in flight, and adds its sum to h[i] with FP64
-// atomics (h is cleared first).  V streams once, at full width of the grid.
-constexpr int DOTS_CHUNK = 2048;
-template <class CB>
-__global__ void __launch_bounds__(256) dots_kernel(const CB* __restrict__ V, int64_t ldv, int k, const CB* __restrict__ w,
-                                                   int64_t n, double2* h) {
-  typedef typename CT<CB>::R R;
-  const int lane = threadIdx.x & 31;
-  const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
-  if (i >= k) return;
-  const int64_t r0 = int64_t(blockIdx.y) * DOTS_CHUNK;
-  const int64_t r1 = r0 + DOTS_CHUNK < n ? r0 + DOTS_CHUNK : n;
-  const CB* v = V + int64_t(i) * ldv;
-  R sr = 0, si = 0, tr = 0, ti = 0;
-  int64_t t = r0 + lane;
-  for (; t + 32 < r1; t += 64) {
-    const CB a0 = v[t], b0 = w[t], a1 = v[t + 32], b1 = w[t + 32];
-    cfma(sr, si, a0.x, -a0.y, b0.x, b0.y);  // conj(a) b
-    cfma(tr, ti, a1.x, -a1.y, b1.x, b1.y);
-  }
-  if (t < r1) {
-    const CB a0 = v[t], b0 = w[t];
-    cfma(sr, si, a0.x, -a0.y, b0.x, b0.y);
-  }
-  double dr = double(sr) + double(tr), di = double(si) + double(ti);
-  for (int o = 16; o > 0; o >>= 1) {
-    dr += __shfl_xor_sync(0xffffffffu, dr, o);
-    di += __shfl_xor_sync(0xffffffffu, di, o);
-  }
-  if (lane == 0) {
-    atomicAdd(&h[i].x, dr);
-    atomicAdd(&h[i].y, di);
-  }
-}
-
 // w += sign * V[:, :k] h (arithmetic in w's precision).  A CTA owns 32 rows;
 // its 8 warps take every 8th Krylov column, four columns in flight, and the
 // partial sums meet in shared memory.
@@ -1109,13 +1072,6 @@ void vscale3(int64_t n, int64_t ne, double s1, double s2, double s3, const CX* x
   vscale3_kernel<CX, CY><<<unsigned((n + 255) / 256), 256, 0, s>>>(n, ne, s1, s2, s3, x, y), ::sldm::count_launch();
   SLDM_CUDA(cudaGetLastError());
 }
-template <class CB>
-void vdots(const CB* V, int64_t ldv, int k, const CB* w, int64_t n, double2* h, cudaStream_t s) {
-  SLDM_CUDA(cudaMemsetAsync(h, 0, size_t(k) * sizeof(double2), s));
-  dots_kernel<CB><<<dim3(unsigned((k + 7) / 8), unsigned((n + DOTS_CHUNK - 1) / DOTS_CHUNK)), 256, 0, s>>>(V, ldv, k, w, n, h),
-      ::sldm::count_launch();
-  SLDM_CUDA(cudaGetLastError());
-}
 template <class CB, class CW>
 void vmul(const CB* V, int64_t ldv, int k, const double2* h, double sign, CW* w, int64_t n, cudaStream_t s) {
   vmul_kernel<CB, CW><<<unsigned((n + 31) / 32), 256, 0, s>>>(V, ldv, k, h, sign, w, n), ::sldm::count_launch();
@@ -1142,10 +1098,170 @@ SLDM_VEC_INST(float2, float2)
 SLDM_VEC_INST(float2, double2)
 SLDM_VEC_INST(double2, float2)
 #undef SLDM_VEC_INST
-template void vdots<double2>(const double2*, int64_t, int, const double2*, int64_t, double2*, cudaStream_t);
-template void vdots<float2>(const float2*, int64_t, int, const float2*, int64_t, double2*, cudaStream_t);
 template void vnorm2<double2>(const double2*, int64_t, double*, cudaStream_t);
 template void vnorm2<float2>(const float2*, int64_t, double*, cudaStream_t);
+
+// ---------------------------------------------------------------- batched Gram-Schmidt
+// One launch per pass for every live right-hand side of a lockstep step.  The
+// bases have a column stride ldv that is a multiple of 64 entries and zero
+// rows from n up to ldv, so every lane handles two consecutive rows (one
+// 16-byte load in complex64) with no tail.
+__device__ __forceinline__ void ld_pair(const float2* p, float2& a, float2& b) {
+  const float4 q = *reinterpret_cast<const float4*>(p);
+  a = make_float2(q.x, q.y);
+  b = make_float2(q.z, q.w);
+}
+__device__ __forceinline__ void ld_pair(const double2* p, double2& a, double2& b) {
+  a = p[0];
+  b = p[1];
+}
+__device__ __forceinline__ void st_pair(float2* p, float2 a, float2 b) {
+  *reinterpret_cast<float4*>(p) = make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ void st_pair(double2* p, double2 a, double2 b) {
+  p[0] = a;
+  p[1] = b;
+}
+
+// h_j[i] += V_j[:, i]^H V_j[:, k] for i < k.  Grid (ceil(k / 8), row chunks, na):
+// warp i % 8 of a CTA takes column i over the CTA's KRYLOV_CHUNK rows.
+constexpr int KRYLOV_CHUNK = 2048;
+template <class CB>
+__global__ void __launch_bounds__(256) krylov_dots_kernel(KrylovStep ks) {
+  typedef typename CT<CB>::R R;
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (i >= ks.k) return;
+  const CB* V = reinterpret_cast<const CB*>(ks.V[blockIdx.z]);
+  const CB* __restrict__ v = V + int64_t(i) * ks.ldv;
+  const CB* __restrict__ w = V + int64_t(ks.k) * ks.ldv;
+  const int64_t r0 = int64_t(blockIdx.y) * KRYLOV_CHUNK;
+  const int64_t r1 = r0 + KRYLOV_CHUNK < ks.ldv ? r0 + KRYLOV_CHUNK : ks.ldv;
+  R sr = 0, si = 0, tr = 0, ti = 0;
+#pragma unroll 4
+  for (int64_t t = r0 + 2 * lane; t < r1; t += 64) {
+    CB a0, a1, b0, b1;
+    ld_pair(v + t, a0, a1);
+    ld_pair(w + t, b0, b1);
+    cfma(sr, si, a0.x, -a0.y, b0.x, b0.y);  // conj(a) b
+    cfma(tr, ti, a1.x, -a1.y, b1.x, b1.y);
+  }
+  double dr = double(sr) + double(tr), di = double(si) + double(ti);
+  for (int o = 16; o > 0; o >>= 1) {
+    dr += __shfl_xor_sync(0xffffffffu, dr, o);
+    di += __shfl_xor_sync(0xffffffffu, di, o);
+  }
+  if (lane == 0) {
+    atomicAdd(&ks.h[blockIdx.z][i].x, dr);
+    atomicAdd(&ks.h[blockIdx.z][i].y, di);
+  }
+}
+
+// V_j[:, k] -= V_j[:, :k] h_j, and with `norm` nrm[j] += |V_j[:, k]|^2 after the
+// update.  Grid (ldv / 64, na): a CTA owns 64 rows, its 8 warps take every 8th
+// column (four in flight) and the partial sums meet in shared memory.
+template <class CB>
+__global__ void __launch_bounds__(256) krylov_update_kernel(KrylovStep ks, int norm) {
+  typedef typename CT<CB>::R R;
+  __shared__ R part[8][32][4];
+  const int lane = threadIdx.x & 31, slice = threadIdx.x >> 5;
+  const int j = blockIdx.y;
+  CB* V = reinterpret_cast<CB*>(ks.V[j]);
+  const double2* __restrict__ h = ks.h[j];
+  const int64_t t = int64_t(blockIdx.x) * 64 + 2 * lane;
+  R s0r = 0, s0i = 0, s1r = 0, s1i = 0;
+  int i = slice;
+  for (; i + 24 < ks.k; i += 32) {
+    CB a[4], b[4];
+    double2 c[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      ld_pair(V + int64_t(i + 8 * u) * ks.ldv + t, a[u], b[u]);
+      c[u] = h[i + 8 * u];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      cfma(s0r, s0i, R(a[u].x), R(a[u].y), R(c[u].x), R(c[u].y));
+      cfma(s1r, s1i, R(b[u].x), R(b[u].y), R(c[u].x), R(c[u].y));
+    }
+  }
+  for (; i < ks.k; i += 8) {
+    CB a, b;
+    ld_pair(V + int64_t(i) * ks.ldv + t, a, b);
+    const double2 c = h[i];
+    cfma(s0r, s0i, R(a.x), R(a.y), R(c.x), R(c.y));
+    cfma(s1r, s1i, R(b.x), R(b.y), R(c.x), R(c.y));
+  }
+  part[slice][lane][0] = s0r;
+  part[slice][lane][1] = s0i;
+  part[slice][lane][2] = s1r;
+  part[slice][lane][3] = s1i;
+  __syncthreads();
+  if (slice == 0) {
+    R q[4] = {0, 0, 0, 0};
+    for (int z = 0; z < 8; ++z)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) q[c] += part[z][lane][c];
+    CB* w = V + int64_t(ks.k) * ks.ldv + t;
+    CB a, b;
+    ld_pair(w, a, b);
+    a.x -= q[0];
+    a.y -= q[1];
+    b.x -= q[2];
+    b.y -= q[3];
+    st_pair(w, a, b);
+    if (norm) {
+      double nn = double(a.x) * double(a.x) + double(a.y) * double(a.y) + double(b.x) * double(b.x) +
+                  double(b.y) * double(b.y);
+      for (int o = 16; o > 0; o >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
+      if (lane == 0) atomicAdd(ks.nrm + j, nn);
+    }
+  }
+}
+
+template <class CB>
+void krylov_dots(const KrylovStep& ks, cudaStream_t s) {
+  if (ks.k <= 0 || ks.na <= 0) return;
+  krylov_dots_kernel<CB><<<dim3(unsigned((ks.k + 7) / 8), unsigned((ks.ldv + KRYLOV_CHUNK - 1) / KRYLOV_CHUNK), ks.na), 256, 0,
+                           s>>>(ks), ::sldm::count_launch();
+  SLDM_CUDA(cudaGetLastError());
+}
+template <class CB>
+void krylov_update(const KrylovStep& ks, bool norm, cudaStream_t s) {
+  if (ks.na <= 0) return;
+  krylov_update_kernel<CB><<<dim3(unsigned(ks.ldv / 64), ks.na), 256, 0, s>>>(ks, norm ? 1 : 0), ::sldm::count_launch();
+  SLDM_CUDA(cudaGetLastError());
+}
+template void krylov_dots<float2>(const KrylovStep&, cudaStream_t);
+template void krylov_dots<double2>(const KrylovStep&, cudaStream_t);
+template void krylov_update<float2>(const KrylovStep&, bool, cudaStream_t);
+template void krylov_update<double2>(const KrylovStep&, bool, cudaStream_t);
+
+// y_j = a_j s(i) x_j[i] for the na column pairs, s = s1, s2, s3 on the three blocks
+template <class CX, class CY>
+__global__ void vscale3_batch_kernel(int64_t n, int64_t ne, double s1, double s2, double s3, VecBatch<CX, CY> b) {
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const int j = blockIdx.y;
+  const double sc = b.a[j] * (t < ne ? s1 : (t < 2 * ne ? s2 : s3));
+  const CX v = b.x[j][t];
+  b.y[j][t] = cmake<CY>(sc * double(v.x), sc * double(v.y));
+}
+template <class CX, class CY>
+void vscale3_batch(int64_t n, int64_t ne, double s1, double s2, double s3, const VecBatch<CX, CY>& b, int na,
+                   cudaStream_t s) {
+  if (na <= 0) return;
+  vscale3_batch_kernel<CX, CY><<<dim3(unsigned((n + 255) / 256), na), 256, 0, s>>>(n, ne, s1, s2, s3, b), ::sldm::count_launch();
+  SLDM_CUDA(cudaGetLastError());
+}
+template void vscale3_batch<double2, double2>(int64_t, int64_t, double, double, double, const VecBatch<double2, double2>&, int,
+                                              cudaStream_t);
+template void vscale3_batch<float2, double2>(int64_t, int64_t, double, double, double, const VecBatch<float2, double2>&, int,
+                                             cudaStream_t);
+template void vscale3_batch<double2, float2>(int64_t, int64_t, double, double, double, const VecBatch<double2, float2>&, int,
+                                             cudaStream_t);
+template void vscale3_batch<float2, float2>(int64_t, int64_t, double, double, double, const VecBatch<float2, float2>&, int,
+                                            cudaStream_t);
 
 // ---------------------------------------------------------------- conversions
 template <class C>

@@ -75,10 +75,33 @@ void apply_glue_combine(const sldm_mesh* m, const ApplyDims& D, double k0, const
                         const void* z2, const void* w1, const void* w2, const void* w3, const void* e, const void* a,
                         const void* c, double2* y, int64_t ldy, int nrhs, cudaStream_t s);
 
+// One Gram-Schmidt pass over the Krylov bases of the live right-hand sides of a
+// lockstep step: column k of each basis against its columns 0..k-1.  The
+// bases have column stride ldv (a multiple of 64) and zero rows n..ldv-1.
+struct KrylovStep {
+  int64_t n = 0, ldv = 0;
+  int k = 0, na = 0;
+  void* V[MAX_NRHS] = {};       // basis of right-hand side j (complex64 or complex128)
+  double2* h[MAX_NRHS] = {};    // its k projection coefficients (accumulated; cleared by the caller)
+  double* nrm = nullptr;        // na squared norms of column k after an update with norm (cleared by the caller)
+};
+template <class CB>
+void krylov_dots(const KrylovStep& ks, cudaStream_t s);                // h_j += V_j[:, :k]^H V_j[:, k]
+template <class CB>
+void krylov_update(const KrylovStep& ks, bool norm, cudaStream_t s);   // V_j[:, k] -= V_j[:, :k] h_j
+template <class CX, class CY>
+struct VecBatch {
+  const CX* x[MAX_NRHS] = {};
+  CY* y[MAX_NRHS] = {};
+  double a[MAX_NRHS] = {};
+};
+// y_j = a_j s(i) x_j (s = s1 on [0, ne), s2 on [ne, 2 ne), s3 beyond), j < na, in place allowed
+template <class CX, class CY>
+void vscale3_batch(int64_t n, int64_t ne, double s1, double s2, double s3, const VecBatch<CX, CY>& b, int na,
+                   cudaStream_t s);
+
 // complex128 or complex64 storage (instantiated for double2 and float2; mixed
 // pairs for vmul, vaxpby and vscale3)
-template <class CB>
-void vdots(const CB* V, int64_t ldv, int k, const CB* w, int64_t n, double2* h, cudaStream_t s);
 template <class CB, class CW>
 void vmul(const CB* V, int64_t ldv, int k, const double2* h, double sign, CW* w, int64_t n, cudaStream_t s);
 template <class C>
