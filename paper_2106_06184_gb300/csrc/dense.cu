@@ -635,13 +635,24 @@ struct GemvTile {
 static_assert(GemvTile<float2, float2>::ROWS == 32 && GemvTile<double2, double2>::ROWS == 16, "tile rows");
 
 template <int N>
-__device__ __forceinline__ void cp_async(void* dst, const void* src, bool valid) {
-  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
-  const int n = valid ? N : 0;  // 0: fill the destination with zeros, read nothing
+__device__ __forceinline__ void cp_async_s(unsigned d, const void* src, bool valid) {  // shared address d
+  const int n = valid ? N : 0;
   if constexpr (N == 16)
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
   else
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
+}
+// packed FP32 pairs: (lo, hi) in one 64-bit register pair, d = a * b + d per component
+__device__ __forceinline__ unsigned long long f32x2(float lo, float hi) {
+  unsigned long long u;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(u) : "f"(lo), "f"(hi));
+  return u;
+}
+__device__ __forceinline__ void f32x2_split(unsigned long long u, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(u));
+}
+__device__ __forceinline__ void ffma2(unsigned long long& d, unsigned long long a, unsigned long long b) {
+  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(d) : "l"(a), "l"(b));
 }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
@@ -687,41 +698,75 @@ __global__ void __launch_bounds__(256, 2) gemv_tile_kernel(const GemvJob* __rest
   const CM* __restrict__ A = reinterpret_cast<const CM*>(J.A);
   const CV* __restrict__ x = reinterpret_cast<const CV*>(J.x);
   const int nch = (J.n + CW - 1) / CW;
+  // per-thread copy sources (row 0 / right-hand side 0 stand in for rows or
+  // right-hand sides outside the job: valid addresses, copied as zeros) and
+  // shared-memory destinations in stage 0
+  const CM* asrc[RW];
+  bool arow[RW];
+#pragma unroll
+  for (int i = 0; i < RW; ++i) {
+    arow[i] = row0 + i < J.m;
+    asrc[i] = A + int64_t(arow[i] ? row0 + i : 0) * J.lda + lane;
+  }
+  constexpr int XPT = (NR * CW + 255) / 256;  // x entries per thread per chunk
+  const CV* xsrc[XPT];
+  bool xok[XPT];
+  int xcol[XPT];
+#pragma unroll
+  for (int q = 0; q < XPT; ++q) {
+    const int e = q * 256 + threadIdx.x, r = e / CW;
+    xcol[q] = e % CW;
+    xok[q] = (NR * CW % 256 == 0 || e < NR * CW) && r < nrhs;
+    xsrc[q] = x + (xok[q] ? int64_t(r) * J.ldx : 0) + xcol[q];
+  }
+  const unsigned a_dst = static_cast<unsigned>(__cvta_generic_to_shared(As + warp * RW * CW + lane));
+  const unsigned x_dst = static_cast<unsigned>(__cvta_generic_to_shared(Xs + threadIdx.x));
+  constexpr unsigned x_stage = NR * CW * sizeof(CV);
   auto issue = [&](int ch) {
     if (ch < nch) {
-      const int st = ch % ST;
-      CM* a = As + (st * 8 + warp) * RW * CW;
+      const int st = ch & (ST - 1), c0 = ch * CW;
+      const unsigned ad = a_dst + st * unsigned(T::a_stage), xd = x_dst + st * x_stage;
+      if (c0 + CW <= J.n) {  // a whole chunk: only row / right-hand-side validity
 #pragma unroll
-      for (int i = 0; i < RW; ++i)
+        for (int i = 0; i < RW; ++i)
 #pragma unroll
-        for (int j = 0; j < 2; ++j) {
-          const int col = ch * CW + j * 32 + lane, row = row0 + i;
-          const bool ok = row < J.m && col < J.n;
-          cp_async<sizeof(CM)>(a + (i * 2 + j) * 32 + lane, ok ? A + int64_t(row) * J.lda + col : A, ok);
-        }
-      CV* xs = Xs + st * NR * CW;
+          for (int j = 0; j < 2; ++j) cp_async_s<sizeof(CM)>(ad + (i * 2 + j) * 32 * sizeof(CM), asrc[i] + c0 + j * 32, arow[i]);
 #pragma unroll
-      for (int e0 = 0; e0 < NR * CW; e0 += 256) {
-        const int e = e0 + threadIdx.x;
-        if (NR * CW % 256 == 0 || e < NR * CW) {
-          const int r = e / CW, col = ch * CW + e % CW;
-          const bool ok = r < nrhs && col < J.n;
-          cp_async<sizeof(CV)>(xs + e, ok ? x + int64_t(r) * J.ldx + col : x, ok);
-        }
+        for (int q = 0; q < XPT; ++q)
+          if (NR * CW % 256 == 0 || q * 256 + int(threadIdx.x) < NR * CW)
+            cp_async_s<sizeof(CV)>(xd + q * 256 * sizeof(CV), xsrc[q] + c0, xok[q]);
+      } else {
+#pragma unroll
+        for (int i = 0; i < RW; ++i)
+#pragma unroll
+          for (int j = 0; j < 2; ++j) {
+            const bool ok = arow[i] && c0 + j * 32 + lane < J.n;
+            cp_async_s<sizeof(CM)>(ad + (i * 2 + j) * 32 * sizeof(CM), ok ? asrc[i] + c0 + j * 32 : A, ok);
+          }
+#pragma unroll
+        for (int q = 0; q < XPT; ++q)
+          if (NR * CW % 256 == 0 || q * 256 + int(threadIdx.x) < NR * CW) {
+            const bool ok = xok[q] && c0 + xcol[q] < J.n;
+            cp_async_s<sizeof(CV)>(xd + q * 256 * sizeof(CV), ok ? xsrc[q] + c0 : x, ok);
+          }
       }
     }
     cp_commit();  // possibly empty: keeps one group per chunk
   };
 #pragma unroll
   for (int c = 0; c < ST - 1; ++c) issue(c);
+  constexpr bool PACKED = std::is_same<CM, float2>::value && std::is_same<CV, float2>::value;
   R acc[RW * NR * 2];
+  unsigned long long acc2[PACKED ? RW * NR : 1];  // (re, im) pairs for the packed FP32 FMAs
 #pragma unroll
   for (int i = 0; i < RW * NR * 2; ++i) acc[i] = R(0);
+#pragma unroll
+  for (int i = 0; i < (PACKED ? RW * NR : 1); ++i) acc2[i] = 0ull;
   for (int ch = 0; ch < nch; ++ch) {
     cp_wait<ST - 2>();  // this thread's copies of chunk ch have landed
     __syncthreads();    // everyone's have, and chunk ch - 1 is consumed
     issue(ch + ST - 1); // into the slot of chunk ch - 1
-    const int st = ch % ST;
+    const int st = ch & (ST - 1);
     const CM* a = As + (st * 8 + warp) * RW * CW;
     const CV* xs = Xs + st * NR * CW;
 #pragma unroll
@@ -729,13 +774,43 @@ __global__ void __launch_bounds__(256, 2) gemv_tile_kernel(const GemvJob* __rest
       CM av[RW];
 #pragma unroll
       for (int i = 0; i < RW; ++i) av[i] = a[(i * 2 + j) * 32 + lane];
+      if constexpr (PACKED) {
+        // (acc_re, acc_im) += (a_re, a_re) (x_re, x_im) + (a_im, a_im) (-x_im, x_re):
+        // the same two FMAs per component, in the same order, as cfma
+        unsigned long long p1[RW], p2[RW];
 #pragma unroll
-      for (int r = 0; r < NR; ++r) {
-        const CV xv = xs[r * CW + j * 32 + lane];
+        for (int i = 0; i < RW; ++i) {
+          p1[i] = f32x2(float(av[i].x), float(av[i].x));
+          p2[i] = f32x2(float(av[i].y), float(av[i].y));
+        }
 #pragma unroll
-        for (int i = 0; i < RW; ++i)
-          cfma(acc[(i * NR + r) * 2], acc[(i * NR + r) * 2 + 1], R(av[i].x), R(av[i].y), R(xv.x), R(xv.y));
+        for (int r = 0; r < NR; ++r) {
+          const CV xv = xs[r * CW + j * 32 + lane];
+          const unsigned long long x1 = f32x2(float(xv.x), float(xv.y)), x2 = f32x2(-float(xv.y), float(xv.x));
+#pragma unroll
+          for (int i = 0; i < RW; ++i) {
+            ffma2(acc2[i * NR + r], p1[i], x1);
+            ffma2(acc2[i * NR + r], p2[i], x2);
+          }
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+          const CV xv = xs[r * CW + j * 32 + lane];
+#pragma unroll
+          for (int i = 0; i < RW; ++i)
+            cfma(acc[(i * NR + r) * 2], acc[(i * NR + r) * 2 + 1], R(av[i].x), R(av[i].y), R(xv.x), R(xv.y));
+        }
       }
+    }
+  }
+  if constexpr (PACKED) {
+#pragma unroll
+    for (int i = 0; i < RW * NR; ++i) {
+      float lo, hi;
+      f32x2_split(acc2[i], lo, hi);
+      acc[2 * i] = R(lo);
+      acc[2 * i + 1] = R(hi);
     }
   }
   cp_wait<0>();
