@@ -105,19 +105,31 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
 # DRAM traffic per algorithmic byte of the HBM-streaming GEMV stage, from one
-# ncu capture (dram__bytes_read.sum + dram__bytes_write.sum of the gemv_main
-# launch, 4 x 4 metasurface, 423,936,000 algorithmic bytes per launch; summary in
-# profiles/gemv_main_metasurface-4x4-c64.md), valid while the kernel source is
-# unchanged (sha256 prefix of the kernel's text in dense.cu).
-GEMV_TRAFFIC = dict(sha="e09483bce0c5daf0", per_alg_byte=(424.169472e6 + 3.703040e6) / 423.936e6)
+# ncu capture of each GEMV kernel (dram__bytes_read.sum + dram__bytes_write.sum
+# of the gemv_main launch, 4 x 4 metasurface, 423,936,000 algorithmic bytes per
+# launch; summaries in profiles/gemv_main_metasurface-4x4-c64.md (one
+# right-hand side) and profiles/gemv_tile_metasurface-4x4-8angles-c64.md (8)),
+# valid while that kernel's source is unchanged (sha256 prefix of its text in
+# dense.cu).
+GEMV_TRAFFIC = {
+    "gemv_jobs_kernel": dict(sha="1c5c6f7e0080bcec", per_alg_byte=(424.169472e6 + 3.703040e6) / 423.936e6),
+    "gemv_tile_kernel": dict(sha="6197b6df0e88fdd4", per_alg_byte=(425.902336e6 + 3.562240e6) / 423.936e6),
+}
 
 
-def gemv_kernel_sha():
+def kernel_sha(name):
+    """sha256 prefix of a kernel's definition in dense.cu (its template line to the closing brace)."""
     import hashlib
     s = open(os.path.join(ROOT, "paper_2106_06184_gb300", "csrc", "dense.cu")).read()
-    a = s.index("// ---------------------------------------------------------------- batched skinny GEMV")
-    b = s.index("template <class C>\nvoid gemv_jobs(")
-    return hashlib.sha256(s[a:b].encode()).hexdigest()[:16]
+    i = s.index(" " + name + "(")
+    a = s.rindex("template <", 0, i)
+    depth, j = 0, s.index("{", i)
+    while True:
+        depth += {"{": 1, "}": -1}.get(s[j], 0)
+        if depth == 0:
+            break
+        j += 1
+    return hashlib.sha256(s[a:j + 1].encode()).hexdigest()[:16]
 
 
 def lu_flops(obj_sizes):
@@ -354,8 +366,9 @@ def run_ours(args, rank, world):
                 "peak_source": hbm_src if c["bound"] == "hbm" else "derived",
                 "traffic": None, "share_of_step": timers[dom][0] / total_ms if world == 1 else None,
                 "algorithmic_unit": c.get("bytes_per_launch") or c.get("flops_per_step")}
-        if dom == "gemv_main" and gemv_kernel_sha() == GEMV_TRAFFIC["sha"]:
-            roof["traffic"] = GEMV_TRAFFIC["per_alg_byte"] * c["bytes_per_launch"]
+        kern = "gemv_tile_kernel" if nrhs > 1 else "gemv_jobs_kernel"
+        if dom == "gemv_main" and kernel_sha(kern) == GEMV_TRAFFIC[kern]["sha"]:
+            roof["traffic"] = GEMV_TRAFFIC[kern]["per_alg_byte"] * c["bytes_per_launch"]
             roof["traffic_source"] = "ncu capture of the 4x4 case, scaled by algorithmic bytes"
     kernel_ms = {k: round(v[0] / args.steps, 4) for k, v in sorted(timers.items(), key=lambda kv: -kv[1][0])}
     out = {
@@ -392,7 +405,8 @@ METRIC = ("solves/s (per plane-wave right-hand side: assemble + RHS + GMRES to t
 # uniformly drawn triangle pairs of every fill (scaled by the pair counts), the
 # reflected fill on a random subset of triangles (scaled by the square of the
 # fraction), the layered tables whole, and the dense solves (Y of each object by
-# LU of M_l, the final system by LU) on half-size random matrices (scaled by 8).
+# LU of M_l, the final system by LU) on random matrices 1/d of the size, d at
+# least 2 and large enough for an order of at most 2,048 (scaled by d^3).
 ORACLE_FULL = r"""
 import sys, time, numpy as np
 sys.path.insert(0, {root!r})
@@ -438,6 +452,7 @@ P = m.xyz[m.tri]
 Pb = m.bxyz[m.btri]
 est = 0.0
 NS = {npairs}
+DMAX = 2048  # largest order of a timed dense solve
 
 def timed_pairs(fn, k, ta, tb, Psrc, touch_fn, total, nsrc):
     # uniformly drawn pairs; with split sources: the far-pair rule, then grouped by the size
@@ -483,12 +498,13 @@ for o in range(m.nobj):
     for k in (ko, kb):
         ta = rng.integers(t0_, t1_, ns); cb = rng.integers(6 * t0_, 6 * t1_, ns)
         est += timed_pairs(F._K_pairs, k, ta, cb, Pb, touch_K, 6.0 * n_o ** 2, 6 * n_o)
-    # Y = M_l^-1 R_l on half-size random matrices, scaled by 8
+    # Y = M_l^-1 R_l on random matrices 1/d of the size (order at most DMAX), scaled by d^3
     e0_, e1_ = m.edge_range[o]
-    n, r = (e1_ - e0_ + n_o - 1) // {ddiv}, (e1_ - e0_) // {ddiv}
+    d = max({ddiv}, -(-(e1_ - e0_ + n_o - 1) // DMAX))
+    n, r = (e1_ - e0_ + n_o - 1) // d, (e1_ - e0_) // d
     A_ = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
     B_ = rng.standard_normal((n, r)) + 1j * rng.standard_normal((n, r))
-    t0 = time.perf_counter(); np.linalg.solve(A_, B_); est += {ddiv} ** 3 * (time.perf_counter() - t0)
+    t0 = time.perf_counter(); np.linalg.solve(A_, B_); est += d ** 3 * (time.perf_counter() - t0)
 if st is not None:
     t0 = time.perf_counter()
     T = S.default_tables(m, st, lay, omega)
@@ -498,8 +514,9 @@ if st is not None:
     LY.fill_reflected(m, st, lay, omega, T, sub)
     est += (time.perf_counter() - t0) * (m.nt / len(sub)) ** 2
 N = 2 * m.ne + m.nt - m.nobj
-A_ = rng.standard_normal((N // {ddiv}, N // {ddiv})) + 1j * rng.standard_normal((N // {ddiv}, N // {ddiv}))
-t0 = time.perf_counter(); sla.lu_solve(sla.lu_factor(A_), np.ones(N // {ddiv})); est += {ddiv} ** 3 * (time.perf_counter() - t0)
+d = max({ddiv}, -(-N // DMAX))
+A_ = rng.standard_normal((N // d, N // d)) + 1j * rng.standard_normal((N // d, N // d))
+t0 = time.perf_counter(); sla.lu_solve(sla.lu_factor(A_), np.ones(N // d)); est += (N / (N // d)) ** 3 * (time.perf_counter() - t0)
 print(est, time.perf_counter() - t_all)
 """
 
@@ -517,9 +534,10 @@ def oracle_step_seconds(name=None, step=0, quick=False):
         script = ORACLE_SAMPLED.format(root=ROOT, name=name, step=step, npairs=npairs, nsub=nsub, ddiv=ddiv)
         sample = (f"extrapolated from a sample at frequency index {step}: {npairs} uniformly drawn triangle pairs per "
                   f"fill (global L, each object's L, Kbar with k and k_l), the reflected fill on {nsub} random "
-                  f"triangles, the layered tables whole, the dense solves on matrices 1/{ddiv} of the size; "
+                  f"triangles, the layered tables whole, the dense solves on matrices 1/d of the size (d >= {ddiv}, "
+                  "order <= 2048, scaled by d^3); "
                   "single thread")
-    r = subprocess.run([sys.executable, "-c", script], capture_output=True, text=True, env=env, timeout=900, cwd=ROOT)
+    r = subprocess.run([sys.executable, "-c", script], capture_output=True, text=True, env=env, timeout=300, cwd=ROOT)
     if r.returncode != 0:
         raise RuntimeError(r.stderr[-2000:])
     return float(r.stdout.strip().splitlines()[-1].split()[0]), sample
@@ -581,10 +599,14 @@ def main():
     else:
         out = run_ours(args, rank, world)
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
-            t, sample = oracle_step_seconds(args.workload, len(_freqs(WORKLOADS[args.workload])) // 2)
-            out["cpu_baseline"] = {"value": len(np.atleast_2d(WORKLOADS[args.workload]["khat"])) / t, "unit": "solves/s",
-                                   "cores": 1, "kind": "oracle",
-                                   "sample": sample, "cpu": cpu_model(), "nproc": os.cpu_count()}
+            try:
+                t, sample = oracle_step_seconds(args.workload, len(_freqs(WORKLOADS[args.workload])) // 2)
+                out["cpu_baseline"] = {"value": len(np.atleast_2d(WORKLOADS[args.workload]["khat"])) / t,
+                                       "unit": "solves/s", "cores": 1, "kind": "oracle",
+                                       "sample": sample, "cpu": cpu_model(), "nproc": os.cpu_count()}
+            except Exception as e:  # the GPU line stands without it
+                out["cpu_baseline"] = {"value": None, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                                       "error": str(e).strip().splitlines()[-1][:300]}
     if rank == 0 and out is not None:
         print(json.dumps(out))
     if world > 1:
