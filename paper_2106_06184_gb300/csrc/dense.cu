@@ -654,6 +654,29 @@ __device__ __forceinline__ void f32x2_split(unsigned long long u, float& lo, flo
 __device__ __forceinline__ void ffma2(unsigned long long& d, unsigned long long a, unsigned long long b) {
   asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(d) : "l"(a), "l"(b));
 }
+// s + c += a1 b1 + a2 b2 + a1 b1lo + a2 b2lo, where b = b + blo is a split
+// complex128 entry: the two main products are split exactly (product + FMA
+// residual, Dekker / Kahan), the products enter s by TwoSum (Knuth; intrinsics
+// keep the compiler from fusing or reordering), and every rounding error and
+// low-order term gathers in c.  With s and c in FP32 the sum carries ~48 bits,
+// on the FP32 pipe (64 x the FP64 rate of this part).
+__device__ __forceinline__ void two_sum_into(float& s, float& c, float p) {
+  const float t = __fadd_rn(s, p);
+  const float bp = __fsub_rn(t, s);
+  const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+  s = t;
+  c = __fadd_rn(c, e);
+}
+__device__ __forceinline__ void comp_mac(float& s, float& c, float a1, float b1, float a2, float b2, float b1lo,
+                                         float b2lo) {
+  const float p1 = __fmul_rn(a1, b1), p2 = __fmul_rn(a2, b2);
+  const float e1 = __fmaf_rn(a1, b1, -p1), e2 = __fmaf_rn(a2, b2, -p2);
+  two_sum_into(s, c, p1);
+  two_sum_into(s, c, p2);
+  c = __fadd_rn(c, __fadd_rn(e1, e2));
+  c = __fmaf_rn(a1, b1lo, c);
+  c = __fmaf_rn(a2, b2lo, c);
+}
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_wait() {
@@ -756,14 +779,31 @@ __global__ void __launch_bounds__(256, 2) gemv_tile_kernel(const GemvJob* __rest
 #pragma unroll
   for (int c = 0; c < ST - 1; ++c) issue(c);
   constexpr bool PACKED = std::is_same<CM, float2>::value && std::is_same<CV, float2>::value;
+  constexpr bool COMP = std::is_same<CM, float2>::value && std::is_same<CV, double2>::value;
   R acc[RW * NR * 2];
   unsigned long long acc2[PACKED ? RW * NR : 1];  // (re, im) pairs for the packed FP32 FMAs
+  float cs[COMP ? RW * NR * 2 : 1], cc[COMP ? RW * NR * 2 : 1];  // compensated sums: value cs + cc
 #pragma unroll
   for (int i = 0; i < RW * NR * 2; ++i) acc[i] = R(0);
 #pragma unroll
   for (int i = 0; i < (PACKED ? RW * NR : 1); ++i) acc2[i] = 0ull;
+#pragma unroll
+  for (int i = 0; i < (COMP ? RW * NR * 2 : 1); ++i) cs[i] = cc[i] = 0.0f;
   for (int ch = 0; ch < nch; ++ch) {
     cp_wait<ST - 2>();  // this thread's copies of chunk ch have landed
+    if constexpr (COMP) {
+      // each thread splits the complex128 x entries it copied, in place, into
+      // (hi, lo) complex64 pairs: x = hi + lo to 2^-48 relative
+      CV* xs = Xs + (ch & (ST - 1)) * NR * CW;
+#pragma unroll
+      for (int q = 0; q < XPT; ++q)
+        if (NR * CW % 256 == 0 || q * 256 + int(threadIdx.x) < NR * CW) {
+          const double2 v = xs[q * 256 + threadIdx.x];
+          const float hr = __double2float_rn(v.x), hi = __double2float_rn(v.y);
+          reinterpret_cast<float4*>(xs)[q * 256 + threadIdx.x] =
+              make_float4(hr, hi, __double2float_rn(v.x - double(hr)), __double2float_rn(v.y - double(hi)));
+        }
+    }
     __syncthreads();    // everyone's have, and chunk ch - 1 is consumed
     issue(ch + ST - 1); // into the slot of chunk ch - 1
     const int st = ch & (ST - 1);
@@ -793,6 +833,18 @@ __global__ void __launch_bounds__(256, 2) gemv_tile_kernel(const GemvJob* __rest
             ffma2(acc2[i * NR + r], p2[i], x2);
           }
         }
+      } else if constexpr (COMP) {
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+          const float4 xv = reinterpret_cast<const float4*>(xs)[r * CW + j * 32 + lane];
+#pragma unroll
+          for (int i = 0; i < RW; ++i) {
+            const int o = (i * NR + r) * 2;
+            const float ar = float(av[i].x), ai = float(av[i].y);
+            comp_mac(cs[o], cc[o], ar, xv.x, -ai, xv.y, xv.z, xv.w);      // re: ar xr - ai xi
+            comp_mac(cs[o + 1], cc[o + 1], ar, xv.y, ai, xv.x, xv.w, xv.z);  // im: ar xi + ai xr
+          }
+        }
       } else {
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
@@ -812,6 +864,10 @@ __global__ void __launch_bounds__(256, 2) gemv_tile_kernel(const GemvJob* __rest
       acc[2 * i] = R(lo);
       acc[2 * i + 1] = R(hi);
     }
+  }
+  if constexpr (COMP) {
+#pragma unroll
+    for (int i = 0; i < RW * NR * 2; ++i) acc[i] = R(cs[i]) + R(cc[i]);
   }
   cp_wait<0>();
   constexpr int K = RW * NR * 2;
@@ -865,10 +921,13 @@ void gemv_jobs_mixed(const GemvPlan& plan, int nrhs, cudaStream_t s) {
   const int64_t threads = plan.total_rows * 32;
   const unsigned blocks = unsigned((threads + 255) / 256);
   ScopedTimer tm(plan.name, s);
-  if (nrhs >= 2 && plan.tiles != nullptr) {
+  constexpr bool comp = std::is_same<CM, float2>::value && std::is_same<CV, double2>::value;
+  if ((nrhs >= 2 || comp) && plan.tiles != nullptr) {
     if (plan.ntiles == 0) return;
     SLDM_REQUIRE((plan.tile_rows == GemvTile<CM, CV>::ROWS), SLDM_EINVAL, "GEMV plan tiled for another vector type");
-    if (nrhs <= 2) launch_tile<CM, CV, 2>(plan, nrhs, s);
+    if (nrhs <= 1) {
+      if constexpr (comp) launch_tile<CM, CV, 1>(plan, nrhs, s);  // the only one-column use
+    } else if (nrhs <= 2) launch_tile<CM, CV, 2>(plan, nrhs, s);
     else if (nrhs <= 4) launch_tile<CM, CV, 4>(plan, nrhs, s);
     else launch_tile<CM, CV, 8>(plan, nrhs, s);
   } else if (nrhs <= 1)
