@@ -113,7 +113,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # dense.cu).
 GEMV_TRAFFIC = {
     "gemv_jobs_kernel": dict(sha="1c5c6f7e0080bcec", per_alg_byte=(424.169472e6 + 3.703040e6) / 423.936e6),
-    "gemv_tile_kernel": dict(sha="6197b6df0e88fdd4", per_alg_byte=(425.902336e6 + 3.562240e6) / 423.936e6),
+    "gemv_tile_kernel": dict(sha="43fbbe3c6438984e", per_alg_byte=(425.892608e6 + 0.485888e6) / 423.936e6),
 }
 
 

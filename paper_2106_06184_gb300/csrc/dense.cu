@@ -514,12 +514,11 @@ template void lu_solve_batched<float2>(const std::vector<LUSysT<float2>>&, cudaS
 template void lu_solve_batched<double2>(const std::vector<LUSysT<double2>>&, cudaStream_t);
 
 // ---------------------------------------------------------------- batched skinny GEMV
-// Each warp owns one row of one job and produces that row for all right-hand
-// sides of the pass.  Rows are split over jobs by an exclusive prefix sum.  The
-// matrix entries are CM (complex64 or complex128) and stream through once with
-// two 16-byte loads per lane in flight; the vectors and the accumulation are CV
-// (a complex64 matrix may be applied in FP64: the residual of iterative
-// refinement).
+// One right-hand side (instantiated with NR = 1; several go to the row-tile
+// kernel below).  Each warp owns one row of one job; rows are split over jobs
+// by an exclusive prefix sum.  The matrix entries are CM (complex64 or
+// complex128) and stream through once with two 16-byte loads per lane in
+// flight; the vectors and the accumulation are CV.
 template <class CM, class CV, int NR>
 __global__ void __launch_bounds__(256, NR == 1 ? 6 : 1) gemv_jobs_kernel(const GemvJob* __restrict__ jobs, const int64_t* __restrict__ rowstart,
                                                         int njobs, int64_t total_rows, int nrhs) {
@@ -922,20 +921,19 @@ void gemv_jobs_mixed(const GemvPlan& plan, int nrhs, cudaStream_t s) {
   const unsigned blocks = unsigned((threads + 255) / 256);
   ScopedTimer tm(plan.name, s);
   constexpr bool comp = std::is_same<CM, float2>::value && std::is_same<CV, double2>::value;
-  if ((nrhs >= 2 || comp) && plan.tiles != nullptr) {
+  if (nrhs >= 2 || comp) {
+    SLDM_REQUIRE((plan.tiles != nullptr && plan.tile_rows == GemvTile<CM, CV>::ROWS), SLDM_EINVAL,
+                 "GEMV plan without row tiles for this vector type");
     if (plan.ntiles == 0) return;
-    SLDM_REQUIRE((plan.tile_rows == GemvTile<CM, CV>::ROWS), SLDM_EINVAL, "GEMV plan tiled for another vector type");
     if (nrhs <= 1) {
       if constexpr (comp) launch_tile<CM, CV, 1>(plan, nrhs, s);  // the only one-column use
     } else if (nrhs <= 2) launch_tile<CM, CV, 2>(plan, nrhs, s);
     else if (nrhs <= 4) launch_tile<CM, CV, 4>(plan, nrhs, s);
     else launch_tile<CM, CV, 8>(plan, nrhs, s);
-  } else if (nrhs <= 1)
-    gemv_jobs_kernel<CM, CV, 1><<<blocks, 256, 0, s>>>(plan.jobs, plan.rowstart, plan.njobs, plan.total_rows, nrhs), ::sldm::count_launch();
-  else if (nrhs <= 4)
-    gemv_jobs_kernel<CM, CV, 4><<<blocks, 256, 0, s>>>(plan.jobs, plan.rowstart, plan.njobs, plan.total_rows, nrhs), ::sldm::count_launch();
-  else
-    gemv_jobs_kernel<CM, CV, 8><<<blocks, 256, 0, s>>>(plan.jobs, plan.rowstart, plan.njobs, plan.total_rows, nrhs), ::sldm::count_launch();
+  } else {
+    gemv_jobs_kernel<CM, CV, 1><<<blocks, 256, 0, s>>>(plan.jobs, plan.rowstart, plan.njobs, plan.total_rows, nrhs);
+    count_launch();
+  }
   SLDM_CUDA(cudaGetLastError());
 }
 template void gemv_jobs_mixed<float2, double2>(const GemvPlan&, int, cudaStream_t);

@@ -11,7 +11,8 @@
 //   2. lu_swap_kernel    apply the panel's row interchanges to the columns right
 //                        of the panel and to B (the L columns left of the panel
 //                        are never read again: B is carried along instead);
-//   3. lu_trsm_kernel    U12 = L11^-1 A12 (unit lower) on those columns;
+//   3. lu_trsm_kernel    U12 = L11^-1 A12 (unit lower) on those columns (one
+//                        warp per 32 columns, staged in shared memory);
 //   4. lu_gemm_kernel    A22 -= L21 U12 on the trailing rows of those columns.
 //
 // then back substitution U X = B panel by panel from the bottom (upper
@@ -252,39 +253,61 @@ __global__ void lu_swap_kernel(Cols<C> S, int j0, int nb, const int* __restrict_
 
 // ---------------------------------------------------------------- 3. triangular solves on the panel's rows
 // lower = 1: X = L11^-1 X (unit lower, L11 = A[j0.., j0..]); lower = 0: X = U11^-1 X
-// (upper, non-unit).  One thread per column; the nb x nb triangle in shared memory.
+// (upper, non-unit).  One warp per 32 columns, one thread per column: the nb x nb
+// triangle and the warp's nb x 32 block of X are staged in shared memory by
+// cp.async (every copy in flight at once), solved there and written back.  The
+// FP64 pipe (two FMA per SM per clock) bounds it, so the grid is made of many
+// small CTAs to reach every SM.
+constexpr int TRSM_COLS = 32;
+template <int N>
+__device__ __forceinline__ void cp_async_n(void* dst, const void* src) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+  if constexpr (N == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
 template <class C>
-__global__ void lu_trsm_kernel(Cols<C> S, const C* __restrict__ A, int n, int j0, int nb, int lower,
-                               const int* __restrict__ err) {
+__global__ void __launch_bounds__(TRSM_COLS) lu_trsm_kernel(Cols<C> S, const C* __restrict__ A, int n, int j0, int nb,
+                                                            int lower, const int* __restrict__ err) {
   if (*err) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* T = reinterpret_cast<C*>(smem_raw);
-  for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) T[t] = A[int64_t(j0 + t / nb) * n + j0 + t % nb];
-  __syncthreads();
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= S.count()) return;
+  C* T = reinterpret_cast<C*>(smem_raw);  // nb x nb
+  C* X = T + nb * nb;                     // nb x TRSM_COLS
+  const int t = threadIdx.x;
+  for (int e = t; e < nb * nb; e += TRSM_COLS)
+    cp_async_n<sizeof(C)>(T + e, A + int64_t(j0 + e / nb) * n + j0 + e % nb);
+  const int q = blockIdx.x * TRSM_COLS + t;
+  const bool mine = q < S.count();
   int64_t ld = 0;
-  C* col = S.col(q, ld);
-  col += int64_t(j0) * ld;
+  C* col = mine ? S.col(q, ld) + int64_t(j0) * ld : nullptr;
+  if (mine)
+    for (int k = 0; k < nb; ++k) cp_async_n<sizeof(C)>(X + k * TRSM_COLS + t, col + int64_t(k) * ld);
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  __syncthreads();
+  if (!mine) return;
+  C* x = X + t;
   if (lower) {
     for (int j = 1; j < nb; ++j) {
-      C acc = col[int64_t(j) * ld];
+      C acc = x[j * TRSM_COLS];
       for (int k = 0; k < j; ++k) {
-        const C l = T[j * nb + k], x = col[int64_t(k) * ld];
-        cfms(acc.x, acc.y, l.x, l.y, x.x, x.y);
+        const C l = T[j * nb + k], v = x[k * TRSM_COLS];
+        cfms(acc.x, acc.y, l.x, l.y, v.x, v.y);
       }
-      col[int64_t(j) * ld] = acc;
+      x[j * TRSM_COLS] = acc;
     }
   } else {
     for (int j = nb - 1; j >= 0; --j) {
-      C acc = col[int64_t(j) * ld];
+      C acc = x[j * TRSM_COLS];
       for (int k = j + 1; k < nb; ++k) {
-        const C u = T[j * nb + k], x = col[int64_t(k) * ld];
-        cfms(acc.x, acc.y, u.x, u.y, x.x, x.y);
+        const C u = T[j * nb + k], v = x[k * TRSM_COLS];
+        cfms(acc.x, acc.y, u.x, u.y, v.x, v.y);
       }
-      col[int64_t(j) * ld] = cdiv_(acc, T[j * nb + j]);
+      x[j * TRSM_COLS] = cdiv_(acc, T[j * nb + j]);
     }
   }
+  for (int k = 0; k < nb; ++k) col[int64_t(k) * ld] = x[k * TRSM_COLS];
 }
 
 // ---------------------------------------------------------------- 4. trailing update
@@ -389,7 +412,7 @@ void lu_solve_blocked(const LUSysT<C>& S, cudaStream_t s) {
   int per_sm = 0;
   SLDM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lu_panel_kernel<C>, PANEL_THREADS, panel_smem));
   SLDM_REQUIRE(per_sm >= 1, SLDM_ENOTSUP, "LU: panel kernel does not fit on an SM");
-  const size_t trsm_smem = size_t(NB) * NB * sizeof(C);
+  const size_t trsm_smem = (size_t(NB) * NB + size_t(NB) * TRSM_COLS) * sizeof(C);
   const size_t gemm_smem = size_t(2) * GT * NB * sizeof(C);
   SLDM_CUDA(cudaFuncSetAttribute(lu_trsm_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(trsm_smem)));
   SLDM_CUDA(cudaFuncSetAttribute(lu_gemm_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(gemm_smem)));
@@ -419,7 +442,8 @@ void lu_solve_blocked(const LUSysT<C>& S, cudaStream_t s) {
     const int nq = (n - j0 - nb) + r;
     if (nq > 0) {
       lu_swap_kernel<C><<<(nq + 255) / 256, 256, 0, s>>>(R, j0, nb, piv.p, err.p), count_launch();
-      lu_trsm_kernel<C><<<(nq + 127) / 128, 128, trsm_smem, s>>>(R, S.A, n, j0, nb, 1, err.p), count_launch();
+      lu_trsm_kernel<C><<<(nq + TRSM_COLS - 1) / TRSM_COLS, TRSM_COLS, trsm_smem, s>>>(R, S.A, n, j0, nb, 1, err.p),
+          count_launch();
       if (j0 + nb < n) {
         dim3 grid((nq + GT - 1) / GT, (n - j0 - nb + GT - 1) / GT);
         lu_gemm_kernel<C><<<grid, 256, gemm_smem, s>>>(R, S.A, n, j0 + nb, n, j0, j0, nb, err.p), count_launch();
@@ -433,7 +457,8 @@ void lu_solve_blocked(const LUSysT<C>& S, cudaStream_t s) {
     const int npan = (n + NB - 1) / NB;
     for (int p = npan - 1; p >= 0; --p) {
       const int j0 = p * NB, nb = std::min(NB, n - j0);
-      lu_trsm_kernel<C><<<(r + 127) / 128, 128, trsm_smem, s>>>(Bc, S.A, n, j0, nb, 0, err.p), count_launch();
+      lu_trsm_kernel<C><<<(r + TRSM_COLS - 1) / TRSM_COLS, TRSM_COLS, trsm_smem, s>>>(Bc, S.A, n, j0, nb, 0, err.p),
+          count_launch();
       if (j0 > 0) {
         dim3 grid((r + GT - 1) / GT, (j0 + GT - 1) / GT);
         lu_gemm_kernel<C><<<grid, 256, gemm_smem, s>>>(Bc, S.A, n, 0, j0, j0, j0, nb, err.p), count_launch();
