@@ -217,9 +217,11 @@ int sldm_apply(const sldm_op* op, const void* x, void* y, int32_t nrhs, int32_t 
 int sldm_rhs_planewave(const sldm_op* op, const double* khat, const double* pol, int32_t nrhs,
                        void* b, int32_t where, void* stream);
 
-/* Solve Z x = b by restarted GMRES with FP64 Arnoldi (classical Gram-Schmidt
- * twice) and Givens rotations (Sec. IV, GMRES), matrix-vector products in the
- * operator's precision, right-preconditioned by P of Eq. pcext (Sec. III:
+/* Solve Z x = b by restarted GMRES with Arnoldi by classical Gram-Schmidt
+ * twice and Givens rotations in FP64 (Sec. IV, GMRES); the matrix-vector
+ * products, the Krylov basis and the preconditioner's Schur inverses are held
+ * in the operator's precision (complex64 operators: FP32 Gram-Schmidt with
+ * FP64 sums across threads), right-preconditioned by P of Eq. pcext (Sec. III:
  * diagonals of the blocks, with the analytic block inverse through the Schur
  * complement of the charge block, formed per object at assembly).  Up to 8
  * right-hand sides run in lockstep, each with its own Krylov basis, sharing one
@@ -231,7 +233,8 @@ int sldm_rhs_planewave(const sldm_op* op, const double* khat, const double* pol,
  * reported relres refer to ||Dr (b - Z x)|| / ||Dr b||.
  * Complex64 operators (unless refine = SLDM_REFINE_OFF): iterative refinement
  * with an FP64 residual.  The residual at every restart is the product of the
- * stored complex64 blocks with complex128 vectors, accumulated in FP64, and each
+ * stored complex64 blocks with complex128 vectors, accumulated to ~48 bits
+ * (exactly split products in compensated FP32 sums), and each
  * GMRES cycle (products in complex64) stops once it has reduced that residual
  * by 1e-5; tol then refers to the FP64 residual of the stored operator.
  * Returns SLDM_ENOTCONV (x holds the last iterate) if tol is not reached. */

@@ -169,7 +169,8 @@ static void apply_dev(const sldm_op* op_, const double2* x, double2* y, int nrhs
   }
 }
 
-// acc64: a complex64 operator's product accumulated in FP64 (iterative refinement)
+// acc64: a complex64 operator's product with complex128 vectors, accumulated to
+// ~48 bits (compensated FP32 sums of exactly split products; iterative refinement)
 static void apply_any(const sldm_op* op, const double2* x, double2* y, int nrhs, cudaStream_t s, bool acc64 = false) {
   ScopedTimer tm("apply", s);
   if (op->prec == SLDM_PREC_F32) {
@@ -452,7 +453,7 @@ static double dnorm(sldm_op* op, const double2* v, cudaStream_t s) {
 // the products of one step are made together (one multi-RHS pass over the
 // blocks).  Right-hand sides in op->wb, initial guesses in op->wx (N x nr);
 // relres[r] = ||Dr (b_r - Z x_r)|| / ||Dr b_r||.  With `refine` (complex64
-// operators) the true residual at every restart is accumulated in FP64 and each
+// operators) the true residual at every restart is accumulated to ~48 bits and each
 // cycle stops once it has reduced that residual by REFINE_CYCLE: the cycles are
 // the correction solves of iterative refinement, in the operator's precision.
 // CB is the storage of the Krylov bases (complex64 for complex64 operators,

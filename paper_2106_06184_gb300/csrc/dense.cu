@@ -5,7 +5,8 @@
 //    pass) streaming row-major complex blocks once per pass: the HBM-bound
 //    matrix-vector product that drives GMRES;
 //  - the sparse/elementwise glue of the structured product Z x (Eq. finalsystem);
-//  - FP64 vector kernels for GMRES (Arnoldi by classical Gram-Schmidt twice).
+//  - vector kernels for GMRES (Arnoldi by classical Gram-Schmidt twice), in the
+//    Krylov basis' precision, batched over the lockstep right-hand sides.
 #include <algorithm>
 #include <atomic>
 #include <type_traits>
