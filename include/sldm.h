@@ -65,12 +65,21 @@ extern "C" {
 #define SLDM_ECUDA -5      /* a CUDA runtime call failed */
 #define SLDM_EBUSY -6      /* the handle is in use */
 #define SLDM_ENOTSUP -7    /* feature not available in this build */
+#define SLDM_ETIMEOUT -8   /* a bounded wait inside a kernel ran out (the context stays usable) */
 
 #define SLDM_HOST 0
 #define SLDM_DEVICE 1
 
 #define SLDM_PREC_F64 0    /* complex128 operator, FP64 fill */
 #define SLDM_PREC_F32 1    /* complex64 operator, FP32 bulk fill, FP64 singular terms */
+/* complex64 operator with an FP64-accurate residual: every block is filled (and
+ * Y11, Y21 factored) in FP64, then kept as two complex64 parts hi = fl32(v) and
+ * lo = fl32(v - hi), so v = hi + lo to ~2^-48 relative.  GMRES cycles apply hi in
+ * FP32 arithmetic; the residual of iterative refinement, and sldm_apply, apply
+ * hi + lo with compensated FP32 sums (~48 bits), so refined solutions converge to
+ * those of the FP64 discrete system.  Twice the operator memory of SLDM_PREC_F32
+ * (the same as SLDM_PREC_F64). */
+#define SLDM_PREC_F32X2 2
 
 #define SLDM_BOTTOM_HALFSPACE 0
 #define SLDM_BOTTOM_PEC 1
@@ -101,7 +110,7 @@ typedef struct {
 } sldm_mesh_info;
 
 typedef struct {
-  int32_t precision;    /* SLDM_PREC_F64 or SLDM_PREC_F32 */
+  int32_t precision;    /* SLDM_PREC_F64, SLDM_PREC_F32 or SLDM_PREC_F32X2 */
   int32_t reserved;
   void* stream;         /* stream the fill runs on (NULL = default) */
 } sldm_assemble_opts;
@@ -206,7 +215,9 @@ int sldm_op_table(const sldm_op* op, int32_t which, void* dst, int64_t* dims, do
 
 /* y = Z x for nrhs right-hand sides (Eq. finalsystem), column-major N x nrhs
  * complex128 with leading dimension N.  Z is applied in its structured form:
- * global L^A_m, L^phi_m products plus per-object blocks, never a dense Z. */
+ * global L^A_m, L^phi_m products plus per-object blocks, never a dense Z.
+ * SLDM_PREC_F32 operators multiply in FP32; SLDM_PREC_F32X2 operators apply
+ * hi + lo with ~48-bit compensated sums (the FP64 operator). */
 int sldm_apply(const sldm_op* op, const void* x, void* y, int32_t nrhs, int32_t where, void* stream);
 
 /* Right-hand sides for plane waves (Eq. finalsystem right-hand side):
@@ -236,7 +247,9 @@ int sldm_rhs_planewave(const sldm_op* op, const double* khat, const double* pol,
  * stored complex64 blocks with complex128 vectors, accumulated to ~48 bits
  * (exactly split products in compensated FP32 sums), and each
  * GMRES cycle (products in complex64) stops once it has reduced that residual
- * by 1e-5; tol then refers to the FP64 residual of the stored operator.
+ * by 1e-5; tol then refers to the FP64 residual of the stored operator.  With
+ * SLDM_PREC_F32X2 the residual's operator is hi + lo, the FP64 fill, so tol
+ * refers to the FP64 discrete system itself (as with SLDM_PREC_F64).
  * Returns SLDM_ENOTCONV (x holds the last iterate) if tol is not reached. */
 int sldm_solve(const sldm_op* op, const void* b, void* x, int32_t nrhs, const sldm_solve_opts* opts,
                sldm_solve_info* info, int32_t where, void* stream);
@@ -270,7 +283,10 @@ int sldm_farfield(const sldm_op* op, const void* x, int32_t where, const double*
  *    on the GPU (different streams, or different threads) race and must be
  *    serialised by the caller.
  *  - The first call on a device resolves the array's device address with that
- *    device current; make that first call before any stream capture begins. */
+ *    device current; make that first call before any stream capture begins.
+ *    The address is kept for the life of the process: after cudaDeviceReset (or
+ *    anything else that destroys the device's primary context) it is stale, so
+ *    do not use this entry point on that device again in the same process. */
 int sldm_kbar_noalloc(const sldm_mesh* mesh, int32_t obj, double k_re, double k_im, void* K_out, void* stream);
 
 /* Kernel timers (profiling aid, Sec. IV "CPU time breakdown" counterpart):
@@ -290,6 +306,29 @@ int sldm_timer_names(char* buf, size_t len);
  * kernel, timed or not), for counting the launches of a timed region.
  * The paper has no counterpart.  SLDM_EINVAL if out is NULL. */
 int sldm_launch_count(int64_t* out);
+
+/* Device-memory budget (the paper has no counterpart; it serves admission
+ * control when many operators share one GPU).  The library counts the bytes of
+ * every device buffer it holds, over all handles and devices; with a budget of
+ * `bytes` > 0 an allocation that would take the count above it fails, and the
+ * call that made it returns SLDM_ENOMEM having released what it took.  0 (the
+ * default) means no limit.  Buffers already held are not affected by a smaller
+ * budget.  SLDM_EINVAL if bytes < 0. */
+int sldm_set_device_budget(int64_t bytes);
+/* Bytes of device memory the library holds now (all handles, all devices). */
+int sldm_device_bytes(int64_t* in_use);
+
+/* Fault injection for tests of the failure paths (no counterpart in the paper).
+ * SLDM_INJECT_LU_STALL: the next `count` launches of the batched direct solver
+ * (the cooperative LU of M_l and of the preconditioner's Schur complements) make
+ * their first CTA wait first on a device flag that nothing sets.  That wait is
+ * bounded like every wait of the solver (a few hundred ms); when it runs out the
+ * CTA records the failure, every other CTA leaves at its next wait, and the call
+ * that launched the solver (sldm_assemble) returns SLDM_ETIMEOUT.  No fault is
+ * raised and the CUDA context stays usable.  count = 0 clears the injection.
+ * SLDM_EINVAL for an unknown `what` or a negative count. */
+#define SLDM_INJECT_LU_STALL 1
+int sldm_test_inject(int32_t what, int32_t count);
 
 #ifdef __cplusplus
 }

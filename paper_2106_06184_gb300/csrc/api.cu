@@ -35,7 +35,8 @@ struct ObjInfo {
 
 struct sldm_op {
   const sldm_mesh* mesh = nullptr;
-  int prec = SLDM_PREC_F64;
+  int prec = SLDM_PREC_F64;   // storage of the solver's operator: SLDM_PREC_F64 or SLDM_PREC_F32
+  bool x2 = false;            // SLDM_PREC_F32X2: complex64 operator plus the low parts of an FP64 fill
   size_t esz = 16;
   double k0 = 0, freq = 0;
   int device = 0;
@@ -43,6 +44,7 @@ struct sldm_op {
   sldm::cplx kb, eps_b;
   double mu_b = 1;
   sldm::DBuf<char> LAm, LPm, loc;
+  sldm::DBuf<char> LAm_lo, LPm_lo, loc_lo;  // SLDM_PREC_F32X2: FP64 value - complex64 value, in complex64
   std::vector<sldm::ObjInfo> obj;
   sldm::DBuf<double> ix_val;
   // structured product: work vectors for up to WR right-hand sides per pass
@@ -77,7 +79,8 @@ struct sldm_op {
 namespace sldm {
 
 static int64_t op_bytes(const sldm_op* op) {
-  return int64_t(op->LAm.bytes() + op->LPm.bytes() + op->loc.bytes() + op->ix_val.bytes() + op->V.bytes() +
+  return int64_t(op->LAm.bytes() + op->LPm.bytes() + op->loc.bytes() + op->LAm_lo.bytes() + op->LPm_lo.bytes() +
+                 op->loc_lo.bytes() + op->ix_val.bytes() + op->V.bytes() +
                  op->pc.sinv.bytes() + op->pc.sinv32.bytes() + op->pc.lam.bytes() + op->pc.pdiag.bytes());
 }
 
@@ -90,17 +93,23 @@ static void make_plans(sldm_op* op, size_t es_m, size_t es_v, DBuf<GemvJob>& dj1
   auto P = [&](DBuf<char>& b, int64_t off) { return (void*)(b.p + off * es_v); };
   const char* loc = op->loc.p;
   auto L = [&](int64_t off) { return (const void*)(loc + off * es_m); };
+  // the low parts (SLDM_PREC_F32X2) enter only the FP64-accumulated products
+  const bool lo = op->x2 && es_v == sizeof(double2);
+  auto Lo = [&](int64_t off) { return lo ? (const void*)(op->loc_lo.p + off * es_m) : nullptr; };
+  const void* LAlo = lo ? op->LAm_lo.p : nullptr;
+  const void* LPlo = lo ? op->LPm_lo.p : nullptr;
   std::vector<GemvJob> j1, j2;
   for (auto& o : op->obj) {
-    j1.push_back({L(o.oY11), o.ne, o.ne, o.ne, P(op->we, o.e0), ne, P(op->wt1, o.e0), ne, 1, 0, 0, 0});
-    if (o.nq > 0) j1.push_back({L(o.oY21), o.ne, o.nq, o.ne, P(op->we, o.e0), ne, P(op->wt2, o.q0), nq, 1, 0, 0, 0});
+    j1.push_back({L(o.oY11), o.ne, o.ne, o.ne, P(op->we, o.e0), ne, P(op->wt1, o.e0), ne, 1, 0, 0, 0, Lo(o.oY11)});
+    if (o.nq > 0)
+      j1.push_back({L(o.oY21), o.ne, o.nq, o.ne, P(op->we, o.e0), ne, P(op->wt2, o.q0), nq, 1, 0, 0, 0, Lo(o.oY21)});
   }
-  j2.push_back({op->LAm.p, ne, int32_t(ne), int32_t(ne), P(op->wa, 0), ne, P(op->wz1, 0), ne, 1, 0, 0, 0});
-  j2.push_back({op->LPm.p, nt, int32_t(nt), int32_t(nt), P(op->wbc, 0), nt, P(op->wz2, 0), nt, 1, 0, 0, 0});
+  j2.push_back({op->LAm.p, ne, int32_t(ne), int32_t(ne), P(op->wa, 0), ne, P(op->wz1, 0), ne, 1, 0, 0, 0, LAlo});
+  j2.push_back({op->LPm.p, nt, int32_t(nt), int32_t(nt), P(op->wbc, 0), nt, P(op->wz2, 0), nt, 1, 0, 0, 0, LPlo});
   for (auto& o : op->obj) {
-    j2.push_back({L(o.oLA), o.ne, o.ne, o.ne, P(op->wj, o.e0), ne, P(op->ww1, o.e0), ne, 1, 0, 0, 0});
-    j2.push_back({L(o.oK), o.ne, o.ne, o.ne, P(op->we, o.e0), ne, P(op->ww2, o.e0), ne, 1, 0, 0, 0});
-    j2.push_back({L(o.oLP), o.nt, o.nt, o.nt, P(op->wbu, o.t0), nt, P(op->ww3, o.t0), nt, 1, 0, 0, 0});
+    j2.push_back({L(o.oLA), o.ne, o.ne, o.ne, P(op->wj, o.e0), ne, P(op->ww1, o.e0), ne, 1, 0, 0, 0, Lo(o.oLA)});
+    j2.push_back({L(o.oK), o.ne, o.ne, o.ne, P(op->we, o.e0), ne, P(op->ww2, o.e0), ne, 1, 0, 0, 0, Lo(o.oK)});
+    j2.push_back({L(o.oLP), o.nt, o.nt, o.nt, P(op->wbu, o.t0), nt, P(op->ww3, o.t0), nt, 1, 0, 0, 0, Lo(o.oLP)});
   }
   auto mk = [&](std::vector<GemvJob>& j, DBuf<GemvJob>& dj, DBuf<int64_t>& drs, DBuf<int2>& dt, GemvPlan& plan) {
     std::vector<int64_t> rs(j.size());
@@ -121,6 +130,7 @@ static void make_plans(sldm_op* op, size_t es_m, size_t es_v, DBuf<GemvJob>& dj1
     plan.tiles = dt.p;
     plan.ntiles = int(tiles.size());
     plan.tile_rows = gemv_tile_rows(es_v);
+    plan.has_lo = lo;
   };
   mk(j1, dj1, drs1, dt1, p1);
   mk(j2, dj2, drs2, dt2, p2);
@@ -231,8 +241,10 @@ static std::vector<int> repeated_objects(const HostMesh& h, const sldm_material*
   return ref;
 }
 
+// finish = false: stop before the GEMV plans and the preconditioner (the
+// caller converts the operator first, see split_to_x2)
 template <class R>
-static void assemble_impl(sldm_op* op, const sldm_material* mats, cudaStream_t s) {
+static void assemble_impl(sldm_op* op, const sldm_material* mats, cudaStream_t s, bool finish = true) {
   typedef typename std::conditional<sizeof(R) == 4, float2, double2>::type C;
   const sldm_mesh* m = op->mesh;
   const HostMesh& h = m->h;
@@ -400,6 +412,7 @@ static void assemble_impl(sldm_op* op, const sldm_material* mats, cudaStream_t s
     mgf_fill_reflected<C>(m, op->H, omega, op->T, op->LAm.p, op->ne, op->LPm.p, op->nt, s);
     SLDM_CUDA(cudaStreamSynchronize(s));
   }
+  if (!finish) return;
   build_plans<C>(op);
   // ---- preconditioner P (Eq. pcext): diagonals and the per-object Schur complement inverses
   {
@@ -408,6 +421,36 @@ static void assemble_impl(sldm_op* op, const sldm_material* mats, cudaStream_t s
     prec_setup<C>(op->pc, m, po, op->k0, op->LAm.p, op->LPm.p, op->loc.p, op->ix_val.p, s);
     op->pc.ready = true;
   }
+  SLDM_CUDA(cudaStreamSynchronize(s));
+}
+
+// SLDM_PREC_F32X2: the operator filled and factored in FP64 is kept as complex64
+// pairs, hi = fl32(v) and lo = fl32(v - hi), so that v = hi + lo to ~2^-48.  The
+// GMRES cycles apply hi (complex64, FP32 arithmetic); the residual of iterative
+// refinement applies hi + lo with compensated FP32 sums, i.e. the FP64 operator.
+static void split_to_x2(sldm_op* op, cudaStream_t s) {
+  auto split = [&](DBuf<char>& full, DBuf<char>& lo) {
+    const int64_t n = int64_t(full.bytes() / sizeof(double2));
+    DBuf<char> hi;
+    hi.alloc(size_t(n) * sizeof(float2));
+    lo.alloc(size_t(n) * sizeof(float2));
+    split_c128(reinterpret_cast<const double2*>(full.p), n, reinterpret_cast<float2*>(hi.p),
+               reinterpret_cast<float2*>(lo.p), s);
+    SLDM_CUDA(cudaStreamSynchronize(s));
+    std::swap(full.p, hi.p);  // full now holds hi; the complex128 copy leaves with `hi`
+    std::swap(full.n, hi.n);
+  };
+  split(op->LAm, op->LAm_lo);
+  split(op->LPm, op->LPm_lo);
+  split(op->loc, op->loc_lo);
+  op->prec = SLDM_PREC_F32;
+  op->esz = sizeof(float2);
+  op->x2 = true;
+  build_plans<float2>(op);
+  std::vector<PrecObj> po;
+  for (auto& oi : op->obj) po.push_back({oi.e0, oi.ne, oi.t0, oi.nt, oi.q0, 0, oi.oLA, oi.oK, oi.oLP});
+  prec_setup<float2>(op->pc, op->mesh, po, op->k0, op->LAm.p, op->LPm.p, op->loc.p, op->ix_val.p, s);
+  op->pc.ready = true;
   SLDM_CUDA(cudaStreamSynchronize(s));
 }
 
@@ -769,8 +812,10 @@ int sldm_assemble(const sldm_mesh* m, const sldm_stack* st, const sldm_material*
   auto* op = new sldm_op();
   try {
     op->mesh = m;
-    op->prec = opts ? opts->precision : SLDM_PREC_F64;
-    SLDM_REQUIRE(op->prec == SLDM_PREC_F64 || op->prec == SLDM_PREC_F32, SLDM_EINVAL, "assemble: unknown precision");
+    const int prec = opts ? opts->precision : SLDM_PREC_F64;
+    SLDM_REQUIRE(prec == SLDM_PREC_F64 || prec == SLDM_PREC_F32 || prec == SLDM_PREC_F32X2, SLDM_EINVAL,
+                 "assemble: unknown precision");
+    op->prec = prec == SLDM_PREC_F32 ? SLDM_PREC_F32 : SLDM_PREC_F64;  // X2 fills in FP64, then splits
     op->esz = op->prec == SLDM_PREC_F32 ? 8 : 16;
     op->freq = freq_hz;
     op->device = dev;
@@ -823,8 +868,14 @@ int sldm_assemble(const sldm_mesh* m, const sldm_stack* st, const sldm_material*
     op->kb = op->k0 * std::sqrt(op->eps_b * op->mu_b);
     cudaStream_t s = opts ? (cudaStream_t)opts->stream : 0;
     ScopedTimer tm("assemble", s);
-    if (op->prec == SLDM_PREC_F32) assemble_impl<float>(op, per_obj, s);
-    else assemble_impl<double>(op, per_obj, s);
+    if (op->prec == SLDM_PREC_F32) {
+      assemble_impl<float>(op, per_obj, s);
+    } else if (prec == SLDM_PREC_F32X2) {
+      assemble_impl<double>(op, per_obj, s, false);
+      split_to_x2(op, s);
+    } else {
+      assemble_impl<double>(op, per_obj, s);
+    }
   } catch (...) {
     delete op;
     throw;
@@ -841,7 +892,7 @@ int sldm_op_info_get(const sldm_op* op, sldm_op_info* info) {
   info->nt = op->nt;
   info->nobj = op->nobj;
   info->device_bytes = op_bytes(op);
-  info->precision = op->prec;
+  info->precision = op->x2 ? SLDM_PREC_F32X2 : op->prec;
   info->k0 = op->k0;
   API_END
 }
@@ -888,8 +939,17 @@ int sldm_op_block(const sldm_op* op, int32_t which, int32_t obj, void* dst, int3
     tmp.alloc(n);
     d = tmp.p;
   }
-  if (op->prec == SLDM_PREC_F32) to_c128<float2>(src, n, d, 0);
-  else to_c128<double2>(src, n, d, 0);
+  if (op->prec == SLDM_PREC_F32) {
+    to_c128<float2>(src, n, d, 0);
+    if (op->x2) {  // the FP64 value: hi + lo
+      const char* lo = which == SLDM_BLOCK_LAM   ? op->LAm_lo.p
+                       : which == SLDM_BLOCK_LPM ? op->LPm_lo.p
+                                                 : op->loc_lo.p + (src - op->loc.p);
+      add_lo_c128(reinterpret_cast<const float2*>(lo), n, d, 0);
+    }
+  } else {
+    to_c128<double2>(src, n, d, 0);
+  }
   if (where == SLDM_HOST) SLDM_CUDA(cudaMemcpy(dst, d, n * sizeof(double2), cudaMemcpyDeviceToHost));
   SLDM_CUDA(cudaDeviceSynchronize());
   API_END
@@ -930,14 +990,15 @@ int sldm_apply(const sldm_op* op, const void* x, void* y, int32_t nrhs, int32_t 
   SLDM_REQUIRE(op && x && y && nrhs >= 1, SLDM_EINVAL, "apply: invalid arguments");
   cudaStream_t s = (cudaStream_t)stream;
   const size_t bytes = size_t(op->N) * nrhs * sizeof(double2);
+  // SLDM_PREC_F32X2: the product of the FP64 operator (hi + lo, compensated FP32 sums)
   if (where == SLDM_DEVICE) {
-    apply_any(op, (const double2*)x, (double2*)y, nrhs, s);
+    apply_any(op, (const double2*)x, (double2*)y, nrhs, s, op->x2);
   } else {
     DBuf<double2> dx, dy;
     dx.alloc(size_t(op->N) * nrhs);
     dy.alloc(size_t(op->N) * nrhs);
     SLDM_CUDA(cudaMemcpyAsync(dx.p, x, bytes, cudaMemcpyHostToDevice, s));
-    apply_any(op, dx.p, dy.p, nrhs, s);
+    apply_any(op, dx.p, dy.p, nrhs, s, op->x2);
     SLDM_CUDA(cudaMemcpyAsync(y, dy.p, bytes, cudaMemcpyDeviceToHost, s));
     SLDM_CUDA(cudaStreamSynchronize(s));
   }

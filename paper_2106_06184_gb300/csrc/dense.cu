@@ -253,10 +253,13 @@ __global__ void __launch_bounds__(LU_THREADS) lu_coop_kernel(const LUSysT<C>* __
                                                              const LUGroup* __restrict__ groups, const int* __restrict__ cta_group,
                                                              C* diag_all, int* pivrow_all, unsigned* flag_all,
                                                              const int64_t* __restrict__ off, unsigned* ctr, int* err,
-                                                             int max_own) {
+                                                             int max_own, const unsigned* stall_flag) {
   typedef decltype(diag_all->x) R;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* smem = reinterpret_cast<C*>(smem_raw);
+  // injected failure (sldm_test_inject): CTA 0 first waits on a flag that nothing
+  // sets; the wait runs out, records err = 2 and every CTA leaves at its next wait
+  if (stall_flag != nullptr && blockIdx.x == 0 && !wait_at_least(stall_flag, 1u, err)) return;
   const int gid = cta_group[blockIdx.x];
   const LUGroup G = groups[gid];
   const int rank = blockIdx.x - G.cta0;
@@ -483,7 +486,7 @@ void lu_solve_batched(const std::vector<LUSysT<C>>& all, cudaStream_t s) {
   pivrow.alloc(dtot);
   flags.alloc(dtot);
   flags.zero(s);
-  ctr.alloc(groups.size());
+  ctr.alloc(groups.size() + 1);  // one more: the flag of an injected stall, never set
   ctr.zero(s);
   err.alloc(1);
   err.zero(s);
@@ -498,8 +501,9 @@ void lu_solve_batched(const std::vector<LUSysT<C>>& all, cudaStream_t s) {
   unsigned* a8 = ctr.p;
   int* a9 = err.p;
   int a10 = max_own;
+  const unsigned* a11 = take_lu_stall() ? ctr.p + groups.size() : nullptr;
   void* args[] = {(void*)&a0, (void*)&a1, (void*)&a2, (void*)&a3, (void*)&a4, (void*)&a5,
-                  (void*)&a6, (void*)&a7, (void*)&a8, (void*)&a9, (void*)&a10};
+                  (void*)&a6, (void*)&a7, (void*)&a8, (void*)&a9, (void*)&a10, (void*)&a11};
   {
     ScopedTimer tm("lu_coop", s);
     SLDM_CUDA(cudaLaunchCooperativeKernel((void*)lu_coop_kernel<C>, dim3(G), dim3(LU_THREADS), args, smem, s));
@@ -508,7 +512,7 @@ void lu_solve_batched(const std::vector<LUSysT<C>>& all, cudaStream_t s) {
   int herr = 0;
   SLDM_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
   SLDM_CUDA(cudaStreamSynchronize(s));
-  SLDM_REQUIRE(herr != 2, SLDM_ECUDA, "LU: a wait for a published column ran out of its limit");
+  SLDM_REQUIRE(herr != 2, SLDM_ETIMEOUT, "LU: a wait for a published column ran out of its limit");
   SLDM_REQUIRE(herr == 0, SLDM_ENUMERIC, "LU of M_l: zero or non-finite pivot");
 }
 template void lu_solve_batched<float2>(const std::vector<LUSysT<float2>>&, cudaStream_t);
@@ -627,9 +631,10 @@ struct GemvTile {
   static constexpr int ST = 4;                         // pipeline stages
   static constexpr int ROWS = 8 * RW;                  // rows per CTA
   static constexpr size_t a_stage = size_t(8) * RW * CW * sizeof(CM);
-  template <int NR>
+  // LO: a second matrix tile (the low parts) per stage
+  template <int NR, bool LO = false>
   static constexpr size_t smem() {
-    return size_t(ST) * (a_stage + size_t(NR) * CW * sizeof(CV));
+    return size_t(ST) * ((LO ? 2 : 1) * a_stage + size_t(NR) * CW * sizeof(CV));
   }
 };
 static_assert(GemvTile<float2, float2>::ROWS == 32 && GemvTile<double2, double2>::ROWS == 16, "tile rows");
@@ -705,31 +710,38 @@ __device__ __forceinline__ void warp_tsum(R (&v)[K], int lane) {
   }
 }
 
-template <class CM, class CV, int NR>
-__global__ void __launch_bounds__(256, 2) gemv_tile_kernel(const GemvJob* __restrict__ jobs, const int2* __restrict__ tiles,
-                                                          int nrhs) {
+// LO (complex64 blocks with complex128 vectors only): the job's Alo block streams
+// beside A through the same pipeline, and its products with the high part of x
+// join the error sum, so the result is that of the FP64 operator A + Alo.
+template <class CM, class CV, int NR, bool LO = false>
+__global__ void __launch_bounds__(256, LO ? 1 : 2) gemv_tile_kernel(const GemvJob* __restrict__ jobs,
+                                                                   const int2* __restrict__ tiles, int nrhs) {
   typedef GemvTile<CM, CV> T;
   typedef typename CT<CV>::R R;
   constexpr int RW = T::RW, CW = T::CW, ST = T::ST;
+  constexpr size_t a_all = (LO ? 2 : 1) * T::a_stage;     // matrix bytes per stage
   extern __shared__ __align__(16) unsigned char gsm[];
-  CM* As = reinterpret_cast<CM*>(gsm);                     // [ST][8 warps][RW][2][32]
-  CV* Xs = reinterpret_cast<CV*>(gsm + ST * T::a_stage);   // [ST][NR][CW]
+  CM* As = reinterpret_cast<CM*>(gsm);                     // [ST][8 warps][RW][2][32] (+ the same for Alo)
+  CV* Xs = reinterpret_cast<CV*>(gsm + ST * a_all);        // [ST][NR][CW]
   const int2 t = tiles[blockIdx.x];
   const GemvJob J = jobs[t.x];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int row0 = t.y + warp * RW;
   const CM* __restrict__ A = reinterpret_cast<const CM*>(J.A);
+  const CM* __restrict__ Alo = reinterpret_cast<const CM*>(LO ? J.Alo : J.A);
   const CV* __restrict__ x = reinterpret_cast<const CV*>(J.x);
   const int nch = (J.n + CW - 1) / CW;
   // per-thread copy sources (row 0 / right-hand side 0 stand in for rows or
   // right-hand sides outside the job: valid addresses, copied as zeros) and
   // shared-memory destinations in stage 0
   const CM* asrc[RW];
+  int64_t aoff[RW];  // element offset of this lane's entry of row i (the same in Alo)
   bool arow[RW];
 #pragma unroll
   for (int i = 0; i < RW; ++i) {
     arow[i] = row0 + i < J.m;
-    asrc[i] = A + int64_t(arow[i] ? row0 + i : 0) * J.lda + lane;
+    aoff[i] = int64_t(arow[i] ? row0 + i : 0) * J.lda + lane;
+    asrc[i] = A + aoff[i];
   }
   constexpr int XPT = (NR * CW + 255) / 256;  // x entries per thread per chunk
   const CV* xsrc[XPT];
@@ -748,12 +760,17 @@ __global__ void __launch_bounds__(256, 2) gemv_tile_kernel(const GemvJob* __rest
   auto issue = [&](int ch) {
     if (ch < nch) {
       const int st = ch & (ST - 1), c0 = ch * CW;
-      const unsigned ad = a_dst + st * unsigned(T::a_stage), xd = x_dst + st * x_stage;
+      const unsigned ad = a_dst + st * unsigned(a_all), xd = x_dst + st * x_stage;
       if (c0 + CW <= J.n) {  // a whole chunk: only row / right-hand-side validity
 #pragma unroll
         for (int i = 0; i < RW; ++i)
 #pragma unroll
-          for (int j = 0; j < 2; ++j) cp_async_s<sizeof(CM)>(ad + (i * 2 + j) * 32 * sizeof(CM), asrc[i] + c0 + j * 32, arow[i]);
+          for (int j = 0; j < 2; ++j) {
+            cp_async_s<sizeof(CM)>(ad + (i * 2 + j) * 32 * sizeof(CM), asrc[i] + c0 + j * 32, arow[i]);
+            if constexpr (LO)
+              cp_async_s<sizeof(CM)>(ad + unsigned(T::a_stage) + (i * 2 + j) * 32 * sizeof(CM), Alo + aoff[i] + c0 + j * 32,
+                                     arow[i]);
+          }
 #pragma unroll
         for (int q = 0; q < XPT; ++q)
           if (NR * CW % 256 == 0 || q * 256 + int(threadIdx.x) < NR * CW)
@@ -765,6 +782,9 @@ __global__ void __launch_bounds__(256, 2) gemv_tile_kernel(const GemvJob* __rest
           for (int j = 0; j < 2; ++j) {
             const bool ok = arow[i] && c0 + j * 32 + lane < J.n;
             cp_async_s<sizeof(CM)>(ad + (i * 2 + j) * 32 * sizeof(CM), ok ? asrc[i] + c0 + j * 32 : A, ok);
+            if constexpr (LO)
+              cp_async_s<sizeof(CM)>(ad + unsigned(T::a_stage) + (i * 2 + j) * 32 * sizeof(CM),
+                                     ok ? Alo + aoff[i] + c0 + j * 32 : Alo, ok);
           }
 #pragma unroll
         for (int q = 0; q < XPT; ++q)
@@ -807,7 +827,8 @@ __global__ void __launch_bounds__(256, 2) gemv_tile_kernel(const GemvJob* __rest
     __syncthreads();    // everyone's have, and chunk ch - 1 is consumed
     issue(ch + ST - 1); // into the slot of chunk ch - 1
     const int st = ch & (ST - 1);
-    const CM* a = As + (st * 8 + warp) * RW * CW;
+    const CM* a = reinterpret_cast<const CM*>(gsm + st * a_all) + warp * RW * CW;
+    const CM* alo = reinterpret_cast<const CM*>(gsm + st * a_all + T::a_stage) + warp * RW * CW;
     const CV* xs = Xs + st * NR * CW;
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
@@ -834,6 +855,11 @@ __global__ void __launch_bounds__(256, 2) gemv_tile_kernel(const GemvJob* __rest
           }
         }
       } else if constexpr (COMP) {
+        CM lv[RW];
+        if constexpr (LO) {
+#pragma unroll
+          for (int i = 0; i < RW; ++i) lv[i] = alo[(i * 2 + j) * 32 + lane];
+        }
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
           const float4 xv = reinterpret_cast<const float4*>(xs)[r * CW + j * 32 + lane];
@@ -843,6 +869,11 @@ __global__ void __launch_bounds__(256, 2) gemv_tile_kernel(const GemvJob* __rest
             const float ar = float(av[i].x), ai = float(av[i].y);
             comp_mac(cs[o], cc[o], ar, xv.x, -ai, xv.y, xv.z, xv.w);      // re: ar xr - ai xi
             comp_mac(cs[o + 1], cc[o + 1], ar, xv.y, ai, xv.x, xv.w, xv.z);  // im: ar xi + ai xr
+            if constexpr (LO) {  // + Alo x_hi: terms of 2^-24 relative, the rounding of their sum is below 2^-48
+              const float lr = float(lv[i].x), li = float(lv[i].y);
+              cc[o] = __fmaf_rn(lr, xv.x, __fmaf_rn(-li, xv.y, cc[o]));
+              cc[o + 1] = __fmaf_rn(lr, xv.y, __fmaf_rn(li, xv.x, cc[o + 1]));
+            }
           }
         }
       } else {
@@ -899,19 +930,21 @@ __global__ void __launch_bounds__(256, 2) gemv_tile_kernel(const GemvJob* __rest
   }
 }
 
-template <class CM, class CV, int NR>
+template <class CM, class CV, int NR, bool LO = false>
 static void launch_tile(const GemvPlan& plan, int nrhs, cudaStream_t s) {
   typedef GemvTile<CM, CV> T;
-  constexpr size_t smem = T::template smem<NR>();
+  constexpr size_t smem = T::template smem<NR, LO>();
+  static_assert(smem <= 227 * 1024, "tile kernel exceeds the shared memory of one CTA");
   static std::atomic<uint64_t> done{0};  // devices whose attribute is set
   int dev = 0;
   SLDM_CUDA(cudaGetDevice(&dev));
   const uint64_t bit = uint64_t(1) << (dev & 63);
   if (!(done.load() & bit)) {
-    SLDM_CUDA(cudaFuncSetAttribute(gemv_tile_kernel<CM, CV, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    SLDM_CUDA(cudaFuncSetAttribute(gemv_tile_kernel<CM, CV, NR, LO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   int(smem)));
     done.fetch_or(bit);
   }
-  gemv_tile_kernel<CM, CV, NR><<<unsigned(plan.ntiles), 256, smem, s>>>(plan.jobs, plan.tiles, nrhs);
+  gemv_tile_kernel<CM, CV, NR, LO><<<unsigned(plan.ntiles), 256, smem, s>>>(plan.jobs, plan.tiles, nrhs);
   count_launch();
 }
 
@@ -926,6 +959,16 @@ void gemv_jobs_mixed(const GemvPlan& plan, int nrhs, cudaStream_t s) {
     SLDM_REQUIRE((plan.tiles != nullptr && plan.tile_rows == GemvTile<CM, CV>::ROWS), SLDM_EINVAL,
                  "GEMV plan without row tiles for this vector type");
     if (plan.ntiles == 0) return;
+    if constexpr (comp) {
+      if (plan.has_lo) {  // the FP64 operator held as a complex64 pair
+        if (nrhs <= 1) launch_tile<CM, CV, 1, true>(plan, nrhs, s);
+        else if (nrhs <= 2) launch_tile<CM, CV, 2, true>(plan, nrhs, s);
+        else if (nrhs <= 4) launch_tile<CM, CV, 4, true>(plan, nrhs, s);
+        else launch_tile<CM, CV, 8, true>(plan, nrhs, s);
+        SLDM_CUDA(cudaGetLastError());
+        return;
+      }
+    }
     if (nrhs <= 1) {
       if constexpr (comp) launch_tile<CM, CV, 1>(plan, nrhs, s);  // the only one-column use
     } else if (nrhs <= 2) launch_tile<CM, CV, 2>(plan, nrhs, s);
@@ -1418,6 +1461,37 @@ void to_c128(const void* src, int64_t n, double2* dst, cudaStream_t s) {
 template <class C>
 void from_c128(const double2* src, int64_t n, void* dst, cudaStream_t s) {
   from_c128_kernel<C><<<unsigned((n + 255) / 256), 256, 0, s>>>(src, n, (C*)dst), ::sldm::count_launch();
+  SLDM_CUDA(cudaGetLastError());
+}
+
+// FP64 operator kept as a complex64 pair: hi = fl32(v), lo = fl32(v - hi)
+__global__ void split_c128_kernel(const double2* __restrict__ src, int64_t n, float2* __restrict__ hi,
+                                  float2* __restrict__ lo) {
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < n; t += stride) {
+    const double2 v = src[t];
+    const float hr = __double2float_rn(v.x), hv = __double2float_rn(v.y);
+    hi[t] = make_float2(hr, hv);
+    lo[t] = make_float2(__double2float_rn(v.x - double(hr)), __double2float_rn(v.y - double(hv)));
+  }
+}
+__global__ void add_lo_c128_kernel(const float2* __restrict__ lo, int64_t n, double2* dst) {
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < n; t += stride) {
+    dst[t].x += double(lo[t].x);
+    dst[t].y += double(lo[t].y);
+  }
+}
+void split_c128(const double2* src, int64_t n, float2* hi, float2* lo, cudaStream_t s) {
+  if (n <= 0) return;
+  const unsigned blocks = unsigned(std::min<int64_t>((n + 255) / 256, 152 * 32));
+  split_c128_kernel<<<blocks, 256, 0, s>>>(src, n, hi, lo), ::sldm::count_launch();
+  SLDM_CUDA(cudaGetLastError());
+}
+void add_lo_c128(const float2* lo, int64_t n, double2* dst, cudaStream_t s) {
+  if (n <= 0) return;
+  const unsigned blocks = unsigned(std::min<int64_t>((n + 255) / 256, 152 * 32));
+  add_lo_c128_kernel<<<blocks, 256, 0, s>>>(lo, n, dst), ::sldm::count_launch();
   SLDM_CUDA(cudaGetLastError());
 }
 

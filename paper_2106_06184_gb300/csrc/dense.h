@@ -38,6 +38,9 @@ struct GemvJob {
   int64_t ldy;
   double ar, ai;
   int32_t beta, pad;
+  // low parts of a complex64 block whose FP64 value is A + Alo (same layout and
+  // lda), or null; read only by the FP64-accumulated complex64 product
+  const void* Alo;
 };
 struct GemvPlan {
   const char* name = "gemv";   // timer name of its launches
@@ -50,6 +53,9 @@ struct GemvPlan {
   int2* tiles = nullptr;
   int ntiles = 0;
   int tile_rows = 0;
+  // every job carries Alo (complex64 blocks with complex128 vectors only): the
+  // product is that of the FP64 operator A + Alo
+  bool has_lo = false;
 };
 // right-hand sides per pass of the structured product and the preconditioner
 constexpr int MAX_NRHS = 8;
@@ -113,6 +119,10 @@ void vscale3(int64_t n, int64_t ne, double s1, double s2, double s3, const CX* x
 
 template <class C>
 void to_c128(const void* src, int64_t n, double2* dst, cudaStream_t s);
+// hi = complex64 rounding of src, lo = complex64 rounding of src - hi (src = hi + lo to ~2^-48)
+void split_c128(const double2* src, int64_t n, float2* hi, float2* lo, cudaStream_t s);
+// dst += lo (complex64 low parts onto a complex128 copy of the high parts)
+void add_lo_c128(const float2* lo, int64_t n, double2* dst, cudaStream_t s);
 template <class C>
 void from_c128(const double2* src, int64_t n, void* dst, cudaStream_t s);
 template <class C>

@@ -1035,6 +1035,11 @@ constexpr size_t NOALLOC_MAX_TILES = 4096;
 constexpr size_t NOALLOC_KB_OFF = NOALLOC_TILE_OFF + NOALLOC_MAX_TILES * sizeof(TileRef);  // complex128 block
 constexpr size_t NOALLOC_MAX_KB = (NOALLOC_BYTES - NOALLOC_KB_OFF) / sizeof(double2);
 
+static_assert(sizeof(KTask) <= NOALLOC_TILE_OFF - NOALLOC_TASK_OFF, "task record overlaps the tile list");
+static_assert(NOALLOC_TILE_OFF % alignof(TileRef) == 0, "tile list misaligned");
+static_assert(NOALLOC_KB_OFF % alignof(double2) == 0 && NOALLOC_KB_OFF % 16 == 0, "scratch block misaligned");
+static_assert(NOALLOC_KB_OFF < NOALLOC_BYTES, "no room for the scratch block");
+
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
 
 // Device address of g_noalloc_scratch per device, resolved once with that device current.

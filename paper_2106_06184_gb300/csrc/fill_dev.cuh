@@ -60,8 +60,10 @@ __device__ __forceinline__ void add_d(void* base, int64_t idx, double re, double
 }
 
 // ---------------------------------------------------------------- FP64 closed forms
-// Integrals over the flat triangle (p1, p2, p3) seen from r (see the oracle's
-// derivation: contour reduction with the surface divergence theorem).
+// Integrals over the flat triangle (p1, p2, p3) seen from r: each surface
+// integral is reduced to a sum over the three edges with the surface divergence
+// theorem in the plane of the triangle (Wilton, Rao, Glisson, Schaubert, Al-Bundak
+// and Butler, IEEE Trans. AP-32, 1984; Graglia, IEEE Trans. AP-41, 1993).
 struct Pot {
   double inv_r, r;            // int 1/R, int R
   double por[3], pr[3];       // int (rho' - rho)/R, int (rho' - rho) R

@@ -49,6 +49,15 @@ struct ScopedTimer {
   }
 };
 
+// ---------------------------------------------------------------- device-memory budget
+// Bytes held by every DBuf of the library (all devices) and the optional limit
+// set by sldm_set_device_budget (0 = none).  budget_take throws SLDM_ENOMEM
+// when the limit would be exceeded.
+void budget_take(size_t bytes);
+void budget_give(size_t bytes);
+// Test injection (sldm_test_inject): consumes one pending LU stall, if any.
+bool take_lu_stall();
+
 // ---------------------------------------------------------------- device buffers
 template <class T>
 struct DBuf {
@@ -59,16 +68,21 @@ struct DBuf {
   DBuf& operator=(const DBuf&) = delete;
   ~DBuf() { release(); }
   void release() {
-    if (p) cudaFree(p);
+    if (p) {
+      cudaFree(p);
+      budget_give(n * sizeof(T));
+    }
     p = nullptr;
     n = 0;
   }
   void alloc(size_t count) {
     release();
     if (count == 0) return;
+    budget_take(count * sizeof(T));
     cudaError_t e = cudaMalloc(&p, count * sizeof(T));
     if (e != cudaSuccess) {
       p = nullptr;
+      budget_give(count * sizeof(T));
       throw Error{SLDM_ENOMEM, "cudaMalloc of " + std::to_string(count * sizeof(T)) + " bytes failed"};
     }
     n = count;

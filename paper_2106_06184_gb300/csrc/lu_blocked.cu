@@ -469,7 +469,7 @@ void lu_solve_blocked(const LUSysT<C>& S, cudaStream_t s) {
   int herr[2] = {0, 0};
   SLDM_CUDA(cudaMemcpyAsync(herr, err.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
   SLDM_CUDA(cudaStreamSynchronize(s));
-  SLDM_REQUIRE(herr[0] != 2, SLDM_ECUDA, "LU: a panel barrier ran out of its wait limit");
+  SLDM_REQUIRE(herr[0] != 2, SLDM_ETIMEOUT, "LU: a panel barrier ran out of its wait limit");
   SLDM_REQUIRE(herr[0] == 0, SLDM_ENUMERIC,
                "LU: zero or non-finite pivot in column " + std::to_string(herr[1]) + " of " + std::to_string(n));
 }

@@ -8,6 +8,30 @@
 
 namespace sldm {
 
+// ---------------------------------------------------------------- device-memory budget
+static std::atomic<int64_t> g_bytes{0};
+static std::atomic<int64_t> g_budget{0};
+
+void budget_take(size_t bytes) {
+  const int64_t b = int64_t(bytes);
+  const int64_t now = g_bytes.fetch_add(b) + b;
+  const int64_t lim = g_budget.load();
+  if (lim > 0 && now > lim) {
+    g_bytes.fetch_sub(b);
+    throw Error{SLDM_ENOMEM, "device-memory budget exceeded: " + std::to_string(now) + " > " + std::to_string(lim) +
+                                 " bytes"};
+  }
+}
+void budget_give(size_t bytes) { g_bytes.fetch_sub(int64_t(bytes)); }
+
+static std::atomic<int> g_lu_stall{0};
+bool take_lu_stall() {
+  int v = g_lu_stall.load();
+  while (v > 0)
+    if (g_lu_stall.compare_exchange_weak(v, v - 1)) return true;
+  return false;
+}
+
 namespace {
 struct Pending {
   std::string name;
@@ -118,3 +142,30 @@ int sldm_timer_names(char* buf, size_t len) {
 }
 
 }  // extern "C"
+
+extern "C" int sldm_set_device_budget(int64_t bytes) {
+  if (bytes < 0) {
+    sldm::set_error("set_device_budget: negative budget");
+    return SLDM_EINVAL;
+  }
+  sldm::g_budget.store(bytes);
+  return SLDM_OK;
+}
+
+extern "C" int sldm_device_bytes(int64_t* in_use) {
+  if (!in_use) {
+    sldm::set_error("device_bytes: null argument");
+    return SLDM_EINVAL;
+  }
+  *in_use = sldm::g_bytes.load();
+  return SLDM_OK;
+}
+
+extern "C" int sldm_test_inject(int32_t what, int32_t count) {
+  if (what != SLDM_INJECT_LU_STALL || count < 0) {
+    sldm::set_error("test_inject: unknown injection or negative count");
+    return SLDM_EINVAL;
+  }
+  sldm::g_lu_stall.store(count);
+  return SLDM_OK;
+}

@@ -15,9 +15,10 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libsldm.so")
 
-OK, EINVAL, ENOMEM, ENOTCONV, ENUMERIC, ECUDA, EBUSY, ENOTSUP = 0, -1, -2, -3, -4, -5, -6, -7
+OK, EINVAL, ENOMEM, ENOTCONV, ENUMERIC, ECUDA, EBUSY, ENOTSUP, ETIMEOUT = 0, -1, -2, -3, -4, -5, -6, -7, -8
+INJECT_LU_STALL = 1
 HOST, DEVICE = 0, 1
-PREC_F64, PREC_F32 = 0, 1
+PREC_F64, PREC_F32, PREC_F32X2 = 0, 1, 2
 BOTTOM_HALFSPACE, BOTTOM_PEC = 0, 1
 (BLOCK_LAM, BLOCK_LPM, BLOCK_LA, BLOCK_LP, BLOCK_K, BLOCK_Y11, BLOCK_Y21, BLOCK_IX, BLOCK_KBAR_L) = range(9)
 
@@ -87,6 +88,9 @@ EXPORTS = {
     "sldm_timer_get": (C.c_int, [C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "sldm_timer_names": (C.c_int, [C.c_char_p, C.c_size_t]),
     "sldm_launch_count": (C.c_int, [C.POINTER(C.c_int64)]),
+    "sldm_set_device_budget": (C.c_int, [C.c_int64]),
+    "sldm_device_bytes": (C.c_int, [C.POINTER(C.c_int64)]),
+    "sldm_test_inject": (C.c_int, [C.c_int32, C.c_int32]),
 }
 
 
@@ -143,6 +147,25 @@ def launch_count(lib=None) -> int:
     n = C.c_int64()
     L.check(L.lib.sldm_launch_count(C.byref(n)))
     return n.value
+
+
+def set_device_budget(nbytes, lib=None):
+    """sldm_set_device_budget: limit on the device bytes the library holds (0 = none)."""
+    L = lib or load()
+    L.check(L.lib.sldm_set_device_budget(int(nbytes)))
+
+
+def device_bytes(lib=None) -> int:
+    L = lib or load()
+    v = C.c_int64()
+    L.check(L.lib.sldm_device_bytes(C.byref(v)))
+    return v.value
+
+
+def test_inject(what, count, lib=None):
+    """sldm_test_inject (failure-path tests)."""
+    L = lib or load()
+    L.check(L.lib.sldm_test_inject(int(what), int(count)))
 
 
 def load(path=LIB_PATH) -> Library:
@@ -264,6 +287,15 @@ class Operator:
         out = np.zeros((r.value, c.value), np.complex128)
         self.L.check(self.L.lib.sldm_op_block(self.h, which, obj, out.ctypes.data_as(C.c_void_p), HOST,
                                               C.byref(r), C.byref(c)))
+        return out
+
+    def block_into(self, which, out, obj=0):
+        """sldm_op_block into a caller buffer (numpy: host; torch CUDA tensor: device), complex128."""
+        r, c = C.c_int64(), C.c_int64()
+        self.L.check(self.L.lib.sldm_op_block(self.h, which, obj, None, HOST, C.byref(r), C.byref(c)))
+        assert tuple(out.shape) == (r.value, c.value)
+        p, w = _ptr(out)
+        self.L.check(self.L.lib.sldm_op_block(self.h, which, obj, p, w, C.byref(r), C.byref(c)))
         return out
 
     def table(self, which):
