@@ -5,7 +5,9 @@
 #include <cmath>
 #include <complex>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <array>
 
 #include "dense.h"
 #include "internal.h"
@@ -193,56 +195,132 @@ static void apply_any(const sldm_op* op, const double2* x, double2* y, int nrhs,
 
 static cplx eps_complex(double eps_r, double sigma, double omega) { return cplx(eps_r, -sigma / (omega * EPS0_)); }
 
+// Objects o and r have the same shape when they have the same triangles and
+// edges in the same local order (vertex and edge ids shifted by constants, the
+// same edge signs) and vertices that differ by one translation to 1e-12 of the
+// object's size; `shift` receives that translation (o's vertices minus r's).
+static bool same_shape(const HostMesh& h, int o, int r, double shift[3]) {
+  const int t0 = h.tri_begin[o], nt = h.tri_begin[o + 1] - t0, e0 = h.edge_begin[o], ne = h.edge_begin[o + 1] - e0;
+  const int u0 = h.tri_begin[r], ue0 = h.edge_begin[r];
+  if (h.tri_begin[r + 1] - u0 != nt || h.edge_begin[r + 1] - ue0 != ne) return false;
+  if (h.bedge_begin[o + 1] - h.bedge_begin[o] != h.bedge_begin[r + 1] - h.bedge_begin[r]) return false;
+  const int64_t dv = int64_t(h.tri[3 * size_t(t0)]) - h.tri[3 * size_t(u0)];
+  double lo = 1e300, hi = -1e300;
+  for (int d = 0; d < 3; ++d)
+    shift[d] = h.xyz[3 * size_t(h.tri[3 * size_t(t0)]) + d] - h.xyz[3 * size_t(h.tri[3 * size_t(u0)]) + d];
+  for (int i = 0; i < 3 * nt; ++i) {
+    const size_t io = 3 * size_t(t0) + i, ir = 3 * size_t(u0) + i;
+    if (!(int64_t(h.tri[io]) - h.tri[ir] == dv && h.tri_edge[io] - e0 == h.tri_edge[ir] - ue0 &&
+          h.tri_sign[io] == h.tri_sign[ir]))
+      return false;
+  }
+  for (int j = 0; j < ne; ++j)
+    if (!(h.uv[2 * size_t(e0 + j)] - h.uv[2 * size_t(ue0 + j)] == dv &&
+          h.uv[2 * size_t(e0 + j) + 1] - h.uv[2 * size_t(ue0 + j) + 1] == dv))
+      return false;
+  double dmax = 0;
+  for (int i = 0; i < 3 * nt; ++i) {
+    const size_t vo = size_t(h.tri[3 * size_t(t0) + i]), vr = size_t(h.tri[3 * size_t(u0) + i]);
+    for (int d = 0; d < 3; ++d) {
+      dmax = std::max(dmax, std::fabs(h.xyz[3 * vo + d] - h.xyz[3 * vr + d] - shift[d]));
+      lo = std::min(lo, h.xyz[3 * vr + d]);
+      hi = std::max(hi, h.xyz[3 * vr + d]);
+    }
+  }
+  return dmax <= 1e-12 * (hi - lo);
+}
+
 // ref[o] = the first object that object o repeats, else o.  Object o repeats r
-// when they have the same material, the same triangles and edges in the same
-// local order (vertex and edge ids shifted by constants, the same edge signs)
-// and vertices that differ by one translation to 1e-12 of the object's size.
-// Interior blocks and Y depend only on that shape and material (the
-// equivalent configuration uses the homogeneous kernel of the background
-// layer, which a translation leaves unchanged), so they are filled once.
+// when they have the same shape (same_shape) and the same material.  Interior
+// blocks and Y depend only on that shape and material (the equivalent
+// configuration uses the homogeneous kernel of the background layer, which a
+// translation leaves unchanged), so they are filled once.
 static std::vector<int> repeated_objects(const HostMesh& h, const sldm_material* mats) {
   const int nobj = int(h.nobj);
   std::vector<int> ref(nobj);
+  double sh[3];
   for (int o = 0; o < nobj; ++o) {
     ref[o] = o;
-    const int t0 = h.tri_begin[o], nt = h.tri_begin[o + 1] - t0, e0 = h.edge_begin[o], ne = h.edge_begin[o + 1] - e0;
     for (int r = 0; r < o && ref[o] == o; ++r) {
       if (ref[r] != r) continue;
-      const int u0 = h.tri_begin[r], ue0 = h.edge_begin[r];
-      if (h.tri_begin[r + 1] - u0 != nt || h.edge_begin[r + 1] - ue0 != ne) continue;
-      if (h.bedge_begin[o + 1] - h.bedge_begin[o] != h.bedge_begin[r + 1] - h.bedge_begin[r]) continue;
       const sldm_material &a = mats[o], &b = mats[r];
       if (a.eps_r != b.eps_r || a.mu_r != b.mu_r || a.sigma != b.sigma || a.layer != b.layer) continue;
-      const int64_t dv = int64_t(h.tri[3 * size_t(t0)]) - h.tri[3 * size_t(u0)];
-      bool same = true;
-      double shift[3], lo = 1e300, hi = -1e300;
-      for (int d = 0; d < 3; ++d) shift[d] = h.xyz[3 * size_t(h.tri[3 * size_t(t0)]) + d] - h.xyz[3 * size_t(h.tri[3 * size_t(u0)]) + d];
-      for (int i = 0; i < 3 * nt && same; ++i) {
-        const size_t io = 3 * size_t(t0) + i, ir = 3 * size_t(u0) + i;
-        same = int64_t(h.tri[io]) - h.tri[ir] == dv && h.tri_edge[io] - e0 == h.tri_edge[ir] - ue0 &&
-               h.tri_sign[io] == h.tri_sign[ir];
-      }
-      for (int j = 0; j < ne && same; ++j)
-        same = h.uv[2 * size_t(e0 + j)] - h.uv[2 * size_t(ue0 + j)] == dv &&
-               h.uv[2 * size_t(e0 + j) + 1] - h.uv[2 * size_t(ue0 + j) + 1] == dv;
-      if (!same) continue;
-      double dmax = 0;
-      for (int i = 0; i < 3 * nt; ++i) {
-        const size_t vo = size_t(h.tri[3 * size_t(t0) + i]), vr = size_t(h.tri[3 * size_t(u0) + i]);
-        for (int d = 0; d < 3; ++d) {
-          dmax = std::max(dmax, std::fabs(h.xyz[3 * vo + d] - h.xyz[3 * vr + d] - shift[d]));
-          lo = std::min(lo, h.xyz[3 * vr + d]);
-          hi = std::max(hi, h.xyz[3 * vr + d]);
-        }
-      }
-      if (dmax <= 1e-12 * (hi - lo)) ref[o] = r;
+      if (same_shape(h, o, r, sh)) ref[o] = r;
     }
   }
   return ref;
 }
 
-// finish = false: stop before the GEMV plans and the preconditioner (the
-// caller converts the operator first, see split_to_x2)
+// Reuse of the global blocks L^A_m, L^phi_m.  The block of object pair (i, j)
+// (rows: i's edges or triangles, columns: j's) integrates G(r, r') over i's test
+// and j's source triangles.  In a homogeneous background G depends on r - r'
+// only, so two pairs whose objects have the same shapes at the same relative
+// displacement have equal blocks; in a layered background G depends on the
+// horizontal part of r - r' and on z and z' apart, so the pairs must also share
+// the objects' heights.  `reps` lists one pair per distinct block (filled), the
+// copies send each representative block to its repeats.  Objects of one shape
+// class and their translations: cls[o], shift[o] (from the class's first object).
+struct GlobalReuse {
+  std::vector<std::pair<int, int>> reps;
+  std::vector<BlockCopy> copyA, copyP;
+};
+static GlobalReuse global_reuse(const HostMesh& h, bool layered) {
+  const int nobj = int(h.nobj);
+  std::vector<int> cls(nobj);
+  std::vector<std::array<double, 3>> shift(nobj);
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (int64_t v = 0; v < h.nv; ++v)
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = std::min(lo[d], h.xyz[3 * v + d]);
+      hi[d] = std::max(hi[d], h.xyz[3 * v + d]);
+    }
+  const double tol = 1e-12 * std::max({hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2]});
+  for (int o = 0; o < nobj; ++o) {
+    cls[o] = o;
+    shift[o] = {0.0, 0.0, 0.0};
+    for (int r = 0; r < o; ++r) {
+      if (cls[r] != r) continue;
+      double sh[3];
+      if (same_shape(h, o, r, sh)) {
+        cls[o] = r;
+        shift[o] = {sh[0], sh[1], sh[2]};
+        break;
+      }
+    }
+  }
+  GlobalReuse g;
+  struct Rep {
+    int i, j;
+    double d[3], zi;
+  };
+  std::map<std::pair<int, int>, std::vector<Rep>> by_cls;
+  for (int i = 0; i < nobj; ++i)
+    for (int j = 0; j < nobj; ++j) {
+      double d[3];
+      for (int k = 0; k < 3; ++k) d[k] = shift[j][k] - shift[i][k];
+      const double zi = layered ? shift[i][2] : 0.0;
+      auto& list = by_cls[{cls[i], cls[j]}];
+      const Rep* hit = nullptr;
+      for (const Rep& r : list)
+        if (std::fabs(r.d[0] - d[0]) <= tol && std::fabs(r.d[1] - d[1]) <= tol && std::fabs(r.d[2] - d[2]) <= tol &&
+            std::fabs(r.zi - zi) <= tol) {
+          hit = &r;
+          break;
+        }
+      if (!hit) {
+        list.push_back({i, j, {d[0], d[1], d[2]}, zi});
+        g.reps.push_back({i, j});
+        continue;
+      }
+      const int ri = hit->i, rj = hit->j;
+      g.copyA.push_back({h.edge_begin[ri], h.edge_begin[rj], h.edge_begin[i], h.edge_begin[j],
+                         h.edge_begin[i + 1] - h.edge_begin[i], h.edge_begin[j + 1] - h.edge_begin[j]});
+      g.copyP.push_back({h.tri_begin[ri], h.tri_begin[rj], h.tri_begin[i], h.tri_begin[j],
+                         h.tri_begin[i + 1] - h.tri_begin[i], h.tri_begin[j + 1] - h.tri_begin[j]});
+    }
+  return g;
+}
+
 template <class R>
 static void assemble_impl(sldm_op* op, const sldm_material* mats, cudaStream_t s, bool finish = true) {
   typedef typename std::conditional<sizeof(R) == 4, float2, double2>::type C;
@@ -255,6 +333,7 @@ static void assemble_impl(sldm_op* op, const sldm_material* mats, cudaStream_t s
   op->LPm.alloc(op->nt * op->nt * es);
   op->LAm.zero(s);
   op->LPm.zero(s);
+  GlobalReuse gr;
   {
     LTask t{};
     t.t0 = 0; t.ntest = int32_t(op->nt); t.s0 = 0; t.nsrc = int32_t(op->nt);
@@ -264,7 +343,26 @@ static void assemble_impl(sldm_op* op, const sldm_material* mats, cudaStream_t s
     t.sAr = op->mu_b; t.sAi = 0;
     cplx ip = 1.0 / op->eps_b;
     t.sPr = ip.real(); t.sPi = ip.imag();
-    fill_L<R>(m, {t}, s);
+    // repeated object pairs (arrays of identical objects) fill one block per
+    // distinct relative placement; a background that splits sources (a good
+    // conductor) keeps the single task, whose far-pair cut spans the whole fill
+    if (op->nobj > 1 && !split_rules_L(h, t).split) gr = global_reuse(h, op->layered);
+    if (!gr.copyA.empty()) {
+      std::vector<LTask> tasks;
+      for (auto& pr : gr.reps) {
+        LTask u = t;
+        u.t0 = h.tri_begin[pr.first];
+        u.ntest = h.tri_begin[pr.first + 1] - u.t0;
+        u.s0 = h.tri_begin[pr.second];
+        u.nsrc = h.tri_begin[pr.second + 1] - u.s0;
+        tasks.push_back(u);
+      }
+      fill_L<R>(m, tasks, s);
+      copy_blocks(gr.copyA, es, op->LAm.p, op->ne, s);
+      copy_blocks(gr.copyP, es, op->LPm.p, op->nt, s);
+    } else {
+      fill_L<R>(m, {t}, s);
+    }
   }
   // ---- per-object layout of the local blocks
   int64_t off = 0;

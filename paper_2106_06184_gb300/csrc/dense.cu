@@ -1495,6 +1495,51 @@ void add_lo_c128(const float2* lo, int64_t n, double2* dst, cudaStream_t s) {
   SLDM_CUDA(cudaGetLastError());
 }
 
+// One warp per copied row: the rows of every copy, in order, split by an
+// exclusive prefix sum; 16-byte loads when the entries are complex128 or the
+// row segment is 16-byte aligned.
+template <class C>
+__global__ void __launch_bounds__(256) copy_blocks_kernel(const BlockCopy* __restrict__ cp, const int64_t* __restrict__ rs,
+                                                          int ncp, int64_t total_rows, C* M, int64_t ld) {
+  const int64_t w = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= total_rows) return;
+  int lo = 0, hi = ncp - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (rs[mid] <= w) lo = mid;
+    else hi = mid - 1;
+  }
+  const BlockCopy c = cp[lo];
+  const int64_t r = w - rs[lo];
+  const C* src = M + (c.sr + r) * ld + c.sc;
+  C* dst = M + (c.dr + r) * ld + c.dc;
+  for (int j = lane; j < c.nc; j += 32) dst[j] = __ldcs(src + j);
+}
+
+void copy_blocks(const std::vector<BlockCopy>& copies, size_t esz, void* M, int64_t ld, cudaStream_t s) {
+  if (copies.empty()) return;
+  std::vector<int64_t> rs(copies.size());
+  int64_t acc = 0;
+  for (size_t i = 0; i < copies.size(); ++i) {
+    rs[i] = acc;
+    acc += copies[i].nr;
+  }
+  DBuf<BlockCopy> dc;
+  DBuf<int64_t> drs;
+  dc.upload(copies, s);
+  drs.upload(rs, s);
+  const unsigned blocks = unsigned((acc * 32 + 255) / 256);
+  ScopedTimer tm("copy_blocks", s);
+  if (esz == sizeof(double2))
+    copy_blocks_kernel<double2><<<blocks, 256, 0, s>>>(dc.p, drs.p, int(copies.size()), acc, (double2*)M, ld);
+  else
+    copy_blocks_kernel<float2><<<blocks, 256, 0, s>>>(dc.p, drs.p, int(copies.size()), acc, (float2*)M, ld);
+  count_launch();
+  SLDM_CUDA(cudaGetLastError());
+  SLDM_CUDA(cudaStreamSynchronize(s));  // the copy lists are released on return
+}
+
 // add alpha * I_x (CSR, rows of an object) into a dense block
 template <class C>
 __global__ void add_ix_kernel(int e0, int ne_o, double alpha, const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,

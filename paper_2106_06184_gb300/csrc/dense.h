@@ -127,6 +127,13 @@ template <class C>
 void from_c128(const double2* src, int64_t n, void* dst, cudaStream_t s);
 template <class C>
 void copy_scaled(const void* src, int64_t n, double alpha, void* dst, cudaStream_t s);
+// Copies of sub-blocks within one row-major matrix (leading dimension ld):
+// rows [sr, sr + nr) x cols [sc, sc + nc) to [dr, dr + nr) x [dc, dc + nc).
+// Sources are never destinations of the same call.
+struct BlockCopy {
+  int32_t sr, sc, dr, dc, nr, nc;
+};
+void copy_blocks(const std::vector<BlockCopy>& copies, size_t esz, void* M, int64_t ld, cudaStream_t s);
 template <class C>
 void add_ix(const sldm_mesh* m, int obj, double alpha, const double* ix_val, void* K, int64_t ld, cudaStream_t s);
 

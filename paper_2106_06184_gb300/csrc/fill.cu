@@ -97,16 +97,24 @@ struct TileRef {
   int32_t task, test0, src0, pad;
 };
 
+// Centroids as hi + lo in the fill's precision (for FP32: two floats, c to ~2^-48),
+// so the centroid difference of a pair, (hi - hi') + (lo - lo'), is formed to the
+// fill's precision relative to the distance without FP64 operations in the loop.
 template <class R>
 struct TestRec {
   R rho[18], W[6], av[9], sig[3];
-  double c[3];
-  double invA;
+  R chi[3], clo[3];
+  R invA;
   int32_t v[3], e[3];
 };
+template <class R>
+__device__ __forceinline__ void split_hl(double v, R& hi, R& lo) {
+  hi = R(v);
+  lo = R(v - double(hi));
+}
 
 template <class R>
-__global__ void __launch_bounds__(TILE_SRC) fill_L_bulk(const LTask* __restrict__ tasks, const TileRef* __restrict__ tiles,
+__global__ void __launch_bounds__(TILE_SRC, sizeof(R) == 4 ? 5 : 1) fill_L_bulk(const LTask* __restrict__ tasks, const TileRef* __restrict__ tiles,
                                                         const double* __restrict__ geo, const int32_t* __restrict__ tri,
                                                         const int32_t* __restrict__ tri_edge) {
   __shared__ TestRec<R> T[TILE_TEST];
@@ -123,11 +131,11 @@ __global__ void __launch_bounds__(TILE_SRC) fill_L_bulk(const LTask* __restrict_
       for (int d = 0; d < 9; ++d) T[idx].av[d] = R(g[GEO_AV + d]);
       for (int d = 0; d < 3; ++d) {
         T[idx].sig[d] = R(g[GEO_SIG + d]);
-        T[idx].c[d] = g[GEO_C + d];
+        split_hl(g[GEO_C + d], T[idx].chi[d], T[idx].clo[d]);
         T[idx].v[d] = tri[3 * tg + d];
         T[idx].e[d] = tri_edge[3 * tg + d];
       }
-      T[idx].invA = 1.0 / g[GEO_A];
+      T[idx].invA = R(1.0 / g[GEO_A]);
     }
   }
   __syncthreads();
@@ -135,8 +143,7 @@ __global__ void __launch_bounds__(TILE_SRC) fill_L_bulk(const LTask* __restrict_
   if (s >= tk.nsrc) return;
   const int sg = tk.s0 + s;
   const double* gs = geo + size_t(sg) * GEO_STRIDE;
-  R rs[18], Ws[6], bv[9], sg_[3];
-  double cs[3];
+  R rs[18], Ws[6], bv[9], sg_[3], cshi[3], cslo[3];
 #pragma unroll
   for (int d = 0; d < 18; ++d) rs[d] = R(gs[GEO_RHO + d]);
 #pragma unroll
@@ -146,13 +153,15 @@ __global__ void __launch_bounds__(TILE_SRC) fill_L_bulk(const LTask* __restrict_
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     sg_[d] = R(gs[GEO_SIG + d]);
-    cs[d] = gs[GEO_C + d];
+    split_hl(gs[GEO_C + d], cshi[d], cslo[d]);
   }
-  const double invAs = 1.0 / gs[GEO_A];
+  const R invAs = R(1.0 / gs[GEO_A]);
   const int32_t sv0 = tri[3 * sg], sv1 = tri[3 * sg + 1], sv2 = tri[3 * sg + 2];
   const int32_t se[3] = {tri_edge[3 * sg], tri_edge[3 * sg + 1], tri_edge[3 * sg + 2]};
   const R kr = R(tk.kr), ki = R(tk.ki);
-  const R c4pi = R(INV4PI);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) Ws[k] *= R(INV4PI);  // 1/(4 pi) of G folded into the source weights
+  const R sAr = R(tk.sAr), sAi = R(tk.sAi), sPr = R(tk.sPr), sPi = R(tk.sPi);
 
   for (int tt = 0; tt < TILE_TEST; ++tt) {
     if (tile.test0 + tt >= tk.ntest) break;
@@ -162,7 +171,9 @@ __global__ void __launch_bounds__(TILE_SRC) fill_L_bulk(const LTask* __restrict_
 #pragma unroll
     for (int i = 0; i < 3; ++i) touch |= (X.v[i] == sv0) | (X.v[i] == sv1) | (X.v[i] == sv2);
     if (touch) continue;
-    const R dc0 = R(X.c[0] - cs[0]), dc1 = R(X.c[1] - cs[1]), dc2 = R(X.c[2] - cs[2]);
+    const R dc0 = (X.chi[0] - cshi[0]) + (X.clo[0] - cslo[0]);
+    const R dc1 = (X.chi[1] - cshi[1]) + (X.clo[1] - cslo[1]);
+    const R dc2 = (X.chi[2] - cshi[2]) + (X.clo[2] - cslo[2]);
     R m0r = 0, m0i = 0, mqr[3] = {0, 0, 0}, mqi[3] = {0, 0, 0}, msr[3] = {0, 0, 0}, msi[3] = {0, 0, 0};
     R mqsr = 0, mqsi = 0;
 #pragma unroll
@@ -177,7 +188,7 @@ __global__ void __launch_bounds__(TILE_SRC) fill_L_bulk(const LTask* __restrict_
         const R Rr = r2 * ir;
         R sn, cn;
         M<R>::sincos_(kr * Rr, &sn, &cn);
-        const R amp = (ki != R(0) ? M<R>::exp_(ki * Rr) : R(1)) * c4pi * ir * Ws[k];
+        const R amp = (ki != R(0) ? M<R>::exp_(ki * Rr) : R(1)) * ir * Ws[k];
         const R gr = amp * cn, gi = -amp * sn;
         ar += gr;
         ai += gi;
@@ -221,16 +232,16 @@ __global__ void __launch_bounds__(TILE_SRC) fill_L_bulk(const LTask* __restrict_
           const R sc = X.sig[i] * sg_[j];
           vr *= sc;
           vi *= sc;
-          M<R>::add(tk.A, row + (se[j] - tk.e_col0), vr * R(tk.sAr) - vi * R(tk.sAi), vr * R(tk.sAi) + vi * R(tk.sAr));
+          M<R>::add(tk.A, row + (se[j] - tk.e_col0), vr * sAr - vi * sAi, vr * sAi + vi * sAr);
         }
       }
     }
     if (tk.P) {
-      const R sc = R(X.invA * invAs);
+      const R sc = X.invA * invAs;
       const R vr = m0r * sc, vi = m0i * sc;
       const int t = tile.test0 + tt;
-      M<R>::store(tk.P, int64_t(t + tk.t0 - tk.t_row0) * tk.ldP + (sg - tk.t_col0), double(vr * R(tk.sPr) - vi * R(tk.sPi)),
-                  double(vr * R(tk.sPi) + vi * R(tk.sPr)));
+      M<R>::store_r(tk.P, int64_t(t + tk.t0 - tk.t_row0) * tk.ldP + (sg - tk.t_col0), vr * sPr - vi * sPi,
+                    vr * sPi + vi * sPr);
     }
   }
 }
@@ -343,7 +354,7 @@ __global__ void fill_L_touch(const LTask* __restrict__ tasks, const int32_t* __r
 
 // ---------------------------------------------------------------- bulk Kbar kernel (primal test x child source)
 template <class R>
-__global__ void __launch_bounds__(TILE_SRC) fill_K_bulk(const KTask* __restrict__ tasks, const TileRef* __restrict__ tiles,
+__global__ void __launch_bounds__(TILE_SRC, sizeof(R) == 4 ? 5 : 1) fill_K_bulk(const KTask* __restrict__ tasks, const TileRef* __restrict__ tiles,
                                                         const double* __restrict__ geo, const double* __restrict__ bgeo,
                                                         const int32_t* __restrict__ tri, const int32_t* __restrict__ tri_edge,
                                                         const int32_t* __restrict__ btri_edge) {
@@ -360,7 +371,7 @@ __global__ void __launch_bounds__(TILE_SRC) fill_K_bulk(const KTask* __restrict_
       for (int d = 0; d < 9; ++d) T[idx].av[d] = R(g[GEO_AV + d]);
       for (int d = 0; d < 3; ++d) {
         T[idx].sig[d] = R(g[GEO_SIG + d]);
-        T[idx].c[d] = g[GEO_C + d];
+        split_hl(g[GEO_C + d], T[idx].chi[d], T[idx].clo[d]);
         T[idx].v[d] = tri[3 * tg + d];
         T[idx].e[d] = tri_edge[3 * tg + d];
       }
@@ -374,8 +385,7 @@ __global__ void __launch_bounds__(TILE_SRC) fill_K_bulk(const KTask* __restrict_
   const int32_t cv = tri[3 * par + ((kk & 1) ? (pp + 1) % 3 : pp)];  // child's primal vertex
   const int32_t ce = tri_edge[3 * par + (pp + 2) % 3];                // edge of the child's midpoint
   const double* gs = bgeo + size_t(cg) * GEO_STRIDE;
-  R rs[18], Ws[6], bv[9], sg_[3];
-  double cs[3];
+  R rs[18], Ws[6], bv[9], sg_[3], cshi[3], cslo[3];
 #pragma unroll
   for (int d = 0; d < 18; ++d) rs[d] = R(gs[GEO_RHO + d]);
 #pragma unroll
@@ -385,11 +395,12 @@ __global__ void __launch_bounds__(TILE_SRC) fill_K_bulk(const KTask* __restrict_
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     sg_[d] = R(gs[GEO_SIG + d]);
-    cs[d] = gs[GEO_C + d];
+    split_hl(gs[GEO_C + d], cshi[d], cslo[d]);
   }
   const int32_t be[3] = {btri_edge[3 * cg], btri_edge[3 * cg + 1], btri_edge[3 * cg + 2]};
   const R kr = R(tk.kr), ki = R(tk.ki);
-  const R c4pi = R(INV4PI);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) Ws[k] *= R(INV4PI);  // 1/(4 pi) of grad G folded into the source weights
 
   for (int tt = 0; tt < TILE_TEST; ++tt) {
     const int t = tile.test0 + tt;
@@ -400,7 +411,9 @@ __global__ void __launch_bounds__(TILE_SRC) fill_K_bulk(const KTask* __restrict_
 #pragma unroll
     for (int i = 0; i < 3; ++i) touch |= (X.v[i] == cv) | (X.e[i] == ce);
     if (touch) continue;  // FP64 extraction kernel
-    const R dc0 = R(X.c[0] - cs[0]), dc1 = R(X.c[1] - cs[1]), dc2 = R(X.c[2] - cs[2]);
+    const R dc0 = (X.chi[0] - cshi[0]) + (X.clo[0] - cslo[0]);
+    const R dc1 = (X.chi[1] - cshi[1]) + (X.clo[1] - cslo[1]);
+    const R dc2 = (X.chi[2] - cshi[2]) + (X.clo[2] - cslo[2]);
     R p1r = 0, p1i = 0, p2r[3] = {0, 0, 0}, p2i[3] = {0, 0, 0}, xr[3] = {0, 0, 0}, xi[3] = {0, 0, 0};
     R sr[3] = {0, 0, 0}, si[3] = {0, 0, 0};
 #pragma unroll
@@ -416,7 +429,7 @@ __global__ void __launch_bounds__(TILE_SRC) fill_K_bulk(const KTask* __restrict_
         const R Rr = r2 * ir;
         R sn, cn;
         M<R>::sincos_(kr * Rr, &sn, &cn);
-        const R amp = (ki != R(0) ? M<R>::exp_(ki * Rr) : R(1)) * c4pi * ir * ir * ir * Ws[k];
+        const R amp = (ki != R(0) ? M<R>::exp_(ki * Rr) : R(1)) * ir * ir * ir * Ws[k];
         // g1 = -(1 + j k R) exp(-j k R) / (4 pi R^3)
         const R er = amp * cn, ei = -amp * sn;
         const R ar = R(1) - ki * Rr, ai = kr * Rr;
@@ -591,17 +604,24 @@ __global__ void fill_K_touch(const KTask* __restrict__ tasks, const int32_t* __r
 }
 
 // ---------------------------------------------------------------- host launchers
-// Task of each object's touching pairs: the task whose test-triangle range
-// holds the object (tasks cover whole objects), or -1.
+// Task of each object's touching pairs: the first task whose test-triangle and
+// source ranges both hold the object (tasks cover whole objects), or -1 (an
+// object whose own block no task fills).
+static int32_t src_begin(const LTask& t) { return t.s0; }
+static int32_t src_end(const LTask& t) { return t.s0 + t.nsrc; }
+static int32_t src_begin(const KTask& t) { return t.c0 / 6; }
+static int32_t src_end(const KTask& t) { return (t.c0 + t.nsrc) / 6; }
 template <class T>
 static std::vector<int32_t> object_tasks(const HostMesh& h, const std::vector<T>& tasks) {
   std::vector<int32_t> ot(size_t(h.nobj), -1);
   for (int64_t o = 0; o < h.nobj; ++o)
-    for (size_t i = 0; i < tasks.size(); ++i)
-      if (h.tri_begin[o] >= tasks[i].t0 && h.tri_begin[o] < tasks[i].t0 + tasks[i].ntest) {
+    for (size_t i = 0; i < tasks.size(); ++i) {
+      const int32_t b = h.tri_begin[o];
+      if (b >= tasks[i].t0 && b < tasks[i].t0 + tasks[i].ntest && b >= src_begin(tasks[i]) && b < src_end(tasks[i])) {
         ot[size_t(o)] = int32_t(i);
         break;
       }
+    }
   return ot;
 }
 
