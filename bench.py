@@ -68,6 +68,21 @@ for _n in (8, 4):
     for _sfx in ("", "-8angles"):
         WORKLOADS[f"metasurface-{_n}x{_n}-cyl-epsr6-1um-freespace-c64x2{_sfx}"] = dict(
             WORKLOADS[f"metasurface-{_n}x{_n}-cyl-epsr6-1um-freespace-c64{_sfx}"], precision=2)
+# Largest single-GPU case: the 8 x 8 metasurface under 32 plane waves per request
+# (incidence 0 - 77.5 deg in 2.5 deg steps in the xz plane, TE and TM
+# alternating), complex64 operator with the FP64-accurate refinement residual,
+# GMRES to 1e-8 of the FP64 system, 181-angle RCS per plane wave; free space (the
+# glass half-space of the paper-shaped case puts the cylinders on an interface,
+# which the layered kernel here does not take).  4 x 4: the profiling case.
+_TH32 = np.radians(2.5 * np.arange(32))
+for _n in (8, 4):
+    for _p, _sfx in ((2, "c64x2"), (1, "c64")):
+        WORKLOADS[f"metasurface-{_n}x{_n}-cyl-epsr6-1um-freespace-{_sfx}-32angles"] = dict(
+            WORKLOADS[f"metasurface-{_n}x{_n}-cyl-epsr6-1um-freespace-c64"], precision=_p,
+            khat=[[float(np.sin(t)), 0.0, -float(np.cos(t))] for t in _TH32],
+            pol=[[0.0, 1.0, 0.0] if i % 2 == 0 else [float(np.cos(t)), 0.0, float(np.sin(t))]
+                 for i, t in enumerate(_TH32)],
+            n_angles=181, e2e_steps=3)
 # Multiscale conductor in a layered substrate: a copper bar (sigma 5.8e7 S/m,
 # 100 x 2 x 1 um, 2,048 graded triangles, N = 8,191) in the middle of a 10 um SiO2
 # layer (eps_r 3.9) over 200 um of Si (eps_r 11.9, sigma 10 S/m) over a PEC ground,
@@ -79,7 +94,7 @@ WORKLOADS["copper-wire-sio2-si-pec-1MHz-50GHz-fp64"] = dict(
     layers=[(1.0, 1.0, 0.0, 0.0), (3.9, 1.0, 0.0, 10e-6), (11.9, 1.0, 10.0, 200e-6)], z_top=0.0, bottom="pec",
     freqs=WIRE_FREQS, precision=0, tol=1e-8, maxit=6000, khat=[0.0, 0.0, -1.0], pol=[1.0, 0.0, 0.0], n_angles=0,
     e2e_steps=20)
-DEFAULT_WORKLOAD = "copper-wire-sio2-si-pec-1MHz-50GHz-fp64"
+DEFAULT_WORKLOAD = "metasurface-8x8-cyl-epsr6-1um-freespace-c64x2-32angles"
 
 
 def _freqs(W):
@@ -108,6 +123,18 @@ L2_FLUSH_BYTES = 512 << 20  # larger than the 129 MB L2
 FALLBACK_HBM_GBS = 6800.0
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# Fill rooflines, in Green's-function evaluations per second (36 per triangle pair).
+# FP32 fill: bound by the special-function unit, 16 operations per SM per clock,
+# three per evaluation of a lossless kernel (1/R, sin and cos of k R; a lossy
+# kernel adds exp):  152 x 16 x 2.07 GHz / 3.
+# FP64 fill: bound by the FP64 pipe (2 FMA-pipe operations per SM per clock on
+# this part) with FP64_OPS_PER_EVAL pipe operations per evaluation, the count of
+# fill_L_bulk<double> as ncu reports it (DFMA + DMUL + DADD per evaluation).
+SFU_OPS_PER_S = 152 * 16 * 2.07e9
+FILL_F32_PEAK_EVALS = SFU_OPS_PER_S / 3.0
+FP64_OPS_PER_S = 152 * 2 * 2.07e9
+FP64_OPS_PER_EVAL = 43.0
+FILL_F64_PEAK_EVALS = FP64_OPS_PER_S / FP64_OPS_PER_EVAL
 
 
 # DRAM traffic per algorithmic byte of the HBM-streaming GEMV stage, from one
@@ -299,6 +326,7 @@ def run_ours(args, rank, world):
     launches = sldm.launch_count() - launches0
     sldm.timers_enable(False)
     timers = sldm.timers_read()
+    units = {k: sldm.timer_units(k) for k in timers}
     clk = clocks.stop()
     torch.cuda.synchronize()
     if world > 1:
@@ -333,49 +361,64 @@ def run_ours(args, rank, world):
     value = n_units / (total_ms / 1e3)
     e2e_value = world * nrhs / statistics.median(e2e_times) if e2e_times else None
 
-    # ---- roofline of the dominant kernel (live CUDA-event timings)
+    # ---- rooflines (live CUDA-event timings; algorithmic units counted by the library)
     hbm, hbm_src = peaks()
-    W_esz = 16 if W["precision"] == 0 else 8  # complex64 blocks (c64x2: the GMRES cycles' stream)
     ne, nt, nobj = mesh.ne, mesh.nt, mesh.nobj
     uv, tp, tm = mesh.edges()
     tri_obj = np.zeros(nt, np.int64) if obj_ids is None else np.asarray(obj_ids)
     obj_sizes = [(int(np.sum(tri_obj[tp] == o)), int(np.sum(tri_obj == o))) for o in range(nobj)]
-    cand = {}
-    if "gemv_main" in timers:
-        # the HBM-streaming stage: L^A_m, L^phi_m and every object's L^A, K, L^phi, once per launch
-        ms, cnt = timers["gemv_main"]
-        s1, s2 = gemv_split(ne, nt, obj_sizes, W_esz)
-        achieved = s2 / (ms / cnt / 1e3) / 1e9
-        cand["gemv_main"] = dict(bound="hbm", achieved=achieved, peak=hbm, unit="GB/s", ms=ms, bytes_per_launch=s2)
+    fp64_fill = W["precision"] in (0, 2)   # c64x2 fills in FP64, then splits
+
+    def matvec_entry(name):
+        """HBM roofline of one GEMV stage: matrix bytes per launch / mean launch time."""
+        if name not in timers or units.get(name, 0) <= 0:
+            return None
+        ms, cnt = timers[name]
+        per_launch = units[name] / cnt
+        achieved = per_launch / (ms / cnt / 1e3) / 1e9
+        e = {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+             "peak_source": hbm_src, "traffic": None, "algorithmic_unit": per_launch, "launches": cnt,
+             "ms_per_launch": ms / cnt}
+        kern = "gemv_tile_kernel" if (nrhs > 1 or W["precision"] == 2) else "gemv_jobs_kernel"
+        if name == "gemv_main" and kern in GEMV_TRAFFIC and kernel_sha(kern) == GEMV_TRAFFIC[kern]["sha"]:
+            e["traffic"] = GEMV_TRAFFIC[kern]["per_alg_byte"] * per_launch
+            e["traffic_source"] = "ncu capture of the 4x4 case, scaled by algorithmic bytes"
+        return e
+
+    def fill_entry(name):
+        """ALU roofline of a bulk fill kernel: Green's-function evaluations per second."""
+        if name not in timers or units.get(name, 0) <= 0:
+            return None
+        ms, cnt = timers[name]
+        per_launch = units[name] / cnt
+        evals = per_launch / (ms / cnt / 1e3)
+        peak = FILL_F64_PEAK_EVALS if fp64_fill else FILL_F32_PEAK_EVALS
+        return {"kernel": name, "bound": "alu", "achieved": evals / 1e9, "peak": peak / 1e9, "unit": "Geval/s",
+                "frac": evals / peak, "peak_source": "derived (FP64 pipe)" if fp64_fill else "derived (SFU)",
+                "traffic": None, "algorithmic_unit": per_launch, "launches": cnt, "ms_per_launch": ms / cnt,
+                "precision": "fp64" if fp64_fill else "fp32"}
+
+    roof_mv = matvec_entry("gemv_main")
+    fills = [f for f in (fill_entry(k) for k in ("fill_L_bulk", "fill_K_bulk")) if f]
+    roof_fill = max(fills, key=lambda f: f["ms_per_launch"] * f["launches"]) if fills else None
     # the direct solves: the batched look-ahead LU (small objects) and the blocked LU (large ones)
     lu_ms = sum(timers[k][0] for k in ("lu_coop", "lu_blocked") if k in timers)
-    if lu_ms > 0:
+    roof_lu = None
+    if lu_ms > 0 and W["precision"] in (0, 2):
+        ms = lu_ms / args.steps
+        ach = lu_flops(obj_sizes) / (ms / 1e3) / 1e12
+        roof_lu = {"kernel": "lu", "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                   "frac": ach / FP64_PEAK_TFLOPS, "peak_source": "derived (FP64 pipe)", "traffic": None,
+                   "algorithmic_unit": lu_flops(obj_sizes), "launches": None, "ms_per_launch": None}
         timers["lu"] = (lu_ms, sum(timers[k][1] for k in ("lu_coop", "lu_blocked") if k in timers))
-    if "lu" in timers and W["precision"] == 0:
-        ms = timers["lu"][0] / args.steps
-        cand["lu"] = dict(bound="alu", achieved=lu_flops(obj_sizes) / (ms / 1e3) / 1e12, peak=FP64_PEAK_TFLOPS,
-                          unit="TFLOP/s", ms=timers["lu"][0], flops_per_step=lu_flops(obj_sizes))
-    for k in ("fill_K_split", "fill_L_split", "fill_K_bulk", "fill_L_bulk", "lu", "fill_K_touch", "fill_L_touch",
-              "fill_reflected"):
-        if k in timers and k not in cand:
-            cand[k] = dict(bound="alu", achieved=None, peak=FP64_PEAK_TFLOPS if W["precision"] == 0 else FP32_PEAK_TFLOPS,
-                           unit="TFLOP/s", ms=timers[k][0])
-    dom = max(cand, key=lambda k: timers[k][0]) if cand else None
-    # report the HBM-bound product when it is a large share, else the dominant kernel
-    if "gemv_main" in cand and timers["gemv_main"][0] >= 0.25 * timers[dom][0]:
-        dom = "gemv_main"
+    # the dominant kernel of the step among these
+    cands = [(roof_mv, "gemv_main"), (roof_fill, roof_fill["kernel"] if roof_fill else None), (roof_lu, "lu")]
+    cands = [(r, k) for r, k in cands if r is not None]
     roof = None
-    if dom:
-        c = cand[dom]
-        roof = {"kernel": dom, "bound": c["bound"], "achieved": c["achieved"], "peak": c["peak"], "unit": c["unit"],
-                "frac": (c["achieved"] / c["peak"]) if c["achieved"] is not None else None,
-                "peak_source": hbm_src if c["bound"] == "hbm" else "derived",
-                "traffic": None, "share_of_step": timers[dom][0] / total_ms if world == 1 else None,
-                "algorithmic_unit": c.get("bytes_per_launch") or c.get("flops_per_step")}
-        kern = "gemv_tile_kernel" if nrhs > 1 else "gemv_jobs_kernel"
-        if dom == "gemv_main" and kernel_sha(kern) == GEMV_TRAFFIC[kern]["sha"]:
-            roof["traffic"] = GEMV_TRAFFIC[kern]["per_alg_byte"] * c["bytes_per_launch"]
-            roof["traffic_source"] = "ncu capture of the 4x4 case, scaled by algorithmic bytes"
+    if cands:
+        r, k = max(cands, key=lambda rk: timers[rk[1]][0])
+        roof = dict(r)
+        roof["share_of_step"] = timers[k][0] / total_ms if world == 1 else None
     kernel_ms = {k: round(v[0] / args.steps, 4) for k, v in sorted(timers.items(), key=lambda kv: -kv[1][0])}
     out = {
         "metric": METRIC,
@@ -390,7 +433,7 @@ def run_ours(args, rank, world):
                    "parallelism": f"replicas x{world}", "l2": "flushed between steps (512 MB write)"},
         "latency_ms": {"p50": float(np.percentile(times, 50)), "p99": float(np.percentile(times, 99))},
         "gmres": {"iters": int(np.median(iters)), "relres_max": float(max(relres))},
-        "roofline": roof,
+        "roofline": roof, "roofline_matvec": roof_mv, "roofline_fill": roof_fill,
         "kernel_ms_per_step": kernel_ms,
         "gpu_launches": int(launches),
         "clocks": clk,
@@ -528,13 +571,15 @@ print(est, time.perf_counter() - t_all)
 
 
 def oracle_step_seconds(name=None, step=0, quick=False):
-    """Seconds of one oracle solve of the workload (single thread) and the sample's description.
-    quick: a smaller sample (the reference arm times one per step)."""
+    """One oracle solve of the workload on one host thread: (seconds per step, sample
+    description, extrapolated?, seconds actually spent).  quick: a smaller sample
+    (the reference arm times one per step)."""
     name = name or DEFAULT_WORKLOAD
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     if name.startswith("sphere"):
         script = ORACLE_FULL.format(root=ROOT)
         sample = "one full solve of the workload (oracle assemble + dense LU + RCS), single thread"
+        extrap = False
     else:
         npairs, nsub, ddiv = (1000, 48, 4) if quick else (3000, 96, 2)
         script = ORACLE_SAMPLED.format(root=ROOT, name=name, step=step, npairs=npairs, nsub=nsub, ddiv=ddiv)
@@ -543,10 +588,35 @@ def oracle_step_seconds(name=None, step=0, quick=False):
                   f"triangles, the layered tables whole, the dense solves on matrices 1/d of the size (d >= {ddiv}, "
                   "order <= 2048, scaled by d^3); "
                   "single thread")
+        extrap = True
     r = subprocess.run([sys.executable, "-c", script], capture_output=True, text=True, env=env, timeout=300, cwd=ROOT)
     if r.returncode != 0:
         raise RuntimeError(r.stderr[-2000:])
-    return float(r.stdout.strip().splitlines()[-1].split()[0]), sample
+    vals = [float(v) for v in r.stdout.strip().splitlines()[-1].split()]
+    return vals[0], sample, extrap, (vals[1] if len(vals) > 1 else vals[0])
+
+
+def oracle_all_cores(name, step, ncores):
+    """The oracle on every host core: ncores single-threaded copies of the same
+    sampled solve run at once (independent requests, as the GPU's replicas), each
+    extrapolated as above; aggregate solves/s = sum of the copies' rates.
+    Returns (aggregate steps/s, wall seconds spent)."""
+    name = name or DEFAULT_WORKLOAD
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    if name.startswith("sphere"):
+        script = ORACLE_FULL.format(root=ROOT)
+    else:
+        script = ORACLE_SAMPLED.format(root=ROOT, name=name, step=step, npairs=1000, nsub=48, ddiv=4)
+    t0 = time.perf_counter()
+    procs = [subprocess.Popen([sys.executable, "-c", script], stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True,
+                              env=env, cwd=ROOT) for _ in range(ncores)]
+    rate = 0.0
+    for pr in procs:
+        out, err = pr.communicate(timeout=600)
+        if pr.returncode != 0:
+            raise RuntimeError(err[-2000:])
+        rate += 1.0 / float(out.strip().splitlines()[-1].split()[0])
+    return rate, time.perf_counter() - t0
 
 
 def cpu_model():
@@ -562,10 +632,11 @@ def cpu_model():
 def run_reference(args, rank, world):
     if rank != 0:
         return None
-    times = []
-    sample = None
+    times, spent = [], 0.0
+    sample, extrap = None, False
     for i in range(args.warmup + args.steps):
-        t, sample = oracle_step_seconds(args.workload, i, quick=True)
+        t, sample, extrap, sp = oracle_step_seconds(args.workload, i, quick=True)
+        spent += sp
         if i >= args.warmup:
             times.append(t)
     total = sum(times)
@@ -577,9 +648,10 @@ def run_reference(args, rank, world):
         "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "c128", "data": "synthetic",
         "config": {"workload": args.workload, "parallelism": "host cores"},
+        "extrapolated": extrap,
         "latency_ms": {"p50": 1e3 * float(np.percentile(times, 50)), "p99": 1e3 * float(np.percentile(times, 99))},
         "cpu_baseline": {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": sample,
-                         "cpu": cpu_model(), "nproc": os.cpu_count()},
+                         "extrapolated": extrap, "sampled_s": spent, "cpu": cpu_model(), "nproc": os.cpu_count()},
         "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 
@@ -605,14 +677,26 @@ def main():
     else:
         out = run_ours(args, rank, world)
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
+            nr = len(np.atleast_2d(WORKLOADS[args.workload]["khat"]))
+            fi = len(_freqs(WORKLOADS[args.workload])) // 2
             try:
-                t, sample = oracle_step_seconds(args.workload, len(_freqs(WORKLOADS[args.workload])) // 2)
-                out["cpu_baseline"] = {"value": len(np.atleast_2d(WORKLOADS[args.workload]["khat"])) / t,
-                                       "unit": "solves/s", "cores": 1, "kind": "oracle",
-                                       "sample": sample, "cpu": cpu_model(), "nproc": os.cpu_count()}
+                t, sample, extrap, spent = oracle_step_seconds(args.workload, fi)
+                out["cpu_baseline"] = {"value": nr / t, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                                       "sample": sample, "extrapolated": extrap, "sampled_s": spent,
+                                       "cpu": cpu_model(), "nproc": os.cpu_count()}
             except Exception as e:  # the GPU line stands without it
                 out["cpu_baseline"] = {"value": None, "unit": "solves/s", "cores": 1, "kind": "oracle",
                                        "error": str(e).strip().splitlines()[-1][:300]}
+            try:
+                ncores = os.cpu_count() or 1
+                rate, wall = oracle_all_cores(args.workload, fi, ncores)
+                out["cpu_baseline_all_cores"] = {
+                    "value": nr * rate, "unit": "solves/s", "cores": ncores, "kind": "oracle",
+                    "sample": f"{ncores} single-threaded copies of the sampled solve at once (the quick sample of "
+                              "the reference arm), aggregate rate", "extrapolated": not args.workload.startswith("sphere"),
+                    "sampled_s": wall}
+            except Exception as e:
+                out["cpu_baseline_all_cores"] = {"value": None, "error": str(e).strip().splitlines()[-1][:300]}
     if rank == 0 and out is not None:
         print(json.dumps(out))
     if world > 1:

@@ -300,6 +300,12 @@ int sldm_timers_enable(int32_t on);
 int sldm_timers_reset(void);
 /* Total milliseconds and number of timed launches under `name` (0 if none). */
 int sldm_timer_get(const char* name, double* total_ms, int64_t* count);
+/* Algorithmic work of the launches timed under `name` since the last reset (the
+ * units a roofline divides by the time): "gemv*" the matrix bytes streamed
+ * (every entry of every block once per launch, low parts included);
+ * "fill_L_bulk", "fill_K_bulk" the Green's-function evaluations (36 per
+ * non-touching triangle pair).  0 for names without a count. */
+int sldm_timer_units(const char* name, double* units);
 /* Comma-separated names with recorded launches, NUL-terminated, truncated to len. */
 int sldm_timer_names(char* buf, size_t len);
 /* Number of kernel launches the library has made in this process (every

@@ -10,6 +10,7 @@
 #include <array>
 
 #include "dense.h"
+#include "gemm_tc.h"
 #include "internal.h"
 #include "mgf.h"
 #include "precond.h"
@@ -56,6 +57,7 @@ struct sldm_op {
   sldm::DBuf<int64_t> rs1, rs2;
   sldm::DBuf<int2> tl1, tl2;
   sldm::GemvPlan plan1, plan2;
+  sldm::TcPlan tc1, tc2;  // complex64: the same plans on the tensor cores (9 to 32 right-hand sides per pass)
   // complex64 operator applied with complex128 vectors (FP64 residuals of iterative refinement)
   sldm::DBuf<sldm::GemvJob> jobs1d, jobs2d;
   sldm::DBuf<int64_t> rs1d, rs2d;
@@ -90,7 +92,8 @@ static int64_t op_bytes(const sldm_op* op) {
 // vector entries of es_v bytes (the work vectors hold complex128, so both the
 // operator's precision and FP64 fit).
 static void make_plans(sldm_op* op, size_t es_m, size_t es_v, DBuf<GemvJob>& dj1, DBuf<int64_t>& drs1, DBuf<int2>& dt1,
-                       GemvPlan& p1, DBuf<GemvJob>& dj2, DBuf<int64_t>& drs2, DBuf<int2>& dt2, GemvPlan& p2) {
+                       GemvPlan& p1, DBuf<GemvJob>& dj2, DBuf<int64_t>& drs2, DBuf<int2>& dt2, GemvPlan& p2,
+                       TcPlan* tc1 = nullptr, TcPlan* tc2 = nullptr) {
   const int64_t ne = op->ne, nt = op->nt, nq = op->nq;
   auto P = [&](DBuf<char>& b, int64_t off) { return (void*)(b.p + off * es_v); };
   const char* loc = op->loc.p;
@@ -113,7 +116,8 @@ static void make_plans(sldm_op* op, size_t es_m, size_t es_v, DBuf<GemvJob>& dj1
     j2.push_back({L(o.oK), o.ne, o.ne, o.ne, P(op->we, o.e0), ne, P(op->ww2, o.e0), ne, 1, 0, 0, 0, Lo(o.oK)});
     j2.push_back({L(o.oLP), o.nt, o.nt, o.nt, P(op->wbu, o.t0), nt, P(op->ww3, o.t0), nt, 1, 0, 0, 0, Lo(o.oLP)});
   }
-  auto mk = [&](std::vector<GemvJob>& j, DBuf<GemvJob>& dj, DBuf<int64_t>& drs, DBuf<int2>& dt, GemvPlan& plan) {
+  auto mk = [&](std::vector<GemvJob>& j, DBuf<GemvJob>& dj, DBuf<int64_t>& drs, DBuf<int2>& dt, GemvPlan& plan,
+                TcPlan* tc) {
     std::vector<int64_t> rs(j.size());
     std::vector<int2> tiles;
     int64_t acc = 0;
@@ -133,9 +137,16 @@ static void make_plans(sldm_op* op, size_t es_m, size_t es_v, DBuf<GemvJob>& dj1
     plan.ntiles = int(tiles.size());
     plan.tile_rows = gemv_tile_rows(es_v);
     plan.has_lo = lo;
+    plan.bytes = 0;
+    for (auto& jb : j) plan.bytes += double(jb.m) * jb.n * es_m * (lo ? 2 : 1);
+    plan.tc = nullptr;
+    if (tc) {  // complex64 blocks and vectors: tensor-core passes of 9 to 32 right-hand sides
+      tc_plan_build(j, *tc, 0);
+      if (tc->ok) plan.tc = tc;
+    }
   };
-  mk(j1, dj1, drs1, dt1, p1);
-  mk(j2, dj2, drs2, dt2, p2);
+  mk(j1, dj1, drs1, dt1, p1, tc1);
+  mk(j2, dj2, drs2, dt2, p2, tc2);
   p1.name = "gemv_y";     // Y11, Y21 (per object)
   p2.name = "gemv_main";  // L^A_m, L^phi_m and the internal blocks
 }
@@ -151,7 +162,9 @@ static void build_plans(sldm_op* op) {
   op->wbc.alloc(nt * WR * ev); op->wbu.alloc(nt * WR * ev);
   op->wz1.alloc(ne * WR * ev); op->wz2.alloc(nt * WR * ev);
   op->ww1.alloc(ne * WR * ev); op->ww2.alloc(ne * WR * ev); op->ww3.alloc(nt * WR * ev);
-  make_plans(op, sizeof(C), sizeof(C), op->jobs1, op->rs1, op->tl1, op->plan1, op->jobs2, op->rs2, op->tl2, op->plan2);
+  const bool c64 = sizeof(C) == sizeof(float2);
+  make_plans(op, sizeof(C), sizeof(C), op->jobs1, op->rs1, op->tl1, op->plan1, op->jobs2, op->rs2, op->tl2, op->plan2,
+             c64 ? &op->tc1 : nullptr, c64 ? &op->tc2 : nullptr);
   if (sizeof(C) == sizeof(float2)) {
     make_plans(op, sizeof(C), sizeof(double2), op->jobs1d, op->rs1d, op->tl1d, op->plan1d, op->jobs2d, op->rs2d, op->tl2d,
                op->plan2d);
@@ -617,6 +630,9 @@ static void gmres_block(sldm_op* op, bool use_p, bool refine, bool x_zero, int m
     if (bnorm[r] == 0) SLDM_CUDA(cudaMemsetAsync(col(op->wx, r), 0, N * sizeof(double2), s));  // b = 0: x = 0
   }
   auto residuals = [&]() {  // wr = Dr (b - Z x), every column
+    tc_check(op->tc1, s);     // a tensor-core pass whose bounded wait ran out: SLDM_ETIMEOUT
+    tc_check(op->tc2, s);
+    tc_check(op->pc.tc, s);
     if (x_zero) SLDM_CUDA(cudaMemsetAsync(op->wr.p, 0, size_t(nr) * N * sizeof(double2), s));  // Z 0 = 0
     else apply_any(op, op->wx.p, op->wr.p, nr, s, refine);
     x_zero = false;

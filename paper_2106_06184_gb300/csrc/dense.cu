@@ -12,6 +12,7 @@
 #include <type_traits>
 
 #include "dense.h"
+#include "gemm_tc.h"
 
 namespace sldm {
 
@@ -715,7 +716,7 @@ __device__ __forceinline__ void warp_tsum(R (&v)[K], int lane) {
 // join the error sum, so the result is that of the FP64 operator A + Alo.
 template <class CM, class CV, int NR, bool LO = false>
 __global__ void __launch_bounds__(256, LO ? 1 : 2) gemv_tile_kernel(const GemvJob* __restrict__ jobs,
-                                                                   const int2* __restrict__ tiles, int nrhs) {
+                                                                   const int2* __restrict__ tiles, int nrhs, int col0) {
   typedef GemvTile<CM, CV> T;
   typedef typename CT<CV>::R R;
   constexpr int RW = T::RW, CW = T::CW, ST = T::ST;
@@ -729,7 +730,8 @@ __global__ void __launch_bounds__(256, LO ? 1 : 2) gemv_tile_kernel(const GemvJo
   const int row0 = t.y + warp * RW;
   const CM* __restrict__ A = reinterpret_cast<const CM*>(J.A);
   const CM* __restrict__ Alo = reinterpret_cast<const CM*>(LO ? J.Alo : J.A);
-  const CV* __restrict__ x = reinterpret_cast<const CV*>(J.x);
+  // right-hand sides col0 .. col0 + nrhs - 1 of the job's vectors
+  const CV* __restrict__ x = reinterpret_cast<const CV*>(J.x) + int64_t(col0) * J.ldx;
   const int nch = (J.n + CW - 1) / CW;
   // per-thread copy sources (row 0 / right-hand side 0 stand in for rows or
   // right-hand sides outside the job: valid addresses, copied as zeros) and
@@ -905,7 +907,7 @@ __global__ void __launch_bounds__(256, LO ? 1 : 2) gemv_tile_kernel(const GemvJo
   constexpr int V = K >= 32 ? K / 32 : 1;
   constexpr int S = K >= 32 ? 0 : (K == 16 ? 1 : K == 8 ? 2 : K == 4 ? 3 : 4);
   warp_tsum<K, 16>(acc, lane);
-  CV* y = reinterpret_cast<CV*>(J.y);
+  CV* y = reinterpret_cast<CV*>(J.y) + int64_t(col0) * J.ldy;
   auto put = [&](int p, R re, R im) {  // p = row-in-warp * NR + rhs
     const int i = p / NR, r = p % NR, row = row0 + i;
     if (row < J.m && r < nrhs) {
@@ -931,7 +933,7 @@ __global__ void __launch_bounds__(256, LO ? 1 : 2) gemv_tile_kernel(const GemvJo
 }
 
 template <class CM, class CV, int NR, bool LO = false>
-static void launch_tile(const GemvPlan& plan, int nrhs, cudaStream_t s) {
+static void launch_tile(const GemvPlan& plan, int nrhs, cudaStream_t s, int col0) {
   typedef GemvTile<CM, CV> T;
   constexpr size_t smem = T::template smem<NR, LO>();
   static_assert(smem <= 227 * 1024, "tile kernel exceeds the shared memory of one CTA");
@@ -944,7 +946,7 @@ static void launch_tile(const GemvPlan& plan, int nrhs, cudaStream_t s) {
                                    int(smem)));
     done.fetch_or(bit);
   }
-  gemv_tile_kernel<CM, CV, NR, LO><<<unsigned(plan.ntiles), 256, smem, s>>>(plan.jobs, plan.tiles, nrhs);
+  gemv_tile_kernel<CM, CV, NR, LO><<<unsigned(plan.ntiles), 256, smem, s>>>(plan.jobs, plan.tiles, nrhs, col0);
   count_launch();
 }
 
@@ -953,27 +955,42 @@ void gemv_jobs_mixed(const GemvPlan& plan, int nrhs, cudaStream_t s) {
   if (plan.njobs == 0) return;
   const int64_t threads = plan.total_rows * 32;
   const unsigned blocks = unsigned((threads + 255) / 256);
-  ScopedTimer tm(plan.name, s);
+  SLDM_REQUIRE(nrhs >= 1 && nrhs <= MAX_NRHS, SLDM_EINVAL, "GEMV: 1 to 32 right-hand sides per pass");
   constexpr bool comp = std::is_same<CM, float2>::value && std::is_same<CV, double2>::value;
+  constexpr bool c64 = std::is_same<CM, float2>::value && std::is_same<CV, float2>::value;
+  if constexpr (c64) {
+    if (nrhs > TILE_NRHS && plan.tc != nullptr && plan.tc->ok) {  // one tensor-core pass
+      ScopedTimer tm(plan.name, s);
+      timer_units(plan.name, plan.bytes);
+      gemm_tc(plan, *plan.tc, nrhs, s);
+      return;
+    }
+  }
+  ScopedTimer tm(plan.name, s);
+  timer_units(plan.name, plan.bytes * double((nrhs + TILE_NRHS - 1) / TILE_NRHS));
   if (nrhs >= 2 || comp) {
     SLDM_REQUIRE((plan.tiles != nullptr && plan.tile_rows == GemvTile<CM, CV>::ROWS), SLDM_EINVAL,
                  "GEMV plan without row tiles for this vector type");
     if (plan.ntiles == 0) return;
-    if constexpr (comp) {
-      if (plan.has_lo) {  // the FP64 operator held as a complex64 pair
-        if (nrhs <= 1) launch_tile<CM, CV, 1, true>(plan, nrhs, s);
-        else if (nrhs <= 2) launch_tile<CM, CV, 2, true>(plan, nrhs, s);
-        else if (nrhs <= 4) launch_tile<CM, CV, 4, true>(plan, nrhs, s);
-        else launch_tile<CM, CV, 8, true>(plan, nrhs, s);
-        SLDM_CUDA(cudaGetLastError());
-        return;
+    // passes of up to 8 right-hand sides on the CUDA cores
+    for (int c0 = 0; c0 < nrhs; c0 += TILE_NRHS) {
+      const int nr = std::min(TILE_NRHS, nrhs - c0);
+      if constexpr (comp) {
+        if (plan.has_lo) {  // the FP64 operator held as a complex64 pair
+          if (nr <= 1) launch_tile<CM, CV, 1, true>(plan, nr, s, c0);
+          else if (nr <= 2) launch_tile<CM, CV, 2, true>(plan, nr, s, c0);
+          else if (nr <= 4) launch_tile<CM, CV, 4, true>(plan, nr, s, c0);
+          else launch_tile<CM, CV, 8, true>(plan, nr, s, c0);
+          continue;
+        }
       }
+      if (nr <= 1) {
+        if constexpr (comp) launch_tile<CM, CV, 1>(plan, nr, s, c0);  // the only one-column use
+        else launch_tile<CM, CV, 2>(plan, nr, s, c0);
+      } else if (nr <= 2) launch_tile<CM, CV, 2>(plan, nr, s, c0);
+      else if (nr <= 4) launch_tile<CM, CV, 4>(plan, nr, s, c0);
+      else launch_tile<CM, CV, 8>(plan, nr, s, c0);
     }
-    if (nrhs <= 1) {
-      if constexpr (comp) launch_tile<CM, CV, 1>(plan, nrhs, s);  // the only one-column use
-    } else if (nrhs <= 2) launch_tile<CM, CV, 2>(plan, nrhs, s);
-    else if (nrhs <= 4) launch_tile<CM, CV, 4>(plan, nrhs, s);
-    else launch_tile<CM, CV, 8>(plan, nrhs, s);
   } else {
     gemv_jobs_kernel<CM, CV, 1><<<blocks, 256, 0, s>>>(plan.jobs, plan.rowstart, plan.njobs, plan.total_rows, nrhs);
     count_launch();

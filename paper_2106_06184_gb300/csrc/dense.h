@@ -42,6 +42,7 @@ struct GemvJob {
   // lda), or null; read only by the FP64-accumulated complex64 product
   const void* Alo;
 };
+struct TcPlan;
 struct GemvPlan {
   const char* name = "gemv";   // timer name of its launches
   GemvJob* jobs = nullptr;     // device
@@ -56,9 +57,16 @@ struct GemvPlan {
   // every job carries Alo (complex64 blocks with complex128 vectors only): the
   // product is that of the FP64 operator A + Alo
   bool has_lo = false;
+  double bytes = 0;  // matrix bytes one launch streams (its timer's algorithmic units)
+  // complex64 blocks and vectors: the tensor-core plan for 9 to 32 right-hand
+  // sides per pass (gemm_tc.h), or null / not ok for passes of 8 on the CUDA cores
+  const TcPlan* tc = nullptr;
 };
-// right-hand sides per pass of the structured product and the preconditioner
-constexpr int MAX_NRHS = 8;
+// right-hand sides in lockstep (GMRES) and per pass of the structured product
+// and the preconditioner: up to 32 (tensor cores for complex64 operators; the
+// CUDA-core kernels take 8 per launch)
+constexpr int MAX_NRHS = 32;
+constexpr int TILE_NRHS = 8;
 // rows per tile of the several-right-hand-side kernel for vectors of es_v bytes
 inline int gemv_tile_rows(size_t es_v) { return es_v == 8 ? 32 : 16; }
 template <class C>

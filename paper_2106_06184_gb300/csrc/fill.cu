@@ -655,6 +655,15 @@ void fill_L(const sldm_mesh* m, const std::vector<LTask>& tasks, cudaStream_t s)
   dt.upload(tasks, s);
   dtl.upload(tiles, s);
   const DevMesh& d = m->d;
+  const std::vector<int32_t> ot = unsplit_object_tasks(m->h, tasks, split);
+  if (timers_on()) {  // evaluations of the bulk kernel: 36 per non-touching pair of the unsplit tasks
+    double pairs = 0;
+    for (size_t i = 0; i < tasks.size(); ++i)
+      if (!split[i]) pairs += double(tasks[i].ntest) * tasks[i].nsrc;
+    for (size_t k = 0; k < m->h.touchL_a.size(); ++k)
+      if (ot[size_t(m->h.obj[m->h.touchL_a[k]])] >= 0) pairs -= 1;
+    timer_units("fill_L_bulk", 36.0 * pairs);
+  }
   for (size_t off = 0; off < tiles.size(); off += 1u << 30) {
     unsigned nb = unsigned(std::min<size_t>(tiles.size() - off, 1u << 30));
     ScopedTimer tm("fill_L_bulk", s);
@@ -663,7 +672,7 @@ void fill_L(const sldm_mesh* m, const std::vector<LTask>& tasks, cudaStream_t s)
   SLDM_CUDA(cudaGetLastError());
   const int np = int(m->h.touchL_a.size());
   DBuf<int32_t> dot;
-  dot.upload(unsplit_object_tasks(m->h, tasks, split), s);
+  dot.upload(ot, s);
   if (np > 0) {
     ScopedTimer tm("fill_L_touch", s);
     fill_L_touch<R><<<unsigned((int64_t(np) * 8 + 255) / 256), 256, 0, s>>>(dt.p, dot.p, d.obj.p, d.touchL_a.p, d.touchL_b.p, np,
@@ -695,6 +704,17 @@ void fill_K(const sldm_mesh* m, const std::vector<KTask>& tasks, cudaStream_t s)
   dt.upload(tasks, s);
   dtl.upload(tiles, s);
   const DevMesh& d = m->d;
+  if (timers_on()) {  // evaluations of the bulk kernel: 36 per pair that is neither a child of its test triangle nor touching
+    const std::vector<int32_t> ot = unsplit_object_tasks(m->h, tasks, split);
+    double pairs = 0;
+    for (size_t i = 0; i < tasks.size(); ++i)
+      if (!split[i]) pairs += double(tasks[i].ntest) * tasks[i].nsrc;
+    for (int64_t o = 0; o < m->h.nobj; ++o)
+      if (ot[size_t(o)] >= 0) pairs -= 6.0 * (m->h.tri_begin[o + 1] - m->h.tri_begin[o]);
+    for (size_t k = 0; k < m->h.touchK_a.size(); ++k)
+      if (ot[size_t(m->h.obj[m->h.touchK_a[k]])] >= 0) pairs -= 1;
+    timer_units("fill_K_bulk", 36.0 * pairs);
+  }
   if (!tiles.empty()) {
     ScopedTimer tm("fill_K_bulk", s);
     fill_K_bulk<R><<<unsigned(tiles.size()), TILE_SRC, 0, s>>>(dt.p, dtl.p, d.geo.p, d.bgeo.p, d.tri.p, d.tri_edge.p,

@@ -1,0 +1,595 @@
+// Complex64 block products with 9 to 32 right-hand sides on the tcgen05 tensor
+// cores (the multi-RHS matrix-vector products of GMRES on Eq. finalsystem, one
+// pass over the stored blocks per step).
+//
+// Complex product as one real GEMM.  A complex64 row-major block A (m x n) is,
+// byte for byte, a row-major FP32 matrix A' of m rows and 2n columns (re, im
+// interleaved).  With B' (2n x 64) holding, for right-hand side r, the columns
+//     B'[2c, 2r] = Re x_r[c],  B'[2c+1, 2r] = -Im x_r[c]
+//     B'[2c, 2r+1] = Im x_r[c], B'[2c+1, 2r+1] = Re x_r[c],
+// D = A' B' holds Re y_r in column 2r and Im y_r in column 2r+1.  A' is the
+// stored block itself (the MMA's K-major A operand, streamed by TMA); B' is built
+// per K chunk in shared memory from the complex64 vectors.
+//
+// FP32 accuracy from TF32 operands (three products): with hi(v) = v rounded to
+// TF32 (|v - hi| <= 2^-12 |v|) and lo(v) = v - hi rounded to TF32 (error <= 2^-24 |v|),
+//     D = hi(A) hi(B) + lo(A) hi(B) + hi(A) lo(B)        (FP32 accumulation),
+// the dropped lo(A) lo(B) (<= 2^-24 |A||B|) and the two roundings of lo leave
+// each product term within ~3 x 2^-24 of |A||B|, FP32-like.
+//
+// Per CTA (one per SM, persistent over its tiles, longest first), 128-row
+// tiles streamed in stages of 4 TMA boxes (128 rows x 4 x 128 B, 128-byte
+// swizzled): 512 contiguous bytes of every row per stage, which DRAM serves at
+// ~0.98 of the copy rate, against ~0.65 for 128-byte runs.  Each stage is
+// split into four K sub-chunks of 32 FP32 columns.  Warp-specialised,
+// synchronised by mbarriers only:
+//   warp 0   TMA: a ring of 2 stages (128 KB in flight per SM);
+//   warps 2-5 split: thread = row; for each sub-chunk reads its row, splits it
+//            into hi and lo and stores both into a TMEM operand buffer (A of
+//            the MMA in tensor memory: lane = row, column = K), and builds hi/lo
+//            of the B' sub-chunk (64 x 128 B, swizzled) in shared memory from
+//            vectors copied (cp.async) three sub-chunks ahead; the ring stage is
+//            freed after its fourth sub-chunk;
+//   warp 1   MMA: one thread issues 12 MMAs per sub-chunk (4 K steps x 3
+//            products, M 128, N 64, K 8) into one of two 64-column TMEM
+//            accumulators, a fresh one for every stage (a segment of 128 K
+//            columns), and commits them to the operand buffer's barrier;
+//   warps 6-13 epilogue: fold each segment's accumulator into compensated FP32
+//            sums in registers (warp w: TMEM lanes 32 (w % 4) .., 32 of the 64
+//            columns), and at the end of a tile write Y.
+// The tensor core rounds its FP32 accumulator at every MMA: a tile's ~10^4
+// MMAs into one accumulator would lose ~2^-17 of the result; segments of 48
+// MMAs and compensated sums across them keep the product as accurate as an
+// FP32 CUDA-core product.
+// Operand buffers (TMEM A, shared B') and accumulators are double-buffered.
+// Tiles are padded to whole stages (zero columns from TMA and zero B').
+#include <cuda.h>
+
+#include <algorithm>
+#include <cstring>
+#include <queue>
+
+#include "gemm_tc.h"
+
+namespace sldm {
+
+namespace {
+
+constexpr int TC_M = 128;
+constexpr int TC_N = 2 * TC_MAX_NRHS;  // 64 accumulator columns
+constexpr int TC_KC = 32;              // FP32 columns of A per chunk: one 128-byte swizzle row
+constexpr int TC_BPS = 4;              // TMA boxes (sub-chunks) per stage
+constexpr int TC_R = 2;                // stages in the ring
+constexpr int TC_THREADS = 448;        // 14 warps: TMA, MMA, 4 split, 8 epilogue
+constexpr uint32_t TC_A_BYTES = TC_M * TC_KC * 4;  // 16 KB: one box, one sub-chunk
+constexpr uint32_t TC_STAGE_BYTES = TC_BPS * TC_A_BYTES;
+constexpr uint32_t TC_B_BYTES = TC_N * TC_KC * 4;  // 8 KB
+constexpr uint32_t TC_BBUF = 2 * TC_B_BYTES;       // B' hi, lo
+constexpr uint32_t TC_RING = TC_R * TC_STAGE_BYTES;
+// TMEM: accumulators at columns 0 and 64, A operand buffers (hi 32 + lo 32 columns) at 128 and 192
+constexpr uint32_t TC_TMEM_COLS = 256;
+constexpr uint32_t TC_ACC_COL = 0, TC_AOP_COL = 128;
+// vectors: a ring of 4 sub-chunks, copied 3 ahead; per sub-chunk each of the 128
+// split threads holds the 8 complex64 entries it needs (64 B)
+constexpr int TC_XR = 4;
+constexpr uint32_t TC_XBYTES = 128 * 64;  // 8 KB per sub-chunk
+constexpr size_t TC_SMEM = size_t(TC_RING) + 2 * size_t(TC_BBUF) + size_t(TC_XR) * TC_XBYTES + 1024 + 256;
+constexpr uint32_t TC_SPIN = 1u << 21;  // try_wait rounds before a wait is declared failed
+
+static_assert(TC_BBUF % 1024 == 0 && TC_A_BYTES % 1024 == 0 && TC_B_BYTES % 1024 == 0, "swizzle atoms are 1 KB aligned");
+static_assert(TC_SMEM <= 227 * 1024, "ring and operand buffers exceed the shared memory of a CTA");
+
+// instruction descriptor, kind::tf32: D FP32 (bits 4-5 = 1), A and B TF32 (bits
+// 7-9, 10-12 = 2), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at 24-28
+constexpr uint32_t TC_IDESC = (1u << 4) | (2u << 7) | (2u << 10) | (uint32_t(TC_N >> 3) << 17) | (uint32_t(TC_M >> 4) << 24);
+
+// shared-memory matrix descriptor of a K-major operand in the 128-byte swizzled
+// layout: start address >> 4 (bits 0-13), leading byte offset 16 B (unused for
+// this layout, bits 16-29), stride byte offset 1024 B between 8-row groups
+// (bits 32-45), descriptor version 1 (bit 46), swizzle mode 2 = 128 B (bits 61-63)
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  return uint64_t((saddr & 0x3FFFFu) >> 4) | (uint64_t(1) << 16) | (uint64_t(1024 >> 4) << 32) | (uint64_t(1) << 46) |
+         (uint64_t(2) << 61);
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+// bounded wait for the phase of parity `parity` to complete; gives up early
+// when another warp recorded a failure in *fail (shared memory)
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const volatile int* fail = nullptr) {
+  for (uint32_t it = 0; it < TC_SPIN; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (fail && (it & 63) == 63 && *fail) return false;
+  }
+  return false;
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const void* map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(map), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+// D (TMEM) (+)= A (TMEM: lane = row, one TF32 per column) x B (shared memory descriptor)
+__device__ __forceinline__ void tc_mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(b), "r"(TC_IDESC), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// 32 consecutive accumulator columns of this warp's 32 TMEM lanes
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// 32 consecutive TMEM columns of this warp's 32 lanes from registers
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const float (&v)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};\n" ::"r"(taddr),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
+      "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
+      "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+      "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15])),
+      "r"(__float_as_uint(v[16])), "r"(__float_as_uint(v[17])), "r"(__float_as_uint(v[18])), "r"(__float_as_uint(v[19])),
+      "r"(__float_as_uint(v[20])), "r"(__float_as_uint(v[21])), "r"(__float_as_uint(v[22])), "r"(__float_as_uint(v[23])),
+      "r"(__float_as_uint(v[24])), "r"(__float_as_uint(v[25])), "r"(__float_as_uint(v[26])), "r"(__float_as_uint(v[27])),
+      "r"(__float_as_uint(v[28])), "r"(__float_as_uint(v[29])), "r"(__float_as_uint(v[30])), "r"(__float_as_uint(v[31]))
+      : "memory");
+}
+
+// FP32 -> TF32 (10 mantissa bits), round to nearest, ties away from zero: the
+// result is an FP32 value with its 13 low mantissa bits zero, which the MMA
+// takes exactly
+__device__ __forceinline__ float tf32_rn(float v) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+  return __uint_as_float(r);
+}
+// v = hi + lo: hi = tf32(v) (|v - hi| <= 2^-12 |v|), lo = tf32(v - hi) (rounding
+// error <= 2^-12 |v - hi| <= 2^-24 |v|), both exact TF32 operands
+__device__ __forceinline__ void tf32_split(float v, float& hi, float& lo) {
+  hi = tf32_rn(v);
+  lo = tf32_rn(v - hi);
+}
+
+// byte offset of 16-byte chunk j (0..7) of row `row` in a 128-byte swizzled tile
+__device__ __forceinline__ uint32_t sw128_off(int row, int j) { return uint32_t(row) * 128u + uint32_t((j ^ (row & 7)) * 16); }
+
+}  // namespace
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    gemm_tc_kernel(const GemvJob* __restrict__ jobs, const unsigned char* __restrict__ maps, const TcTile* __restrict__ tiles,
+                   const int32_t* __restrict__ cta_begin, int nrhs, int* err) {
+  extern __shared__ unsigned char tc_raw[];
+  const int t_begin = cta_begin[blockIdx.x], t_end = cta_begin[blockIdx.x + 1];
+  if (t_begin >= t_end) return;
+  const uint32_t raw = smem_u32(tc_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;  // ring[R], B'[2], x ring
+  unsigned char* gb = tc_raw + (base - raw);
+  const uint32_t bbuf0 = base + TC_RING;
+  const uint32_t xring = bbuf0 + 2 * TC_BBUF;
+  const uint32_t bars = xring + TC_XR * TC_XBYTES;
+  // barriers (8 bytes each): full[R], empty[R], ready[2], wfree[2], accfull[2], accempty[2]
+  auto full = [&](int s) { return bars + 8u * uint32_t(s); };
+  auto empty = [&](int s) { return bars + 8u * uint32_t(TC_R + s); };
+  auto ready = [&](int b) { return bars + 8u * uint32_t(2 * TC_R + b); };
+  auto wfree = [&](int b) { return bars + 8u * uint32_t(2 * TC_R + 2 + b); };
+  auto accfull = [&](int a) { return bars + 8u * uint32_t(2 * TC_R + 4 + a); };
+  auto accempty = [&](int a) { return bars + 8u * uint32_t(2 * TC_R + 6 + a); };
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gb + (bars - base) + 8 * (2 * TC_R + 8));
+  __shared__ int s_fail;
+  volatile int* vfail = &s_fail;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  if (tid == 0) {
+    for (int q = 0; q < TC_R; ++q) {
+      mbar_init(full(q), 1);
+      mbar_init(empty(q), 4);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(ready(b), 4);
+      mbar_init(wfree(b), 1);
+      mbar_init(accfull(b), 1);
+      mbar_init(accempty(b), 8);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_fail = 0;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TC_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  // sub-chunks of a tile, padded to whole stages
+  auto nk_of = [&](int t) {
+    const int nk = (2 * jobs[tiles[t].job].n + TC_KC - 1) / TC_KC;
+    return (nk + TC_BPS - 1) / TC_BPS * TC_BPS;
+  };
+  int total = 0;  // sub-chunks of this CTA (a multiple of TC_BPS)
+  for (int t = t_begin; t < t_end; ++t) total += nk_of(t);
+  const int nstages = total / TC_BPS;
+
+  if (warp == 0) {
+    // ---------------- TMA producer: one stage = 4 boxes along K
+    if (lane == 0) {
+      int tile = t_begin, k = 0, nk = nk_of(t_begin), st = 0;
+      for (; st < nstages; ++st) {
+        const int q = st % TC_R;
+        if (st >= TC_R && !mbar_wait(empty(q), uint32_t(((st / TC_R) - 1) & 1), vfail)) {
+          *vfail = 1;
+          break;
+        }
+        const TcTile T = tiles[tile];
+        mbar_expect_tx(full(q), TC_STAGE_BYTES);
+#pragma unroll
+        for (int bx = 0; bx < TC_BPS; ++bx)
+          tma_load_2d(base + uint32_t(q) * TC_STAGE_BYTES + uint32_t(bx) * TC_A_BYTES, maps + size_t(T.job) * 128,
+                      (k + bx) * TC_KC, T.row0, full(q));
+        k += TC_BPS;
+        if (k == nk) {
+          k = 0;
+          if (++tile < t_end) nk = nk_of(tile);
+        }
+      }
+      // the loads in flight (the latest stage of each slot) land before the CTA leaves
+      for (int q = (st > TC_R ? st - TC_R : 0); q < st; ++q) mbar_wait(full(q % TC_R), uint32_t((q / TC_R) & 1));
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    // ---------------- MMA issuer
+    if (lane == 0) {
+      int tile_i = 0, k = 0, nk = nk_of(t_begin), last = -1;
+      for (int g = 0; g < total; ++g) {
+        const int b = g & 1, seg = g / TC_BPS, j = g % TC_BPS;
+        bool ok = true;
+        if (j == 0 && seg >= 2) ok = mbar_wait(accempty(seg & 1), uint32_t(((seg >> 1) - 1) & 1), vfail);
+        if (ok) ok = mbar_wait(ready(b), uint32_t((g >> 1) & 1), vfail);
+        if (!ok) {
+          *vfail = 1;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t acc = tmem + TC_ACC_COL + uint32_t(seg & 1) * 64u;
+        const uint32_t aop = tmem + TC_AOP_COL + uint32_t(b) * 64u;  // hi at +0, lo at +32
+        const uint32_t bh = bbuf0 + uint32_t(b) * TC_BBUF, bl = bh + TC_B_BYTES;
+#pragma unroll
+        for (int ks = 0; ks < TC_KC / 8; ++ks) {
+          const uint32_t o = uint32_t(ks) * 32u;  // 8 TF32 = 32 bytes along K in the swizzle row of B'
+          const uint32_t ac = uint32_t(ks) * 8u;  // 8 TMEM columns of A
+          const uint32_t acc0 = (j > 0 || ks > 0) ? 1u : 0u;  // a fresh accumulator per segment
+          tc_mma_ts(acc, aop + ac, sw128_desc(bh + o), acc0);
+          tc_mma_ts(acc, aop + 32u + ac, sw128_desc(bh + o), 1u);
+          tc_mma_ts(acc, aop + ac, sw128_desc(bl + o), 1u);
+        }
+        tc_commit(wfree(b));
+        if (j == TC_BPS - 1) tc_commit(accfull(seg & 1));
+        last = g;
+        if (++k == nk) {
+          k = 0;
+          ++tile_i;
+          if (t_begin + tile_i < t_end) nk = nk_of(t_begin + tile_i);
+        }
+      }
+      // the MMAs in flight (they complete in order) finish before the CTA leaves
+      if (last >= 0) mbar_wait(wfree(last & 1), uint32_t((last >> 1) & 1));
+    }
+    __syncwarp();
+  } else if (warp < 6) {
+    // ---------------- split warps: thread = row of the tile (TMEM lane quarter warp % 4)
+    const int q4 = warp & 3, row = 32 * q4 + lane;
+    // share of B' (64 rows x 8 chunks of 16 B, hi and lo): 16-byte chunk c = ti & 7 of rows
+    // 2 (rb + 8 m) + rr, m = 0..3 (rr = (ti >> 3) & 1, rb = ti >> 4): a warp stores 4 whole rows
+    // per instruction, free of bank conflicts.  Those need x_{rb + 8m} at complex columns 2c, 2c + 1.
+    const int ti = tid - 64, bc = ti & 7, brr = (ti >> 3) & 1, brb = ti >> 4;
+    int xt = t_begin, xk = 0, xnk = nk_of(t_begin), xg = 0;
+    const float2* xjob = reinterpret_cast<const float2*>(jobs[tiles[t_begin].job].x);
+    int64_t xld = jobs[tiles[t_begin].job].ldx;
+    int xn_cols = jobs[tiles[t_begin].job].n;
+    auto copy_x = [&]() {  // sub-chunk xg into its ring slot (zero-filled beyond the job's columns or nrhs)
+      if (xg < total) {
+        const int c0 = xk * (TC_KC / 2) + 2 * bc;
+        // slot layout [entry e = 2m + u][thread]: consecutive threads, consecutive 8-byte words
+        const uint32_t dst = xring + uint32_t(xg % TC_XR) * TC_XBYTES + uint32_t(ti) * 8u;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          const int r = brb + 8 * m;
+          const float2* x = xjob + int64_t(r < nrhs ? r : 0) * xld;
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const bool v = r < nrhs && c0 + u < xn_cols;
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(dst + uint32_t(2 * m + u) * 1024u),
+                         "l"(v ? x + c0 + u : xjob), "r"(v ? 8 : 0)
+                         : "memory");
+          }
+        }
+        if (++xk == xnk) {
+          xk = 0;
+          if (++xt < t_end) {
+            const GemvJob& J = jobs[tiles[xt].job];
+            xnk = nk_of(xt);
+            xjob = reinterpret_cast<const float2*>(J.x);
+            xld = J.ldx;
+            xn_cols = J.n;
+          }
+        }
+        ++xg;
+      }
+      asm volatile("cp.async.commit_group;\n" ::: "memory");  // one group per sub-chunk, possibly empty
+    };
+    for (int i = 0; i < TC_XR - 1; ++i) copy_x();
+    for (int g = 0; g < total; ++g) {
+      const int st = g / TC_BPS, j = g % TC_BPS, q = st % TC_R, b = g & 1;
+      copy_x();                                                                  // sub-chunk g + 3
+      asm volatile("cp.async.wait_group %0;\n" ::"n"(TC_XR - 1) : "memory");  // this thread's copies of g landed
+      float4 xv[4];  // (x_{rb+8m}[2c], x_{rb+8m}[2c+1]) as (re, im, re, im)
+      {
+        const float2* xs = reinterpret_cast<const float2*>(gb + (xring - base) + size_t(g % TC_XR) * TC_XBYTES) + ti;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          const float2 a0 = xs[(2 * m) * 128], a1 = xs[(2 * m + 1) * 128];
+          xv[m] = make_float4(a0.x, a0.y, a1.x, a1.y);
+        }
+      }
+      bool ok = mbar_wait(full(q), uint32_t((st / TC_R) & 1), vfail);
+      if (ok && g >= 2) ok = mbar_wait(wfree(b), uint32_t(((g >> 1) - 1) & 1), vfail);
+      ok = __all_sync(0xffffffffu, ok);  // the TMEM stores below need the whole warp
+      if (!ok) {
+        *vfail = 1;
+        break;
+      }
+      // this row of box j of the landed stage: 8 x 16 B, swizzled
+      const unsigned char* rp = gb + size_t(q) * TC_STAGE_BYTES + size_t(j) * TC_A_BYTES + size_t(row) * 128;
+      float h[32], l[32];
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj) {
+        const float4 a = *reinterpret_cast<const float4*>(rp + ((jj ^ (row & 7)) * 16));
+        tf32_split(a.x, h[4 * jj], l[4 * jj]);
+        tf32_split(a.y, h[4 * jj + 1], l[4 * jj + 1]);
+        tf32_split(a.z, h[4 * jj + 2], l[4 * jj + 2]);
+        tf32_split(a.w, h[4 * jj + 3], l[4 * jj + 3]);
+      }
+      const uint32_t ta = tmem + (uint32_t(32 * q4) << 16) + TC_AOP_COL + uint32_t(b) * 64u;
+      tmem_st32(ta, h);
+      tmem_st32(ta + 32u, l);
+      // hi/lo of B' for this sub-chunk: row 2r gives Re y_r ([xr, -xi] per complex column), row 2r+1 Im y_r ([xi, xr])
+      {
+        unsigned char* Bh = gb + TC_RING + size_t(b) * TC_BBUF;
+        unsigned char* Bl = Bh + TC_B_BYTES;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          const int brow = 2 * (brb + 8 * m) + brr;
+          const float4 a = xv[m];
+          const float4 v = brr ? make_float4(a.y, a.x, a.w, a.z) : make_float4(a.x, -a.y, a.z, -a.w);
+          float4 hv, lv;
+          tf32_split(v.x, hv.x, lv.x);
+          tf32_split(v.y, hv.y, lv.y);
+          tf32_split(v.z, hv.z, lv.z);
+          tf32_split(v.w, hv.w, lv.w);
+          const uint32_t off = sw128_off(brow, bc);
+          *reinterpret_cast<float4*>(Bh + off) = hv;
+          *reinterpret_cast<float4*>(Bl + off) = lv;
+        }
+      }
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+      fence_async_smem();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) {
+        if (j == TC_BPS - 1) mbar_arrive(empty(q));  // the stage's last sub-chunk: it may be refilled
+        mbar_arrive(ready(b));                        // A (TMEM) and B' (shared) of this sub-chunk are in place
+      }
+    }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");  // no copy in flight when the CTA leaves
+  } else {
+    // ---------------- epilogue warps: TMEM lane quarter warp % 4, accumulator columns 32 half ..
+    const int q4 = warp & 3, half = (warp - 6) >> 2;
+    float cs[32], cc[32];  // compensated sums of this row's 32 columns over the tile's segments
+#pragma unroll
+    for (int i = 0; i < 32; ++i) cs[i] = cc[i] = 0.f;
+    int seg = 0;
+    for (int t = t_begin; t < t_end; ++t) {
+      const int nseg = nk_of(t) / TC_BPS;
+      bool ok = true;
+      for (int sg = 0; sg < nseg; ++sg, ++seg) {
+        ok = __all_sync(0xffffffffu, mbar_wait(accfull(seg & 1), uint32_t((seg >> 1) & 1), vfail));
+        if (!ok) break;  // the TMEM loads below need the whole warp
+        tc_fence_after();
+        float v[32];
+        tmem_ld32(tmem + (uint32_t(32 * q4) << 16) + TC_ACC_COL + uint32_t(seg & 1) * 64u + uint32_t(half * 32), v);
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(accempty(seg & 1));  // the accumulator may take the next segment
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {  // TwoSum (Knuth): cs + cc carries the running sum
+          const float sum = __fadd_rn(cs[i], v[i]);
+          const float bp = __fsub_rn(sum, cs[i]);
+          cc[i] = __fadd_rn(cc[i], __fadd_rn(__fsub_rn(cs[i], __fsub_rn(sum, bp)), __fsub_rn(v[i], bp)));
+          cs[i] = sum;
+        }
+      }
+      if (!ok) {
+        *vfail = 1;
+        break;
+      }
+      const TcTile T = tiles[t];
+      const GemvJob J = jobs[T.job];
+      const int row = T.row0 + 32 * q4 + lane;
+      if (row < J.m) {
+        float2* y = reinterpret_cast<float2*>(J.y);
+        const float ar = float(J.ar), ai = float(J.ai);
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          const int r = half * 16 + c;
+          if (r < nrhs) {
+            const float re = cs[2 * c] + cc[2 * c], im = cs[2 * c + 1] + cc[2 * c + 1];
+            float2 o = make_float2(ar * re - ai * im, ar * im + ai * re);
+            float2* yy = y + int64_t(r) * J.ldy + row;
+            if (J.beta) {
+              const float2 bb = *yy;
+              o.x += bb.x;
+              o.y += bb.y;
+            }
+            *yy = o;
+          }
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 32; ++i) cs[i] = cc[i] = 0.f;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (tid == 0 && *vfail) atomicExch(err, 1);
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS) : "memory");
+}
+
+// ---------------------------------------------------------------- host side
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*, const cuuint64_t*,
+                                  const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encoder() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+void tc_plan_build(const std::vector<GemvJob>& jobs, TcPlan& tp, cudaStream_t s) {
+  tp.ok = false;
+  EncodeTiledFn enc = encoder();
+  if (!enc || jobs.empty()) return;
+  static_assert(sizeof(CUtensorMap) == 128, "tensor map size");
+  std::vector<unsigned char> maps(jobs.size() * 128);
+  std::vector<TcTile> tl;
+  std::vector<int> cost;
+  for (size_t i = 0; i < jobs.size(); ++i) {
+    const GemvJob& J = jobs[i];
+    const uint64_t pitch = uint64_t(J.lda) * 8;
+    if (J.m <= 0 || J.n <= 0 || pitch % 16 != 0 || (reinterpret_cast<uintptr_t>(J.A) & 15) != 0) return;
+    alignas(64) CUtensorMap map;
+    const cuuint64_t dims[2] = {cuuint64_t(2) * J.n, cuuint64_t(J.m)};
+    const cuuint64_t strides[1] = {pitch};
+    const cuuint32_t box[2] = {cuuint32_t(TC_KC), cuuint32_t(TC_M)};
+    const cuuint32_t estr[2] = {1, 1};
+    if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(J.A), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return;
+    std::memcpy(&maps[i * 128], &map, 128);
+    const int nk = ((2 * J.n + TC_KC - 1) / TC_KC + TC_BPS - 1) / TC_BPS * TC_BPS;
+    for (int r0 = 0; r0 < J.m; r0 += TC_M) {
+      tl.push_back({int32_t(i), r0});
+      cost.push_back(nk);
+    }
+  }
+  // longest tiles first, each to the least loaded CTA
+  int dev = 0, nsm = 0;
+  SLDM_CUDA(cudaGetDevice(&dev));
+  SLDM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  const int nctas = std::max(1, std::min<int>(nsm, int(tl.size())));
+  std::vector<size_t> order(tl.size());
+  for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return cost[a] > cost[b]; });
+  std::vector<std::vector<TcTile>> per(nctas);
+  typedef std::pair<long long, int> LoadCta;
+  std::priority_queue<LoadCta, std::vector<LoadCta>, std::greater<LoadCta>> pq;
+  for (int c = 0; c < nctas; ++c) pq.push({0, c});
+  for (size_t i : order) {
+    LoadCta lc = pq.top();
+    pq.pop();
+    per[lc.second].push_back(tl[i]);
+    pq.push({lc.first + cost[i], lc.second});
+  }
+  std::vector<TcTile> flat;
+  std::vector<int32_t> begin(1, 0);
+  for (auto& v : per) {
+    flat.insert(flat.end(), v.begin(), v.end());
+    begin.push_back(int32_t(flat.size()));
+  }
+  tp.maps.upload(maps, s);
+  tp.tiles.upload(flat, s);
+  tp.cta_begin.upload(begin, s);
+  tp.err.alloc(1);
+  tp.err.zero(s);
+  tp.nctas = nctas;
+  SLDM_CUDA(cudaStreamSynchronize(s));
+  tp.ok = true;
+}
+
+void gemm_tc(const GemvPlan& plan, const TcPlan& tp, int nrhs, cudaStream_t s) {
+  SLDM_REQUIRE(tp.ok && nrhs >= 1 && nrhs <= TC_MAX_NRHS, SLDM_EINVAL, "tensor-core product: invalid plan or nrhs");
+  static bool attr_set[64] = {false};
+  int dev = 0;
+  SLDM_CUDA(cudaGetDevice(&dev));
+  if (!attr_set[dev & 63]) {
+    SLDM_CUDA(cudaFuncSetAttribute(gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(TC_SMEM)));
+    attr_set[dev & 63] = true;
+  }
+  ScopedTimer tm("gemm_tc", s);
+  gemm_tc_kernel<<<unsigned(tp.nctas), TC_THREADS, TC_SMEM, s>>>(plan.jobs, tp.maps.p, tp.tiles.p, tp.cta_begin.p, nrhs,
+                                                                  tp.err.p);
+  count_launch();
+  SLDM_CUDA(cudaGetLastError());
+}
+
+void tc_check(const TcPlan& tp, cudaStream_t s) {
+  if (!tp.ok) return;
+  int h = 0;
+  SLDM_CUDA(cudaMemcpyAsync(&h, tp.err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  SLDM_CUDA(cudaStreamSynchronize(s));
+  if (h) {
+    SLDM_CUDA(cudaMemsetAsync(tp.err.p, 0, sizeof(int), s));
+    throw Error{SLDM_ETIMEOUT, "tensor-core product: a bounded wait ran out"};
+  }
+}
+
+}  // namespace sldm

@@ -1,0 +1,36 @@
+// Multi-right-hand-side complex64 block products on the 5th-generation tensor
+// cores (gemm_tc.cu): Y = alpha A X (+ Y) for 9 to 32 right-hand sides per pass.
+#pragma once
+#include "dense.h"
+
+namespace sldm {
+
+// Right-hand sides one tensor-core pass takes (accumulator width 2 x 32 FP32 columns).
+constexpr int TC_MAX_NRHS = 32;
+
+struct TcTile {
+  int32_t job, row0;
+};
+
+// Per GEMV plan: one TMA tensor map per job (the block seen as a row-major FP32
+// matrix of m rows and 2n columns), the 128-row tiles of every job, and their
+// assignment to CTAs (longest first, to the least loaded CTA).
+struct TcPlan {
+  DBuf<unsigned char> maps;  // 128-byte tensor maps, 64-byte aligned
+  DBuf<TcTile> tiles;
+  DBuf<int32_t> cta_begin;   // CTA c takes tiles [cta_begin[c], cta_begin[c + 1])
+  DBuf<int> err;             // set to 1 by a CTA whose bounded wait ran out
+  int nctas = 0;
+  bool ok = false;           // every job fits the tensor-core path
+};
+
+// Builds tp for the jobs of a complex64 plan (host copies of the jobs).  tp.ok is
+// false (and the plan keeps the CUDA-core kernels) when a job's row pitch is
+// not a multiple of 16 bytes or the driver's tensor-map encoder is unavailable.
+void tc_plan_build(const std::vector<GemvJob>& jobs, TcPlan& tp, cudaStream_t s);
+// One pass over every job of `plan` for nrhs (<= 32) right-hand sides.
+void gemm_tc(const GemvPlan& plan, const TcPlan& tp, int nrhs, cudaStream_t s);
+// SLDM_ETIMEOUT when a tensor-core pass recorded a bounded wait that ran out (reads and clears the flag).
+void tc_check(const TcPlan& tp, cudaStream_t s);
+
+}  // namespace sldm

@@ -38,6 +38,8 @@ bool timers_on();
 void count_launch();
 void timer_begin(const char* name, cudaStream_t s);
 void timer_end(cudaStream_t s);
+// adds the algorithmic units (bytes moved, kernel evaluations) of a timed launch
+void timer_units(const char* name, double units);
 struct ScopedTimer {
   cudaStream_t s;
   bool on;

@@ -257,6 +257,13 @@ void prec_setup(Precond& P, const sldm_mesh* m, const std::vector<PrecObj>& objs
   P.plan.ntiles = int(tiles.size());
   P.plan.tile_rows = gemv_tile_rows(ev);
   P.plan.name = "gemv_pc";
+  P.plan.bytes = 0;
+  for (auto& jb : jobs) P.plan.bytes += double(jb.m) * jb.n * ev;
+  P.plan.tc = nullptr;
+  if (P.f32) {
+    tc_plan_build(jobs, P.tc, s);
+    if (P.tc.ok) P.plan.tc = &P.tc;
+  }
   SLDM_CUDA(cudaStreamSynchronize(s));
 }
 
@@ -282,7 +289,7 @@ static void prec_apply_t(const Precond& P, const sldm_mesh* m, const double2* r,
 
 void prec_apply(const Precond& P, const sldm_mesh* m, const double2* r, double2* x, int64_t ld, int nr, cudaStream_t s) {
   ScopedTimer tm("precond", s);
-  SLDM_REQUIRE((nr >= 1 && nr <= MAX_NRHS), SLDM_EINVAL, "preconditioner: 1 to 8 columns");
+  SLDM_REQUIRE((nr >= 1 && nr <= MAX_NRHS), SLDM_EINVAL, "preconditioner: 1 to 32 columns");
   if (P.f32) prec_apply_t<float2>(P, m, r, x, ld, nr, s);
   else prec_apply_t<double2>(P, m, r, x, ld, nr, s);
 }

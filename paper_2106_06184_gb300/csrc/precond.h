@@ -1,6 +1,7 @@
 // Preconditioner P of Eq. pcext (precond.cu).
 #pragma once
 #include "dense.h"
+#include "gemm_tc.h"
 
 namespace sldm {
 
@@ -24,6 +25,7 @@ struct Precond {
   DBuf<int64_t> rs;
   DBuf<int2> tiles;
   GemvPlan plan;
+  TcPlan tc;  // complex64: the Schur-inverse products on the tensor cores (9 to 32 columns)
   bool ready = false;
 };
 

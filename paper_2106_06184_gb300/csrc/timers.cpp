@@ -90,6 +90,13 @@ void timer_end(cudaStream_t s) {
   if (g_pending.size() > 4096) resolve_locked();
 }
 
+// algorithmic units (bytes, evaluations) of the timed launches, per name
+static std::map<std::string, double> g_units;
+void timer_units(const char* name, double units) {
+  std::lock_guard<std::mutex> l(g_mu);
+  if (g_on) g_units[name] += units;
+}
+
 static std::atomic<int64_t> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
@@ -113,6 +120,15 @@ int sldm_timers_reset(void) {
   std::lock_guard<std::mutex> l(sldm::g_mu);
   sldm::resolve_locked();
   sldm::g_acc.clear();
+  sldm::g_units.clear();
+  return SLDM_OK;
+}
+
+int sldm_timer_units(const char* name, double* units) {
+  if (!name || !units) return SLDM_EINVAL;
+  std::lock_guard<std::mutex> l(sldm::g_mu);
+  auto it = sldm::g_units.find(name);
+  *units = it == sldm::g_units.end() ? 0.0 : it->second;
   return SLDM_OK;
 }
 

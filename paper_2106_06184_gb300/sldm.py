@@ -88,6 +88,7 @@ EXPORTS = {
     "sldm_timer_get": (C.c_int, [C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "sldm_timer_names": (C.c_int, [C.c_char_p, C.c_size_t]),
     "sldm_launch_count": (C.c_int, [C.POINTER(C.c_int64)]),
+    "sldm_timer_units": (C.c_int, [C.c_char_p, C.POINTER(C.c_double)]),
     "sldm_set_device_budget": (C.c_int, [C.c_int64]),
     "sldm_device_bytes": (C.c_int, [C.POINTER(C.c_int64)]),
     "sldm_test_inject": (C.c_int, [C.c_int32, C.c_int32]),
@@ -139,6 +140,14 @@ def timers_read(lib=None):
         L.check(L.lib.sldm_timer_get(name.encode(), C.byref(ms), C.byref(n)))
         out[name] = (ms.value, n.value)
     return out
+
+
+def timer_units(name, lib=None) -> float:
+    """sldm_timer_units: algorithmic units (bytes or evaluations) of the timed launches of `name`."""
+    L = lib or load()
+    v = C.c_double()
+    L.check(L.lib.sldm_timer_units(name.encode(), C.byref(v)))
+    return v.value
 
 
 def launch_count(lib=None) -> int:
