@@ -24,7 +24,8 @@
 // split into four K sub-chunks of 32 FP32 columns.  Warp-specialised,
 // synchronised by mbarriers only:
 //   warp 0   TMA: a ring of 2 stages (128 KB in flight per SM);
-//   warps 2-5 split: thread = row; for each sub-chunk reads its row, splits it
+//   warps 2-9 split (two per TMEM lane quarter, half the K columns each):
+//            thread = row; for each sub-chunk reads its row, splits it
 //            into hi and lo and stores both into a TMEM operand buffer (A of
 //            the MMA in tensor memory: lane = row, column = K), and builds hi/lo
 //            of the B' sub-chunk (64 x 128 B, swizzled) in shared memory from
@@ -34,14 +35,14 @@
 //            products, M 128, N 64, K 8) into one of two 64-column TMEM
 //            accumulators, a fresh one for every stage (a segment of 128 K
 //            columns), and commits them to the operand buffer's barrier;
-//   warps 6-13 epilogue: fold each segment's accumulator into compensated FP32
+//   warps 10-17 epilogue: fold each segment's accumulator into compensated FP32
 //            sums in registers (warp w: TMEM lanes 32 (w % 4) .., 32 of the 64
 //            columns), and at the end of a tile write Y.
 // The tensor core rounds its FP32 accumulator at every MMA: a tile's ~10^4
 // MMAs into one accumulator would lose ~2^-17 of the result; segments of 48
 // MMAs and compensated sums across them keep the product as accurate as an
 // FP32 CUDA-core product.
-// Operand buffers (TMEM A, shared B') and accumulators are double-buffered.
+// Operand buffers (TMEM A, shared B') are triple-, accumulators double-buffered.
 // Tiles are padded to whole stages (zero columns from TMA and zero B').
 #include <cuda.h>
 
@@ -60,20 +61,21 @@ constexpr int TC_N = 2 * TC_MAX_NRHS;  // 64 accumulator columns
 constexpr int TC_KC = 32;              // FP32 columns of A per chunk: one 128-byte swizzle row
 constexpr int TC_BPS = 4;              // TMA boxes (sub-chunks) per stage
 constexpr int TC_R = 2;                // stages in the ring
-constexpr int TC_THREADS = 448;        // 14 warps: TMA, MMA, 4 split, 8 epilogue
+constexpr int TC_THREADS = 576;        // 18 warps: TMA, MMA, 8 split, 8 epilogue
+constexpr int TC_NB = 3;               // operand buffers (TMEM A hi/lo, shared B' hi/lo)
 constexpr uint32_t TC_A_BYTES = TC_M * TC_KC * 4;  // 16 KB: one box, one sub-chunk
 constexpr uint32_t TC_STAGE_BYTES = TC_BPS * TC_A_BYTES;
 constexpr uint32_t TC_B_BYTES = TC_N * TC_KC * 4;  // 8 KB
 constexpr uint32_t TC_BBUF = 2 * TC_B_BYTES;       // B' hi, lo
 constexpr uint32_t TC_RING = TC_R * TC_STAGE_BYTES;
-// TMEM: accumulators at columns 0 and 64, A operand buffers (hi 32 + lo 32 columns) at 128 and 192
-constexpr uint32_t TC_TMEM_COLS = 256;
+// TMEM: accumulators at columns 0 and 64, A operand buffers (hi 32 + lo 32 columns each) from 128
+constexpr uint32_t TC_TMEM_COLS = 512;
 constexpr uint32_t TC_ACC_COL = 0, TC_AOP_COL = 128;
-// vectors: a ring of 4 sub-chunks, copied 3 ahead; per sub-chunk each of the 128
-// split threads holds the 8 complex64 entries it needs (64 B)
+// vectors: a ring of 4 sub-chunks, copied 3 ahead; per sub-chunk each of the 256
+// split threads holds the 4 complex64 entries it needs (32 B)
 constexpr int TC_XR = 4;
-constexpr uint32_t TC_XBYTES = 128 * 64;  // 8 KB per sub-chunk
-constexpr size_t TC_SMEM = size_t(TC_RING) + 2 * size_t(TC_BBUF) + size_t(TC_XR) * TC_XBYTES + 1024 + 256;
+constexpr uint32_t TC_XBYTES = 256 * 32;  // 8 KB per sub-chunk
+constexpr size_t TC_SMEM = size_t(TC_RING) + TC_NB * size_t(TC_BBUF) + size_t(TC_XR) * TC_XBYTES + 1024 + 256;
 constexpr uint32_t TC_SPIN = 1u << 21;  // try_wait rounds before a wait is declared failed
 
 static_assert(TC_BBUF % 1024 == 0 && TC_A_BYTES % 1024 == 0 && TC_B_BYTES % 1024 == 0, "swizzle atoms are 1 KB aligned");
@@ -138,46 +140,39 @@ __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence:
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-// 32 consecutive accumulator columns of this warp's 32 TMEM lanes
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-  uint32_t r[32];
+// 16 consecutive accumulator columns of this warp's 32 TMEM lanes
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
+      "[%16];\n"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
-        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr)
       : "memory");
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
-
-// 32 consecutive TMEM columns of this warp's 32 lanes from registers
-__device__ __forceinline__ void tmem_st32(uint32_t taddr, const float (&v)[32]) {
+// 16 consecutive TMEM columns of this warp's 32 lanes from registers
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16]) {
   asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};\n" ::"r"(taddr),
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16};\n" ::"r"(taddr),
       "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
       "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
       "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
-      "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15])),
-      "r"(__float_as_uint(v[16])), "r"(__float_as_uint(v[17])), "r"(__float_as_uint(v[18])), "r"(__float_as_uint(v[19])),
-      "r"(__float_as_uint(v[20])), "r"(__float_as_uint(v[21])), "r"(__float_as_uint(v[22])), "r"(__float_as_uint(v[23])),
-      "r"(__float_as_uint(v[24])), "r"(__float_as_uint(v[25])), "r"(__float_as_uint(v[26])), "r"(__float_as_uint(v[27])),
-      "r"(__float_as_uint(v[28])), "r"(__float_as_uint(v[29])), "r"(__float_as_uint(v[30])), "r"(__float_as_uint(v[31]))
+      "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15]))
       : "memory");
 }
 
 // FP32 -> TF32 (10 mantissa bits), round to nearest, ties away from zero: the
 // result is an FP32 value with its 13 low mantissa bits zero, which the MMA
-// takes exactly
+// takes exactly.  On the bit pattern: add half of the dropped unit (0x1000,
+// carrying into the exponent when the mantissa overflows) and clear the 13
+// bits - two full-rate integer operations (finite inputs below ~3.4e38)
 __device__ __forceinline__ float tf32_rn(float v) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
-  return __uint_as_float(r);
+  return __uint_as_float((__float_as_uint(v) + 0x1000u) & 0xFFFFE000u);
 }
 // v = hi + lo: hi = tf32(v) (|v - hi| <= 2^-12 |v|), lo = tf32(v - hi) (rounding
 // error <= 2^-12 |v - hi| <= 2^-24 |v|), both exact TF32 operands
@@ -191,7 +186,8 @@ __device__ __forceinline__ uint32_t sw128_off(int row, int j) { return uint32_t(
 
 }  // namespace
 
-__global__ void __launch_bounds__(TC_THREADS, 1)
+// 18 warps over the 4 SM sub-partitions (5, 5, 4, 4) x 32 threads x 96 registers <= 16,384 each
+__global__ void __maxnreg__(96)
     gemm_tc_kernel(const GemvJob* __restrict__ jobs, const unsigned char* __restrict__ maps, const TcTile* __restrict__ tiles,
                    const int32_t* __restrict__ cta_begin, int nrhs, int* err) {
   extern __shared__ unsigned char tc_raw[];
@@ -201,16 +197,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const uint32_t base = (raw + 1023u) & ~1023u;  // ring[R], B'[2], x ring
   unsigned char* gb = tc_raw + (base - raw);
   const uint32_t bbuf0 = base + TC_RING;
-  const uint32_t xring = bbuf0 + 2 * TC_BBUF;
+  const uint32_t xring = bbuf0 + TC_NB * TC_BBUF;
   const uint32_t bars = xring + TC_XR * TC_XBYTES;
-  // barriers (8 bytes each): full[R], empty[R], ready[2], wfree[2], accfull[2], accempty[2]
+  // barriers (8 bytes each): full[R], empty[R], ready[NB], wfree[NB], accfull[2], accempty[2]
   auto full = [&](int s) { return bars + 8u * uint32_t(s); };
   auto empty = [&](int s) { return bars + 8u * uint32_t(TC_R + s); };
   auto ready = [&](int b) { return bars + 8u * uint32_t(2 * TC_R + b); };
-  auto wfree = [&](int b) { return bars + 8u * uint32_t(2 * TC_R + 2 + b); };
-  auto accfull = [&](int a) { return bars + 8u * uint32_t(2 * TC_R + 4 + a); };
-  auto accempty = [&](int a) { return bars + 8u * uint32_t(2 * TC_R + 6 + a); };
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gb + (bars - base) + 8 * (2 * TC_R + 8));
+  auto wfree = [&](int b) { return bars + 8u * uint32_t(2 * TC_R + TC_NB + b); };
+  auto accfull = [&](int a) { return bars + 8u * uint32_t(2 * TC_R + 2 * TC_NB + a); };
+  auto accempty = [&](int a) { return bars + 8u * uint32_t(2 * TC_R + 2 * TC_NB + 2 + a); };
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gb + (bars - base) + 8 * (2 * TC_R + 2 * TC_NB + 4));
   __shared__ int s_fail;
   volatile int* vfail = &s_fail;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -218,13 +214,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   if (tid == 0) {
     for (int q = 0; q < TC_R; ++q) {
       mbar_init(full(q), 1);
-      mbar_init(empty(q), 4);
+      mbar_init(empty(q), 8);
     }
-    for (int b = 0; b < 2; ++b) {
-      mbar_init(ready(b), 4);
+    for (int b = 0; b < TC_NB; ++b) {
+      mbar_init(ready(b), 8);
       mbar_init(wfree(b), 1);
-      mbar_init(accfull(b), 1);
-      mbar_init(accempty(b), 8);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(accfull(a), 1);
+      mbar_init(accempty(a), 8);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_fail = 0;
@@ -279,10 +277,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (lane == 0) {
       int tile_i = 0, k = 0, nk = nk_of(t_begin), last = -1;
       for (int g = 0; g < total; ++g) {
-        const int b = g & 1, seg = g / TC_BPS, j = g % TC_BPS;
+        const int b = g % TC_NB, seg = g / TC_BPS, j = g % TC_BPS;
         bool ok = true;
         if (j == 0 && seg >= 2) ok = mbar_wait(accempty(seg & 1), uint32_t(((seg >> 1) - 1) & 1), vfail);
-        if (ok) ok = mbar_wait(ready(b), uint32_t((g >> 1) & 1), vfail);
+        if (ok) ok = mbar_wait(ready(b), uint32_t((g / TC_NB) & 1), vfail);
         if (!ok) {
           *vfail = 1;
           break;
@@ -310,15 +308,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
       }
       // the MMAs in flight (they complete in order) finish before the CTA leaves
-      if (last >= 0) mbar_wait(wfree(last & 1), uint32_t((last >> 1) & 1));
+      if (last >= 0) mbar_wait(wfree(last % TC_NB), uint32_t((last / TC_NB) & 1));
     }
     __syncwarp();
-  } else if (warp < 6) {
-    // ---------------- split warps: thread = row of the tile (TMEM lane quarter warp % 4)
-    const int q4 = warp & 3, row = 32 * q4 + lane;
+  } else if (warp < 10) {
+    // ---------------- split warps: thread = row of the tile (TMEM lane quarter warp % 4); the
+    // two warps of a lane quarter take the K columns 16 kh .. 16 kh + 15 of each sub-chunk
+    const int q4 = warp & 3, kh = (warp - 2) >> 2, row = 32 * q4 + lane;
     // share of B' (64 rows x 8 chunks of 16 B, hi and lo): 16-byte chunk c = ti & 7 of rows
-    // 2 (rb + 8 m) + rr, m = 0..3 (rr = (ti >> 3) & 1, rb = ti >> 4): a warp stores 4 whole rows
-    // per instruction, free of bank conflicts.  Those need x_{rb + 8m} at complex columns 2c, 2c + 1.
+    // 2 (rb + 16 m) + rr, m = 0, 1 (rr = (ti >> 3) & 1, rb = ti >> 4): a warp stores 4 whole rows
+    // per instruction, free of bank conflicts.  Those need x_{rb + 16m} at complex columns 2c, 2c + 1.
     const int ti = tid - 64, bc = ti & 7, brr = (ti >> 3) & 1, brb = ti >> 4;
     int xt = t_begin, xk = 0, xnk = nk_of(t_begin), xg = 0;
     const float2* xjob = reinterpret_cast<const float2*>(jobs[tiles[t_begin].job].x);
@@ -330,13 +329,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         // slot layout [entry e = 2m + u][thread]: consecutive threads, consecutive 8-byte words
         const uint32_t dst = xring + uint32_t(xg % TC_XR) * TC_XBYTES + uint32_t(ti) * 8u;
 #pragma unroll
-        for (int m = 0; m < 4; ++m) {
-          const int r = brb + 8 * m;
+        for (int m = 0; m < 2; ++m) {
+          const int r = brb + 16 * m;
           const float2* x = xjob + int64_t(r < nrhs ? r : 0) * xld;
 #pragma unroll
           for (int u = 0; u < 2; ++u) {
             const bool v = r < nrhs && c0 + u < xn_cols;
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(dst + uint32_t(2 * m + u) * 1024u),
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(dst + uint32_t(2 * m + u) * 2048u),
                          "l"(v ? x + c0 + u : xjob), "r"(v ? 8 : 0)
                          : "memory");
           }
@@ -357,46 +356,46 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     };
     for (int i = 0; i < TC_XR - 1; ++i) copy_x();
     for (int g = 0; g < total; ++g) {
-      const int st = g / TC_BPS, j = g % TC_BPS, q = st % TC_R, b = g & 1;
+      const int st = g / TC_BPS, j = g % TC_BPS, q = st % TC_R, b = g % TC_NB;
       copy_x();                                                                  // sub-chunk g + 3
       asm volatile("cp.async.wait_group %0;\n" ::"n"(TC_XR - 1) : "memory");  // this thread's copies of g landed
-      float4 xv[4];  // (x_{rb+8m}[2c], x_{rb+8m}[2c+1]) as (re, im, re, im)
+      float4 xv[2];  // (x_{rb+16m}[2c], x_{rb+16m}[2c+1]) as (re, im, re, im)
       {
         const float2* xs = reinterpret_cast<const float2*>(gb + (xring - base) + size_t(g % TC_XR) * TC_XBYTES) + ti;
 #pragma unroll
-        for (int m = 0; m < 4; ++m) {
-          const float2 a0 = xs[(2 * m) * 128], a1 = xs[(2 * m + 1) * 128];
+        for (int m = 0; m < 2; ++m) {
+          const float2 a0 = xs[(2 * m) * 256], a1 = xs[(2 * m + 1) * 256];
           xv[m] = make_float4(a0.x, a0.y, a1.x, a1.y);
         }
       }
       bool ok = mbar_wait(full(q), uint32_t((st / TC_R) & 1), vfail);
-      if (ok && g >= 2) ok = mbar_wait(wfree(b), uint32_t(((g >> 1) - 1) & 1), vfail);
+      if (ok && g >= TC_NB) ok = mbar_wait(wfree(b), uint32_t(((g / TC_NB) - 1) & 1), vfail);
       ok = __all_sync(0xffffffffu, ok);  // the TMEM stores below need the whole warp
       if (!ok) {
         *vfail = 1;
         break;
       }
-      // this row of box j of the landed stage: 8 x 16 B, swizzled
+      // this row's half of box j of the landed stage: 4 x 16 B, swizzled
       const unsigned char* rp = gb + size_t(q) * TC_STAGE_BYTES + size_t(j) * TC_A_BYTES + size_t(row) * 128;
-      float h[32], l[32];
+      float h[16], l[16];
 #pragma unroll
-      for (int jj = 0; jj < 8; ++jj) {
-        const float4 a = *reinterpret_cast<const float4*>(rp + ((jj ^ (row & 7)) * 16));
+      for (int jj = 0; jj < 4; ++jj) {
+        const float4 a = *reinterpret_cast<const float4*>(rp + (((4 * kh + jj) ^ (row & 7)) * 16));
         tf32_split(a.x, h[4 * jj], l[4 * jj]);
         tf32_split(a.y, h[4 * jj + 1], l[4 * jj + 1]);
         tf32_split(a.z, h[4 * jj + 2], l[4 * jj + 2]);
         tf32_split(a.w, h[4 * jj + 3], l[4 * jj + 3]);
       }
-      const uint32_t ta = tmem + (uint32_t(32 * q4) << 16) + TC_AOP_COL + uint32_t(b) * 64u;
-      tmem_st32(ta, h);
-      tmem_st32(ta + 32u, l);
+      const uint32_t ta = tmem + (uint32_t(32 * q4) << 16) + TC_AOP_COL + uint32_t(b) * 64u + uint32_t(16 * kh);
+      tmem_st16(ta, h);
+      tmem_st16(ta + 32u, l);
       // hi/lo of B' for this sub-chunk: row 2r gives Re y_r ([xr, -xi] per complex column), row 2r+1 Im y_r ([xi, xr])
       {
         unsigned char* Bh = gb + TC_RING + size_t(b) * TC_BBUF;
         unsigned char* Bl = Bh + TC_B_BYTES;
 #pragma unroll
-        for (int m = 0; m < 4; ++m) {
-          const int brow = 2 * (brb + 8 * m) + brr;
+        for (int m = 0; m < 2; ++m) {
+          const int brow = 2 * (brb + 16 * m) + brr;
           const float4 a = xv[m];
           const float4 v = brr ? make_float4(a.y, a.x, a.w, a.z) : make_float4(a.x, -a.y, a.z, -a.w);
           float4 hv, lv;
@@ -421,7 +420,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");  // no copy in flight when the CTA leaves
   } else {
     // ---------------- epilogue warps: TMEM lane quarter warp % 4, accumulator columns 32 half ..
-    const int q4 = warp & 3, half = (warp - 6) >> 2;
+    const int q4 = warp & 3, half = (warp - 10) >> 2;
     float cs[32], cc[32];  // compensated sums of this row's 32 columns over the tile's segments
 #pragma unroll
     for (int i = 0; i < 32; ++i) cs[i] = cc[i] = 0.f;
@@ -433,18 +432,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         ok = __all_sync(0xffffffffu, mbar_wait(accfull(seg & 1), uint32_t((seg >> 1) & 1), vfail));
         if (!ok) break;  // the TMEM loads below need the whole warp
         tc_fence_after();
-        float v[32];
-        tmem_ld32(tmem + (uint32_t(32 * q4) << 16) + TC_ACC_COL + uint32_t(seg & 1) * 64u + uint32_t(half * 32), v);
+#pragma unroll
+        for (int hq = 0; hq < 2; ++hq) {
+          float v[16];
+          tmem_ld16(tmem + (uint32_t(32 * q4) << 16) + TC_ACC_COL + uint32_t(seg & 1) * 64u + uint32_t(half * 32 + 16 * hq),
+                    v);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {  // TwoSum (Knuth): cs + cc carries the running sum
+            const int c = 16 * hq + i;
+            const float sum = __fadd_rn(cs[c], v[i]);
+            const float bp = __fsub_rn(sum, cs[c]);
+            cc[c] = __fadd_rn(cc[c], __fadd_rn(__fsub_rn(cs[c], __fsub_rn(sum, bp)), __fsub_rn(v[i], bp)));
+            cs[c] = sum;
+          }
+        }
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(accempty(seg & 1));  // the accumulator may take the next segment
-#pragma unroll
-        for (int i = 0; i < 32; ++i) {  // TwoSum (Knuth): cs + cc carries the running sum
-          const float sum = __fadd_rn(cs[i], v[i]);
-          const float bp = __fsub_rn(sum, cs[i]);
-          cc[i] = __fadd_rn(cc[i], __fadd_rn(__fsub_rn(cs[i], __fsub_rn(sum, bp)), __fsub_rn(v[i], bp)));
-          cs[i] = sum;
-        }
       }
       if (!ok) {
         *vfail = 1;
