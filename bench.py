@@ -145,17 +145,21 @@ FILL_F64_PEAK_EVALS = FP64_OPS_PER_S / FP64_OPS_PER_EVAL
 # valid while that kernel's source is unchanged (sha256 prefix of its text in
 # dense.cu).
 GEMV_TRAFFIC = {
-    "gemv_jobs_kernel": dict(sha="1c5c6f7e0080bcec", per_alg_byte=(424.169472e6 + 3.703040e6) / 423.936e6),
-    "gemv_tile_kernel": dict(sha="43fbbe3c6438984e", per_alg_byte=(425.892608e6 + 0.485888e6) / 423.936e6),
+    # main-stage launch of the 4 x 4 metasurface, 32 right-hand sides (profiles/gemm_tc_metasurface-4x4-32angles-c64x2.md)
+    "gemm_tc_kernel": dict(sha="e4ed5894daacc53a", file="gemm_tc.cu",
+                           per_alg_byte=(430.977024e6 + 9.762560e6) / 423.936e6),
 }
 
 
-def kernel_sha(name):
-    """sha256 prefix of a kernel's definition in dense.cu (its template line to the closing brace)."""
+def kernel_sha(name, file="dense.cu"):
+    """sha256 prefix of a kernel's definition in csrc/<file> (its template or attribute line to the closing brace)."""
     import hashlib
-    s = open(os.path.join(ROOT, "paper_2106_06184_gb300", "csrc", "dense.cu")).read()
+    s = open(os.path.join(ROOT, "paper_2106_06184_gb300", "csrc", file)).read()
     i = s.index(" " + name + "(")
-    a = s.rindex("template <", 0, i)
+    a = s.rindex("__global__", 0, i)
+    t = s.rfind("template <", 0, i)
+    if t >= 0 and t > s.rfind("}", 0, a):
+        a = t
     depth, j = 0, s.index("{", i)
     while True:
         depth += {"{": 1, "}": -1}.get(s[j], 0)
@@ -379,10 +383,12 @@ def run_ours(args, rank, world):
         e = {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
              "peak_source": hbm_src, "traffic": None, "algorithmic_unit": per_launch, "launches": cnt,
              "ms_per_launch": ms / cnt}
-        kern = "gemv_tile_kernel" if (nrhs > 1 or W["precision"] == 2) else "gemv_jobs_kernel"
-        if name == "gemv_main" and kern in GEMV_TRAFFIC and kernel_sha(kern) == GEMV_TRAFFIC[kern]["sha"]:
-            e["traffic"] = GEMV_TRAFFIC[kern]["per_alg_byte"] * per_launch
-            e["traffic_source"] = "ncu capture of the 4x4 case, scaled by algorithmic bytes"
+        kern = "gemm_tc_kernel" if "gemm_tc" in timers else ("gemv_tile_kernel" if nrhs > 1 else "gemv_jobs_kernel")
+        tr = GEMV_TRAFFIC.get(kern)
+        if name == "gemv_main" and tr and kernel_sha(kern, tr["file"]) == tr["sha"]:
+            e["traffic"] = tr["per_alg_byte"] * per_launch
+            e["traffic_source"] = "ncu capture of the 4x4 case (same kernel source), scaled by algorithmic bytes"
+        e["kernel_impl"] = kern
         return e
 
     def fill_entry(name):

@@ -91,7 +91,14 @@ void geometry(const HostMesh& hm, DevMesh& dm, cudaStream_t s) {
 
 // ---------------------------------------------------------------- bulk L kernel
 constexpr int TILE_SRC = 128;  // source triangles per CTA (one per thread)
-constexpr int TILE_TEST = 8;   // test triangles per CTA
+constexpr int TILE_TEST = 8;   // test triangles per CTA (FP64 fills)
+// Test triangles per CTA: each thread converts its source record to the fill's
+// precision once per CTA, so the FP32 fills take 32 test triangles to keep those
+// conversions (on the narrow FP64 pipe of this part) off the per-pair cost.
+template <class R>
+constexpr int tile_test() {
+  return sizeof(R) == 4 ? 32 : TILE_TEST;
+}
 
 struct TileRef {
   int32_t task, test0, src0, pad;
@@ -117,11 +124,11 @@ template <class R>
 __global__ void __launch_bounds__(TILE_SRC, sizeof(R) == 4 ? 5 : 1) fill_L_bulk(const LTask* __restrict__ tasks, const TileRef* __restrict__ tiles,
                                                         const double* __restrict__ geo, const int32_t* __restrict__ tri,
                                                         const int32_t* __restrict__ tri_edge) {
-  __shared__ TestRec<R> T[TILE_TEST];
+  __shared__ TestRec<R> T[tile_test<R>()];
   const TileRef tile = tiles[blockIdx.x];
   const LTask tk = tasks[tile.task];
   // load the test tile
-  for (int idx = threadIdx.x; idx < TILE_TEST; idx += blockDim.x) {
+  for (int idx = threadIdx.x; idx < tile_test<R>(); idx += blockDim.x) {
     int t = tile.test0 + idx;
     if (t < tk.ntest) {
       int tg = tk.t0 + t;
@@ -163,7 +170,7 @@ __global__ void __launch_bounds__(TILE_SRC, sizeof(R) == 4 ? 5 : 1) fill_L_bulk(
   for (int k = 0; k < 6; ++k) Ws[k] *= R(INV4PI);  // 1/(4 pi) of G folded into the source weights
   const R sAr = R(tk.sAr), sAi = R(tk.sAi), sPr = R(tk.sPr), sPi = R(tk.sPi);
 
-  for (int tt = 0; tt < TILE_TEST; ++tt) {
+  for (int tt = 0; tt < tile_test<R>(); ++tt) {
     if (tile.test0 + tt >= tk.ntest) break;
     const TestRec<R>& X = T[tt];
     // touching pairs (sharing a vertex) are computed by the FP64 extraction kernel
@@ -358,10 +365,10 @@ __global__ void __launch_bounds__(TILE_SRC, sizeof(R) == 4 ? 5 : 1) fill_K_bulk(
                                                         const double* __restrict__ geo, const double* __restrict__ bgeo,
                                                         const int32_t* __restrict__ tri, const int32_t* __restrict__ tri_edge,
                                                         const int32_t* __restrict__ btri_edge) {
-  __shared__ TestRec<R> T[TILE_TEST];
+  __shared__ TestRec<R> T[tile_test<R>()];
   const TileRef tile = tiles[blockIdx.x];
   const KTask tk = tasks[tile.task];
-  for (int idx = threadIdx.x; idx < TILE_TEST; idx += blockDim.x) {
+  for (int idx = threadIdx.x; idx < tile_test<R>(); idx += blockDim.x) {
     int t = tile.test0 + idx;
     if (t < tk.ntest) {
       int tg = tk.t0 + t;
@@ -402,7 +409,7 @@ __global__ void __launch_bounds__(TILE_SRC, sizeof(R) == 4 ? 5 : 1) fill_K_bulk(
 #pragma unroll
   for (int k = 0; k < 6; ++k) Ws[k] *= R(INV4PI);  // 1/(4 pi) of grad G folded into the source weights
 
-  for (int tt = 0; tt < TILE_TEST; ++tt) {
+  for (int tt = 0; tt < tile_test<R>(); ++tt) {
     const int t = tile.test0 + tt;
     if (t >= tk.ntest) break;
     const TestRec<R>& X = T[tt];
@@ -647,7 +654,7 @@ void fill_L(const sldm_mesh* m, const std::vector<LTask>& tasks, cudaStream_t s)
   std::vector<TileRef> tiles;
   for (size_t i = 0; i < tasks.size(); ++i) {
     if (split[i]) continue;
-    for (int t0 = 0; t0 < tasks[i].ntest; t0 += TILE_TEST)
+    for (int t0 = 0; t0 < tasks[i].ntest; t0 += tile_test<R>())
       for (int s0 = 0; s0 < tasks[i].nsrc; s0 += TILE_SRC) tiles.push_back({int32_t(i), t0, s0, 0});
   }
   DBuf<LTask> dt;
@@ -696,7 +703,7 @@ void fill_K(const sldm_mesh* m, const std::vector<KTask>& tasks, cudaStream_t s)
   std::vector<TileRef> tiles;
   for (size_t i = 0; i < tasks.size(); ++i) {
     if (split[i]) continue;
-    for (int t0 = 0; t0 < tasks[i].ntest; t0 += TILE_TEST)
+    for (int t0 = 0; t0 < tasks[i].ntest; t0 += tile_test<R>())
       for (int s0 = 0; s0 < tasks[i].nsrc; s0 += TILE_SRC) tiles.push_back({int32_t(i), t0, s0, 0});
   }
   DBuf<KTask> dt;
