@@ -453,3 +453,92 @@ def plane_wave_normal(stack, l, omega, E0=1.0):
             v = a * np.exp(-1j * ks[i] * d) + c * np.exp(1j * ks[i] * d)
     zref = stack.z_top if l == 0 else stack.bounds(l)[1]
     return a, c, ks[l], zref
+
+
+def _oblique_lines(stack, omega, kt_abs, pol_type):
+    """Per layer: k_z, line impedance and the reflection coefficient looking down at
+    the layer's bottom (a transmission line in z for the transverse E of one
+    polarisation; pol_type 'TE': Z = w mu / k_z, 'TM': Z = k_z / (w eps))."""
+    k0 = omega / C0
+    L = len(stack.layers)
+    kz, Z, d, finite = [], [], [], []
+    for i in range(L):
+        eps, mu = stack.eps(i, omega), stack.mu(i)
+        q = complex(kz_of(k0 * np.sqrt(eps * mu), kt_abs))
+        kz.append(q)
+        Z.append(omega * MU0 * mu / q if pol_type == "TE" else q / (omega * EPS0 * eps))
+        d.append(stack.layers[i][3])
+        finite.append(i > 0 and (stack.bottom == "pec" or i < L - 1))
+    down = [0j] * L
+    down[L - 1] = -1.0 + 0j if stack.bottom == "pec" else 0j
+    for i in range(L - 2, -1, -1):
+        f = (Z[i + 1] - Z[i]) / (Z[i + 1] + Z[i])
+        ph = down[i + 1] * np.exp(-2j * kz[i + 1] * d[i + 1]) if finite[i + 1] else 0j
+        down[i] = (f + ph) / (1 + f * ph)
+    return kz, Z, d, finite, down
+
+
+def plane_wave_oblique(stack, omega, khat, pol, E0=1.0):
+    """Plane wave incident from the upper half-space on the stack, in every layer.
+
+    Incident field E_inc = pol E0 exp(-j k0 khat . r) (khat_z < 0, pol . khat = 0).
+    The transverse wavevector kt = k0 (khat_x, khat_y) is the same in every layer;
+    with rho = kt / |kt| (for normal incidence, the transverse direction of pol)
+    and phi = z x rho, the field splits into a TE part (E along phi) and a TM
+    part (H along phi).  For each, the transverse E component V(z) is a
+    transmission line in z: in layer i, V = a exp(+j k_z (z - zref)) + c exp(-j k_z
+    (z - zref)) (down- and up-going waves), zref the layer's top (z_top for the
+    upper half-space), the ratio c / a at a layer's bottom the reflection
+    coefficient looking down, and V continuous across each interface.  In layer i
+    the field is
+        E = exp(-j kt . r) [phi V_TE + rho V_TM + z (|kt| / k_z) (a_TM e^{+} - c_TM e^{-})],
+    the z part from div E = 0 for each of the two TM waves.  Returns a list over
+    the layers of dicts {a_te, c_te, a_tm, c_tm, kz, zref} and the common
+    {kt (2,), krho, rho (3,), phi (3,)}."""
+    khat = np.asarray(khat, float)
+    pol = np.asarray(pol, complex)
+    k0 = omega / C0
+    kt = k0 * khat[:2]
+    krho = float(np.hypot(kt[0], kt[1]))
+    if krho > 1e-12 * k0:
+        rho = np.array([kt[0] / krho, kt[1] / krho, 0.0])
+    else:
+        pt = np.array([pol[0], pol[1]])
+        n = np.linalg.norm(pt)
+        rho = np.array([pt[0].real, pt[1].real, 0.0]) / n if n > 0 else np.array([1.0, 0.0, 0.0])
+        rho = rho / np.linalg.norm(rho)
+    phi = np.cross([0.0, 0.0, 1.0], rho)
+    L = len(stack.layers)
+    out = [dict() for _ in range(L)]
+    for ptype, key in (("TE", "te"), ("TM", "tm")):
+        kz, Z, d, finite, down = _oblique_lines(stack, omega, krho, ptype)
+        v0 = E0 * (pol @ phi if ptype == "TE" else pol @ rho)
+        a = v0 * np.exp(1j * kz[0] * stack.z_top)      # down-going amplitude at z_top
+        c = a * down[0]
+        out[0]["a_" + key], out[0]["c_" + key], out[0]["kz"], out[0]["zref"] = a, c, kz[0], stack.z_top
+        v = a + c                                        # V at z_top
+        z = stack.z_top
+        for i in range(1, L):
+            gtop = down[i] * np.exp(-2j * kz[i] * d[i]) if finite[i] else 0j
+            a = v / (1 + gtop)
+            c = a * gtop
+            out[i]["a_" + key], out[i]["c_" + key], out[i]["kz"], out[i]["zref"] = a, c, kz[i], z
+            if finite[i]:
+                v = a * np.exp(-1j * kz[i] * d[i]) + c * np.exp(1j * kz[i] * d[i])
+                z -= d[i]
+    return out, dict(kt=kt, krho=krho, rho=rho, phi=phi)
+
+
+def incident_field(stack, l, omega, khat, pol, r, E0=1.0):
+    """The field of plane_wave_oblique in layer l at points r (n, 3) -> (n, 3) complex."""
+    layers, g = plane_wave_oblique(stack, omega, khat, pol, E0)
+    c = layers[l]
+    r = np.atleast_2d(r)
+    zeta = r[:, 2] - c["zref"]
+    ep, em = np.exp(1j * c["kz"] * zeta), np.exp(-1j * c["kz"] * zeta)
+    vte = c["a_te"] * ep + c["c_te"] * em
+    vtm = c["a_tm"] * ep + c["c_tm"] * em
+    ez = (g["krho"] / c["kz"]) * (c["a_tm"] * ep - c["c_tm"] * em)
+    lat = np.exp(-1j * (r[:, 0] * g["kt"][0] + r[:, 1] * g["kt"][1]))
+    return lat[:, None] * (g["phi"][None, :] * vte[:, None] + g["rho"][None, :] * vtm[:, None]
+                           + np.array([0.0, 0.0, 1.0])[None, :] * ez[:, None])

@@ -161,14 +161,12 @@ def rhs(a: Assembled, khat=(0, 0, -1), pol=(1, 0, 0), E0=1.0):
         from .fill import ETA0
         from . import quadrature as Q
         stack, layer, _ = a.layered
-        if tuple(khat) != (0, 0, -1):
-            raise ValueError("layered backgrounds: normal incidence from the top only")
-        ca, cc, k, zref = LY.plane_wave_normal(stack, layer, a.k0 * C0, E0)
+        # the incident wave of the stack (oblique incidence from the upper half-space)
         A = m.xyz[m.tri]
         rq = Q.points(A)
         wq = Q.weights(m.area)
-        ez = ca * np.exp(1j * k * (rq[..., 2] - zref)) + cc * np.exp(-1j * k * (rq[..., 2] - zref))
-        Einc = np.asarray(pol, complex)[None, None, :] * ez[..., None] / ETA0
+        Einc = LY.incident_field(stack, layer, a.k0 * C0, khat, pol, rq.reshape(-1, 3), E0)
+        Einc = Einc.reshape(rq.shape) / ETA0
         for i in range(3):
             fi = (rq - A[:, i][:, None, :]) * (m.E.tri_sign[:, i] / (2 * m.area))[:, None, None]
             np.add.at(b, m.E.tri_edge[:, i], np.einsum('tq,tqd,tqd->t', wq, fi, Einc))

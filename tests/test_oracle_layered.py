@@ -121,3 +121,133 @@ def test_sphere_over_pec_equals_image_pair_in_free_space():
     ne, nt = m.ne, m.nt
     for a_, b_ in ((x[:ne], x2[:ne]), (x[ne:2 * ne], x2[m2.ne:m2.ne + ne]), (x[2 * ne:], x2[2 * m2.ne:2 * m2.ne + nt - 1])):
         assert np.linalg.norm(a_ - b_) <= 1e-11 * np.linalg.norm(b_)
+
+
+def _curl(fun, r, h=1e-6):
+    """curl of a vector field by central differences (fun: (n,3) -> (n,3))."""
+    J = np.zeros((3, 3), complex)   # J[i, j] = d E_i / d x_j
+    for j in range(3):
+        e = np.zeros(3)
+        e[j] = h
+        J[:, j] = (fun(np.array([r + e]))[0] - fun(np.array([r - e]))[0]) / (2 * h)
+    return np.array([J[2, 1] - J[1, 2], J[0, 2] - J[2, 0], J[1, 0] - J[0, 1]])
+
+
+OBLIQUE_STACK = LY.Stack([(1.0, 1.0, 0.0, np.inf), (4.0, 1.0, 0.0, 0.2 * LAM),
+                          (2.5, 2.0, 0.0, 0.07 * LAM), (11.9, 1.0, 0.05, np.inf)], z_top=0.1 * LAM)
+
+
+def _oblique(theta, phi):
+    th, ph = np.radians(theta), np.radians(phi)
+    khat = np.array([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), -np.cos(th)])
+    e_te = np.array([-np.sin(ph), np.cos(ph), 0.0])
+    e_tm = np.cross(e_te, khat)
+    return khat, e_te, e_tm
+
+
+@pytest.mark.parametrize("bottom", ["halfspace", "pec"])
+def test_oblique_wave_meets_interface_conditions(bottom):
+    """Oblique incidence through a lossy, magnetic stack: across every interface
+    the tangential E, the normal eps E and the tangential H = curl E / (-j w mu)
+    are continuous; on a PEC ground the tangential E vanishes; inside each
+    layer E is divergence-free (so the z part of the TM wave is right)."""
+    layers = list(OBLIQUE_STACK.layers)
+    if bottom == "pec":  # every layer below the upper half-space finite, a PEC under the last
+        layers[-1] = (11.9, 1.0, 0.05, 0.11 * LAM)
+    st = LY.Stack(layers, OBLIQUE_STACK.z_top, bottom)
+    khat, e_te, e_tm = _oblique(40.0, 25.0)
+    pol = (0.6 * e_te + 0.8j * e_tm)
+    L = len(st.layers)
+    zs = [st.bounds(i)[0] for i in range(L - 1)] if bottom == "halfspace" else [st.bounds(i)[0] for i in range(L)]
+    xy = np.array([0.11, -0.07]) * LAM
+    for i, z in enumerate(zs):
+        r = np.array([xy[0], xy[1], z])
+        fa = lambda p, i=i: LY.incident_field(st, i, W, khat, pol, p)
+        Ea = fa(np.array([r]))[0]
+        Ha = _curl(fa, r) / (-1j * W * LY.MU0 * st.mu(i))
+        if i == L - 1:  # PEC under the last layer
+            assert np.abs(Ea[:2]).max() < 1e-12
+            continue
+        fb = lambda p, i=i: LY.incident_field(st, i + 1, W, khat, pol, p)
+        Eb = fb(np.array([r]))[0]
+        Hb = _curl(fb, r) / (-1j * W * LY.MU0 * st.mu(i + 1))
+        assert np.abs(Ea[:2] - Eb[:2]).max() < 1e-12
+        assert abs(st.eps(i, W) * Ea[2] - st.eps(i + 1, W) * Eb[2]) < 1e-12 * abs(st.eps(i + 1, W))
+        assert np.abs(Ha[:2] - Hb[:2]).max() < 1e-7 * np.abs(Ha).max()
+    for i in range(L):
+        zb, zu = st.bounds(i)
+        z = zu - 0.03 * LAM if np.isfinite(zu) else zb + 0.05 * LAM
+        r = np.array([0.02 * LAM, 0.05 * LAM, z])
+        div = 0j
+        for j in range(3):
+            e = np.zeros(3)
+            e[j] = 1e-6
+            div += (LY.incident_field(st, i, W, khat, pol, np.array([r + e]))[0][j]
+                    - LY.incident_field(st, i, W, khat, pol, np.array([r - e]))[0][j]) / 2e-6
+        assert abs(div) < 1e-6 * K0
+
+
+def test_oblique_reduces_to_normal_and_free_space():
+    st = OBLIQUE_STACK
+    pts = lambda i: np.array([[0.1, 0.2, st.bounds(i)[1] - 0.01 * LAM if i else st.z_top + 0.3 * LAM]])
+    # theta = 0: the normal-incidence transfer of the x polarisation
+    for i in range(len(st.layers)):
+        E = LY.incident_field(st, i, W, [0, 0, -1.0], [1.0, 0, 0], pts(i))[0]
+        a, c, k, zref = LY.plane_wave_normal(st, i, W)
+        z = pts(i)[0, 2]
+        assert abs(E[0] - (a * np.exp(1j * k * (z - zref)) + c * np.exp(-1j * k * (z - zref)))) < 1e-13
+        assert abs(E[1]) < 1e-14 and abs(E[2]) < 1e-14
+    # identical layers: the free-space wave itself
+    same = LY.Stack([(1.0, 1.0, 0.0, np.inf), (1.0, 1.0, 0.0, 0.2 * LAM), (1.0, 1.0, 0.0, np.inf)], z_top=0.0)
+    khat, e_te, e_tm = _oblique(63.0, -110.0)
+    pol = 0.3 * e_te - 0.4j * e_tm
+    r = np.array([[0.3, -0.2, 0.4], [0.1, 0.1, -0.1], [-0.2, 0.5, -0.9]]) * LAM
+    for i, p in zip((0, 1, 2), r):
+        E = LY.incident_field(same, i, W, khat, pol, p[None])[0]
+        assert np.abs(E - pol * np.exp(-1j * K0 * khat @ p)).max() < 1e-13
+
+
+def test_oblique_fresnel_and_brewster():
+    """Air over glass: the reflected TE / TM amplitudes are the Fresnel
+    coefficients (transverse E convention), zero for TM at Brewster's angle
+    tan theta_B = n, and the power balance |r|^2 + Re(k_z2 / k_z1 ...) |t|^2 = 1."""
+    n = 1.5
+    st = LY.Stack([(1.0, 1.0, 0.0, np.inf), (n * n, 1.0, 0.0, np.inf)], z_top=0.0)
+    for theta in (0.0, 30.0, np.degrees(np.arctan(n)), 75.0):
+        khat, e_te, e_tm = _oblique(theta, 10.0)
+        ct = np.cos(np.radians(theta))
+        ct2 = np.sqrt(1 - (np.sin(np.radians(theta)) / n) ** 2)
+        lay, _ = LY.plane_wave_oblique(st, W, khat, e_te)
+        r_te = (ct - n * ct2) / (ct + n * ct2)
+        assert abs(lay[0]["c_te"] / lay[0]["a_te"] - r_te) < 1e-14
+        t = lay[1]["a_te"] / lay[0]["a_te"]
+        assert abs(abs(r_te) ** 2 + n * ct2 / ct * abs(t) ** 2 - 1) < 1e-13
+        lay, _ = LY.plane_wave_oblique(st, W, khat, e_tm)
+        r_tm = (ct2 / n - ct) / (ct2 / n + ct)  # Z = k_z / (w eps): (Z2 - Z1) / (Z2 + Z1)
+        assert abs(lay[0]["c_tm"] / lay[0]["a_tm"] - r_tm) < 1e-14
+        if abs(theta - np.degrees(np.arctan(n))) < 1e-9:
+            assert abs(lay[0]["c_tm"]) < 1e-14
+
+
+def test_oblique_sphere_over_pec_equals_image_pair():
+    """A sphere over a PEC ground lit at 35 degrees (TE + TM mixed) solves like the
+    sphere and its mirror image in free space lit by the incident wave plus its
+    mirror wave (k_z and the tangential E reversed, the normal E kept)."""
+    f, h, rad = 300e6, 0.15, 0.1
+    v, fc = icosphere(1, rad, (0.0, 0.0, h))
+    m = Mesh(v, fc)
+    st = LY.Stack([(1.0, 1.0, 0.0, np.inf)], z_top=0.0, bottom="pec")
+    khat, e_te, e_tm = _oblique(35.0, 20.0)
+    pol = 0.8 * e_te + 0.6j * e_tm
+    A = S.assemble(m, [S.Material(4.0)], st, f, layer=0)
+    x = S.solve(A, S.rhs(A, khat=khat, pol=pol))
+    vi = v.copy()
+    vi[:, 2] *= -1
+    xyz, tri, obj = merge((v, fc), (vi, fc[:, ::-1].copy()))
+    m2 = Mesh(xyz, tri, obj)
+    A2 = S.assemble(m2, [S.Material(4.0)] * 2, S.Material(), f)
+    mirror = np.array([1.0, 1.0, -1.0])
+    x2 = S.solve(A2, S.rhs(A2, khat=khat, pol=pol) + S.rhs(A2, khat=khat * mirror, pol=-pol * mirror))
+    ne, nt = m.ne, m.nt
+    for a_, b_ in ((x[:ne], x2[:ne]), (x[ne:2 * ne], x2[m2.ne:m2.ne + ne]), (x[2 * ne:], x2[2 * m2.ne:2 * m2.ne + nt - 1])):
+        assert np.linalg.norm(a_ - b_) <= 1e-11 * np.linalg.norm(b_)
