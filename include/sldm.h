@@ -183,7 +183,8 @@ int sldm_mesh_destroy(sldm_mesh* mesh);
  * images of the adjacent interfaces, and a remainder tabulated from Sommerfeld
  * integrals on 256 log-spaced rho x 128 points in z + z' and in |z - z'|,
  * bilinearly interpolated); the equivalent configuration (Eq. AEFIEeqvdis) uses
- * the homogeneous kernel of layer l.  Plane waves: normal incidence from the top. */
+ * the homogeneous kernel of layer l.  Plane waves: any incidence from the upper
+ * half-space, carried through the stack as TE and TM transmission lines. */
 int sldm_stack_create(const sldm_layer* layers, int32_t nlayers, double z_top, int32_t bottom,
                       sldm_stack** out);
 int sldm_stack_destroy(sldm_stack* stack);
@@ -224,7 +225,14 @@ int sldm_apply(const sldm_op* op, const void* x, void* y, int32_t nrhs, int32_t 
  * b = [e_inc; 0; 0], e_inc[m] = int f_m . E_inc / eta0,
  * E_inc = pol E0 exp(-j k0 khat . r) with E0 = 1 V/m.
  * khat, pol: nrhs x 3 (real unit direction, real polarisation), host.
- * b: N x nrhs complex128, column-major. */
+ * b: N x nrhs complex128, column-major.  In a stratified background the wave
+ * comes from the upper half-space (khat_z < 0, else SLDM_EINVAL) and E_inc is
+ * the total field of the stack in the objects' layer: with kt = k0 (khat_x, khat_y),
+ * rho = kt / |kt| (at normal incidence the transverse direction of pol) and
+ * phi = z x rho, the TE part (E along phi) and the TM part (H along phi) each
+ * follow a transmission line in z with line impedances w mu / k_z and
+ * k_z / (w eps), continuous transverse E and the reflection coefficient of the
+ * layers below at every interface. */
 int sldm_rhs_planewave(const sldm_op* op, const double* khat, const double* pol, int32_t nrhs,
                        void* b, int32_t where, void* stream);
 

@@ -1141,13 +1141,13 @@ int sldm_rhs_planewave(const sldm_op* op, const double* khat, const double* pol,
   SLDM_CUDA(cudaMemsetAsync(db, 0, size_t(op->N) * nrhs * sizeof(double2), s));
   if (op->layered) {
     for (int r = 0; r < nrhs; ++r)
-      SLDM_REQUIRE(std::fabs(khat[3 * r]) < 1e-12 && std::fabs(khat[3 * r + 1]) < 1e-12 && khat[3 * r + 2] < 0, SLDM_ENOTSUP,
-                   "rhs_planewave: layered backgrounds take normal incidence from the top (khat = -z)");
-    std::complex<double> ca, cc, ck;
-    double zref;
-    mgf_plane_wave_normal(op->H, op->thick, op->z_top, 2 * PI_ * op->freq, &ca, &cc, &ck, &zref);
-    const double coef[7] = {ca.real(), ca.imag(), cc.real(), cc.imag(), ck.real(), ck.imag(), zref};
-    rhs_planewave_layered(op->mesh, coef, dk.p, nrhs, db, op->N, s);
+      SLDM_REQUIRE(khat[3 * r + 2] < 0, SLDM_EINVAL, "rhs_planewave: layered backgrounds take incidence from the top (khat_z < 0)");
+    std::vector<double> rec(size_t(PW_REC) * nrhs);
+    for (int r = 0; r < nrhs; ++r)
+      mgf_plane_wave(op->H, op->thick, op->z_top, 2 * PI_ * op->freq, khat + 3 * r, pol + 3 * r, rec.data() + size_t(PW_REC) * r);
+    DBuf<double> drec;
+    drec.upload(rec, s);
+    rhs_planewave_layered(op->mesh, drec.p, nrhs, db, op->N, s);
   } else {
     rhs_planewave(op->mesh, op->k0, dk.p, nrhs, db, op->N, s);
   }

@@ -846,45 +846,65 @@ __global__ void rhs_kernel(int ne, int nrhs, double k0, const double* __restrict
   b[int64_t(r) * ld + m] = make_double2(acc_r, acc_i);
 }
 
-// Normal incidence through a stack: in the objects' layer E_inc = pol (a e^{+j k (z - zref)} + c e^{-j k (z - zref)}).
-__global__ void rhs_layered_kernel(int ne, int nrhs, double ar, double ai, double cr, double ci, double kr, double ki, double zref,
-                                   const double* __restrict__ kp, const int32_t* __restrict__ tplus,
+// Plane wave through a stack, in the objects' layer (record layout PW_*):
+// E = e^{-j kt.r} [phi V_TE + rho V_TM + z (|kt| / k_z)(a_TM e^+ - c_TM e^-)],
+// V = a e^+ + c e^-, e^{+-} = e^{+-j k_z (z - zref)}, phi = z x rho.
+__global__ void rhs_layered_kernel(int ne, const double* __restrict__ rec, const int32_t* __restrict__ tplus,
                                    const int32_t* __restrict__ tminus, const int32_t* __restrict__ tri_edge,
                                    const double* __restrict__ geo, double2* b, int64_t ld) {
   int m = blockIdx.x * blockDim.x + threadIdx.x;
   int r = blockIdx.y;
   if (m >= ne) return;
-  const double* pol = kp + 6 * r + 3;
+  const double* P = rec + size_t(r) * PW_REC;
+  const double ktx = P[PW_KT], kty = P[PW_KT + 1], rx = P[PW_RHO], ry = P[PW_RHO + 1];
+  const double px = -ry, py = rx;
+  const double2 ate = make_double2(P[PW_A], P[PW_A + 1]), cte = make_double2(P[PW_A + 2], P[PW_A + 3]);
+  const double2 atm = make_double2(P[PW_A + 4], P[PW_A + 5]), ctm = make_double2(P[PW_A + 6], P[PW_A + 7]);
+  const double kr = P[PW_KZ], ki = P[PW_KZ + 1], zref = P[PW_ZREF];
+  // |kt| / k_z
+  const double kn = kr * kr + ki * ki;
+  const double qr = P[PW_KRHO] * kr / kn, qi = -P[PW_KRHO] * ki / kn;
   double acc_r = 0, acc_i = 0;
   for (int side = 0; side < 2; ++side) {
     int t = side == 0 ? tplus[m] : tminus[m];
     const double* g = geo + size_t(t) * GEO_STRIDE;
     int i = tri_edge[3 * t] == m ? 0 : (tri_edge[3 * t + 1] == m ? 1 : 2);
     for (int q = 0; q < 6; ++q) {
-      double fp = 0;
-      for (int d = 0; d < 3; ++d) fp += g[GEO_SIG + i] * (g[GEO_RHO + 3 * q + d] + g[GEO_AV + 3 * i + d]) * pol[d];
-      const double dz = g[GEO_C + 2] + g[GEO_RHO + 3 * q + 2] - zref;
-      // e^{+j k dz} = e^{-ki dz} (cos(kr dz) + j sin(kr dz)),  e^{-j k dz} = e^{ki dz} (cos - j sin)
+      double f[3], x[3];
+      for (int d = 0; d < 3; ++d) {
+        f[d] = g[GEO_SIG + i] * (g[GEO_RHO + 3 * q + d] + g[GEO_AV + 3 * i + d]);
+        x[d] = g[GEO_C + d] + g[GEO_RHO + 3 * q + d];
+      }
+      const double dz = x[2] - zref;
+      // e^{+j k_z dz} = e^{-ki dz} (cos(kr dz) + j sin(kr dz)),  e^{-j k_z dz} = e^{ki dz} (cos - j sin)
       double sn, cn;
       sincos(kr * dz, &sn, &cn);
       const double ep = exp(-ki * dz), em = exp(ki * dz);
       const double ur = ep * cn, ui = ep * sn, vr = em * cn, vi = -em * sn;
-      const double er = ar * ur - ai * ui + cr * vr - ci * vi;
-      const double ei = ar * ui + ai * ur + cr * vi + ci * vr;
-      const double w = g[GEO_W + q] * fp / ETA0;
-      acc_r += w * er;
-      acc_i += w * ei;
+      const double vte_r = ate.x * ur - ate.y * ui + cte.x * vr - cte.y * vi;
+      const double vte_i = ate.x * ui + ate.y * ur + cte.x * vi + cte.y * vr;
+      const double vtm_r = atm.x * ur - atm.y * ui + ctm.x * vr - ctm.y * vi;
+      const double vtm_i = atm.x * ui + atm.y * ur + ctm.x * vi + ctm.y * vr;
+      const double dr = atm.x * ur - atm.y * ui - (ctm.x * vr - ctm.y * vi);
+      const double di = atm.x * ui + atm.y * ur - (ctm.x * vi + ctm.y * vr);
+      const double ez_r = qr * dr - qi * di, ez_i = qr * di + qi * dr;
+      const double fp = f[0] * px + f[1] * py, fr = f[0] * rx + f[1] * ry;
+      const double sr = fp * vte_r + fr * vtm_r + f[2] * ez_r, si = fp * vte_i + fr * vtm_i + f[2] * ez_i;
+      double sl, cl;  // e^{-j kt.r}
+      sincos(ktx * x[0] + kty * x[1], &sl, &cl);
+      const double w = g[GEO_W + q] / ETA0;
+      acc_r += w * (sr * cl + si * sl);
+      acc_i += w * (si * cl - sr * sl);
     }
   }
   b[int64_t(r) * ld + m] = make_double2(acc_r, acc_i);
 }
 
-void rhs_planewave_layered(const sldm_mesh* m, const double coef[7], const double* kp, int nrhs, double2* b, int64_t ld,
-                           cudaStream_t s) {
+void rhs_planewave_layered(const sldm_mesh* m, const double* rec, int nrhs, double2* b, int64_t ld, cudaStream_t s) {
   int ne = int(m->h.ne);
   dim3 grid((ne + 127) / 128, nrhs);
-  rhs_layered_kernel<<<grid, 128, 0, s>>>(ne, nrhs, coef[0], coef[1], coef[2], coef[3], coef[4], coef[5], coef[6], kp,
-                                          m->d.tplus.p, m->d.tminus.p, m->d.tri_edge.p, m->d.geo.p, b, ld), ::sldm::count_launch();
+  rhs_layered_kernel<<<grid, 128, 0, s>>>(ne, rec, m->d.tplus.p, m->d.tminus.p, m->d.tri_edge.p, m->d.geo.p, b, ld),
+      ::sldm::count_launch();
   SLDM_CUDA(cudaGetLastError());
 }
 

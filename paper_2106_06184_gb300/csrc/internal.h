@@ -227,9 +227,11 @@ void gram_ix(const sldm_mesh* m, double* vals, cudaStream_t s);
 // e_inc for nrhs plane waves into b (complex128, column-major N x nrhs, ld)
 void rhs_planewave(const sldm_mesh* m, double k0, const double* khat_pol_dev, int nrhs, double2* b,
                    int64_t ld, cudaStream_t s);
-// e_inc for normal incidence through a stack: coef = (Re a, Im a, Re c, Im c, Re k, Im k, zref)
-void rhs_planewave_layered(const sldm_mesh* m, const double coef[7], const double* khat_pol_dev, int nrhs, double2* b,
-                           int64_t ld, cudaStream_t s);
+// Plane wave through a stack, one record per right-hand side (filled by mgf_plane_wave):
+// kt (x, y), rho (x, y), a_TE, c_TE, a_TM, c_TM (re, im), k_z (re, im), |kt|, zref.
+constexpr int PW_KT = 0, PW_RHO = 2, PW_A = 4, PW_KZ = 12, PW_KRHO = 14, PW_ZREF = 15, PW_REC = 16;
+// e_inc in the objects' layer of a stack for nrhs plane waves (records rec_dev, PW_REC doubles each)
+void rhs_planewave_layered(const sldm_mesh* m, const double* rec_dev, int nrhs, double2* b, int64_t ld, cudaStream_t s);
 // far field vector F(theta, phi) of RWG coefficients jd (complex128) -> rcs (double), device
 void farfield(const sldm_mesh* m, double k0, const double2* jd, const double* ang_dev, int n, double* rcs,
               cudaStream_t s);

@@ -545,37 +545,72 @@ MgfStatic mgf_static(const MgfStackHost& H) {
 }
 
 // Normal-incidence plane wave through the stack: E_x = a e^{+j k (z - zref)} + c e^{-j k (z - zref)} in layer l.
-void mgf_plane_wave_normal(const MgfStackHost& H, const std::vector<double>& thick, double z_top, double omega,
-                           std::complex<double>* a_out, std::complex<double>* c_out, std::complex<double>* k_out,
-                           double* zref_out) {
+// Oblique plane wave through the stack, incident from the upper half-space.  The
+// transverse wavevector kt = k0 (khat_x, khat_y) is common to all layers; with
+// rho = kt / |kt| (at normal incidence the transverse direction of pol) and
+// phi = z x rho the field splits into TE (E along phi, line impedance
+// w mu0 mu_i / k_z,i) and TM (H along phi, impedance k_z,i / (w eps0 eps_i)).  For each,
+// the transverse E is a transmission line in z: in layer i it is
+// a e^{+j k_z (z - zref)} + c e^{-j k_z (z - zref)}, c / a at the layer's bottom the
+// reflection coefficient looking down, continuous across every interface.  In the
+// objects' layer E = e^{-j kt.r} [phi V_TE + rho V_TM + z (|kt| / k_z)(a_TM e^+ - c_TM e^-)].
+void mgf_plane_wave(const MgfStackHost& H, const std::vector<double>& thick, double z_top, double omega, const double* khat,
+                    const double* pol, double rec[PW_REC]) {
   typedef std::complex<double> C;
   const int L = int(H.eps.size());
   const double k0 = omega / C0_;
-  std::vector<C> ks(L), eta(L), down(L);
+  const double ktx = k0 * khat[0], kty = k0 * khat[1];
+  const double krho = std::hypot(ktx, kty);
+  double rx, ry;
+  if (krho > 1e-12 * k0) {
+    rx = ktx / krho;
+    ry = kty / krho;
+  } else {
+    const double n = std::hypot(pol[0], pol[1]);
+    rx = n > 0 ? pol[0] / n : 1.0;
+    ry = n > 0 ? pol[1] / n : 0.0;
+  }
+  const double px = -ry, py = rx;  // phi = z x rho
+  std::vector<C> kz(L), Z(L), down(L);
   std::vector<bool> finite(L);
   for (int i = 0; i < L; ++i) {
-    ks[i] = k0 * std::sqrt(H.eps[i] * H.mu[i]);
-    eta[i] = std::sqrt(H.mu[i] / H.eps[i]);
+    C q = std::sqrt(C(k0 * k0) * H.eps[i] * H.mu[i] - C(krho * krho));
+    if (q.imag() > 0) q = -q;
+    kz[i] = q;
     finite[i] = i > 0 && (H.pec || i < L - 1);
   }
-  down[L - 1] = H.pec ? C(-1) : C(0);
-  for (int i = L - 2; i >= 0; --i) {
-    const C f = (eta[i + 1] - eta[i]) / (eta[i + 1] + eta[i]);
-    const C ph = finite[i + 1] ? down[i + 1] * std::exp(C(0, -2) * ks[i + 1] * thick[i + 1]) : C(0);
-    down[i] = (f + ph) / (C(1) + f * ph);
+  for (int pt = 0; pt < 2; ++pt) {  // 0: TE, 1: TM
+    for (int i = 0; i < L; ++i)
+      Z[i] = pt == 0 ? C(omega * MU0_ * H.mu[i]) / kz[i] : kz[i] / (omega * EPS0_ * H.eps[i]);
+    down[L - 1] = H.pec ? C(-1) : C(0);
+    for (int i = L - 2; i >= 0; --i) {
+      const C f = (Z[i + 1] - Z[i]) / (Z[i + 1] + Z[i]);
+      const C ph = finite[i + 1] ? down[i + 1] * std::exp(C(0, -2) * kz[i + 1] * thick[i + 1]) : C(0);
+      down[i] = (f + ph) / (C(1) + f * ph);
+    }
+    const double v0 = pt == 0 ? pol[0] * px + pol[1] * py : pol[0] * rx + pol[1] * ry;
+    C a = v0 * std::exp(C(0, 1) * kz[0] * z_top), c = a * down[0];
+    C v = a + c;
+    for (int i = 1; i <= H.l; ++i) {
+      const C gtop = finite[i] ? down[i] * std::exp(C(0, -2) * kz[i] * thick[i]) : C(0);
+      a = v / (C(1) + gtop);
+      c = a * gtop;
+      if (finite[i]) v = a * std::exp(C(0, -1) * kz[i] * thick[i]) + c * std::exp(C(0, 1) * kz[i] * thick[i]);
+    }
+    rec[PW_A + 4 * pt] = a.real();
+    rec[PW_A + 4 * pt + 1] = a.imag();
+    rec[PW_A + 4 * pt + 2] = c.real();
+    rec[PW_A + 4 * pt + 3] = c.imag();
   }
-  C a = std::exp(C(0, 1) * k0 * z_top), c = a * down[0];
-  C v = a + c;
-  for (int i = 1; i <= H.l; ++i) {
-    const C gtop = finite[i] ? down[i] * std::exp(C(0, -2) * ks[i] * thick[i]) : C(0);
-    a = v / (C(1) + gtop);
-    c = a * gtop;
-    if (finite[i]) v = a * std::exp(C(0, -1) * ks[i] * thick[i]) + c * std::exp(C(0, 1) * ks[i] * thick[i]);
-  }
-  *a_out = a;
-  *c_out = c;
-  *k_out = ks[H.l];
-  *zref_out = H.l == 0 ? z_top : H.zu;
+  // at normal incidence pol.rho carries the whole wave, so the TM form holds with krho = 0
+  rec[PW_KT] = ktx;
+  rec[PW_KT + 1] = kty;
+  rec[PW_RHO] = rx;
+  rec[PW_RHO + 1] = ry;
+  rec[PW_KZ] = kz[H.l].real();
+  rec[PW_KZ + 1] = kz[H.l].imag();
+  rec[PW_KRHO] = krho;
+  rec[PW_ZREF] = H.l == 0 ? z_top : H.zu;
 }
 
 template void mgf_fill_reflected<float2>(const sldm_mesh*, const MgfStackHost&, double, const MgfTables&, void*, int64_t, void*,

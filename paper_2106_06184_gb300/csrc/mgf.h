@@ -40,7 +40,9 @@ void mgf_build_tables(const MgfStackHost& H, double omega, double rho_min, doubl
 template <class C>
 void mgf_fill_reflected(const sldm_mesh* m, const MgfStackHost& H, double omega, const MgfTables& T, void* LA, int64_t ldA,
                         void* LP, int64_t ldP, cudaStream_t s);
-void mgf_plane_wave_normal(const MgfStackHost& H, const std::vector<double>& thick, double z_top, double omega,
-                           std::complex<double>* a, std::complex<double>* c, std::complex<double>* k, double* zref);
+// Per right-hand side record of a plane wave in the objects' layer (layout PW_*):
+// kt (2), rho (2), a_TE, c_TE, a_TM, c_TM (complex), k_z (complex), |kt|, zref.
+void mgf_plane_wave(const MgfStackHost& H, const std::vector<double>& thick, double z_top, double omega, const double* khat,
+                    const double* pol, double rec[PW_REC]);
 
 }  // namespace sldm

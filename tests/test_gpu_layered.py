@@ -79,6 +79,33 @@ def test_layered_blocks_and_solution(which, request):
     assert rel(x, c.x) < 1e-8
 
 
+@pytest.mark.parametrize("which", ["over_pec", "in_slab"])
+def test_layered_oblique_incidence(which, request):
+    """Oblique TE, TM and mixed plane waves through the stack (one batched call of
+    five right-hand sides, incl. grazing 80 degrees and normal incidence) against
+    the oracle's stack-transferred field, then the solution of one of them."""
+    c = request.getfixturevalue(which)
+    sl, m, st, op = c.gpu(0)
+    waves = []
+    for th, ph, a_te, a_tm in ((35.0, 20.0, 1.0, 0.0), (35.0, 20.0, 0.0, 1.0), (60.0, -130.0, 0.6, 0.8),
+                               (80.0, 45.0, 0.8, -0.6), (0.0, 0.0, 0.0, 1.0)):
+        t, p = np.radians(th), np.radians(ph)
+        khat = np.array([np.sin(t) * np.cos(p), np.sin(t) * np.sin(p), -np.cos(t)])
+        e_te = np.array([-np.sin(p), np.cos(p), 0.0])
+        waves.append((khat, a_te * e_te + a_tm * np.cross(e_te, khat)))
+    K = np.array([w[0] for w in waves])
+    P = np.array([w[1] for w in waves])
+    b = np.zeros((len(waves), op.N), complex)
+    op.rhs_planewave(K, P, b)
+    for r, (khat, pol) in enumerate(waves):
+        ref = S.rhs(c.A, khat=khat, pol=pol)
+        assert rel(b[r], ref) < 1e-12, (r, rel(b[r], ref))
+    x = np.zeros(op.N, complex)
+    op.solve(b[2], x, tol=1e-11)
+    xr = S.solve(c.A, S.rhs(c.A, khat=waves[2][0], pol=waves[2][1]))
+    assert rel(x, xr) < 1e-8
+
+
 def test_layered_tables_match_oracle(in_slab):
     c = in_slab
     sl, m, st, op = c.gpu(0)
@@ -96,7 +123,7 @@ def test_layered_tables_match_oracle(in_slab):
 def test_layered_fp32_and_invalid_cases(in_slab, over_pec):
     sl, m, st, op = in_slab.gpu(1)
     assert relmax(op.block(sl.BLOCK_LAM), in_slab.A.LAm) < 1e-5
-    # far field is free-space only; oblique incidence is not available in a stack
+    # far field is free-space only; a wave must come from the upper half-space
     x = np.zeros(op.N, complex)
     with pytest.raises(sl.SldmError):
         op.farfield(x, np.array([0.1]), np.array([0.0]))
