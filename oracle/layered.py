@@ -227,6 +227,13 @@ def spectral(stack, l, omega, kr, s=None, dd=None, part="full", z=None, zp=None)
         out["xx"] = out["xx"] - mu_r * (guh * E1 + gdh * E2) * g
         out["phi"] = out["phi"] - (gue * E1 + gde * E2) * g / eps_r
         out["zz"] = out["zz"] - mu_r * ((guh - 2 * gue) * E1 + (gdh - 2 * gde) * E2) * g
+        # z-rho / rho-z: the static (k -> 0, k_rho -> infinity) single reflections, whose
+        # S1 transform is closed-form (static_zr): exp(-k_rho zeta) in place of E1, E2
+        X1 = np.exp(-kr * (2 * zu - s_)) if top else zero
+        X2 = np.exp(-kr * (s_ - 2 * zb)) if bot else zero
+        cu, cd = gue - guh, gde - gdh
+        out["zr"] = out["zr"] - 0.5j * mu_r / kr * (-cu * X1 + cd * X2)
+        out["rz"] = out["rz"] - 0.5j * mu_r / kr * (cu * X1 - cd * X2)
     return out
 
 
@@ -299,7 +306,12 @@ def build_tables(stack, l, omega, rho_min, rho_max, zmin, zmax, nr=256, ns=128, 
         zetas.append(2 * zu - 2 * zmax)
     if np.isfinite(zb):
         zetas.append(2 * zmin - 2 * zb)
-    zeta_a = min(zetas) if zetas else 1.0
+    # Objects may rest on an interface (z + z' - 2 z_b = 0 there): the Sommerfeld tail
+    # is then cut where exp(-k_rho zeta_floor) < 1e-14, zeta_floor = 1/16 of the
+    # objects' height (the remainder decays algebraically once the static images,
+    # z-rho / rho-z included, are out; the cut costs ~1e-4 of the remainder).
+    zeta_floor = (zmax - zmin) / 16 if zmax > zmin else 1e-3 * rho_max
+    zeta_a = max(min(zetas), zeta_floor) if zetas else 1.0
     A, B = {}, {}
     nodes, w = sommerfeld_nodes(stack, l, omega, rho_max, zeta_a)
     vals = {c: np.stack([spectral(stack, l, omega, nodes, s=si, part="A")[c] for si in s], axis=1) for c in COMPONENTS}
@@ -307,7 +319,7 @@ def build_tables(stack, l, omega, rho_min, rho_max, zmin, zmax, nr=256, ns=128, 
         v = transform(vals[c], nodes, w, rho, ORDER[c])
         A[c] = -1j * v if ORDER[c] == 1 else v
     if np.isfinite(zu) and np.isfinite(zb):
-        zeta_b = 2 * (zu - zb) - (zmax - zmin)
+        zeta_b = max(2 * (zu - zb) - (zmax - zmin), zeta_floor)
         nodes, w = sommerfeld_nodes(stack, l, omega, rho_max, zeta_b)
         vals = {c: np.stack([spectral(stack, l, omega, nodes, dd=di, part="B")[c] for di in d], axis=1)
                 for c in COMPONENTS}
@@ -353,8 +365,12 @@ def remainder(T: Tables, rho, z, zp):
     return out
 
 
-def images(stack, l, omega, rho, z, zp):
-    """Quasistatic image kernels {xx, phi, zz} (spherical waves of layer l)."""
+def images(stack, l, omega, rho, z, zp, use_top=1.0, use_bot=1.0):
+    """Quasistatic image kernels: {xx, phi, zz} spherical waves of layer l from the
+    image points, {zr, rz} the static z-rho / rho-z images (static_zr).  use_top /
+    use_bot (0 or 1, broadcastable) drop one interface's images where they are
+    integrated apart (pairs touching through that interface); a coincident image
+    point (R = 0) contributes 0 here."""
     k0 = omega / C0
     eps_r, mu_r = stack.eps(l, omega), stack.mu(l)
     k = k0 * np.sqrt(eps_r * mu_r)
@@ -363,17 +379,36 @@ def images(stack, l, omega, rho, z, zp):
 
     def G(zeta):
         R = np.sqrt(rho ** 2 + zeta ** 2)
-        return np.exp(-1j * k * R) / (4 * np.pi * R)
-    G1 = G(2 * zu - z - zp) if np.isfinite(zu) else 0.0
-    G2 = G(z + zp - 2 * zb) if np.isfinite(zb) else 0.0
+        with np.errstate(invalid="ignore", divide="ignore"):
+            return np.where(R > 0, np.exp(-1j * k * R) / (4 * np.pi * np.where(R > 0, R, 1.0)), 0.0)
+    G1 = use_top * G(2 * zu - z - zp) if np.isfinite(zu) else 0.0
+    G2 = use_bot * G(z + zp - 2 * zb) if np.isfinite(zb) else 0.0
+    F1 = use_top * static_zr(rho, 2 * zu - z - zp) if np.isfinite(zu) else 0.0
+    F2 = use_bot * static_zr(rho, z + zp - 2 * zb) if np.isfinite(zb) else 0.0
+    cu, cd = gue - guh, gde - gdh
     return {"xx": mu_r * (guh * G1 + gdh * G2), "phi": (gue * G1 + gde * G2) / eps_r,
-            "zz": mu_r * ((guh - 2 * gue) * G1 + (gdh - 2 * gde) * G2)}
+            "zz": mu_r * ((guh - 2 * gue) * G1 + (gdh - 2 * gde) * G2),
+            "zr": mu_r * (-cu * F1 + cd * F2), "rz": mu_r * (cu * F1 - cd * F2)}
+
+
+def static_zr(rho, zeta):
+    """1/(4 pi) int_0^inf exp(-k zeta) J1(k rho) dk = (1 - zeta/R) / (4 pi rho) = rho / (4 pi R (R + zeta)),
+    R = sqrt(rho^2 + zeta^2), zeta >= 0: the spatial form of the static z-rho image (0 at R = 0)."""
+    rho = np.asarray(rho, float)
+    zeta = np.asarray(zeta, float)
+    R = np.sqrt(rho * rho + zeta * zeta)
+    den = R * (R + zeta)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        return np.where(den > 0, rho / np.where(den > 0, den, 1.0), 0.0) / (4 * np.pi)
 
 
 # ----------------------------------------------------------------------------- fill of L^A_m, L^phi_m
 def fill_reflected(mesh, stack, l, omega, T: Tables, tris):
     """Reflected part (images + tabulated remainder) of L^A_m and L^phi_m over ``tris``,
-    all triangle pairs by the 6 x 6 product rule (the kernels are smooth off interfaces)."""
+    by the 6 x 6 product rule, except the images of an interface for pairs of
+    triangles that touch through it (touch_image): the remainder is smooth, and an
+    image is singular only where a triangle meets the mirror of the other, i.e. at a
+    shared vertex on that interface."""
     tris = np.asarray(tris)
     e_of = mesh.E.tri_edge
     edges = np.unique(e_of[tris])
@@ -396,7 +431,8 @@ def fill_reflected(mesh, stack, l, omega, T: Tables, tris):
         rho = np.sqrt(dv[..., 0] ** 2 + dv[..., 1] ** 2)
         z = np.broadcast_to(rq[:, :, None, 2], rho.shape)
         zp = np.broadcast_to(rs[:, None, :, 2], rho.shape)
-        im = images(stack, l, omega, rho, z, zp)
+        t_top, t_bot = touch_masks(mesh, stack, l, ta, tb)
+        im = images(stack, l, omega, rho, z, zp, use_top=(~t_top)[:, None, None], use_bot=(~t_bot)[:, None, None])
         rm = remainder(T, rho, z, zp)
         gxx = im["xx"] + rm["xx"]
         gzz = im["zz"] + rm["zz"]
@@ -411,10 +447,16 @@ def fill_reflected(mesh, stack, l, omega, T: Tables, tris):
         t_zz = np.einsum('pqs,pqi,psj->pij', W * gzz, fa_z, fb_z)
         rhf_b = np.einsum('pqsa,psja->pqsj', rh, fb_t)                   # rhohat . f_n,t
         rhf_a = np.einsum('pqsa,pqia->pqsi', rh, fa_t)                   # rhohat . f_m,t
-        t_zr = np.einsum('pqs,pqi,pqsj->pij', W * rm["zr"], fa_z, rhf_b)
-        t_rz = np.einsum('pqs,pqsi,psj->pij', W * rm["rz"], rhf_a, fb_z)
+        t_zr = np.einsum('pqs,pqi,pqsj->pij', W * (im["zr"] + rm["zr"]), fa_z, rhf_b)
+        t_rz = np.einsum('pqs,pqsi,psj->pij', W * (im["rz"] + rm["rz"]), rhf_a, fb_z)
         la = t_xx + t_zz + t_zr + t_rz
         lp = np.einsum('pqs->p', W * kphi) / (mesh.area[ta] * mesh.area[tb])
+        for plane, tm in (("top", t_top), ("bottom", t_bot)):
+            if tm.any():
+                i = np.nonzero(tm)[0]
+                la_t, lp_t = touch_image(mesh, stack, l, omega, ta[i], tb[i], plane)
+                la[i] += la_t
+                lp[i] += lp_t
         rows = eidx[e_of[ta]][:, :, None] * np.ones((1, 1, 3), dtype=np.int64)
         cols = eidx[e_of[tb]][:, None, :] * np.ones((1, 3, 1), dtype=np.int64)
         np.add.at(LA, (rows.ravel(), cols.ravel()), la.ravel())
@@ -542,3 +584,148 @@ def incident_field(stack, l, omega, khat, pol, r, E0=1.0):
     lat = np.exp(-1j * (r[:, 0] * g["kt"][0] + r[:, 1] * g["kt"][1]))
     return lat[:, None] * (g["phi"][None, :] * vte[:, None] + g["rho"][None, :] * vtm[:, None]
                            + np.array([0.0, 0.0, 1.0])[None, :] * ez[:, None])
+
+
+# ----------------------------------------------------------------------------- objects resting on an interface
+DUFFY_N = 16     # Gauss-Legendre points per direction of the Duffy rule (touch_image)
+
+
+def touch_masks(mesh, stack, l, ta, tb):
+    """Pairs (ta[p], tb[p]) touching through the top / bottom interface of layer l:
+    they share a vertex that lies on that interface (to 1e-9 of the mesh size)."""
+    zb, zu = stack.bounds(l)
+    z = mesh.xyz[:, 2]
+    tol = 1e-9 * np.ptp(mesh.xyz, axis=0).max()
+    out = []
+    for zI in (zu, zb):
+        if not np.isfinite(zI):
+            out.append(np.zeros(len(ta), dtype=bool))
+            continue
+        on = np.abs(z - zI) <= tol
+        va, vb = mesh.tri[ta], mesh.tri[tb]
+        share = (va[:, :, None] == vb[:, None, :]) & on[va][:, :, None]
+        out.append(share.any(axis=(1, 2)))
+    return out[0], out[1]
+
+
+def closest_point(r, T):
+    """The point of triangle T (3, 3) nearest to r (3,)."""
+    a, b, c = T
+    n = np.cross(b - a, c - a)
+    p = r - (r - a) @ n / (n @ n) * n                                  # projection on the plane
+    # barycentric coordinates of p
+    v0, v1, v2 = b - a, c - a, p - a
+    d00, d01, d11, d20, d21 = v0 @ v0, v0 @ v1, v1 @ v1, v2 @ v0, v2 @ v1
+    den = d00 * d11 - d01 * d01
+    bv = (d11 * d20 - d01 * d21) / den
+    bw = (d00 * d21 - d01 * d20) / den
+    if bv >= 0 and bw >= 0 and bv + bw <= 1:
+        return p
+    best, bd = None, np.inf
+    for u, v in ((a, b), (b, c), (c, a)):
+        t = np.clip((r - u) @ (v - u) / ((v - u) @ (v - u)), 0.0, 1.0)
+        q = u + t * (v - u)
+        d = np.linalg.norm(r - q)
+        if d < bd:
+            best, bd = q, d
+    return best
+
+
+def duffy_rule(r, T, n=DUFFY_N):
+    """Points (M, 3) and weights (M,) over triangle T for kernels singular at the point
+    of T nearest to r: T is split at that point Q into (Q, T_i, T_i+1) and each part
+    mapped from the unit square by p = Q + u (T_i - Q) + u v (T_i+1 - T_i), dS = 2 a u du dv
+    (Duffy, SIAM J. Numer. Anal. 19, 1982), n x n Gauss-Legendre points; parts of
+    zero area are dropped."""
+    Qp = closest_point(r, T)
+    x, w = np.polynomial.legendre.leggauss(n)
+    x, w = 0.5 * (x + 1), 0.5 * w
+    u, v = np.meshgrid(x, x, indexing="ij")
+    wu = np.outer(w, w)
+    full = np.linalg.norm(np.cross(T[1] - T[0], T[2] - T[0]))
+    pts, wts = [], []
+    for i in range(3):
+        P1, P2 = T[i], T[(i + 1) % 3]
+        a2 = np.linalg.norm(np.cross(P1 - Qp, P2 - P1))
+        if a2 <= 1e-12 * full:
+            continue
+        p = Qp + u[..., None] * (P1 - Qp) + (u * v)[..., None] * (P2 - P1)
+        pts.append(p.reshape(-1, 3))
+        wts.append((a2 * u * wu).ravel())
+    return np.concatenate(pts), np.concatenate(wts)
+
+
+def touch_image(mesh, stack, l, omega, ta, tb, plane):
+    """The images of one interface ('top' or 'bottom') of layer l for pairs touching
+    through it: (la (P, 3, 3), lp (P,)) added to the product-rule terms without them.
+
+    The image of source point r' in the interface z_I is r'' = (x', y', 2 z_I - z'),
+    so an image term integrates over the mirrored source triangle, where the RWG
+    keeps its transverse part and flips its z part.  xx, phi, zz: the spherical wave
+    G = exp(-j k_l R)/(4 pi R) from r'', with 1/R and R integrated in closed form
+    over the mirrored triangle and the rest by its 6 points (the direct term's
+    touching rule).  z-rho, rho-z: the static kernel rhohat (1 - zeta/R)/(4 pi rho) =
+    (r - r'')_t / (4 pi R (R + zeta)), zeta = |z - z''|, inner integral by duffy_rule
+    on the mirrored triangle.  The outer integral is the 6-point rule."""
+    from .fill import green_smooth
+    from .singular import integrals
+    k0 = omega / C0
+    eps_r, mu_r = stack.eps(l, omega), stack.mu(l)
+    k = k0 * np.sqrt(eps_r * mu_r)
+    zb, zu = stack.bounds(l)
+    gue, guh, gde, gdh = static_reflections(stack, l, omega)
+    if plane == "bottom":
+        zI, ge, gh = zb, gde, gdh
+        czr = mu_r * (gde - gdh)
+    else:
+        zI, ge, gh = zu, gue, guh
+        czr = -mu_r * (gue - guh)
+    crz = -czr
+    cxx, czz, cphi = mu_r * gh, mu_r * (gh - 2 * ge), ge / eps_r
+    xyz, tri = mesh.xyz, mesh.tri
+    A = xyz[tri[ta]]
+    Bm = xyz[tri[tb]].copy()
+    Bm[..., 2] = 2 * zI - Bm[..., 2]
+    P = len(ta)
+    rq, rs = Q.points(A), Q.points(Bm)
+    wq, ws = Q.weights(mesh.area[ta]), Q.weights(mesh.area[tb])
+    sa = mesh.E.tri_sign[ta] / (2 * mesh.area[ta])[:, None]             # (P, 3)
+    sb = mesh.E.tri_sign[tb] / (2 * mesh.area[tb])[:, None]
+    fa = (rq[:, :, None, :] - A[:, None, :, :]) * sa[:, None, :, None]   # (P, 6, 3i, 3)
+    # spherical-wave images: int G and int p G over the mirrored triangle
+    R = np.linalg.norm(rq[:, :, None, :] - rs[:, None, :, :], axis=-1)
+    Gs = green_smooth(k, R) * ws[:, None, :]
+    I0 = Gs.sum(axis=2)                                                  # (P, 6)
+    Ip = np.einsum('pqs,psd->pqd', Gs, rs)                               # (P, 6, 3)
+    I = integrals(rq.reshape(-1, 3), np.repeat(Bm, 6, axis=0))
+    rho = I['rho'].reshape(P, 6, 3)
+    inv_r, rr = I['inv_r'].reshape(P, 6), I['r'].reshape(P, 6)
+    I0 = I0 + inv_r / (4 * np.pi) - k * k * rr / (8 * np.pi)
+    Ip = Ip + (I['p_over_r'].reshape(P, 6, 3) + rho * inv_r[..., None]) / (4 * np.pi) \
+        - k * k * (I['p_r'].reshape(P, 6, 3) + rho * rr[..., None]) / (8 * np.pi)
+    inner = Ip[:, :, None, :] - Bm[:, None, :, :] * I0[:, :, None, None]   # int (p'' - v''_j) G: (P, 6, 3j, 3)
+    la = cxx * np.einsum('pq,pqid,pqjd->pij', wq, fa[..., :2], inner[..., :2]) * sb[:, None, :]
+    la = la - czz * np.einsum('pq,pqi,pqj->pij', wq, fa[..., 2], inner[..., 2]) * sb[:, None, :]
+    lp = cphi * np.einsum('pq,pq->p', wq, I0) / (mesh.area[ta] * mesh.area[tb])
+    # static z-rho / rho-z images by the Duffy rule
+    la = la.astype(complex)
+    for p in range(P):
+        for q in range(6):
+            r = rq[p, q]
+            pts, wts = duffy_rule(r, Bm[p], DUFFY_N)
+            d = r - pts
+            Rr = np.linalg.norm(d, axis=1)
+            zeta = np.abs(r[2] - pts[:, 2])
+            den = Rr * (Rr + zeta)
+            Wk = np.where(den[:, None] > 0, d[:, :2] / np.where(den > 0, den, 1.0)[:, None], 0.0) \
+                * (wts / (4 * np.pi))[:, None]                              # (M, 2)
+            J0 = Wk.sum(axis=0)                                           # (2,)
+            J1 = Wk.T @ pts                                               # (2, 3)
+            for j in range(3):
+                vj = Bm[p, j]
+                tj = (J1[0, 0] - vj[0] * J0[0]) + (J1[1, 1] - vj[1] * J0[1])   # int W . (p'' - v''_j)_t
+                zj = J1[:, 2] - vj[2] * J0                                      # int W (p'' - v''_j)_z
+                for i in range(3):
+                    f = fa[p, q, i]
+                    la[p, i, j] += wq[p, q] * sb[p, j] * (czr * f[2] * tj - crz * (f[:2] @ zj))
+    return la, lp

@@ -251,3 +251,146 @@ def test_oblique_sphere_over_pec_equals_image_pair():
     ne, nt = m.ne, m.nt
     for a_, b_ in ((x[:ne], x2[:ne]), (x[ne:2 * ne], x2[m2.ne:m2.ne + ne]), (x[2 * ne:], x2[2 * m2.ne:2 * m2.ne + nt - 1])):
         assert np.linalg.norm(a_ - b_) <= 1e-11 * np.linalg.norm(b_)
+
+
+# ----------------------------------------------------------------------------- objects resting on an interface
+def _resting_cylinder(zI, up=True):
+    """A 240-triangle cylinder (r = 0.1 lam, h = 0.15 lam) whose base (up) or top
+    (not up) lies on the plane z = zI."""
+    from workloads.meshes import cylinder
+    h = 0.15 * LAM
+    v, f = cylinder(0.1 * LAM, h, center=(0.0, 0.0, zI if up else zI - h))
+    return Mesh(v, f)
+
+
+def _brute_image_pair(m, st, l, a, b, plane, n=40):
+    """One interface's image terms of pair (a, b) straight from images() on the
+    original source triangle: inner integrals by a 40 x 40 Duffy rule centred at the
+    point of b nearest to the mirror of each outer point."""
+    from oracle import quadrature as Q
+    zb, zu = st.bounds(l)
+    zI = zb if plane == "bottom" else zu
+    A, B = m.xyz[m.tri[a]], m.xyz[m.tri[b]]
+    rq, wq = Q.points(A[None])[0], Q.weights(m.area[[a]])[0]
+    sa, sb = m.E.tri_sign[a] / (2 * m.area[a]), m.E.tri_sign[b] / (2 * m.area[b])
+    la = np.zeros((3, 3), complex)
+    lp = 0j
+    for q in range(6):
+        r = rq[q]
+        rm = np.array([r[0], r[1], 2 * zI - r[2]])
+        pts, wts = LY.duffy_rule(rm, B, n)
+        dv = r - pts
+        rho = np.hypot(dv[:, 0], dv[:, 1])
+        im = LY.images(st, l, W, rho, r[2], pts[:, 2], use_top=float(plane == "top"), use_bot=float(plane == "bottom"))
+        with np.errstate(invalid="ignore", divide="ignore"):
+            rh = np.where(rho[:, None] > 0, dv[:, :2] / rho[:, None], 0.0)
+        fa = sa[:, None] * (r - A)                                          # (3i, 3)
+        for j in range(3):
+            fb = sb[j] * (pts - B[j])                                       # (M, 3)
+            Vx = im["xx"][:, None] * fb[:, :2] + im["rz"][:, None] * rh * fb[:, 2:3]
+            Vz = im["zz"] * fb[:, 2] + im["zr"] * np.einsum('md,md->m', rh, fb[:, :2])
+            V = np.concatenate([(wts[:, None] * Vx).sum(0), [(wts * Vz).sum()]])
+            la[:, j] += wq[q] * fa @ V
+        lp += wq[q] * (wts * im["phi"]).sum()
+    return la, lp / (m.area[a] * m.area[b])
+
+
+def _touch_classes(m, zI):
+    """Triangles with all three / two / one vertices on z = zI."""
+    tol = 1e-9 * LAM
+    on = np.abs(m.xyz[:, 2] - zI) <= tol
+    cnt = on[m.tri].sum(axis=1)
+    return [np.nonzero(cnt == c)[0] for c in (3, 2, 1)]
+
+
+@pytest.mark.parametrize("plane", ["bottom", "top"])
+def test_touch_image_against_brute_force(plane):
+    """The images of a pair touching through an interface (closed forms over the
+    mirrored triangle, Duffy rule for the static z-rho terms) against the same
+    kernels from images() integrated over the original source triangle by a fine
+    Duffy rule, for every kind of touch: coincident cap triangles on the interface,
+    caps sharing an edge or a vertex, a side triangle meeting a cap at an edge on
+    the interface, side triangles meeting at a vertex on it.  The slab is magnetic
+    so that both the TE and TM statics enter."""
+    st = LY.Stack([(1.0, 1.0, 0.0, np.inf), (4.0, 1.5, 0.0, 0.4 * LAM), (11.9, 1.0, 0.0, np.inf)], z_top=0.0)
+    l = 1
+    zI = -0.4 * LAM if plane == "bottom" else 0.0
+    m = _resting_cylinder(zI, up=(plane == "bottom"))
+    cap, side2, side1 = _touch_classes(m, zI)
+    tri = m.tri
+    share = lambda a, b: len(set(tri[a]) & set(tri[b]))
+    pairs = [(cap[0], cap[0])]
+    pairs.append((cap[0], next(b for b in cap if b != cap[0] and share(cap[0], b) == 2)))
+    pairs.append((cap[0], next(b for b in cap if share(cap[0], b) == 1)))
+    s2 = next(a for a in side2 if any(share(a, c) == 2 for c in cap))
+    c2 = next(c for c in cap if share(s2, c) == 2)
+    pairs += [(s2, c2), (c2, s2), (s2, s2)]
+    s1 = next(a for a in side1 if share(a, s2) >= 1)
+    pairs += [(s1, s1), (s2, s1), (s1, s2)]
+    ta = np.array([p[0] for p in pairs])
+    tb = np.array([p[1] for p in pairs])
+    t_top, t_bot = LY.touch_masks(m, st, l, ta, tb)
+    assert (t_bot if plane == "bottom" else t_top).all() and not (t_top if plane == "bottom" else t_bot).any()
+    la, lp = LY.touch_image(m, st, l, W, ta, tb, plane)
+    for p, (a, b) in enumerate(pairs):
+        bl, bp = _brute_image_pair(m, st, l, a, b, plane)
+        scale = np.abs(bl).max()
+        assert np.abs(la[p] - bl).max() <= 2e-6 * scale, (a, b, np.abs(la[p] - bl).max() / scale)
+        assert abs(lp[p] - bp) <= 2e-6 * abs(bp), (a, b, abs(lp[p] - bp) / abs(bp))
+
+
+def test_table_on_the_interface_against_fine_sommerfeld():
+    """An object resting on glass: the remainder table's row on the interface
+    (z + z' = 2 z_b, where nothing decays exponentially), at its rho nodes, against
+    the same spectral remainder integrated with a tail 20 times longer; and off the
+    interface the images + interpolated remainder still reproduce the full
+    Sommerfeld kernel."""
+    st = LY.Stack([(1.0, 1.0, 0.0, np.inf), (2.25, 1.0, 0.0, np.inf)], z_top=0.0)
+    h = 0.3 * LAM
+    T = LY.build_tables(st, 0, W, 1e-3 * LAM, 2 * LAM, 0.0, h)
+    ir = np.array([0, 60, 120, 180, 255])      # table nodes: the tail cut alone, no interpolation
+    rho = T.rho[ir]
+    nodes, w = LY.sommerfeld_nodes(st, 0, W, 2 * LAM, h / 16 / 20)
+    sp = LY.spectral(st, 0, W, nodes, s=0.0, part="A")
+    rm = {c: T.A[c][ir, 0] for c in LY.COMPONENTS}
+    for c in LY.COMPONENTS:
+        v = LY.transform(sp[c][:, None], nodes, w, rho, LY.ORDER[c])[:, 0]
+        ref = -1j * v if LY.ORDER[c] == 1 else v
+        scale = np.abs(T.A[c]).max()
+        assert np.abs(rm[c] - ref).max() <= 1e-3 * scale, (c, np.abs(rm[c] - ref).max() / scale)
+    z, zp = 0.1 * LAM, 0.02 * LAM
+    rho = np.array([0.03, 0.2, 0.8]) * LAM
+    full = LY.spatial_full(st, 0, W, rho, z, zp)
+    im = LY.images(st, 0, W, rho, z, zp)
+    rm = LY.remainder(T, rho, z, zp)
+    R0 = np.sqrt(rho ** 2 + (z - zp) ** 2)
+    direct = {"xx": G(K0, R0), "phi": G(K0, R0), "zz": G(K0, R0), "zr": 0, "rz": 0}
+    for c in LY.COMPONENTS:
+        tot = direct[c] + im[c] + rm[c]
+        assert np.abs(tot - full[c]).max() <= 2e-3 * np.abs(full[c]).max(), c
+
+
+def test_resting_cylinder_blocks_are_reciprocal():
+    """A cylinder resting on glass: the reflected L^A_m and L^phi_m are complex
+    symmetric (reciprocity; the z-rho and rho-z images pair up): to rounding where
+    no pair touches through the interface (the product rule is the same both ways),
+    and in norm to the accuracy of the touching-pair rule (closed-form inner, 6-point
+    outer integral, as for the direct term).  The transparent object (eps = air)
+    leaves the incident field unscattered (J_Delta = 0)."""
+    st = LY.Stack([(1.0, 1.0, 0.0, np.inf), (2.25, 1.0, 0.0, np.inf)], z_top=0.0)
+    m = _resting_cylinder(0.0)
+    T = S.default_tables(m, st, 0, W)
+    LA, LP = LY.fill_reflected(m, st, 0, W, T, np.arange(m.nt))
+    ta, tb = np.repeat(np.arange(m.nt), m.nt), np.tile(np.arange(m.nt), m.nt)
+    touch = LY.touch_masks(m, st, 0, ta, tb)[1].reshape(m.nt, m.nt)
+    assert touch.any()
+    assert np.max(np.abs((LP - LP.T)[~touch])) <= 1e-13 * np.max(np.abs(LP))
+    e_touch = np.zeros((m.ne, m.ne), dtype=bool)
+    for a, b in zip(*np.nonzero(touch)):
+        e_touch[np.ix_(m.E.tri_edge[a], m.E.tri_edge[b])] = True
+    assert np.max(np.abs((LA - LA.T)[~(e_touch | e_touch.T)])) <= 1e-13 * np.max(np.abs(LA))
+    assert np.linalg.norm(LA - LA.T) <= 2e-3 * np.linalg.norm(LA)
+    assert np.linalg.norm(LP - LP.T) <= 2e-3 * np.linalg.norm(LP)
+    A = S.assemble(m, [S.Material(1.0)], st, F, layer=0, tables=T)
+    x = S.solve(A, S.rhs(A, khat=[np.sin(0.3), 0, -np.cos(0.3)], pol=[0, 1.0, 0]))
+    assert np.linalg.norm(S.j_delta(A, x)) <= 1e-9 * np.linalg.norm(x[:m.ne])
