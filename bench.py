@@ -83,6 +83,18 @@ for _n in (8, 4):
             pol=[[0.0, 1.0, 0.0] if i % 2 == 0 else [float(np.cos(t)), 0.0, float(np.sin(t))]
                  for i, t in enumerate(_TH32)],
             n_angles=181, e2e_steps=3)
+# The paper-shaped case: the same 8 x 8 cylinders resting on a glass half-space
+# (eps_r 2.25 below z = 0, air above), 32 plane waves from the air side through the
+# interface (incidence 0 - 77.5 deg, TE/TM alternating), complex64 operator with the
+# FP64-accurate refinement residual, GMRES to 1e-8 of the FP64 system.  The far
+# field above a stack is not built, so the step ends at the currents.  4 x 4: the
+# profiling case.
+for _n in (8, 4):
+    for _p, _sfx in ((2, "c64x2"), (1, "c64")):
+        WORKLOADS[f"metasurface-{_n}x{_n}-cyl-epsr6-1um-onglass-{_sfx}-32angles"] = dict(
+            WORKLOADS[f"metasurface-{_n}x{_n}-cyl-epsr6-1um-freespace-{_sfx}-32angles"],
+            mats=[(6.0, 1.0, 0.0, 0)] * (_n * _n), layers=[(1.0, 1.0, 0.0, 0.0), (2.25, 1.0, 0.0, 0.0)], z_top=0.0,
+            bottom="halfspace", n_angles=0)
 # Multiscale conductor in a layered substrate: a copper bar (sigma 5.8e7 S/m,
 # 100 x 2 x 1 um, 2,048 graded triangles, N = 8,191) in the middle of a 10 um SiO2
 # layer (eps_r 3.9) over 200 um of Si (eps_r 11.9, sigma 10 S/m) over a PEC ground,

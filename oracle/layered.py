@@ -44,6 +44,7 @@ and a part depending on (rho, z - z') (double reflections), tabulated separately
 """
 from __future__ import annotations
 
+import functools
 from dataclasses import dataclass
 
 import numpy as np
@@ -631,6 +632,15 @@ def closest_point(r, T):
     return best
 
 
+@functools.lru_cache(maxsize=8)
+def _unit_square_rule(n):
+    """n x n Gauss-Legendre points (u, v) and weights on the unit square."""
+    x, w = np.polynomial.legendre.leggauss(n)
+    x, w = 0.5 * (x + 1), 0.5 * w
+    u, v = np.meshgrid(x, x, indexing="ij")
+    return u, v, np.outer(w, w)
+
+
 def duffy_rule(r, T, n=DUFFY_N):
     """Points (M, 3) and weights (M,) over triangle T for kernels singular at the point
     of T nearest to r: T is split at that point Q into (Q, T_i, T_i+1) and each part
@@ -638,10 +648,7 @@ def duffy_rule(r, T, n=DUFFY_N):
     (Duffy, SIAM J. Numer. Anal. 19, 1982), n x n Gauss-Legendre points; parts of
     zero area are dropped."""
     Qp = closest_point(r, T)
-    x, w = np.polynomial.legendre.leggauss(n)
-    x, w = 0.5 * (x + 1), 0.5 * w
-    u, v = np.meshgrid(x, x, indexing="ij")
-    wu = np.outer(w, w)
+    u, v, wu = _unit_square_rule(n)
     full = np.linalg.norm(np.cross(T[1] - T[0], T[2] - T[0]))
     pts, wts = [], []
     for i in range(3):

@@ -334,6 +334,29 @@ static GlobalReuse global_reuse(const HostMesh& h, bool layered) {
   return g;
 }
 
+// Sommerfeld remainder tables of the objects' layer over the objects' extent:
+// 256 log-spaced rho from 1e-3 of the shortest edge to 1.01 x the mesh diagonal,
+// 128 points in z + z' and in |z - z'| over the objects' heights.
+static void layered_tables(sldm_op* op, cudaStream_t s) {
+  const HostMesh& h = op->mesh->h;
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (int64_t v = 0; v < h.nv; ++v)
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = std::min(lo[d], h.xyz[3 * v + d]);
+      hi[d] = std::max(hi[d], h.xyz[3 * v + d]);
+    }
+  double span = 0, emin = 1e300;
+  for (int d = 0; d < 3; ++d) span += (hi[d] - lo[d]) * (hi[d] - lo[d]);
+  span = std::sqrt(span) * 1.01;
+  for (int64_t n = 0; n < h.ne; ++n) {
+    const double* p = &h.xyz[3 * h.uv[2 * n]];
+    const double* q = &h.xyz[3 * h.uv[2 * n + 1]];
+    emin = std::min(emin, std::sqrt((p[0] - q[0]) * (p[0] - q[0]) + (p[1] - q[1]) * (p[1] - q[1]) + (p[2] - q[2]) * (p[2] - q[2])));
+  }
+  op->T.Q = mgf_static(op->H);
+  mgf_build_tables(op->H, 2 * PI_ * op->freq, 1e-3 * emin, span, lo[2], hi[2], op->T, s);
+}
+
 template <class R>
 static void assemble_impl(sldm_op* op, const sldm_material* mats, cudaStream_t s, bool finish = true) {
   typedef typename std::conditional<sizeof(R) == 4, float2, double2>::type C;
@@ -347,6 +370,7 @@ static void assemble_impl(sldm_op* op, const sldm_material* mats, cudaStream_t s
   op->LAm.zero(s);
   op->LPm.zero(s);
   GlobalReuse gr;
+  std::vector<RTask> rtasks;  // blocks of L^A_m, L^phi_m filled here (the rest are copies)
   {
     LTask t{};
     t.t0 = 0; t.ntest = int32_t(op->nt); t.s0 = 0; t.nsrc = int32_t(op->nt);
@@ -369,12 +393,17 @@ static void assemble_impl(sldm_op* op, const sldm_material* mats, cudaStream_t s
         u.s0 = h.tri_begin[pr.second];
         u.nsrc = h.tri_begin[pr.second + 1] - u.s0;
         tasks.push_back(u);
+        rtasks.push_back({u.t0, u.ntest, u.s0, u.nsrc});
       }
       fill_L<R>(m, tasks, s);
-      copy_blocks(gr.copyA, es, op->LAm.p, op->ne, s);
-      copy_blocks(gr.copyP, es, op->LPm.p, op->nt, s);
+      // in a stack the repeats are copied once the reflected part is in
+      if (!op->layered) {
+        copy_blocks(gr.copyA, es, op->LAm.p, op->ne, s);
+        copy_blocks(gr.copyP, es, op->LPm.p, op->nt, s);
+      }
     } else {
       fill_L<R>(m, {t}, s);
+      rtasks.push_back({0, int32_t(op->nt), 0, int32_t(op->nt)});
     }
   }
   // ---- per-object layout of the local blocks
@@ -502,25 +531,13 @@ static void assemble_impl(sldm_op* op, const sldm_material* mats, cudaStream_t s
     }
     SLDM_CUDA(cudaStreamSynchronize(s));
   }
-  // ---- layered background: add the reflected part (images + tabulated remainder) to L^A_m, L^phi_m
+  // ---- layered background: add the reflected part (images + tabulated remainder)
+  //      to the filled blocks of L^A_m, L^phi_m, then copy the repeated ones
   if (op->layered) {
-    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
-    for (int64_t v = 0; v < h.nv; ++v)
-      for (int d = 0; d < 3; ++d) {
-        lo[d] = std::min(lo[d], h.xyz[3 * v + d]);
-        hi[d] = std::max(hi[d], h.xyz[3 * v + d]);
-      }
-    double span = 0, emin = 1e300;
-    for (int d = 0; d < 3; ++d) span += (hi[d] - lo[d]) * (hi[d] - lo[d]);
-    span = std::sqrt(span) * 1.01;
-    for (int64_t n = 0; n < h.ne; ++n) {
-      const double* p = &h.xyz[3 * h.uv[2 * n]];
-      const double* q = &h.xyz[3 * h.uv[2 * n + 1]];
-      emin = std::min(emin, std::sqrt((p[0] - q[0]) * (p[0] - q[0]) + (p[1] - q[1]) * (p[1] - q[1]) + (p[2] - q[2]) * (p[2] - q[2])));
-    }
-    op->T.Q = mgf_static(op->H);
-    mgf_build_tables(op->H, omega, 1e-3 * emin, span, lo[2], hi[2], op->T, s);
-    mgf_fill_reflected<C>(m, op->H, omega, op->T, op->LAm.p, op->ne, op->LPm.p, op->nt, s);
+    layered_tables(op, s);
+    mgf_fill_reflected<C>(m, op->H, omega, op->T, rtasks, op->LAm.p, op->ne, op->LPm.p, op->nt, s);
+    copy_blocks(gr.copyA, es, op->LAm.p, op->ne, s);
+    copy_blocks(gr.copyP, es, op->LPm.p, op->nt, s);
     SLDM_CUDA(cudaStreamSynchronize(s));
   }
   if (!finish) return;
@@ -972,9 +989,20 @@ int sldm_assemble(const sldm_mesh* m, const sldm_stack* st, const sldm_material*
       H.top = lay > 0;
       H.bot = zb > -1e299;
       op->z_top = st->z_top;
+      // objects lie inside their layer and may rest on its interfaces (to 1e-9 of the mesh size)
+      double span = 0;
+      for (int d = 0; d < 3; ++d) {
+        double a = 1e300, b = -1e300;
+        for (int64_t v = 0; v < m->h.nv; ++v) {
+          a = std::min(a, m->h.xyz[3 * v + d]);
+          b = std::max(b, m->h.xyz[3 * v + d]);
+        }
+        span = std::max(span, b - a);
+      }
+      const double tol = 1e-9 * span;
       for (int64_t v = 0; v < m->h.nv; ++v)
-        SLDM_REQUIRE(m->h.xyz[3 * v + 2] > zb && m->h.xyz[3 * v + 2] < zu, SLDM_EINVAL,
-                     "assemble: the objects must lie strictly inside their layer");
+        SLDM_REQUIRE(m->h.xyz[3 * v + 2] >= zb - tol && m->h.xyz[3 * v + 2] <= zu + tol, SLDM_EINVAL,
+                     "assemble: the objects must lie inside their layer (they may rest on an interface)");
     }
     const sldm_layer& L = st->layers[lay];
     op->eps_b = eps_complex(L.eps_r, L.sigma, 2 * PI_ * freq_hz);

@@ -19,6 +19,7 @@
 #include <complex>
 
 #include "dense.h"
+#include "fill_dev.cuh"
 #include "mgf.h"
 
 namespace sldm {
@@ -190,10 +191,17 @@ __device__ void spectral_rem(const DevStack& S, const MgfStatic& Q, cx kr, int p
     out[0] = out[0] - (mur * (guh * E1 + gdh * E2)) * g;
     out[1] = out[1] - ((gue * E1 + gde * E2) * g) / epsl;
     out[2] = out[2] - (mur * ((guh - 2.0 * gue) * E1 + (gdh - 2.0 * gde) * E2)) * g;
+    // z-rho / rho-z: the static single reflections exp(-k_rho zeta) (closed form in space: static_zr)
+    const cx X1 = S.top ? cexp_(-(kr * mk(2 * S.zu - arg))) : zero;
+    const cx X2 = S.bot ? cexp_(-(kr * mk(arg - 2 * S.zb))) : zero;
+    const cx cu = gue - guh, cdn = gde - gdh;
+    const cx c = mk(0, 0.5 * mur) / kr;
+    out[3] = out[3] - c * (cdn * X2 - cu * X1);
+    out[4] = out[4] - c * (cu * X1 - cdn * X2);
   }
 }
 
-// F[node][j][c] = w_node k_node g_c(k_node; arg_j) / (2 pi)
+// F[c][node][j] = w_node k_node g_c(k_node; arg_j) / (2 pi)
 __global__ void mgf_spectral_kernel(DevStack S, MgfStatic Q, const double2* __restrict__ nodes,
                                     const double2* __restrict__ weights, int nnodes, const double* __restrict__ args,
                                     int nargs, int part, double2* F) {
@@ -207,7 +215,7 @@ __global__ void mgf_spectral_kernel(DevStack S, MgfStatic Q, const double2* __re
   const cx f = (0.5 / 3.14159265358979323846) * (w * kr);
   for (int c = 0; c < 5; ++c) {
     const cx v = f * g[c];
-    F[(int64_t(n) * nargs + j) * 5 + c] = make_double2(v.r, v.i);
+    F[(int64_t(c) * nnodes + n) * nargs + j] = make_double2(v.r, v.i);
   }
 }
 
@@ -219,30 +227,75 @@ __global__ void mgf_bessel_kernel(const double2* __restrict__ nodes, int nnodes,
   const int i = int(idx / nnodes), n = int(idx % nnodes);
   const double2 k = nodes[n];
   cx j0, j1;
-  // real and complex arguments alike: the periodic trapezoid rule is accurate to
-  // rounding for any argument once it has 2(|z| + 40) points
-  bessel01_complex(mk(k.x * rho[i], k.y * rho[i]), &j0, &j1);
+  if (k.y == 0.0) {
+    // real axis (the tail panels, arguments up to ~1e4): the math library's J0, J1
+    j0 = mk(::j0(k.x * rho[i]));
+    j1 = mk(::j1(k.x * rho[i]));
+  } else {
+    // the elliptic arc (|z| below ~1e2): the periodic trapezoid rule is accurate to
+    // rounding once it has 2(|z| + 40) points
+    bessel01_complex(mk(k.x * rho[i], k.y * rho[i]), &j0, &j1);
+  }
   Jm[int64_t(i) * nnodes + n] = make_double2(j0.r, j0.i);
   Jm[int64_t(nr) * nnodes + int64_t(i) * nnodes + n] = make_double2(j1.r, j1.i);
 }
 
-// table[c][i][j] = sum_n J_{order(c)}[i][n] F[n][j][c]  (times -j for the order-1 components)
-__global__ void mgf_contract_kernel(const double2* __restrict__ Jm, const double2* __restrict__ F, int nnodes, int nr,
-                                    int nargs, double2* table) {
+// part[split][c][i][j] = sum over the split's nodes n of J_{order(c)}[i][n] F[c][n][j]:
+// a complex product (rows i: rho, columns j: arguments) blocked as CT_I rows x 128
+// columns per CTA, CT_N nodes of J staged in shared memory per step, the nodes
+// split over gridDim.z / 5 CTAs (summed in a fixed order by mgf_sum_splits).
+constexpr int CT_I = 8, CT_N = 32;
+__global__ void __launch_bounds__(128) mgf_contract_kernel(const double2* __restrict__ Jm, const double2* __restrict__ F, int nnodes,
+                                                           int nr, int nargs, int per_split, double2* part) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  const int i = blockIdx.y;
-  const int c = blockIdx.z;
-  if (j >= nargs) return;
+  const int i0 = blockIdx.y * CT_I;
+  const int c = blockIdx.z % 5, split = blockIdx.z / 5;
   const int order = c >= 3 ? 1 : 0;
-  const double2* J = Jm + int64_t(order) * nr * nnodes + int64_t(i) * nnodes;
-  cx acc = mk(0);
-  for (int n = 0; n < nnodes; ++n) {
-    const double2 a = J[n];
-    const double2 b = F[(int64_t(n) * nargs + j) * 5 + c];
-    acc = acc + cx{a.x, a.y} * cx{b.x, b.y};
+  const double2* J = Jm + int64_t(order) * nr * nnodes;
+  const double2* Fc = F + int64_t(c) * nnodes * nargs;
+  const int n_begin = split * per_split, n_end = min(nnodes, n_begin + per_split);
+  __shared__ double2 Js[CT_I][CT_N];
+  cx acc[CT_I];
+#pragma unroll
+  for (int ii = 0; ii < CT_I; ++ii) acc[ii] = mk(0);
+  for (int n0 = n_begin; n0 < n_end; n0 += CT_N) {
+    for (int e = threadIdx.x; e < CT_I * CT_N; e += blockDim.x) {
+      const int ii = e / CT_N, q = e % CT_N;
+      const int gi = i0 + ii, gn = n0 + q;
+      Js[ii][q] = (gi < nr && gn < n_end) ? J[int64_t(gi) * nnodes + gn] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+    if (j < nargs) {
+      const int nq = min(CT_N, n_end - n0);
+      for (int q = 0; q < nq; ++q) {
+        const double2 f = Fc[int64_t(n0 + q) * nargs + j];
+#pragma unroll
+        for (int ii = 0; ii < CT_I; ++ii) {
+          const double2 a = Js[ii][q];
+          acc[ii].r = fma(a.x, f.x, fma(-a.y, f.y, acc[ii].r));
+          acc[ii].i = fma(a.x, f.y, fma(a.y, f.x, acc[ii].i));
+        }
+      }
+    }
+    __syncthreads();
   }
-  if (order == 1) acc = mk(0, -1) * acc;
-  table[(int64_t(c) * nr + i) * nargs + j] = make_double2(acc.r, acc.i);
+  if (j >= nargs) return;
+  for (int ii = 0; ii < CT_I; ++ii)
+    if (i0 + ii < nr) part[((int64_t(split) * 5 + c) * nr + i0 + ii) * nargs + j] = make_double2(acc[ii].r, acc[ii].i);
+}
+
+// table[c][i][j] = sum over splits of part (in split order), times -j for the order-1 components
+__global__ void mgf_sum_splits(const double2* __restrict__ part, int nsplit, int64_t per, int nr, int nargs, double2* table) {
+  const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (idx >= per) return;
+  double re = 0, im = 0;
+  for (int sp = 0; sp < nsplit; ++sp) {
+    const double2 v = part[int64_t(sp) * per + idx];
+    re += v.x;
+    im += v.y;
+  }
+  const int c = int(idx / (int64_t(nr) * nargs));
+  table[idx] = c >= 3 ? make_double2(im, -re) : make_double2(re, im);
 }
 
 // ---------------------------------------------------------------- host: nodes and tables
@@ -342,7 +395,18 @@ static void build_one(const MgfStackHost& H, const MgfStatic& Q, double omega, c
     mgf_spectral_kernel<<<unsigned((tot + 127) / 128), 128, 0, s>>>(S, Q, dn.p, dw.p, nn, da.p, na, part, F.p), ::sldm::count_launch();
     const int64_t totb = int64_t(nn) * nr;
     mgf_bessel_kernel<<<unsigned((totb + 127) / 128), 128, 0, s>>>(dn.p, nn, dr.p, nr, Jm.p), ::sldm::count_launch();
-    mgf_contract_kernel<<<dim3((na + 127) / 128, nr, 5), 128, 0, s>>>(Jm.p, F.p, nn, nr, na, out), ::sldm::count_launch();
+    // split the nodes so that the product runs ~4 CTAs per SM
+    const int base = ((na + 127) / 128) * ((nr + CT_I - 1) / CT_I) * 5;
+    const int nsplit = std::max(1, std::min(64, (4 * 152 + base - 1) / base));
+    const int per_split = ((nn + nsplit - 1) / nsplit + CT_N - 1) / CT_N * CT_N;
+    const int64_t per = int64_t(5) * nr * na;
+    DBuf<double2> part;
+    part.alloc(size_t(nsplit) * per);
+    mgf_contract_kernel<<<dim3((na + 127) / 128, (nr + CT_I - 1) / CT_I, 5 * nsplit), 128, 0, s>>>(Jm.p, F.p, nn, nr, na,
+                                                                                                   per_split, part.p),
+        ::sldm::count_launch();
+    mgf_sum_splits<<<unsigned((per + 255) / 256), 256, 0, s>>>(part.p, nsplit, per, nr, na, out), ::sldm::count_launch();
+    SLDM_CUDA(cudaStreamSynchronize(s));
   }
   SLDM_CUDA(cudaGetLastError());
   SLDM_CUDA(cudaStreamSynchronize(s));
@@ -365,6 +429,11 @@ void mgf_build_tables(const MgfStackHost& H, double omega, double rho_min, doubl
   T.d1 = zmax - zmin;
   T.A.alloc(size_t(5) * T.nr * T.ns);
   T.B.alloc(size_t(5) * T.nr * T.nd);
+  // Objects may rest on an interface, where z + z' - 2 z_b = 0 and nothing decays
+  // exponentially: the Sommerfeld tail is cut where exp(-k_rho zeta_floor) < 1e-14,
+  // zeta_floor = 1/16 of the objects' height (the remainder decays algebraically
+  // once every static image is out).
+  const double zfloor = zmax > zmin ? (zmax - zmin) / 16 : 1e-3 * rho_max;
   double zeta_a = 1.0;
   {
     bool any = false;
@@ -377,12 +446,12 @@ void mgf_build_tables(const MgfStackHost& H, double omega, double rho_min, doubl
       zm = std::min(zm, 2 * zmin - 2 * H.zb);
       any = true;
     }
-    if (any) zeta_a = zm;
+    if (any) zeta_a = std::max(zm, zfloor);
   }
-  SLDM_REQUIRE(zeta_a > 0, SLDM_EINVAL, "layered background: an object touches or crosses an interface");
   build_one(H, T.Q, omega, rho, sv, 0, zeta_a, T.A.p, s);
+  T.hasB = H.top && H.bot;
   if (H.top && H.bot) {
-    const double zeta_b = 2 * (H.zu - H.zb) - (zmax - zmin);
+    const double zeta_b = std::max(2 * (H.zu - H.zb) - (zmax - zmin), zfloor);
     build_one(H, T.Q, omega, rho, dv, 1, zeta_b, T.B.p, s);
   } else {
     T.B.zero(s);
@@ -395,6 +464,7 @@ struct TabView {
   const double2* B;
   int nr, ns, nd;
   double lr0, lr1, s0, s1, d1;
+  int hasB;
 };
 
 __device__ __forceinline__ cx bilin(const double2* t, int nr, int ny, double fx, double fy, int c) {
@@ -410,21 +480,49 @@ __device__ __forceinline__ cx bilin(const double2* t, int nr, int ny, double fx,
   return {w00 * a00.x + w10 * a10.x + w01 * a01.x + w11 * a11.x, w00 * a00.y + w10 * a10.y + w01 * a01.y + w11 * a11.y};
 }
 
-// One thread per (test, source) triangle pair, 6 x 6 points; kernels are smooth
-// (objects keep away from the interfaces), so every pair uses the product rule.
+// Static z-rho image in space: rho / (4 pi R (R + zeta)), R = |(rho, zeta)|, zeta >= 0; 0 at R = 0.
+__device__ __forceinline__ double static_zr(double rho, double zeta) {
+  const double R = sqrt(rho * rho + zeta * zeta);
+  const double den = R * (R + zeta);
+  return den > 0 ? (0.25 / 3.14159265358979323846) * rho / den : 0.0;
+}
+
+// Pair (t, s) touches through an interface when the triangles share a vertex on
+// it: bits 0-2 (bottom) and 4-6 (top) of onmask flag vertices on the interfaces.
+__device__ __forceinline__ bool touch_through(const int32_t* tri, int t, int s, int mt, int ms, int shift) {
+  if (!((mt >> shift) & 7) || !((ms >> shift) & 7)) return false;
+  for (int i = 0; i < 3; ++i) {
+    if (!((mt >> (shift + i)) & 1)) continue;
+    for (int j = 0; j < 3; ++j)
+      if (((ms >> (shift + j)) & 1) && tri[3 * t + i] == tri[3 * s + j]) return true;
+  }
+  return false;
+}
+
+// One thread per (test, source) triangle pair of a block task, 6 x 6 points: the
+// images (spherical waves and static z-rho / rho-z) and the tabulated remainder.
+// An interface's images are left out for pairs touching through it (they are
+// integrated apart by fill_reflected_touch); a coincident image point adds 0.
 template <class C>
-__global__ void __launch_bounds__(128) fill_reflected_kernel(int nt, const double* __restrict__ geo, const int32_t* __restrict__ tri_edge,
-                                                             DevStack S, MgfStatic Q, TabView T, C* LA, int64_t ldA, C* LP,
-                                                             int64_t ldP) {
+__global__ void __launch_bounds__(128) fill_reflected_kernel(const RTask* __restrict__ tasks, const double* __restrict__ geo,
+                                                             const int32_t* __restrict__ tri_edge, const int32_t* __restrict__ tri,
+                                                             const int32_t* __restrict__ onmask, DevStack S, MgfStatic Q, TabView T,
+                                                             C* LA, int64_t ldA, C* LP, int64_t ldP) {
+  const RTask tk = tasks[blockIdx.y];
   const int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (p >= int64_t(nt) * nt) return;
-  const int t = int(p / nt), sidx = int(p % nt);
+  if (p >= int64_t(tk.ntest) * tk.nsrc) return;
+  const int t = tk.t0 + int(p / tk.nsrc), sidx = tk.s0 + int(p % tk.nsrc);
   const double* gt = geo + size_t(t) * GEO_STRIDE;
   const double* gs = geo + size_t(sidx) * GEO_STRIDE;
   const double k0 = S.omega / C0_;
   const cx epsl = S.eps[S.l];
   const double mur = S.mu[S.l];
   const cx k = k0 * csqrt_(mur * epsl);
+  const int mt = onmask[t], ms = onmask[sidx];
+  const double use_bot = touch_through(tri, t, sidx, mt, ms, 0) ? 0.0 : 1.0;
+  const double use_top = touch_through(tri, t, sidx, mt, ms, 4) ? 0.0 : 1.0;
+  const cx gue = {Q.gue.r, Q.gue.i}, guh = {Q.guh.r, Q.guh.i}, gde = {Q.gde.r, Q.gde.i}, gdh = {Q.gdh.r, Q.gdh.i};
+  const cx cu = gue - guh, cdn = gde - gdh;
   cx loc[9];
   for (int i = 0; i < 9; ++i) loc[i] = mk(0);
   cx lp = mk(0);
@@ -446,15 +544,19 @@ __global__ void __launch_bounds__(128) fill_reflected_kernel(int nt, const doubl
       const double zz = r[2], zp = rs[2];
       // quasistatic images
       cx G1 = mk(0), G2 = mk(0);
+      double F1 = 0, F2 = 0;
       if (S.top) {
-        const double R = sqrt(rho * rho + (2 * S.zu - zz - zp) * (2 * S.zu - zz - zp));
-        G1 = (inv4pi / R) * cexp_(mk(0, -R) * k);
+        const double zeta = 2 * S.zu - zz - zp;
+        const double R = sqrt(rho * rho + zeta * zeta);
+        if (R > 0) G1 = (use_top * inv4pi / R) * cexp_(mk(0, -R) * k);
+        F1 = use_top * static_zr(rho, zeta);
       }
       if (S.bot) {
-        const double R = sqrt(rho * rho + (zz + zp - 2 * S.zb) * (zz + zp - 2 * S.zb));
-        G2 = (inv4pi / R) * cexp_(mk(0, -R) * k);
+        const double zeta = zz + zp - 2 * S.zb;
+        const double R = sqrt(rho * rho + zeta * zeta);
+        if (R > 0) G2 = (use_bot * inv4pi / R) * cexp_(mk(0, -R) * k);
+        F2 = use_bot * static_zr(rho, zeta);
       }
-      const cx gue = {Q.gue.r, Q.gue.i}, guh = {Q.guh.r, Q.guh.i}, gde = {Q.gde.r, Q.gde.i}, gdh = {Q.gdh.r, Q.gdh.i};
       cx gxx = mur * (guh * G1 + gdh * G2);
       cx gphi = (gue * G1 + gde * G2) / epsl;
       cx gzz = mur * ((guh - 2.0 * gue) * G1 + (gdh - 2.0 * gde) * G2);
@@ -465,13 +567,21 @@ __global__ void __launch_bounds__(128) fill_reflected_kernel(int nt, const doubl
       const double dd = zz - zp;
       const double fd = T.d1 > 0 ? fabs(dd) / T.d1 * (T.nd - 1) : 0.0;
       const double sg = dd > 0 ? 1.0 : (dd < 0 ? -1.0 : 0.0);
-      gxx = gxx + bilin(T.A, T.nr, T.ns, fx, fs, 0) + bilin(T.B, T.nr, T.nd, fx, fd, 0);
-      gphi = gphi + bilin(T.A, T.nr, T.ns, fx, fs, 1) + bilin(T.B, T.nr, T.nd, fx, fd, 1);
-      gzz = gzz + bilin(T.A, T.nr, T.ns, fx, fs, 2) + bilin(T.B, T.nr, T.nd, fx, fd, 2);
-      // the S1 (z-rho, rho-z) kernels vanish linearly at rho = 0: below rho_min scale by rho / rho_min
+      gxx = gxx + bilin(T.A, T.nr, T.ns, fx, fs, 0);
+      gphi = gphi + bilin(T.A, T.nr, T.ns, fx, fs, 1);
+      gzz = gzz + bilin(T.A, T.nr, T.ns, fx, fs, 2);
+      cx bzr = bilin(T.A, T.nr, T.ns, fx, fs, 3), brz = bilin(T.A, T.nr, T.ns, fx, fs, 4);
+      if (T.hasB) {
+        gxx = gxx + bilin(T.B, T.nr, T.nd, fx, fd, 0);
+        gphi = gphi + bilin(T.B, T.nr, T.nd, fx, fd, 1);
+        gzz = gzz + bilin(T.B, T.nr, T.nd, fx, fd, 2);
+        bzr = bzr + sg * bilin(T.B, T.nr, T.nd, fx, fd, 3);
+        brz = brz + sg * bilin(T.B, T.nr, T.nd, fx, fd, 4);
+      }
+      // the S1 (z-rho, rho-z) remainders vanish linearly at rho = 0: below rho_min scale by rho / rho_min
       const double lin = fmin(rho * exp(-T.lr0), 1.0);
-      const cx gzr = lin * (bilin(T.A, T.nr, T.ns, fx, fs, 3) + sg * bilin(T.B, T.nr, T.nd, fx, fd, 3));
-      const cx grz = lin * (bilin(T.A, T.nr, T.ns, fx, fs, 4) + sg * bilin(T.B, T.nr, T.nd, fx, fd, 4));
+      const cx gzr = lin * bzr + mur * (cdn * F2 - cu * F1);
+      const cx grz = lin * brz + mur * (cu * F1 - cdn * F2);
       const double hx = rho > 0 ? dx / rho : 0.0, hy = rho > 0 ? dy / rho : 0.0;
       const double w = gs[GEO_W + sq];
       for (int j = 0; j < 3; ++j) {
@@ -506,17 +616,294 @@ __global__ void __launch_bounds__(128) fill_reflected_kernel(int nt, const doubl
   dp->y = decltype(dp->y)(double(dp->y) + sc * lp.i);
 }
 
+// ---------------------------------------------------------------- pairs touching through an interface
+// Gauss-Legendre nodes and weights on [0, 1] of the Duffy rule
+static __constant__ double c_duffy_x[MGF_DUFFY_N], c_duffy_w[MGF_DUFFY_N];
+
+// The point of triangle (a, b, c) nearest to r: the projection on the plane when
+// inside, else the nearest point of the three edges.
+__device__ void closest_point(const double* r, const double* a, const double* b, const double* c, double* out) {
+  double v0[3], v1[3], n[3];
+  for (int d = 0; d < 3; ++d) {
+    v0[d] = b[d] - a[d];
+    v1[d] = c[d] - a[d];
+  }
+  n[0] = v0[1] * v1[2] - v0[2] * v1[1];
+  n[1] = v0[2] * v1[0] - v0[0] * v1[2];
+  n[2] = v0[0] * v1[1] - v0[1] * v1[0];
+  const double nn = n[0] * n[0] + n[1] * n[1] + n[2] * n[2];
+  const double h = ((r[0] - a[0]) * n[0] + (r[1] - a[1]) * n[1] + (r[2] - a[2]) * n[2]) / nn;
+  double p[3], v2[3];
+  for (int d = 0; d < 3; ++d) {
+    p[d] = r[d] - h * n[d];
+    v2[d] = p[d] - a[d];
+  }
+  const double d00 = v0[0] * v0[0] + v0[1] * v0[1] + v0[2] * v0[2];
+  const double d01 = v0[0] * v1[0] + v0[1] * v1[1] + v0[2] * v1[2];
+  const double d11 = v1[0] * v1[0] + v1[1] * v1[1] + v1[2] * v1[2];
+  const double d20 = v2[0] * v0[0] + v2[1] * v0[1] + v2[2] * v0[2];
+  const double d21 = v2[0] * v1[0] + v2[1] * v1[1] + v2[2] * v1[2];
+  const double den = d00 * d11 - d01 * d01;
+  const double bv = (d11 * d20 - d01 * d21) / den, bw = (d00 * d21 - d01 * d20) / den;
+  if (bv >= 0 && bw >= 0 && bv + bw <= 1) {
+    for (int d = 0; d < 3; ++d) out[d] = p[d];
+    return;
+  }
+  const double* E[4] = {a, b, c, a};
+  double best = 1e300;
+  for (int e = 0; e < 3; ++e) {
+    const double* u = E[e];
+    const double* v = E[e + 1];
+    double uv[3], ur[3];
+    for (int d = 0; d < 3; ++d) {
+      uv[d] = v[d] - u[d];
+      ur[d] = r[d] - u[d];
+    }
+    double t = (ur[0] * uv[0] + ur[1] * uv[1] + ur[2] * uv[2]) / (uv[0] * uv[0] + uv[1] * uv[1] + uv[2] * uv[2]);
+    t = fmin(fmax(t, 0.0), 1.0);
+    double qd[3], dist = 0;
+    for (int d = 0; d < 3; ++d) {
+      qd[d] = u[d] + t * uv[d];
+      dist += (r[d] - qd[d]) * (r[d] - qd[d]);
+    }
+    dist = sqrt(dist);
+    if (dist < best) {
+      best = dist;
+      for (int d = 0; d < 3; ++d) out[d] = qd[d];
+    }
+  }
+}
+
+// One group of 8 threads per pair touching through an interface (thread q < 6:
+// outer point q of the test triangle): that interface's images over the mirrored
+// source triangle (x', y', 2 z_I - z'), where the RWG keeps its transverse part and
+// flips its z part.  xx, phi, zz: the spherical wave with 1/R and R in closed form
+// over the mirrored triangle and the rest by its 6 points; z-rho, rho-z: the static
+// kernel (r - r'')_t / (4 pi R (R + zeta)) by the Duffy rule (n x n Gauss points on
+// each of the three parts of the mirrored triangle split at its point nearest r).
 template <class C>
-void mgf_fill_reflected(const sldm_mesh* m, const MgfStackHost& H, double omega, const MgfTables& T, void* LA, int64_t ldA,
-                        void* LP, int64_t ldP, cudaStream_t s) {
+__global__ void fill_reflected_touch(const int32_t* __restrict__ pairs, int npairs, const double* __restrict__ geo,
+                                     const double* __restrict__ xyz, const int32_t* __restrict__ tri,
+                                     const int32_t* __restrict__ tri_edge, DevStack S, MgfStatic Q, C* LA, int64_t ldA, C* LP,
+                                     int64_t ldP) {
+  const int64_t gt_ = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int p = int(gt_ >> 3), q = int(gt_ & 7);
+  const bool valid = p < npairs;
+  const int t = valid ? pairs[3 * p] : 0, sidx = valid ? pairs[3 * p + 1] : 0, top = valid ? pairs[3 * p + 2] : 0;
+  const bool act = valid && q < 6;
+  double m[20];
+#pragma unroll
+  for (int i = 0; i < 20; ++i) m[i] = 0.0;
+  const double* gt = geo + size_t(t) * GEO_STRIDE;
+  const double* gs = geo + size_t(sidx) * GEO_STRIDE;
+  if (act) {
+    const double k0 = S.omega / C0_;
+    const cx epsl = S.eps[S.l];
+    const double mur = S.mu[S.l];
+    const cx k = k0 * csqrt_(mur * epsl);
+    const cx k2 = k * k;
+    const double zI = top ? S.zu : S.zb;
+    const cx ge = top ? cx{Q.gue.r, Q.gue.i} : cx{Q.gde.r, Q.gde.i};
+    const cx gh = top ? cx{Q.guh.r, Q.guh.i} : cx{Q.gdh.r, Q.gdh.i};
+    const cx czr = top ? -(mur * (ge - gh)) : mur * (ge - gh), crz = -czr;
+    const cx cxx = mur * gh, czz = mur * (gh - 2.0 * ge), cphi = ge / epsl;
+    double Bm[3][3];  // mirrored source vertices
+    for (int j = 0; j < 3; ++j)
+      for (int d = 0; d < 3; ++d) Bm[j][d] = d == 2 ? 2 * zI - xyz[3 * tri[3 * sidx + j] + 2] : xyz[3 * tri[3 * sidx + j] + d];
+    double r[3], f[3][3];
+    for (int d = 0; d < 3; ++d) r[d] = gt[GEO_C + d] + gt[GEO_RHO + 3 * q + d];
+    for (int i = 0; i < 3; ++i)
+      for (int d = 0; d < 3; ++d) f[i][d] = gt[GEO_SIG + i] * (gt[GEO_RHO + 3 * q + d] + gt[GEO_AV + 3 * i + d]);
+    // int G and int p G over the mirrored triangle
+    cx I0 = mk(0), Ip[3] = {mk(0), mk(0), mk(0)};
+    for (int j = 0; j < 6; ++j) {
+      double rs[3];
+      for (int d = 0; d < 3; ++d) rs[d] = gs[GEO_C + d] + gs[GEO_RHO + 3 * j + d];
+      rs[2] = 2 * zI - rs[2];
+      const double dx = r[0] - rs[0], dy = r[1] - rs[1], dz = r[2] - rs[2];
+      const cd g = green_smooth(cd{k.r, k.i}, sqrt(dx * dx + dy * dy + dz * dz));
+      const double w = gs[GEO_W + j];
+      I0 = I0 + w * cx{g.r, g.i};
+      for (int d = 0; d < 3; ++d) Ip[d] = Ip[d] + (w * rs[d]) * cx{g.r, g.i};
+    }
+    Pot P;
+    potentials(r, Bm[0], Bm[1], Bm[2], P);
+    I0 = I0 + mk(INV4PI * P.inv_r) - (0.5 * INV4PI * P.r) * k2;
+    for (int d = 0; d < 3; ++d)
+      Ip[d] = Ip[d] + mk(INV4PI * (P.por[d] + P.rho[d] * P.inv_r)) - (0.5 * INV4PI * (P.pr[d] + P.rho[d] * P.r)) * k2;
+    // static z-rho kernel by the Duffy rule: J0 = int W, J1[d][e] = int W_d p_e
+    double J0[2] = {0, 0}, J1[2][3] = {{0, 0, 0}, {0, 0, 0}};
+    {
+      double Qp[3];
+      closest_point(r, Bm[0], Bm[1], Bm[2], Qp);
+      double e1[3], e2[3];
+      for (int d = 0; d < 3; ++d) {
+        e1[d] = Bm[1][d] - Bm[0][d];
+        e2[d] = Bm[2][d] - Bm[0][d];
+      }
+      const double fx_ = e1[1] * e2[2] - e1[2] * e2[1], fy_ = e1[2] * e2[0] - e1[0] * e2[2], fz_ = e1[0] * e2[1] - e1[1] * e2[0];
+      const double full = sqrt(fx_ * fx_ + fy_ * fy_ + fz_ * fz_);
+      for (int sub = 0; sub < 3; ++sub) {
+        const double* P1 = Bm[sub];
+        const double* P2 = Bm[(sub + 1) % 3];
+        double a1[3], a2v[3];
+        for (int d = 0; d < 3; ++d) {
+          a1[d] = P1[d] - Qp[d];
+          a2v[d] = P2[d] - P1[d];
+        }
+        const double cx_ = a1[1] * a2v[2] - a1[2] * a2v[1], cy_ = a1[2] * a2v[0] - a1[0] * a2v[2],
+                     cz_ = a1[0] * a2v[1] - a1[1] * a2v[0];
+        const double a2 = sqrt(cx_ * cx_ + cy_ * cy_ + cz_ * cz_);
+        if (a2 <= 1e-12 * full) continue;
+        for (int iu = 0; iu < MGF_DUFFY_N; ++iu) {
+          const double u = c_duffy_x[iu];
+          for (int iv = 0; iv < MGF_DUFFY_N; ++iv) {
+            const double v = c_duffy_x[iv];
+            const double wt = a2 * u * c_duffy_w[iu] * c_duffy_w[iv];
+            double pt[3];
+            for (int d = 0; d < 3; ++d) pt[d] = Qp[d] + u * a1[d] + u * v * a2v[d];
+            const double dx = r[0] - pt[0], dy = r[1] - pt[1], dz = r[2] - pt[2];
+            const double R = sqrt(dx * dx + dy * dy + dz * dz);
+            const double den = R * (R + fabs(dz));
+            if (!(den > 0)) continue;
+            const double s_ = wt * INV4PI / den;
+            const double wx = s_ * dx, wy = s_ * dy;
+            J0[0] += wx;
+            J0[1] += wy;
+            for (int e = 0; e < 3; ++e) {
+              J1[0][e] += wx * pt[e];
+              J1[1][e] += wy * pt[e];
+            }
+          }
+        }
+      }
+    }
+    const double wq = gt[GEO_W + q];
+    for (int j = 0; j < 3; ++j) {
+      const double sb = gs[GEO_SIG + j];
+      cx in[3];
+      for (int d = 0; d < 3; ++d) in[d] = Ip[d] - Bm[j][d] * I0;  // int (p'' - v''_j) G
+      const double tj = (J1[0][0] - Bm[j][0] * J0[0]) + (J1[1][1] - Bm[j][1] * J0[1]);
+      const double zj0 = J1[0][2] - Bm[j][2] * J0[0], zj1 = J1[1][2] - Bm[j][2] * J0[1];
+      for (int i = 0; i < 3; ++i) {
+        const cx v = (wq * sb) * (cxx * (f[i][0] * in[0] + f[i][1] * in[1]) - czz * (f[i][2] * in[2]) +
+                                  czr * (f[i][2] * tj) - crz * (f[i][0] * zj0 + f[i][1] * zj1));
+        m[2 * (3 * i + j)] = v.r;
+        m[2 * (3 * i + j) + 1] = v.i;
+      }
+    }
+    const cx l = (wq / (gt[GEO_A] * gs[GEO_A])) * (cphi * I0);
+    m[18] = l.r;
+    m[19] = l.i;
+  }
+#pragma unroll
+  for (int i = 0; i < 20; ++i) m[i] = grp_sum8(m[i]);
+  if (!valid || q != 0) return;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      C* dst = LA + int64_t(tri_edge[3 * t + i]) * ldA + tri_edge[3 * sidx + j];
+      if (sizeof(dst->x) == 4) {
+        atomicAdd(reinterpret_cast<float2*>(dst), make_float2(float(m[2 * (3 * i + j)]), float(m[2 * (3 * i + j) + 1])));
+      } else {
+        atomicAdd(reinterpret_cast<double*>(dst), m[2 * (3 * i + j)]);
+        atomicAdd(reinterpret_cast<double*>(dst) + 1, m[2 * (3 * i + j) + 1]);
+      }
+    }
+  C* dp = LP + int64_t(t) * ldP + sidx;
+  if (sizeof(dp->x) == 4) {
+    atomicAdd(reinterpret_cast<float2*>(dp), make_float2(float(m[18]), float(m[19])));
+  } else {
+    atomicAdd(reinterpret_cast<double*>(dp), m[18]);
+    atomicAdd(reinterpret_cast<double*>(dp) + 1, m[19]);
+  }
+}
+
+// Per triangle: bits 0-2 / 4-6 flag vertices on the bottom / top interface of the
+// objects' layer (to 1e-9 of the mesh size); the pairs touching through an
+// interface among the listed blocks (t, s, 0 = bottom / 1 = top).
+void mgf_touch_setup(const HostMesh& h, const MgfStackHost& H, const std::vector<RTask>& tasks, std::vector<int32_t>& onmask,
+                     std::vector<int32_t>& pairs) {
+  double span = 0;
+  for (int d = 0; d < 3; ++d) {
+    double a = 1e300, b = -1e300;
+    for (int64_t v = 0; v < h.nv; ++v) {
+      a = std::min(a, h.xyz[3 * v + d]);
+      b = std::max(b, h.xyz[3 * v + d]);
+    }
+    span = std::max(span, b - a);
+  }
+  const double tol = 1e-9 * span;
+  onmask.assign(h.nt, 0);
+  std::vector<int32_t> touching;
+  for (int64_t t = 0; t < h.nt; ++t) {
+    int msk = 0;
+    for (int i = 0; i < 3; ++i) {
+      const double z = h.xyz[3 * size_t(h.tri[3 * t + i]) + 2];
+      if (H.bot && std::fabs(z - H.zb) <= tol) msk |= 1 << i;
+      if (H.top && std::fabs(z - H.zu) <= tol) msk |= 1 << (4 + i);
+    }
+    onmask[t] = msk;
+    if (msk) touching.push_back(int32_t(t));
+  }
+  pairs.clear();
+  for (const RTask& k : tasks)
+    for (int32_t a : touching) {
+      if (a < k.t0 || a >= k.t0 + k.ntest) continue;
+      for (int32_t b : touching) {
+        if (b < k.s0 || b >= k.s0 + k.nsrc) continue;
+        for (int plane = 0; plane < 2; ++plane) {
+          const int sh = plane ? 4 : 0;
+          bool hit = false;
+          for (int i = 0; i < 3 && !hit; ++i)
+            for (int j = 0; j < 3 && !hit; ++j)
+              hit = ((onmask[a] >> (sh + i)) & 1) && ((onmask[b] >> (sh + j)) & 1) && h.tri[3 * size_t(a) + i] == h.tri[3 * size_t(b) + j];
+          if (hit) {
+            pairs.push_back(a);
+            pairs.push_back(b);
+            pairs.push_back(plane);
+          }
+        }
+      }
+    }
+}
+
+template <class C>
+void mgf_fill_reflected(const sldm_mesh* m, const MgfStackHost& H, double omega, const MgfTables& T,
+                        const std::vector<RTask>& tasks, void* LA, int64_t ldA, void* LP, int64_t ldP, cudaStream_t s) {
+  if (tasks.empty()) return;
   const DevStack S = dev_stack(H, omega);
-  TabView tv{T.A.p, T.B.p, T.nr, T.ns, T.nd, T.lr0, T.lr1, T.s0, T.s1, T.d1};
-  const int nt = int(m->h.nt);
-  const int64_t np = int64_t(nt) * nt;
+  TabView tv{T.A.p, T.B.p, T.nr, T.ns, T.nd, T.lr0, T.lr1, T.s0, T.s1, T.d1, T.hasB ? 1 : 0};
   ScopedTimer tm("fill_reflected", s);
-  fill_reflected_kernel<C><<<unsigned((np + 127) / 128), 128, 0, s>>>(nt, m->d.geo.p, m->d.tri_edge.p, S, T.Q, tv, (C*)LA, ldA,
-                                                                      (C*)LP, ldP), ::sldm::count_launch();
+  std::vector<int32_t> onmask, pairs;
+  mgf_touch_setup(m->h, H, tasks, onmask, pairs);
+  DBuf<RTask> dt;
+  DBuf<int32_t> dm, dp;
+  dt.upload(tasks, s);
+  dm.upload(onmask, s);
+  int64_t most = 0;
+  for (const RTask& k : tasks) most = std::max(most, int64_t(k.ntest) * k.nsrc);
+  fill_reflected_kernel<C><<<dim3(unsigned((most + 127) / 128), unsigned(tasks.size())), 128, 0, s>>>(
+      dt.p, m->d.geo.p, m->d.tri_edge.p, m->d.tri.p, dm.p, S, T.Q, tv, (C*)LA, ldA, (C*)LP, ldP), ::sldm::count_launch();
   SLDM_CUDA(cudaGetLastError());
+  const int np = int(pairs.size() / 3);
+  if (np > 0) {
+    std::vector<double> x, w;
+    gauss_legendre(MGF_DUFFY_N, x, w);
+    for (int i = 0; i < MGF_DUFFY_N; ++i) {
+      x[i] = 0.5 * (x[i] + 1);
+      w[i] = 0.5 * w[i];
+    }
+    SLDM_CUDA(cudaMemcpyToSymbol(c_duffy_x, x.data(), sizeof(double) * MGF_DUFFY_N));
+    SLDM_CUDA(cudaMemcpyToSymbol(c_duffy_w, w.data(), sizeof(double) * MGF_DUFFY_N));
+    dp.upload(pairs, s);
+    const int64_t threads = int64_t(np) * 8;
+    fill_reflected_touch<C><<<unsigned((threads + 127) / 128), 128, 0, s>>>(dp.p, np, m->d.geo.p, m->d.xyz.p, m->d.tri.p,
+                                                                            m->d.tri_edge.p, S, T.Q, (C*)LA, ldA, (C*)LP, ldP),
+        ::sldm::count_launch();
+    SLDM_CUDA(cudaGetLastError());
+  }
+  // the uploads above are released at scope exit: finish their readers first
+  SLDM_CUDA(cudaStreamSynchronize(s));
 }
 
 // ---------------------------------------------------------------- stack helpers (host)
@@ -613,9 +1000,9 @@ void mgf_plane_wave(const MgfStackHost& H, const std::vector<double>& thick, dou
   rec[PW_ZREF] = H.l == 0 ? z_top : H.zu;
 }
 
-template void mgf_fill_reflected<float2>(const sldm_mesh*, const MgfStackHost&, double, const MgfTables&, void*, int64_t, void*,
-                                         int64_t, cudaStream_t);
-template void mgf_fill_reflected<double2>(const sldm_mesh*, const MgfStackHost&, double, const MgfTables&, void*, int64_t, void*,
-                                          int64_t, cudaStream_t);
+template void mgf_fill_reflected<float2>(const sldm_mesh*, const MgfStackHost&, double, const MgfTables&,
+                                         const std::vector<RTask>&, void*, int64_t, void*, int64_t, cudaStream_t);
+template void mgf_fill_reflected<double2>(const sldm_mesh*, const MgfStackHost&, double, const MgfTables&,
+                                          const std::vector<RTask>&, void*, int64_t, void*, int64_t, cudaStream_t);
 
 }  // namespace sldm

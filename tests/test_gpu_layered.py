@@ -135,3 +135,90 @@ def test_layered_fp32_and_invalid_cases(in_slab, over_pec):
     st2 = sl.Stack([(1.0, 1.0, 0.0, 0.0)], z_top=0.0, bottom=sl.BOTTOM_PEC)
     with pytest.raises(sl.SldmError):
         sl.Operator(mm, st2, [(4.0, 1.0, 0.0, 0)], 300e6)
+
+
+# ---------------------------------------------------------------- objects resting on an interface
+LAM_OPT = 1e-6
+F_OPT = 299792458.0 / LAM_OPT
+GLASS = [(1.0, 1.0, 0.0, np.inf), (2.25, 1.0, 0.0, np.inf)]
+
+
+@pytest.fixture(scope="module")
+def on_glass():
+    """One cylinder (r = 120 nm, h = 300 nm, eps 6) resting on a glass half-space at 1 um."""
+    from workloads.meshes import cylinder
+    v, f = cylinder(120e-9, 300e-9)
+    return LCase(v, f, [(6.0, 1.0, 0.0)], GLASS, 0.0, "halfspace", 0, F_OPT)
+
+
+@pytest.fixture(scope="module")
+def array_on_glass():
+    """2 x 2 such cylinders at a 500 nm period: the oracle's L^A_m, L^phi_m only
+    (homogeneous fill + reflected part), to check the copied repeated blocks."""
+    from oracle import fill as OF
+    from workloads.meshes import cylinder_array
+    v, f, obj = cylinder_array(2, 2, 120e-9, 300e-9, 500e-9)
+    c = LCase.__new__(LCase)
+    c.xyz, c.tri, c.mats, c.freq, c.obj = v, f, [(6.0, 1.0, 0.0)] * 4, F_OPT, obj
+    c.layers, c.z_top, c.bottom, c.layer = GLASS, 0.0, "halfspace", 0
+    c.om = OMesh(v, f, obj)
+    c.stack = LY.Stack(GLASS, z_top=0.0)
+    w = 2 * np.pi * F_OPT
+    k0 = w / 299792458.0
+    tris = np.arange(c.om.nt)
+    LA, LP = OF.fill_L(c.om, k0, tris)
+    LAr, LPr = LY.fill_reflected(c.om, c.stack, 0, w, S.default_tables(c.om, c.stack, 0, w), tris)
+    c.LAm, c.LPm = LA + LAr, LP + LPr
+    return c
+
+
+def _gpu_case(c, prec=0):
+    import torch  # noqa: F401
+    from paper_2106_06184_gb300 import sldm
+    m = sldm.Mesh(c.xyz, c.tri, getattr(c, "obj", None))
+    st = sldm.Stack([(l[0], l[1], l[2], l[3] if np.isfinite(l[3]) else 0.0) for l in c.layers], z_top=c.z_top,
+                    bottom=sldm.BOTTOM_HALFSPACE)
+    op = sldm.Operator(m, st, [tuple(mm[:3]) + (c.layer,) for mm in c.mats], c.freq, precision=prec)
+    return sldm, op
+
+
+def test_resting_on_glass_blocks_and_oblique_solution(on_glass):
+    """A cylinder resting on glass (images of pairs touching through the interface
+    integrated apart, static z-rho images, Sommerfeld tail floor): L^A_m, L^phi_m
+    against the oracle at the table bound, then 35-degree TM incidence solved."""
+    c = on_glass
+    sl, op = _gpu_case(c)
+    A = c.A
+    for name, got, ref in (("LAm", op.block(sl.BLOCK_LAM), A.LAm), ("LPm", op.block(sl.BLOCK_LPM), A.LPm)):
+        assert relmax(got, ref) < 3e-9 and rel(got, ref) < 3e-9, (name, relmax(got, ref))
+    t = np.radians(35.0)
+    khat = np.array([np.sin(t), 0.0, -np.cos(t)])
+    pol = np.array([np.cos(t), 0.0, np.sin(t)])
+    b = np.zeros(op.N, complex)
+    op.rhs_planewave(khat, pol, b)
+    ref_b = S.rhs(A, khat=khat, pol=pol)
+    assert rel(b, ref_b) < 1e-12
+    x = np.zeros(op.N, complex)
+    op.solve(b, x, tol=1e-11)
+    assert rel(x, S.solve(A, ref_b)) < 1e-8
+
+
+def test_resting_array_blocks(array_on_glass):
+    """2 x 2 resting cylinders: the repeated blocks (filled once per relative
+    placement, reflected part included, then copied) against the oracle."""
+    c = array_on_glass
+    sl, op = _gpu_case(c)
+    for name, got, ref in (("LAm", op.block(sl.BLOCK_LAM), c.LAm), ("LPm", op.block(sl.BLOCK_LPM), c.LPm)):
+        assert relmax(got, ref) < 3e-9 and rel(got, ref) < 3e-9, (name, relmax(got, ref))
+
+
+def test_resting_on_glass_complex64_refined(on_glass):
+    """The complex64 operator with the FP64-accurate residual (hi + lo) on the
+    resting cylinder: currents within 1e-6 of the FP64 oracle."""
+    from paper_2106_06184_gb300 import sldm
+    c = on_glass
+    sl, op = _gpu_case(c, prec=sldm.PREC_F32X2)
+    b = S.rhs(c.A, khat=[0, 0, -1.0], pol=[1.0, 0, 0])
+    x = np.zeros(op.N, complex)
+    op.solve(b.copy(), x, tol=1e-10)
+    assert rel(x, S.solve(c.A, b)) < 1e-6
