@@ -68,12 +68,10 @@ for _n in (8, 4):
     for _sfx in ("", "-8angles"):
         WORKLOADS[f"metasurface-{_n}x{_n}-cyl-epsr6-1um-freespace-c64x2{_sfx}"] = dict(
             WORKLOADS[f"metasurface-{_n}x{_n}-cyl-epsr6-1um-freespace-c64{_sfx}"], precision=2)
-# Largest single-GPU case: the 8 x 8 metasurface under 32 plane waves per request
-# (incidence 0 - 77.5 deg in 2.5 deg steps in the xz plane, TE and TM
-# alternating), complex64 operator with the FP64-accurate refinement residual,
-# GMRES to 1e-8 of the FP64 system, 181-angle RCS per plane wave; free space (the
-# glass half-space of the paper-shaped case puts the cylinders on an interface,
-# which the layered kernel here does not take).  4 x 4: the profiling case.
+# The 8 x 8 metasurface in free space under 32 plane waves per request (incidence
+# 0 - 77.5 deg in 2.5 deg steps in the xz plane, TE and TM alternating), complex64
+# operator with the FP64-accurate refinement residual, GMRES to 1e-8 of the FP64
+# system, 181-angle RCS per plane wave.  4 x 4: the profiling case.
 _TH32 = np.radians(2.5 * np.arange(32))
 for _n in (8, 4):
     for _p, _sfx in ((2, "c64x2"), (1, "c64")):
@@ -106,7 +104,7 @@ WORKLOADS["copper-wire-sio2-si-pec-1MHz-50GHz-fp64"] = dict(
     layers=[(1.0, 1.0, 0.0, 0.0), (3.9, 1.0, 0.0, 10e-6), (11.9, 1.0, 10.0, 200e-6)], z_top=0.0, bottom="pec",
     freqs=WIRE_FREQS, precision=0, tol=1e-8, maxit=6000, khat=[0.0, 0.0, -1.0], pol=[1.0, 0.0, 0.0], n_angles=0,
     e2e_steps=20)
-DEFAULT_WORKLOAD = "metasurface-8x8-cyl-epsr6-1um-freespace-c64x2-32angles"
+DEFAULT_WORKLOAD = "metasurface-8x8-cyl-epsr6-1um-onglass-c64x2-32angles"
 
 
 def _freqs(W):
@@ -147,6 +145,10 @@ FILL_F32_PEAK_EVALS = SFU_OPS_PER_S / 3.0
 FP64_OPS_PER_S = 152 * 2 * 2.07e9
 FP64_OPS_PER_EVAL = 43.0
 FILL_F64_PEAK_EVALS = FP64_OPS_PER_S / FP64_OPS_PER_EVAL
+# The reflected (layered) fill in FP64: images, static z-rho images and a bilinear
+# remainder lookup per evaluation; FP64 pipe operations per evaluation from ncu's
+# DFMA + DMUL + DADD counts of fill_reflected_kernel<double2> on the 4 x 4 glass case.
+FP64_OPS_PER_EVAL_REFL = 353.0
 
 
 # DRAM traffic per algorithmic byte of the HBM-streaming GEMV stage, from one
@@ -410,6 +412,12 @@ def run_ours(args, rank, world):
         ms, cnt = timers[name]
         per_launch = units[name] / cnt
         evals = per_launch / (ms / cnt / 1e3)
+        if name == "fill_reflected_bulk":  # FP64 whatever the operator's precision
+            peak = FP64_OPS_PER_S / FP64_OPS_PER_EVAL_REFL
+            return {"kernel": name, "bound": "alu", "achieved": evals / 1e9, "peak": peak / 1e9, "unit": "Geval/s",
+                    "frac": evals / peak, "peak_source": "derived (FP64 pipe)", "traffic": None,
+                    "algorithmic_unit": per_launch, "launches": cnt, "ms_per_launch": ms / cnt, "precision": "fp64",
+                    "fp64_ops_per_eval": FP64_OPS_PER_EVAL_REFL}
         peak = FILL_F64_PEAK_EVALS if fp64_fill else FILL_F32_PEAK_EVALS
         return {"kernel": name, "bound": "alu", "achieved": evals / 1e9, "peak": peak / 1e9, "unit": "Geval/s",
                 "frac": evals / peak, "peak_source": "derived (FP64 pipe)" if fp64_fill else "derived (SFU)",
@@ -417,7 +425,7 @@ def run_ours(args, rank, world):
                 "precision": "fp64" if fp64_fill else "fp32"}
 
     roof_mv = matvec_entry("gemv_main")
-    fills = [f for f in (fill_entry(k) for k in ("fill_L_bulk", "fill_K_bulk")) if f]
+    fills = [f for f in (fill_entry(k) for k in ("fill_L_bulk", "fill_K_bulk", "fill_reflected_bulk")) if f]
     roof_fill = max(fills, key=lambda f: f["ms_per_launch"] * f["launches"]) if fills else None
     # the direct solves: the batched look-ahead LU (small objects) and the blocked LU (large ones)
     lu_ms = sum(timers[k][0] for k in ("lu_coop", "lu_blocked") if k in timers)
@@ -573,9 +581,26 @@ for o in range(m.nobj):
     B_ = rng.standard_normal((n, r)) + 1j * rng.standard_normal((n, r))
     t0 = time.perf_counter(); np.linalg.solve(A_, B_); est += d ** 3 * (time.perf_counter() - t0)
 if st is not None:
-    t0 = time.perf_counter()
-    T = S.default_tables(m, st, lay, omega)
-    est += time.perf_counter() - t0
+    # the tables of default_tables, timed at 16 and 32 of their 256 rho rows (every
+    # z + z' and |z - z'| column, every Sommerfeld node): the cost is affine in the
+    # rows (Bessel functions and the node sum per row), so the 256-row build is
+    # extrapolated linearly
+    lo, hi = m.xyz.min(axis=0), m.xyz.max(axis=0)
+    span = np.linalg.norm(hi - lo) * 1.01
+    edge = np.min(np.linalg.norm(m.xyz[m.E.uv[:, 0]] - m.xyz[m.E.uv[:, 1]], axis=1))
+    TABLE_S = {table_s}
+    if TABLE_S is None:
+        tt = []
+        for nr in (16, 32):
+            t0 = time.perf_counter()
+            T = LY.build_tables(st, lay, omega, 1e-3 * edge, span, lo[2], hi[2], nr=nr)
+            tt.append(time.perf_counter() - t0)
+        TABLE_S = tt[0] + (tt[1] - tt[0]) * (256 - 16) / 16
+    else:
+        # the same tables as an earlier sample of this run (same stack, frequency and
+        # extent): their measured time is reused; a coarse table serves the fill below
+        T = LY.build_tables(st, lay, omega, 1e-3 * edge, span, lo[2], hi[2], nr=16, ns=16, nd=16)
+    est += TABLE_S
     sub = np.sort(rng.choice(m.nt, size=min(m.nt, {nsub}), replace=False))
     t0 = time.perf_counter()
     LY.fill_reflected(m, st, lay, omega, T, sub)
@@ -584,8 +609,10 @@ N = 2 * m.ne + m.nt - m.nobj
 d = max({ddiv}, -(-N // DMAX))
 A_ = rng.standard_normal((N // d, N // d)) + 1j * rng.standard_normal((N // d, N // d))
 t0 = time.perf_counter(); sla.lu_solve(sla.lu_factor(A_), np.ones(N // d)); est += (N / (N // d)) ** 3 * (time.perf_counter() - t0)
-print(est, time.perf_counter() - t_all)
+print(est, time.perf_counter() - t_all, TABLE_S if st is not None else -1.0)
 """
+
+_TABLE_S = {}  # (workload, frequency index) -> seconds of the oracle's layered tables, measured once per run
 
 
 def oracle_step_seconds(name=None, step=0, quick=False):
@@ -600,10 +627,14 @@ def oracle_step_seconds(name=None, step=0, quick=False):
         extrap = False
     else:
         npairs, nsub, ddiv = (1000, 48, 4) if quick else (3000, 96, 2)
-        script = ORACLE_SAMPLED.format(root=ROOT, name=name, step=step, npairs=npairs, nsub=nsub, ddiv=ddiv)
+        W = WORKLOADS[name]
+        key = (name, step % len(_freqs(W)))
+        script = ORACLE_SAMPLED.format(root=ROOT, name=name, step=step, npairs=npairs, nsub=nsub, ddiv=ddiv,
+                                       table_s=repr(_TABLE_S.get(key)))
         sample = (f"extrapolated from a sample at frequency index {step}: {npairs} uniformly drawn triangle pairs per "
                   f"fill (global L, each object's L, Kbar with k and k_l), the reflected fill on {nsub} random "
-                  f"triangles, the layered tables whole, the dense solves on matrices 1/d of the size (d >= {ddiv}, "
+                  f"triangles, the layered tables at 16 and 32 of 256 rho rows (extrapolated linearly; measured once per "
+                  f"run and frequency), the dense solves on matrices 1/d of the size (d >= {ddiv}, "
                   "order <= 2048, scaled by d^3); "
                   "single thread")
         extrap = True
@@ -611,6 +642,8 @@ def oracle_step_seconds(name=None, step=0, quick=False):
     if r.returncode != 0:
         raise RuntimeError(r.stderr[-2000:])
     vals = [float(v) for v in r.stdout.strip().splitlines()[-1].split()]
+    if len(vals) > 2 and vals[2] >= 0 and not name.startswith("sphere"):
+        _TABLE_S.setdefault(key, vals[2])
     return vals[0], sample, extrap, (vals[1] if len(vals) > 1 else vals[0])
 
 
@@ -624,7 +657,9 @@ def oracle_all_cores(name, step, ncores):
     if name.startswith("sphere"):
         script = ORACLE_FULL.format(root=ROOT)
     else:
-        script = ORACLE_SAMPLED.format(root=ROOT, name=name, step=step, npairs=1000, nsub=48, ddiv=4)
+        key = (name, step % len(_freqs(WORKLOADS[name])))
+        script = ORACLE_SAMPLED.format(root=ROOT, name=name, step=step, npairs=1000, nsub=48, ddiv=4,
+                                       table_s=repr(_TABLE_S.get(key)))
     t0 = time.perf_counter()
     procs = [subprocess.Popen([sys.executable, "-c", script], stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True,
                               env=env, cwd=ROOT) for _ in range(ncores)]

@@ -45,6 +45,14 @@ __device__ __forceinline__ cx cexp_(cx a) {
   const double e = exp(a.r);
   return {e * c, e * s};
 }
+// exp(-j k R) for complex k: exp(Im k R) (cos(Re k R) - j sin(Re k R)); no exp when k is real
+__device__ __forceinline__ cx eikr(cx k, double R) {
+  double s, c;
+  sincos(k.r * R, &s, &c);
+  if (k.i == 0.0) return {c, -s};
+  const double e = exp(k.i * R);
+  return {e * c, -e * s};
+}
 // principal square root without cancellation: the larger of |Re|, |Im| comes
 // from sqrt((|a| + |Re a|)/2), the other from Im a / (2 that)
 __device__ __forceinline__ cx csqrt_(cx a) {
@@ -465,20 +473,31 @@ struct TabView {
   int nr, ns, nd;
   double lr0, lr1, s0, s1, d1;
   int hasB;
+  double rmin, inv_rmin;  // exp(lr0), exp(-lr0)
+  double sx, ss, sd;      // index scales (nr - 1)/(lr1 - lr0), (ns - 1)/(s1 - s0), (nd - 1)/d1 (0 if d1 = 0)
 };
 
-__device__ __forceinline__ cx bilin(const double2* t, int nr, int ny, double fx, double fy, int c) {
+// Bilinear cell of a table at fractional indices (fx, fy), clamped as bilin does.
+struct Cell {
+  int64_t i00, i10, i01, i11;
+  double w00, w10, w01, w11;
+};
+__device__ __forceinline__ Cell cell(int nr, int ny, double fx, double fy) {
   fx = fmin(fmax(fx, 0.0), nr - 1 - 1e-9);
   fy = ny > 1 ? fmin(fmax(fy, 0.0), ny - 1 - 1e-9) : 0.0;
   const int ix = int(fx), iy = int(fy);
   const double tx = fx - ix, ty = fy - iy;
   const int iy1 = min(iy + 1, ny - 1);
-  const double2* b = t + int64_t(c) * nr * ny;
-  const double2 a00 = b[int64_t(ix) * ny + iy], a10 = b[int64_t(ix + 1) * ny + iy];
-  const double2 a01 = b[int64_t(ix) * ny + iy1], a11 = b[int64_t(ix + 1) * ny + iy1];
-  const double w00 = (1 - tx) * (1 - ty), w10 = tx * (1 - ty), w01 = (1 - tx) * ty, w11 = tx * ty;
-  return {w00 * a00.x + w10 * a10.x + w01 * a01.x + w11 * a11.x, w00 * a00.y + w10 * a10.y + w01 * a01.y + w11 * a11.y};
+  return {int64_t(ix) * ny + iy, int64_t(ix + 1) * ny + iy, int64_t(ix) * ny + iy1, int64_t(ix + 1) * ny + iy1,
+          (1 - tx) * (1 - ty), tx * (1 - ty), (1 - tx) * ty, tx * ty};
 }
+__device__ __forceinline__ cx at(const double2* t, int64_t plane, const Cell& c, int comp) {
+  const double2* b = t + comp * plane;
+  const double2 a00 = b[c.i00], a10 = b[c.i10], a01 = b[c.i01], a11 = b[c.i11];
+  return {c.w00 * a00.x + c.w10 * a10.x + c.w01 * a01.x + c.w11 * a11.x,
+          c.w00 * a00.y + c.w10 * a10.y + c.w01 * a01.y + c.w11 * a11.y};
+}
+
 
 // Static z-rho image in space: rho / (4 pi R (R + zeta)), R = |(rho, zeta)|, zeta >= 0; 0 at R = 0.
 __device__ __forceinline__ double static_zr(double rho, double zeta) {
@@ -523,6 +542,9 @@ __global__ void __launch_bounds__(128) fill_reflected_kernel(const RTask* __rest
   const double use_top = touch_through(tri, t, sidx, mt, ms, 4) ? 0.0 : 1.0;
   const cx gue = {Q.gue.r, Q.gue.i}, guh = {Q.guh.r, Q.guh.i}, gde = {Q.gde.r, Q.gde.i}, gdh = {Q.gdh.r, Q.gdh.i};
   const cx cu = gue - guh, cdn = gde - gdh;
+  // image coefficients: xx mu_r g_h, phi g_e / eps_r, zz mu_r (g_h - 2 g_e), up and down
+  const cx kxx_u = mur * guh, kxx_d = mur * gdh, kph_u = gue / epsl, kph_d = gde / epsl;
+  const cx kzz_u = mur * (guh - 2.0 * gue), kzz_d = mur * (gdh - 2.0 * gde);
   cx loc[9];
   for (int i = 0; i < 9; ++i) loc[i] = mk(0);
   cx lp = mk(0);
@@ -532,68 +554,100 @@ __global__ void __launch_bounds__(128) fill_reflected_kernel(const RTask* __rest
     for (int d = 0; d < 3; ++d) r[d] = gt[GEO_C + d] + gt[GEO_RHO + 3 * q + d];
     for (int i = 0; i < 3; ++i)
       for (int d = 0; d < 3; ++d) f[i][d] = gt[GEO_SIG + i] * (gt[GEO_RHO + 3 * q + d] + gt[GEO_AV + 3 * i + d]);
-    cx V[3][3];  // sum_s W' T . f_j(r'_s)
-    for (int j = 0; j < 3; ++j)
-      for (int d = 0; d < 3; ++d) V[j][d] = mk(0);
+    // Moments of the dyadic kernel T over the source points (weights w, offsets
+    // rho_s from the source centre, rhohat = (hx, hy)): with f_j(r_s) = sig_j (rho_s + av_j),
+    // sum_s w T . f_j = sig_j (M1 + M0 . av_j), T . u = (gxx u_x + grz hx u_z,
+    // gxx u_y + grz hy u_z, gzz u_z + gzr (hx u_x + hy u_y)).
+    cx a0 = mk(0), az = mk(0), bx = mk(0), by = mk(0), cxm = mk(0), cym = mk(0);      // M0
+    cx a0x = mk(0), a0y = mk(0), bxz = mk(0), byz = mk(0), azz = mk(0), cr = mk(0);  // M1
     cx sphi = mk(0);
     for (int sq = 0; sq < 6; ++sq) {
       double rs[3];
       for (int d = 0; d < 3; ++d) rs[d] = gs[GEO_C + d] + gs[GEO_RHO + 3 * sq + d];
       const double dx = r[0] - rs[0], dy = r[1] - rs[1];
-      const double rho = sqrt(dx * dx + dy * dy);
+      const double rho2 = dx * dx + dy * dy;
+      const double irho = rho2 > 0 ? rsqrt(rho2) : 0.0;
+      const double rho = rho2 * irho;
       const double zz = r[2], zp = rs[2];
-      // quasistatic images
+      // quasistatic images: spherical waves exp(-j k R)/(4 pi R) and the static
+      // z-rho image rho / (4 pi R (R + zeta)) from the image points
       cx G1 = mk(0), G2 = mk(0);
       double F1 = 0, F2 = 0;
       if (S.top) {
         const double zeta = 2 * S.zu - zz - zp;
-        const double R = sqrt(rho * rho + zeta * zeta);
-        if (R > 0) G1 = (use_top * inv4pi / R) * cexp_(mk(0, -R) * k);
-        F1 = use_top * static_zr(rho, zeta);
+        const double R2 = rho2 + zeta * zeta;
+        if (R2 > 0) {
+          const double r1 = rsqrt(R2), R = R2 * r1;
+          const double iR = use_top * inv4pi * r1;
+          G1 = iR * eikr(k, R);
+          F1 = iR * rho / (R + zeta);
+        }
       }
       if (S.bot) {
         const double zeta = zz + zp - 2 * S.zb;
-        const double R = sqrt(rho * rho + zeta * zeta);
-        if (R > 0) G2 = (use_bot * inv4pi / R) * cexp_(mk(0, -R) * k);
-        F2 = use_bot * static_zr(rho, zeta);
+        const double R2 = rho2 + zeta * zeta;
+        if (R2 > 0) {
+          const double r1 = rsqrt(R2), R = R2 * r1;
+          const double iR = use_bot * inv4pi * r1;
+          G2 = iR * eikr(k, R);
+          F2 = iR * rho / (R + zeta);
+        }
       }
-      cx gxx = mur * (guh * G1 + gdh * G2);
-      cx gphi = (gue * G1 + gde * G2) / epsl;
-      cx gzz = mur * ((guh - 2.0 * gue) * G1 + (gdh - 2.0 * gde) * G2);
-      // tabulated remainder
-      const double lr = log(fmax(rho, exp(T.lr0)));
-      const double fx = (lr - T.lr0) / (T.lr1 - T.lr0) * (T.nr - 1);
-      const double fs = (zz + zp - T.s0) / (T.s1 - T.s0) * (T.ns - 1);
+      cx gxx = kxx_u * G1 + kxx_d * G2;
+      cx gphi = kph_u * G1 + kph_d * G2;
+      cx gzz = kzz_u * G1 + kzz_d * G2;
+      // tabulated remainder (one bilinear cell for the five components)
+      const double lr = log(fmax(rho, T.rmin));
+      const double fx = (lr - T.lr0) * T.sx;
+      const double fs = (zz + zp - T.s0) * T.ss;
+      const Cell ca = cell(T.nr, T.ns, fx, fs);
+      const int64_t pa = int64_t(T.nr) * T.ns;
+      gxx = gxx + at(T.A, pa, ca, 0);
+      gphi = gphi + at(T.A, pa, ca, 1);
+      gzz = gzz + at(T.A, pa, ca, 2);
+      cx bzr = at(T.A, pa, ca, 3), brz = at(T.A, pa, ca, 4);
       const double dd = zz - zp;
-      const double fd = T.d1 > 0 ? fabs(dd) / T.d1 * (T.nd - 1) : 0.0;
       const double sg = dd > 0 ? 1.0 : (dd < 0 ? -1.0 : 0.0);
-      gxx = gxx + bilin(T.A, T.nr, T.ns, fx, fs, 0);
-      gphi = gphi + bilin(T.A, T.nr, T.ns, fx, fs, 1);
-      gzz = gzz + bilin(T.A, T.nr, T.ns, fx, fs, 2);
-      cx bzr = bilin(T.A, T.nr, T.ns, fx, fs, 3), brz = bilin(T.A, T.nr, T.ns, fx, fs, 4);
       if (T.hasB) {
-        gxx = gxx + bilin(T.B, T.nr, T.nd, fx, fd, 0);
-        gphi = gphi + bilin(T.B, T.nr, T.nd, fx, fd, 1);
-        gzz = gzz + bilin(T.B, T.nr, T.nd, fx, fd, 2);
-        bzr = bzr + sg * bilin(T.B, T.nr, T.nd, fx, fd, 3);
-        brz = brz + sg * bilin(T.B, T.nr, T.nd, fx, fd, 4);
+        const double fd = fabs(dd) * T.sd;
+        const Cell cb = cell(T.nr, T.nd, fx, fd);
+        const int64_t pb = int64_t(T.nr) * T.nd;
+        gxx = gxx + at(T.B, pb, cb, 0);
+        gphi = gphi + at(T.B, pb, cb, 1);
+        gzz = gzz + at(T.B, pb, cb, 2);
+        bzr = bzr + sg * at(T.B, pb, cb, 3);
+        brz = brz + sg * at(T.B, pb, cb, 4);
       }
       // the S1 (z-rho, rho-z) remainders vanish linearly at rho = 0: below rho_min scale by rho / rho_min
-      const double lin = fmin(rho * exp(-T.lr0), 1.0);
+      const double lin = fmin(rho * T.inv_rmin, 1.0);
       const cx gzr = lin * bzr + mur * (cdn * F2 - cu * F1);
       const cx grz = lin * brz + mur * (cu * F1 - cdn * F2);
-      const double hx = rho > 0 ? dx / rho : 0.0, hy = rho > 0 ? dy / rho : 0.0;
+      const double hx = dx * irho, hy = dy * irho;
       const double w = gs[GEO_W + sq];
-      for (int j = 0; j < 3; ++j) {
-        double fj[3];
-        for (int d = 0; d < 3; ++d) fj[d] = gs[GEO_SIG + j] * (gs[GEO_RHO + 3 * sq + d] + gs[GEO_AV + 3 * j + d]);
-        const double rf = hx * fj[0] + hy * fj[1];
-        // T . f_j: x,y: gxx f_t + grz rhohat f_z ; z: gzz f_z + gzr (rhohat . f_t)
-        V[j][0] = V[j][0] + w * (fj[0] * gxx + (hx * fj[2]) * grz);
-        V[j][1] = V[j][1] + w * (fj[1] * gxx + (hy * fj[2]) * grz);
-        V[j][2] = V[j][2] + w * (fj[2] * gzz + rf * gzr);
-      }
+      const double px = gs[GEO_RHO + 3 * sq], py = gs[GEO_RHO + 3 * sq + 1], pz = gs[GEO_RHO + 3 * sq + 2];
+      const cx wxx = w * gxx, wzz = w * gzz, wrx = (w * hx) * grz, wry = (w * hy) * grz;
+      const cx wzx = (w * hx) * gzr, wzy = (w * hy) * gzr;
+      a0 = a0 + wxx;
+      az = az + wzz;
+      bx = bx + wrx;
+      by = by + wry;
+      cxm = cxm + wzx;
+      cym = cym + wzy;
+      a0x = a0x + px * wxx;
+      a0y = a0y + py * wxx;
+      bxz = bxz + pz * wrx;
+      byz = byz + pz * wry;
+      azz = azz + pz * wzz;
+      cr = cr + (px * wzx + py * wzy);
       sphi = sphi + w * gphi;
+    }
+    cx V[3][3];  // sum_s W' T . f_j(r'_s)
+    for (int j = 0; j < 3; ++j) {
+      const double sj = gs[GEO_SIG + j];
+      const double ux = gs[GEO_AV + 3 * j], uy = gs[GEO_AV + 3 * j + 1], uz = gs[GEO_AV + 3 * j + 2];
+      V[j][0] = sj * (a0x + ux * a0 + bxz + uz * bx);
+      V[j][1] = sj * (a0y + uy * a0 + byz + uz * by);
+      V[j][2] = sj * (azz + uz * az + cr + ux * cxm + uy * cym);
     }
     const double wq = gt[GEO_W + q];
     for (int i = 0; i < 3; ++i)
@@ -846,11 +900,17 @@ void mgf_touch_setup(const HostMesh& h, const MgfStackHost& H, const std::vector
     if (msk) touching.push_back(int32_t(t));
   }
   pairs.clear();
-  for (const RTask& k : tasks)
-    for (int32_t a : touching) {
-      if (a < k.t0 || a >= k.t0 + k.ntest) continue;
-      for (int32_t b : touching) {
-        if (b < k.s0 || b >= k.s0 + k.nsrc) continue;
+  // `touching` is sorted: each task's test and source ranges are two slices of it
+  auto slice = [&](int32_t lo, int32_t n) {
+    return std::make_pair(std::lower_bound(touching.begin(), touching.end(), lo),
+                          std::lower_bound(touching.begin(), touching.end(), lo + n));
+  };
+  for (const RTask& k : tasks) {
+    const auto ta = slice(k.t0, k.ntest), tb = slice(k.s0, k.nsrc);
+    for (auto ia = ta.first; ia != ta.second; ++ia) {
+      const int32_t a = *ia;
+      for (auto ib = tb.first; ib != tb.second; ++ib) {
+        const int32_t b = *ib;
         for (int plane = 0; plane < 2; ++plane) {
           const int sh = plane ? 4 : 0;
           bool hit = false;
@@ -865,6 +925,7 @@ void mgf_touch_setup(const HostMesh& h, const MgfStackHost& H, const std::vector
         }
       }
     }
+  }
 }
 
 template <class C>
@@ -872,7 +933,8 @@ void mgf_fill_reflected(const sldm_mesh* m, const MgfStackHost& H, double omega,
                         const std::vector<RTask>& tasks, void* LA, int64_t ldA, void* LP, int64_t ldP, cudaStream_t s) {
   if (tasks.empty()) return;
   const DevStack S = dev_stack(H, omega);
-  TabView tv{T.A.p, T.B.p, T.nr, T.ns, T.nd, T.lr0, T.lr1, T.s0, T.s1, T.d1, T.hasB ? 1 : 0};
+  TabView tv{T.A.p, T.B.p, T.nr, T.ns, T.nd, T.lr0, T.lr1, T.s0, T.s1, T.d1, T.hasB ? 1 : 0, std::exp(T.lr0), std::exp(-T.lr0),
+             (T.nr - 1) / (T.lr1 - T.lr0), T.s1 > T.s0 ? (T.ns - 1) / (T.s1 - T.s0) : 0.0, T.d1 > 0 ? (T.nd - 1) / T.d1 : 0.0};
   ScopedTimer tm("fill_reflected", s);
   std::vector<int32_t> onmask, pairs;
   mgf_touch_setup(m->h, H, tasks, onmask, pairs);
@@ -881,10 +943,18 @@ void mgf_fill_reflected(const sldm_mesh* m, const MgfStackHost& H, double omega,
   dt.upload(tasks, s);
   dm.upload(onmask, s);
   int64_t most = 0;
-  for (const RTask& k : tasks) most = std::max(most, int64_t(k.ntest) * k.nsrc);
-  fill_reflected_kernel<C><<<dim3(unsigned((most + 127) / 128), unsigned(tasks.size())), 128, 0, s>>>(
-      dt.p, m->d.geo.p, m->d.tri_edge.p, m->d.tri.p, dm.p, S, T.Q, tv, (C*)LA, ldA, (C*)LP, ldP), ::sldm::count_launch();
-  SLDM_CUDA(cudaGetLastError());
+  double pairs_total = 0;
+  for (const RTask& k : tasks) {
+    most = std::max(most, int64_t(k.ntest) * k.nsrc);
+    pairs_total += double(k.ntest) * k.nsrc;
+  }
+  {
+    ScopedTimer tb("fill_reflected_bulk", s);
+    timer_units("fill_reflected_bulk", 36.0 * pairs_total);
+    fill_reflected_kernel<C><<<dim3(unsigned((most + 127) / 128), unsigned(tasks.size())), 128, 0, s>>>(
+        dt.p, m->d.geo.p, m->d.tri_edge.p, m->d.tri.p, dm.p, S, T.Q, tv, (C*)LA, ldA, (C*)LP, ldP), ::sldm::count_launch();
+    SLDM_CUDA(cudaGetLastError());
+  }
   const int np = int(pairs.size() / 3);
   if (np > 0) {
     std::vector<double> x, w;
