@@ -104,6 +104,23 @@ WORKLOADS["copper-wire-sio2-si-pec-1MHz-50GHz-fp64"] = dict(
     layers=[(1.0, 1.0, 0.0, 0.0), (3.9, 1.0, 0.0, 10e-6), (11.9, 1.0, 10.0, 200e-6)], z_top=0.0, bottom="pec",
     freqs=WIRE_FREQS, precision=0, tol=1e-8, maxit=6000, khat=[0.0, 0.0, -1.0], pol=[1.0, 0.0, 0.0], n_angles=0,
     e2e_steps=20)
+# Serving (BASELINE's config 4, scaled to sizes the direct Y solve serves): a seeded
+# catalogue of 16 models (4 spheres and 4 ellipsoids, icosphere sub 1 or 2, semi-axes
+# U[0.05, 0.2] m, eps_r U[2, 12], loss tangent U[0, 0.02]; each in free space and
+# 1.2 semi-axes above a 3-layer ground: air / 5 cm slab eps_r 4 / half-space eps_r 10,
+# sigma 0.01 S/m) x 16 frequency bins (k0 a_max log-uniform 0.1 - 2), i.e. 256 cache
+# keys; requests arrive as a Poisson stream of 200 per second (200 per step), each
+# drawing its key from a Zipf(1.1) popularity over the keys (so keys repeat), 1 - 16
+# plane waves (incidence U[0, 70] deg, azimuth uniform, TE or TM), tolerance 1e-8.
+# Served by 2 workers, lockstep batches of up to 32 right-hand sides, complex64
+# operators with the FP64-accurate residual, a 150 GB operator cache; the plain FP64
+# single-solve path (one right-hand side per solve, one worker) replays one step's
+# trace for comparison.
+WORKLOADS["serving-catalogue-poisson200-c64x2"] = dict(
+    kind="serving", n_models=16, n_freqs=16, rate=200.0, requests=200, zipf=1.1, nrhs_max=16, tol=1e-8,
+    workers=2, max_batch=32, precision=2, budget=150 << 30, khat=[0.0, 0.0, -1.0], pol=[1.0, 0.0, 0.0],
+    mesh=lambda: icosphere(1, 0.1), obj=None, mats=[(4.0, 1.0, 0.0)], bg=(1.0, 1.0, 0.0, 0.0), freq=300e6,
+    n_angles=0)
 DEFAULT_WORKLOAD = "metasurface-8x8-cyl-epsr6-1um-onglass-c64x2-32angles"
 
 
@@ -284,6 +301,159 @@ def max_over_ranks(value, world, device):
     t = torch.tensor([float(value)], dtype=torch.float64, device=device)
     torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
     return float(t.item())
+
+
+# ----------------------------------------------------------------------------- serving
+def serving_catalogue(W, seed=2106_06184 + 4):
+    """The serving workload's models [(xyz, tri, mats, layered, a_max)] and, per model,
+    its frequency bins."""
+    from workloads.meshes import ellipsoid
+    rng = np.random.default_rng(seed)
+    models = []
+    for i in range(W["n_models"] // 2):
+        sub = int(rng.integers(1, 3))
+        ax = rng.uniform(0.05, 0.2, 3) if i % 2 else np.full(3, rng.uniform(0.05, 0.2))
+        eps = float(rng.uniform(2, 12))
+        tand = float(rng.uniform(0, 0.02))
+        a = float(ax.max())
+        xyz, tri = ellipsoid(sub, tuple(ax), (0.0, 0.0, 1.2 * a))
+        for layered in (False, True):
+            models.append(dict(xyz=xyz, tri=tri, eps=eps, tand=tand, layered=layered, a=a))
+    c0 = 299792458.0
+    for m in models:
+        ka = np.exp(np.linspace(np.log(0.1), np.log(2.0), W["n_freqs"]))
+        m["freqs"] = [float(k * c0 / (2 * np.pi * m["a"])) for k in ka]
+        # conductivity for the loss tangent at the middle of the band
+        fm = m["freqs"][len(m["freqs"]) // 2]
+        m["sigma"] = m["tand"] * 2 * np.pi * fm * 8.8541878128e-12 * m["eps"]
+    return models
+
+
+def serving_trace(W, step, nkeys):
+    """Seeded request trace of one step: [(arrival_s, key, khat (n, 3), pol (n, 3))]."""
+    rng = np.random.default_rng(2106_06184 + 1000 + step)
+    perm = np.random.default_rng(2106_06184 + 999).permutation(nkeys)
+    p = 1.0 / np.arange(1, nkeys + 1) ** W["zipf"]
+    p /= p.sum()
+    t = np.cumsum(rng.exponential(1.0 / W["rate"], W["requests"]))
+    out = []
+    for i in range(W["requests"]):
+        key = int(perm[rng.choice(nkeys, p=p)])
+        n = int(rng.integers(1, W["nrhs_max"] + 1))
+        th = np.radians(rng.uniform(0, 70, n))
+        ph = rng.uniform(-np.pi, np.pi, n)
+        khat = np.stack([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), -np.cos(th)], axis=1)
+        e_te = np.stack([-np.sin(ph), np.cos(ph), np.zeros(n)], axis=1)
+        pol = np.where(rng.random((n, 1)) < 0.5, e_te, np.cross(e_te, khat))
+        out.append((float(t[i] - t[0]), key, khat, pol))
+    return out
+
+
+def run_serving(args, rank, world):
+    """Replays seeded Poisson request traces against the server in real time (a
+    submitting thread sleeps until each arrival); a step is one trace.  value =
+    right-hand sides solved per second from the first arrival to the last result;
+    latency = submit -> result per request."""
+    import threading
+    import torch
+
+    from paper_2106_06184_gb300 import sldm
+
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    W = WORKLOADS[args.workload]
+    cat = serving_catalogue(W)
+    free = sldm.Stack([(1.0, 1.0, 0.0, 0.0)])
+    ground = sldm.Stack([(1.0, 1.0, 0.0, 0.0), (4.0, 1.0, 0.0, 0.05), (10.0, 1.0, 0.01, 0.0)], z_top=0.0)
+    meshes = [sldm.Mesh(m["xyz"], m["tri"]) for m in cat]
+    keys = [(mi, f) for mi, m in enumerate(cat) for f in m["freqs"]]
+
+    def make_server(workers, max_batch, precision):
+        srv = sldm.Server(workers=workers, max_batch=max_batch, precision=precision, budget_bytes=W["budget"])
+        ids = [srv.add_model(meshes[i], ground if m["layered"] else free,
+                             [(m["eps"], 1.0, m["sigma"], 0)]) for i, m in enumerate(cat)]
+        return srv, ids
+
+    def replay(srv, ids, step):
+        trace = serving_trace(W, step, len(keys))
+        xs = [np.zeros((len(kh), meshes[keys[k][0]].n_unknowns), complex) for _, k, kh, _ in trace]
+        tickets = [None] * len(trace)
+
+        def submit():
+            t0 = time.perf_counter()
+            for i, (ta, k, kh, po) in enumerate(trace):
+                d = ta - (time.perf_counter() - t0)
+                if d > 0:
+                    time.sleep(d)
+                mi, f = keys[k]
+                tickets[i] = srv.submit(ids[mi], f, kh, po, xs[i], tol=W["tol"])
+
+        t0 = time.perf_counter()
+        th = threading.Thread(target=submit)
+        th.start()
+        th.join()
+        res = [srv.wait(t, timeout=3600) for t in tickets]
+        wall = time.perf_counter() - t0
+        nrhs = sum(len(kh) for _, _, kh, _ in trace)
+        lat = np.array([r["t_done"] - r["t_submit"] for r in res])
+        bad = sum(r["code"] != sldm.OK for r in res)
+        h2d = sum(kh.nbytes * 2 for _, _, kh, _ in trace)
+        d2h = sum(x.nbytes for x in xs)
+        return dict(wall=wall, nrhs=nrhs, lat=lat, bad=bad, hits=sum(r["cache_hit"] for r in res),
+                    relres=max(r["relres"] for r in res), h2d=h2d, d2h=d2h, xs=xs)
+
+    srv, ids = make_server(W["workers"], W["max_batch"], W["precision"])
+    for i in range(args.warmup):
+        replay(srv, ids, i)
+    clocks = ClockSampler(dev)
+    clocks.start()
+    sldm.timers_reset()
+    sldm.timers_enable(True)
+    launches0 = sldm.launch_count()
+    runs = [replay(srv, ids, args.warmup + i) for i in range(args.steps)]
+    launches = sldm.launch_count() - launches0
+    sldm.timers_enable(False)
+    timers = sldm.timers_read()
+    clk = clocks.stop()
+    st = srv.stats()
+    srv.close()
+    wall = sum(r["wall"] for r in runs)
+    nrhs = sum(r["nrhs"] for r in runs)
+    lat = np.concatenate([r["lat"] for r in runs])
+    value = nrhs / wall
+    # the plain FP64 single-solve path on the first timed step's trace (cold cache, then warm)
+    base, bids = make_server(1, 1, 0)
+    replay(base, bids, args.warmup)
+    b = replay(base, bids, args.warmup)
+    base.close()
+    # the two paths' currents on that trace agree to the solve tolerance times the conditioning
+    agree = max(np.linalg.norm(x - y) / max(np.linalg.norm(y), 1e-300) for x, y in zip(runs[0]["xs"], b["xs"]))
+    kernel_ms = {k: round(v[0] / args.steps, 4) for k, v in sorted(timers.items(), key=lambda kv: -kv[1][0])}
+    out = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": wall / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "c64+c64 (FP64-accurate residual)", "data": "synthetic",
+        "config": {"workload": args.workload, "requests_per_step": W["requests"], "arrival_rate_per_s": W["rate"],
+                   "keys": len(keys), "workers": W["workers"], "max_batch": W["max_batch"],
+                   "budget_bytes": W["budget"], "l2": "the trace's operators exceed L2 in aggregate; no flush"},
+        "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3), "p99": float(np.percentile(lat, 99) * 1e3),
+                       "max": float(lat.max() * 1e3)},
+        "server": {k: st[k] for k in ("requests", "rhs", "batches", "hits", "misses", "evictions", "rejected",
+                                      "cached_ops", "cached_bytes")},
+        "failed_requests": int(sum(r["bad"] for r in runs)),
+        "relres_max": float(max(r["relres"] for r in runs)),
+        "fp64_single_baseline": {"value": b["nrhs"] / b["wall"], "unit": "solves/s",
+                                 "latency_ms": {"p50": float(np.percentile(b["lat"], 50) * 1e3),
+                                                "p99": float(np.percentile(b["lat"], 99) * 1e3)},
+                                 "failed_requests": int(b["bad"]), "workers": 1, "max_batch": 1, "precision": "f64",
+                                 "trace": "the first timed step's, warm cache"},
+        "served_vs_fp64_single_max_rel_diff": float(agree),
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": int(runs[0]["h2d"]),
+                "d2h_bytes_per_step": int(runs[0]["d2h"]),
+                "note": "requests carry host arrays (plane waves in, currents out): the served value is end to end"},
+        "gpu_launches": int(launches), "clocks": clk, "kernel_ms_per_step": kernel_ms,
+    }
+    return out
 
 
 # ----------------------------------------------------------------------------- our arm
@@ -682,9 +852,75 @@ def cpu_model():
     return platform.processor() or platform.machine()
 
 
+ORACLE_SERVING = r"""
+import sys, time, numpy as np
+sys.path.insert(0, {root!r})
+import scipy.linalg as sla
+import bench
+from oracle.topology import Mesh
+from oracle import system as S, layered as LY
+W = bench.WORKLOADS[{name!r}]
+cat = bench.serving_catalogue(W)
+keys = [(mi, f) for mi, m in enumerate(cat) for f in m["freqs"]]
+ground = LY.Stack([(1.0, 1.0, 0.0, np.inf), (4.0, 1.0, 0.0, 0.05), (10.0, 1.0, 0.01, np.inf)], z_top=0.0)
+trace = bench.serving_trace(W, {step}, len(keys))
+t_all = time.perf_counter()
+nrhs = 0
+for ta, k, kh, po in trace:
+    mi, f = keys[k]
+    m = cat[mi]
+    mesh = Mesh(m["xyz"], m["tri"])
+    mat = S.Material(m["eps"], 1.0, m["sigma"])
+    if m["layered"]:
+        A = S.assemble(mesh, [mat], ground, f, layer=0)
+    else:
+        A = S.assemble(mesh, [mat], S.Material(), f)
+    lu = sla.lu_factor(A.Z)
+    for r in range(len(kh)):
+        sla.lu_solve(lu, S.rhs(A, khat=kh[r], pol=po[r]))
+    nrhs += len(kh)
+    if time.perf_counter() - t_all > {budget_s}:
+        break
+print(time.perf_counter() - t_all, nrhs)
+"""
+
+
+def oracle_serving(name, step, budget_s=20.0):
+    """The oracle on the serving trace of `step`, request by request (assembly of the
+    dense system, LU, one back substitution per plane wave; no cache), in order
+    until budget_s seconds are spent: (seconds, right-hand sides solved)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    script = ORACLE_SERVING.format(root=ROOT, name=name, step=step, budget_s=budget_s)
+    r = subprocess.run([sys.executable, "-c", script], capture_output=True, text=True, env=env, timeout=900, cwd=ROOT)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    t, n = r.stdout.strip().splitlines()[-1].split()
+    return float(t), int(n)
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return None
+    if WORKLOADS[args.workload].get("kind") == "serving":
+        spent, rhs, times = 0.0, 0, []
+        for i in range(args.warmup + args.steps):
+            t, n = oracle_serving(args.workload, i, budget_s=10.0 if i < args.warmup else 20.0)
+            if i >= args.warmup:
+                spent += t
+                rhs += n
+                times.append(t / max(n, 1))
+        v = rhs / spent
+        sample = ("the oracle on each timed step's request trace in arrival order (dense assembly, LU, one back "
+                  "substitution per plane wave; no operator cache), until 20 s were spent; single thread")
+        return {
+            "impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * spent / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+            "config": {"workload": args.workload, "parallelism": "host cores"}, "extrapolated": False,
+            "cpu_baseline": {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": sample,
+                             "sampled_s": spent, "cpu": cpu_model(), "nproc": os.cpu_count()},
+            "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }
     times, spent = [], 0.0
     sample, extrap = None, False
     for i in range(args.warmup + args.steps):
@@ -727,6 +963,8 @@ def main():
         torch.distributed.init_process_group("nccl" if args.impl == "ours" else "gloo")
     if args.impl == "reference":
         out = run_reference(args, rank, world)
+    elif WORKLOADS[args.workload].get("kind") == "serving":
+        out = run_serving(args, rank, world)
     else:
         out = run_ours(args, rank, world)
         if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -303,7 +303,9 @@ int sldm_kbar_noalloc(const sldm_mesh* mesh, int32_t obj, double k_re, double k_
  * ("fill_L_bulk", "fill_L_touch", "fill_K_bulk", "fill_K_touch", "lu_update",
  * "lu_pivot", "lu_backsub", "gemv", "apply", "gmres_iter").  Timings are
  * accumulated per name; reading them synchronises on the recorded events.
- * Not thread-safe with respect to concurrent launches on several streams. */
+ * Timed regions pair up within their calling thread, so several threads (the
+ * serving workers, each on its own stream) may be timed at once; a region's time
+ * then includes whatever else shared the device. */
 int sldm_timers_enable(int32_t on);
 int sldm_timers_reset(void);
 /* Total milliseconds and number of timed launches under `name` (0 if none). */
@@ -343,6 +345,93 @@ int sldm_device_bytes(int64_t* in_use);
  * SLDM_EINVAL for an unknown `what` or a negative count. */
 #define SLDM_INJECT_LU_STALL 1
 int sldm_test_inject(int32_t what, int32_t count);
+
+/* ---------------------------------------------------------------------------
+ * Serving (no counterpart in the paper, which solves one configuration at a
+ * time): a request loop over many configurations sharing one GPU.  A request
+ * names a registered model (mesh + background + materials), a frequency and
+ * plane waves; the server keeps assembled operators resident in a cache keyed by
+ * (model, frequency), admits new ones within a device-memory budget by evicting
+ * the least recently used operators that no worker is using, solves queued
+ * requests of one key together (their right-hand sides in one lockstep GMRES,
+ * up to max_batch), and runs `workers` threads, each with its own CUDA stream,
+ * so that requests for different operators overlap on the device.  The
+ * solution of a request does not depend on what it was batched with beyond the
+ * solve tolerance (each right-hand side of a lockstep solve stops on its own
+ * residual).
+ * ------------------------------------------------------------------------- */
+typedef struct sldm_server sldm_server;
+
+typedef struct {
+  int32_t workers;      /* worker threads (each with its own CUDA stream), >= 1 */
+  int32_t max_batch;    /* right-hand sides per lockstep solve, 1..32 */
+  int32_t precision;    /* precision of the cached operators: SLDM_PREC_* */
+  int32_t maxit;        /* GMRES iterations per right-hand side (0 = 2000) */
+  int64_t budget_bytes; /* device memory for cached operators (0 = no limit) */
+} sldm_server_opts;
+
+typedef struct {
+  int32_t model;        /* from sldm_server_add_model */
+  int32_t nrhs;         /* plane waves, >= 1 (any number: batches split them) */
+  double freq_hz;
+  const double* khat;   /* nrhs x 3, host; copied by sldm_server_submit */
+  const double* pol;    /* nrhs x 3, host; copied by sldm_server_submit */
+  double tol;           /* relative residual per right-hand side (0 = 1e-8) */
+  void* x;              /* host, N x nrhs complex128 (column-major): receives the
+                           solution; borrowed until sldm_server_wait returns */
+} sldm_request;
+
+typedef struct {
+  int32_t code;         /* SLDM_OK or the failing call's status */
+  int32_t iters;        /* GMRES iterations of the solves that carried this request */
+  double relres;        /* largest final relative residual of its right-hand sides */
+  double t_submit, t_start, t_done; /* seconds on the server's clock */
+  int32_t cache_hit;    /* 1 when its operator was resident */
+  int32_t batch_rhs;    /* right-hand sides in the lockstep solve that carried it */
+} sldm_result;
+
+typedef struct {
+  int64_t requests, rhs, batches;      /* completed */
+  int64_t hits, misses, evictions, rejected;
+  int64_t cached_ops, cached_bytes;    /* now */
+  double lat_p50, lat_p99, lat_max;    /* seconds, submit -> done, completed requests */
+} sldm_server_stats;
+
+/* Start the workers.  SLDM_EINVAL for invalid options. */
+int sldm_server_create(const sldm_server_opts* opts, sldm_server** out);
+/* Register a model; the server borrows mesh and stack (they must outlive it) and
+ * copies the materials (one per object).  *model receives its id. */
+int sldm_server_add_model(sldm_server* srv, const sldm_mesh* mesh, const sldm_stack* stack,
+                          const sldm_material* per_obj, int32_t* model);
+/* Queue a request; *ticket identifies it for sldm_server_wait.  SLDM_EINVAL for
+ * an unknown model or invalid fields. */
+int sldm_server_submit(sldm_server* srv, const sldm_request* req, int64_t* ticket);
+/* Wait up to timeout_s seconds (< 0: no limit) for a request; fills *res and
+ * forgets the ticket.  SLDM_ETIMEOUT if it is still pending (ticket kept),
+ * SLDM_EINVAL for an unknown ticket.  The request's own outcome is res->code;
+ * when it failed, sldm_last_error in the waiting thread gives the message. */
+int sldm_server_wait(sldm_server* srv, int64_t ticket, double timeout_s, sldm_result* res);
+int sldm_server_stats_get(sldm_server* srv, sldm_server_stats* st);
+/* Drop every cached operator that no worker is using. */
+int sldm_server_flush(sldm_server* srv);
+/* Finish the queued requests, stop the workers, free the cache. */
+int sldm_server_destroy(sldm_server* srv);
+
+/* The server's host-side policies as plain functions (no device work), for
+ * checking them without a GPU:
+ * sldm_cache_plan: an LRU cache of capacity `budget` bytes (0 = unbounded)
+ *   accessed by keys[i] with sizes bytes[i] (same key, same size), i = 0..n-1,
+ *   one access at a time and nothing pinned; action[i] = 0 hit, 1 miss admitted,
+ *   2 miss larger than the budget (not cached); evicted[i] = entries evicted to
+ *   admit access i.
+ * sldm_batch_plan: a FIFO queue of n requests (keys[i], nrhs[i]); a batch takes
+ *   the oldest request, then the following requests of its key in order while
+ *   the right-hand sides fit in max_batch (a request larger than max_batch is a
+ *   batch of its own, solved in slices); batch[i] = index of request i's batch,
+ *   batches numbered in the order they are formed. */
+int sldm_cache_plan(int64_t n, const int64_t* keys, const int64_t* bytes, int64_t budget, int32_t* action,
+                    int32_t* evicted);
+int sldm_batch_plan(int64_t n, const int64_t* keys, const int32_t* nrhs, int32_t max_batch, int32_t* batch);
 
 #ifdef __cplusplus
 }

@@ -448,7 +448,16 @@ void lu_solve_batched(const std::vector<LUSysT<C>>& all, cudaStream_t s) {
   const size_t smem = size_t(2) * nmax * sizeof(C) + size_t(2) * max_own * sizeof(C) + size_t(max_own) * sizeof(int);
   SLDM_REQUIRE(smem <= 220 * 1024, SLDM_ENOTSUP,
                "LU: object too large for the in-kernel direct factorisation (n = " + std::to_string(nmax) + ")");
-  SLDM_CUDA(cudaFuncSetAttribute(lu_coop_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+  {
+    // the limit is per function and context, shared by every thread that launches
+    // it: set once to the largest size accepted above, never to this call's size
+    static std::atomic<uint64_t> set{0};
+    const uint64_t bit = uint64_t(1) << (dev & 63);
+    if (!(set.load() & bit)) {
+      SLDM_CUDA(cudaFuncSetAttribute(lu_coop_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+      set.fetch_or(bit);
+    }
+  }
   int per_sm = 0;
   SLDM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lu_coop_kernel<C>, LU_THREADS, smem));
   SLDM_REQUIRE(per_sm >= 1, SLDM_ENOTSUP, "LU: kernel does not fit on an SM");

@@ -47,6 +47,7 @@
 #include <cuda.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <queue>
 
@@ -494,16 +495,15 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 static EncodeTiledFn encoder() {
-  static EncodeTiledFn fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
+  // looked up once (thread-safe initialisation of a local static)
+  static const EncodeTiledFn fn = [] {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeTiledFn>(p);
-  }
+      return reinterpret_cast<EncodeTiledFn>(p);
+    return EncodeTiledFn(nullptr);
+  }();
   return fn;
 }
 
@@ -571,12 +571,13 @@ void tc_plan_build(const std::vector<GemvJob>& jobs, TcPlan& tp, cudaStream_t s)
 
 void gemm_tc(const GemvPlan& plan, const TcPlan& tp, int nrhs, cudaStream_t s) {
   SLDM_REQUIRE(tp.ok && nrhs >= 1 && nrhs <= TC_MAX_NRHS, SLDM_EINVAL, "tensor-core product: invalid plan or nrhs");
-  static bool attr_set[64] = {false};
+  static std::atomic<uint64_t> attr_set{0};  // devices whose attribute is set
   int dev = 0;
   SLDM_CUDA(cudaGetDevice(&dev));
-  if (!attr_set[dev & 63]) {
+  const uint64_t bit = uint64_t(1) << (dev & 63);
+  if (!(attr_set.load() & bit)) {
     SLDM_CUDA(cudaFuncSetAttribute(gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(TC_SMEM)));
-    attr_set[dev & 63] = true;
+    attr_set.fetch_or(bit);
   }
   ScopedTimer tm("gemm_tc", s);
   gemm_tc_kernel<<<unsigned(tp.nctas), TC_THREADS, TC_SMEM, s>>>(plan.jobs, tp.maps.p, tp.tiles.p, tp.cta_begin.p, nrhs,

@@ -21,6 +21,7 @@
 // FMA per SM per clock) is what bounds it, so the tiles are sized for
 // occupancy of the FP64 pipe, not for shared-memory reuse.
 #include <algorithm>
+#include <atomic>
 
 #include "dense.h"
 
@@ -408,7 +409,18 @@ void lu_solve_blocked(const LUSysT<C>& S, cudaStream_t s) {
   const int max_chunk = (n + nsm - 1) / nsm > PANEL_MIN_ROWS ? (n + nsm - 1) / nsm : PANEL_MIN_ROWS;
   const size_t panel_smem = (size_t(max_chunk) * NB + NB) * sizeof(C);
   SLDM_REQUIRE(panel_smem <= 200 * 1024, SLDM_ENOTSUP, "LU: panel too large for shared memory");
-  SLDM_CUDA(cudaFuncSetAttribute(lu_panel_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(panel_smem)));
+  {
+    // per function and context, shared by every launching thread: set once to the
+    // largest size accepted above, never to this call's size
+    static std::atomic<uint64_t> set{0};
+    int dev = 0;
+    SLDM_CUDA(cudaGetDevice(&dev));
+    const uint64_t bit = uint64_t(1) << (dev & 63);
+    if (!(set.load() & bit)) {
+      SLDM_CUDA(cudaFuncSetAttribute(lu_panel_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+      set.fetch_or(bit);
+    }
+  }
   int per_sm = 0;
   SLDM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lu_panel_kernel<C>, PANEL_THREADS, panel_smem));
   SLDM_REQUIRE(per_sm >= 1, SLDM_ENOTSUP, "LU: panel kernel does not fit on an SM");

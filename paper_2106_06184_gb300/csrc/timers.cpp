@@ -41,7 +41,7 @@ std::mutex g_mu;
 bool g_on = false;
 std::vector<cudaEvent_t> g_pool;
 std::vector<Pending> g_pending;
-std::vector<std::pair<std::string, cudaEvent_t>> g_open;  // per begin, matched LIFO by end
+thread_local std::vector<std::pair<std::string, cudaEvent_t>> t_open;  // per begin, matched LIFO by end in its thread
 std::map<std::string, std::pair<double, int64_t>> g_acc;
 
 cudaEvent_t get_event() {
@@ -76,14 +76,14 @@ void timer_begin(const char* name, cudaStream_t s) {
   std::lock_guard<std::mutex> l(g_mu);
   cudaEvent_t a = get_event();
   cudaEventRecord(a, s);
-  g_open.push_back({name, a});
+  t_open.push_back({name, a});
 }
 
 void timer_end(cudaStream_t s) {
   std::lock_guard<std::mutex> l(g_mu);
-  if (g_open.empty()) return;
-  auto o = g_open.back();
-  g_open.pop_back();
+  if (t_open.empty()) return;
+  auto o = t_open.back();
+  t_open.pop_back();
   cudaEvent_t b = get_event();
   cudaEventRecord(b, s);
   g_pending.push_back({o.first, o.second, b});

@@ -61,6 +61,27 @@ class OpInfo(C.Structure):
                 ("device_bytes", C.c_int64), ("precision", C.c_int32), ("reserved", C.c_int32), ("k0", C.c_double)]
 
 
+class ServerOpts(C.Structure):
+    _fields_ = [("workers", C.c_int32), ("max_batch", C.c_int32), ("precision", C.c_int32), ("maxit", C.c_int32),
+                ("budget_bytes", C.c_int64)]
+
+
+class Request(C.Structure):
+    _fields_ = [("model", C.c_int32), ("nrhs", C.c_int32), ("freq_hz", C.c_double), ("khat", C.c_void_p),
+                ("pol", C.c_void_p), ("tol", C.c_double), ("x", C.c_void_p)]
+
+
+class Result(C.Structure):
+    _fields_ = [("code", C.c_int32), ("iters", C.c_int32), ("relres", C.c_double), ("t_submit", C.c_double),
+                ("t_start", C.c_double), ("t_done", C.c_double), ("cache_hit", C.c_int32), ("batch_rhs", C.c_int32)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("requests", C.c_int64), ("rhs", C.c_int64), ("batches", C.c_int64), ("hits", C.c_int64),
+                ("misses", C.c_int64), ("evictions", C.c_int64), ("rejected", C.c_int64), ("cached_ops", C.c_int64),
+                ("cached_bytes", C.c_int64), ("lat_p50", C.c_double), ("lat_p99", C.c_double), ("lat_max", C.c_double)]
+
+
 EXPORTS = {
     "sldm_last_error": (None, [C.c_char_p, C.c_size_t]),
     "sldm_mesh_create": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p, C.POINTER(C.c_void_p)]),
@@ -92,6 +113,15 @@ EXPORTS = {
     "sldm_set_device_budget": (C.c_int, [C.c_int64]),
     "sldm_device_bytes": (C.c_int, [C.POINTER(C.c_int64)]),
     "sldm_test_inject": (C.c_int, [C.c_int32, C.c_int32]),
+    "sldm_server_create": (C.c_int, [C.POINTER(ServerOpts), C.POINTER(C.c_void_p)]),
+    "sldm_server_add_model": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int32)]),
+    "sldm_server_submit": (C.c_int, [C.c_void_p, C.POINTER(Request), C.POINTER(C.c_int64)]),
+    "sldm_server_wait": (C.c_int, [C.c_void_p, C.c_int64, C.c_double, C.POINTER(Result)]),
+    "sldm_server_stats_get": (C.c_int, [C.c_void_p, C.POINTER(ServerStats)]),
+    "sldm_server_flush": (C.c_int, [C.c_void_p]),
+    "sldm_server_destroy": (C.c_int, [C.c_void_p]),
+    "sldm_cache_plan": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
+    "sldm_batch_plan": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
 }
 
 
@@ -359,3 +389,88 @@ class Operator:
             self.h = None
 
     __del__ = close
+
+
+class Server:
+    """sldm_server: the request loop over cached operators (argument marshalling only)."""
+
+    h = None
+
+    def __init__(self, workers=2, max_batch=32, precision=PREC_F32X2, budget_bytes=0, maxit=0, lib=None):
+        self.L = lib or load()
+        opts = ServerOpts(workers, max_batch, precision, maxit, int(budget_bytes))
+        h = C.c_void_p()
+        self.L.check(self.L.lib.sldm_server_create(C.byref(opts), C.byref(h)))
+        self.h = h
+        self._keep = {}  # ticket -> (khat, pol, x) kept alive until wait
+        self._models = []
+
+    def add_model(self, mesh, stack, materials):
+        mats = (Material * len(materials))(*[Material(m[0], m[1], m[2], m[3] if len(m) > 3 else 0, 0)
+                                             for m in materials])
+        mid = C.c_int32()
+        self.L.check(self.L.lib.sldm_server_add_model(self.h, mesh.h, stack.h, mats, C.byref(mid)))
+        self._models.append((mesh, stack))
+        return mid.value
+
+    def submit(self, model, freq_hz, khat, pol, x, tol=1e-8):
+        """x: host complex128 array (nrhs, N) receiving the solutions."""
+        khat = np.ascontiguousarray(np.atleast_2d(khat), np.float64)
+        pol = np.ascontiguousarray(np.atleast_2d(pol), np.float64)
+        if not (isinstance(x, np.ndarray) and x.dtype == np.complex128 and x.flags.c_contiguous):
+            raise ValueError("x must be a C-contiguous complex128 host array")
+        req = Request(model, len(khat), freq_hz, khat.ctypes.data_as(C.c_void_p), pol.ctypes.data_as(C.c_void_p), tol,
+                      x.ctypes.data_as(C.c_void_p))
+        t = C.c_int64()
+        self.L.check(self.L.lib.sldm_server_submit(self.h, C.byref(req), C.byref(t)))
+        self._keep[t.value] = (khat, pol, x)
+        return t.value
+
+    def wait(self, ticket, timeout=-1.0):
+        r = Result()
+        self.L.check(self.L.lib.sldm_server_wait(self.h, ticket, float(timeout), C.byref(r)))
+        self._keep.pop(ticket, None)
+        out = {f: getattr(r, f) for f, _ in Result._fields_}
+        if r.code != OK:
+            buf = C.create_string_buffer(1024)
+            self.L.lib.sldm_last_error(buf, 1024)
+            out["error"] = buf.value.decode(errors="replace")
+        return out
+
+    def stats(self):
+        st = ServerStats()
+        self.L.check(self.L.lib.sldm_server_stats_get(self.h, C.byref(st)))
+        return {f: getattr(st, f) for f, _ in ServerStats._fields_}
+
+    def flush(self):
+        self.L.check(self.L.lib.sldm_server_flush(self.h))
+
+    def close(self):
+        if self.h:
+            self.L.lib.sldm_server_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+
+def cache_plan(keys, sizes, budget, lib=None):
+    """The server's LRU admission policy on an access sequence: (action, evicted)."""
+    L = lib or load()
+    keys = np.ascontiguousarray(keys, np.int64)
+    sizes = np.ascontiguousarray(sizes, np.int64)
+    act = np.zeros(len(keys), np.int32)
+    ev = np.zeros(len(keys), np.int32)
+    L.check(L.lib.sldm_cache_plan(len(keys), keys.ctypes.data_as(C.c_void_p), sizes.ctypes.data_as(C.c_void_p),
+                                  int(budget), act.ctypes.data_as(C.c_void_p), ev.ctypes.data_as(C.c_void_p)))
+    return act, ev
+
+
+def batch_plan(keys, nrhs, max_batch, lib=None):
+    """The server's batching policy on a FIFO queue: the batch index of each request."""
+    L = lib or load()
+    keys = np.ascontiguousarray(keys, np.int64)
+    nrhs = np.ascontiguousarray(nrhs, np.int32)
+    out = np.zeros(len(keys), np.int32)
+    L.check(L.lib.sldm_batch_plan(len(keys), keys.ctypes.data_as(C.c_void_p), nrhs.ctypes.data_as(C.c_void_p),
+                                  int(max_batch), out.ctypes.data_as(C.c_void_p)))
+    return out
