@@ -111,7 +111,12 @@ typedef struct {
 
 typedef struct {
   int32_t precision;    /* SLDM_PREC_F64, SLDM_PREC_F32 or SLDM_PREC_F32X2 */
-  int32_t reserved;
+  int32_t nested_min;   /* SLDM_PREC_F64 only: objects whose M_l has at least this order
+                           (ne + nt - 1) get Y E by inner solves instead of a formed Y
+                           (Sec. III: direct factorisation below ~1000 triangles): an
+                           FP32 approximate inverse of M_l and FP64 iterative refinement
+                           to 1e-13 per product; 0 = 2500, < 0 = always form Y.  Falls
+                           back to the FP64 LU when the refinement would contract slowly. */
   void* stream;         /* stream the fill runs on (NULL = default) */
 } sldm_assemble_opts;
 

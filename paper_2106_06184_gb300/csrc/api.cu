@@ -6,6 +6,7 @@
 #include <complex>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <array>
 
@@ -13,6 +14,7 @@
 #include "gemm_tc.h"
 #include "internal.h"
 #include "mgf.h"
+#include "nested.h"
 #include "precond.h"
 
 namespace sldm {
@@ -32,6 +34,7 @@ struct ObjInfo {
   int64_t oLA, oLP, oK, oY11, oY21;  // element offsets in op->loc
   cplx k, eps_c;
   double mu_r;
+  bool nested = false;  // Y E by inner solves (nested.h); Y11, Y21 are not formed
 };
 
 }  // namespace sldm
@@ -77,13 +80,22 @@ struct sldm_op {
   sldm::DBuf<double2> V, wb, wx, wr, wtmp, wtmp2, wacc, wz, dh;
   int ws_nr = 0;
   sldm::DBuf<double> dnorm;
+  // large objects: Y E by inner solves (nested.h), and their scratch (n_max x WR)
+  int nested_min = 2500;  // order of M_l from which Y is not formed (< 0: never)
+  bool want_x2 = false;   // assembling for SLDM_PREC_F32X2 (split after the FP64 fill)
+  std::vector<std::unique_ptr<sldm::NestedUse>> nested;
+  sldm::DBuf<double2> wnt, wny, wnr;
+  int64_t ldn = 0;
   std::mutex busy;
 };
 
 namespace sldm {
 
 static int64_t op_bytes(const sldm_op* op) {
-  return int64_t(op->LAm.bytes() + op->LPm.bytes() + op->loc.bytes() + op->LAm_lo.bytes() + op->LPm_lo.bytes() +
+  int64_t nb = int64_t(op->wnt.bytes() + op->wny.bytes() + op->wnr.bytes());
+  for (const auto& u : op->nested)
+    if (u->mat && u->obj == u->mat_owner) nb += int64_t(u->mat->M.bytes() + u->mat->R.bytes() + u->mat->X.bytes());
+  return nb + int64_t(op->LAm.bytes() + op->LPm.bytes() + op->loc.bytes() + op->LAm_lo.bytes() + op->LPm_lo.bytes() +
                  op->loc_lo.bytes() + op->ix_val.bytes() + op->V.bytes() +
                  op->pc.sinv.bytes() + op->pc.sinv32.bytes() + op->pc.lam.bytes() + op->pc.pdiag.bytes());
 }
@@ -105,6 +117,7 @@ static void make_plans(sldm_op* op, size_t es_m, size_t es_v, DBuf<GemvJob>& dj1
   const void* LPlo = lo ? op->LPm_lo.p : nullptr;
   std::vector<GemvJob> j1, j2;
   for (auto& o : op->obj) {
+    if (o.nested) continue;  // Y E by inner solves in apply_dev
     j1.push_back({L(o.oY11), o.ne, o.ne, o.ne, P(op->we, o.e0), ne, P(op->wt1, o.e0), ne, 1, 0, 0, 0, Lo(o.oY11)});
     if (o.nq > 0)
       j1.push_back({L(o.oY21), o.ne, o.nq, o.ne, P(op->we, o.e0), ne, P(op->wt2, o.q0), nq, 1, 0, 0, 0, Lo(o.oY21)});
@@ -171,6 +184,16 @@ static void build_plans(sldm_op* op) {
     op->plan1d.name = "gemv_y_f64acc";
     op->plan2d.name = "gemv_main_f64acc";
   }
+  if (!op->nested.empty()) {  // inner-solve objects: scratch of the largest M_l, and their plans
+    int64_t nmax = 0;
+    for (auto& u : op->nested) nmax = std::max<int64_t>(nmax, u->mat->n);
+    op->ldn = (nmax + 63) / 64 * 64;
+    op->wnt.alloc(size_t(op->ldn) * WR);
+    op->wny.alloc(size_t(op->ldn) * WR);
+    op->wnr.alloc(size_t(op->ldn) * WR);
+    for (auto& u : op->nested)
+      nested_plans(*u, reinterpret_cast<const double2*>(op->we.p), ne, op->wnt.p, op->wny.p, op->wnr.p, op->ldn);
+  }
 }
 
 // y = Z x for nrhs columns, x/y complex128 on the device (column stride N)
@@ -185,7 +208,13 @@ static void apply_dev(const sldm_op* op_, const double2* x, double2* y, int nrhs
     const double2* xr = x + int64_t(r0) * op->N;
     double2* yr = y + int64_t(r0) * op->N;
     apply_glue_split<CV>(xr, op->N, D, op->wj.p, op->we.p, op->wu.p, nr, s);
-    gemv_jobs_mixed<CM, CV>(p1, nr, s);
+    if (p1.njobs > 0) gemv_jobs_mixed<CM, CV>(p1, nr, s);
+    if (!op->nested.empty()) {
+      if (sizeof(CV) != sizeof(double2)) throw Error{SLDM_EINVAL, "apply: inner-solve objects need complex128 vectors"};
+      for (const auto& u : op->nested)
+        nested_apply(*u, op->wnt.p, op->wny.p, op->wnr.p, op->ldn, reinterpret_cast<double2*>(op->wt1.p), op->ne,
+                     reinterpret_cast<double2*>(op->wt2.p), op->nq, nr, op->mesh->h.ell, s);
+    }
     apply_glue_prep<CV>(op->mesh, D, op->wj.p, op->wu.p, op->wt1.p, op->wt2.p, op->wa.p, op->wc.p, op->wbc.p, op->wbu.p, nr,
                         s, op->mesh->d.tri_begin.p, op->mesh->d.edge_begin.p);
     gemv_jobs_mixed<CM, CV>(p2, nr, s);
@@ -500,16 +529,57 @@ static void assemble_impl(sldm_op* op, const sldm_material* mats, cudaStream_t s
     Ml.alloc(ml_total);
     Rl.alloc(rl_total);
     std::vector<LUSysT<C>> sys;
+    // large objects of an FP64 operator: Y E by inner solves (nested.h) instead of Y
+    auto inner = [&](const ObjInfo& oi) {
+      return sizeof(C) == sizeof(double2) && !op->want_x2 && op->nested_min >= 0 && oi.ne + oi.nq >= op->nested_min;
+    };
+    std::vector<int> cand;
     for (int o = 0; o < op->nobj; ++o) {
       if (ref[o] != o) continue;
       const ObjInfo& oi = op->obj[o];
       build_Ml<C>(m, o, op->k0, op->LAm.p, op->ne, op->LPm.p, op->nt, Kl.p + kl_off[o] * es, oi.ne, op->ix_val.p,
                   Ml.p + ml_off[o], Rl.p + rl_off[o], s);
-      sys.push_back({Ml.p + ml_off[o], Rl.p + rl_off[o], oi.ne + oi.nq, oi.ne});
+      if (inner(oi)) cand.push_back(o);
+      else sys.push_back({Ml.p + ml_off[o], Rl.p + rl_off[o], oi.ne + oi.nq, oi.ne});
     }
     lu_solve_batched<C>(sys, s);
+    std::vector<std::shared_ptr<NestedMat>> nmat(op->nobj);
+    if constexpr (sizeof(C) == sizeof(double2)) {
+      std::vector<LUSysT<C>> fallback;  // refinement too slow: the FP64 LU after all
+      for (int o : cand) {
+        const ObjInfo& oi = op->obj[o];
+        auto mat = std::make_shared<NestedMat>();
+        mat->n = oi.ne + oi.nq;
+        mat->ne = oi.ne;
+        mat->nq = oi.nq;
+        const int64_t n = mat->n;
+        mat->M.alloc(size_t(n) * n);
+        mat->R.alloc(size_t(n) * oi.ne);
+        SLDM_CUDA(cudaMemcpyAsync(mat->M.p, Ml.p + ml_off[o], size_t(n) * n * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+        SLDM_CUDA(cudaMemcpyAsync(mat->R.p, Rl.p + rl_off[o], size_t(n) * oi.ne * sizeof(double2), cudaMemcpyDeviceToDevice,
+                                  s));
+        if (nested_setup(*mat, s)) {
+          nmat[o] = mat;
+        } else {
+          fallback.push_back({Ml.p + ml_off[o], Rl.p + rl_off[o], int32_t(n), oi.ne});
+        }
+      }
+      lu_solve_batched<C>(fallback, s);
+    }
     for (int o = 0; o < op->nobj; ++o) {
-      if (ref[o] != o) continue;
+      const int r = ref[o];
+      if (!nmat[r]) continue;
+      op->obj[o].nested = true;
+      auto u = std::make_unique<NestedUse>();
+      u->obj = o;
+      u->mat_owner = r;
+      u->mat = nmat[r];
+      u->e0 = op->obj[o].e0;
+      u->q0 = op->obj[o].q0;
+      op->nested.push_back(std::move(u));
+    }
+    for (int o = 0; o < op->nobj; ++o) {
+      if (ref[o] != o || op->obj[o].nested) continue;
       const ObjInfo& oi = op->obj[o];
       // undo the length scaling of M_l: Y11 = Yh11 / l, Y21 = l Yh21
       copy_scaled<C>(Rl.p + rl_off[o], int64_t(oi.ne) * oi.ne, 1.0 / h.ell, loc + oi.oY11 * es, s);
@@ -525,6 +595,7 @@ static void assemble_impl(sldm_op* op, const sldm_material* mats, cudaStream_t s
       SLDM_CUDA(cudaMemcpyAsync(loc + oi.oLP * es, loc + ri.oLP * es, int64_t(oi.nt) * oi.nt * es,
                                 cudaMemcpyDeviceToDevice, s));
       SLDM_CUDA(cudaMemcpyAsync(loc + oi.oK * es, loc + ri.oK * es, n_ee * es, cudaMemcpyDeviceToDevice, s));
+      if (oi.nested) continue;  // Y is not formed
       SLDM_CUDA(cudaMemcpyAsync(loc + oi.oY11 * es, loc + ri.oY11 * es, n_ee * es, cudaMemcpyDeviceToDevice, s));
       SLDM_CUDA(cudaMemcpyAsync(loc + oi.oY21 * es, loc + ri.oY21 * es, int64_t(oi.nq) * oi.ne * es,
                                 cudaMemcpyDeviceToDevice, s));
@@ -947,6 +1018,8 @@ int sldm_assemble(const sldm_mesh* m, const sldm_stack* st, const sldm_material*
     SLDM_REQUIRE(prec == SLDM_PREC_F64 || prec == SLDM_PREC_F32 || prec == SLDM_PREC_F32X2, SLDM_EINVAL,
                  "assemble: unknown precision");
     op->prec = prec == SLDM_PREC_F32 ? SLDM_PREC_F32 : SLDM_PREC_F64;  // X2 fills in FP64, then splits
+    op->want_x2 = prec == SLDM_PREC_F32X2;
+    if (opts && opts->nested_min != 0) op->nested_min = opts->nested_min;
     op->esz = op->prec == SLDM_PREC_F32 ? 8 : 16;
     op->freq = freq_hz;
     op->device = dev;
@@ -1055,8 +1128,12 @@ int sldm_op_block(const sldm_op* op, int32_t which, int32_t obj, void* dst, int3
     case SLDM_BLOCK_LA: r = c = oi->ne; src = op->loc.p + oi->oLA * op->esz; break;
     case SLDM_BLOCK_LP: r = c = oi->nt; src = op->loc.p + oi->oLP * op->esz; break;
     case SLDM_BLOCK_K: r = c = oi->ne; src = op->loc.p + oi->oK * op->esz; break;
-    case SLDM_BLOCK_Y11: r = c = oi->ne; src = op->loc.p + oi->oY11 * op->esz; break;
-    case SLDM_BLOCK_Y21: r = oi->nq; c = oi->ne; src = op->loc.p + oi->oY21 * op->esz; break;
+    case SLDM_BLOCK_Y11:
+      SLDM_REQUIRE(!oi->nested, SLDM_ENOTSUP, "op_block: Y is applied by inner solves for this object (not formed)");
+      r = c = oi->ne; src = op->loc.p + oi->oY11 * op->esz; break;
+    case SLDM_BLOCK_Y21:
+      SLDM_REQUIRE(!oi->nested, SLDM_ENOTSUP, "op_block: Y is applied by inner solves for this object (not formed)");
+      r = oi->nq; c = oi->ne; src = op->loc.p + oi->oY21 * op->esz; break;
     default: SLDM_REQUIRE(false, SLDM_EINVAL, "op_block: unknown block");
   }
   if (rows) *rows = r;

@@ -44,7 +44,7 @@ class MeshInfo(C.Structure):
 
 
 class AssembleOpts(C.Structure):
-    _fields_ = [("precision", C.c_int32), ("reserved", C.c_int32), ("stream", C.c_void_p)]
+    _fields_ = [("precision", C.c_int32), ("nested_min", C.c_int32), ("stream", C.c_void_p)]
 
 
 class SolveOpts(C.Structure):
@@ -306,12 +306,12 @@ class Operator:
 
     h = None
 
-    def __init__(self, mesh: Mesh, stack: Stack, materials, freq_hz, precision=PREC_F64, stream=None):
+    def __init__(self, mesh: Mesh, stack: Stack, materials, freq_hz, precision=PREC_F64, stream=None, nested_min=0):
         self.L = mesh.L
         self.mesh, self.stack = mesh, stack
         mats = (Material * len(materials))(*[Material(m[0], m[1], m[2], m[3] if len(m) > 3 else 0, 0)
                                              for m in materials])
-        opts = AssembleOpts(precision, 0, _stream(stream))
+        opts = AssembleOpts(precision, int(nested_min), _stream(stream))
         h = C.c_void_p()
         self.L.check(self.L.lib.sldm_assemble(mesh.h, stack.h, mats, freq_hz, C.byref(opts), C.byref(h)))
         self.h = h
