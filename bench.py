@@ -165,7 +165,7 @@ FILL_F64_PEAK_EVALS = FP64_OPS_PER_S / FP64_OPS_PER_EVAL
 # The reflected (layered) fill in FP64: images, static z-rho images and a bilinear
 # remainder lookup per evaluation; FP64 pipe operations per evaluation from ncu's
 # DFMA + DMUL + DADD counts of fill_reflected_kernel<double2> on the 4 x 4 glass case.
-FP64_OPS_PER_EVAL_REFL = 353.0
+FP64_OPS_PER_EVAL_REFL = 292.0
 
 
 # DRAM traffic per algorithmic byte of the HBM-streaming GEMV stage, from one

@@ -127,7 +127,7 @@ typedef struct {
 
 typedef struct {
   double tol;           /* relative residual of the length-scaled system (default 1e-8), see sldm_solve */
-  int32_t restart;      /* GMRES restart length m (default 300; at most N) */
+  int32_t restart;      /* GMRES restart length m (default 300; at most N and 1000) */
   int32_t maxit;        /* maximum iterations per right-hand side (default 2000) */
   int32_t x0_given;     /* nonzero: x holds the initial guess on entry */
   int32_t precond;      /* SLDM_PRECOND_P (0, default) or SLDM_PRECOND_NONE */

@@ -37,6 +37,29 @@ struct ObjInfo {
   bool nested = false;  // Y E by inner solves (nested.h); Y11, Y21 are not formed
 };
 
+// Pinned flag buffers and events of the GMRES convergence polls (one per slot).
+struct PollRing {
+  static constexpr int SLOTS = 2;  // the host runs at most one step ahead of what it knows
+  cudaEvent_t ev[SLOTS] = {};
+  int32_t* flags[SLOTS] = {};
+  bool ready = false;
+  void init(int n) {
+    if (ready) return;
+    for (int i = 0; i < SLOTS; ++i) {
+      SLDM_CUDA(cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming));
+      SLDM_CUDA(cudaMallocHost(&flags[i], sizeof(int32_t) * n));
+    }
+    ready = true;
+  }
+  ~PollRing() {
+    if (!ready) return;
+    for (int i = 0; i < SLOTS; ++i) {
+      cudaEventDestroy(ev[i]);
+      cudaFreeHost(flags[i]);
+    }
+  }
+};
+
 }  // namespace sldm
 
 struct sldm_op {
@@ -80,6 +103,12 @@ struct sldm_op {
   sldm::DBuf<double2> V, wb, wx, wr, wtmp, wtmp2, wacc, wz, dh;
   int ws_nr = 0;
   sldm::DBuf<double> dnorm;
+  // GMRES on the device: Hessenberg, rotations, residual vectors, per right-hand side state
+  sldm::DBuf<double2> gH, gcs, gsn, gg;
+  sldm::DBuf<sldm::GmresState> gst;
+  sldm::DBuf<double> gscale;
+  sldm::DBuf<int> gon;
+  sldm::PollRing polls;
   // large objects: Y E by inner solves (nested.h), and their scratch (n_max x WR)
   int nested_min = 2500;  // order of M_l from which Y is not formed (< 0: never)
   bool want_x2 = false;   // assembling for SLDM_PREC_F32X2 (split after the FP64 fill)
@@ -670,6 +699,15 @@ static void ensure_ws(sldm_op* op, int m, int nr) {
   op->wz.alloc(N * W);
   op->dh.alloc(W * 2 * (m + 2));
   op->dnorm.alloc(W);
+  // Hessenberg matrices, rotations and residual vectors on the device
+  op->gH.alloc(W * size_t(m + 1) * m);
+  op->gcs.alloc(W * size_t(m));
+  op->gsn.alloc(W * size_t(m));
+  op->gg.alloc(W * size_t(m + 1));
+  op->gst.alloc(W);
+  op->gscale.alloc(W);
+  op->gon.alloc(W);
+  op->polls.init(int(W));
   op->ws_m = m;
   op->ws_nr = nr;
 }
@@ -731,12 +769,16 @@ static void gmres_block(sldm_op* op, bool use_p, bool refine, bool x_zero, int m
     }
   };
   residuals();
-  std::vector<std::vector<cplx>> H(nr, std::vector<cplx>(size_t(m + 1) * m)), g(nr, std::vector<cplx>(m + 1)),
-      cs(nr, std::vector<cplx>(m)), sn(nr, std::vector<cplx>(m));
+  // Hessenberg matrices, rotations and convergence tests live on the device
+  // (gmres_givens): the host learns which right-hand sides still iterate from
+  // a copy of their flags that it reads without waiting, or after at most
+  // LAG newer steps have been queued, so converged ones run at most LAG extra
+  // (frozen) steps and the host never waits on a step it has just queued.
+  constexpr int LAG = PollRing::SLOTS - 1;
   std::vector<int> it(nr, 0), kused(nr, 0);
   std::vector<char> live(nr, 0);
-  std::vector<double2> hh(size_t(sldm_op::WR) * 2 * (m + 2));
-  std::vector<double> hn(sldm_op::WR);
+  std::vector<GmresState> hst(nr);
+  PollRing& polls = op->polls;
   for (;;) {
     std::vector<int> act;
     for (int r = 0; r < nr; ++r) {
@@ -744,19 +786,51 @@ static void gmres_block(sldm_op* op, bool use_p, bool refine, bool x_zero, int m
       if (bnorm[r] > 0 && beta[r] / bnorm[r] > tol && it[r] < maxit) act.push_back(r);
     }
     if (act.empty()) break;
-    for (int r : act) {
-      vaxpby<double2, CB>(N, 1.0 / beta[r], col(op->wr, r), 0.0, Vr(r), s);
-      std::fill(g[r].begin(), g[r].end(), cplx(0));
-      g[r][0] = beta[r];
-      kused[r] = 0;
-      live[r] = 1;
+    {
+      std::vector<double2> g0(size_t(nr) * (m + 1), make_double2(0.0, 0.0));
+      for (int r = 0; r < nr; ++r) {
+        hst[r] = GmresState{it[r], 0, 0, 0, bnorm[r], beta[r]};
+        g0[size_t(r) * (m + 1)] = make_double2(beta[r], 0.0);
+      }
+      for (int r : act) {
+        vaxpby<double2, CB>(N, 1.0 / beta[r], col(op->wr, r), 0.0, Vr(r), s);
+        hst[r].live = 1;
+        live[r] = 1;
+        kused[r] = 0;
+      }
+      SLDM_CUDA(cudaMemcpyAsync(op->gg.p, g0.data(), g0.size() * sizeof(double2), cudaMemcpyHostToDevice, s));
+      SLDM_CUDA(cudaMemcpyAsync(op->gst.p, hst.data(), nr * sizeof(GmresState), cudaMemcpyHostToDevice, s));
+      SLDM_CUDA(cudaStreamSynchronize(s));  // g0, hst are host temporaries
     }
+    std::vector<int> on, on_dev;
+    int next_poll = 0, oldest = 0;  // ring of outstanding flag copies [oldest, next_poll)
+    auto consume = [&](bool wait) {
+      while (oldest < next_poll) {
+        const int sl = oldest % PollRing::SLOTS;
+        if (!wait) {
+          const cudaError_t q = cudaEventQuery(polls.ev[sl]);
+          if (q == cudaErrorNotReady) break;
+          SLDM_CUDA(q);
+        } else {
+          SLDM_CUDA(cudaEventSynchronize(polls.ev[sl]));
+        }
+        for (int r : act)
+          if (!polls.flags[sl][r]) live[r] = 0;
+        ++oldest;
+        wait = false;  // one forced wait at most
+      }
+    };
     for (int k = 0; k < m; ++k) {
-      std::vector<int> on;
+      on.clear();
       for (int r : act)
         if (live[r]) on.push_back(r);
       if (on.empty()) break;
       const int na = int(on.size());
+      if (on != on_dev) {
+        SLDM_CUDA(cudaMemcpyAsync(op->gon.p, on.data(), na * sizeof(int), cudaMemcpyHostToDevice, s));
+        SLDM_CUDA(cudaStreamSynchronize(s));  // `on` is reused by the host
+        on_dev = on;
+      }
       // the products of this step, together: w_r = Dr Z P^-1 Dr^-1 v_r (or Dr Z Dc v_r)
       VecBatch<CB, double2> bv;
       for (int j = 0; j < na; ++j) {
@@ -797,55 +871,57 @@ static void gmres_block(sldm_op* op, bool use_p, bool refine, bool x_zero, int m
         krylov_dots<CB>(ks, s);
         krylov_update<CB>(ks, true, s);
       }
-      SLDM_CUDA(cudaMemcpyAsync(hh.data(), op->dh.p, size_t(nr) * 2 * (m + 2) * sizeof(double2), cudaMemcpyDeviceToHost, s));
-      SLDM_CUDA(cudaMemcpyAsync(hn.data(), op->dnorm.p, size_t(na) * sizeof(double), cudaMemcpyDeviceToHost, s));
-      SLDM_CUDA(cudaStreamSynchronize(s));
-      VecBatch<CB, CB> bn;  // v_{k+1} = w / h_{k+1,k}
-      for (int j = 0; j < na; ++j) {
-        const int r = on[j];
-        const double2* hr = hh.data() + size_t(r) * 2 * (m + 2);
-        const double h1 = std::sqrt(hn[j]);
-        bn.x[j] = bn.y[j] = Vr(r) + int64_t(k + 1) * ldv;
-        bn.a[j] = h1 > 0 ? 1.0 / h1 : 0.0;
-        std::vector<cplx>& Hr = H[r];
-        for (int i = 0; i <= k; ++i) Hr[size_t(i) * m + k] = cplx(hr[i].x, hr[i].y) + cplx(hr[(m + 2) + i].x, hr[(m + 2) + i].y);
-        Hr[size_t(k + 1) * m + k] = h1;
-        for (int i = 0; i < k; ++i) {  // previous rotations
-          cplx a = Hr[size_t(i) * m + k], b = Hr[size_t(i + 1) * m + k];
-          Hr[size_t(i) * m + k] = cs[r][i] * a + sn[r][i] * b;
-          Hr[size_t(i + 1) * m + k] = -std::conj(sn[r][i]) * a + cs[r][i] * b;
-        }
-        cplx a = Hr[size_t(k) * m + k], b = Hr[size_t(k + 1) * m + k];
-        double t = std::sqrt(std::norm(a) + std::norm(b));
-        if (std::abs(a) == 0) {
-          cs[r][k] = 0;
-          sn[r][k] = 1;
-          Hr[size_t(k) * m + k] = b;
-        } else {
-          cs[r][k] = std::abs(a) / t;
-          sn[r][k] = (a / std::abs(a)) * std::conj(b) / t;
-          Hr[size_t(k) * m + k] = (a / std::abs(a)) * t;
-        }
-        Hr[size_t(k + 1) * m + k] = 0;
-        g[r][k + 1] = -std::conj(sn[r][k]) * g[r][k];
-        g[r][k] = cs[r][k] * g[r][k];
-        ++it[r];
-        kused[r] = k + 1;
-        if (std::abs(g[r][k + 1]) / bnorm[r] <= tol || it[r] >= maxit || h1 == 0) live[r] = 0;
-        if (refine && std::abs(g[r][k + 1]) <= REFINE_CYCLE * beta[r]) live[r] = 0;
+      // rotations and convergence tests on the device; v_{k+1} = w / h_{k+1,k}
+      GivensArgs ga{};
+      ga.k = k;
+      ga.m = m;
+      ga.na = na;
+      ga.refine = refine ? 1 : 0;
+      ga.on = op->gon.p;
+      ga.dh = op->dh.p;
+      ga.ldh = 2 * (m + 2);
+      ga.nrm = op->dnorm.p;
+      ga.H = op->gH.p;
+      ga.cs = op->gcs.p;
+      ga.sn = op->gsn.p;
+      ga.g = op->gg.p;
+      ga.st = op->gst.p;
+      ga.tol = tol;
+      ga.cycle = REFINE_CYCLE;
+      ga.maxit = maxit;
+      ga.scale = op->gscale.p;
+      gmres_givens(ga, s);
+      VecBatch<CB, CB> bn;
+      for (int j = 0; j < na; ++j) bn.x[j] = bn.y[j] = Vr(on[j]) + int64_t(k + 1) * ldv;
+      vscale_dev_batch<CB>(N, bn, op->gscale.p, na, s);
+      // queue a copy of the flags; read the finished copies, waiting only when LAG are pending
+      {
+        if (next_poll - oldest == PollRing::SLOTS) consume(true);
+        const int sl = next_poll % PollRing::SLOTS;
+        SLDM_CUDA(cudaMemcpy2DAsync(polls.flags[sl], sizeof(int32_t), &op->gst.p[0].live, sizeof(GmresState),
+                                    sizeof(int32_t), nr, cudaMemcpyDeviceToHost, s));
+        SLDM_CUDA(cudaEventRecord(polls.ev[sl], s));
+        ++next_poll;
+        consume(next_poll - oldest > LAG);
       }
-      vscale3_batch(N, ne, 1.0, 1.0, 1.0, bn, na, s);
     }
-    // y = H^-1 g (upper triangular);  x += (P^-1 Dr^-1 or Dc) V y
+    // the cycle's state; y = H^-1 g on the device;  x += (P^-1 Dr^-1 or Dc) V y
+    SLDM_CUDA(cudaMemcpyAsync(hst.data(), op->gst.p, nr * sizeof(GmresState), cudaMemcpyDeviceToHost, s));
+    SLDM_CUDA(cudaStreamSynchronize(s));
     for (int r : act) {
+      it[r] = hst[r].it;
+      kused[r] = hst[r].kused;
+    }
+    std::vector<int> solve;
+    for (int r : act)
+      if (kused[r] > 0) solve.push_back(r);
+    if (!solve.empty()) {
+      SLDM_CUDA(cudaMemcpyAsync(op->gon.p, solve.data(), solve.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+      gmres_backsolve(int(solve.size()), op->gon.p, m, op->gH.p, op->gg.p, op->gst.p, op->dh.p, 2 * (m + 2), s);
+      SLDM_CUDA(cudaStreamSynchronize(s));  // `solve` is a host temporary
+    }
+    for (int r : solve) {
       const int ku = kused[r];
-      std::vector<cplx> y(ku);
-      for (int i = ku - 1; i >= 0; --i) {
-        cplx acc = g[r][i];
-        for (int j = i + 1; j < ku; ++j) acc -= H[r][size_t(i) * m + j] * y[j];
-        y[i] = acc / H[r][size_t(i) * m + i];
-      }
-      SLDM_CUDA(cudaMemcpyAsync(dhr(r), y.data(), ku * sizeof(double2), cudaMemcpyHostToDevice, s));
       SLDM_CUDA(cudaMemsetAsync(col(op->wacc, r), 0, N * sizeof(double2), s));
       vmul<CB, double2>(Vr(r), ldv, ku, dhr(r), 1.0, col(op->wacc, r), N, s);
       if (use_p) {
@@ -1272,6 +1348,7 @@ int sldm_solve(const sldm_op* op_, const void* b, void* x, int32_t nrhs, const s
   double tol = (opts && opts->tol > 0) ? opts->tol : 1e-8;
   int m = (opts && opts->restart > 0) ? opts->restart : 300;
   m = int(std::min<int64_t>(m, op->N));
+  SLDM_REQUIRE(m <= 1000, SLDM_EINVAL, "solve: restart length above 1000");
   int maxit = (opts && opts->maxit > 0) ? opts->maxit : 2000;
   bool x0 = opts && opts->x0_given;
   bool use_p = !(opts && opts->precond == SLDM_PRECOND_NONE) && op->pc.ready;

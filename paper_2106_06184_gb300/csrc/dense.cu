@@ -1631,4 +1631,153 @@ __global__ void scale_kernel(C* A, int64_t n, double sr, double si) {
 INST(float2)
 INST(double2)
 
+// ---------------------------------------------------------------- GMRES on the device
+__device__ __forceinline__ double2 zmul(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__device__ __forceinline__ double2 zconj(double2 a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ double2 zadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double zabs(double2 a) { return hypot(a.x, a.y); }
+
+// One warp per active right-hand side: the lanes stage column k of H and the
+// earlier rotations in shared memory, lane 0 applies the rotations in order (each
+// depends on the previous one) and the new one, and the lanes write the column back.
+__global__ void gmres_givens_kernel(GivensArgs a) {
+  extern __shared__ __align__(16) unsigned char gv_raw[];
+  double2* gsm = reinterpret_cast<double2*>(gv_raw);  // column (m + 2), cs (m), sn (m)
+  const int j = blockIdx.x;
+  if (j >= a.na) return;
+  const int r = a.on[j];
+  GmresState* st = a.st + r;
+  const int lane = threadIdx.x;
+  if (!st->live) {
+    if (lane == 0) a.scale[j] = 0.0;
+    return;
+  }
+  const int m = a.m, k = a.k;
+  const double2* hr = a.dh + int64_t(r) * a.ldh;
+  double2* H = a.H + int64_t(r) * (m + 1) * m;
+  double2* cs = a.cs + int64_t(r) * m;
+  double2* sn = a.sn + int64_t(r) * m;
+  double2* g = a.g + int64_t(r) * (m + 1);
+  double2* col = gsm;
+  double2* scs = gsm + (m + 2);
+  double2* ssn = scs + m;
+  const double h1 = sqrt(a.nrm[j]);
+  for (int i = lane; i <= k; i += 32) col[i] = zadd(hr[i], hr[(m + 2) + i]);
+  for (int i = lane; i < k; i += 32) {
+    scs[i] = cs[i];
+    ssn[i] = sn[i];
+  }
+  if (lane == 0) col[k + 1] = make_double2(h1, 0.0);
+  __syncwarp();
+  if (lane == 0) {
+    for (int i = 0; i < k; ++i) {  // the earlier rotations
+      const double2 x = col[i], y = col[i + 1];
+      col[i] = zadd(zmul(scs[i], x), zmul(ssn[i], y));
+      const double2 msn = zconj(ssn[i]);
+      col[i + 1] = zadd(make_double2(-(msn.x * x.x - msn.y * x.y), -(msn.x * x.y + msn.y * x.x)), zmul(scs[i], y));
+    }
+    const double2 x = col[k], y = col[k + 1];
+    const double ax = zabs(x);
+    const double t = sqrt(x.x * x.x + x.y * x.y + y.x * y.x + y.y * y.y);
+    double2 c, sv;
+    if (ax == 0) {
+      c = make_double2(0.0, 0.0);
+      sv = make_double2(1.0, 0.0);
+      col[k] = y;
+    } else {
+      const double2 ph = make_double2(x.x / ax, x.y / ax);  // a / |a|
+      c = make_double2(ax / t, 0.0);
+      const double2 p = zmul(ph, zconj(y));
+      sv = make_double2(p.x / t, p.y / t);
+      col[k] = make_double2(ph.x * t, ph.y * t);
+    }
+    col[k + 1] = make_double2(0.0, 0.0);
+    cs[k] = c;
+    sn[k] = sv;
+    const double2 gk = g[k];
+    const double2 msn = zconj(sv);
+    g[k + 1] = make_double2(-(msn.x * gk.x - msn.y * gk.y), -(msn.x * gk.y + msn.y * gk.x));
+    g[k] = zmul(c, gk);
+    st->it += 1;
+    st->kused = k + 1;
+    const double res = zabs(g[k + 1]);
+    if (res / st->bnorm <= a.tol || st->it >= a.maxit || h1 == 0) st->live = 0;
+    if (a.refine && res <= a.cycle * st->beta) st->live = 0;
+    a.scale[j] = h1 > 0 ? 1.0 / h1 : 0.0;
+  }
+  __syncwarp();
+  for (int i = lane; i <= k + 1; i += 32) H[int64_t(i) * m + k] = col[i];
+}
+
+void gmres_givens(const GivensArgs& a, cudaStream_t s) {
+  if (a.na <= 0) return;
+  const size_t smem = size_t(3 * a.m + 2) * sizeof(double2);
+  SLDM_REQUIRE(smem <= 48 * 1024, SLDM_EINVAL, "GMRES: restart length too large for the device rotations");
+  gmres_givens_kernel<<<a.na, 32, smem, s>>>(a), ::sldm::count_launch();
+  SLDM_CUDA(cudaGetLastError());
+}
+
+// one warp per right-hand side: back substitution, row by row from the bottom,
+// the sum over the columns to the right split across the lanes
+__global__ void gmres_backsolve_kernel(int na, const int* __restrict__ on, int m, const double2* __restrict__ H,
+                                       const double2* __restrict__ g, const GmresState* __restrict__ st, double2* dh,
+                                       int64_t ldh) {
+  const int j = blockIdx.x;
+  if (j >= na) return;
+  const int r = on[j];
+  const int ku = st[r].kused;
+  const double2* Hr = H + int64_t(r) * (m + 1) * m;
+  const double2* gr = g + int64_t(r) * (m + 1);
+  double2* y = dh + int64_t(r) * ldh;
+  const int lane = threadIdx.x;
+  for (int i = ku - 1; i >= 0; --i) {
+    double sr = 0, si = 0;
+    for (int c = i + 1 + lane; c < ku; c += 32) {
+      const double2 h = Hr[int64_t(i) * m + c], v = y[c];
+      sr += h.x * v.x - h.y * v.y;
+      si += h.x * v.y + h.y * v.x;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      sr += __shfl_down_sync(0xffffffffu, sr, o);
+      si += __shfl_down_sync(0xffffffffu, si, o);
+    }
+    if (lane == 0) {
+      const double2 acc = make_double2(gr[i].x - sr, gr[i].y - si);
+      const double2 d = Hr[int64_t(i) * m + i];
+      const double dn = d.x * d.x + d.y * d.y;
+      y[i] = make_double2((acc.x * d.x + acc.y * d.y) / dn, (acc.y * d.x - acc.x * d.y) / dn);
+    }
+    __syncwarp();
+  }
+}
+
+void gmres_backsolve(int na, const int* on, int m, const double2* H, const double2* g, const GmresState* st, double2* dh,
+                     int64_t ldh, cudaStream_t s) {
+  if (na <= 0) return;
+  gmres_backsolve_kernel<<<na, 32, 0, s>>>(na, on, m, H, g, st, dh, ldh), ::sldm::count_launch();
+  SLDM_CUDA(cudaGetLastError());
+}
+
+template <class CB>
+__global__ void vscale_dev_kernel(int64_t n, VecBatch<CB, CB> b, const double* __restrict__ scale) {
+  const int j = blockIdx.y;
+  const double a = scale[j];
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    CB v = b.x[j][i];
+    v.x = decltype(v.x)(double(v.x) * a);
+    v.y = decltype(v.y)(double(v.y) * a);
+    b.y[j][i] = v;
+  }
+}
+
+template <class CB>
+void vscale_dev_batch(int64_t n, const VecBatch<CB, CB>& b, const double* scale, int na, cudaStream_t s) {
+  if (na <= 0) return;
+  const unsigned gx = unsigned(std::min<int64_t>((n + 255) / 256, 1024));
+  vscale_dev_kernel<CB><<<dim3(gx, na), 256, 0, s>>>(n, b, scale), ::sldm::count_launch();
+  SLDM_CUDA(cudaGetLastError());
+}
+template void vscale_dev_batch<double2>(int64_t, const VecBatch<double2, double2>&, const double*, int, cudaStream_t);
+template void vscale_dev_batch<float2>(int64_t, const VecBatch<float2, float2>&, const double*, int, cudaStream_t);
+
 }  // namespace sldm

@@ -145,4 +145,41 @@ void copy_blocks(const std::vector<BlockCopy>& copies, size_t esz, void* M, int6
 template <class C>
 void add_ix(const sldm_mesh* m, int obj, double alpha, const double* ix_val, void* K, int64_t ld, cudaStream_t s);
 
+// ---------------------------------------------------------------- GMRES on the device
+// Per right-hand side r of a lockstep GMRES cycle: iterations, columns in use,
+// whether it still iterates, ||b|| and the cycle's starting residual.
+struct GmresState {
+  int32_t it, kused, live, pad;
+  double bnorm, beta;
+};
+// Step k of the Arnoldi process for the na active right-hand sides on[j]:
+// column k of H_r from the two Gram-Schmidt passes (dh + r * ldh: coefficients
+// of pass one at [0, k], pass two at [m + 2, m + 2 + k]) and h_{k+1,k} =
+// sqrt(nrm[j]); the earlier Givens rotations, a new one annihilating h_{k+1,k},
+// the rotated residual vector g_r; then the convergence tests (|g_{k+1}| <=
+// tol ||b||, it >= maxit, h_{k+1,k} = 0, and with refine |g_{k+1}| <= cycle
+// beta) clear live.  scale[j] = 1 / h_{k+1,k} for the next basis vector (0 once
+// the right-hand side has stopped).  H: (m + 1) x m row-major per right-hand
+// side, cs, sn: m, g: m + 1 (complex).
+struct GivensArgs {
+  int k, m, na, refine;
+  const int* on;
+  const double2* dh;
+  int64_t ldh;
+  const double* nrm;
+  double2 *H, *cs, *sn, *g;
+  GmresState* st;
+  double tol, cycle;
+  int maxit, pad;
+  double* scale;
+};
+void gmres_givens(const GivensArgs& a, cudaStream_t s);
+// y_r = H_r^-1 g_r (upper triangular, kused_r columns) into dh + r * ldh, for the na
+// right-hand sides on[j] (one warp each).
+void gmres_backsolve(int na, const int* on, int m, const double2* H, const double2* g, const GmresState* st, double2* dh,
+                     int64_t ldh, cudaStream_t s);
+// y_j = scale[j] x_j (scale on the device), j < na, in place allowed
+template <class CB>
+void vscale_dev_batch(int64_t n, const VecBatch<CB, CB>& b, const double* scale, int na, cudaStream_t s);
+
 }  // namespace sldm
