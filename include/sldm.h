@@ -145,7 +145,10 @@ typedef struct {
   int64_t n_unknowns, ne, nt, nobj;
   int64_t device_bytes; /* device memory held by the operator */
   int32_t precision;
-  int32_t reserved;
+  int32_t tc_from;      /* complex64 operators: the smallest lockstep width whose
+                           products run on the tensor cores (9, 17, or 33 = never),
+                           chosen at assembly by timing both paths on the
+                           operator's own blocks; 0 otherwise */
   double k0;
 } sldm_op_info;
 
@@ -336,6 +339,15 @@ int sldm_launch_count(int64_t* out);
  * default) means no limit.  Buffers already held are not affected by a smaller
  * budget.  SLDM_EINVAL if bytes < 0. */
 int sldm_set_device_budget(int64_t bytes);
+/* Tensor-core policy of the complex64 products assembled from now on (no
+ * counterpart in the paper): 0 (default) measures, per operator, one pass on the
+ * tensor cores and as passes of 8 on the CUDA cores at 16 and 32 right-hand sides
+ * and sends lockstep widths from the winning point on to the tensor cores
+ * (sldm_op_info.tc_from), once per product shape in the process (later operators
+ * of the same shape reuse the decision); 1..33 forces that smallest width (33 =
+ * never).
+ * SLDM_EINVAL otherwise. */
+int sldm_set_tc_policy(int32_t tc_from);
 /* Bytes of device memory the library holds now (all handles, all devices). */
 int sldm_device_bytes(int64_t* in_use);
 

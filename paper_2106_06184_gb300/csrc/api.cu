@@ -194,7 +194,7 @@ static void make_plans(sldm_op* op, size_t es_m, size_t es_v, DBuf<GemvJob>& dj1
 }
 
 template <class C>
-static void build_plans(sldm_op* op) {
+static void build_plans(sldm_op* op, cudaStream_t s) {
   const int64_t ne = op->ne, nt = op->nt, nq = op->nq;
   const int WR = sldm_op::WR;
   const size_t ev = sizeof(double2);
@@ -207,6 +207,16 @@ static void build_plans(sldm_op* op) {
   const bool c64 = sizeof(C) == sizeof(float2);
   make_plans(op, sizeof(C), sizeof(C), op->jobs1, op->rs1, op->tl1, op->plan1, op->jobs2, op->rs2, op->tl2, op->plan2,
              c64 ? &op->tc1 : nullptr, c64 ? &op->tc2 : nullptr);
+  if (c64) {
+    // where the tensor cores start to beat passes of 8 on the CUDA cores, measured
+    // on this operator's own blocks (finite inputs: the work vectors zeroed)
+    for (DBuf<char>* w : {&op->wj, &op->we, &op->wu, &op->wt1, &op->wt2, &op->wa, &op->wc, &op->wbc, &op->wbu, &op->wz1,
+                          &op->wz2, &op->ww1, &op->ww2, &op->ww3})
+      w->zero(s);
+    gemv_autotune(op->plan1, s);
+    gemv_autotune(op->plan2, s);
+    SLDM_CUDA(cudaStreamSynchronize(s));
+  }
   if (sizeof(C) == sizeof(float2)) {
     make_plans(op, sizeof(C), sizeof(double2), op->jobs1d, op->rs1d, op->tl1d, op->plan1d, op->jobs2d, op->rs2d, op->tl2d,
                op->plan2d);
@@ -641,7 +651,7 @@ static void assemble_impl(sldm_op* op, const sldm_material* mats, cudaStream_t s
     SLDM_CUDA(cudaStreamSynchronize(s));
   }
   if (!finish) return;
-  build_plans<C>(op);
+  build_plans<C>(op, s);
   // ---- preconditioner P (Eq. pcext): diagonals and the per-object Schur complement inverses
   {
     std::vector<PrecObj> po;
@@ -674,7 +684,7 @@ static void split_to_x2(sldm_op* op, cudaStream_t s) {
   op->prec = SLDM_PREC_F32;
   op->esz = sizeof(float2);
   op->x2 = true;
-  build_plans<float2>(op);
+  build_plans<float2>(op, s);
   std::vector<PrecObj> po;
   for (auto& oi : op->obj) po.push_back({oi.e0, oi.ne, oi.t0, oi.nt, oi.q0, 0, oi.oLA, oi.oK, oi.oLP});
   prec_setup<float2>(op->pc, op->mesh, po, op->k0, op->LAm.p, op->LPm.p, op->loc.p, op->ix_val.p, s);
@@ -1184,6 +1194,7 @@ int sldm_op_info_get(const sldm_op* op, sldm_op_info* info) {
   info->nobj = op->nobj;
   info->device_bytes = op_bytes(op);
   info->precision = op->x2 ? SLDM_PREC_F32X2 : op->prec;
+  info->tc_from = op->prec == SLDM_PREC_F32 ? op->plan2.tc_from : 0;
   info->k0 = op->k0;
   API_END
 }

@@ -9,6 +9,9 @@
 //    Krylov basis' precision, batched over the lockstep right-hand sides.
 #include <algorithm>
 #include <atomic>
+#include <tuple>
+#include <mutex>
+#include <map>
 #include <type_traits>
 
 #include "dense.h"
@@ -968,7 +971,7 @@ void gemv_jobs_mixed(const GemvPlan& plan, int nrhs, cudaStream_t s) {
   constexpr bool comp = std::is_same<CM, float2>::value && std::is_same<CV, double2>::value;
   constexpr bool c64 = std::is_same<CM, float2>::value && std::is_same<CV, float2>::value;
   if constexpr (c64) {
-    if (nrhs > TILE_NRHS && plan.tc != nullptr && plan.tc->ok) {  // one tensor-core pass
+    if (nrhs >= plan.tc_from && plan.tc != nullptr && plan.tc->ok) {  // one tensor-core pass
       ScopedTimer tm(plan.name, s);
       timer_units(plan.name, plan.bytes);
       gemm_tc(plan, *plan.tc, nrhs, s);
@@ -1009,6 +1012,67 @@ void gemv_jobs_mixed(const GemvPlan& plan, int nrhs, cudaStream_t s) {
 template void gemv_jobs_mixed<float2, double2>(const GemvPlan&, int, cudaStream_t);
 template void gemv_jobs_mixed<float2, float2>(const GemvPlan&, int, cudaStream_t);
 template void gemv_jobs_mixed<double2, double2>(const GemvPlan&, int, cudaStream_t);
+
+static std::atomic<int> g_tc_force{0};  // sldm_set_tc_policy: 0 = measure, else the width to use
+
+// decisions by plan shape (jobs, rows, bytes streamed per pass): a shape is timed once per process
+static std::mutex g_tune_mu;
+static std::map<std::tuple<int, int64_t, double>, int> g_tuned;
+
+void gemv_autotune(GemvPlan& plan, cudaStream_t s) {
+  if (plan.njobs == 0 || plan.tc == nullptr || !plan.tc->ok) return;
+  if (const int f = g_tc_force.load()) {
+    plan.tc_from = f;
+    return;
+  }
+  const auto key = std::make_tuple(plan.njobs, plan.total_rows, plan.bytes);
+  {
+    std::lock_guard<std::mutex> l(g_tune_mu);
+    auto it = g_tuned.find(key);
+    if (it != g_tuned.end()) {
+      plan.tc_from = it->second;
+      return;
+    }
+  }
+  cudaEvent_t e0, e1;
+  SLDM_CUDA(cudaEventCreate(&e0));
+  SLDM_CUDA(cudaEventCreate(&e1));
+  auto timed = [&](int nrhs, int from) {
+    plan.tc_from = from;
+    gemv_jobs_mixed<float2, float2>(plan, nrhs, s);  // warm
+    float best = 1e30f;
+    for (int rep = 0; rep < 2; ++rep) {
+      SLDM_CUDA(cudaEventRecord(e0, s));
+      gemv_jobs_mixed<float2, float2>(plan, nrhs, s);
+      SLDM_CUDA(cudaEventRecord(e1, s));
+      SLDM_CUDA(cudaEventSynchronize(e1));
+      float ms = 0;
+      SLDM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      best = std::min(best, ms);
+    }
+    return best;
+  };
+  timers_mute(true);  // keep the tuning passes out of the kernel timers
+  float tc16 = 0, cc16 = 0, tc32 = 0, cc32 = 0;
+  try {
+    tc16 = timed(16, 1);
+    cc16 = timed(16, MAX_NRHS + 1);
+    tc32 = timed(32, 1);
+    cc32 = timed(32, MAX_NRHS + 1);
+  } catch (...) {
+    timers_mute(false);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    throw;
+  }
+  timers_mute(false);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  plan.tc_from = tc16 < cc16 ? TILE_NRHS + 1 : (tc32 < cc32 ? 2 * TILE_NRHS + 1 : MAX_NRHS + 1);
+  std::lock_guard<std::mutex> l(g_tune_mu);
+  g_tuned[key] = plan.tc_from;
+}
+
 
 template <class C>
 void gemv_jobs(const GemvPlan& plan, int nrhs, cudaStream_t s) {
@@ -1781,3 +1845,9 @@ template void vscale_dev_batch<double2>(int64_t, const VecBatch<double2, double2
 template void vscale_dev_batch<float2>(int64_t, const VecBatch<float2, float2>&, const double*, int, cudaStream_t);
 
 }  // namespace sldm
+
+extern "C" int sldm_set_tc_policy(int32_t tc_from) {
+  if (tc_from != 0 && (tc_from < 1 || tc_from > sldm::MAX_NRHS + 1)) return SLDM_EINVAL;
+  sldm::g_tc_force.store(tc_from);
+  return SLDM_OK;
+}

@@ -43,6 +43,11 @@ struct GemvJob {
   const void* Alo;
 };
 struct TcPlan;
+// right-hand sides in lockstep (GMRES) and per pass of the structured product
+// and the preconditioner: up to 32 (tensor cores for complex64 operators; the
+// CUDA-core kernels take 8 per launch)
+constexpr int MAX_NRHS = 32;
+constexpr int TILE_NRHS = 8;
 struct GemvPlan {
   const char* name = "gemv";   // timer name of its launches
   GemvJob* jobs = nullptr;     // device
@@ -61,12 +66,14 @@ struct GemvPlan {
   // complex64 blocks and vectors: the tensor-core plan for 9 to 32 right-hand
   // sides per pass (gemm_tc.h), or null / not ok for passes of 8 on the CUDA cores
   const TcPlan* tc = nullptr;
+  // smallest lockstep width sent to the tensor cores (set by gemv_autotune;
+  // 33 = never): below it, passes of 8 on the CUDA cores
+  int tc_from = TILE_NRHS + 1;
 };
 // right-hand sides in lockstep (GMRES) and per pass of the structured product
 // and the preconditioner: up to 32 (tensor cores for complex64 operators; the
 // CUDA-core kernels take 8 per launch)
-constexpr int MAX_NRHS = 32;
-constexpr int TILE_NRHS = 8;
+
 // rows per tile of the several-right-hand-side kernel for vectors of es_v bytes
 inline int gemv_tile_rows(size_t es_v) { return es_v == 8 ? 32 : 16; }
 template <class C>
@@ -74,6 +81,12 @@ void gemv_jobs(const GemvPlan& plan, int nrhs, cudaStream_t s);
 // complex64 matrix, complex128 vectors, FP64 accumulation
 template <class CM, class CV>
 void gemv_jobs_mixed(const GemvPlan& plan, int nrhs, cudaStream_t s);
+// Measures, on this plan's own blocks, one complex64 pass at 16 and at 32
+// right-hand sides on the tensor cores and as passes of 8 on the CUDA cores, and
+// sets plan.tc_from to where the tensor cores start to win (9, 17 or 33 =
+// never).  The plan's output vectors are overwritten; its inputs must hold
+// finite values (the caller zeroes them).
+void gemv_autotune(GemvPlan& plan, cudaStream_t s);
 
 struct ApplyDims {
   int32_t ne, nt, nq, nobj;

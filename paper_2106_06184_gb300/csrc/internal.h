@@ -33,6 +33,9 @@ struct Error {
 // Optional CUDA-event timing of named launches (sldm_timers_enable).  When
 // disabled, timer_begin/timer_end cost one branch.
 bool timers_on();
+// Mute (or unmute) the timers for the calling thread only: its launches are
+// left out of every timed name (autotuning passes).
+void timers_mute(bool m);
 // Counts kernel launches made by the library (sldm_launch_count); called right
 // after each launch statement.
 void count_launch();

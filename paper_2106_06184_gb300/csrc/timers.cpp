@@ -70,7 +70,9 @@ void resolve_locked() {
 }
 }  // namespace
 
-bool timers_on() { return g_on; }
+thread_local bool t_mute = false;  // this thread's launches are not timed (tuning passes)
+bool timers_on() { return g_on && !t_mute; }
+void timers_mute(bool m) { t_mute = m; }
 
 void timer_begin(const char* name, cudaStream_t s) {
   std::lock_guard<std::mutex> l(g_mu);
@@ -94,7 +96,7 @@ void timer_end(cudaStream_t s) {
 static std::map<std::string, double> g_units;
 void timer_units(const char* name, double units) {
   std::lock_guard<std::mutex> l(g_mu);
-  if (g_on) g_units[name] += units;
+  if (g_on && !t_mute) g_units[name] += units;
 }
 
 static std::atomic<int64_t> g_launches{0};

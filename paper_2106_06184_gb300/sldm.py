@@ -58,7 +58,7 @@ class SolveInfo(C.Structure):
 
 class OpInfo(C.Structure):
     _fields_ = [("n_unknowns", C.c_int64), ("ne", C.c_int64), ("nt", C.c_int64), ("nobj", C.c_int64),
-                ("device_bytes", C.c_int64), ("precision", C.c_int32), ("reserved", C.c_int32), ("k0", C.c_double)]
+                ("device_bytes", C.c_int64), ("precision", C.c_int32), ("tc_from", C.c_int32), ("k0", C.c_double)]
 
 
 class ServerOpts(C.Structure):
@@ -111,6 +111,7 @@ EXPORTS = {
     "sldm_launch_count": (C.c_int, [C.POINTER(C.c_int64)]),
     "sldm_timer_units": (C.c_int, [C.c_char_p, C.POINTER(C.c_double)]),
     "sldm_set_device_budget": (C.c_int, [C.c_int64]),
+    "sldm_set_tc_policy": (C.c_int, [C.c_int32]),
     "sldm_device_bytes": (C.c_int, [C.POINTER(C.c_int64)]),
     "sldm_test_inject": (C.c_int, [C.c_int32, C.c_int32]),
     "sldm_server_create": (C.c_int, [C.POINTER(ServerOpts), C.POINTER(C.c_void_p)]),
@@ -186,6 +187,12 @@ def launch_count(lib=None) -> int:
     n = C.c_int64()
     L.check(L.lib.sldm_launch_count(C.byref(n)))
     return n.value
+
+
+def set_tc_policy(tc_from=0, lib=None):
+    """0: the tensor-core crossover is measured per operator; else forced."""
+    L = lib or load()
+    L.check(L.lib.sldm_set_tc_policy(int(tc_from)))
 
 
 def set_device_budget(nbytes, lib=None):
@@ -319,6 +326,7 @@ class Operator:
         self.L.check(self.L.lib.sldm_op_info_get(h, C.byref(info)))
         self.N, self.ne, self.nt, self.nobj = info.n_unknowns, info.ne, info.nt, info.nobj
         self.k0, self.device_bytes, self.precision = info.k0, info.device_bytes, info.precision
+        self.tc_from = info.tc_from
 
     def block(self, which, obj=0):
         r, c = C.c_int64(), C.c_int64()

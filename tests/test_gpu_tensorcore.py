@@ -1,7 +1,9 @@
 """The tensor-core multi-RHS product (tcgen05, 3 x TF32 with FP32 accumulation)
 against the CUDA-core product of the same complex64 operator, through the C ABI.
 
-9 to 32 right-hand sides per pass go to the tensor cores: every block as a
+With the policy forced to 9 (sldm_set_tc_policy), 9 to 32 right-hand sides per
+pass go to the tensor cores (by default the crossover is measured per operator,
+checked last): every block as a
 real FP32 GEMM (complex64 storage read as interleaved FP32), 128-row tiles,
 K chunks of 32 FP32 columns, ragged rows and columns zero-filled by TMA.  The
 split into round-to-nearest TF32 high and low parts keeps FP32 accuracy: each
@@ -43,11 +45,15 @@ CASES = {
 }
 
 
-def _op(sl, name, prec):
+def _op(sl, name, prec, tc_from=9):
     xyz, tri, obj, mats, f = CASES[name]()
     m = sl.Mesh(xyz, tri, obj)
     st = sl.Stack([(1.0, 1.0, 0.0, 0.0)])
-    return sl.Operator(m, st, mats, f, precision=prec)
+    sl.set_tc_policy(tc_from)
+    try:
+        return sl.Operator(m, st, mats, f, precision=prec)
+    finally:
+        sl.set_tc_policy(0)
 
 
 @pytest.mark.parametrize("name", ["sphere", "two_lossy", "cyl4"])
@@ -133,3 +139,26 @@ def test_32_lockstep_solves_match_single_solves(prec):
         xr = np.zeros(op.N, complex)
         op.solve(np.ascontiguousarray(b[r]), xr, tol=1e-10)
         assert rel(x[r], xr) < 1e-7, (r, rel(x[r], xr))
+
+
+@pytest.mark.parametrize("name", ["sphere", "cyl4"])
+def test_autotuned_crossover(name):
+    """Default policy: the operator records the measured crossover (9, 17 or 33),
+    a 16-column product goes to the tensor cores exactly when the crossover says
+    so, and agrees with the forced tensor-core product to FP32 accuracy."""
+    sl = _sl()
+    op = _op(sl, name, 1, tc_from=0)
+    assert op.tc_from in (9, 17, 33)
+    forced = _op(sl, name, 1, tc_from=9)
+    assert forced.tc_from == 9
+    rng = np.random.default_rng(5)
+    X = np.ascontiguousarray(rng.standard_normal((16, op.N)) + 1j * rng.standard_normal((16, op.N)))
+    Y, Yf = np.zeros_like(X), np.zeros_like(X)
+    sl.timers_reset()
+    sl.timers_enable(True)
+    op.apply(X, Y, nrhs=16)
+    sl.timers_enable(False)
+    ran_tc = sl.timers_read().get("gemm_tc", (0, 0))[1] > 0
+    assert ran_tc == (op.tc_from <= 16)
+    forced.apply(X, Yf, nrhs=16)
+    assert rel(Y, Yf) < 4e-6
