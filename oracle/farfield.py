@@ -27,3 +27,40 @@ def rcs(mesh, k0, jd, theta, phi=0.0, E0=1.0):
         Fv += np.einsum('t,tq,atq,tqd->ad', c, wq, ph, fi)
     Fperp = Fv - rhat * np.einsum('ad,ad->a', rhat, Fv)[:, None]
     return ETA0 ** 2 * np.sum(np.abs(Fperp) ** 2, axis=1) / (4 * np.pi * abs(E0) ** 2)
+
+
+def rcs_layered(mesh, stack, layer, omega, jd, theta, phi=0.0, E0=1.0):
+    """Bistatic RCS above a stratified background (observation in the upper half-space).
+
+    By reciprocity, the far-field component along p of the current radiating in
+    layer `layer` of the stack is the current's reaction with the stack's total
+    field of a plane wave arriving from the observation direction rhat with
+    polarisation p (oracle.layered.incident_field with khat = -rhat): the
+    free-space factor exp(+j k0 rhat . r') p becomes that field.  With
+    F_p = sum_n j_Delta,n int f_n . E_(-rhat, p) dS' for p = theta-hat, phi-hat,
+    sigma = eta0^2 (|F_theta|^2 + |F_phi|^2) / (4 pi |E0|^2).  theta < pi/2."""
+    from . import layered as LY
+    theta = np.atleast_1d(np.asarray(theta, float))
+    phi = np.broadcast_to(np.asarray(phi, float), theta.shape)
+    if np.any(theta >= np.pi / 2):
+        raise ValueError("layered far field: observation directions in the upper half-space only")
+    A = mesh.xyz[mesh.tri]
+    rq = Q.points(A)
+    wq = Q.weights(mesh.area)
+    pts = rq.reshape(-1, 3)
+    out = np.zeros(len(theta))
+    for a, (th, ph) in enumerate(zip(theta, phi)):
+        rhat = np.array([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)])
+        that = np.array([np.cos(th) * np.cos(ph), np.cos(th) * np.sin(ph), -np.sin(th)])
+        phat = np.array([-np.sin(ph), np.cos(ph), 0.0])
+        s = 0.0
+        for p in (that, phat):
+            E = LY.incident_field(stack, layer, omega, -rhat, p, pts).reshape(rq.shape)   # (nt, 6, 3)
+            F = 0j
+            for i in range(3):
+                fi = (rq - A[:, i][:, None, :]) * (mesh.E.tri_sign[:, i] / (2 * mesh.area))[:, None, None]
+                c = jd[mesh.E.tri_edge[:, i]]
+                F += np.einsum('t,tq,tqd,tqd->', c, wq, fi, E)
+            s += abs(F) ** 2
+        out[a] = ETA0 ** 2 * s / (4 * np.pi * abs(E0) ** 2)
+    return out

@@ -394,3 +394,37 @@ def test_resting_cylinder_blocks_are_reciprocal():
     A = S.assemble(m, [S.Material(1.0)], st, F, layer=0, tables=T)
     x = S.solve(A, S.rhs(A, khat=[np.sin(0.3), 0, -np.cos(0.3)], pol=[0, 1.0, 0]))
     assert np.linalg.norm(S.j_delta(A, x)) <= 1e-9 * np.linalg.norm(x[:m.ne])
+
+
+def test_layered_rcs_reductions():
+    """The far field above a stack: identical layers give the free-space RCS, and
+    a sphere over a PEC ground radiates in the upper half-space like the sphere and
+    its mirror image in free space (same solutions as the image-pair pin above)."""
+    from oracle import farfield
+    f, h, rad = 300e6, 0.15, 0.1
+    w = 2 * np.pi * f
+    th = np.radians([0.0, 20.0, 45.0, 70.0, 85.0])
+    v, fc = icosphere(1, rad, (0.0, 0.0, h))
+    m = Mesh(v, fc)
+    same = LY.Stack([(1.0, 1.0, 0.0, np.inf), (1.0, 1.0, 0.0, 0.1), (1.0, 1.0, 0.0, np.inf)], z_top=0.0)
+    A = S.assemble(m, [S.Material(4.0)], S.Material(), f)
+    jd = S.j_delta(A, S.solve(A, S.rhs(A)))
+    ref = farfield.rcs(m, A.k0, jd, th)
+    got = farfield.rcs_layered(m, same, 0, w, jd, th)
+    assert np.max(np.abs(got - ref) / ref) < 1e-12
+    got = farfield.rcs_layered(m, same, 0, w, jd, th, phi=np.pi / 3)
+    assert np.max(np.abs(got - farfield.rcs(m, A.k0, jd, th, phi=np.pi / 3)) / ref.max()) < 1e-12
+    # sphere over PEC vs the image pair in free space
+    st = LY.Stack([(1.0, 1.0, 0.0, np.inf)], z_top=0.0, bottom="pec")
+    A = S.assemble(m, [S.Material(4.0)], st, f, layer=0)
+    x = S.solve(A, S.rhs(A))
+    vi = v.copy()
+    vi[:, 2] *= -1
+    xyz, tri, obj = merge((v, fc), (vi, fc[:, ::-1].copy()))
+    m2 = Mesh(xyz, tri, obj)
+    A2 = S.assemble(m2, [S.Material(4.0)] * 2, S.Material(), f)
+    x2 = S.solve(A2, S.rhs(A2, khat=(0, 0, -1)) - S.rhs(A2, khat=(0, 0, 1)))
+    for ph in (0.0, 1.1):
+        ref = farfield.rcs(m2, A2.k0, S.j_delta(A2, x2), th, phi=ph)
+        got = farfield.rcs_layered(m, st, 0, w, S.j_delta(A, x), th, phi=ph)
+        assert np.max(np.abs(got - ref) / ref.max()) < 1e-9, (ph, got, ref)
