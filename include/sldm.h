@@ -270,10 +270,19 @@ int sldm_rhs_planewave(const sldm_op* op, const double* khat, const double* pol,
 int sldm_solve(const sldm_op* op, const void* b, void* x, int32_t nrhs, const sldm_solve_opts* opts,
                sldm_solve_info* info, int32_t where, void* stream);
 
-/* Bistatic radar cross section (m^2) of the solution x (N complex128, `where`)
- * in free space: the equivalent current J_Delta = H - H_eq radiating in the
- * background (Sec. IV-A).  theta, phi, rcs: n doubles, host.  SLDM_ENOTSUP for
- * stratified backgrounds. */
+/* Bistatic radar cross section (m^2) of the solution x (N complex128, `where`):
+ * the equivalent current J_Delta = H - H_eq radiating in the background (Sec.
+ * IV-A).  theta, phi, rcs: n doubles, host.  Above a stratified background the
+ * observation directions must lie in the upper half-space (0 <= theta < pi/2,
+ * else SLDM_EINVAL) and the far field follows by reciprocity: each component is
+ * the current's reaction with the stack's plane wave (sldm_rhs_planewave's field)
+ * arriving from the observation direction with that polarisation,
+ * sigma = eta0^2 (|F_theta|^2 + |F_phi|^2) / (4 pi). */
+/* The same for nrhs solutions at once (x: N x nrhs complex128, column-major;
+ * rcs: n x nrhs, column-major, host): the phase factors or the stack's waves at
+ * each quadrature point are shared by the right-hand sides. */
+int sldm_farfield_n(const sldm_op* op, const void* x, int32_t nrhs, int32_t where, const double* theta,
+                    const double* phi, int32_t n, double* rcs);
 int sldm_farfield(const sldm_op* op, const void* x, int32_t where, const double* theta,
                   const double* phi, int32_t n, double* rcs);
 

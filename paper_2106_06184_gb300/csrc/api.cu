@@ -1404,46 +1404,77 @@ int sldm_solve(const sldm_op* op_, const void* b, void* x, int32_t nrhs, const s
   API_END
 }
 
-int sldm_farfield(const sldm_op* op_, const void* x, int32_t where, const double* theta, const double* phi, int32_t n,
-                  double* rcs) {
+int sldm_farfield_n(const sldm_op* op_, const void* x, int32_t nrhs, int32_t where, const double* theta, const double* phi,
+                    int32_t n, double* rcs) {
   API_BEGIN
-  SLDM_REQUIRE(op_ && x && theta && phi && rcs && n >= 1, SLDM_EINVAL, "farfield: invalid arguments");
-  SLDM_REQUIRE(!op_->layered, SLDM_ENOTSUP, "farfield: free-space far field only (homogeneous background)");
+  SLDM_REQUIRE(op_ && x && theta && phi && rcs && n >= 1 && nrhs >= 1, SLDM_EINVAL, "farfield: invalid arguments");
   sldm_op* op = const_cast<sldm_op*>(op_);
+  if (op->layered)
+    for (int i = 0; i < n; ++i)
+      SLDM_REQUIRE(theta[i] >= 0 && theta[i] < 0.5 * PI_, SLDM_EINVAL,
+                   "farfield: above a stack, observation directions in the upper half-space only (theta < pi/2)");
   cudaStream_t s = 0;
   ScopedTimer tm("farfield", s);
+  const int WR = sldm_op::WR;
+  const int nr_pass = std::min(nrhs, WR);
   DBuf<double2> dx, jd;
-  dx.alloc(op->N);
-  jd.alloc(op->ne);
-  SLDM_CUDA(cudaMemcpyAsync(dx.p, x, op->N * sizeof(double2),
-                            where == SLDM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
-  // j_Delta = j - Y11 e (per object), from the first two stages of the structured product
+  dx.alloc(size_t(op->N) * nr_pass);
+  jd.alloc(size_t(op->ne) * nrhs);
   ApplyDims D{int32_t(op->ne), int32_t(op->nt), int32_t(op->nq), int32_t(op->nobj)};
-  if (op->prec == SLDM_PREC_F32) {
-    apply_glue_split<float2>(dx.p, op->N, D, op->wj.p, op->we.p, op->wu.p, 1, s);
-    gemv_jobs<float2>(op->plan1, 1, s);
-    apply_glue_prep<float2>(op->mesh, D, op->wj.p, op->wu.p, op->wt1.p, op->wt2.p, op->wa.p, op->wc.p, op->wbc.p,
-                            op->wbu.p, 1, s, op->mesh->d.tri_begin.p, op->mesh->d.edge_begin.p);
-    to_c128<float2>(op->wa.p, op->ne, jd.p, s);
-  } else {
-    apply_glue_split<double2>(dx.p, op->N, D, op->wj.p, op->we.p, op->wu.p, 1, s);
-    gemv_jobs<double2>(op->plan1, 1, s);
-    apply_glue_prep<double2>(op->mesh, D, op->wj.p, op->wu.p, op->wt1.p, op->wt2.p, op->wa.p, op->wc.p, op->wbc.p,
-                             op->wbu.p, 1, s, op->mesh->d.tri_begin.p, op->mesh->d.edge_begin.p);
-    to_c128<double2>(op->wa.p, op->ne, jd.p, s);
-  }
-  std::vector<double> ang(2 * size_t(n));
-  for (int i = 0; i < n; ++i) {
-    ang[2 * i] = theta[i];
-    ang[2 * i + 1] = phi[i];
+  // j_Delta = j - Y11 e (per object), from the first two stages of the structured product
+  for (int r0 = 0; r0 < nrhs; r0 += WR) {
+    const int nr = std::min(WR, nrhs - r0);
+    const size_t bytes = size_t(op->N) * nr * sizeof(double2);
+    const char* xs = static_cast<const char*>(x) + size_t(op->N) * r0 * sizeof(double2);
+    SLDM_CUDA(cudaMemcpyAsync(dx.p, xs, bytes, where == SLDM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    if (op->prec == SLDM_PREC_F32) {
+      apply_glue_split<float2>(dx.p, op->N, D, op->wj.p, op->we.p, op->wu.p, nr, s);
+      gemv_jobs<float2>(op->plan1, nr, s);
+      apply_glue_prep<float2>(op->mesh, D, op->wj.p, op->wu.p, op->wt1.p, op->wt2.p, op->wa.p, op->wc.p, op->wbc.p,
+                              op->wbu.p, nr, s, op->mesh->d.tri_begin.p, op->mesh->d.edge_begin.p);
+      to_c128<float2>(op->wa.p, int64_t(op->ne) * nr, jd.p + int64_t(op->ne) * r0, s);
+    } else {
+      apply_glue_split<double2>(dx.p, op->N, D, op->wj.p, op->we.p, op->wu.p, nr, s);
+      gemv_jobs<double2>(op->plan1, nr, s);
+      for (const auto& u : op->nested)  // objects whose Y E comes from inner solves
+        nested_apply(*u, op->wnt.p, op->wny.p, op->wnr.p, op->ldn, reinterpret_cast<double2*>(op->wt1.p), op->ne,
+                     reinterpret_cast<double2*>(op->wt2.p), op->nq, nr, op->mesh->h.ell, s);
+      apply_glue_prep<double2>(op->mesh, D, op->wj.p, op->wu.p, op->wt1.p, op->wt2.p, op->wa.p, op->wc.p, op->wbc.p,
+                               op->wbu.p, nr, s, op->mesh->d.tri_begin.p, op->mesh->d.edge_begin.p);
+      to_c128<double2>(op->wa.p, int64_t(op->ne) * nr, jd.p + int64_t(op->ne) * r0, s);
+    }
   }
   DBuf<double> da, dr;
-  da.upload(ang, s);
-  dr.alloc(n);
-  farfield(op->mesh, op->k0, jd.p, da.p, n, dr.p, s);
-  SLDM_CUDA(cudaMemcpyAsync(rcs, dr.p, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+  dr.alloc(size_t(n) * nrhs);
+  if (op->layered) {
+    // reciprocity: the stack's theta- and phi-polarised waves arriving from each direction
+    std::vector<double> rec(size_t(2) * n * PW_REC);
+    for (int i = 0; i < n; ++i) {
+      const double st = std::sin(theta[i]), ct = std::cos(theta[i]), sp = std::sin(phi[i]), cp = std::cos(phi[i]);
+      const double khat[3] = {-st * cp, -st * sp, -ct};
+      const double pt[3] = {ct * cp, ct * sp, -st}, pp[3] = {-sp, cp, 0.0};
+      mgf_plane_wave(op->H, op->thick, op->z_top, 2 * PI_ * op->freq, khat, pt, rec.data() + size_t(2 * i) * PW_REC);
+      mgf_plane_wave(op->H, op->thick, op->z_top, 2 * PI_ * op->freq, khat, pp, rec.data() + size_t(2 * i + 1) * PW_REC);
+    }
+    da.upload(rec, s);
+    farfield_layered(op->mesh, jd.p, op->ne, nrhs, da.p, n, dr.p, s);
+  } else {
+    std::vector<double> ang(2 * size_t(n));
+    for (int i = 0; i < n; ++i) {
+      ang[2 * i] = theta[i];
+      ang[2 * i + 1] = phi[i];
+    }
+    da.upload(ang, s);
+    farfield(op->mesh, op->k0, jd.p, op->ne, nrhs, da.p, n, dr.p, s);
+  }
+  SLDM_CUDA(cudaMemcpyAsync(rcs, dr.p, size_t(n) * nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
   SLDM_CUDA(cudaStreamSynchronize(s));
   API_END
+}
+
+int sldm_farfield(const sldm_op* op, const void* x, int32_t where, const double* theta, const double* phi, int32_t n,
+                  double* rcs) {
+  return sldm_farfield_n(op, x, 1, where, theta, phi, n, rcs);
 }
 
 }  // extern "C"

@@ -849,6 +849,37 @@ __global__ void rhs_kernel(int ne, int nrhs, double k0, const double* __restrict
 // Plane wave through a stack, in the objects' layer (record layout PW_*):
 // E = e^{-j kt.r} [phi V_TE + rho V_TM + z (|kt| / k_z)(a_TM e^+ - c_TM e^-)],
 // V = a e^+ + c e^-, e^{+-} = e^{+-j k_z (z - zref)}, phi = z x rho.
+__device__ void stack_wave(const double* __restrict__ P, const double x[3], double er[3], double ei[3]) {
+  const double ktx = P[PW_KT], kty = P[PW_KT + 1], rx = P[PW_RHO], ry = P[PW_RHO + 1];
+  const double px = -ry, py = rx;
+  const double kr = P[PW_KZ], ki = P[PW_KZ + 1];
+  const double kn = kr * kr + ki * ki;
+  const double qr = P[PW_KRHO] * kr / kn, qi = -P[PW_KRHO] * ki / kn;  // |kt| / k_z
+  const double dz = x[2] - P[PW_ZREF];
+  // e^{+j k_z dz} = e^{-ki dz} (cos(kr dz) + j sin(kr dz)),  e^{-j k_z dz} = e^{ki dz} (cos - j sin)
+  double sn, cn;
+  sincos(kr * dz, &sn, &cn);
+  const double ep = exp(-ki * dz), em = exp(ki * dz);
+  const double ur = ep * cn, ui = ep * sn, vr = em * cn, vi = -em * sn;
+  const double ater = P[PW_A], atei = P[PW_A + 1], cter = P[PW_A + 2], ctei = P[PW_A + 3];
+  const double atmr = P[PW_A + 4], atmi = P[PW_A + 5], ctmr = P[PW_A + 6], ctmi = P[PW_A + 7];
+  const double vte_r = ater * ur - atei * ui + cter * vr - ctei * vi;
+  const double vte_i = ater * ui + atei * ur + cter * vi + ctei * vr;
+  const double vtm_r = atmr * ur - atmi * ui + ctmr * vr - ctmi * vi;
+  const double vtm_i = atmr * ui + atmi * ur + ctmr * vi + ctmi * vr;
+  const double dr = atmr * ur - atmi * ui - (ctmr * vr - ctmi * vi);
+  const double di = atmr * ui + atmi * ur - (ctmr * vi + ctmi * vr);
+  const double ez_r = qr * dr - qi * di, ez_i = qr * di + qi * dr;
+  double sl, cl;  // e^{-j kt.r}
+  sincos(ktx * x[0] + kty * x[1], &sl, &cl);
+  const double fr[3] = {px * vte_r + rx * vtm_r, py * vte_r + ry * vtm_r, ez_r};
+  const double fi[3] = {px * vte_i + rx * vtm_i, py * vte_i + ry * vtm_i, ez_i};
+  for (int d = 0; d < 3; ++d) {
+    er[d] = fr[d] * cl + fi[d] * sl;
+    ei[d] = fi[d] * cl - fr[d] * sl;
+  }
+}
+
 __global__ void rhs_layered_kernel(int ne, const double* __restrict__ rec, const int32_t* __restrict__ tplus,
                                    const int32_t* __restrict__ tminus, const int32_t* __restrict__ tri_edge,
                                    const double* __restrict__ geo, double2* b, int64_t ld) {
@@ -856,45 +887,21 @@ __global__ void rhs_layered_kernel(int ne, const double* __restrict__ rec, const
   int r = blockIdx.y;
   if (m >= ne) return;
   const double* P = rec + size_t(r) * PW_REC;
-  const double ktx = P[PW_KT], kty = P[PW_KT + 1], rx = P[PW_RHO], ry = P[PW_RHO + 1];
-  const double px = -ry, py = rx;
-  const double2 ate = make_double2(P[PW_A], P[PW_A + 1]), cte = make_double2(P[PW_A + 2], P[PW_A + 3]);
-  const double2 atm = make_double2(P[PW_A + 4], P[PW_A + 5]), ctm = make_double2(P[PW_A + 6], P[PW_A + 7]);
-  const double kr = P[PW_KZ], ki = P[PW_KZ + 1], zref = P[PW_ZREF];
-  // |kt| / k_z
-  const double kn = kr * kr + ki * ki;
-  const double qr = P[PW_KRHO] * kr / kn, qi = -P[PW_KRHO] * ki / kn;
   double acc_r = 0, acc_i = 0;
   for (int side = 0; side < 2; ++side) {
     int t = side == 0 ? tplus[m] : tminus[m];
     const double* g = geo + size_t(t) * GEO_STRIDE;
     int i = tri_edge[3 * t] == m ? 0 : (tri_edge[3 * t + 1] == m ? 1 : 2);
     for (int q = 0; q < 6; ++q) {
-      double f[3], x[3];
+      double f[3], x[3], er[3], ei[3];
       for (int d = 0; d < 3; ++d) {
         f[d] = g[GEO_SIG + i] * (g[GEO_RHO + 3 * q + d] + g[GEO_AV + 3 * i + d]);
         x[d] = g[GEO_C + d] + g[GEO_RHO + 3 * q + d];
       }
-      const double dz = x[2] - zref;
-      // e^{+j k_z dz} = e^{-ki dz} (cos(kr dz) + j sin(kr dz)),  e^{-j k_z dz} = e^{ki dz} (cos - j sin)
-      double sn, cn;
-      sincos(kr * dz, &sn, &cn);
-      const double ep = exp(-ki * dz), em = exp(ki * dz);
-      const double ur = ep * cn, ui = ep * sn, vr = em * cn, vi = -em * sn;
-      const double vte_r = ate.x * ur - ate.y * ui + cte.x * vr - cte.y * vi;
-      const double vte_i = ate.x * ui + ate.y * ur + cte.x * vi + cte.y * vr;
-      const double vtm_r = atm.x * ur - atm.y * ui + ctm.x * vr - ctm.y * vi;
-      const double vtm_i = atm.x * ui + atm.y * ur + ctm.x * vi + ctm.y * vr;
-      const double dr = atm.x * ur - atm.y * ui - (ctm.x * vr - ctm.y * vi);
-      const double di = atm.x * ui + atm.y * ur - (ctm.x * vi + ctm.y * vr);
-      const double ez_r = qr * dr - qi * di, ez_i = qr * di + qi * dr;
-      const double fp = f[0] * px + f[1] * py, fr = f[0] * rx + f[1] * ry;
-      const double sr = fp * vte_r + fr * vtm_r + f[2] * ez_r, si = fp * vte_i + fr * vtm_i + f[2] * ez_i;
-      double sl, cl;  // e^{-j kt.r}
-      sincos(ktx * x[0] + kty * x[1], &sl, &cl);
+      stack_wave(P, x, er, ei);
       const double w = g[GEO_W + q] / ETA0;
-      acc_r += w * (sr * cl + si * sl);
-      acc_i += w * (si * cl - sr * sl);
+      acc_r += w * (f[0] * er[0] + f[1] * er[1] + f[2] * er[2]);
+      acc_i += w * (f[0] * ei[0] + f[1] * ei[1] + f[2] * ei[2]);
     }
   }
   b[int64_t(r) * ld + m] = make_double2(acc_r, acc_i);
@@ -916,13 +923,44 @@ void rhs_planewave(const sldm_mesh* m, double k0, const double* kp, int nrhs, do
 }
 
 // ---------------------------------------------------------------- far field / RCS
-// F = sum_m jd_m int f_m exp(+j k0 rhat . r); sigma = eta0^2 |(I - rr) F|^2 / (4 pi)
-__global__ void farfield_kernel(int nt, double k0, const double2* __restrict__ jd, const int32_t* __restrict__ tri_edge,
-                                const double* __restrict__ geo, const double* __restrict__ ang, double* rcs) {
-  const int a = blockIdx.x;
+// Right-hand sides per CTA of the far-field kernels: the phase factors (or the
+// stack's waves) at a quadrature point are computed once for all of them.
+constexpr int FF_NR = 8;
+constexpr int FF_THREADS = 128;
+
+// Sum of NV per-thread values over the CTA (warp shuffles, then one value per
+// warp in shared memory); the totals land in out[] of thread 0.
+template <int NV>
+__device__ __forceinline__ void ff_reduce(double* v, double (*sh)[NV], double* out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int c = 0; c < NV; ++c) {
+    double x = v[c];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (lane == 0) sh[warp][c] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int c = 0; c < NV; ++c) {
+      double x = 0;
+      for (int w = 0; w < FF_THREADS / 32; ++w) x += sh[w][c];
+      out[c] = x;
+    }
+}
+
+// F_r = sum_m jd_r,m int f_m exp(+j k0 rhat . r); sigma = eta0^2 |(I - rr) F_r|^2 / (4 pi)
+// CTA (a, g): angle a, right-hand sides [g FF_NR, g FF_NR + cnt); jd column r at jd + r ldj
+__global__ void __launch_bounds__(FF_THREADS) farfield_kernel(int nt, double k0, const double2* __restrict__ jd, int64_t ldj,
+                                                              int nr, const int32_t* __restrict__ tri_edge,
+                                                              const double* __restrict__ geo, const double* __restrict__ ang,
+                                                              int n, double* rcs) {
+  const int a = blockIdx.x, r0 = blockIdx.y * FF_NR;
+  const int cnt = min(FF_NR, nr - r0);
   const double th = ang[2 * a], ph = ang[2 * a + 1];
   const double rh[3] = {sin(th) * cos(ph), sin(th) * sin(ph), cos(th)};
-  double F[6] = {0, 0, 0, 0, 0, 0};
+  double F[6 * FF_NR];
+#pragma unroll
+  for (int c = 0; c < 6 * FF_NR; ++c) F[c] = 0;
   for (int t = threadIdx.x; t < nt; t += blockDim.x) {
     const double* g = geo + size_t(t) * GEO_STRIDE;
     for (int q = 0; q < 6; ++q) {
@@ -931,45 +969,109 @@ __global__ void farfield_kernel(int nt, double k0, const double2* __restrict__ j
       double sn, cn;
       sincos(k0 * pr, &sn, &cn);
       for (int i = 0; i < 3; ++i) {
-        double2 c = jd[tri_edge[3 * t + i]];
-        double wr = g[GEO_W + q] * g[GEO_SIG + i];
-        // c * exp(+j k0 rhat.r)
-        double er = (c.x * cn - c.y * sn) * wr, ei = (c.x * sn + c.y * cn) * wr;
-        for (int d = 0; d < 3; ++d) {
-          double f = g[GEO_RHO + 3 * q + d] + g[GEO_AV + 3 * i + d];
-          F[2 * d] += er * f;
-          F[2 * d + 1] += ei * f;
+        const int e = tri_edge[3 * t + i];
+        const double wr = g[GEO_W + q] * g[GEO_SIG + i];
+        double f[3];
+        for (int d = 0; d < 3; ++d) f[d] = g[GEO_RHO + 3 * q + d] + g[GEO_AV + 3 * i + d];
+#pragma unroll
+        for (int r = 0; r < FF_NR; ++r) {
+          if (r >= cnt) break;
+          const double2 c = jd[int64_t(r0 + r) * ldj + e];
+          // c exp(+j k0 rhat.r)
+          const double er = (c.x * cn - c.y * sn) * wr, ei = (c.x * sn + c.y * cn) * wr;
+          for (int d = 0; d < 3; ++d) {
+            F[6 * r + 2 * d] += er * f[d];
+            F[6 * r + 2 * d + 1] += ei * f[d];
+          }
         }
       }
     }
   }
-  __shared__ double sh[6][256];
-  for (int c = 0; c < 6; ++c) sh[c][threadIdx.x] = F[c];
-  __syncthreads();
-  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w)
-      for (int c = 0; c < 6; ++c) sh[c][threadIdx.x] += sh[c][threadIdx.x + w];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    double fr[3], fi[3];
+  __shared__ double sh[FF_THREADS / 32][6 * FF_NR];
+  __shared__ double tot[6 * FF_NR];
+  ff_reduce<6 * FF_NR>(F, sh, tot);
+  if (threadIdx.x != 0) return;
+  for (int r = 0; r < cnt; ++r) {
+    const double* fr = tot + 6 * r;
+    const double dr = rh[0] * fr[0] + rh[1] * fr[2] + rh[2] * fr[4];
+    const double di = rh[0] * fr[1] + rh[1] * fr[3] + rh[2] * fr[5];
+    double s2 = 0;
     for (int d = 0; d < 3; ++d) {
-      fr[d] = sh[2 * d][0];
-      fi[d] = sh[2 * d + 1][0];
+      const double pr_ = fr[2 * d] - rh[d] * dr, pi_ = fr[2 * d + 1] - rh[d] * di;
+      s2 += pr_ * pr_ + pi_ * pi_;
     }
-    double dr = rh[0] * fr[0] + rh[1] * fr[1] + rh[2] * fr[2];
-    double di = rh[0] * fi[0] + rh[1] * fi[1] + rh[2] * fi[2];
-    double s = 0;
-    for (int d = 0; d < 3; ++d) {
-      double pr_ = fr[d] - rh[d] * dr, pi_ = fi[d] - rh[d] * di;
-      s += pr_ * pr_ + pi_ * pi_;
-    }
-    rcs[a] = ETA0 * ETA0 * s / (4 * PI);
+    rcs[int64_t(r0 + r) * n + a] = ETA0 * ETA0 * s2 / (4 * PI);
   }
 }
 
-void farfield(const sldm_mesh* m, double k0, const double2* jd, const double* ang, int n, double* rcs, cudaStream_t s) {
-  farfield_kernel<<<n, 256, 0, s>>>(int(m->h.nt), k0, jd, m->d.tri_edge.p, m->d.geo.p, ang, rcs), ::sldm::count_launch();
+void farfield(const sldm_mesh* m, double k0, const double2* jd, int64_t ldj, int nr, const double* ang, int n, double* rcs,
+              cudaStream_t s) {
+  farfield_kernel<<<dim3(n, (nr + FF_NR - 1) / FF_NR), FF_THREADS, 0, s>>>(int(m->h.nt), k0, jd, ldj, nr, m->d.tri_edge.p,
+                                                                           m->d.geo.p, ang, n, rcs),
+      ::sldm::count_launch();
+  SLDM_CUDA(cudaGetLastError());
+}
+
+// Far field above a stack: for angle a, the reaction of the currents with the
+// stack's plane waves arriving from the observation direction, theta- and
+// phi-polarised (records rec[2a], rec[2a + 1]);  sigma = eta0^2 (|F_t|^2 + |F_p|^2) / (4 pi)
+__global__ void __launch_bounds__(FF_THREADS) farfield_layered_kernel(int nt, const double2* __restrict__ jd, int64_t ldj,
+                                                                      int nr, const int32_t* __restrict__ tri_edge,
+                                                                      const double* __restrict__ geo,
+                                                                      const double* __restrict__ rec, int n, double* rcs) {
+  const int a = blockIdx.x, r0 = blockIdx.y * FF_NR;
+  const int cnt = min(FF_NR, nr - r0);
+  const double* P0 = rec + size_t(2 * a) * PW_REC;
+  const double* P1 = P0 + PW_REC;
+  double F[4 * FF_NR];
+#pragma unroll
+  for (int c = 0; c < 4 * FF_NR; ++c) F[c] = 0;
+  for (int t = threadIdx.x; t < nt; t += blockDim.x) {
+    const double* g = geo + size_t(t) * GEO_STRIDE;
+    for (int q = 0; q < 6; ++q) {
+      double x[3];
+      for (int d = 0; d < 3; ++d) x[d] = g[GEO_C + d] + g[GEO_RHO + 3 * q + d];
+      double e0r[3], e0i[3], e1r[3], e1i[3];
+      stack_wave(P0, x, e0r, e0i);
+      stack_wave(P1, x, e1r, e1i);
+      for (int i = 0; i < 3; ++i) {
+        const int e = tri_edge[3 * t + i];
+        const double w = g[GEO_W + q] * g[GEO_SIG + i];
+        double p0r = 0, p0i = 0, p1r = 0, p1i = 0;  // f_i . E_p
+        for (int d = 0; d < 3; ++d) {
+          const double f = g[GEO_RHO + 3 * q + d] + g[GEO_AV + 3 * i + d];
+          p0r += f * e0r[d];
+          p0i += f * e0i[d];
+          p1r += f * e1r[d];
+          p1i += f * e1i[d];
+        }
+#pragma unroll
+        for (int r = 0; r < FF_NR; ++r) {
+          if (r >= cnt) break;
+          const double2 c = jd[int64_t(r0 + r) * ldj + e];
+          F[4 * r] += w * (c.x * p0r - c.y * p0i);
+          F[4 * r + 1] += w * (c.x * p0i + c.y * p0r);
+          F[4 * r + 2] += w * (c.x * p1r - c.y * p1i);
+          F[4 * r + 3] += w * (c.x * p1i + c.y * p1r);
+        }
+      }
+    }
+  }
+  __shared__ double sh[FF_THREADS / 32][4 * FF_NR];
+  __shared__ double tot[4 * FF_NR];
+  ff_reduce<4 * FF_NR>(F, sh, tot);
+  if (threadIdx.x != 0) return;
+  for (int r = 0; r < cnt; ++r) {
+    const double* fr = tot + 4 * r;
+    rcs[int64_t(r0 + r) * n + a] = ETA0 * ETA0 * (fr[0] * fr[0] + fr[1] * fr[1] + fr[2] * fr[2] + fr[3] * fr[3]) / (4 * PI);
+  }
+}
+
+void farfield_layered(const sldm_mesh* m, const double2* jd, int64_t ldj, int nr, const double* rec, int n, double* rcs,
+                      cudaStream_t s) {
+  farfield_layered_kernel<<<dim3(n, (nr + FF_NR - 1) / FF_NR), FF_THREADS, 0, s>>>(int(m->h.nt), jd, ldj, nr, m->d.tri_edge.p,
+                                                                                   m->d.geo.p, rec, n, rcs),
+      ::sldm::count_launch();
   SLDM_CUDA(cudaGetLastError());
 }
 

@@ -235,8 +235,14 @@ void rhs_planewave(const sldm_mesh* m, double k0, const double* khat_pol_dev, in
 constexpr int PW_KT = 0, PW_RHO = 2, PW_A = 4, PW_KZ = 12, PW_KRHO = 14, PW_ZREF = 15, PW_REC = 16;
 // e_inc in the objects' layer of a stack for nrhs plane waves (records rec_dev, PW_REC doubles each)
 void rhs_planewave_layered(const sldm_mesh* m, const double* rec_dev, int nrhs, double2* b, int64_t ld, cudaStream_t s);
-// far field vector F(theta, phi) of RWG coefficients jd (complex128) -> rcs (double), device
-void farfield(const sldm_mesh* m, double k0, const double2* jd, const double* ang_dev, int n, double* rcs,
-              cudaStream_t s);
+// RCS above a stack: per angle the theta- and phi-polarised plane-wave records
+// (2n records of PW_REC doubles, device) of waves arriving from the observation
+// direction; jd: nr columns of complex128 RWG coefficients (stride ldj), rcs:
+// n x nr (stride n), device
+void farfield_layered(const sldm_mesh* m, const double2* jd, int64_t ldj, int nr, const double* rec_dev, int n, double* rcs,
+                      cudaStream_t s);
+// far field in free space: angles (theta, phi) pairs, device; jd, rcs as above
+void farfield(const sldm_mesh* m, double k0, const double2* jd, int64_t ldj, int nr, const double* ang_dev, int n,
+              double* rcs, cudaStream_t s);
 
 }  // namespace sldm

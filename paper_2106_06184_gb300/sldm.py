@@ -103,6 +103,8 @@ EXPORTS = {
     "sldm_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.POINTER(SolveOpts),
                              C.POINTER(SolveInfo), C.c_int32, C.c_void_p]),
     "sldm_farfield": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
+    "sldm_farfield_n": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32,
+                                  C.c_void_p]),
     "sldm_kbar_noalloc": (C.c_int, [C.c_void_p, C.c_int32, C.c_double, C.c_double, C.c_void_p, C.c_void_p]),
     "sldm_timers_enable": (C.c_int, [C.c_int32]),
     "sldm_timers_reset": (C.c_int, []),
@@ -389,6 +391,17 @@ class Operator:
         self.L.check(self.L.lib.sldm_farfield(self.h, px, wx, theta.ctypes.data_as(C.c_void_p),
                                               phi.ctypes.data_as(C.c_void_p), len(theta),
                                               out.ctypes.data_as(C.c_void_p)))
+        return out
+
+    def farfield_n(self, x, theta, phi, nrhs):
+        """RCS of nrhs solutions x (nrhs, N) at once: (nrhs, len(theta))."""
+        theta = np.ascontiguousarray(theta, np.float64)
+        phi = np.ascontiguousarray(np.broadcast_to(phi, theta.shape), np.float64)
+        out = np.zeros((nrhs, len(theta)))
+        px, wx = _ptr(x)
+        self.L.check(self.L.lib.sldm_farfield_n(self.h, px, nrhs, wx, theta.ctypes.data_as(C.c_void_p),
+                                                phi.ctypes.data_as(C.c_void_p), len(theta),
+                                                out.ctypes.data_as(C.c_void_p)))
         return out
 
     def close(self):

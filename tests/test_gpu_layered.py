@@ -123,10 +123,11 @@ def test_layered_tables_match_oracle(in_slab):
 def test_layered_fp32_and_invalid_cases(in_slab, over_pec):
     sl, m, st, op = in_slab.gpu(1)
     assert relmax(op.block(sl.BLOCK_LAM), in_slab.A.LAm) < 1e-5
-    # far field is free-space only; a wave must come from the upper half-space
+    # above a stack the far field is taken in the upper half-space only; a wave
+    # must come from the upper half-space
     x = np.zeros(op.N, complex)
     with pytest.raises(sl.SldmError):
-        op.farfield(x, np.array([0.1]), np.array([0.0]))
+        op.farfield(x, np.array([np.pi / 2 + 0.1]), np.array([0.0]))
     with pytest.raises(sl.SldmError):
         op.rhs_planewave([1.0, 0, 0], [0, 0, 1.0], np.zeros(op.N, complex))
     # an object crossing an interface is rejected
@@ -222,3 +223,25 @@ def test_resting_on_glass_complex64_refined(on_glass):
     x = np.zeros(op.N, complex)
     op.solve(b.copy(), x, tol=1e-10)
     assert rel(x, S.solve(c.A, b)) < 1e-6
+
+
+def test_layered_rcs(on_glass, over_pec):
+    """The far field above the stack against the oracle's (reciprocity with the
+    stack's plane waves): the cylinder on glass under 35-degree TM incidence and the
+    sphere over PEC, 6 upper-hemisphere directions in two azimuth planes each."""
+    from oracle import farfield
+    th = np.radians(np.linspace(0.0, 85.0, 6))
+    t = np.radians(35.0)
+    cases = [(on_glass, [np.sin(t), 0.0, -np.cos(t)], [np.cos(t), 0.0, np.sin(t)]),
+             (over_pec, [0.0, 0.0, -1.0], [1.0, 0.0, 0.0])]
+    for c, khat, pol in cases:
+        op = _gpu_case(c)[1] if c is on_glass else c.gpu(0)[3]
+        b = np.zeros(op.N, complex)
+        op.rhs_planewave(khat, pol, b)
+        x = np.zeros(op.N, complex)
+        op.solve(b, x, tol=1e-11)
+        xr = S.solve(c.A, S.rhs(c.A, khat=khat, pol=pol))
+        for ph in (0.0, 1.0):
+            got = op.farfield(x, th, np.full_like(th, ph))
+            ref = farfield.rcs_layered(c.om, c.stack, c.layer, 2 * np.pi * c.freq, S.j_delta(c.A, xr), th, phi=ph)
+            assert np.max(np.abs(got - ref)) <= 1e-7 * np.max(ref), (ph, got, ref)
