@@ -8,8 +8,10 @@
 //     B'[2c, 2r] = Re x_r[c],  B'[2c+1, 2r] = -Im x_r[c]
 //     B'[2c, 2r+1] = Im x_r[c], B'[2c+1, 2r+1] = Re x_r[c],
 // D = A' B' holds Re y_r in column 2r and Im y_r in column 2r+1.  A' is the
-// stored block itself (the MMA's K-major A operand, streamed by TMA); B' is built
-// per K chunk in shared memory from the complex64 vectors.
+// stored block itself (the MMA's K-major A operand, streamed by TMA); B' (hi and
+// lo, below) is built for every K chunk of every job once per pass by
+// tc_bprime_kernel into global memory and streamed by TMA as well (it is the same
+// for all row tiles of a job, so building it in each tile would repeat the work).
 //
 // FP32 accuracy from TF32 operands (three products): with hi(v) = v rounded to
 // TF32 (|v - hi| <= 2^-12 |v|) and lo(v) = v - hi rounded to TF32 (error <= 2^-24 |v|),
@@ -24,12 +26,13 @@
 // split into four K sub-chunks of 32 FP32 columns.  Warp-specialised,
 // synchronised by mbarriers only:
 //   warp 0   TMA: a ring of 2 stages (128 KB in flight per SM);
+//   warp 18  TMA: B' hi/lo of each sub-chunk (one 128-row x 128 B box) into the
+//            operand buffer of that sub-chunk once the MMAs that read it before
+//            have completed;
 //   warps 2-9 split (two per TMEM lane quarter, half the K columns each):
 //            thread = row; for each sub-chunk reads its row, splits it
 //            into hi and lo and stores both into a TMEM operand buffer (A of
-//            the MMA in tensor memory: lane = row, column = K), and builds hi/lo
-//            of the B' sub-chunk (64 x 128 B, swizzled) in shared memory from
-//            vectors copied (cp.async) three sub-chunks ahead; the ring stage is
+//            the MMA in tensor memory: lane = row, column = K); the ring stage is
 //            freed after its fourth sub-chunk;
 //   warp 1   MMA: one thread issues 12 MMAs per sub-chunk (4 K steps x 3
 //            products, M 128, N 64, K 8) into one of two 64-column TMEM
@@ -42,7 +45,9 @@
 // MMAs into one accumulator would lose ~2^-17 of the result; segments of 48
 // MMAs and compensated sums across them keep the product as accurate as an
 // FP32 CUDA-core product.
-// Operand buffers (TMEM A, shared B') are triple-, accumulators double-buffered.
+// Operand buffers (TMEM A, shared B') are triple-, accumulators double-buffered
+// (deeper operand buffering, 5, and a third ring stage with 2 operand buffers
+// were measured: no gain, and a loss).
 // Tiles are padded to whole stages (zero columns from TMA and zero B').
 #include <cuda.h>
 
@@ -62,7 +67,7 @@ constexpr int TC_N = 2 * TC_MAX_NRHS;  // 64 accumulator columns
 constexpr int TC_KC = 32;              // FP32 columns of A per chunk: one 128-byte swizzle row
 constexpr int TC_BPS = 4;              // TMA boxes (sub-chunks) per stage
 constexpr int TC_R = 2;                // stages in the ring
-constexpr int TC_THREADS = 576;        // 18 warps: TMA, MMA, 8 split, 8 epilogue
+constexpr int TC_THREADS = 608;        // 19 warps: TMA (A), MMA, 8 split, 8 epilogue, TMA (B')
 constexpr int TC_NB = 3;               // operand buffers (TMEM A hi/lo, shared B' hi/lo)
 constexpr uint32_t TC_A_BYTES = TC_M * TC_KC * 4;  // 16 KB: one box, one sub-chunk
 constexpr uint32_t TC_STAGE_BYTES = TC_BPS * TC_A_BYTES;
@@ -72,11 +77,7 @@ constexpr uint32_t TC_RING = TC_R * TC_STAGE_BYTES;
 // TMEM: accumulators at columns 0 and 64, A operand buffers (hi 32 + lo 32 columns each) from 128
 constexpr uint32_t TC_TMEM_COLS = 512;
 constexpr uint32_t TC_ACC_COL = 0, TC_AOP_COL = 128;
-// vectors: a ring of 4 sub-chunks, copied 3 ahead; per sub-chunk each of the 256
-// split threads holds the 4 complex64 entries it needs (32 B)
-constexpr int TC_XR = 4;
-constexpr uint32_t TC_XBYTES = 256 * 32;  // 8 KB per sub-chunk
-constexpr size_t TC_SMEM = size_t(TC_RING) + TC_NB * size_t(TC_BBUF) + size_t(TC_XR) * TC_XBYTES + 1024 + 256;
+constexpr size_t TC_SMEM = size_t(TC_RING) + TC_NB * size_t(TC_BBUF) + 1024 + 256;
 constexpr uint32_t TC_SPIN = 1u << 21;  // try_wait rounds before a wait is declared failed
 
 static_assert(TC_BBUF % 1024 == 0 && TC_A_BYTES % 1024 == 0 && TC_B_BYTES % 1024 == 0, "swizzle atoms are 1 KB aligned");
@@ -187,27 +188,28 @@ __device__ __forceinline__ uint32_t sw128_off(int row, int j) { return uint32_t(
 
 }  // namespace
 
-// 18 warps over the 4 SM sub-partitions (5, 5, 4, 4) x 32 threads x 96 registers <= 16,384 each
+// 19 warps over the 4 SM sub-partitions (5, 5, 5, 4) x 32 threads x 96 registers <= 16,384 each
 __global__ void __maxnreg__(96)
     gemm_tc_kernel(const GemvJob* __restrict__ jobs, const unsigned char* __restrict__ maps, const TcTile* __restrict__ tiles,
-                   const int32_t* __restrict__ cta_begin, int nrhs, int* err) {
+                   const int32_t* __restrict__ cta_begin, const unsigned char* __restrict__ bmap,
+                   const int32_t* __restrict__ job_base, int nrhs, int* err) {
   extern __shared__ unsigned char tc_raw[];
   const int t_begin = cta_begin[blockIdx.x], t_end = cta_begin[blockIdx.x + 1];
   if (t_begin >= t_end) return;
   const uint32_t raw = smem_u32(tc_raw);
-  const uint32_t base = (raw + 1023u) & ~1023u;  // ring[R], B'[2], x ring
+  const uint32_t base = (raw + 1023u) & ~1023u;  // ring[R], B'[NB]
   unsigned char* gb = tc_raw + (base - raw);
   const uint32_t bbuf0 = base + TC_RING;
-  const uint32_t xring = bbuf0 + TC_NB * TC_BBUF;
-  const uint32_t bars = xring + TC_XR * TC_XBYTES;
-  // barriers (8 bytes each): full[R], empty[R], ready[NB], wfree[NB], accfull[2], accempty[2]
+  const uint32_t bars = bbuf0 + TC_NB * TC_BBUF;
+  // barriers (8 bytes each): full[R], empty[R], ready[NB], wfree[NB], accfull[2], accempty[2], bfull[NB]
   auto full = [&](int s) { return bars + 8u * uint32_t(s); };
   auto empty = [&](int s) { return bars + 8u * uint32_t(TC_R + s); };
   auto ready = [&](int b) { return bars + 8u * uint32_t(2 * TC_R + b); };
   auto wfree = [&](int b) { return bars + 8u * uint32_t(2 * TC_R + TC_NB + b); };
   auto accfull = [&](int a) { return bars + 8u * uint32_t(2 * TC_R + 2 * TC_NB + a); };
   auto accempty = [&](int a) { return bars + 8u * uint32_t(2 * TC_R + 2 * TC_NB + 2 + a); };
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gb + (bars - base) + 8 * (2 * TC_R + 2 * TC_NB + 4));
+  auto bfull = [&](int b) { return bars + 8u * uint32_t(2 * TC_R + 2 * TC_NB + 4 + b); };
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gb + (bars - base) + 8 * (2 * TC_R + 3 * TC_NB + 4));
   __shared__ int s_fail;
   volatile int* vfail = &s_fail;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -225,6 +227,7 @@ __global__ void __maxnreg__(96)
       mbar_init(accfull(a), 1);
       mbar_init(accempty(a), 8);
     }
+    for (int b = 0; b < TC_NB; ++b) mbar_init(bfull(b), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_fail = 0;
   }
@@ -282,6 +285,7 @@ __global__ void __maxnreg__(96)
         bool ok = true;
         if (j == 0 && seg >= 2) ok = mbar_wait(accempty(seg & 1), uint32_t(((seg >> 1) - 1) & 1), vfail);
         if (ok) ok = mbar_wait(ready(b), uint32_t((g / TC_NB) & 1), vfail);
+        if (ok) ok = mbar_wait(bfull(b), uint32_t((g / TC_NB) & 1), vfail);
         if (!ok) {
           *vfail = 1;
           break;
@@ -316,59 +320,8 @@ __global__ void __maxnreg__(96)
     // ---------------- split warps: thread = row of the tile (TMEM lane quarter warp % 4); the
     // two warps of a lane quarter take the K columns 16 kh .. 16 kh + 15 of each sub-chunk
     const int q4 = warp & 3, kh = (warp - 2) >> 2, row = 32 * q4 + lane;
-    // share of B' (64 rows x 8 chunks of 16 B, hi and lo): 16-byte chunk c = ti & 7 of rows
-    // 2 (rb + 16 m) + rr, m = 0, 1 (rr = (ti >> 3) & 1, rb = ti >> 4): a warp stores 4 whole rows
-    // per instruction, free of bank conflicts.  Those need x_{rb + 16m} at complex columns 2c, 2c + 1.
-    const int ti = tid - 64, bc = ti & 7, brr = (ti >> 3) & 1, brb = ti >> 4;
-    int xt = t_begin, xk = 0, xnk = nk_of(t_begin), xg = 0;
-    const float2* xjob = reinterpret_cast<const float2*>(jobs[tiles[t_begin].job].x);
-    int64_t xld = jobs[tiles[t_begin].job].ldx;
-    int xn_cols = jobs[tiles[t_begin].job].n;
-    auto copy_x = [&]() {  // sub-chunk xg into its ring slot (zero-filled beyond the job's columns or nrhs)
-      if (xg < total) {
-        const int c0 = xk * (TC_KC / 2) + 2 * bc;
-        // slot layout [entry e = 2m + u][thread]: consecutive threads, consecutive 8-byte words
-        const uint32_t dst = xring + uint32_t(xg % TC_XR) * TC_XBYTES + uint32_t(ti) * 8u;
-#pragma unroll
-        for (int m = 0; m < 2; ++m) {
-          const int r = brb + 16 * m;
-          const float2* x = xjob + int64_t(r < nrhs ? r : 0) * xld;
-#pragma unroll
-          for (int u = 0; u < 2; ++u) {
-            const bool v = r < nrhs && c0 + u < xn_cols;
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(dst + uint32_t(2 * m + u) * 2048u),
-                         "l"(v ? x + c0 + u : xjob), "r"(v ? 8 : 0)
-                         : "memory");
-          }
-        }
-        if (++xk == xnk) {
-          xk = 0;
-          if (++xt < t_end) {
-            const GemvJob& J = jobs[tiles[xt].job];
-            xnk = nk_of(xt);
-            xjob = reinterpret_cast<const float2*>(J.x);
-            xld = J.ldx;
-            xn_cols = J.n;
-          }
-        }
-        ++xg;
-      }
-      asm volatile("cp.async.commit_group;\n" ::: "memory");  // one group per sub-chunk, possibly empty
-    };
-    for (int i = 0; i < TC_XR - 1; ++i) copy_x();
     for (int g = 0; g < total; ++g) {
       const int st = g / TC_BPS, j = g % TC_BPS, q = st % TC_R, b = g % TC_NB;
-      copy_x();                                                                  // sub-chunk g + 3
-      asm volatile("cp.async.wait_group %0;\n" ::"n"(TC_XR - 1) : "memory");  // this thread's copies of g landed
-      float4 xv[2];  // (x_{rb+16m}[2c], x_{rb+16m}[2c+1]) as (re, im, re, im)
-      {
-        const float2* xs = reinterpret_cast<const float2*>(gb + (xring - base) + size_t(g % TC_XR) * TC_XBYTES) + ti;
-#pragma unroll
-        for (int m = 0; m < 2; ++m) {
-          const float2 a0 = xs[(2 * m) * 256], a1 = xs[(2 * m + 1) * 256];
-          xv[m] = make_float4(a0.x, a0.y, a1.x, a1.y);
-        }
-      }
       bool ok = mbar_wait(full(q), uint32_t((st / TC_R) & 1), vfail);
       if (ok && g >= TC_NB) ok = mbar_wait(wfree(b), uint32_t(((g / TC_NB) - 1) & 1), vfail);
       ok = __all_sync(0xffffffffu, ok);  // the TMEM stores below need the whole warp
@@ -390,35 +343,36 @@ __global__ void __maxnreg__(96)
       const uint32_t ta = tmem + (uint32_t(32 * q4) << 16) + TC_AOP_COL + uint32_t(b) * 64u + uint32_t(16 * kh);
       tmem_st16(ta, h);
       tmem_st16(ta + 32u, l);
-      // hi/lo of B' for this sub-chunk: row 2r gives Re y_r ([xr, -xi] per complex column), row 2r+1 Im y_r ([xi, xr])
-      {
-        unsigned char* Bh = gb + TC_RING + size_t(b) * TC_BBUF;
-        unsigned char* Bl = Bh + TC_B_BYTES;
-#pragma unroll
-        for (int m = 0; m < 2; ++m) {
-          const int brow = 2 * (brb + 16 * m) + brr;
-          const float4 a = xv[m];
-          const float4 v = brr ? make_float4(a.y, a.x, a.w, a.z) : make_float4(a.x, -a.y, a.z, -a.w);
-          float4 hv, lv;
-          tf32_split(v.x, hv.x, lv.x);
-          tf32_split(v.y, hv.y, lv.y);
-          tf32_split(v.z, hv.z, lv.z);
-          tf32_split(v.w, hv.w, lv.w);
-          const uint32_t off = sw128_off(brow, bc);
-          *reinterpret_cast<float4*>(Bh + off) = hv;
-          *reinterpret_cast<float4*>(Bl + off) = lv;
-        }
-      }
       asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-      fence_async_smem();
       tc_fence_before();
       __syncwarp();
       if (lane == 0) {
         if (j == TC_BPS - 1) mbar_arrive(empty(q));  // the stage's last sub-chunk: it may be refilled
-        mbar_arrive(ready(b));                        // A (TMEM) and B' (shared) of this sub-chunk are in place
+        mbar_arrive(ready(b));                        // A of this sub-chunk is in TMEM
       }
     }
-    asm volatile("cp.async.wait_group 0;\n" ::: "memory");  // no copy in flight when the CTA leaves
+  } else if (warp == 18) {
+    // ---------------- TMA producer of B' (hi rows 0-63, lo rows 64-127 of one box per
+    // sub-chunk, built for the pass by tc_bprime_kernel) into the operand buffers
+    if (lane == 0) {
+      int tile = t_begin, k = 0, nk = nk_of(t_begin), g = 0;
+      for (; g < total; ++g) {
+        const int b = g % TC_NB;
+        if (g >= TC_NB && !mbar_wait(wfree(b), uint32_t(((g / TC_NB) - 1) & 1), vfail)) {
+          *vfail = 1;
+          break;
+        }
+        mbar_expect_tx(bfull(b), TC_BBUF);
+        tma_load_2d(bbuf0 + uint32_t(b) * TC_BBUF, bmap, 0, 2 * TC_N * (job_base[tiles[tile].job] + k), bfull(b));
+        if (++k == nk) {
+          k = 0;
+          if (++tile < t_end) nk = nk_of(tile);
+        }
+      }
+      // the loads in flight land before the CTA leaves
+      for (int q = (g > TC_NB ? g - TC_NB : 0); q < g; ++q) mbar_wait(bfull(q % TC_NB), uint32_t((q / TC_NB) & 1));
+    }
+    __syncwarp();
   } else {
     // ---------------- epilogue warps: TMEM lane quarter warp % 4, accumulator columns 32 half ..
     const int q4 = warp & 3, half = (warp - 10) >> 2;
@@ -489,6 +443,33 @@ __global__ void __maxnreg__(96)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS) : "memory");
 }
 
+// B' of every sub-chunk of the pass (hi rows 0-63, lo rows 64-127, 32 FP32 columns
+// each, row-major; TMA applies the 128-byte swizzle): for right-hand side r and
+// complex column c = 16 kc + u / 2 of the sub-chunk's job, row 2r holds
+// (Re x_r[c], -Im x_r[c]) and row 2r + 1 (Im x_r[c], Re x_r[c]) at columns u, u + 1
+// (u even), TF32 hi and lo parts; zero for r >= nrhs and beyond the job's columns.
+__global__ void tc_bprime_kernel(const GemvJob* __restrict__ jobs, const int32_t* __restrict__ gjob,
+                                 const int32_t* __restrict__ gkc, int nrhs, float* __restrict__ bp) {
+  const int gidx = blockIdx.x;
+  const GemvJob& J = jobs[gjob[gidx]];
+  const int kc = gkc[gidx];
+  const float2* x = reinterpret_cast<const float2*>(J.x);
+  for (int e = threadIdx.x; e < TC_N * TC_KC / 2; e += blockDim.x) {  // (row, complex column) pairs
+    const int brow = e / (TC_KC / 2), cl = e % (TC_KC / 2);
+    const int r = brow >> 1, c = kc * (TC_KC / 2) + cl;
+    float2 v = make_float2(0.f, 0.f);
+    if (r < nrhs && c < J.n) v = x[int64_t(r) * J.ldx + c];
+    const float a0 = (brow & 1) ? v.y : v.x, a1 = (brow & 1) ? v.x : -v.y;
+    float h0, l0, h1, l1;
+    tf32_split(a0, h0, l0);
+    tf32_split(a1, h1, l1);
+    float* hi = bp + (size_t(gidx) * 2 * TC_N + brow) * TC_KC + 2 * cl;
+    float* lo = hi + size_t(TC_N) * TC_KC;
+    *reinterpret_cast<float2*>(hi) = make_float2(h0, h1);
+    *reinterpret_cast<float2*>(lo) = make_float2(l0, l1);
+  }
+}
+
 // ---------------------------------------------------------------- host side
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*, const cuuint64_t*,
                                   const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
@@ -515,6 +496,7 @@ void tc_plan_build(const std::vector<GemvJob>& jobs, TcPlan& tp, cudaStream_t s)
   std::vector<unsigned char> maps(jobs.size() * 128);
   std::vector<TcTile> tl;
   std::vector<int> cost;
+  std::vector<int32_t> job_base, gjob, gkc;
   for (size_t i = 0; i < jobs.size(); ++i) {
     const GemvJob& J = jobs[i];
     const uint64_t pitch = uint64_t(J.lda) * 8;
@@ -530,6 +512,11 @@ void tc_plan_build(const std::vector<GemvJob>& jobs, TcPlan& tp, cudaStream_t s)
       return;
     std::memcpy(&maps[i * 128], &map, 128);
     const int nk = ((2 * J.n + TC_KC - 1) / TC_KC + TC_BPS - 1) / TC_BPS * TC_BPS;
+    job_base.push_back(int32_t(gjob.size()));
+    for (int kc = 0; kc < nk; ++kc) {
+      gjob.push_back(int32_t(i));
+      gkc.push_back(kc);
+    }
     for (int r0 = 0; r0 < J.m; r0 += TC_M) {
       tl.push_back({int32_t(i), r0});
       cost.push_back(nk);
@@ -559,6 +546,25 @@ void tc_plan_build(const std::vector<GemvJob>& jobs, TcPlan& tp, cudaStream_t s)
     flat.insert(flat.end(), v.begin(), v.end());
     begin.push_back(int32_t(flat.size()));
   }
+  // B' for every sub-chunk and its tensor map (boxes of 128 rows x 128 B, swizzled like the A boxes)
+  tp.nsub = int(gjob.size());
+  tp.bprime.alloc(size_t(tp.nsub) * 2 * TC_N * TC_KC);
+  {
+    alignas(64) CUtensorMap bm;
+    const cuuint64_t dims[2] = {cuuint64_t(TC_KC), cuuint64_t(tp.nsub) * 2 * TC_N};
+    const cuuint64_t strides[1] = {cuuint64_t(TC_KC) * 4};
+    const cuuint32_t box[2] = {cuuint32_t(TC_KC), cuuint32_t(2 * TC_N)};
+    const cuuint32_t estr[2] = {1, 1};
+    if (enc(&bm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, tp.bprime.p, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return;
+    std::vector<unsigned char> bmv(128);
+    std::memcpy(bmv.data(), &bm, 128);
+    tp.bmap.upload(bmv, s);
+  }
+  tp.job_base.upload(job_base, s);
+  tp.gjob.upload(gjob, s);
+  tp.gkc.upload(gkc, s);
   tp.maps.upload(maps, s);
   tp.tiles.upload(flat, s);
   tp.cta_begin.upload(begin, s);
@@ -580,8 +586,10 @@ void gemm_tc(const GemvPlan& plan, const TcPlan& tp, int nrhs, cudaStream_t s) {
     attr_set.fetch_or(bit);
   }
   ScopedTimer tm("gemm_tc", s);
-  gemm_tc_kernel<<<unsigned(tp.nctas), TC_THREADS, TC_SMEM, s>>>(plan.jobs, tp.maps.p, tp.tiles.p, tp.cta_begin.p, nrhs,
-                                                                  tp.err.p);
+  tc_bprime_kernel<<<unsigned(tp.nsub), 256, 0, s>>>(plan.jobs, tp.gjob.p, tp.gkc.p, nrhs, tp.bprime.p);
+  count_launch();
+  gemm_tc_kernel<<<unsigned(tp.nctas), TC_THREADS, TC_SMEM, s>>>(plan.jobs, tp.maps.p, tp.tiles.p, tp.cta_begin.p,
+                                                                  tp.bmap.p, tp.job_base.p, nrhs, tp.err.p);
   count_launch();
   SLDM_CUDA(cudaGetLastError());
 }

@@ -14,12 +14,20 @@ struct TcTile {
 
 // Per GEMV plan: one TMA tensor map per job (the block seen as a row-major FP32
 // matrix of m rows and 2n columns), the 128-row tiles of every job, and their
-// assignment to CTAs (longest first, to the least loaded CTA).
+// assignment to CTAs (longest first, to the least loaded CTA); the real-form
+// right-hand-side operand B' of every K chunk, rebuilt for each pass.
 struct TcPlan {
   DBuf<unsigned char> maps;  // 128-byte tensor maps, 64-byte aligned
   DBuf<TcTile> tiles;
   DBuf<int32_t> cta_begin;   // CTA c takes tiles [cta_begin[c], cta_begin[c + 1])
   DBuf<int> err;             // set to 1 by a CTA whose bounded wait ran out
+  // B' of the pass (built from the vectors before each pass): sub-chunk g of the
+  // plan is (job gjob[g], K chunk gkc[g]), job j's first sub-chunk job_base[j];
+  // 128 rows x 32 FP32 per sub-chunk (hi, lo), read by TMA through bmap
+  DBuf<float> bprime;
+  DBuf<unsigned char> bmap;
+  DBuf<int32_t> job_base, gjob, gkc;
+  int nsub = 0;
   int nctas = 0;
   bool ok = false;           // every job fits the tensor-core path
 };
