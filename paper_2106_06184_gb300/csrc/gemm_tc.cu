@@ -34,15 +34,21 @@
 //            into hi and lo and stores both into a TMEM operand buffer (A of
 //            the MMA in tensor memory: lane = row, column = K); the ring stage is
 //            freed after its fourth sub-chunk;
-//   warp 1   MMA: one thread issues 12 MMAs per sub-chunk (4 K steps x 3
-//            products, M 128, N 64, K 8) into one of two 64-column TMEM
-//            accumulators, a fresh one for every stage (a segment of 128 K
-//            columns), and commits them to the operand buffer's barrier;
-//   warps 10-17 epilogue: fold each segment's accumulator into compensated FP32
-//            sums in registers (warp w: TMEM lanes 32 (w % 4) .., 32 of the 64
-//            columns), and at the end of a tile write Y.
+//   warp 1   MMA: one thread issues 8 MMAs per sub-chunk, per K step of 8:
+//            hi(A) x [hi(B') | lo(B')] (M 128, N 128: B' hi and lo are the two
+//            halves of one 128-row operand) and lo(A) x hi(B') (N 64) into the
+//            first half, into one of two 128-column TMEM accumulators, a fresh
+//            one for every stage (a segment of 128 K columns), and commits them
+//            to the operand buffer's barrier.  Two products per K step instead
+//            of three N = 64 ones: the tensor pipe spends ~70 cycles on an
+//            M 128 N 64 K 8 TF32 product, so three of them per K step took more
+//            of its time than the stage's HBM transfer leaves;
+//   warps 10-17 epilogue: fold each segment's accumulator (the sum of its two
+//            halves) into compensated FP32 sums in registers (warp w: TMEM
+//            lanes 32 (w % 4) .., 32 of the 64 output columns), and at the end
+//            of a tile write Y.
 // The tensor core rounds its FP32 accumulator at every MMA: a tile's ~10^4
-// MMAs into one accumulator would lose ~2^-17 of the result; segments of 48
+// MMAs into one accumulator would lose ~2^-17 of the result; segments of 32
 // MMAs and compensated sums across them keep the product as accurate as an
 // FP32 CUDA-core product.
 // Operand buffers (TMEM A, shared B') are triple-, accumulators double-buffered
@@ -74,9 +80,12 @@ constexpr uint32_t TC_STAGE_BYTES = TC_BPS * TC_A_BYTES;
 constexpr uint32_t TC_B_BYTES = TC_N * TC_KC * 4;  // 8 KB
 constexpr uint32_t TC_BBUF = 2 * TC_B_BYTES;       // B' hi, lo
 constexpr uint32_t TC_RING = TC_R * TC_STAGE_BYTES;
-// TMEM: accumulators at columns 0 and 64, A operand buffers (hi 32 + lo 32 columns each) from 128
+// TMEM: two accumulators of 128 columns (hi(A) hi(B') in 0-63, hi(A) lo(B') in
+// 64-127) at columns 0 and 128, A operand buffers (hi 32 + lo 32 columns each) from 256
 constexpr uint32_t TC_TMEM_COLS = 512;
-constexpr uint32_t TC_ACC_COL = 0, TC_AOP_COL = 128;
+constexpr uint32_t TC_ACC_COLS = 2 * TC_N;
+constexpr uint32_t TC_ACC_COL = 0, TC_AOP_COL = 2 * TC_ACC_COLS;
+static_assert(TC_AOP_COL + TC_NB * 64 <= TC_TMEM_COLS, "accumulators and operand buffers exceed the TMEM allocation");
 constexpr size_t TC_SMEM = size_t(TC_RING) + TC_NB * size_t(TC_BBUF) + 1024 + 256;
 constexpr uint32_t TC_SPIN = 1u << 21;  // try_wait rounds before a wait is declared failed
 
@@ -85,7 +94,10 @@ static_assert(TC_SMEM <= 227 * 1024, "ring and operand buffers exceed the shared
 
 // instruction descriptor, kind::tf32: D FP32 (bits 4-5 = 1), A and B TF32 (bits
 // 7-9, 10-12 = 2), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at 24-28
-constexpr uint32_t TC_IDESC = (1u << 4) | (2u << 7) | (2u << 10) | (uint32_t(TC_N >> 3) << 17) | (uint32_t(TC_M >> 4) << 24);
+constexpr uint32_t tc_idesc(int n) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | (uint32_t(n >> 3) << 17) | (uint32_t(TC_M >> 4) << 24);
+}
+constexpr uint32_t TC_IDESC_N64 = tc_idesc(TC_N), TC_IDESC_N128 = tc_idesc(2 * TC_N);
 
 // shared-memory matrix descriptor of a K-major operand in the 128-byte swizzled
 // layout: start address >> 4 (bits 0-13), leading byte offset 16 B (unused for
@@ -129,10 +141,10 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const void* map, int x
       : "memory");
 }
 // D (TMEM) (+)= A (TMEM: lane = row, one TF32 per column) x B (shared memory descriptor)
-__device__ __forceinline__ void tc_mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t acc) {
+__device__ __forceinline__ void tc_mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc, uint32_t acc) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d_tmem),
-      "r"(a_tmem), "l"(b), "r"(TC_IDESC), "r"(acc)
+      "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc)
       : "memory");
 }
 __device__ __forceinline__ void tc_commit(uint32_t bar) {
@@ -142,19 +154,22 @@ __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence:
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-// 16 consecutive accumulator columns of this warp's 32 TMEM lanes
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+// 8 consecutive accumulator columns of this warp's 32 TMEM lanes, at two column offsets
+__device__ __forceinline__ void tmem_ld8x2(uint32_t taddr, uint32_t off, float (&v)[8], float (&w)[8]) {
   uint32_t r[16];
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
-      "[%16];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%16];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8, %9, %10, %11, %12, %13, %14, %15}, [%17];\n"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
         "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr)
+      : "r"(taddr), "r"(taddr + off)
       : "memory");
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+  for (int i = 0; i < 8; ++i) {
+    v[i] = __uint_as_float(r[i]);
+    w[i] = __uint_as_float(r[8 + i]);
+  }
 }
 // 16 consecutive TMEM columns of this warp's 32 lanes from registers
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16]) {
@@ -291,17 +306,17 @@ __global__ void __maxnreg__(96)
           break;
         }
         tc_fence_after();
-        const uint32_t acc = tmem + TC_ACC_COL + uint32_t(seg & 1) * 64u;
+        const uint32_t acc = tmem + TC_ACC_COL + uint32_t(seg & 1) * TC_ACC_COLS;
         const uint32_t aop = tmem + TC_AOP_COL + uint32_t(b) * 64u;  // hi at +0, lo at +32
-        const uint32_t bh = bbuf0 + uint32_t(b) * TC_BBUF, bl = bh + TC_B_BYTES;
+        const uint32_t bh = bbuf0 + uint32_t(b) * TC_BBUF;            // B' hi rows 0-63, lo rows 64-127
 #pragma unroll
         for (int ks = 0; ks < TC_KC / 8; ++ks) {
           const uint32_t o = uint32_t(ks) * 32u;  // 8 TF32 = 32 bytes along K in the swizzle row of B'
           const uint32_t ac = uint32_t(ks) * 8u;  // 8 TMEM columns of A
           const uint32_t acc0 = (j > 0 || ks > 0) ? 1u : 0u;  // a fresh accumulator per segment
-          tc_mma_ts(acc, aop + ac, sw128_desc(bh + o), acc0);
-          tc_mma_ts(acc, aop + 32u + ac, sw128_desc(bh + o), 1u);
-          tc_mma_ts(acc, aop + ac, sw128_desc(bl + o), 1u);
+          // hi(A) [hi(B') | lo(B')] in one N = 128 product, then lo(A) hi(B') into columns 0-63
+          tc_mma_ts(acc, aop + ac, sw128_desc(bh + o), TC_IDESC_N128, acc0);
+          tc_mma_ts(acc, aop + 32u + ac, sw128_desc(bh + o), TC_IDESC_N64, 1u);
         }
         tc_commit(wfree(b));
         if (j == TC_BPS - 1) tc_commit(accfull(seg & 1));
@@ -388,13 +403,16 @@ __global__ void __maxnreg__(96)
         if (!ok) break;  // the TMEM loads below need the whole warp
         tc_fence_after();
 #pragma unroll
-        for (int hq = 0; hq < 2; ++hq) {
-          float v[16];
-          tmem_ld16(tmem + (uint32_t(32 * q4) << 16) + TC_ACC_COL + uint32_t(seg & 1) * 64u + uint32_t(half * 32 + 16 * hq),
-                    v);
+        for (int hq = 0; hq < 4; ++hq) {
+          float v[8], w[8];  // hi(A) hi(B') + lo(A) hi(B'), and hi(A) lo(B')
+          tmem_ld8x2(tmem + (uint32_t(32 * q4) << 16) + TC_ACC_COL + uint32_t(seg & 1) * TC_ACC_COLS +
+                         uint32_t(half * 32 + 8 * hq),
+                     TC_N, v, w);
 #pragma unroll
-          for (int i = 0; i < 16; ++i) {  // TwoSum (Knuth): cs + cc carries the running sum
-            const int c = 16 * hq + i;
+          for (int i = 0; i < 8; ++i) v[i] = __fadd_rn(v[i], w[i]);
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {  // TwoSum (Knuth): cs + cc carries the running sum
+            const int c = 8 * hq + i;
             const float sum = __fadd_rn(cs[c], v[i]);
             const float bp = __fsub_rn(sum, cs[c]);
             cc[c] = __fadd_rn(cc[c], __fadd_rn(__fsub_rn(cs[c], __fsub_rn(sum, bp)), __fsub_rn(v[i], bp)));
