@@ -193,8 +193,8 @@ FP64_OPS_PER_EVAL_REFL = 292.0
 # dense.cu).
 GEMV_TRAFFIC = {
     # main-stage launch of the 4 x 4 metasurface, 32 right-hand sides (profiles/gemm_tc_metasurface-4x4-32angles-c64x2.md)
-    "gemm_tc_kernel": dict(sha="e4ed5894daacc53a", file="gemm_tc.cu",
-                           per_alg_byte=(430.977024e6 + 9.762560e6) / 423.936e6),
+    "gemm_tc_kernel": dict(sha="78e503ea925c5ae5", file="gemm_tc.cu",
+                           per_alg_byte=(450.872235e6 + 7.982507e6) / 423.936e6),
 }
 
 

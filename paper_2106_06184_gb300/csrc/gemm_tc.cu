@@ -13,11 +13,13 @@
 // tc_bprime_kernel into global memory and streamed by TMA as well (it is the same
 // for all row tiles of a job, so building it in each tile would repeat the work).
 //
-// FP32 accuracy from TF32 operands (three products): with hi(v) = v rounded to
-// TF32 (|v - hi| <= 2^-12 |v|) and lo(v) = v - hi rounded to TF32 (error <= 2^-24 |v|),
+// Near-FP32 accuracy from TF32 operands (three products): with hi(v) = v rounded
+// to TF32 (10 stored mantissa bits: |v - hi| <= 2^-11 |v|) and lo(v) = v - hi
+// rounded to TF32 (error <= 2^-11 |v - hi| <= 2^-22 |v|),
 //     D = hi(A) hi(B) + lo(A) hi(B) + hi(A) lo(B)        (FP32 accumulation),
-// the dropped lo(A) lo(B) (<= 2^-24 |A||B|) and the two roundings of lo leave
-// each product term within ~3 x 2^-24 of |A||B|, FP32-like.
+// the dropped lo(A) lo(B) (<= 2^-22 |A||B|) and the two roundings of lo leave
+// each product term within 3 x 2^-22 of |A||B| (about 2^-22 for typical data),
+// against 2^-24 for an FP32 product; the sums are compensated (below).
 //
 // Per CTA (one per SM, persistent over its tiles, longest first), 128-row
 // tiles streamed in stages of 4 TMA boxes (128 rows x 4 x 128 B, 128-byte
@@ -51,9 +53,9 @@
 // MMAs into one accumulator would lose ~2^-17 of the result; segments of 32
 // MMAs and compensated sums across them keep the product as accurate as an
 // FP32 CUDA-core product.
-// Operand buffers (TMEM A, shared B') are triple-, accumulators double-buffered
-// (deeper operand buffering, 5, and a third ring stage with 2 operand buffers
-// were measured: no gain, and a loss).
+// Operand buffers: 4 for A (TMEM, the most that fits beside the two 128-column
+// accumulators), 6 for B' (shared memory), so that the B' loads, whose latency
+// from L2 under the streaming load is ~10^3 cycles, are issued well ahead.
 // Tiles are padded to whole stages (zero columns from TMA and zero B').
 #include <cuda.h>
 
@@ -74,7 +76,8 @@ constexpr int TC_KC = 32;              // FP32 columns of A per chunk: one 128-b
 constexpr int TC_BPS = 4;              // TMA boxes (sub-chunks) per stage
 constexpr int TC_R = 2;                // stages in the ring
 constexpr int TC_THREADS = 608;        // 19 warps: TMA (A), MMA, 8 split, 8 epilogue, TMA (B')
-constexpr int TC_NB = 3;               // operand buffers (TMEM A hi/lo, shared B' hi/lo)
+constexpr int TC_NA = 4;               // A operand buffers (TMEM, hi/lo)
+constexpr int TC_NBB = 6;              // B' operand buffers (shared, hi/lo)
 constexpr uint32_t TC_A_BYTES = TC_M * TC_KC * 4;  // 16 KB: one box, one sub-chunk
 constexpr uint32_t TC_STAGE_BYTES = TC_BPS * TC_A_BYTES;
 constexpr uint32_t TC_B_BYTES = TC_N * TC_KC * 4;  // 8 KB
@@ -85,8 +88,10 @@ constexpr uint32_t TC_RING = TC_R * TC_STAGE_BYTES;
 constexpr uint32_t TC_TMEM_COLS = 512;
 constexpr uint32_t TC_ACC_COLS = 2 * TC_N;
 constexpr uint32_t TC_ACC_COL = 0, TC_AOP_COL = 2 * TC_ACC_COLS;
-static_assert(TC_AOP_COL + TC_NB * 64 <= TC_TMEM_COLS, "accumulators and operand buffers exceed the TMEM allocation");
-constexpr size_t TC_SMEM = size_t(TC_RING) + TC_NB * size_t(TC_BBUF) + 1024 + 256;
+static_assert(TC_AOP_COL + TC_NA * 64 <= TC_TMEM_COLS, "accumulators and operand buffers exceed the TMEM allocation");
+constexpr int TC_NBARS = 2 * TC_R + 2 * TC_NA + 4 + 2 * TC_NBB;
+constexpr size_t TC_SMEM = size_t(TC_RING) + TC_NBB * size_t(TC_BBUF) + 1024 + 256;
+static_assert(8 * TC_NBARS + 4 <= 256, "barriers and the TMEM slot exceed their shared-memory space");
 constexpr uint32_t TC_SPIN = 1u << 21;  // try_wait rounds before a wait is declared failed
 
 static_assert(TC_BBUF % 1024 == 0 && TC_A_BYTES % 1024 == 0 && TC_B_BYTES % 1024 == 0, "swizzle atoms are 1 KB aligned");
@@ -152,7 +157,6 @@ __device__ __forceinline__ void tc_commit(uint32_t bar) {
 }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 // 8 consecutive accumulator columns of this warp's 32 TMEM lanes, at two column offsets
 __device__ __forceinline__ void tmem_ld8x2(uint32_t taddr, uint32_t off, float (&v)[8], float (&w)[8]) {
@@ -191,15 +195,13 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16]) 
 __device__ __forceinline__ float tf32_rn(float v) {
   return __uint_as_float((__float_as_uint(v) + 0x1000u) & 0xFFFFE000u);
 }
-// v = hi + lo: hi = tf32(v) (|v - hi| <= 2^-12 |v|), lo = tf32(v - hi) (rounding
-// error <= 2^-12 |v - hi| <= 2^-24 |v|), both exact TF32 operands
+// v = hi + lo: hi = tf32(v) (|v - hi| <= 2^-11 |v|), lo = tf32(v - hi) (rounding
+// error <= 2^-11 |v - hi| <= 2^-22 |v|), both exact TF32 operands
 __device__ __forceinline__ void tf32_split(float v, float& hi, float& lo) {
   hi = tf32_rn(v);
   lo = tf32_rn(v - hi);
 }
 
-// byte offset of 16-byte chunk j (0..7) of row `row` in a 128-byte swizzled tile
-__device__ __forceinline__ uint32_t sw128_off(int row, int j) { return uint32_t(row) * 128u + uint32_t((j ^ (row & 7)) * 16); }
 
 }  // namespace
 
@@ -215,16 +217,17 @@ __global__ void __maxnreg__(96)
   const uint32_t base = (raw + 1023u) & ~1023u;  // ring[R], B'[NB]
   unsigned char* gb = tc_raw + (base - raw);
   const uint32_t bbuf0 = base + TC_RING;
-  const uint32_t bars = bbuf0 + TC_NB * TC_BBUF;
-  // barriers (8 bytes each): full[R], empty[R], ready[NB], wfree[NB], accfull[2], accempty[2], bfull[NB]
+  const uint32_t bars = bbuf0 + TC_NBB * TC_BBUF;
+  // barriers (8 bytes each): full[R], empty[R], ready[NA], wfree[NA], accfull[2], accempty[2], bfull[NBB], bfree[NBB]
   auto full = [&](int s) { return bars + 8u * uint32_t(s); };
   auto empty = [&](int s) { return bars + 8u * uint32_t(TC_R + s); };
   auto ready = [&](int b) { return bars + 8u * uint32_t(2 * TC_R + b); };
-  auto wfree = [&](int b) { return bars + 8u * uint32_t(2 * TC_R + TC_NB + b); };
-  auto accfull = [&](int a) { return bars + 8u * uint32_t(2 * TC_R + 2 * TC_NB + a); };
-  auto accempty = [&](int a) { return bars + 8u * uint32_t(2 * TC_R + 2 * TC_NB + 2 + a); };
-  auto bfull = [&](int b) { return bars + 8u * uint32_t(2 * TC_R + 2 * TC_NB + 4 + b); };
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gb + (bars - base) + 8 * (2 * TC_R + 3 * TC_NB + 4));
+  auto wfree = [&](int b) { return bars + 8u * uint32_t(2 * TC_R + TC_NA + b); };
+  auto accfull = [&](int a) { return bars + 8u * uint32_t(2 * TC_R + 2 * TC_NA + a); };
+  auto accempty = [&](int a) { return bars + 8u * uint32_t(2 * TC_R + 2 * TC_NA + 2 + a); };
+  auto bfull = [&](int b) { return bars + 8u * uint32_t(2 * TC_R + 2 * TC_NA + 4 + b); };
+  auto bfree = [&](int b) { return bars + 8u * uint32_t(2 * TC_R + 2 * TC_NA + 4 + TC_NBB + b); };
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gb + (bars - base) + 8 * TC_NBARS);
   __shared__ int s_fail;
   volatile int* vfail = &s_fail;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -234,7 +237,7 @@ __global__ void __maxnreg__(96)
       mbar_init(full(q), 1);
       mbar_init(empty(q), 8);
     }
-    for (int b = 0; b < TC_NB; ++b) {
+    for (int b = 0; b < TC_NA; ++b) {
       mbar_init(ready(b), 8);
       mbar_init(wfree(b), 1);
     }
@@ -242,7 +245,10 @@ __global__ void __maxnreg__(96)
       mbar_init(accfull(a), 1);
       mbar_init(accempty(a), 8);
     }
-    for (int b = 0; b < TC_NB; ++b) mbar_init(bfull(b), 1);
+    for (int b = 0; b < TC_NBB; ++b) {
+      mbar_init(bfull(b), 1);
+      mbar_init(bfree(b), 1);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_fail = 0;
   }
@@ -257,10 +263,7 @@ __global__ void __maxnreg__(96)
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   // sub-chunks of a tile, padded to whole stages
-  auto nk_of = [&](int t) {
-    const int nk = (2 * jobs[tiles[t].job].n + TC_KC - 1) / TC_KC;
-    return (nk + TC_BPS - 1) / TC_BPS * TC_BPS;
-  };
+  auto nk_of = [&](int t) { return tiles[t].nk; };
   int total = 0;  // sub-chunks of this CTA (a multiple of TC_BPS)
   for (int t = t_begin; t < t_end; ++t) total += nk_of(t);
   const int nstages = total / TC_BPS;
@@ -280,7 +283,7 @@ __global__ void __maxnreg__(96)
 #pragma unroll
         for (int bx = 0; bx < TC_BPS; ++bx)
           tma_load_2d(base + uint32_t(q) * TC_STAGE_BYTES + uint32_t(bx) * TC_A_BYTES, maps + size_t(T.job) * 128,
-                      (k + bx) * TC_KC, T.row0, full(q));
+                      (T.k0 + k + bx) * TC_KC, T.row0, full(q));
         k += TC_BPS;
         if (k == nk) {
           k = 0;
@@ -296,11 +299,11 @@ __global__ void __maxnreg__(96)
     if (lane == 0) {
       int tile_i = 0, k = 0, nk = nk_of(t_begin), last = -1;
       for (int g = 0; g < total; ++g) {
-        const int b = g % TC_NB, seg = g / TC_BPS, j = g % TC_BPS;
+        const int b = g % TC_NA, bb = g % TC_NBB, seg = g / TC_BPS, j = g % TC_BPS;
         bool ok = true;
         if (j == 0 && seg >= 2) ok = mbar_wait(accempty(seg & 1), uint32_t(((seg >> 1) - 1) & 1), vfail);
-        if (ok) ok = mbar_wait(ready(b), uint32_t((g / TC_NB) & 1), vfail);
-        if (ok) ok = mbar_wait(bfull(b), uint32_t((g / TC_NB) & 1), vfail);
+        if (ok) ok = mbar_wait(ready(b), uint32_t((g / TC_NA) & 1), vfail);
+        if (ok) ok = mbar_wait(bfull(bb), uint32_t((g / TC_NBB) & 1), vfail);
         if (!ok) {
           *vfail = 1;
           break;
@@ -308,7 +311,7 @@ __global__ void __maxnreg__(96)
         tc_fence_after();
         const uint32_t acc = tmem + TC_ACC_COL + uint32_t(seg & 1) * TC_ACC_COLS;
         const uint32_t aop = tmem + TC_AOP_COL + uint32_t(b) * 64u;  // hi at +0, lo at +32
-        const uint32_t bh = bbuf0 + uint32_t(b) * TC_BBUF;            // B' hi rows 0-63, lo rows 64-127
+        const uint32_t bh = bbuf0 + uint32_t(bb) * TC_BBUF;           // B' hi rows 0-63, lo rows 64-127
 #pragma unroll
         for (int ks = 0; ks < TC_KC / 8; ++ks) {
           const uint32_t o = uint32_t(ks) * 32u;  // 8 TF32 = 32 bytes along K in the swizzle row of B'
@@ -319,6 +322,7 @@ __global__ void __maxnreg__(96)
           tc_mma_ts(acc, aop + 32u + ac, sw128_desc(bh + o), TC_IDESC_N64, 1u);
         }
         tc_commit(wfree(b));
+        tc_commit(bfree(bb));
         if (j == TC_BPS - 1) tc_commit(accfull(seg & 1));
         last = g;
         if (++k == nk) {
@@ -328,7 +332,10 @@ __global__ void __maxnreg__(96)
         }
       }
       // the MMAs in flight (they complete in order) finish before the CTA leaves
-      if (last >= 0) mbar_wait(wfree(last % TC_NB), uint32_t((last / TC_NB) & 1));
+      if (last >= 0) {
+        mbar_wait(wfree(last % TC_NA), uint32_t((last / TC_NA) & 1));
+        mbar_wait(bfree(last % TC_NBB), uint32_t((last / TC_NBB) & 1));
+      }
     }
     __syncwarp();
   } else if (warp < 10) {
@@ -336,9 +343,9 @@ __global__ void __maxnreg__(96)
     // two warps of a lane quarter take the K columns 16 kh .. 16 kh + 15 of each sub-chunk
     const int q4 = warp & 3, kh = (warp - 2) >> 2, row = 32 * q4 + lane;
     for (int g = 0; g < total; ++g) {
-      const int st = g / TC_BPS, j = g % TC_BPS, q = st % TC_R, b = g % TC_NB;
+      const int st = g / TC_BPS, j = g % TC_BPS, q = st % TC_R, b = g % TC_NA;
       bool ok = mbar_wait(full(q), uint32_t((st / TC_R) & 1), vfail);
-      if (ok && g >= TC_NB) ok = mbar_wait(wfree(b), uint32_t(((g / TC_NB) - 1) & 1), vfail);
+      if (ok && g >= TC_NA) ok = mbar_wait(wfree(b), uint32_t(((g / TC_NA) - 1) & 1), vfail);
       ok = __all_sync(0xffffffffu, ok);  // the TMEM stores below need the whole warp
       if (!ok) {
         *vfail = 1;
@@ -372,20 +379,21 @@ __global__ void __maxnreg__(96)
     if (lane == 0) {
       int tile = t_begin, k = 0, nk = nk_of(t_begin), g = 0;
       for (; g < total; ++g) {
-        const int b = g % TC_NB;
-        if (g >= TC_NB && !mbar_wait(wfree(b), uint32_t(((g / TC_NB) - 1) & 1), vfail)) {
+        const int b = g % TC_NBB;
+        if (g >= TC_NBB && !mbar_wait(bfree(b), uint32_t(((g / TC_NBB) - 1) & 1), vfail)) {
           *vfail = 1;
           break;
         }
         mbar_expect_tx(bfull(b), TC_BBUF);
-        tma_load_2d(bbuf0 + uint32_t(b) * TC_BBUF, bmap, 0, 2 * TC_N * (job_base[tiles[tile].job] + k), bfull(b));
+        tma_load_2d(bbuf0 + uint32_t(b) * TC_BBUF, bmap, 0, 2 * TC_N * (job_base[tiles[tile].job] + tiles[tile].k0 + k),
+                    bfull(b));
         if (++k == nk) {
           k = 0;
           if (++tile < t_end) nk = nk_of(tile);
         }
       }
       // the loads in flight land before the CTA leaves
-      for (int q = (g > TC_NB ? g - TC_NB : 0); q < g; ++q) mbar_wait(bfull(q % TC_NB), uint32_t((q / TC_NB) & 1));
+      for (int q = (g > TC_NBB ? g - TC_NBB : 0); q < g; ++q) mbar_wait(bfull(q % TC_NBB), uint32_t((q / TC_NBB) & 1));
     }
     __syncwarp();
   } else {
@@ -440,12 +448,16 @@ __global__ void __maxnreg__(96)
             const float re = cs[2 * c] + cc[2 * c], im = cs[2 * c + 1] + cc[2 * c + 1];
             float2 o = make_float2(ar * re - ai * im, ar * im + ai * re);
             float2* yy = y + int64_t(r) * J.ldy + row;
-            if (J.beta) {
-              const float2 bb = *yy;
-              o.x += bb.x;
-              o.y += bb.y;
+            if (T.split) {
+              atomicAdd(yy, o);  // one of the two K halves of the tile (Y zeroed before the pass)
+            } else {
+              if (J.beta) {
+                const float2 bb = *yy;
+                o.x += bb.x;
+                o.y += bb.y;
+              }
+              *yy = o;
             }
-            *yy = o;
           }
         }
       }
@@ -466,9 +478,21 @@ __global__ void __maxnreg__(96)
 // complex column c = 16 kc + u / 2 of the sub-chunk's job, row 2r holds
 // (Re x_r[c], -Im x_r[c]) and row 2r + 1 (Im x_r[c], Re x_r[c]) at columns u, u + 1
 // (u even), TF32 hi and lo parts; zero for r >= nrhs and beyond the job's columns.
+// Blocks nsub and above zero the Y rows of the tiles split along K.
 __global__ void tc_bprime_kernel(const GemvJob* __restrict__ jobs, const int32_t* __restrict__ gjob,
-                                 const int32_t* __restrict__ gkc, int nrhs, float* __restrict__ bp) {
+                                 const int32_t* __restrict__ gkc, int nsub, const TcTile* __restrict__ ztiles, int nrhs,
+                                 float* __restrict__ bp) {
   const int gidx = blockIdx.x;
+  if (gidx >= nsub) {  // Y rows of a tile split along K: zeroed, the two halves add into them
+    const TcTile T = ztiles[gidx - nsub];
+    const GemvJob& J = jobs[T.job];
+    float2* y = reinterpret_cast<float2*>(J.y);
+    for (int e = threadIdx.x; e < TC_M * nrhs; e += blockDim.x) {
+      const int row = T.row0 + e % TC_M, r = e / TC_M;
+      if (row < J.m) y[int64_t(r) * J.ldy + row] = make_float2(0.f, 0.f);
+    }
+    return;
+  }
   const GemvJob& J = jobs[gjob[gidx]];
   const int kc = gkc[gidx];
   const float2* x = reinterpret_cast<const float2*>(J.x);
@@ -515,6 +539,7 @@ void tc_plan_build(const std::vector<GemvJob>& jobs, TcPlan& tp, cudaStream_t s)
   std::vector<TcTile> tl;
   std::vector<int> cost;
   std::vector<int32_t> job_base, gjob, gkc;
+  std::vector<TcTile> tp_zero;  // tiles split along K: their Y rows are zeroed before each pass
   for (size_t i = 0; i < jobs.size(); ++i) {
     const GemvJob& J = jobs[i];
     const uint64_t pitch = uint64_t(J.lda) * 8;
@@ -536,14 +561,40 @@ void tc_plan_build(const std::vector<GemvJob>& jobs, TcPlan& tp, cudaStream_t s)
       gkc.push_back(kc);
     }
     for (int r0 = 0; r0 < J.m; r0 += TC_M) {
-      tl.push_back({int32_t(i), r0});
+      tl.push_back({int32_t(i), r0, 0, nk, 0});
       cost.push_back(nk);
     }
   }
-  // longest tiles first, each to the least loaded CTA
   int dev = 0, nsm = 0;
   SLDM_CUDA(cudaGetDevice(&dev));
   SLDM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  // Tiles are whole rows of 128 x the job's K: a few long tiles against the SM
+  // count leave CTAs idle at the end (the longest-first assignment of 180 tiles
+  // of one length to 152 CTAs gives 28 of them two).  Tiles longer than 0.3 of
+  // a CTA's mean load are split into two K halves (whole stages) that add into
+  // Y atomically: two additions into zero commute, so the result stays
+  // independent of their order.  Jobs that accumulate into Y (beta) keep whole tiles.
+  {
+    long long tot = 0;
+    for (int c : cost) tot += c;
+    const double lim = 0.3 * double(tot) / double(std::max(1, std::min<int>(nsm, int(tl.size()))));
+    const size_t n0 = tl.size();
+    for (size_t i = 0; i < n0; ++i) {
+      if (cost[i] < 4 * TC_BPS || double(cost[i]) <= lim || jobs[tl[i].job].beta) continue;
+      const int h = cost[i] / TC_BPS / 2 * TC_BPS;
+      TcTile b = tl[i];
+      b.k0 = h;
+      b.nk = cost[i] - h;
+      b.split = 1;
+      tl[i].nk = h;
+      tl[i].split = 1;
+      cost[i] = h;
+      tp_zero.push_back(tl[i]);
+      tl.push_back(b);
+      cost.push_back(b.nk);
+    }
+  }
+  // longest tiles first, each to the least loaded CTA
   const int nctas = std::max(1, std::min<int>(nsm, int(tl.size())));
   std::vector<size_t> order(tl.size());
   for (size_t i = 0; i < order.size(); ++i) order[i] = i;
@@ -580,6 +631,8 @@ void tc_plan_build(const std::vector<GemvJob>& jobs, TcPlan& tp, cudaStream_t s)
     std::memcpy(bmv.data(), &bm, 128);
     tp.bmap.upload(bmv, s);
   }
+  tp.nzero = int(tp_zero.size());
+  if (tp.nzero > 0) tp.ztiles.upload(tp_zero, s);
   tp.job_base.upload(job_base, s);
   tp.gjob.upload(gjob, s);
   tp.gkc.upload(gkc, s);
@@ -604,7 +657,8 @@ void gemm_tc(const GemvPlan& plan, const TcPlan& tp, int nrhs, cudaStream_t s) {
     attr_set.fetch_or(bit);
   }
   ScopedTimer tm("gemm_tc", s);
-  tc_bprime_kernel<<<unsigned(tp.nsub), 256, 0, s>>>(plan.jobs, tp.gjob.p, tp.gkc.p, nrhs, tp.bprime.p);
+  tc_bprime_kernel<<<unsigned(tp.nsub + tp.nzero), 256, 0, s>>>(plan.jobs, tp.gjob.p, tp.gkc.p, tp.nsub, tp.ztiles.p, nrhs,
+                                                                tp.bprime.p);
   count_launch();
   gemm_tc_kernel<<<unsigned(tp.nctas), TC_THREADS, TC_SMEM, s>>>(plan.jobs, tp.maps.p, tp.tiles.p, tp.cta_begin.p,
                                                                   tp.bmap.p, tp.job_base.p, nrhs, tp.err.p);

@@ -8,13 +8,15 @@ namespace sldm {
 // Right-hand sides one tensor-core pass takes (accumulator width 2 x 32 FP32 columns).
 constexpr int TC_MAX_NRHS = 32;
 
+// 128 rows of a job from row0, over K sub-chunks [k0, k0 + nk) of 32 FP32
+// columns (whole stages); split: one of two K halves of the rows, added into Y
 struct TcTile {
-  int32_t job, row0;
+  int32_t job, row0, k0, nk, split;
 };
 
 // Per GEMV plan: one TMA tensor map per job (the block seen as a row-major FP32
-// matrix of m rows and 2n columns), the 128-row tiles of every job, and their
-// assignment to CTAs (longest first, to the least loaded CTA); the real-form
+// matrix of m rows and 2n columns), the 128-row tiles of every job (long ones in
+// two K halves), and their assignment to CTAs (longest first, to the least loaded CTA); the real-form
 // right-hand-side operand B' of every K chunk, rebuilt for each pass.
 struct TcPlan {
   DBuf<unsigned char> maps;  // 128-byte tensor maps, 64-byte aligned
@@ -27,7 +29,8 @@ struct TcPlan {
   DBuf<float> bprime;
   DBuf<unsigned char> bmap;
   DBuf<int32_t> job_base, gjob, gkc;
-  int nsub = 0;
+  DBuf<TcTile> ztiles;       // the first halves of the split tiles (their Y rows are zeroed per pass)
+  int nsub = 0, nzero = 0;
   int nctas = 0;
   bool ok = false;           // every job fits the tensor-core path
 };

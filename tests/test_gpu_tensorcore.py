@@ -5,13 +5,16 @@ With the policy forced to 9 (sldm_set_tc_policy), 9 to 32 right-hand sides per
 pass go to the tensor cores (by default the crossover is measured per operator,
 checked last): every block as a
 real FP32 GEMM (complex64 storage read as interleaved FP32), 128-row tiles,
-K chunks of 32 FP32 columns, ragged rows and columns zero-filled by TMA.  The
-split into round-to-nearest TF32 high and low parts keeps FP32 accuracy: each
-product term carries ~3 x 2^-24 of |a||x| (the dropped lo x lo term and the
+K chunks of 32 FP32 columns, ragged rows and columns zero-filled by TMA, long
+tiles split into two K halves that add into Y atomically.  The split into
+round-to-nearest TF32 high and low parts keeps near-FP32 accuracy: each product
+term carries at most 3 x 2^-22 of |a||x| (the dropped lo x lo term and the
 roundings of lo), so the two products differ by 4e-6 relative per column at
 most, and against the FP64 product of the same stored blocks the tensor-core
 result is as accurate as the CUDA-core one (within 2x); a structural mistake (a
-missing split term, a wrong swizzle or sign) gives 1e-3 or more.  FP64
+missing split term, a wrong swizzle or sign, a K half added twice or not at
+all) gives 1e-3 or more.  The split halves add into zero, which commutes, so a
+product repeated on the same inputs is bit-identical.  FP64
 operators take 8 right-hand sides per CUDA-core launch and must agree with
 single products to 1e-13.
 """
@@ -74,6 +77,19 @@ def test_tensor_core_product_matches_cuda_core(name, nrhs):
         y1 = np.zeros(op.N, complex)
         op.apply(np.ascontiguousarray(X[r]), y1, nrhs=1)
         assert rel(Y[r], y1) < 4e-6, (r, rel(Y[r], y1))
+
+
+def test_tensor_core_product_is_bit_reproducible():
+    sl = _sl()
+    op = _op(sl, "cyl4", 1)
+    rng = np.random.default_rng(77)
+    X = np.ascontiguousarray(rng.standard_normal((32, op.N)) + 1j * rng.standard_normal((32, op.N)))
+    Y1 = np.zeros_like(X)
+    Y2 = np.zeros_like(X)
+    op.apply(X, Y1, nrhs=32)
+    for _ in range(3):
+        op.apply(X, Y2, nrhs=32)
+        assert np.array_equal(Y1, Y2)
 
 
 def test_tensor_core_product_is_fp32_accurate():
