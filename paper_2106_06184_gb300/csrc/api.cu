@@ -875,6 +875,9 @@ static void gmres_block(sldm_op* op, bool use_p, bool refine, bool x_zero, int m
           ks.h[j] = dhr(on[j]);
         }
         vscale3_batch(N, ne, 1.0, 1.0, l, bw, na, s);
+        // bytes the two passes move: per pass V[:, :k+1] read by the dots and by the
+        // update, w read by both and written by the update
+        timer_units("gram_schmidt", double(na) * 2.0 * (2.0 * (k + 1) + 3.0) * double(ldv) * sizeof(CB));
         krylov_dots<CB>(ks, s);
         krylov_update<CB>(ks, false, s);
         for (int j = 0; j < na; ++j) ks.h[j] = dhr(on[j]) + (m + 2);

@@ -1424,64 +1424,53 @@ __global__ void __launch_bounds__(256) krylov_dots_kernel(KrylovStep ks) {
 }
 
 // V_j[:, k] -= V_j[:, :k] h_j, and with `norm` nrm[j] += |V_j[:, k]|^2 after the
-// update.  Grid (ldv / 64, na): a CTA owns 64 rows, its 8 warps take every 8th
-// column (four in flight) and the partial sums meet in shared memory.
+// update.  Grid (ldv / 512, na): warp = 64 rows (lane = 2), over all k columns
+// with eight column loads in flight and no exchange between warps.
 template <class CB>
 __global__ void __launch_bounds__(256) krylov_update_kernel(KrylovStep ks, int norm) {
   typedef typename CT<CB>::R R;
-  __shared__ R part[8][32][4];
-  const int lane = threadIdx.x & 31, slice = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int64_t r0 = (int64_t(blockIdx.x) * 8 + (threadIdx.x >> 5)) * 64;
+  if (r0 >= ks.ldv) return;  // whole warps
   const int j = blockIdx.y;
   CB* V = reinterpret_cast<CB*>(ks.V[j]);
   const double2* __restrict__ h = ks.h[j];
-  const int64_t t = int64_t(blockIdx.x) * 64 + 2 * lane;
+  const int64_t t = r0 + 2 * lane;
   R s0r = 0, s0i = 0, s1r = 0, s1i = 0;
-  int i = slice;
-  for (; i + 24 < ks.k; i += 32) {
-    CB a[4], b[4];
-    double2 c[4];
+  int i = 0;
+  for (; i + 8 <= ks.k; i += 8) {
+    CB a[8], b[8];
+    double2 c[8];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      ld_pair(V + int64_t(i + 8 * u) * ks.ldv + t, a[u], b[u]);
-      c[u] = h[i + 8 * u];
+    for (int u = 0; u < 8; ++u) {
+      ld_pair(V + int64_t(i + u) * ks.ldv + t, a[u], b[u]);
+      c[u] = h[i + u];
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < 8; ++u) {
       cfma(s0r, s0i, R(a[u].x), R(a[u].y), R(c[u].x), R(c[u].y));
       cfma(s1r, s1i, R(b[u].x), R(b[u].y), R(c[u].x), R(c[u].y));
     }
   }
-  for (; i < ks.k; i += 8) {
+  for (; i < ks.k; ++i) {
     CB a, b;
     ld_pair(V + int64_t(i) * ks.ldv + t, a, b);
     const double2 c = h[i];
     cfma(s0r, s0i, R(a.x), R(a.y), R(c.x), R(c.y));
     cfma(s1r, s1i, R(b.x), R(b.y), R(c.x), R(c.y));
   }
-  part[slice][lane][0] = s0r;
-  part[slice][lane][1] = s0i;
-  part[slice][lane][2] = s1r;
-  part[slice][lane][3] = s1i;
-  __syncthreads();
-  if (slice == 0) {
-    R q[4] = {0, 0, 0, 0};
-    for (int z = 0; z < 8; ++z)
-#pragma unroll
-      for (int c = 0; c < 4; ++c) q[c] += part[z][lane][c];
-    CB* w = V + int64_t(ks.k) * ks.ldv + t;
-    CB a, b;
-    ld_pair(w, a, b);
-    a.x -= q[0];
-    a.y -= q[1];
-    b.x -= q[2];
-    b.y -= q[3];
-    st_pair(w, a, b);
-    if (norm) {
-      double nn = double(a.x) * double(a.x) + double(a.y) * double(a.y) + double(b.x) * double(b.x) +
-                  double(b.y) * double(b.y);
-      for (int o = 16; o > 0; o >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
-      if (lane == 0) atomicAdd(ks.nrm + j, nn);
-    }
+  CB* w = V + int64_t(ks.k) * ks.ldv + t;
+  CB a, b;
+  ld_pair(w, a, b);
+  a.x -= s0r;
+  a.y -= s0i;
+  b.x -= s1r;
+  b.y -= s1i;
+  st_pair(w, a, b);
+  if (norm) {
+    double nn = double(a.x) * double(a.x) + double(a.y) * double(a.y) + double(b.x) * double(b.x) + double(b.y) * double(b.y);
+    for (int o = 16; o > 0; o >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
+    if (lane == 0) atomicAdd(ks.nrm + j, nn);
   }
 }
 
@@ -1495,7 +1484,8 @@ void krylov_dots(const KrylovStep& ks, cudaStream_t s) {
 template <class CB>
 void krylov_update(const KrylovStep& ks, bool norm, cudaStream_t s) {
   if (ks.na <= 0) return;
-  krylov_update_kernel<CB><<<dim3(unsigned(ks.ldv / 64), ks.na), 256, 0, s>>>(ks, norm ? 1 : 0), ::sldm::count_launch();
+  krylov_update_kernel<CB><<<dim3(unsigned((ks.ldv / 64 + 7) / 8), ks.na), 256, 0, s>>>(ks, norm ? 1 : 0),
+      ::sldm::count_launch();
   SLDM_CUDA(cudaGetLastError());
 }
 template void krylov_dots<float2>(const KrylovStep&, cudaStream_t);
