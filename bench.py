@@ -32,7 +32,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from workloads.meshes import copper_wire, cylinder_array, icosphere  # noqa: E402
+from workloads.meshes import box, copper_wire, cylinder_array, icosphere  # noqa: E402
 
 # ----------------------------------------------------------------------------- workloads
 WORKLOADS = {
@@ -137,7 +137,30 @@ WORKLOADS["sweep-8instances-16freqs-8angles-c64"] = dict(
     budget=150 << 30, khat=[0.0, 0.0, -1.0], pol=[1.0, 0.0, 0.0],
     mesh=lambda: icosphere(1, 0.1), obj=None, mats=[(4.0, 1.0, 0.0)], bg=(1.0, 1.0, 0.0, 0.0), freq=300e6,
     n_angles=0)
+# Delta-gap port (Sec. IV-B, the antenna alone over the ground): the half-wave
+# dipole of the sphere-array experiment, a 75 x 750 x 37.5 mm prism centred at
+# (0, 0, 493.75 mm) (4 x 32 x 2 cells, 800 triangles), over the ground of Table I
+# (sphere-array column: air above z = 375 mm; 525 mm of eps_r 3.47, 1.725 mS/m;
+# half-space eps_r 6.5, 3.338 mS/m below z = -150 mm), driven by a delta-gap edge
+# port at its centre (the ring in the plane y = 0); S11 against 50 ohm at 16
+# frequencies 150 - 250 MHz, one per step (assemble, port right-hand side, GMRES
+# to 1e-8, port current, S11), complex FP64.  The prism is a lossy metal of 1e3
+# S/m (skin depth 1.1 mm at 200 MHz): the skin-depth splitting of the internal
+# kernel caps a source triangle at 4,096 children, which copper (5.8e7 S/m, skin
+# depth 4.7 um) would exceed by orders of magnitude at 2 cm cells.
+WORKLOADS["dipole-tableI-ground-port-s11-150-250MHz-fp64"] = dict(
+    mesh=lambda: box(0.075, 0.75, 0.0375, 4, 32, 2, center=(0.0, 0.0, 0.49375)), obj=None,
+    mats=[(1.0, 1.0, 1e3, 0)],
+    layers=[(1.0, 1.0, 0.0, 0.0), (3.47, 1.0, 0.001725, 0.525), (6.5, 1.0, 0.003338, 0.0)], z_top=0.375,
+    bottom="halfspace", freqs=[float(f) for f in np.linspace(150e6, 250e6, 16)], precision=0, tol=1e-8,
+    ports=[(0, (0.0, 1.0, 0.0), 0.0)], z0=50.0, khat=[0.0, 0.0, -1.0], pol=[1.0, 0.0, 0.0], n_angles=0,
+    e2e_steps=4)
 DEFAULT_WORKLOAD = "metasurface-8x8-cyl-epsr6-1um-onglass-c64x2-32angles"
+
+
+def _nrhs(W):
+    """Right-hand sides per step: one per port, else one per plane wave."""
+    return len(W["ports"]) if "ports" in W else len(np.atleast_2d(W["khat"]))
 
 
 def _freqs(W):
@@ -631,16 +654,32 @@ def run_ours(args, rank, world):
     phi = np.zeros_like(theta)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
-    nrhs = len(np.atleast_2d(W["khat"]))
+    nrhs = _nrhs(W)
+    ports = (sldm.Ports([sldm.port_ring(mesh, o, sv, c) for o, sv, c in W["ports"]]) if "ports" in W else None)
+    s_params = {}
+
+    def excite(op, b):
+        if ports is not None:
+            op.port_rhs(ports, np.eye(nrhs), b)   # one port driven per column, the others shorted
+        else:
+            op.rhs_planewave(W["khat"], W["pol"], b)
+
+    def post(op, x, i):
+        """RCS of every plane wave, or the ports' S matrix (recorded per frequency)."""
+        if ports is not None:
+            Y = op.port_currents(x, ports, ncols=nrhs)
+            Sm = sldm.sparams(Y, W["z0"])
+            s_params[freqs[i % len(freqs)]] = Sm
+            return Sm
+        return op.farfield_n(x, theta, phi, nrhs) if W["n_angles"] else None
 
     def step_device(i):
         op = sldm.Operator(mesh, stack, W["mats"], freqs[i % len(freqs)], precision=W["precision"])
         b = torch.zeros((nrhs, op.N), dtype=torch.complex128, device="cuda")
-        op.rhs_planewave(W["khat"], W["pol"], b)
+        excite(op, b)
         x = torch.zeros_like(b)
         info = op.solve(b, x, nrhs=nrhs, tol=W["tol"], maxit=W.get("maxit", 2000), check=False)
-        rcs = op.farfield_n(x, theta, phi, nrhs) if W["n_angles"] else None
-        return op, info, rcs
+        return op, info, post(op, x, i)
 
     for i in range(args.warmup):
         op, info, rcs = step_device(i)
@@ -690,11 +729,11 @@ def run_ours(args, rank, world):
         m2 = sldm.Mesh(xyz, tri, obj_ids)                       # H2D: vertices and triangles
         op2 = sldm.Operator(m2, stack, W["mats"], freqs[fi % len(freqs)], precision=W["precision"])
         bh = np.zeros((nrhs, op2.N), complex)
-        op2.rhs_planewave(W["khat"], W["pol"], bh)              # D2H: b
+        excite(op2, bh)                                         # D2H: b
         xh = np.zeros((nrhs, op2.N), complex)
         op2.solve(bh, xh, nrhs=nrhs, tol=W["tol"], maxit=W.get("maxit", 2000), check=False)  # H2D: b, D2H: x
-        rcs2 = (op2.farfield_n(xh, theta, phi, nrhs)  # H2D: x, angles; D2H: rcs
-                if W["n_angles"] else np.zeros(0))
+        rcs2 = post(op2, xh, fi)                                # H2D: x; D2H: rcs or port currents
+        rcs2 = np.zeros(0) if rcs2 is None else np.asarray(rcs2)
         e2e_times.append(time.perf_counter() - t0)
         if i == 0:
             h2d = (xyz.nbytes + tri.astype(np.int32).nbytes + bh.nbytes + xh.nbytes
@@ -804,11 +843,19 @@ def run_ours(args, rank, world):
                 "latency_ms_p50": 1e3 * statistics.median(e2e_times) if e2e_times else None},
         "wall_s_timed": t_wall,
     }
+    if ports is not None:
+        out["ports"] = {"n": nrhs, "z0_ohm": W["z0"], "ring_edges": [int(ports.ptr[p + 1] - ports.ptr[p])
+                                                                    for p in range(nrhs)],
+                        "s11": {f"{f / 1e6:.2f} MHz": [float(abs(Sm[0, 0])), float(np.degrees(np.angle(Sm[0, 0])))]
+                                for f, Sm in sorted(s_params.items())},
+                        "s11_format": "[|S11|, phase deg]"}
+        out["config"]["ports"] = nrhs
     return out
 
 
 METRIC = ("solves/s (per plane-wave right-hand side: assemble + RHS + GMRES to the stated relative residual; "
-          "+ bistatic RCS where the workload asks for it)")
+          "+ bistatic RCS where the workload asks for it; a port workload counts one right-hand side per port "
+          "and adds the port currents and S matrix)")
 
 
 # ----------------------------------------------------------------------------- oracle timing
@@ -1153,7 +1200,7 @@ def run_reference(args, rank, world):
             times.append(t)
     total = sum(times)
     # the oracle's dense LU serves every right-hand side of a request
-    v = args.steps * len(np.atleast_2d(WORKLOADS[args.workload]["khat"])) / total
+    v = args.steps * _nrhs(WORKLOADS[args.workload]) / total
     return {
         "impl": "reference", "metric": METRIC,
         "value": v, "unit": "solves/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -1193,7 +1240,7 @@ def main():
     else:
         out = run_ours(args, rank, world)
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
-            nr = len(np.atleast_2d(WORKLOADS[args.workload]["khat"]))
+            nr = _nrhs(WORKLOADS[args.workload])
             fi = len(_freqs(WORKLOADS[args.workload])) // 2
             try:
                 t, sample, extrap, spent = oracle_step_seconds(args.workload, fi)

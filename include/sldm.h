@@ -270,6 +270,50 @@ int sldm_rhs_planewave(const sldm_op* op, const double* khat, const double* pol,
 int sldm_solve(const sldm_op* op, const void* b, void* x, int32_t nrhs, const sldm_solve_opts* opts,
                sldm_solve_info* info, int32_t where, void* stream);
 
+/* ---- Delta-gap edge ports (Sec. IV-B: a delta-gap edge port at the centre of
+ * the dipole, where S11 is measured; Sec. IV-C: two ports on the inductor).
+ * A port is the ring of edges of one object lying in the plane s . r = c, each
+ * with one triangle on either side; an edge's sign is +1 when its T+ lies on
+ * the -s side (the RWG's unit flux crosses the plane along +s).  The source V
+ * is an impressed field V delta(s . r - c) s on the surface, entering the
+ * external EFIE (row 1 of Eq. finalsystem) as an incident field does:
+ * b[edge] = sign V / eta0 on the ring, 0 elsewhere.  The port current is the
+ * electric surface current n x H through the ring along +s:
+ * I = sum over the ring of sign x[edge] / (j k0) (x[edge] = j k0 H coefficient).
+ * Several ports are passed as a CSR on the host: ring_ptr (nports + 1, ring_ptr[0]
+ * = 0, every ring non-empty), edges and signs (+1 or -1) of ring p at
+ * [ring_ptr[p], ring_ptr[p + 1]).  SLDM_EINVAL for a malformed CSR, an edge out
+ * of range or a sign other than +-1. */
+
+/* The ring of object obj in the plane s . r = c (s: 3 doubles, any nonzero
+ * length; vertices within tol of the plane, tol <= 0 takes 1e-9 of the mesh's
+ * largest extent).  edges, signs: host arrays of capacity cap (may be NULL
+ * when cap = 0); *count receives the ring's size, also when it exceeds cap
+ * (then SLDM_EINVAL: call again with a larger cap).  SLDM_EINVAL when no edge
+ * of the object lies in the plane. */
+int sldm_port_ring(const sldm_mesh* m, int32_t obj, const double* s, double c, double tol, int32_t cap,
+                   int32_t* edges, int8_t* signs, int32_t* count);
+
+/* Port excitations: column k of b (N x ncols complex128, column-major, `where`)
+ * is sum_p V[p + nports k] times port p's right-hand side; V: nports x ncols
+ * complex128, column-major, host (V = identity: one port driven per column,
+ * the others shorted). */
+int sldm_port_rhs(const sldm_op* op, int32_t nports, const int32_t* ring_ptr, const int32_t* edges,
+                  const int8_t* signs, const double* V, int32_t ncols, void* b, int32_t where, void* stream);
+
+/* Port currents of solutions x (N x ncols complex128, `where`): I receives
+ * nports x ncols complex128, column-major, host.  With the excitations V =
+ * identity, I is the admittance matrix Y. */
+int sldm_port_currents(const sldm_op* op, int32_t nports, const int32_t* ring_ptr, const int32_t* edges,
+                       const int8_t* signs, const void* x, int32_t ncols, double* I, int32_t where, void* stream);
+
+/* Scattering matrix of an n-port from its admittance matrix, for a real
+ * reference impedance z0 (ohm) at every port: S = (1 - z0 Y)(1 + z0 Y)^-1, i.e.
+ * (Z - z0)(Z + z0)^-1 with Z = Y^-1.  Y, S: n x n complex128, column-major,
+ * host.  SLDM_EINVAL for n < 1 or z0 <= 0, SLDM_ENUMERIC when 1 + z0 Y is
+ * singular. */
+int sldm_port_sparams(int32_t n, const double* Y, double z0, double* S);
+
 /* Bistatic radar cross section (m^2) of the solution x (N complex128, `where`):
  * the equivalent current J_Delta = H - H_eq radiating in the background (Sec.
  * IV-A).  theta, phi, rcs: n doubles, host.  Above a stratified background the

@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libsldm.so")
 SOURCES = ["mesh.cpp", "timers.cpp", "fill.cu", "fill_sub.cu", "dense.cu", "gemm_tc.cu", "lu_blocked.cu", "precond.cu",
-           "mgf.cu", "nested.cu", "api.cu", "serve.cpp"]
+           "mgf.cu", "nested.cu", "ports.cu", "api.cu", "serve.cpp"]
 HEADERS = ["internal.h", "fill_dev.cuh", "dense.h", "gemm_tc.h", "precond.h", "mgf.h", "nested.h", os.path.join("..", "..", "include", "sldm.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

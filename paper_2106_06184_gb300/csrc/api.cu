@@ -1407,6 +1407,43 @@ int sldm_solve(const sldm_op* op_, const void* b, void* x, int32_t nrhs, const s
   API_END
 }
 
+int sldm_port_rhs(const sldm_op* op, int32_t nports, const int32_t* ring_ptr, const int32_t* edges, const int8_t* signs,
+                  const double* V, int32_t ncols, void* b, int32_t where, void* stream) {
+  API_BEGIN
+  SLDM_REQUIRE(op && V && b && ncols >= 1, SLDM_EINVAL, "port_rhs: invalid arguments");
+  port_check(op->mesh->h, nports, ring_ptr, edges, signs);
+  cudaStream_t s = (cudaStream_t)stream;
+  DBuf<double2> tmp;
+  double2* db = (where == SLDM_DEVICE) ? (double2*)b : nullptr;
+  if (!db) {
+    tmp.alloc(size_t(op->N) * ncols);
+    db = tmp.p;
+  }
+  SLDM_CUDA(cudaMemsetAsync(db, 0, size_t(op->N) * ncols * sizeof(double2), s));
+  port_rhs(nports, ring_ptr, edges, signs, reinterpret_cast<const double2*>(V), ncols, db, op->N, s);
+  if (where == SLDM_HOST)
+    SLDM_CUDA(cudaMemcpyAsync(b, db, size_t(op->N) * ncols * sizeof(double2), cudaMemcpyDeviceToHost, s));
+  SLDM_CUDA(cudaStreamSynchronize(s));
+  API_END
+}
+
+int sldm_port_currents(const sldm_op* op, int32_t nports, const int32_t* ring_ptr, const int32_t* edges,
+                       const int8_t* signs, const void* x, int32_t ncols, double* I, int32_t where, void* stream) {
+  API_BEGIN
+  SLDM_REQUIRE(op && x && I && ncols >= 1, SLDM_EINVAL, "port_currents: invalid arguments");
+  port_check(op->mesh->h, nports, ring_ptr, edges, signs);
+  cudaStream_t s = (cudaStream_t)stream;
+  DBuf<double2> tmp;
+  const double2* dx = (where == SLDM_DEVICE) ? (const double2*)x : nullptr;
+  if (!dx) {
+    tmp.alloc(size_t(op->N) * ncols);
+    SLDM_CUDA(cudaMemcpyAsync(tmp.p, x, size_t(op->N) * ncols * sizeof(double2), cudaMemcpyHostToDevice, s));
+    dx = tmp.p;
+  }
+  port_currents(nports, ring_ptr, edges, signs, dx, op->N, ncols, op->k0, reinterpret_cast<double2*>(I), s);
+  API_END
+}
+
 int sldm_farfield_n(const sldm_op* op_, const void* x, int32_t nrhs, int32_t where, const double* theta, const double* phi,
                     int32_t n, double* rcs) {
   API_BEGIN

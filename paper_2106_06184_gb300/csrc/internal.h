@@ -172,6 +172,16 @@ struct sldm_stack {
 
 namespace sldm {
 
+// ---------------------------------------------------------------- delta-gap ports (ports.cu)
+// SLDM_EINVAL unless ring_ptr is a CSR of nports non-empty rings of valid edges with signs +-1.
+void port_check(const HostMesh& h, int32_t nports, const int32_t* ring_ptr, const int32_t* edges, const int8_t* signs);
+// b[:, k] += sum_p V[p + nports k] port_p / eta0 (b on the device, column stride ldb; the rest host arrays).
+void port_rhs(int32_t nports, const int32_t* ring_ptr, const int32_t* edges, const int8_t* signs, const double2* V,
+              int32_t ncols, double2* b, int64_t ldb, cudaStream_t s);
+// I_host[p + nports k] = sum over ring p of sign x[edge, k] / (j k0) (x on the device).
+void port_currents(int32_t nports, const int32_t* ring_ptr, const int32_t* edges, const int8_t* signs, const double2* x,
+                   int64_t ldx, int32_t ncols, double k0, double2* I_host, cudaStream_t s);
+
 // ---------------------------------------------------------------- fill (fill.cu)
 void geometry(const HostMesh& hm, DevMesh& dm, cudaStream_t s);
 

@@ -125,6 +125,13 @@ EXPORTS = {
     "sldm_server_destroy": (C.c_int, [C.c_void_p]),
     "sldm_cache_plan": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     "sldm_batch_plan": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
+    "sldm_port_ring": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_double, C.c_double, C.c_int32, C.c_void_p,
+                                 C.c_void_p, C.POINTER(C.c_int32)]),
+    "sldm_port_rhs": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32,
+                                C.c_void_p, C.c_int32, C.c_void_p]),
+    "sldm_port_currents": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32,
+                                     C.c_void_p, C.c_int32, C.c_void_p]),
+    "sldm_port_sparams": (C.c_int, [C.c_int32, C.c_void_p, C.c_double, C.c_void_p]),
 }
 
 
@@ -404,12 +411,69 @@ class Operator:
                                                 out.ctypes.data_as(C.c_void_p)))
         return out
 
+    def port_rhs(self, ports, V, b, stream=None):
+        """b (N x ncols per column, `where` of b) = sum_p V[p, k] port_p; V: (nports, ncols)."""
+        V = np.ascontiguousarray(np.asarray(V, complex).reshape(ports.n, -1).T)  # column-major nports x ncols
+        pb, wb = _ptr(b)
+        self.L.check(self.L.lib.sldm_port_rhs(self.h, ports.n, *ports.args(), V.ctypes.data_as(C.c_void_p), V.shape[0],
+                                              pb, wb, _stream(stream)))
+        return b
+
+    def port_currents(self, x, ports, ncols=1, stream=None):
+        """Port currents (nports, ncols) of ncols solutions x."""
+        out = np.zeros((ncols, ports.n), complex)  # column-major nports x ncols
+        px, wx = _ptr(x)
+        self.L.check(self.L.lib.sldm_port_currents(self.h, ports.n, *ports.args(), px, ncols,
+                                                   out.ctypes.data_as(C.c_void_p), wx, _stream(stream)))
+        return out.T.copy()
+
     def close(self):
         if self.h:
             self.L.lib.sldm_op_destroy(self.h)
             self.h = None
 
     __del__ = close
+
+
+def port_ring(mesh, obj, s, c, tol=0.0):
+    """(edges, signs) of the delta-gap port of object obj in the plane s . r = c."""
+    L = mesh.L
+    sv = np.ascontiguousarray(s, np.float64)
+    n = C.c_int32(0)
+    code = L.lib.sldm_port_ring(mesh.h, obj, sv.ctypes.data_as(C.c_void_p), c, tol, 0, None, None, C.byref(n))
+    if n.value <= 0:
+        L.check(code)
+    edges = np.zeros(n.value, np.int32)
+    signs = np.zeros(n.value, np.int8)
+    L.check(L.lib.sldm_port_ring(mesh.h, obj, sv.ctypes.data_as(C.c_void_p), c, tol, n.value,
+                                 edges.ctypes.data_as(C.c_void_p), signs.ctypes.data_as(C.c_void_p), C.byref(n)))
+    return edges, signs
+
+
+class Ports:
+    """Several delta-gap ports as the CSR the C ABI takes: a list of (edges, signs)."""
+
+    def __init__(self, rings):
+        self.n = len(rings)
+        self.ptr = np.zeros(self.n + 1, np.int32)
+        self.ptr[1:] = np.cumsum([len(e) for e, _ in rings])
+        self.edges = np.ascontiguousarray(np.concatenate([np.asarray(e, np.int32) for e, _ in rings]))
+        self.signs = np.ascontiguousarray(np.concatenate([np.asarray(g, np.int8) for _, g in rings]))
+
+    def args(self):
+        return (self.ptr.ctypes.data_as(C.c_void_p), self.edges.ctypes.data_as(C.c_void_p),
+                self.signs.ctypes.data_as(C.c_void_p))
+
+
+def sparams(Y, z0=50.0, lib=None):
+    """S = (1 - z0 Y)(1 + z0 Y)^-1 of an admittance matrix Y (n x n)."""
+    L = lib or load()
+    Y = np.atleast_2d(np.asarray(Y, complex))
+    n = Y.shape[0]
+    Yc = np.ascontiguousarray(Y.T)  # column-major
+    out = np.zeros((n, n), complex)
+    L.check(L.lib.sldm_port_sparams(n, Yc.ctypes.data_as(C.c_void_p), float(z0), out.ctypes.data_as(C.c_void_p)))
+    return out.T.copy()
 
 
 class Server:
