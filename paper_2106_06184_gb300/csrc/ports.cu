@@ -188,8 +188,10 @@ int sldm_port_sparams(int32_t n, const double* Y, double z0, double* S) {
         A[size_t(j) * n + i] = d + z0 * y;
         B[size_t(j) * n + i] = d - z0 * y;
       }
-    double scale = 0;
-    for (const cd& a : A) scale = std::max(scale, std::abs(a));
+    // singular when a pivot falls to rounding level of the operands 1 and z0 Y
+    double ymax = 0;
+    for (int i = 0; i < 2 * n * n; i += 2) ymax = std::max(ymax, std::hypot(Y[i], Y[i + 1]));
+    const double scale = 1.0 + z0 * ymax;
     for (int c = 0; c < n; ++c) {
       int piv = c;
       for (int r = c + 1; r < n; ++r)

@@ -41,3 +41,21 @@ def test_last_error_is_callable_without_gpu(lib):
     buf = ctypes.create_string_buffer(64)
     lib.sldm_last_error(buf, ctypes.c_size_t(64))
     assert isinstance(buf.value, bytes)
+
+
+def test_port_sparams_is_host_math_matching_the_oracle(lib):
+    """sldm_port_sparams needs no GPU: S from Y against the oracle's formula,
+    the singular case and invalid arguments."""
+    import numpy as np
+
+    from oracle import ports as PT
+    from paper_2106_06184_gb300 import sldm
+    rng = np.random.default_rng(3)
+    for n in (1, 2, 5):
+        Y = (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) / 50.0
+        Y = Y + Y.T                     # reciprocal
+        assert np.allclose(sldm.sparams(Y, 50.0), PT.s_matrix(Y, 50.0), rtol=1e-12, atol=1e-12)
+    with pytest.raises(sldm.SldmError):
+        sldm.sparams(-np.eye(1) / 50.0, 50.0)
+    with pytest.raises(sldm.SldmError):
+        sldm.sparams(np.eye(2), -1.0)
