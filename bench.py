@@ -105,7 +105,7 @@ WORKLOADS["copper-wire-sio2-si-pec-1MHz-50GHz-fp64"] = dict(
     layers=[(1.0, 1.0, 0.0, 0.0), (3.9, 1.0, 0.0, 10e-6), (11.9, 1.0, 10.0, 200e-6)], z_top=0.0, bottom="pec",
     freqs=WIRE_FREQS, precision=0, tol=1e-8, maxit=6000, khat=[0.0, 0.0, -1.0], pol=[1.0, 0.0, 0.0], n_angles=0,
     e2e_steps=20)
-# Serving (BASELINE's config 4, scaled to sizes the direct Y solve serves): a seeded
+# Serving with continuous batching (scaled to sizes the direct Y solve serves): a seeded
 # catalogue of 16 models (4 spheres and 4 ellipsoids, icosphere sub 1 or 2, semi-axes
 # U[0.05, 0.2] m, eps_r U[2, 12], loss tangent U[0, 0.02]; each in free space and
 # 1.2 semi-axes above a 3-layer ground: air / 5 cm slab eps_r 4 / half-space eps_r 10,
@@ -122,7 +122,7 @@ WORKLOADS["serving-catalogue-poisson200-c64x2"] = dict(
     workers=2, max_batch=32, precision=2, budget=150 << 30, khat=[0.0, 0.0, -1.0], pol=[1.0, 0.0, 0.0],
     mesh=lambda: icosphere(1, 0.1), obj=None, mats=[(4.0, 1.0, 0.0)], bg=(1.0, 1.0, 0.0, 0.0), freq=300e6,
     n_angles=0)
-# Batched frequency sweep over uneven instances (BASELINE's config 3): 8 seeded
+# Batched mixed-precision frequency sweep over uneven instances: 8 seeded
 # instances (7 spheres/ellipsoids, icosphere sub 2 or 3, semi-axes U[0.05, 0.2] m,
 # eps_r U[2, 12], loss tangent U[0, 0.02]; one sub-4 sphere of 0.1 m, eps_r 4) in
 # free space, 16 log-spaced frequencies each from k0 a_max = 0.01 to where
