@@ -207,13 +207,11 @@ FILL_F64_PEAK_EVALS = FP64_OPS_PER_S / FP64_OPS_PER_EVAL
 FP64_OPS_PER_EVAL_REFL = 292.0
 
 
-# DRAM traffic per algorithmic byte of the HBM-streaming GEMV stage, from one
-# ncu capture of each GEMV kernel (dram__bytes_read.sum + dram__bytes_write.sum
-# of the gemv_main launch, 4 x 4 metasurface, 423,936,000 algorithmic bytes per
-# launch; summaries in profiles/gemv_main_metasurface-4x4-c64.md (one
-# right-hand side) and profiles/gemv_tile_metasurface-4x4-8angles-c64.md (8)),
-# valid while that kernel's source is unchanged (sha256 prefix of its text in
-# dense.cu).
+# DRAM traffic per algorithmic byte of the HBM-streaming main product stage, from
+# one ncu capture of the kernel (dram__bytes_read.sum + dram__bytes_write.sum of
+# the gemv_main launch, 4 x 4 metasurface, 423,936,000 algorithmic bytes per
+# launch), valid while that kernel's source is unchanged (sha256 prefix of its
+# text in csrc/<file>); for any other source the line reports traffic null.
 GEMV_TRAFFIC = {
     # main-stage launch of the 4 x 4 metasurface, 32 right-hand sides (profiles/gemm_tc_metasurface-4x4-32angles-c64x2.md)
     "gemm_tc_kernel": dict(sha="78e503ea925c5ae5", file="gemm_tc.cu",
