@@ -170,8 +170,11 @@ void sldm_last_error(char* buf, size_t len);
  * coefficients, touching-pair lists) on the host, then upload it to the
  * current device.  xyz: nv x 3 doubles; tri: nt x 3 vertex indices; obj_id: nt
  * non-decreasing object ids or NULL for one object.  Host pointers.
- * Errors: SLDM_EINVAL when an object is not a closed oriented manifold, a
- * triangle is degenerate, or obj_id is not contiguous. */
+ * Errors: SLDM_EINVAL when an object is not a closed oriented manifold, is
+ * oriented inward (its triangles' vertex order must be counter-clockwise seen
+ * from outside: the formulation takes n as the outward normal, Sec. II), shares
+ * a vertex with another object, a triangle is degenerate, or obj_id is not
+ * contiguous.  These checks run on the host before any device call. */
 int sldm_mesh_create(const double* xyz, int64_t nv, const int32_t* tri, int64_t nt,
                      const int32_t* obj_id, sldm_mesh** out);
 int sldm_mesh_info_get(const sldm_mesh* mesh, sldm_mesh_info* info);

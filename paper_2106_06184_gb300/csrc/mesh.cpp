@@ -143,6 +143,22 @@ void build_host_mesh(const double* xyz, int64_t nv, const int32_t* tri, int64_t 
   SLDM_REQUIRE(build_edges(tv, nt, hm.obj, hm.uv, hm.tplus, hm.tminus, hm.tri_edge, hm.tri_sign, dir, msg),
                SLDM_EINVAL, msg);
   hm.ne = int64_t(hm.tplus.size());
+  // outward normals: a closed oriented surface encloses the signed volume
+  // sum over its triangles of a . (b x c) / 6, positive when every normal points
+  // out (vertices taken relative to the object's first vertex against cancellation)
+  for (int64_t o = 0; o < hm.nobj; ++o) {
+    const double* r = &xyz[3 * hm.tri[3 * int64_t(hm.tri_begin[o])]];
+    double vol = 0;
+    for (int64_t t = hm.tri_begin[o]; t < hm.tri_begin[o + 1]; ++t) {
+      double p[3][3];
+      for (int i = 0; i < 3; ++i)
+        for (int d = 0; d < 3; ++d) p[i][d] = xyz[3 * hm.tri[3 * t + i] + d] - r[d];
+      vol += p[0][0] * (p[1][1] * p[2][2] - p[1][2] * p[2][1]) + p[0][1] * (p[1][2] * p[2][0] - p[1][0] * p[2][2]) +
+             p[0][2] * (p[1][0] * p[2][1] - p[1][1] * p[2][0]);
+    }
+    SLDM_REQUIRE(vol > 0, SLDM_EINVAL,
+                 "object " + std::to_string(o) + " is oriented inward (its normals enclose a negative volume)");
+  }
   {
     double acc = 0;
     for (int64_t n = 0; n < hm.ne; ++n) {
