@@ -29,6 +29,26 @@ def rcs(mesh, k0, jd, theta, phi=0.0, E0=1.0):
     return ETA0 ** 2 * np.sum(np.abs(Fperp) ** 2, axis=1) / (4 * np.pi * abs(E0) ** 2)
 
 
+def amplitude(mesh, k0, jd, rhat):
+    """Complex far-field amplitude A(rhat) of J_Delta in free space, E_s ~ A exp(-j k0 r)/r:
+    A = -eta0/(4 pi) (I - rr) . sum_n j_Delta,n N_n(rhat), one row per direction
+    (rhat: (n, 3) unit vectors).  The RCS above is 4 pi |A|^2 / |E0|^2; the
+    forward amplitude gives the extinction cross section by the optical theorem,
+    sigma_ext = -(4 pi / k0) Im(p . A(khat)) / |E0|^2 for E_inc = p E0 exp(-j k0 khat . r)
+    (the exp(+j w t) form of the theorem)."""
+    rhat = np.atleast_2d(np.asarray(rhat, float))
+    A = mesh.xyz[mesh.tri]
+    rq = Q.points(A)
+    wq = Q.weights(mesh.area)
+    Fv = np.zeros((len(rhat), 3), dtype=complex)
+    ph = np.exp(1j * k0 * np.einsum('tqd,ad->atq', rq, rhat))
+    for i in range(3):
+        fi = (rq - A[:, i][:, None, :]) * (mesh.E.tri_sign[:, i] / (2 * mesh.area))[:, None, None]
+        Fv += np.einsum('t,tq,atq,tqd->ad', jd[mesh.E.tri_edge[:, i]], wq, ph, fi)
+    Fperp = Fv - rhat * np.einsum('ad,ad->a', rhat, Fv)[:, None]
+    return -ETA0 / (4 * np.pi) * Fperp
+
+
 def rcs_layered(mesh, stack, layer, omega, jd, theta, phi=0.0, E0=1.0):
     """Bistatic RCS above a stratified background (observation in the upper half-space).
 

@@ -54,3 +54,13 @@ def rcs_eplane(k0, radius, eps_c, theta_s, mu_r=1.0):
     m = np.sqrt(np.conj(complex(eps_c)) * mu_r)
     _, S2 = amplitudes(k0 * radius, m, theta_s)
     return 4 * np.pi * np.abs(S2) ** 2 / k0 ** 2
+
+
+def efficiencies(x, m):
+    """Extinction and scattering efficiencies (Bohren & Huffman, Sec. 4.4):
+    Q_ext = (2/x^2) sum (2n+1) Re(a_n + b_n), Q_sca = (2/x^2) sum (2n+1)(|a_n|^2 + |b_n|^2);
+    cross sections are Q times pi a^2, absorption = extinction - scattering."""
+    n, a, b = coefficients(x, m)
+    q_ext = 2.0 / x ** 2 * np.sum((2 * n + 1) * np.real(a + b))
+    q_sca = 2.0 / x ** 2 * np.sum((2 * n + 1) * (np.abs(a) ** 2 + np.abs(b) ** 2))
+    return float(q_ext), float(q_sca)
