@@ -187,9 +187,14 @@ int sldm_mesh_destroy(sldm_mesh* mesh);
  * L^phi_m = L^phi(k_b)/eps_b).  Otherwise layers are listed top to bottom:
  * layer 0 is the upper half-space above z_top; each following layer is finite
  * (thickness > 0) except the last one when bottom = SLDM_BOTTOM_HALFSPACE; with
- * SLDM_BOTTOM_PEC a perfect conductor lies under the last layer.  At most 8 layers.
- * In a stratified background every object must lie strictly inside one layer l
- * (sldm_material.layer) and away from its interfaces; the external operators use
+ * SLDM_BOTTOM_PEC a perfect conductor lies under the last layer.  At most 8 layers
+ * (SLDM_ENOTSUP beyond); SLDM_EINVAL for non-positive or non-finite eps_r, mu_r, a
+ * negative or non-finite sigma, a non-finite z_top or a finite layer without a
+ * positive thickness (checked on the host, no device call).
+ * In a stratified background every object lies inside one layer l
+ * (sldm_material.layer, the same for all objects) and may rest on its interfaces
+ * (vertices on an interface to 1e-9 of the mesh size), but none crosses one
+ * (SLDM_EINVAL at assembly); the external operators use
  * the multilayer kernel of that layer (homogeneous kernel of layer l, quasistatic
  * images of the adjacent interfaces, and a remainder tabulated from Sommerfeld
  * integrals on 256 log-spaced rho x 128 points in z + z' and in |z - z'|,

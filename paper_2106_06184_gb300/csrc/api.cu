@@ -1067,9 +1067,11 @@ int sldm_stack_create(const sldm_layer* layers, int32_t nlayers, double z_top, i
   *out = nullptr;
   SLDM_REQUIRE(nlayers <= MGF_MAX_LAYERS, SLDM_ENOTSUP, "stack_create: too many layers");
   SLDM_REQUIRE(bottom == SLDM_BOTTOM_HALFSPACE || bottom == SLDM_BOTTOM_PEC, SLDM_EINVAL, "stack_create: unknown bottom");
+  SLDM_REQUIRE(std::isfinite(z_top), SLDM_EINVAL, "stack_create: z_top must be finite");
   for (int i = 0; i < nlayers; ++i) {
-    SLDM_REQUIRE(layers[i].eps_r > 0 && layers[i].mu_r > 0 && layers[i].sigma >= 0, SLDM_EINVAL,
-                 "stack_create: invalid layer material");
+    SLDM_REQUIRE(layers[i].eps_r > 0 && layers[i].mu_r > 0 && layers[i].sigma >= 0 && std::isfinite(layers[i].eps_r) &&
+                     std::isfinite(layers[i].mu_r) && std::isfinite(layers[i].sigma),
+                 SLDM_EINVAL, "stack_create: invalid layer material");
     const bool finite = i > 0 && (bottom == SLDM_BOTTOM_PEC || i < nlayers - 1);
     SLDM_REQUIRE(!finite || (layers[i].thickness > 0 && std::isfinite(layers[i].thickness)), SLDM_EINVAL,
                  "stack_create: finite layers need a positive thickness");

@@ -1,5 +1,7 @@
-"""sldm_mesh_create rejects invalid meshes on the host, before any device call,
-so these checks need no GPU: each case returns SLDM_EINVAL with its reason.
+"""sldm_mesh_create and sldm_stack_create reject invalid input on the host,
+before any device call, so these checks need no GPU: each case returns
+SLDM_EINVAL (SLDM_ENOTSUP for more layers than the multilayer kernel takes)
+with its reason.
 
 The formulation (Sec. II) takes every object as a closed surface with the
 outward normal n; RWG functions need each interior edge shared by exactly two
@@ -103,3 +105,35 @@ def test_object_with_too_few_triangles(sphere):
 
 def test_empty_mesh():
     assert "empty" in _rejected(np.zeros((0, 3)), np.zeros((0, 3), np.int32))
+
+
+def _stack_rejected(layers, code=None, **kw):
+    sl = _sl()
+    with pytest.raises(sl.SldmError) as e:
+        sl.Stack(layers, **kw)
+    assert e.value.code == (sl.EINVAL if code is None else code), str(e.value)
+    return str(e.value)
+
+
+def test_valid_stacks_need_no_device():
+    sl = _sl()
+    sl.Stack([(1.0, 1.0, 0.0, 0.0)])
+    sl.Stack([(1.0, 1.0, 0.0, 0.0), (3.9, 1.0, 0.0, 10e-6), (11.9, 1.0, 10.0, 200e-6)], z_top=0.0,
+             bottom=sl.BOTTOM_PEC)
+    sl.Stack([(1.0, 1.0, 0.0, 0.0), (2.25, 1.0, 0.0, np.inf)], bottom=sl.BOTTOM_HALFSPACE)  # half-spaces: any thickness
+
+
+def test_invalid_stacks():
+    sl = _sl()
+    air = (1.0, 1.0, 0.0, 0.0)
+    assert "invalid arguments" in _stack_rejected([])
+    for bad in ((0.0, 1.0, 0.0, 0.0), (-2.0, 1.0, 0.0, 0.0), (2.0, 0.0, 0.0, 0.0), (2.0, 1.0, -1.0, 0.0),
+                (np.nan, 1.0, 0.0, 0.0), (np.inf, 1.0, 0.0, 0.0), (2.0, 1.0, np.inf, 0.0)):
+        assert "material" in _stack_rejected([air, bad])
+    # a finite layer (between two interfaces, or any layer above a PEC bottom) needs a thickness
+    for t in (0.0, -1e-3, np.inf, np.nan):
+        assert "thickness" in _stack_rejected([air, (2.0, 1.0, 0.0, t), (4.0, 1.0, 0.0, 0.0)])
+        assert "thickness" in _stack_rejected([air, (2.0, 1.0, 0.0, t)], bottom=sl.BOTTOM_PEC)
+    assert "z_top" in _stack_rejected([air, (2.0, 1.0, 0.0, 0.0)], z_top=np.nan)
+    assert "bottom" in _stack_rejected([air], bottom=7)
+    assert "too many" in _stack_rejected([air] + [(2.0, 1.0, 0.0, 1e-3)] * 8 + [air], code=sl.ENOTSUP)
