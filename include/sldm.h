@@ -213,7 +213,19 @@ int sldm_stack_destroy(sldm_stack* stack);
  * an edge longer than 1/|Im k|, and the 6-point rule runs on each child; a fill
  * with split sources drops the pairs whose bounding spheres are more than
  * 40/|Im k| apart.  SLDM_ENOTSUP beyond 4096 children of one source.
- * per_obj: nobj materials (host).  The mesh and stack must outlive the op. */
+ * Objects that repeat an earlier object (same material, same triangles and edges
+ * in the same local order, vertices equal up to one translation) take its
+ * interior blocks and Y11, Y21; global blocks between object pairs of equal
+ * shapes at equal relative placement (and heights, in a stack) are filled once
+ * and copied (translation invariance of the kernel).
+ * per_obj: nobj materials (host).  The mesh and stack must outlive the op.
+ * Errors: SLDM_EINVAL for a non-positive frequency, a material with a
+ * non-positive or non-finite eps_r or mu_r or a negative sigma, a current device
+ * other than the mesh's, a layer index out of range or an object crossing an
+ * interface; SLDM_ENOTSUP for objects in different layers; SLDM_ENOMEM when the
+ * device or the budget of sldm_set_device_budget runs out; SLDM_ETIMEOUT when a
+ * bounded wait of the batched direct solver runs out.  On every error the call
+ * releases what it took and *out is NULL. */
 int sldm_assemble(const sldm_mesh* mesh, const sldm_stack* stack, const sldm_material* per_obj,
                   double freq_hz, const sldm_assemble_opts* opts, sldm_op** out);
 int sldm_op_info_get(const sldm_op* op, sldm_op_info* info);
@@ -258,9 +270,11 @@ int sldm_rhs_planewave(const sldm_op* op, const double* khat, const double* pol,
  * in the operator's precision (complex64 operators: FP32 Gram-Schmidt with
  * FP64 sums across threads), right-preconditioned by P of Eq. pcext (Sec. III:
  * diagonals of the blocks, with the analytic block inverse through the Schur
- * complement of the charge block, formed per object at assembly).  Up to 8
+ * complement of the charge block, formed per object at assembly).  Up to 32
  * right-hand sides run in lockstep, each with its own Krylov basis, sharing one
- * multi-RHS pass over the blocks per step; more are taken 8 at a time.
+ * multi-RHS pass over the blocks per step (complex64 operators: on the tensor
+ * cores from sldm_op_info.tc_from right-hand sides on, else passes of up to 8 on
+ * the CUDA cores); more are taken 32 at a time.
  * b, x: N x nrhs complex128 column-major.
  * The iteration runs on the length-scaled system Dr Z Dc (Dr = diag(1, 1, l),
  * Dc = diag(1/l, 1, l) on the blocks [j; e; u], l = the mesh's mean edge
@@ -368,10 +382,16 @@ int sldm_kbar_noalloc(const sldm_mesh* mesh, int32_t obj, double k_re, double k_
 
 /* Kernel timers (profiling aid, Sec. IV "CPU time breakdown" counterpart):
  * when enabled, the library records a CUDA event pair around each launch of
- * its main kernels, on the launch's stream, under a fixed name
- * ("fill_L_bulk", "fill_L_touch", "fill_K_bulk", "fill_K_touch", "lu_update",
- * "lu_pivot", "lu_backsub", "gemv", "apply", "gmres_iter").  Timings are
- * accumulated per name; reading them synchronises on the recorded events.
+ * its main kernels and stages, on the launch's stream, under a fixed name
+ * (stages: "assemble", "mgf_tables", "fill_reflected", "apply", "gmres",
+ * "gram_schmidt", "precond", "farfield", "nested_y"; kernels: "fill_L_bulk",
+ * "fill_L_touch", "fill_L_split", "fill_K_bulk", "fill_K_touch", "fill_K_split",
+ * "fill_reflected_bulk", "copy_blocks", "lu_coop", "lu_blocked",
+ * "nested_inverse", "gemm_tc" and the product stages "gemv_main", "gemv_y",
+ * "gemv_pc", and "gemv_main_f64acc", "gemv_y_f64acc" for the FP64-accurate
+ * residual products; names nest, so
+ * a stage's time includes its kernels').  Timings are accumulated per name;
+ * reading them synchronises on the recorded events.
  * Timed regions pair up within their calling thread, so several threads (the
  * serving workers, each on its own stream) may be timed at once; a region's time
  * then includes whatever else shared the device. */
@@ -381,9 +401,11 @@ int sldm_timers_reset(void);
 int sldm_timer_get(const char* name, double* total_ms, int64_t* count);
 /* Algorithmic work of the launches timed under `name` since the last reset (the
  * units a roofline divides by the time): "gemv*" the matrix bytes streamed
- * (every entry of every block once per launch, low parts included);
- * "fill_L_bulk", "fill_K_bulk" the Green's-function evaluations (36 per
- * non-touching triangle pair).  0 for names without a count. */
+ * (every entry of every block once per pass, low parts included);
+ * "fill_L_bulk", "fill_K_bulk", "fill_reflected_bulk" the Green's-function
+ * evaluations (36 per triangle pair the kernel integrates); "gram_schmidt" the
+ * Krylov-basis bytes that the two dot and two update passes of classical
+ * Gram-Schmidt twice stream.  0 for names without a count. */
 int sldm_timer_units(const char* name, double* units);
 /* Comma-separated names with recorded launches, NUL-terminated, truncated to len. */
 int sldm_timer_names(char* buf, size_t len);

@@ -1100,8 +1100,9 @@ int sldm_assemble(const sldm_mesh* m, const sldm_stack* st, const sldm_material*
   SLDM_CUDA(cudaGetDevice(&dev));
   SLDM_REQUIRE(dev == m->device, SLDM_EINVAL, "assemble: current device differs from the mesh's device");
   for (int64_t o = 0; o < m->h.nobj; ++o)
-    SLDM_REQUIRE(per_obj[o].eps_r > 0 && per_obj[o].mu_r > 0 && per_obj[o].sigma >= 0, SLDM_EINVAL,
-                 "assemble: invalid object material");
+    SLDM_REQUIRE(per_obj[o].eps_r > 0 && per_obj[o].mu_r > 0 && per_obj[o].sigma >= 0 &&
+                     std::isfinite(per_obj[o].eps_r) && std::isfinite(per_obj[o].mu_r) && std::isfinite(per_obj[o].sigma),
+                 SLDM_EINVAL, "assemble: invalid object material");
   auto* op = new sldm_op();
   try {
     op->mesh = m;
