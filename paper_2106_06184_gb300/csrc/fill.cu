@@ -15,6 +15,7 @@
 #include <algorithm>
 #include <cmath>
 #include <mutex>
+#include <new>
 
 #include "fill_dev.cuh"
 
@@ -1284,6 +1285,12 @@ extern "C" int sldm_kbar_noalloc(const sldm_mesh* m, int32_t obj, double k_re, d
   } catch (const sldm::Error& e) {
     sldm::set_error(e.msg);
     return e.code;
+  } catch (const std::bad_alloc&) {
+    sldm::set_error("kbar_noalloc: host allocation failed");
+    return SLDM_ENOMEM;
+  } catch (const std::exception& e) {
+    sldm::set_error(e.what());
+    return SLDM_EINVAL;
   }
   return SLDM_OK;
 }

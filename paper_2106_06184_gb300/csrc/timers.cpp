@@ -1,6 +1,8 @@
 // Named CUDA-event timers for the library's launches (sldm_timers_* in sldm.h).
 #include <atomic>
 #include <cstring>
+#include <exception>
+#include <string>
 #include <map>
 #include <mutex>
 
@@ -104,6 +106,15 @@ void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 }  // namespace sldm
 
+namespace {
+// host-side failure inside a C entry point (an allocation of the bookkeeping):
+// reported as a status, never thrown across the C ABI
+int host_failure(const std::exception& e) {
+  sldm::set_error(std::string("timers: ") + e.what());
+  return SLDM_ENOMEM;
+}
+}  // namespace
+
 extern "C" {
 
 int sldm_launch_count(int64_t* out) {
@@ -119,44 +130,60 @@ int sldm_timers_enable(int32_t on) {
 }
 
 int sldm_timers_reset(void) {
-  std::lock_guard<std::mutex> l(sldm::g_mu);
-  sldm::resolve_locked();
-  sldm::g_acc.clear();
-  sldm::g_units.clear();
-  return SLDM_OK;
+  try {
+    std::lock_guard<std::mutex> l(sldm::g_mu);
+    sldm::resolve_locked();
+    sldm::g_acc.clear();
+    sldm::g_units.clear();
+    return SLDM_OK;
+  } catch (const std::exception& e) {
+    return host_failure(e);
+  }
 }
 
 int sldm_timer_units(const char* name, double* units) {
   if (!name || !units) return SLDM_EINVAL;
-  std::lock_guard<std::mutex> l(sldm::g_mu);
-  auto it = sldm::g_units.find(name);
-  *units = it == sldm::g_units.end() ? 0.0 : it->second;
-  return SLDM_OK;
+  try {
+    std::lock_guard<std::mutex> l(sldm::g_mu);
+    auto it = sldm::g_units.find(name);
+    *units = it == sldm::g_units.end() ? 0.0 : it->second;
+    return SLDM_OK;
+  } catch (const std::exception& e) {
+    return host_failure(e);
+  }
 }
 
 int sldm_timer_get(const char* name, double* total_ms, int64_t* count) {
-  std::lock_guard<std::mutex> l(sldm::g_mu);
-  sldm::resolve_locked();
-  auto it = sldm::g_acc.find(name ? name : "");
-  if (total_ms) *total_ms = it == sldm::g_acc.end() ? 0.0 : it->second.first;
-  if (count) *count = it == sldm::g_acc.end() ? 0 : it->second.second;
-  return SLDM_OK;
+  try {
+    std::lock_guard<std::mutex> l(sldm::g_mu);
+    sldm::resolve_locked();
+    auto it = sldm::g_acc.find(name ? name : "");
+    if (total_ms) *total_ms = it == sldm::g_acc.end() ? 0.0 : it->second.first;
+    if (count) *count = it == sldm::g_acc.end() ? 0 : it->second.second;
+    return SLDM_OK;
+  } catch (const std::exception& e) {
+    return host_failure(e);
+  }
 }
 
 int sldm_timer_names(char* buf, size_t len) {
-  std::lock_guard<std::mutex> l(sldm::g_mu);
-  sldm::resolve_locked();
-  std::string s;
-  for (auto& kv : sldm::g_acc) {
-    if (!s.empty()) s += ",";
-    s += kv.first;
+  try {
+    std::lock_guard<std::mutex> l(sldm::g_mu);
+    sldm::resolve_locked();
+    std::string s;
+    for (auto& kv : sldm::g_acc) {
+      if (!s.empty()) s += ",";
+      s += kv.first;
+    }
+    if (buf && len) {
+      size_t n = std::min(len - 1, s.size());
+      std::memcpy(buf, s.data(), n);
+      buf[n] = 0;
+    }
+    return SLDM_OK;
+  } catch (const std::exception& e) {
+    return host_failure(e);
   }
-  if (buf && len) {
-    size_t n = std::min(len - 1, s.size());
-    std::memcpy(buf, s.data(), n);
-    buf[n] = 0;
-  }
-  return SLDM_OK;
 }
 
 }  // extern "C"

@@ -59,3 +59,25 @@ def test_port_sparams_is_host_math_matching_the_oracle(lib):
         sldm.sparams(-np.eye(1) / 50.0, 50.0)
     with pytest.raises(sldm.SldmError):
         sldm.sparams(np.eye(2), -1.0)
+
+
+def test_host_bookkeeping_calls_without_gpu(lib):
+    """Timers, launch counter, device-memory budget and fault injection are host
+    bookkeeping: they answer without a GPU and reject invalid arguments."""
+    c = ctypes
+    u, t, n = c.c_double(-1), c.c_double(-1), c.c_int64(-1)
+    assert lib.sldm_timers_reset() == 0
+    assert lib.sldm_timer_units(b"gemv_main", c.byref(u)) == 0 and u.value == 0.0
+    assert lib.sldm_timer_units(None, c.byref(u)) == -1
+    assert lib.sldm_timer_get(b"no_such_timer", c.byref(t), c.byref(n)) == 0 and (t.value, n.value) == (0.0, 0)
+    buf = c.create_string_buffer(16)
+    assert lib.sldm_timer_names(buf, c.c_size_t(16)) == 0 and buf.value == b""
+    assert lib.sldm_launch_count(None) == -1
+    assert lib.sldm_launch_count(c.byref(n)) == 0 and n.value >= 0
+    assert lib.sldm_set_device_budget(c.c_int64(-1)) == -1
+    assert lib.sldm_set_device_budget(c.c_int64(0)) == 0
+    assert lib.sldm_device_bytes(None) == -1
+    assert lib.sldm_device_bytes(c.byref(n)) == 0 and n.value == 0
+    assert lib.sldm_test_inject(99, 1) == -1 and lib.sldm_test_inject(1, -1) == -1
+    assert lib.sldm_test_inject(1, 0) == 0
+    assert lib.sldm_set_tc_policy(0) == 0 and lib.sldm_set_tc_policy(34) == -1
