@@ -198,6 +198,8 @@ def test_mie_published_sample():
     qsca = 2 / x ** 2 * np.sum((2 * n + 1) * (np.abs(a) ** 2 + np.abs(b) ** 2))
     qback = abs(np.sum((2 * n + 1) * (-1.0) ** n * (a - b))) ** 2 / x ** 2
     assert abs(qext - vals["qext"]) < 1e-4 and abs(qsca - vals["qsca"]) < 1e-4 and abs(qback - vals["qback"]) < 1e-4
+    qe, qs = mie.efficiencies(x, complex(vals["m_re"], vals["m_im"]))
+    assert abs(qe - vals["qext"]) < 1e-4 and abs(qs - vals["qsca"]) < 1e-4
 
 
 def test_mie_rayleigh_limit():
