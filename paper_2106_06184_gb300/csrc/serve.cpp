@@ -320,7 +320,7 @@ void sldm_server::worker_loop() {
             const int i = cols[c0 + c].first, j = cols[c0 + c].second;
             double2* dst = reinterpret_cast<double2*>(batch[i]->x) + int64_t(j) * N;
             SLDM_CUDA(cudaMemcpyAsync(dst, dx.p + int64_t(c) * N, size_t(N) * sizeof(double2), cudaMemcpyDeviceToHost, s));
-            iters[i] += si.iters;
+            if (c == 0 || cols[c0 + c - 1].first != i) iters[i] += si.iters;  // once per solve that carries request i
             relres[i] = std::max(relres[i], si.relres);
           }
           SLDM_CUDA(cudaStreamSynchronize(s));
