@@ -184,10 +184,8 @@ L2_FLUSH_BYTES = 512 << 20  # larger than the 129 MB L2
 
 # Roofline denominators: MEASURED_PEAKS.json when present, else the recorded
 # fallback measurement.  ALU peaks derive from unit counts x maximum SM clock:
-# FP32: 152 SMs x 128 lanes x 2 flop x 2.07 GHz; FP64: 152 SMs x 2 FMA x 2 flop x 2.07 GHz
-# (1.26 TFLOP/s, the part's nominal 1.25).
+# FP64: 152 SMs x 2 FMA x 2 flop x 2.07 GHz (1.26 TFLOP/s, the part's nominal 1.25).
 FALLBACK_HBM_GBS = 6800.0
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # Fill rooflines, in Green's-function evaluations per second (36 per triangle pair).
 # FP32 fill: bound by the special-function unit, 16 operations per SM per clock,
@@ -310,30 +308,6 @@ class ClockSampler:
                     reasons.add(n)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
-
-
-# ----------------------------------------------------------------------------- roofline bookkeeping
-def matvec_bytes(ne, nt, obj_sizes, esz):
-    """Algorithmic bytes of one structured product: every dense block read once
-    (global L^A_m, L^phi_m; per object L^A, K, Y11 (ne_o^2), L^phi (nt_o^2), Y21 ((nt_o - 1) ne_o))."""
-    loc = sum(3 * e * e + t * t + (t - 1) * e for e, t in obj_sizes)
-    return (ne * ne + nt * nt + loc) * esz
-
-
-def gemv_split(ne, nt, obj_sizes, esz):
-    """Bytes read by the two GEMV launches of one product (Y11/Y21 stage, then the rest)."""
-    s1 = sum(e * e + (t - 1) * e for e, t in obj_sizes) * esz
-    return s1, matvec_bytes(ne, nt, obj_sizes, esz) - s1
-
-
-def lu_update_bytes(n, nrhs):
-    """Algorithmic bytes of all trailing updates of an unblocked LU with nrhs right-hand sides
-    (read + write of every updated complex128 entry)."""
-    tot = 0
-    for k in range(n - 1):
-        r = n - k - 1
-        tot += r * (r + nrhs) * 32
-    return tot, n - 1
 
 
 # ----------------------------------------------------------------------------- ranks
