@@ -1657,16 +1657,6 @@ void copy_scaled(const void* src, int64_t n, double alpha, void* dst, cudaStream
   SLDM_CUDA(cudaGetLastError());
 }
 
-// scale a dense block by a complex factor
-template <class C>
-__global__ void scale_kernel(C* A, int64_t n, double sr, double si) {
-  int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (t >= n) return;
-  double ar = A[t].x, ai = A[t].y;
-  A[t].x = decltype(A[t].x)(ar * sr - ai * si);
-  A[t].y = decltype(A[t].y)(ar * si + ai * sr);
-}
-
 #define INST(C)                                                                                                         \
   template void build_Ml<C>(const sldm_mesh*, int, double, const void*, int64_t, const void*, int64_t, const void*,     \
                             int64_t, const double*, C*, C*, cudaStream_t);                                              \
