@@ -16,6 +16,11 @@ quadrature  6-point degree-4 Dunavant rule on triangles
 singular    closed-form potential integrals over a flat triangle (1/R, R, grad 1/R)
 fill        L^(A), L^(phi), K-bar, Gram I_x and plane-wave excitation (Sec. II-B, II-C)
 system      per-object M_l, Y11/Y21, the final SLDM system and its dense solution (Sec. II-D, II-E)
-farfield    far field / radar cross section of J_Delta in free space (Sec. IV-A)
+farfield    far field / radar cross section of J_Delta in free space (Sec. IV-A) and above
+            a stack (by reciprocity with the stack's plane waves); complex far-field amplitude
+layered     multilayer kernel of one layer: stack reflections, quasistatic images, Sommerfeld
+            tables and their bilinear remainder, reflected fill, plane wave through the stack
+            (Sec. II-C, IV)
+ports       delta-gap edge ports, port currents, Y and S parameters (Sec. IV-B, IV-C)
 mie         Mie series of a dielectric sphere (independent pin for Sec. IV-A)
 """
