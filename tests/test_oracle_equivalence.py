@@ -1,5 +1,5 @@
-"""Two routes to the scattered far field of the oracle's solution (Sec. II; the
-cross-check of the survey's reading R11).
+"""Two routes to the scattered far field of the oracle's solution (Sec. II and
+the RCS of Sec. IV-A).
 
 The single-layer method radiates the equivalent current J_Delta = H - H_eq
 alone (H_eq = Y11 E from the equivalent configuration, Eq. Yeqdef).  Love's
