@@ -6,7 +6,6 @@
 #include <algorithm>
 #include <array>
 #include <cmath>
-#include <map>
 #include <unordered_map>
 
 #include "internal.h"
@@ -79,6 +78,80 @@ bool build_edges(const std::vector<int64_t>& tv, int64_t nt, const std::vector<i
     uv[2 * n + 1] = keys[n].v;
     DirInfo p = dir[key2(keys[n].u, keys[n].v)];
     DirInfo q = dir[key2(keys[n].v, keys[n].u)];
+    tp[n] = p.t;
+    tm[n] = q.t;
+    tedge[size_t(p.t) * 3 + p.i] = int32_t(n);
+    tsign[size_t(p.t) * 3 + p.i] = 1;
+    tedge[size_t(q.t) * 3 + q.i] = int32_t(n);
+    tsign[size_t(q.t) * 3 + q.i] = -1;
+  }
+  return true;
+}
+
+// The same edges, numbering and T+/T- as build_edges, found by sorting the
+// directed edges instead of hashing them (no map is kept): used for the
+// barycentric refinement, whose 18 nt directed edges dominate the topology.
+bool build_edges_sorted(const std::vector<int64_t>& tv, int64_t nt, const std::vector<int32_t>& tobj,
+                        std::vector<int64_t>& uv, std::vector<int32_t>& tp, std::vector<int32_t>& tm,
+                        std::vector<int32_t>& tedge, std::vector<int8_t>& tsign, std::string& msg) {
+  struct D {
+    uint64_t key;  // (min, max) vertex pair
+    int32_t t;
+    int8_t i, fwd;  // local edge index; 1 when the triangle runs min -> max
+  };
+  std::vector<D> d(size_t(nt) * 3);
+  for (int64_t t = 0; t < nt; ++t)
+    for (int i = 0; i < 3; ++i) {
+      const int64_t a = tv[t * 3 + (i + 1) % 3], b = tv[t * 3 + (i + 2) % 3];
+      d[size_t(t) * 3 + i] = D{a < b ? key2(a, b) : key2(b, a), int32_t(t), int8_t(i), int8_t(a < b)};
+    }
+  std::sort(d.begin(), d.end(), [](const D& x, const D& y) {
+    if (x.key != y.key) return x.key < y.key;
+    return x.fwd > y.fwd;  // the forward (T+) entry first
+  });
+  const size_t nd = d.size();
+  // a directed edge used twice: two entries of one pair in the same direction
+  for (size_t k = 0; k + 1 < nd; ++k)
+    if (d[k].key == d[k + 1].key && d[k].fwd == d[k + 1].fwd) {
+      msg = "mesh is not an oriented 2-manifold (directed edge used twice)";
+      return false;
+    }
+  // closed: every pair appears once in each direction
+  struct E {
+    int32_t obj;
+    int64_t u, v;
+    size_t k;  // index of the forward entry in d
+  };
+  std::vector<E> edges;
+  edges.reserve(nd / 2);
+  for (size_t k = 0; k < nd;) {
+    if (k + 1 >= nd || d[k + 1].key != d[k].key) {
+      msg = "mesh is not closed (edge with one triangle)";
+      return false;
+    }
+    if (tobj[d[k].t] != tobj[d[k + 1].t]) {
+      msg = "an edge joins two objects (objects must be disjoint)";
+      return false;
+    }
+    edges.push_back({tobj[d[k].t], int64_t(d[k].key >> 32), int64_t(d[k].key & 0xffffffffu), k});
+    k += 2;
+  }
+  std::sort(edges.begin(), edges.end(), [](const E& x, const E& y) {
+    if (x.obj != y.obj) return x.obj < y.obj;
+    if (x.u != y.u) return x.u < y.u;
+    return x.v < y.v;
+  });
+  const size_t ne = edges.size();
+  uv.assign(ne * 2, 0);
+  tp.assign(ne, 0);
+  tm.assign(ne, 0);
+  tedge.assign(size_t(nt) * 3, -1);
+  tsign.assign(size_t(nt) * 3, 0);
+  for (size_t n = 0; n < ne; ++n) {
+    const D& p = d[edges[n].k];      // u -> v: T+
+    const D& q = d[edges[n].k + 1];  // v -> u: T-
+    uv[2 * n] = edges[n].u;
+    uv[2 * n + 1] = edges[n].v;
     tp[n] = p.t;
     tm[n] = q.t;
     tedge[size_t(p.t) * 3 + p.i] = int32_t(n);
@@ -191,8 +264,7 @@ void build_host_mesh(const double* xyz, int64_t nv, const int32_t* tri, int64_t 
   }
   std::vector<int64_t> buv;
   std::vector<int32_t> btp, btm;
-  std::unordered_map<uint64_t, DirInfo> bdir;
-  SLDM_REQUIRE(build_edges(bv, 6 * nt, bobj, buv, btp, btm, hm.btri_edge, hm.btri_sign, bdir, msg), SLDM_EINVAL,
+  SLDM_REQUIRE(build_edges_sorted(bv, 6 * nt, bobj, buv, btp, btm, hm.btri_edge, hm.btri_sign, msg), SLDM_EINVAL,
                "barycentric mesh: " + msg);
   hm.nbe = int64_t(btp.size());
   hm.bedge_begin.assign(size_t(hm.nobj) + 1, 0);
@@ -299,17 +371,43 @@ void build_host_mesh(const double* xyz, int64_t nv, const int32_t* tri, int64_t 
   }
 
   // ---------------- I_x sparsity and contribution lists
-  // row -> map col -> contributions (tri, child, i, j, coef)
-  std::vector<std::vector<std::pair<int32_t, double>>> bc_rows(static_cast<size_t>(hm.nbe));  // bary edge -> (n, coef)
-  for (int64_t n = 0; n < hm.ne; ++n)
-    for (int32_t q = hm.bc_ptr[n]; q < hm.bc_ptr[n + 1]; ++q) bc_rows[hm.bc_row[q]].push_back({int32_t(n), hm.bc_val[q]});
+  // row m (an RWG) -> its nonzero columns n (BC functions), each with the list of
+  // contributions (triangle, child, i, j, coefficient) that the device sums
+  // C transposed (CSR by barycentric edge, BC columns in increasing order): bary edge -> (n, coef)
+  std::vector<int32_t> rb_ptr(size_t(hm.nbe) + 1, 0), rb_n(hm.bc_row.size());
+  std::vector<double> rb_val(hm.bc_row.size());
+  for (int32_t r : hm.bc_row) ++rb_ptr[size_t(r) + 1];
+  for (int64_t k = 0; k < hm.nbe; ++k) rb_ptr[k + 1] += rb_ptr[k];
+  {
+    std::vector<int32_t> fill(rb_ptr.begin(), rb_ptr.end() - 1);
+    for (int64_t n = 0; n < hm.ne; ++n)
+      for (int32_t q = hm.bc_ptr[n]; q < hm.bc_ptr[n + 1]; ++q) {
+        const int32_t at = fill[hm.bc_row[q]]++;
+        rb_n[at] = int32_t(n);
+        rb_val[at] = hm.bc_val[q];
+      }
+  }
   hm.ix_ptr.assign(size_t(hm.ne) + 1, 0);
   hm.ix_col.clear();
   hm.ixc_ptr.assign(1, 0);
   hm.ixc_tri.clear(); hm.ixc_child.clear(); hm.ixc_i.clear(); hm.ixc_j.clear(); hm.ixc_coef.clear();
-  struct Contrib { int32_t t, c, i, j; double coef; };
+  // per row m: the contributions in generation order, grouped by column with a
+  // stable sort (so each column keeps the order in which they were generated)
+  struct Contrib { int32_t n, t, c, i, j; double coef; };
+  std::vector<Contrib> row;
+  {
+    size_t total = 0;  // contributions of every row, to size the outputs once
+    for (int64_t m = 0; m < hm.ne; ++m)
+      for (int32_t t : {hm.tplus[m], hm.tminus[m]})
+        for (int k = 0; k < 18; ++k) {
+          const int32_t be = hm.btri_edge[size_t(6 * t) * 3 + k];
+          total += size_t(rb_ptr[be + 1] - rb_ptr[be]);
+        }
+    for (auto* v : {&hm.ixc_tri, &hm.ixc_child, &hm.ixc_i, &hm.ixc_j}) v->reserve(total);
+    hm.ixc_coef.reserve(total);
+  }
   for (int64_t m = 0; m < hm.ne; ++m) {
-    std::map<int32_t, std::vector<Contrib>> row;
+    row.clear();
     for (int32_t t : {hm.tplus[m], hm.tminus[m]}) {
       int i = -1;
       for (int q = 0; q < 3; ++q)
@@ -318,21 +416,24 @@ void build_host_mesh(const double* xyz, int64_t nv, const int32_t* tri, int64_t 
         int32_t c = 6 * t + k;
         for (int j = 0; j < 3; ++j) {
           int32_t be = hm.btri_edge[size_t(c) * 3 + j];
-          for (auto& nc : bc_rows[be]) row[nc.first].push_back({t, c, i, j, nc.second});
+          for (int32_t q = rb_ptr[be]; q < rb_ptr[be + 1]; ++q) row.push_back({rb_n[q], t, c, i, j, rb_val[q]});
         }
       }
     }
-    for (auto& kv : row) {
-      hm.ix_col.push_back(kv.first);
-      for (auto& cb : kv.second) {
-        hm.ixc_tri.push_back(cb.t);
-        hm.ixc_child.push_back(cb.c);
-        hm.ixc_i.push_back(cb.i);
-        hm.ixc_j.push_back(cb.j);
-        hm.ixc_coef.push_back(cb.coef);
+    std::stable_sort(row.begin(), row.end(), [](const Contrib& x, const Contrib& y) { return x.n < y.n; });
+    for (size_t q = 0; q < row.size(); ++q) {
+      const Contrib& cb = row[q];
+      if (q == 0 || cb.n != row[q - 1].n) {
+        if (q > 0) hm.ixc_ptr.push_back(int32_t(hm.ixc_tri.size()));
+        hm.ix_col.push_back(cb.n);
       }
-      hm.ixc_ptr.push_back(int32_t(hm.ixc_tri.size()));
+      hm.ixc_tri.push_back(cb.t);
+      hm.ixc_child.push_back(cb.c);
+      hm.ixc_i.push_back(cb.i);
+      hm.ixc_j.push_back(cb.j);
+      hm.ixc_coef.push_back(cb.coef);
     }
+    if (!row.empty()) hm.ixc_ptr.push_back(int32_t(hm.ixc_tri.size()));
     hm.ix_ptr[m + 1] = int32_t(hm.ix_col.size());
   }
 }
